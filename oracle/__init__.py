@@ -1,0 +1,218 @@
+"""CPU oracle for the full-amplitude state-vector method (QPanda, arXiv 2212.14201).
+
+TEST INFRASTRUCTURE ONLY.  The product package never imports this module; the test
+suite, the smoke check and the benchmark's CPU-baseline leg do.  The arithmetic
+lives in ``qsim_oracle.c`` (plain C, IEEE double, no fusion or tiling); this file
+compiles it with gcc and wraps it with ctypes.
+
+Every function states the paper passage it follows in the C source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qsim_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOMEM, EUNSUPPORTED = 0, -1, -2, -5
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, OpenMP for the gate loop)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i32, i64, u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+            sig = {
+                "or_gate_matrix": (i32, [P, i32, P, P, P, P]),
+                "or_apply_gate": (i32, [P, i32, P, P]),
+                "or_apply_circuit": (i32, [P, i32, P, i64, P]),
+                "or_apply_matrix": (i32, [P, i32, P, i32, u64, P]),
+                "or_init_zero": (None, [P, i32]),
+                "or_probs": (None, [P, i32, P]),
+                "or_marginal": (i32, [P, i32, P, i32, P]),
+                "or_expect_z": (None, [P, i32, P]),
+                "or_expect_pauli": (i32, [P, i32, P, i64, P]),
+                "or_apply_pauli_sum": (i32, [P, i32, P, i64, P]),
+                "or_splitmix64": (u64, [u64, u64]),
+                "or_block_prefix": (i32, [P, i32, P]),
+                "or_sample": (i32, [P, i32, u64, i64, P]),
+                "or_adjoint_grad": (i32, [i32, P, i64, P, i64, P, i64, P, P]),
+                "or_energy": (i32, [i32, P, i64, P, P, i64, P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _chk(rc: int, what: str):
+    if rc != OK:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data
+
+
+def _state(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.complex128:
+        a = a.view(np.float64)
+    assert a.dtype == np.float64
+    return a
+
+
+def zero_state(n: int) -> np.ndarray:
+    """|0...0> as interleaved float64."""
+    s = np.empty(2 << n, dtype=np.float64)
+    _load().or_init_zero(s.ctypes.data, n)
+    return s
+
+
+def gate_matrix(g: np.ndarray, n: int, params=None):
+    """(target, control mask, 2x2 complex matrix) of one record."""
+    lib = _load()
+    t = ctypes.c_int()
+    cm = ctypes.c_uint64()
+    m = np.empty(8, dtype=np.float64)
+    g = np.ascontiguousarray(np.atleast_1d(g))
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    _chk(lib.or_gate_matrix(_ptr(g), n, _ptr(pr), ctypes.byref(t), ctypes.byref(cm), m.ctypes.data), "gate_matrix")
+    return t.value, cm.value, m.view(np.complex128).reshape(2, 2)
+
+
+def apply_circuit(state: np.ndarray, n: int, gates: np.ndarray, params=None) -> np.ndarray:
+    """Apply every record in order, in place; returns the state."""
+    state = _state(state)
+    gates = np.ascontiguousarray(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    _chk(_load().or_apply_circuit(state.ctypes.data, n, _ptr(gates), len(gates), _ptr(pr)), "apply_circuit")
+    return state
+
+
+def run(n: int, gates: np.ndarray, params=None) -> np.ndarray:
+    """Final state of `gates` from |0...0> (interleaved float64)."""
+    return apply_circuit(zero_state(n), n, gates, params)
+
+
+def apply_matrix(state: np.ndarray, n: int, targets, mat: np.ndarray, ctrl_mask: int = 0) -> np.ndarray:
+    state = _state(state)
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    m = np.ascontiguousarray(mat)
+    if m.dtype == np.complex128:
+        m = m.view(np.float64)
+    m = np.ascontiguousarray(m.reshape(-1), dtype=np.float64)
+    _chk(_load().or_apply_matrix(state.ctypes.data, n, t.ctypes.data, len(t), ctrl_mask, m.ctypes.data), "apply_matrix")
+    return state
+
+
+def probs(state: np.ndarray, n: int) -> np.ndarray:
+    state = _state(state)
+    p = np.empty(1 << n, dtype=np.float64)
+    _load().or_probs(state.ctypes.data, n, p.ctypes.data)
+    return p
+
+
+def marginal(state: np.ndarray, n: int, qubits) -> np.ndarray:
+    state = _state(state)
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    out = np.empty(1 << len(q), dtype=np.float64)
+    _chk(_load().or_marginal(state.ctypes.data, n, q.ctypes.data, len(q), out.ctypes.data), "marginal")
+    return out
+
+
+def expect_z(state: np.ndarray, n: int) -> np.ndarray:
+    state = _state(state)
+    out = np.empty(n, dtype=np.float64)
+    _load().or_expect_z(state.ctypes.data, n, out.ctypes.data)
+    return out
+
+
+def expect_pauli(state: np.ndarray, n: int, terms: np.ndarray) -> float:
+    state = _state(state)
+    terms = np.ascontiguousarray(terms)
+    out = ctypes.c_double()
+    _chk(_load().or_expect_pauli(state.ctypes.data, n, _ptr(terms), len(terms), ctypes.byref(out)), "expect_pauli")
+    return out.value
+
+
+def apply_pauli_sum(state: np.ndarray, n: int, terms: np.ndarray) -> np.ndarray:
+    state = _state(state)
+    terms = np.ascontiguousarray(terms)
+    out = np.empty_like(state)
+    _chk(_load().or_apply_pauli_sum(state.ctypes.data, n, _ptr(terms), len(terms), out.ctypes.data), "apply_pauli_sum")
+    return out
+
+
+def splitmix64(seed: int, s: int) -> int:
+    return int(_load().or_splitmix64(seed, s))
+
+
+def block_prefix(state: np.ndarray, n: int) -> np.ndarray:
+    state = _state(state)
+    L = min(1024, 1 << n)
+    E = np.empty((1 << n) // L + 1, dtype=np.float64)
+    _load().or_block_prefix(state.ctypes.data, n, E.ctypes.data)
+    return E
+
+
+def sample(state: np.ndarray, n: int, seed: int, shots: int) -> np.ndarray:
+    state = _state(state)
+    out = np.empty(shots, dtype=np.uint64)
+    _chk(_load().or_sample(state.ctypes.data, n, seed, shots, out.ctypes.data), "sample")
+    return out
+
+
+def adjoint_grad(n: int, gates: np.ndarray, params: np.ndarray, terms: np.ndarray):
+    """(energy, gradient) by the adjoint recursion."""
+    gates = np.ascontiguousarray(gates)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    terms = np.ascontiguousarray(terms)
+    e = ctypes.c_double()
+    g = np.empty(len(params), dtype=np.float64)
+    _chk(_load().or_adjoint_grad(n, _ptr(gates), len(gates), params.ctypes.data, len(params),
+                                 _ptr(terms), len(terms), ctypes.byref(e), g.ctypes.data), "adjoint_grad")
+    return e.value, g
+
+
+def energy(n: int, gates: np.ndarray, params: np.ndarray, terms: np.ndarray) -> float:
+    gates = np.ascontiguousarray(gates)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    terms = np.ascontiguousarray(terms)
+    e = ctypes.c_double()
+    _chk(_load().or_energy(n, _ptr(gates), len(gates), params.ctypes.data, _ptr(terms), len(terms),
+                           ctypes.byref(e)), "energy")
+    return e.value
+
+
+def as_complex(state: np.ndarray) -> np.ndarray:
+    return _state(state).view(np.complex128)

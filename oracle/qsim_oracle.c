@@ -1,0 +1,504 @@
+/*
+ * Plain CPU oracle for the full-amplitude (Schroedinger) state-vector method of
+ * QPanda (arXiv 2212.14201).  TEST INFRASTRUCTURE ONLY: the product library never
+ * links, loads or calls this file; only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg do.
+ *
+ * Everything here is written to be checked against the paper by eye: one gate is
+ * one pass over the amplitude array with the textbook 2x2 (or 2^k x 2^k) matrix, in
+ * IEEE double precision, with no fusion, tiling or reordering.  It shares no code,
+ * header or constant table with the CUDA library.
+ *
+ * Conventions (the paper is silent on them; the readings are listed in the design
+ * notes): qubit q is bit q of the basis index (qubit 0 = least significant); a
+ * state is 2^n complex doubles stored interleaved (re, im); CNOT/CZ/CR take
+ * (control, target) in that order, as in the paper's listings.
+ *
+ * Compile with -ffp-contract=off: probabilities are re*re + im*im with two
+ * separately rounded products, which the canonical sampler relies on.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL -1
+#define OR_ENOMEM -2
+#define OR_EUNSUPPORTED -5
+
+enum {
+  OR_I = 0, OR_H = 1, OR_X = 2, OR_Y = 3, OR_Z = 4, OR_S = 5, OR_T = 6,
+  OR_RX = 7, OR_RY = 8, OR_RZ = 9, OR_U3 = 10, OR_P = 11,
+  OR_CNOT = 12, OR_CZ = 13, OR_CR = 14
+};
+
+typedef struct {
+  int32_t type, q0, q1, param_idx;
+  uint64_t ctrl_mask;
+  double p[3];
+  int32_t dagger, reserved;
+} or_gate;
+
+typedef struct {
+  double coef;
+  uint64_t xmask, zmask;
+} or_pauli;
+
+typedef struct {
+  double re, im;
+} cplx;
+
+static cplx c_make(double re, double im) { cplx z = {re, im}; return z; }
+static cplx c_add(cplx a, cplx b) { return c_make(a.re + b.re, a.im + b.im); }
+static cplx c_mul(cplx a, cplx b) { return c_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static cplx c_conj(cplx a) { return c_make(a.re, -a.im); }
+static cplx c_expi(double t) { return c_make(cos(t), sin(t)); }
+
+/* ------------------------------------------------------------------------- */
+/* Gate matrices (the paper's gate set: the keyword list of the API and the   */
+/* "Performance of basic gates" experiment).  Textbook forms (Nielsen &       */
+/* Chuang); U3 in the OpenQASM form.  m is row-major: m[0]=U00 m[1]=U01        */
+/* m[2]=U10 m[3]=U11.                                                          */
+/* ------------------------------------------------------------------------- */
+static int gate_matrix_1q(int type, double th, double ph, double la, cplx m[4]) {
+  const double r = 1.0 / sqrt(2.0);
+  double c = cos(th / 2.0), s = sin(th / 2.0);
+  switch (type) {
+    case OR_I: m[0] = c_make(1, 0); m[1] = c_make(0, 0); m[2] = c_make(0, 0); m[3] = c_make(1, 0); break;
+    case OR_H: m[0] = c_make(r, 0); m[1] = c_make(r, 0); m[2] = c_make(r, 0); m[3] = c_make(-r, 0); break;
+    case OR_X: case OR_CNOT:
+      m[0] = c_make(0, 0); m[1] = c_make(1, 0); m[2] = c_make(1, 0); m[3] = c_make(0, 0); break;
+    case OR_Y: m[0] = c_make(0, 0); m[1] = c_make(0, -1); m[2] = c_make(0, 1); m[3] = c_make(0, 0); break;
+    case OR_Z: case OR_CZ:
+      m[0] = c_make(1, 0); m[1] = c_make(0, 0); m[2] = c_make(0, 0); m[3] = c_make(-1, 0); break;
+    case OR_S: m[0] = c_make(1, 0); m[1] = c_make(0, 0); m[2] = c_make(0, 0); m[3] = c_make(0, 1); break;
+    case OR_T: m[0] = c_make(1, 0); m[1] = c_make(0, 0); m[2] = c_make(0, 0); m[3] = c_expi(M_PI / 4.0); break;
+    case OR_RX: /* exp(-i th X / 2) */
+      m[0] = c_make(c, 0); m[1] = c_make(0, -s); m[2] = c_make(0, -s); m[3] = c_make(c, 0); break;
+    case OR_RY: /* exp(-i th Y / 2) */
+      m[0] = c_make(c, 0); m[1] = c_make(-s, 0); m[2] = c_make(s, 0); m[3] = c_make(c, 0); break;
+    case OR_RZ: /* exp(-i th Z / 2) */
+      m[0] = c_expi(-th / 2.0); m[1] = c_make(0, 0); m[2] = c_make(0, 0); m[3] = c_expi(th / 2.0); break;
+    case OR_U3: {
+      cplx el = c_expi(la), ep = c_expi(ph), epl = c_expi(ph + la);
+      m[0] = c_make(c, 0);
+      m[1] = c_make(-el.re * s, -el.im * s);
+      m[2] = c_make(ep.re * s, ep.im * s);
+      m[3] = c_make(epl.re * c, epl.im * c);
+      break;
+    }
+    case OR_P: case OR_CR:
+      m[0] = c_make(1, 0); m[1] = c_make(0, 0); m[2] = c_make(0, 0); m[3] = c_expi(th); break;
+    default: return OR_EINVAL;
+  }
+  return OR_OK;
+}
+
+static int is_two_qubit(int type) { return type == OR_CNOT || type == OR_CZ || type == OR_CR; }
+
+/* Target qubit and full control mask of one record (CNOT/CZ/CR: q0 is the
+ * control, q1 the target). */
+static int qubits_of(const or_gate* g, int n, int* target, uint64_t* cmask) {
+  if (g->type < OR_I || g->type > OR_CR) return OR_EINVAL;
+  if (g->q0 < 0 || g->q0 >= n) return OR_EINVAL;
+  uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  if (g->ctrl_mask & ~full) return OR_EINVAL;
+  uint64_t cm = g->ctrl_mask;
+  int t;
+  if (is_two_qubit(g->type)) {
+    if (g->q1 < 0 || g->q1 >= n || g->q1 == g->q0) return OR_EINVAL;
+    t = g->q1;
+    cm |= 1ull << g->q0;
+  } else {
+    t = g->q0;
+  }
+  if (cm & (1ull << t)) return OR_EINVAL;
+  *target = t;
+  *cmask = cm;
+  return OR_OK;
+}
+
+/* Resolve one record into (target, control mask, 2x2 matrix); dagger gives the
+ * conjugate transpose (the paper's set_dagger, Section "Quantum circuit
+ * visualization" listing). */
+static int resolve(const or_gate* g, int n, const double* params, int* target, uint64_t* cmask, cplx m[4]) {
+  int rc = qubits_of(g, n, target, cmask);
+  if (rc) return rc;
+  double th = g->p[0];
+  if (g->param_idx >= 0) {
+    if (!params) return OR_EINVAL;
+    th = params[g->param_idx];
+  }
+  rc = gate_matrix_1q(g->type, th, g->p[1], g->p[2], m);
+  if (rc) return rc;
+  if (g->dagger) {
+    cplx a = m[0], b = m[1], c = m[2], d = m[3];
+    m[0] = c_conj(a); m[1] = c_conj(c); m[2] = c_conj(b); m[3] = c_conj(d);
+  }
+  return OR_OK;
+}
+
+int or_gate_matrix(const or_gate* g, int n, const double* params, int* target, uint64_t* cmask, double* m8) {
+  cplx m[4];
+  int rc = resolve(g, n, params, target, cmask, m);
+  if (rc) return rc;
+  for (int i = 0; i < 4; ++i) { m8[2 * i] = m[i].re; m8[2 * i + 1] = m[i].im; }
+  return OR_OK;
+}
+
+/* One gate = one sweep over the state (Section "High-performance simulation":
+ * the circuit is an iteration of gates; Section "Multi-simulation methods": the
+ * Schroedinger method updates the state vector by each gate).  Every pair
+ * (x, x | 2^t) with bit t of x clear and all control bits of x set is replaced by
+ * U applied to it.  A gate with controls is the paper's ".control" form. */
+static void apply_2x2(cplx* psi, int n, int t, uint64_t cmask, const cplx m[4]) {
+  const int64_t N = (int64_t)1 << n;
+  const int64_t tb = (int64_t)1 << t;
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < N; ++x) {
+    if ((x & tb) != 0) continue;
+    if (((uint64_t)x & cmask) != cmask) continue;
+    cplx a0 = psi[x], a1 = psi[x | tb];
+    psi[x] = c_add(c_mul(m[0], a0), c_mul(m[1], a1));
+    psi[x | tb] = c_add(c_mul(m[2], a0), c_mul(m[3], a1));
+  }
+}
+
+int or_apply_gate(double* state, int n, const or_gate* g, const double* params) {
+  int t; uint64_t cm; cplx m[4];
+  int rc = resolve(g, n, params, &t, &cm, m);
+  if (rc) return rc;
+  apply_2x2((cplx*)state, n, t, cm, m);
+  return OR_OK;
+}
+
+int or_apply_circuit(double* state, int n, const or_gate* gates, int64_t ng, const double* params) {
+  for (int64_t k = 0; k < ng; ++k) {
+    int rc = or_apply_gate(state, n, &gates[k], params);
+    if (rc) return rc;
+  }
+  return OR_OK;
+}
+
+/* Dense k-qubit matrix gate (the "unitary matrix" gates of 1-3 qubits timed in
+ * "Performance of basic gates", and the unitary blocks that circuit fusion
+ * produces, Section "Quantum circuit fusion").  targets[j] is bit j of the
+ * matrix's row/column index; mat is 2^k x 2^k row-major, interleaved. */
+int or_apply_matrix(double* state, int n, const int* targets, int k, uint64_t cmask, const double* mat) {
+  if (k < 1 || k > 10 || k > n) return OR_EINVAL;
+  uint64_t tmask = 0;
+  for (int j = 0; j < k; ++j) {
+    if (targets[j] < 0 || targets[j] >= n || (tmask >> targets[j]) & 1) return OR_EINVAL;
+    tmask |= 1ull << targets[j];
+  }
+  uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  if ((cmask & ~full) || (cmask & tmask)) return OR_EINVAL;
+  const int64_t N = (int64_t)1 << n;
+  const int d = 1 << k;
+  const cplx* M = (const cplx*)mat;
+  cplx* psi = (cplx*)state;
+#pragma omp parallel
+  {
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * d);
+    cplx* v = (cplx*)malloc(sizeof(cplx) * d);
+#pragma omp for schedule(static)
+    for (int64_t x = 0; x < N; ++x) {
+      if ((uint64_t)x & tmask) continue;
+      if (((uint64_t)x & cmask) != cmask) continue;
+      for (int j = 0; j < d; ++j) {
+        int64_t y = x;
+        for (int b = 0; b < k; ++b)
+          if ((j >> b) & 1) y |= (int64_t)1 << targets[b];
+        idx[j] = y;
+        v[j] = psi[y];
+      }
+      for (int i = 0; i < d; ++i) {
+        cplx acc = c_make(0, 0);
+        for (int j = 0; j < d; ++j) acc = c_add(acc, c_mul(M[i * d + j], v[j]));
+        psi[idx[i]] = acc;
+      }
+    }
+    free(idx);
+    free(v);
+  }
+  return OR_OK;
+}
+
+/* |0...0> (all initial states are |0>, Section "Compared with existing libs"). */
+void or_init_zero(double* state, int n) {
+  memset(state, 0, sizeof(double) * 2 * ((size_t)1 << n));
+  state[0] = 1.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reductions: probability list, marginal probabilities, <Z_i>, Pauli sums     */
+/* (the paper's probability / expectation tools, Section "A variety of        */
+/* convenient tools"; prob_run_list / prob_run_dict in the API keyword list). */
+/* ------------------------------------------------------------------------- */
+static double prob_of(cplx a) { return a.re * a.re + a.im * a.im; }
+
+void or_probs(const double* state, int n, double* p) {
+  const cplx* psi = (const cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  for (int64_t x = 0; x < N; ++x) p[x] = prob_of(psi[x]);
+}
+
+/* out[k] = sum of p_x over x whose bits at qubits[0..nq-1] spell k (qubits[j] is
+ * bit j of k).  Summed in ascending x. */
+int or_marginal(const double* state, int n, const int* qubits, int nq, double* out) {
+  if (nq < 0 || nq > n) return OR_EINVAL;
+  for (int j = 0; j < nq; ++j) {
+    if (qubits[j] < 0 || qubits[j] >= n) return OR_EINVAL;
+    for (int i = 0; i < j; ++i) if (qubits[i] == qubits[j]) return OR_EINVAL;
+  }
+  const cplx* psi = (const cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  memset(out, 0, sizeof(double) * ((size_t)1 << nq));
+  for (int64_t x = 0; x < N; ++x) {
+    int64_t k = 0;
+    for (int j = 0; j < nq; ++j) k |= ((x >> qubits[j]) & 1) << j;
+    out[k] += prob_of(psi[x]);
+  }
+  return OR_OK;
+}
+
+/* <Z_i> = sum_x p_x (1 - 2 x_i), for every qubit i. */
+void or_expect_z(const double* state, int n, double* out) {
+  const cplx* psi = (const cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  for (int i = 0; i < n; ++i) out[i] = 0.0;
+  for (int64_t x = 0; x < N; ++x) {
+    double p = prob_of(psi[x]);
+    for (int i = 0; i < n; ++i) out[i] += ((x >> i) & 1) ? -p : p;
+  }
+}
+
+/* Pauli string P = (x, z masks; a Y where both are set) acting on a basis state:
+ * P|x> = i^{#Y} (-1)^{popcount(x & z)} |x ^ xmask>.  Uses Y|b> = i(-1)^b |1-b>. */
+static cplx pauli_phase(const or_pauli* t, uint64_t x) {
+  int ny = __builtin_popcountll(t->xmask & t->zmask) & 3;
+  int neg = __builtin_popcountll(x & t->zmask) & 1;
+  static const double ire[4] = {1, 0, -1, 0}, iim[4] = {0, 1, 0, -1};
+  cplx ph = c_make(ire[ny], iim[ny]);
+  if (neg) ph = c_make(-ph.re, -ph.im);
+  return ph;
+}
+
+static int check_terms(int n, const or_pauli* terms, int64_t nt) {
+  uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  for (int64_t k = 0; k < nt; ++k)
+    if ((terms[k].xmask | terms[k].zmask) & ~full) return OR_EINVAL;
+  return OR_OK;
+}
+
+/* <psi|H|psi> for H = sum_k coef_k P_k (the paper's Pauli operator and qop
+ * expectation, Sections "Structure of QPanda" and "Variational quantum circuit"):
+ * sum_k coef_k Re sum_x conj(psi_{x^xmask}) phase_k(x) psi_x. */
+int or_expect_pauli(const double* state, int n, const or_pauli* terms, int64_t nt, double* out) {
+  int rc = check_terms(n, terms, nt);
+  if (rc) return rc;
+  const cplx* psi = (const cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  double e = 0.0;
+  for (int64_t k = 0; k < nt; ++k) {
+    cplx s = c_make(0, 0);
+    for (int64_t x = 0; x < N; ++x) {
+      cplx v = c_mul(pauli_phase(&terms[k], (uint64_t)x), psi[x]);
+      s = c_add(s, c_mul(c_conj(psi[x ^ (int64_t)terms[k].xmask]), v));
+    }
+    e += terms[k].coef * s.re;
+  }
+  *out = e;
+  return OR_OK;
+}
+
+/* out = H psi (out must not alias state). */
+int or_apply_pauli_sum(const double* state, int n, const or_pauli* terms, int64_t nt, double* out) {
+  int rc = check_terms(n, terms, nt);
+  if (rc) return rc;
+  const cplx* psi = (const cplx*)state;
+  cplx* o = (cplx*)out;
+  const int64_t N = (int64_t)1 << n;
+  for (int64_t x = 0; x < N; ++x) o[x] = c_make(0, 0);
+  for (int64_t k = 0; k < nt; ++k) {
+    cplx cf = c_make(terms[k].coef, 0);
+    for (int64_t x = 0; x < N; ++x) {
+      cplx v = c_mul(cf, c_mul(pauli_phase(&terms[k], (uint64_t)x), psi[x]));
+      int64_t y = x ^ (int64_t)terms[k].xmask;
+      o[y] = c_add(o[y], v);
+    }
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Measurement sampling (measure_all / run_with_configuration in the API      */
+/* keyword list, the Measure gate of the QProg listings).                      */
+/*                                                                             */
+/* Canonical sampler (the paper fixes no algorithm; this is the reading both   */
+/* sides implement):                                                           */
+/*   u_s   = SplitMix64 output number s (0-based) of the stream seeded `seed`,  */
+/*           mapped to [0,1) as (z >> 11) * 2^-53;                              */
+/*   p_x   = re*re + im*im (two rounded products, one rounded sum);             */
+/*   L     = min(1024, 2^n); block b holds x in [bL, bL + L);                   */
+/*   S_b(j)= p_{bL} + ... + p_{bL+j}, summed left to right;                     */
+/*   E_0 = 0, E_{b+1} = E_b + S_b(L-1)      (left to right over blocks);        */
+/*   C_x   = E_b + S_b(x - bL);                                                 */
+/*   shot s -> the smallest x with C_x > u_s; if there is none (rounding left   */
+/*   the total <= u_s) the largest x with p_x > 0.                              */
+/* C is non-decreasing in x, so the block is the first b with E_{b+1} > u_s.    */
+/* ------------------------------------------------------------------------- */
+uint64_t or_splitmix64(uint64_t seed, uint64_t s) {
+  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static double u01(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+
+int or_block_prefix(const double* state, int n, double* E /* nblocks + 1 */) {
+  const cplx* psi = (const cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  const int64_t L = N < 1024 ? N : 1024;
+  const int64_t nb = N / L;
+  E[0] = 0.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    double S = 0.0;
+    for (int64_t j = 0; j < L; ++j) S += prob_of(psi[b * L + j]);
+    E[b + 1] = E[b] + S;
+  }
+  return OR_OK;
+}
+
+int or_sample(const double* state, int n, uint64_t seed, int64_t shots, uint64_t* out) {
+  const cplx* psi = (const cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  const int64_t L = N < 1024 ? N : 1024;
+  const int64_t nb = N / L;
+  double* E = (double*)malloc(sizeof(double) * (nb + 1));
+  if (!E) return OR_ENOMEM;
+  or_block_prefix(state, n, E);
+  int64_t last_nz = 0;
+  for (int64_t x = N - 1; x >= 0; --x)
+    if (prob_of(psi[x]) > 0.0) { last_nz = x; break; }
+  for (int64_t s = 0; s < shots; ++s) {
+    double u = u01(or_splitmix64(seed, (uint64_t)s));
+    /* first block b with E[b+1] > u (binary search over the non-decreasing E) */
+    int64_t lo = 0, hi = nb;  /* answer in [lo, hi]; hi == nb means none */
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (E[mid + 1] > u) hi = mid; else lo = mid + 1;
+    }
+    if (lo == nb) { out[s] = (uint64_t)last_nz; continue; }
+    int64_t b = lo;
+    double S = 0.0;
+    int64_t pick = b * L + L - 1;
+    for (int64_t j = 0; j < L; ++j) {
+      S += prob_of(psi[b * L + j]);
+      if (E[b] + S > u) { pick = b * L + j; break; }
+    }
+    out[s] = (uint64_t)pick;
+  }
+  free(E);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint differentiation for parametrised rotations (the paper's VQC /      */
+/* VQG_RX..RZ / qop, Section "Variational quantum circuit", does not say how  */
+/* gradients are taken; this is the adjoint recursion of Jones & Gacon,       */
+/* arXiv:2009.02823).  For a gate with dU/dtheta = -(i/2) G U:                 */
+/*   dE/dtheta_k = Im <lambda_k| G_k |psi_k>,                                  */
+/* psi_k = U_k ... U_1 |0>, lambda_k = U_{k+1}^dag ... U_G^dag H psi_G.        */
+/* Generators: RX -> X, RY -> Y, RZ -> Z, P / CR -> -2|1><1| on the target,    */
+/* each times the projector onto the control bits; a dagger flips the sign.    */
+/* ------------------------------------------------------------------------- */
+static int generator_of(const or_gate* g, int n, int* target, uint64_t* cmask, cplx G[4]) {
+  int rc = qubits_of(g, n, target, cmask);
+  if (rc) return rc;
+  double sgn = g->dagger ? -1.0 : 1.0;
+  switch (g->type) {
+    case OR_RX: G[0] = c_make(0, 0); G[1] = c_make(sgn, 0); G[2] = c_make(sgn, 0); G[3] = c_make(0, 0); break;
+    case OR_RY: G[0] = c_make(0, 0); G[1] = c_make(0, -sgn); G[2] = c_make(0, sgn); G[3] = c_make(0, 0); break;
+    case OR_RZ: G[0] = c_make(sgn, 0); G[1] = c_make(0, 0); G[2] = c_make(0, 0); G[3] = c_make(-sgn, 0); break;
+    case OR_P: case OR_CR:
+      G[0] = c_make(0, 0); G[1] = c_make(0, 0); G[2] = c_make(0, 0); G[3] = c_make(-2.0 * sgn, 0); break;
+    default: return OR_EUNSUPPORTED;
+  }
+  return OR_OK;
+}
+
+/* <a| G_(target, cmask) |b>, G acting on pairs whose control bits are all set and
+ * as 0 elsewhere (the generator of a controlled rotation). */
+static cplx braket_gen(const cplx* a, const cplx* b, int n, int t, uint64_t cmask, const cplx G[4]) {
+  const int64_t N = (int64_t)1 << n;
+  const int64_t tb = (int64_t)1 << t;
+  cplx s = c_make(0, 0);
+  for (int64_t x = 0; x < N; ++x) {
+    if ((x & tb) != 0) continue;
+    if (((uint64_t)x & cmask) != cmask) continue;
+    cplx b0 = b[x], b1 = b[x | tb];
+    cplx g0 = c_add(c_mul(G[0], b0), c_mul(G[1], b1));
+    cplx g1 = c_add(c_mul(G[2], b0), c_mul(G[3], b1));
+    s = c_add(s, c_mul(c_conj(a[x]), g0));
+    s = c_add(s, c_mul(c_conj(a[x | tb]), g1));
+  }
+  return s;
+}
+
+int or_adjoint_grad(int n, const or_gate* gates, int64_t ng, const double* params, int64_t np,
+                    const or_pauli* terms, int64_t nt, double* energy, double* grad) {
+  const int64_t N = (int64_t)1 << n;
+  int rc = check_terms(n, terms, nt);
+  if (rc) return rc;
+  for (int64_t k = 0; k < ng; ++k) {
+    if (gates[k].param_idx >= np) return OR_EINVAL;
+    if (gates[k].param_idx >= 0 && gates[k].type != OR_RX && gates[k].type != OR_RY &&
+        gates[k].type != OR_RZ && gates[k].type != OR_P && gates[k].type != OR_CR)
+      return OR_EUNSUPPORTED;
+  }
+  cplx* psi = (cplx*)malloc(sizeof(cplx) * N);
+  cplx* lam = (cplx*)malloc(sizeof(cplx) * N);
+  if (!psi || !lam) { free(psi); free(lam); return OR_ENOMEM; }
+  or_init_zero((double*)psi, n);
+  rc = or_apply_circuit((double*)psi, n, gates, ng, params);
+  if (rc) { free(psi); free(lam); return rc; }
+  or_apply_pauli_sum((const double*)psi, n, terms, nt, (double*)lam);
+  double e = 0.0;
+  for (int64_t x = 0; x < N; ++x) e += c_mul(c_conj(psi[x]), lam[x]).re;
+  *energy = e;
+  for (int64_t j = 0; j < np; ++j) grad[j] = 0.0;
+  for (int64_t k = ng - 1; k >= 0; --k) {
+    const or_gate* g = &gates[k];
+    if (g->param_idx >= 0) {
+      int t; uint64_t cm; cplx G[4];
+      rc = generator_of(g, n, &t, &cm, G);
+      if (rc) { free(psi); free(lam); return rc; }
+      cplx s = braket_gen(lam, psi, n, t, cm, G);
+      grad[g->param_idx] += s.im;
+    }
+    /* step both vectors back through U_k: apply U_k^dagger */
+    or_gate inv = *g;
+    inv.dagger = !g->dagger;
+    or_apply_gate((double*)psi, n, &inv, params);
+    or_apply_gate((double*)lam, n, &inv, params);
+  }
+  free(psi);
+  free(lam);
+  return OR_OK;
+}
+
+/* Energy only (used for parameter-shift and finite-difference pins). */
+int or_energy(int n, const or_gate* gates, int64_t ng, const double* params,
+              const or_pauli* terms, int64_t nt, double* energy) {
+  const int64_t N = (int64_t)1 << n;
+  double* psi = (double*)malloc(sizeof(double) * 2 * N);
+  if (!psi) return OR_ENOMEM;
+  or_init_zero(psi, n);
+  int rc = or_apply_circuit(psi, n, gates, ng, params);
+  if (!rc) rc = or_expect_pauli(psi, n, terms, nt, energy);
+  free(psi);
+  return rc;
+}

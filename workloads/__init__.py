@@ -1,0 +1,234 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module only *draws* inputs: gate programs (as packed records), angle vectors,
+Pauli-sum descriptors and qubit counts.  It contains no gate matrix, no amplitude
+arithmetic and no reduction, so neither side of a parity test can borrow method
+arithmetic from it.
+
+Record layout (56 bytes, little-endian, 8-byte aligned), the wire format both the
+oracle and the CUDA library read:
+
+    int32  type       gate code (GATE_CODES below)
+    int32  q0         target of a 1-qubit gate; control of CNOT / CZ / CR
+    int32  q1         target of CNOT / CZ / CR; -1 otherwise
+    int32  param_idx  >= 0: theta is params[param_idx]; -1: theta is p[0]
+    uint64 ctrl_mask  extra control qubits (bit q set: qubit q must be |1>)
+    f64    p[3]       theta, phi, lambda
+    int32  dagger     1: apply the adjoint of the gate
+    int32  reserved   0
+
+Pauli term layout (24 bytes): f64 coef, uint64 xmask, uint64 zmask; a qubit with
+both bits set carries a Y.
+
+Random draws use SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) with the double
+mapping u = (x >> 11) * 2^-53, so the same seed gives the same program everywhere.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Gate codes of the record format (the paper's gate set, Section "Structure of
+# QPanda" keyword list and the "Performance of basic gates" experiment, plus P,
+# the one-qubit phase gate that CR controls).
+GATE_CODES = {
+    "I": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6,
+    "RX": 7, "RY": 8, "RZ": 9, "U3": 10, "P": 11,
+    "CNOT": 12, "CZ": 13, "CR": 14,
+}
+ONE_QUBIT = ("H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "U3")
+TWO_QUBIT = ("CNOT", "CZ", "CR")
+ANGLED = ("RX", "RY", "RZ", "U3", "P", "CR")
+
+GATE_DTYPE = np.dtype([
+    ("type", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("param_idx", "<i4"),
+    ("ctrl_mask", "<u8"), ("p", "<f8", (3,)), ("dagger", "<i4"), ("reserved", "<i4"),
+], align=True)
+assert GATE_DTYPE.itemsize == 56
+
+PAULI_DTYPE = np.dtype([("coef", "<f8"), ("xmask", "<u8"), ("zmask", "<u8")], align=True)
+assert PAULI_DTYPE.itemsize == 24
+
+_M64 = (1 << 64) - 1
+_GAMMA = 0x9E3779B97F4A7C15
+
+
+class SplitMix64:
+    """Sequential SplitMix64 stream (Steele, Lea & Flood 2014)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _M64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + _GAMMA) & _M64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def below(self, k: int) -> int:
+        """Integer in [0, k) (floor of a uniform double; k is small)."""
+        return min(int(self.uniform() * k), k - 1)
+
+    def angle(self) -> float:
+        return self.uniform() * (2.0 * np.pi)
+
+
+def gate(name: str, q0: int, q1: int = -1, theta: float = 0.0, phi: float = 0.0,
+         lam: float = 0.0, ctrl_mask: int = 0, param_idx: int = -1, dagger: int = 0):
+    """One record as a tuple in GATE_DTYPE field order."""
+    return (GATE_CODES[name], q0, q1, param_idx, ctrl_mask, (theta, phi, lam), dagger, 0)
+
+
+def pack(records) -> np.ndarray:
+    return np.array(list(records), dtype=GATE_DTYPE)
+
+
+def _distinct(rng: SplitMix64, n: int, k: int):
+    out = []
+    while len(out) < k:
+        q = rng.below(n)
+        if q not in out:
+            out.append(q)
+    return out
+
+
+def _draw_gate(rng: SplitMix64, n: int, name: str):
+    if name in TWO_QUBIT:
+        c, t = _distinct(rng, n, 2)
+        theta = rng.angle() if name == "CR" else 0.0
+        return gate(name, c, t, theta=theta)
+    (t,) = _distinct(rng, n, 1)
+    if name == "U3":
+        return gate(name, t, theta=rng.angle(), phi=rng.angle(), lam=rng.angle())
+    if name in ANGLED:
+        return gate(name, t, theta=rng.angle())
+    return gate(name, t)
+
+
+def random_circuit(n: int, n_gates: int, seed: int, two_qubit_prob: float | None = None) -> np.ndarray:
+    """Random program over {H,X,Y,Z,S,T,RX,RY,RZ,U3,CNOT,CZ,CR}.
+
+    two_qubit_prob None: each gate uniform over the 13 types.  Otherwise a gate is
+    two-qubit with that probability (uniform over CNOT, CZ, CR) and else uniform over
+    the ten one-qubit types.  Qubits are distinct and uniform (control drawn first);
+    angles are uniform in [0, 2*pi).
+    """
+    rng = SplitMix64(seed)
+    recs = []
+    names13 = ONE_QUBIT + TWO_QUBIT
+    for _ in range(n_gates):
+        if n < 2:
+            name = ONE_QUBIT[rng.below(len(ONE_QUBIT))]
+        elif two_qubit_prob is None:
+            name = names13[rng.below(len(names13))]
+        elif rng.uniform() < two_qubit_prob:
+            name = TWO_QUBIT[rng.below(3)]
+        else:
+            name = ONE_QUBIT[rng.below(len(ONE_QUBIT))]
+        recs.append(_draw_gate(rng, n, name))
+    return pack(recs)
+
+
+def layered_u3_cz(n: int, depth: int, seed: int) -> np.ndarray:
+    """Depth-`depth` layered circuit: U3(theta,phi,lambda ~ U[0,2pi)) on every qubit,
+    then CZ on brickwork neighbour pairs -- (2j, 2j+1) on even layers, (2j+1, 2j+2)
+    on odd layers.  n=30, depth=20 gives 600 U3 + 290 CZ."""
+    rng = SplitMix64(seed)
+    recs = []
+    for layer in range(depth):
+        for q in range(n):
+            recs.append(gate("U3", q, theta=rng.angle(), phi=rng.angle(), lam=rng.angle()))
+        start = 0 if layer % 2 == 0 else 1
+        for a in range(start, n - 1, 2):
+            recs.append(gate("CZ", a, a + 1))
+    return pack(recs)
+
+
+def hea_ansatz(n: int, layers: int) -> tuple[np.ndarray, int]:
+    """Hardware-efficient ansatz: per layer RY(theta) on every qubit, RZ(theta) on
+    every qubit, then the CNOT ring CNOT(control=(i+1) mod n, target=i), i = 0..n-1.
+    Every rotation reads its own parameter; returns (records, n_params)."""
+    recs = []
+    k = 0
+    for _ in range(layers):
+        for name in ("RY", "RZ"):
+            for q in range(n):
+                recs.append(gate(name, q, param_idx=k))
+                k += 1
+        if n >= 2:
+            for i in range(n):
+                c = (i + 1) % n
+                if c != i:
+                    recs.append(gate("CNOT", c, i))
+    return pack(recs), k
+
+
+def uniform_angles(count: int, seed: int) -> np.ndarray:
+    rng = SplitMix64(seed)
+    return np.array([rng.angle() for _ in range(count)], dtype=np.float64)
+
+
+def zz_chain(n: int, coef: float = 1.0) -> np.ndarray:
+    """sum_{i=0}^{n-2} Z_i Z_{i+1} (open chain)."""
+    return np.array([(coef, 0, (1 << i) | (1 << (i + 1))) for i in range(n - 1)], dtype=PAULI_DTYPE)
+
+
+def tfim(n: int, h: float = 0.7) -> np.ndarray:
+    """Transverse-field Ising, open chain: sum_i Z_i Z_{i+1} + h sum_i X_i."""
+    zz = [(1.0, 0, (1 << i) | (1 << (i + 1))) for i in range(n - 1)]
+    xx = [(h, 1 << i, 0) for i in range(n)]
+    return np.array(zz + xx, dtype=PAULI_DTYPE)
+
+
+def random_paulis(n: int, n_terms: int, seed: int) -> np.ndarray:
+    """Random Pauli strings with uniform coefficients in [-1, 1)."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(n_terms):
+        xm = zm = 0
+        for q in range(n):
+            k = rng.below(4)  # 0 I, 1 X, 2 Y, 3 Z
+            if k in (1, 2):
+                xm |= 1 << q
+            if k in (2, 3):
+                zm |= 1 << q
+        out.append((2.0 * rng.uniform() - 1.0, xm, zm))
+    return np.array(out, dtype=PAULI_DTYPE)
+
+
+def batch_qubit_counts(n_sets: int, seed: int, lo: int = 10, hi: int = 20) -> np.ndarray:
+    """Qubit count per parameter set, uniform over lo..hi inclusive."""
+    rng = SplitMix64(seed)
+    return np.array([lo + rng.below(hi - lo + 1) for _ in range(n_sets)], dtype=np.int32)
+
+
+def random_state(n: int, seed: int) -> np.ndarray:
+    """Unnormalised complex128 vector with entries uniform in [-1,1) x [-1,1)i,
+    scaled by 2^{-n/2}; returned as interleaved float64 (re, im)."""
+    rng = SplitMix64(seed)
+    N = 1 << n
+    v = np.empty(2 * N, dtype=np.float64)
+    scale = 2.0 ** (-n / 2.0)
+    for i in range(2 * N):
+        v[i] = (2.0 * rng.uniform() - 1.0) * scale
+    return v
+
+
+def random_state_fast(n: int, seed: int) -> np.ndarray:
+    """Same distribution as random_state but drawn with numpy's PCG64 (for large n)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    return (g.random(2 << n) * 2.0 - 1.0) * 2.0 ** (-n / 2.0)
+
+
+def random_matrix(k: int, seed: int) -> np.ndarray:
+    """Dense 2^k x 2^k complex matrix (row-major, interleaved re/im), entries uniform
+    in [-1,1) + [-1,1)i scaled by 2^{-k/2}; not unitary."""
+    rng = SplitMix64(seed)
+    d = 1 << k
+    m = np.empty(2 * d * d, dtype=np.float64)
+    for i in range(2 * d * d):
+        m[i] = (2.0 * rng.uniform() - 1.0) * 2.0 ** (-k / 2.0)
+    return m
