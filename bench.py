@@ -1,0 +1,376 @@
+"""Benchmark of the full-amplitude hot path on the n=30 layered circuit.
+
+Workload: n=30 complex128 state (16 GiB) from |0...0>, 20 layers of U3 (angles
+uniform in [0, 2pi), seed 1) on every qubit followed by CZ on brickwork
+neighbour pairs (even layers (2j,2j+1), odd layers (2j+1,2j+2)): 600 U3 + 290 CZ.
+One step = reset to |0>, apply the circuit (fused plan; plain per-gate apply is
+timed beside it), the squared norm, and 1e6 measurement samples (seed 11).
+Metric: amp-updates/s = (gates x 2^n) / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the state does not shard
+without a collective; see the design notes) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+METRIC = "amp-updates/s & HBM GB/s (n=30, fused vs plain); batched VQE grad evals/s"
+UNIT = "amp-updates/s"
+SHOTS = 1_000_000
+SAMPLE_SEED = 11
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=30, help="qubits (30 is the benchmark workload)")
+    ap.add_argument("--depth", type=int, default=20)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-gate arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_for(kernel_kind: int):
+    """DRAM bytes per launch from a committed ncu summary, if its kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    ent = d.get(str(kernel_kind))
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if h != ent["sha256"]:
+        return None
+    return ent["bytes_per_launch_full"]
+
+
+def roofline(records, hbm_peak_gbs):
+    """Dominant kernel class by total device time; algorithmic bytes and flops per launch."""
+    by = {}
+    for r in records:
+        d = by.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0})
+        d["ms"] += r["ms"]
+        d["launches"] += 1
+        rw = 1 if r["kind"] == 20 else 2   # reductions read only; gate kernels read and write
+        d["bytes"] += r["items"] * 16.0 * rw
+        d["flops"] += r["flops"]
+    kind, d = max(by.items(), key=lambda kv: kv[1]["ms"])
+    per_ms = d["ms"] / d["launches"]
+    bpl = d["bytes"] / d["launches"]
+    fpl = d["flops"] / d["launches"]
+    t_hbm = bpl / (hbm_peak_gbs * 1e9)
+    t_fp = fpl / FP64_PEAK_FLOPS
+    total = sum(v["ms"] for v in by.values())
+    if t_fp > t_hbm:
+        ach = fpl / (per_ms * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s (fp64)",
+               "frac": ach / (FP64_PEAK_FLOPS / 1e12)}
+    else:
+        ach = bpl / (per_ms * 1e-3) / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm_peak_gbs, "unit": "GB/s", "frac": ach / hbm_peak_gbs}
+    out.update({"kernel_kind": kind, "launches": d["launches"], "avg_launch_ms": per_ms,
+                "share_of_kernel_time": d["ms"] / total if total else None,
+                "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": fpl,
+                "traffic": traffic_for(kind)})
+    return out
+
+
+def cpu_oracle_sample(n: int, gates: np.ndarray, budget_s: float = 20.0):
+    """Oracle as it stands on the host cores: the first gates of the same circuit at
+    the same n (the state is 2^n complex doubles), amp-updates/s."""
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    psi = oracle.zero_state(n)
+    done = 0
+    t0 = time.perf_counter()
+    for k in range(len(gates)):
+        oracle.apply_circuit(psi, n, gates[k:k + 1])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    del psi
+    return {"value": done * float(1 << n) / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle", "sample": f"first {done} of {len(gates)} gates at n={n} ({dt:.1f} s)"}
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    gates = w.layered_u3_cz(args.n, args.depth, 1)
+    times = []
+    samp = None
+    for i in range(args.warmup + args.steps):
+        samp = cpu_oracle_sample(args.n, gates, budget_s=15.0 if i >= args.warmup else 3.0)
+        if i >= args.warmup:
+            times.append(samp["value"])
+    v = statistics.median(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"layered U3+CZ brickwork, n={args.n}, depth {args.depth}", "n": args.n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": samp["cores"], "kind": "oracle",
+                             "sample": samp["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    import paper_2212_14201_gb300 as q
+    q.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    gates = w.layered_u3_cz(n, args.depth, 1)
+    ng = len(gates)
+    hbm_peak, peak_src = peaks()
+
+    h = q.qs_alloc(n, stream)
+    norm_out = torch.empty(1, dtype=torch.float64, device="cuda")
+    samples = torch.empty(SHOTS, dtype=torch.int64, device="cuda")
+    plan = None
+    plan_stats = None
+    try:
+        plan = q.qs_plan_create(n, gates, q.PLAN_GREEDY, 5)
+        plan_stats = q.qs_plan_get_stats(plan)
+    except q.QsimError:
+        plan = None
+
+    def step(p):
+        q.qs_set_zero(h)
+        q.qs_apply(h, gates, None, p)
+        q.qs_probs(h, [], norm_out)
+        q.qs_sample(h, SAMPLE_SEED, SHOTS, samples)
+
+    def timed(p, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            step(p)
+        torch.cuda.synchronize()
+        barrier(pg)
+        torch.cuda.synchronize()
+        q.qs_timing_enable(h, True)
+        q.qs_timing_fetch(h)
+        l0 = q.qs_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local)
+        if sample_clocks:
+            clk.__enter__()
+        e0.record(stream)
+        for _ in range(steps):
+            step(p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sample_clocks:
+            clk.__exit__()
+        barrier(pg)
+        torch.cuda.synchronize()
+        launches = q.qs_launch_count() - l0
+        recs = q.qs_timing_fetch(h)
+        q.qs_timing_enable(h, False)
+        ms = e0.elapsed_time(e1) / steps
+        return max_over_ranks(pg, ms), recs, launches, (clk.summary() if sample_clocks else None)
+
+    ms, recs, launches, clocks = timed(plan, args.steps, args.warmup, sample_clocks=True)
+    norm2 = float(norm_out.item())
+    amp_updates = ng * float(1 << n)
+    value = world * amp_updates / (ms * 1e-3)
+    roof = roofline(recs, hbm_peak)
+    gate_bytes = sum(r["items"] * 32.0 for r in recs if r["kind"] in (1, 2, 3, 4, 5, 10, 11))
+    step_gate_ms = sum(r["ms"] for r in recs if r["kind"] in (1, 2, 3, 4, 5, 10, 11)) / args.steps
+
+    plain = None
+    if plan is not None and not args.no_plain:
+        pms, precs, _, _ = timed(None, max(1, args.steps - 1), 1)
+        pb = sum(r["items"] * 32.0 for r in precs if r["kind"] in (1, 2, 3, 4, 5))
+        pg_ms = sum(r["ms"] for r in precs if r["kind"] in (1, 2, 3, 4, 5)) / max(1, args.steps - 1)
+        plain = {"value": world * amp_updates / (pms * 1e-3), "ms_per_step": pms,
+                 "hbm_gbs_algorithmic": pb / max(1, args.steps - 1) / (pg_ms * 1e-3) / 1e9}
+
+    # end to end through the public API: host gate list in, norm and samples out to host
+    host_samples = np.empty(SHOTS, dtype=np.uint64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q.qs_set_zero(h)
+        q.qs_apply(h, gates, None, plan)
+        nn = q.qs_probs(h, [])
+        q.qs_sample(h, SAMPLE_SEED, SHOTS, host_samples)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = max_over_ranks(pg, e2e_s)
+    ok_e2e = np.array_equal(host_samples, samples.cpu().numpy().astype(np.uint64)) and abs(nn[0] - norm2) == 0.0
+
+    if plan is not None:
+        q.qs_plan_free(plan)
+    q.qs_free(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_oracle_sample(n, gates)
+        except Exception as ex:  # host RAM too small for the state, for example
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"not run: {ex}"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"layered U3+CZ brickwork, n={n}, depth {args.depth} ({ng} gates), "
+                               f"norm + {SHOTS} samples", "n": n, "gates": ng, "shots": SHOTS,
+                   "mode": "fused" if plan is not None else "plain", "plan": plan_stats,
+                   "l2": "state (16 GiB at n=30) is larger than L2", "parallelism": f"replicas x{world}"},
+        "hbm_gbs": gate_bytes / (step_gate_ms * 1e-3) / 1e9 if step_gate_ms else None,
+        "hbm_gbs_note": "algorithmic bytes of the gate kernels / their device time",
+        "norm2": norm2,
+        "plain": plain,
+        "roofline": roof,
+        "peak_source": {"hbm": peak_src, "fp64": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * amp_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes),
+                "d2h_bytes_per_step": SHOTS * 8 + 8, "matches_device_run": bool(ok_e2e)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * qsim.h -- C ABI of libqsim, a GB300 (sm_103a) full-amplitude state-vector
+ * simulator for the hot path of QPanda's full-amplitude virtual machine
+ * (arXiv 2212.14201): allocate n qubits, apply a gate program (optionally fused),
+ * read probabilities, expectations and measurement samples, and take adjoint
+ * gradients of parametrised circuits.
+ *
+ * Conventions
+ *   - Qubit q is bit q of the basis index (qubit 0 = least significant bit).
+ *   - A state is 2^n complex128 amplitudes, interleaved (re, im), 16 bytes each,
+ *     contiguous in device memory.
+ *   - Every call is asynchronous on the CUDA stream the state was created with,
+ *     except where it returns results into host memory: those synchronise that
+ *     stream before returning.
+ *   - Host arrays passed in are owned by the caller and only read during the call.
+ *   - Every entry point returns an int status: QS_OK (0) or a negative QS_ERR_*.
+ *     Nothing aborts or exits the process.  qs_last_error() gives a message for
+ *     the last failing call on the calling thread.
+ *   - No entry point reads or writes memory the caller did not pass or the
+ *     library did not allocate.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define QS_OK 0
+#define QS_ERR_INVALID_ARG (-1)  /* bad qubit index, overlapping targets/controls, size out of range */
+#define QS_ERR_OOM (-2)          /* a device or host allocation failed */
+#define QS_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define QS_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
+#define QS_ERR_UNSUPPORTED (-5)  /* well-formed request outside what is implemented */
+
+/* ---- gate codes: the paper's gate set (API keyword list and the "Performance
+ * of basic gates" experiment) plus P, the phase gate that CR controls.
+ *   H = [[1,1],[1,-1]]/sqrt2          X = [[0,1],[1,0]]     Y = [[0,-i],[i,0]]
+ *   Z = diag(1,-1)  S = diag(1,i)  T = diag(1,e^{i pi/4})  P(t) = diag(1,e^{it})
+ *   RX(t) = exp(-i t X/2)  RY(t) = exp(-i t Y/2)  RZ(t) = exp(-i t Z/2)
+ *   U3(t,f,l) = [[cos t/2, -e^{il} sin t/2], [e^{if} sin t/2, e^{i(f+l)} cos t/2]]
+ *   CNOT(c,t) = X on t controlled by c; CZ(c,t) = Z on t controlled by c;
+ *   CR(c,t,th) = P(th) on t controlled by c.                                    */
+enum {
+  QS_I = 0, QS_H = 1, QS_X = 2, QS_Y = 3, QS_Z = 4, QS_S = 5, QS_T = 6,
+  QS_RX = 7, QS_RY = 8, QS_RZ = 9, QS_U3 = 10, QS_P = 11,
+  QS_CNOT = 12, QS_CZ = 13, QS_CR = 14
+};
+
+/* One gate of a program (56 bytes).  The paper's ".control" form (Section
+ * "A variety of convenient tools") is ctrl_mask; its set_dagger is `dagger`.
+ *   q0         target of a one-qubit gate; the control of CNOT / CZ / CR
+ *   q1         target of CNOT / CZ / CR; ignored (use -1) otherwise
+ *   param_idx  >= 0: theta is params[param_idx] of the call; -1: theta is p[0]
+ *   ctrl_mask  extra control qubits: the gate acts where all these bits are 1
+ *   p          theta, phi, lambda (radians)
+ *   dagger     nonzero: apply the conjugate transpose                          */
+typedef struct qs_gate {
+  int32_t type;
+  int32_t q0;
+  int32_t q1;
+  int32_t param_idx;
+  uint64_t ctrl_mask;
+  double p[3];
+  int32_t dagger;
+  int32_t reserved;
+} qs_gate;
+
+/* One Pauli string with a real coefficient: qubit q carries X if only bit q of
+ * xmask is set, Z if only bit q of zmask is set, Y if both are set.  A Pauli
+ * sum is an array of these (the paper's Pauli operator, Section "Structure of
+ * QPanda"; qop expectation, Section "Variational quantum circuit").           */
+typedef struct qs_pauli {
+  double coef;
+  uint64_t xmask;
+  uint64_t zmask;
+} qs_pauli;
+
+typedef struct qs_state qs_state; /* opaque */
+typedef struct qs_plan qs_plan;   /* opaque */
+
+/* ---- library ----------------------------------------------------------------- */
+
+/* Message of the last failing call on this thread ("" if none).  The pointer
+ * stays valid until the next call on this thread. */
+const char* qs_last_error(void);
+
+/* Largest qubit count a state may have in this build (34). */
+int qs_max_qubits(void);
+
+/* ---- states (qAlloc_many / init_qvm in the paper's listings) --------------------- */
+
+/* Allocate an n-qubit state (1 <= n <= qs_max_qubits()) on the current CUDA
+ * device, bound to `stream` (a cudaStream_t; NULL = the legacy default stream),
+ * initialised to |0...0>.  The library owns the amplitude buffer and a small
+ * reduction workspace; both are released by qs_free.
+ * Errors: INVALID_ARG (n out of range), OOM, CUDA. */
+int qs_alloc(int n, void* stream, qs_state** out);
+
+/* Wrap an existing device buffer of 2^n complex128 amplitudes (16-byte aligned)
+ * that the caller owns (for example a torch tensor).  Its contents are left as
+ * they are.  The buffer must outlive the state; qs_free does not release it.
+ * Errors: INVALID_ARG (n out of range, NULL or misaligned pointer), OOM, CUDA. */
+int qs_alloc_external(int n, void* device_amps, void* stream, qs_state** out);
+
+/* Release a state (waits for its stream first).  NULL is accepted. */
+int qs_free(qs_state* s);
+
+/* Qubit count, device pointer of the amplitudes, and the bound stream. */
+int qs_num_qubits(const qs_state* s);
+int qs_device_ptr(const qs_state* s, void** out);
+
+/* Reset to |0...0>. */
+int qs_set_zero(qs_state* s);
+
+/* Copy 2^n interleaved complex128 amplitudes in from `amps` (device memory if
+ * on_device != 0, else host memory; synchronous for host memory). */
+int qs_set_state(qs_state* s, const double* amps, int on_device);
+
+/* Copy the 2^n amplitudes out to `dst` (device or host memory). */
+int qs_get_state(const qs_state* s, double* dst, int on_device);
+
+/* Wait for all work queued on the state's stream. */
+int qs_sync(const qs_state* s);
+
+/* ---- gate application (directly_run; Section "High-performance simulation":
+ * a circuit is an iteration of gates, each a map on the state vector) --------- */
+
+/* Apply gates[0..ng-1] in order.  params (host, may be NULL if no record has
+ * param_idx >= 0) supplies theta for parametrised records; param_idx must be
+ * < the caller's params length (not checkable: the caller guarantees it).
+ * plan == NULL: one kernel per gate (plain mode).  Otherwise the plan must have
+ * been created from exactly this gate list and qubit count; its passes are run
+ * (fused mode) with matrices computed from `params` at this call.
+ * Every record is validated before any work is queued: a bad record returns
+ * INVALID_ARG and leaves the state untouched. */
+int qs_apply(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan);
+
+/* Dense k-qubit matrix gate, 1 <= k <= 5 (the "unitary matrix" gates of the
+ * paper's basic-gate experiment).  targets[j] is bit j of the matrix's row and
+ * column index; mat is 2^k x 2^k complex128, row-major, interleaved, in host
+ * memory; it need not be unitary.  The gate acts where all ctrl_mask bits are 1. */
+int qs_apply_matrix(qs_state* s, const int* targets, int k, uint64_t ctrl_mask, const double* mat);
+
+/* out[i] = the adjoint of in[ng-1-i] (the paper's set_dagger on a circuit);
+ * out may not alias in. */
+int qs_gate_list_dagger(const qs_gate* in, size_t ng, qs_gate* out);
+
+/* ---- fusion plans (Fusion.aggregate_operations; Section "Quantum circuit
+ * fusion") ------------------------------------------------------------------ */
+
+#define QS_PLAN_PLAIN 0   /* one pass per gate */
+#define QS_PLAN_GREEDY 1  /* greedy grouping into tiled passes / dense blocks */
+#define QS_PLAN_LEARNED 2 /* groupings scored by the trained cost model */
+
+typedef struct qs_plan_stats {
+  int64_t n_gates;       /* gates in the program */
+  int64_t n_passes;      /* state sweeps the plan makes */
+  int64_t n_tile_passes; /* of which shared-memory tile passes */
+  int64_t n_dense;       /* dense-block ops (in tiles or standalone) */
+  double est_seconds;    /* the planner's cost estimate (0 if none) */
+} qs_plan_stats;
+
+/* Build a plan for n qubits from gates[0..ng-1] (host only; no device work).
+ * kmax: widest dense block allowed (1..5).  mode: QS_PLAN_*.
+ * Errors: INVALID_ARG, UNSUPPORTED (LEARNED without a loaded cost model), OOM. */
+int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, qs_plan** out);
+int qs_plan_free(qs_plan* p);
+int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
+
+/* Pass `pass` of a plan (0 <= pass < n_passes): *kind (0 = one plain gate,
+ * 1 = shared-memory tile pass), *qmask (tile qubits, or the gate's target),
+ * and the indices of its gates into the program in execution order (up to cap
+ * of them into `gates`; *ngates receives the count).  Running the passes in
+ * order applies the same unitary as the program. */
+int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask, uint32_t* gates, size_t cap,
+                      size_t* ngates);
+
+/* ---- reductions (prob_run_list / prob_run_dict, expectation tools) ------------- */
+
+/* Marginal probabilities over qubits[0..nq-1] (0 <= nq <= n; qubits[j] is bit j
+ * of the output index): out has 2^nq entries, out[k] = sum of |a_x|^2 over x
+ * whose listed bits spell k.  nq = 0 gives the squared norm.  out is device
+ * memory if on_device != 0 (asynchronous), else host memory (synchronous). */
+int qs_probs(const qs_state* s, const int* qubits, int nq, double* out, int on_device);
+
+/* Entries of the marginal over qubits[0..nq-1] with probability > threshold,
+ * in increasing index order: idx[i], p[i] for i < min(count, cap) (host memory);
+ * *count receives the total number of such entries. */
+int qs_probs_dict(const qs_state* s, const int* qubits, int nq, double threshold, uint64_t* idx,
+                  double* p, size_t cap, size_t* count);
+
+/* <Z_i> for every qubit i into out[0..n-1] (host memory). */
+int qs_expect_z_all(const qs_state* s, double* out);
+
+/* <psi| sum_k coef_k P_k |psi> into *out (host).  Each term's masks must lie
+ * within the n qubits. */
+int qs_expect_pauli(const qs_state* s, const qs_pauli* terms, size_t nterms, double* out);
+
+/* Draw `shots` computational-basis samples (measure_all / run_with_configuration).
+ * Canonical, bit-reproducible definition: u_s = ((SplitMix64 output number s of
+ * the stream seeded `seed`) >> 11) * 2^-53; p_x = re*re + im*im rounded as two
+ * products and a sum; blocks of L = min(1024, 2^n) amplitudes summed left to
+ * right give the block totals, whose left-to-right prefix gives E_b; the sample
+ * is the smallest x with E_b + (left-to-right partial sum of block b up to x)
+ * > u_s, or, when no x qualifies, the largest x with p_x > 0.
+ * out[s] (uint64, device or host memory) receives the basis index of shot s. */
+int qs_sample(const qs_state* s, uint64_t seed, uint64_t shots, uint64_t* out, int on_device);
+
+
+/* ---- instrumentation ---------------------------------------------------------------
+ * Per-kernel timing log of one state: when enabled, every kernel the library
+ * queues for the state is bracketed by CUDA events on the state's stream.
+ * qs_timing_fetch synchronises the stream, converts the pending pairs to
+ * milliseconds, returns up to `cap` records (host memory, in launch order),
+ * stores the number available in *count and clears the log.  The log is the
+ * training data of the fusion cost model and the live per-kernel timing of the
+ * benchmark.                                                                   */
+enum {
+  QS_K_PHASE1 = 1, QS_K_DIAG = 2, QS_K_ANTI = 3, QS_K_REAL = 4, QS_K_GENERAL = 5, /* one-qubit op classes */
+  QS_K_DENSE = 10,   /* dense k-qubit block */
+  QS_K_TILE = 11,    /* shared-memory tile pass */
+  QS_K_REDUCE = 20,  /* reductions and sampling */
+  QS_K_ADJOINT = 30, /* adjoint-gradient kernels */
+  QS_K_OTHER = 40
+};
+
+typedef struct qs_timing_record {
+  int32_t kind;        /* QS_K_* */
+  int32_t n;           /* qubits of the state */
+  int32_t k;           /* block / tile width (qubits), 1 for one-qubit ops */
+  int32_t n_ops;       /* gates or ops executed by the launch */
+  uint64_t qubit_mask; /* qubits the launch acts on (targets; tile qubits) */
+  uint64_t ctrl_mask;  /* control qubits */
+  double items;        /* amplitudes the launch reads (and writes) */
+  double flops;        /* floating-point operations the launch's arithmetic needs */
+  double ms;           /* device time between the bracketing events */
+} qs_timing_record;
+
+int qs_timing_enable(qs_state* s, int on);
+int qs_timing_fetch(qs_state* s, qs_timing_record* out, size_t cap, size_t* count);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t qs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

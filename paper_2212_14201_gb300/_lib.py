@@ -1,0 +1,324 @@
+"""ctypes binding of libqsim: one Python function per C entry point, same names.
+
+Argument marshalling only -- every step of the simulation runs in the library's
+CUDA kernels.  Importing this module does not load the library; the first call
+does, and raises QsimError if libqsim.so has not been built (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsim.so")
+
+QS_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPORTED"}
+
+PLAN_PLAIN, PLAN_GREEDY, PLAN_LEARNED = 0, 1, 2
+
+GATE_DTYPE = np.dtype([
+    ("type", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("param_idx", "<i4"),
+    ("ctrl_mask", "<u8"), ("p", "<f8", (3,)), ("dagger", "<i4"), ("reserved", "<i4"),
+], align=True)
+PAULI_DTYPE = np.dtype([("coef", "<f8"), ("xmask", "<u8"), ("zmask", "<u8")], align=True)
+
+
+class QsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libqsim {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_tile_passes", ctypes.c_int64),
+                ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double)]
+
+
+class TimingRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("k", ctypes.c_int32), ("n_ops", ctypes.c_int32),
+                ("qubit_mask", ctypes.c_uint64), ("ctrl_mask", ctypes.c_uint64), ("items", ctypes.c_double),
+                ("flops", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+K_PHASE1, K_DIAG, K_ANTI, K_REAL, K_GENERAL, K_DENSE, K_TILE, K_REDUCE, K_ADJOINT, K_OTHER = 1, 2, 3, 4, 5, 10, 11, 20, 30, 40
+
+_lock = threading.Lock()
+_lib = None
+
+P, I32, U64, SZ, DBL = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_double
+PP = ctypes.POINTER(ctypes.c_void_p)
+
+SIGNATURES = {
+    "qs_last_error": (ctypes.c_char_p, []),
+    "qs_max_qubits": (I32, []),
+    "qs_alloc": (I32, [I32, P, PP]),
+    "qs_alloc_external": (I32, [I32, P, P, PP]),
+    "qs_free": (I32, [P]),
+    "qs_num_qubits": (I32, [P]),
+    "qs_device_ptr": (I32, [P, PP]),
+    "qs_set_zero": (I32, [P]),
+    "qs_set_state": (I32, [P, P, I32]),
+    "qs_get_state": (I32, [P, P, I32]),
+    "qs_sync": (I32, [P]),
+    "qs_apply": (I32, [P, P, SZ, P, P]),
+    "qs_apply_matrix": (I32, [P, P, I32, U64, P]),
+    "qs_gate_list_dagger": (I32, [P, SZ, P]),
+    "qs_plan_create": (I32, [I32, P, SZ, I32, I32, PP]),
+    "qs_plan_free": (I32, [P]),
+    "qs_plan_get_stats": (I32, [P, ctypes.POINTER(PlanStats)]),
+    "qs_plan_pass_info": (I32, [P, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64), P, SZ,
+                                ctypes.POINTER(SZ)]),
+    "qs_probs": (I32, [P, P, I32, P, I32]),
+    "qs_probs_dict": (I32, [P, P, I32, DBL, P, P, SZ, ctypes.POINTER(SZ)]),
+    "qs_expect_z_all": (I32, [P, P]),
+    "qs_expect_pauli": (I32, [P, P, SZ, ctypes.POINTER(DBL)]),
+    "qs_sample": (I32, [P, U64, U64, P, I32]),
+    "qs_timing_enable": (I32, [P, I32]),
+    "qs_timing_fetch": (I32, [P, ctypes.POINTER(TimingRecord), SZ, ctypes.POINTER(SZ)]),
+    "qs_launch_count": (U64, []),
+}
+
+
+def lib():
+    """The loaded library (raises QsimError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise QsimError(-3, f"{LIB_PATH} is missing: build it with paper_2212_14201_gb300.build.build()")
+            l = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(l, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = l
+    return _lib
+
+
+def _chk(rc: int):
+    if rc != QS_OK:
+        raise QsimError(rc, lib().qs_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _host_or_dev(x):
+    """(pointer, on_device) of a numpy array or a CUDA torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (1 if x.is_cuda else 0)
+    raise TypeError(f"expected numpy array or torch tensor, got {type(x)}")
+
+
+def as_gates(gates) -> np.ndarray:
+    g = np.ascontiguousarray(gates)
+    if g.dtype != GATE_DTYPE:
+        g = g.astype(GATE_DTYPE)
+    return g
+
+
+def as_paulis(terms) -> np.ndarray:
+    t = np.ascontiguousarray(terms)
+    if t.dtype != PAULI_DTYPE:
+        t = t.astype(PAULI_DTYPE)
+    return t
+
+
+# ---- one wrapper per entry point ---------------------------------------------------
+
+def qs_last_error() -> str:
+    return lib().qs_last_error().decode()
+
+
+def qs_max_qubits() -> int:
+    return lib().qs_max_qubits()
+
+
+def qs_alloc(n: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _chk(lib().qs_alloc(n, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qs_alloc_external(n: int, device_amps, stream=None) -> int:
+    ptr = device_amps if isinstance(device_amps, int) else device_amps.data_ptr()
+    h = ctypes.c_void_p()
+    _chk(lib().qs_alloc_external(n, ptr, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qs_free(h: int):
+    _chk(lib().qs_free(h))
+
+
+def qs_num_qubits(h: int) -> int:
+    r = lib().qs_num_qubits(h)
+    if r < 0:
+        _chk(r)
+    return r
+
+
+def qs_device_ptr(h: int) -> int:
+    p = ctypes.c_void_p()
+    _chk(lib().qs_device_ptr(h, ctypes.byref(p)))
+    return p.value
+
+
+def qs_set_zero(h: int):
+    _chk(lib().qs_set_zero(h))
+
+
+def qs_set_state(h: int, amps):
+    ptr, dev = _host_or_dev(amps)
+    _chk(lib().qs_set_state(h, ptr, dev))
+
+
+def qs_get_state(h: int, out=None):
+    """Copy the amplitudes into `out` (numpy float64 / complex128 array or device
+    tensor); with out=None returns a new numpy complex128 array."""
+    if out is None:
+        n = qs_num_qubits(h)
+        out = np.empty(1 << n, dtype=np.complex128)
+    ptr, dev = _host_or_dev(out)
+    _chk(lib().qs_get_state(h, ptr, dev))
+    return out
+
+
+def qs_sync(h: int):
+    _chk(lib().qs_sync(h))
+
+
+def qs_apply(h: int, gates, params=None, plan: int | None = None):
+    g = as_gates(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    _chk(lib().qs_apply(h, g.ctypes.data if len(g) else None, len(g),
+                        None if pr is None else pr.ctypes.data, plan))
+
+
+def qs_apply_matrix(h: int, targets, mat, ctrl_mask: int = 0):
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    m = np.ascontiguousarray(mat, dtype=np.complex128)
+    _chk(lib().qs_apply_matrix(h, t.ctypes.data, len(t), ctrl_mask, m.ctypes.data))
+
+
+def qs_gate_list_dagger(gates) -> np.ndarray:
+    g = as_gates(gates)
+    out = np.empty_like(g)
+    _chk(lib().qs_gate_list_dagger(g.ctypes.data if len(g) else None, len(g), out.ctypes.data if len(g) else None))
+    return out
+
+
+def qs_plan_create(n: int, gates, mode: int = PLAN_GREEDY, kmax: int = 5) -> int:
+    g = as_gates(gates)
+    h = ctypes.c_void_p()
+    _chk(lib().qs_plan_create(n, g.ctypes.data if len(g) else None, len(g), mode, kmax, ctypes.byref(h)))
+    return h.value
+
+
+def qs_plan_free(p: int):
+    _chk(lib().qs_plan_free(p))
+
+
+def qs_plan_get_stats(p: int) -> dict:
+    st = PlanStats()
+    _chk(lib().qs_plan_get_stats(p, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in PlanStats._fields_}
+
+
+def qs_plan_pass_info(p: int, i: int):
+    """(kind, qubit mask, gate indices) of pass i."""
+    kind, qm, cnt = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_size_t()
+    _chk(lib().qs_plan_pass_info(p, i, ctypes.byref(kind), ctypes.byref(qm), None, 0, ctypes.byref(cnt)))
+    idx = np.empty(max(1, cnt.value), dtype=np.uint32)
+    _chk(lib().qs_plan_pass_info(p, i, ctypes.byref(kind), ctypes.byref(qm), idx.ctypes.data, cnt.value,
+                                 ctypes.byref(cnt)))
+    return kind.value, qm.value, idx[:cnt.value].copy()
+
+
+def qs_plan_passes(p: int) -> list:
+    return [qs_plan_pass_info(p, i) for i in range(qs_plan_get_stats(p)["n_passes"])]
+
+
+def qs_probs(h: int, qubits=None, out=None):
+    """Marginal probabilities over `qubits` (default: all, in order).  `out` may be
+    a device tensor (filled asynchronously) or omitted (returns numpy)."""
+    n = qs_num_qubits(h)
+    q = np.arange(n, dtype=np.int32) if qubits is None else np.ascontiguousarray(qubits, dtype=np.int32)
+    if out is None:
+        out = np.empty(1 << len(q), dtype=np.float64)
+    ptr, dev = _host_or_dev(out)
+    _chk(lib().qs_probs(h, q.ctypes.data if len(q) else None, len(q), ptr, dev))
+    return out
+
+
+def qs_probs_dict(h: int, qubits=None, threshold: float = 0.0) -> dict:
+    n = qs_num_qubits(h)
+    q = np.arange(n, dtype=np.int32) if qubits is None else np.ascontiguousarray(qubits, dtype=np.int32)
+    cnt = ctypes.c_size_t()
+    _chk(lib().qs_probs_dict(h, q.ctypes.data if len(q) else None, len(q), threshold, None, None, 0, ctypes.byref(cnt)))
+    idx = np.empty(max(1, cnt.value), dtype=np.uint64)
+    p = np.empty(max(1, cnt.value), dtype=np.float64)
+    _chk(lib().qs_probs_dict(h, q.ctypes.data if len(q) else None, len(q), threshold, idx.ctypes.data,
+                             p.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    width = len(q)
+    return {format(int(i), f"0{width}b") if width else "": float(v) for i, v in zip(idx[:cnt.value], p[:cnt.value])}
+
+
+def qs_expect_z_all(h: int) -> np.ndarray:
+    out = np.empty(qs_num_qubits(h), dtype=np.float64)
+    _chk(lib().qs_expect_z_all(h, out.ctypes.data))
+    return out
+
+
+def qs_expect_pauli(h: int, terms) -> float:
+    t = as_paulis(terms)
+    out = ctypes.c_double()
+    _chk(lib().qs_expect_pauli(h, t.ctypes.data if len(t) else None, len(t), ctypes.byref(out)))
+    return out.value
+
+
+def qs_sample(h: int, seed: int, shots: int, out=None):
+    if out is None:
+        out = np.empty(shots, dtype=np.uint64)
+    ptr, dev = _host_or_dev(out)
+    _chk(lib().qs_sample(h, seed, shots, ptr, dev))
+    return out
+
+
+def qs_timing_enable(h: int, on: bool = True):
+    _chk(lib().qs_timing_enable(h, 1 if on else 0))
+
+
+def qs_timing_fetch(h: int) -> list[dict]:
+    """Pending per-kernel timing records of the state (synchronises its stream)."""
+    cnt = ctypes.c_size_t()
+    cap = 1 << 16
+    recs = []
+    while True:
+        buf = (TimingRecord * cap)()
+        _chk(lib().qs_timing_fetch(h, buf, cap, ctypes.byref(cnt)))
+        recs += [{k: getattr(buf[i], k) for k, _ in TimingRecord._fields_} for i in range(min(cnt.value, cap))]
+        if cnt.value <= cap:
+            return recs
+        # more records than the buffer held: they were dropped; report it
+        raise QsimError(-1, f"timing log held {cnt.value} records, more than {cap}")
+
+
+def qs_launch_count() -> int:
+    return int(lib().qs_launch_count())

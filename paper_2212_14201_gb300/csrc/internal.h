@@ -1,0 +1,114 @@
+// Internal declarations of libqsim (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+#define QS_MAX_QUBITS 34
+
+struct qs_pending_timing {
+  qs_timing_record rec;
+  cudaEvent_t e0, e1;
+};
+
+struct qs_state {
+  int n = 0;
+  double2* amps = nullptr;  // 2^n amplitudes, device
+  bool owns = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // Reduction / sampling workspace (device), sized at creation for n.
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // Pinned host staging for small reduction results.
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  // Per-kernel timing log (qs_timing_enable / qs_timing_fetch).
+  bool timing = false;
+  std::vector<qs_pending_timing> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace qs {
+
+// ---- errors -------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+#define QS_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::qs::cuda_fail(e_, #call); \
+  } while (0)
+#define QS_TRY(expr)          \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != QS_OK) return rc_; \
+  } while (0)
+
+int check_state(const qs_state* s);
+int launch_check(const char* what);  // cudaGetLastError after a launch
+
+// ---- complex helpers (host) ---------------------------------------------------
+struct C2 {
+  double re, im;
+};
+struct Mat2 {
+  C2 m[4];  // row-major: m[0]=U00 m[1]=U01 m[2]=U10 m[3]=U11
+};
+
+// Target qubit and full control mask of a record; validates indices.
+int gate_qubits(const qs_gate& g, int n, int* target, uint64_t* cmask);
+// 2x2 matrix of a record (dagger applied); params may be NULL if param_idx < 0.
+int gate_matrix(const qs_gate& g, const double* params, Mat2* out);
+int validate_gates(const qs_gate* gates, size_t ng, int n, const double* params);
+
+// ---- one resolved one-qubit op (target + control mask + matrix + class) ---------
+enum OpClass : int {
+  OP_IDENTITY = 0,
+  OP_PHASE1 = 1,   // diag(1, d1): touches the |1> half only
+  OP_DIAG = 2,     // diag(d0, d1)
+  OP_ANTI = 3,     // [[0, b], [c, 0]]
+  OP_REAL = 4,     // real 2x2
+  OP_GENERAL = 5,  // complex 2x2
+};
+// Multiplier codes for diagonal / anti-diagonal entries: exact unit phases are
+// applied with sign flips and swaps (no floating-point instruction).
+enum UnitCode : int { U_ONE = 0, U_I = 1, U_MINUS_ONE = 2, U_MINUS_I = 3, U_GENERAL = 4 };
+
+struct Op1 {
+  int cls;
+  int target;
+  uint64_t cmask;
+  Mat2 m;
+  int code0, code1;  // for PHASE1/DIAG: codes of d0,d1; ANTI: codes of b,c
+};
+Op1 classify(int target, uint64_t cmask, const Mat2& m);
+int unit_code(const C2& z);
+
+// ---- kernels (launchers) --------------------------------------------------------
+int launch_op1(qs_state* s, const Op1& op);
+int launch_dense(qs_state* s, const int* targets, int k, uint64_t cmask, const C2* mat);
+
+// ---- instrumentation -------------------------------------------------------------
+void note_launch(int count = 1);
+// Brackets the kernels queued during its lifetime with timing events (if the
+// state's log is enabled) and counts one launch.
+struct KTimer {
+  qs_state* s;
+  qs_pending_timing pt;
+  bool on;
+  KTimer(qs_state* s, int kind, int k, int n_ops, uint64_t qmask, uint64_t cmask, double items, double flops);
+  ~KTimer();
+};
+
+// ---- workspace ------------------------------------------------------------------
+size_t workspace_bytes(int n);
+int ensure_pinned(qs_state* s, size_t bytes);
+
+}  // namespace qs

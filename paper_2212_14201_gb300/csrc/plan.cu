@@ -1,0 +1,306 @@
+// Fusion plans (Fusion.aggregate_operations; Section "Quantum circuit fusion").
+//
+// The paper merges local sub-circuits into unitary blocks before the run.  Here a
+// plan partitions the program into passes, each one sweep of the state:
+//   PASS_GATE  one op, plain per-gate kernel;
+//   PASS_TILE  a qubit set Q (m <= 12 qubits incl. 0..2) and the gates that run
+//              inside shared-memory tiles of Q in one HBM round trip.
+// Greedy construction (mode GREEDY): scan the remaining gates in program order,
+// growing Q with each non-diagonal target until Q is full; a gate joins the pass
+// unless it must wait for a gate already deferred.  Commutation is tracked per
+// qubit: a gate touches its target "non-diagonally" unless the gate is diagonal,
+// and its controls (and a diagonal gate's target) "diagonally"; two gates on a
+// common qubit commute when both touch it diagonally.  Diagonal gates join any
+// pass (their target may lie outside Q: a per-tile scalar).
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tile.h"
+
+using namespace qs;
+
+enum PassKind { PASS_GATE = 0, PASS_TILE = 1 };
+
+struct PlanPass {
+  int kind = PASS_GATE;
+  uint64_t qmask = 0;
+  std::vector<uint32_t> gates;
+};
+
+struct qs_plan {
+  int n = 0;
+  int mode = 0;
+  int kmax = 1;
+  int m = TILE_MAX_M;
+  size_t ng = 0;
+  uint64_t fingerprint = 0;
+  std::vector<PlanPass> passes;
+  double est_seconds = 0.0;
+  int64_t n_tile = 0;
+};
+
+namespace {
+
+// Structure of a record that the plan depends on (not its angles).
+uint64_t fingerprint(const qs_gate* g, size_t ng) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  for (size_t k = 0; k < ng; ++k) {
+    mix((uint64_t)(uint32_t)g[k].type);
+    mix((uint64_t)(uint32_t)g[k].q0);
+    mix((uint64_t)(uint32_t)g[k].q1);
+    mix(g[k].ctrl_mask);
+    mix((uint64_t)(g[k].dagger != 0));
+  }
+  return h;
+}
+
+// Whether a record is diagonal for every angle: Z, S, T, RZ, P, CZ, CR (and I).
+bool structurally_diagonal(int type) {
+  return type == QS_I || type == QS_Z || type == QS_S || type == QS_T || type == QS_RZ || type == QS_P ||
+         type == QS_CZ || type == QS_CR;
+}
+
+// Cost model of the greedy planner (seconds): a pass costs the larger of its HBM
+// time and its arithmetic time.
+constexpr double kHbmBytesPerS = 6.6e12;
+constexpr double kFp64FlopPerS = 1.0e12;
+
+double op_flops_per_amp(int type) {
+  switch (type) {
+    case QS_U3: case QS_RX: return 14.0;
+    case QS_H: case QS_RY: return 6.0;
+    case QS_RZ: return 6.0;
+    case QS_T: case QS_P: case QS_CR: return 3.0;
+    default: return 0.0;
+  }
+}
+
+double op_touch_fraction(const qs_gate& g, uint64_t cmask) {
+  double f = 1.0 / (double)(1ull << __builtin_popcountll(cmask));
+  if (g.type == QS_Z || g.type == QS_S || g.type == QS_T || g.type == QS_P || g.type == QS_CZ || g.type == QS_CR)
+    f *= 0.5;
+  return f;
+}
+
+}  // namespace
+
+extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, qs_plan** out) {
+  clear_error();
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_ERR_INVALID_ARG, "n out of range");
+  if (kmax < 1 || kmax > 5) return fail(QS_ERR_INVALID_ARG, "kmax outside 1..5");
+  if (ng && !gates) return fail(QS_ERR_INVALID_ARG, "gates is NULL");
+  if (mode != QS_PLAN_PLAIN && mode != QS_PLAN_GREEDY)
+    return fail(QS_ERR_UNSUPPORTED, "plan mode %d needs a trained cost model", mode);
+  std::vector<int> tgt(ng);
+  std::vector<uint64_t> cms(ng);
+  for (size_t k = 0; k < ng; ++k) {
+    int t;
+    uint64_t cm;
+    int rc = gate_qubits(gates[k], n, &t, &cm);
+    if (rc) return fail(rc, "gate %zu: %s", k, qs_last_error());
+    tgt[k] = t;
+    cms[k] = cm;
+  }
+  qs_plan* p = new (std::nothrow) qs_plan;
+  if (!p) return fail(QS_ERR_OOM, "host allocation failed");
+  p->n = n;
+  p->mode = mode;
+  p->kmax = kmax;
+  p->ng = ng;
+  p->fingerprint = fingerprint(gates, ng);
+  p->m = std::min(n, TILE_MAX_M);
+  const double N = (double)(1ull << n);
+  const double pass_bytes = 32.0 * N;
+
+  if (mode == QS_PLAN_PLAIN) {
+    for (size_t k = 0; k < ng; ++k) {
+      PlanPass ps;
+      ps.kind = PASS_GATE;
+      ps.qmask = 1ull << tgt[k];
+      ps.gates.push_back((uint32_t)k);
+      p->passes.push_back(std::move(ps));
+      double f = op_touch_fraction(gates[k], cms[k]);
+      p->est_seconds += std::max(pass_bytes * f / kHbmBytesPerS, N * f * op_flops_per_amp(gates[k].type) / kFp64FlopPerS);
+    }
+    *out = p;
+    return QS_OK;
+  }
+
+  const int L = std::min(n, TILE_LOW);
+  const uint64_t low = (1ull << L) - 1;
+  std::vector<uint32_t> remaining(ng), rest;
+  for (size_t k = 0; k < ng; ++k) remaining[k] = (uint32_t)k;
+  while (!remaining.empty()) {
+    uint64_t Q = low;
+    uint64_t blockedN = 0, blockedD = 0;
+    PlanPass ps;
+    ps.kind = PASS_TILE;
+    rest.clear();
+    int nops = 0;
+    for (uint32_t k : remaining) {
+      const bool diag = structurally_diagonal(gates[k].type);
+      const uint64_t Nm = diag ? 0 : (1ull << tgt[k]);
+      const uint64_t Dm = (diag ? (1ull << tgt[k]) : 0) | cms[k];
+      bool conflict = (Nm & (blockedN | blockedD)) || (Dm & blockedN) || nops >= TILE_MAX_OPS;
+      if (!conflict && Nm && !(Q & Nm)) {
+        if (__builtin_popcountll(Q) < p->m) Q |= Nm;
+        else conflict = true;
+      }
+      if (conflict) {
+        rest.push_back(k);
+        blockedN |= Nm;
+        blockedD |= Dm;
+      } else {
+        ps.gates.push_back(k);
+        ++nops;
+      }
+    }
+    ps.qmask = Q;
+    // Cost: a tile pass sweeps the whole state once; a lone gate is cheaper in the
+    // plain kernel, which touches only the amplitudes it changes.
+    double flops = 0.0, plain = 0.0;
+    for (uint32_t k : ps.gates) {
+      double f = op_touch_fraction(gates[k], cms[k]);
+      flops += N * f * op_flops_per_amp(gates[k].type);
+      plain += std::max(pass_bytes * f / kHbmBytesPerS, N * f * op_flops_per_amp(gates[k].type) / kFp64FlopPerS);
+    }
+    double tile_cost = std::max(pass_bytes / kHbmBytesPerS, flops / kFp64FlopPerS);
+    if (ps.gates.size() == 1 || plain <= tile_cost) {
+      for (uint32_t k : ps.gates) {
+        PlanPass g1;
+        g1.kind = PASS_GATE;
+        g1.qmask = 1ull << tgt[k];
+        g1.gates.push_back(k);
+        p->passes.push_back(std::move(g1));
+      }
+      p->est_seconds += plain;
+    } else {
+      p->passes.push_back(std::move(ps));
+      p->est_seconds += tile_cost;
+      ++p->n_tile;
+    }
+    remaining.swap(rest);
+  }
+  *out = p;
+  return QS_OK;
+}
+
+extern "C" int qs_plan_free(qs_plan* p) {
+  delete p;
+  return QS_OK;
+}
+
+extern "C" int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out) {
+  if (!p || !out) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  out->n_gates = (int64_t)p->ng;
+  out->n_passes = (int64_t)p->passes.size();
+  out->n_tile_passes = p->n_tile;
+  out->n_dense = 0;
+  out->est_seconds = p->est_seconds;
+  return QS_OK;
+}
+
+extern "C" int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask, uint32_t* gates,
+                                 size_t cap, size_t* ngates) {
+  if (!p || !kind || !qmask || !ngates || (cap && !gates)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  if (pass >= p->passes.size()) return fail(QS_ERR_INVALID_ARG, "pass %zu of %zu", pass, p->passes.size());
+  const PlanPass& ps = p->passes[pass];
+  *kind = ps.kind;
+  *qmask = ps.qmask;
+  *ngates = ps.gates.size();
+  for (size_t i = 0; i < ps.gates.size() && i < cap; ++i) gates[i] = ps.gates[i];
+  return QS_OK;
+}
+
+static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params) {
+  const int n = s->n;
+  TileArgs* g = new (std::nothrow) TileArgs;
+  if (!g) return fail(QS_ERR_OOM, "host allocation failed");
+  const uint64_t Q = ps.qmask;
+  int local[64];
+  int m = 0;
+  for (int b = 0; b < n; ++b)
+    if ((Q >> b) & 1) local[b] = m++;
+    else local[b] = -1;
+  int L = 0;
+  while (L < n && ((Q >> L) & 1)) ++L;
+  g->n = n;
+  g->m = m;
+  g->ntiles = 1ull << (n - m);
+  g->nhigh = 0;
+  for (int b = L; b < n; ++b)
+    if ((Q >> b) & 1) g->qhigh[g->nhigh++] = b;
+  g->nout = 0;
+  for (int b = 0; b < n; ++b)
+    if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
+  g->nops = 0;
+  double flops = 0.0;
+  const double N = (double)(1ull << n);
+  int rc = QS_OK;
+  for (uint32_t k : ps.gates) {
+    int t;
+    uint64_t cm;
+    Mat2 mat;
+    if ((rc = gate_qubits(gates[k], n, &t, &cm)) != QS_OK) break;
+    if ((rc = gate_matrix(gates[k], params, &mat)) != QS_OK) break;
+    Op1 op = classify(t, cm, mat);
+    if (op.cls == OP_IDENTITY) continue;
+    TileOp& to = g->ops[g->nops];
+    for (int i = 0; i < 4; ++i) to.m[i] = make_double2(mat.m[i].re, mat.m[i].im);
+    to.code0 = (int8_t)op.code0;
+    to.code1 = (int8_t)op.code1;
+    uint32_t lcm = 0;
+    uint64_t ext = 0;
+    for (int b = 0; b < n; ++b)
+      if ((cm >> b) & 1) {
+        if (local[b] >= 0) lcm |= 1u << local[b];
+        else ext |= 1ull << b;
+      }
+    to.lcmask = lcm;
+    to.ext_cmask = ext;
+    if (local[t] >= 0) {
+      to.kind = (int8_t)op.cls;
+      to.tb = (int8_t)local[t];
+    } else {
+      if (op.cls != OP_PHASE1 && op.cls != OP_DIAG) {
+        rc = fail(QS_ERR_INVALID_ARG, "plan does not match the program (non-diagonal gate %u outside its tile)", k);
+        break;
+      }
+      to.kind = TOP_SCALAR;
+      to.tb = (int8_t)t;
+    }
+    flops += N * op_touch_fraction(gates[k], cm) * op_flops_per_amp(gates[k].type);
+    ++g->nops;
+  }
+  if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, flops, (int)ps.gates.size());
+  delete g;
+  return rc;
+}
+
+int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan) {
+  if (plan->n != s->n || plan->ng != ng || plan->fingerprint != fingerprint(gates, ng))
+    return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
+  for (const PlanPass& ps : plan->passes) {
+    if (ps.kind == PASS_GATE) {
+      const qs_gate& g = gates[ps.gates[0]];
+      int t;
+      uint64_t cm;
+      Mat2 m;
+      QS_TRY(gate_qubits(g, s->n, &t, &cm));
+      QS_TRY(gate_matrix(g, params, &m));
+      QS_TRY(launch_op1(s, classify(t, cm, m)));
+    } else {
+      QS_TRY(run_tile_pass(s, ps, gates, params));
+    }
+  }
+  return QS_OK;
+}

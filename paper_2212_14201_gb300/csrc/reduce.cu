@@ -1,0 +1,395 @@
+// Read-only reductions of the state: marginal probabilities (prob_run_list /
+// prob_run_dict), <Z_i> for every qubit, and Pauli-sum expectations (the paper's
+// probability / expectation tools, Section "A variety of convenient tools"; qop,
+// Section "Variational quantum circuit").
+//
+// Every reduction is deterministic: per-thread partials are combined by a fixed
+// warp-shuffle tree, CTA partials go to the workspace in CTA order and one
+// final CTA adds them in that order.  Results do not depend on timing.
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace qs {
+
+__device__ __forceinline__ double prob(double2 a) { return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one value per thread (blockDim.x == 256); result valid in all threads.
+__device__ double block_sum256(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r += sh[i];
+  return r;
+}
+
+// ---- full probability vector -------------------------------------------------------
+__global__ void k_probs_full(const double2* __restrict__ a, double* __restrict__ p, uint64_t N) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) p[i] = prob(a[i]);
+}
+
+// ---- marginal over nq <= 12 qubits: per-CTA shared histogram ---------------------
+struct MargArgs {
+  uint64_t N;
+  int nq;
+  int q[12];
+};
+
+__device__ __forceinline__ uint32_t extract_bits(uint64_t x, const MargArgs& g) {
+  uint32_t k = 0;
+  for (int j = 0; j < g.nq; ++j) k |= (uint32_t)((x >> g.q[j]) & 1) << j;
+  return k;
+}
+
+// Each CTA owns a contiguous range of the state; a thread accumulates its own
+// elements into a shared histogram with shared-memory atomics would make the sum
+// order timing-dependent, so instead each warp owns a private histogram slice
+// and adds its lanes' values in lane order.
+__global__ void __launch_bounds__(256) k_marginal_small(const double2* __restrict__ a, double* __restrict__ part,
+                                                         const MargArgs g, uint64_t per_cta) {
+  extern __shared__ double hist[];  // [8 warps][2^nq]
+  const int H = 1 << g.nq;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) hist[i] = 0.0;
+  __syncthreads();
+  uint64_t begin = blockIdx.x * per_cta, end = min(g.N, begin + per_cta);
+  double* mine = hist + w * H;
+  for (uint64_t base = begin + (uint64_t)w * 32; base < end; base += 256) {
+    uint64_t x = base + l;
+    double p = x < end ? prob(a[x]) : 0.0;
+    uint32_t k = extract_bits(x, g);
+    // lanes add in lane order (deterministic)
+    for (int src = 0; src < 32; ++src) {
+      double ps = __shfl_sync(0xffffffffu, p, src);
+      uint32_t ks = __shfl_sync(0xffffffffu, k, src);
+      if (l == 0 && base + src < end) mine[ks] += ps;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    double s = 0.0;
+    for (int ww = 0; ww < 8; ++ww) s += hist[ww * H + i];
+    part[(size_t)blockIdx.x * H + i] = s;
+  }
+}
+
+__global__ void k_marginal_finish(const double* __restrict__ part, int nblocks, int H, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * H + i];
+    out[i] = s;
+  }
+}
+
+// ---- marginal over many qubits: one thread per output entry -----------------------
+struct MargBigArgs {
+  uint64_t H;         // 2^nq outputs
+  uint64_t R;         // 2^(n-nq) terms per output
+  int nq, nr;
+  int q[QS_MAX_QUBITS];   // listed qubits
+  int r[QS_MAX_QUBITS];   // remaining qubits, ascending
+};
+
+__global__ void k_marginal_big(const double2* __restrict__ a, double* __restrict__ out, const MargBigArgs g) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.H; k += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t xb = 0;
+    for (int j = 0; j < g.nq; ++j) xb |= ((k >> j) & 1ull) << g.q[j];
+    double s = 0.0;
+    for (uint64_t r = 0; r < g.R; ++r) {
+      uint64_t x = xb;
+      for (int j = 0; j < g.nr; ++j) x |= ((r >> j) & 1ull) << g.r[j];
+      s += prob(a[x]);
+    }
+    out[k] = s;
+  }
+}
+
+// ---- <Z_i> for all i -----------------------------------------------------------------
+// CTA c owns the contiguous range [c*2^r, (c+1)*2^r).  Thread t handles elements
+// t + 256*j: bits 0..7 of the index are t, bits 8..r-1 are j, bits >= r are the CTA.
+// Each thread keeps its total and, for every bit of j, the sum over its elements
+// with that bit set; the CTA combines them into S_i = sum_{x_i = 1} p_x.
+constexpr int ZMAXJ = 26;
+__global__ void __launch_bounds__(256) k_expect_z(const double2* __restrict__ a, int r, double* __restrict__ part) {
+  __shared__ double sh[8];
+  const int jbits = r - 8;
+  const uint64_t base = (uint64_t)blockIdx.x << r;
+  double tot = 0.0;
+  double bs[ZMAXJ];
+#pragma unroll
+  for (int b = 0; b < ZMAXJ; ++b) bs[b] = 0.0;
+  const uint64_t J = 1ull << jbits;
+  for (uint64_t j = 0; j < J; ++j) {
+    double p = prob(a[base + threadIdx.x + (j << 8)]);
+    tot += p;
+#pragma unroll
+    for (int b = 0; b < ZMAXJ; ++b)
+      if (b < jbits && ((j >> b) & 1)) bs[b] += p;
+  }
+  // outputs: [0] total, [1 + i] = S_i for i < r  (bits >= r are handled by the finisher)
+  double* o = part + (size_t)blockIdx.x * (r + 1);
+  double T = block_sum256(tot, sh);
+  if (threadIdx.x == 0) o[0] = T;
+  for (int i = 0; i < 8; ++i) {
+    double v = block_sum256(((threadIdx.x >> i) & 1) ? tot : 0.0, sh);
+    if (threadIdx.x == 0) o[1 + i] = v;
+  }
+  for (int b = 0; b < jbits; ++b) {
+    double v = 0.0;
+#pragma unroll
+    for (int bb = 0; bb < ZMAXJ; ++bb)
+      if (bb == b) v = bs[bb];
+    v = block_sum256(v, sh);
+    if (threadIdx.x == 0) o[1 + 8 + b] = v;
+  }
+}
+
+__global__ void k_expect_z_finish(const double* __restrict__ part, int nblocks, int r, int n, double* __restrict__ out) {
+  // out[i] = T - 2 S_i; thread i handles qubit i; CTA partials added in CTA order.
+  int i = threadIdx.x;
+  if (i >= n) return;
+  double T = 0.0, S = 0.0;
+  for (int c = 0; c < nblocks; ++c) {
+    const double* o = part + (size_t)c * (r + 1);
+    T += o[0];
+    if (i < r) S += o[1 + i];
+    else if ((c >> (i - r)) & 1) S += o[0];
+  }
+  out[i] = T - 2.0 * S;
+}
+
+// ---- Pauli terms ------------------------------------------------------------------------
+// For a term (xm, zm, ny = popcount(xm & zm)):
+//   <P> = sum_x Re( i^ny (-1)^{popcount(x & zm)} conj(a_{x^xm}) a_x ).
+// Up to 8 terms per launch; per-CTA partials, then a fixed-order finish.
+struct PauliArgs {
+  uint64_t N;
+  int nt;
+  uint64_t xm[8], zm[8];
+  int ny[8];
+};
+
+__global__ void __launch_bounds__(256) k_pauli(const double2* __restrict__ a, const PauliArgs g, double* __restrict__ part) {
+  __shared__ double sh[8];
+  double acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < g.N; x += stride) {
+    double2 v = a[x];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k >= g.nt) break;
+      double2 u = a[x ^ g.xm[k]];
+      // w = conj(u) * v ; term = Re(i^ny * w) with sign (-1)^{popcount(x & zm)}
+      double w;
+      if (g.ny[k] & 1) w = fma(u.y, v.x, -u.x * v.y);   // Re(i*w) = -Im(w) = u.y v.x - u.x v.y
+      else w = fma(u.x, v.x, u.y * v.y);                // Re(w)
+      int neg = (__popcll(x & g.zm[k]) + (g.ny[k] >> 1)) & 1;
+      acc[k] += neg ? -w : w;
+    }
+  }
+  for (int k = 0; k < g.nt; ++k) {
+    double s = block_sum256(acc[k], sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 8 + k] = s;
+  }
+}
+
+__global__ void k_pauli_finish(const double* __restrict__ part, int nblocks, int nt, double* __restrict__ out) {
+  int k = threadIdx.x;
+  if (k >= nt) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * 8 + k];
+  out[k] = s;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+static int read_back(qs_state* s, const double* dev, size_t count, double* host) {
+  QS_TRY(ensure_pinned(s, count * sizeof(double)));
+  QS_CUDA(cudaMemcpyAsync(s->pinned, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(cudaStreamSynchronize(s->stream));
+  memcpy(host, s->pinned, count * sizeof(double));
+  return QS_OK;
+}
+
+static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout) {
+  const int n = s->n;
+  const uint64_t N = 1ull << n;
+  bool identity = nq == n;
+  for (int j = 0; j < nq && identity; ++j) identity = qubits[j] == j;
+  KTimer kt(s, QS_K_REDUCE, nq, 1, 0, 0, (double)N, 3.0 * (double)N);
+  if (identity) {
+    k_probs_full<<<(int)std::min<uint64_t>((N + 255) / 256, 152 * 32), 256, 0, s->stream>>>(s->amps, dout, N);
+    return launch_check("probs_full");
+  }
+  if (nq <= 10) {  // 8 warp-private histograms of 2^nq doubles fit in shared memory
+    MargArgs g;
+    g.N = N;
+    g.nq = nq;
+    for (int j = 0; j < nq; ++j) g.q[j] = qubits[j];
+    int nblocks = (int)std::min<uint64_t>(304, std::max<uint64_t>(1, N / 256));
+    uint64_t per = (N + nblocks - 1) / nblocks;
+    per = (per + 255) / 256 * 256;
+    nblocks = (int)((N + per - 1) / per);
+    size_t smem = (size_t)8 * (1 << nq) * sizeof(double);
+    if (smem > 48 * 1024)
+      QS_CUDA(cudaFuncSetAttribute(k_marginal_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    double* part = (double*)s->ws;
+    k_marginal_small<<<nblocks, 256, smem, s->stream>>>(s->amps, part, g, per);
+    QS_TRY(launch_check("marginal_small"));
+    int H = 1 << nq;
+    k_marginal_finish<<<(H + 255) / 256, 256, 0, s->stream>>>(part, nblocks, H, dout);
+    return launch_check("marginal_finish");
+  }
+  MargBigArgs g;
+  g.nq = nq;
+  g.H = 1ull << nq;
+  g.R = 1ull << (n - nq);
+  uint64_t used = 0;
+  for (int j = 0; j < nq; ++j) {
+    g.q[j] = qubits[j];
+    used |= 1ull << qubits[j];
+  }
+  g.nr = 0;
+  for (int b = 0; b < n; ++b)
+    if (!((used >> b) & 1)) g.r[g.nr++] = b;
+  k_marginal_big<<<(int)std::min<uint64_t>((g.H + 255) / 256, 152 * 32), 256, 0, s->stream>>>(s->amps, dout, g);
+  return launch_check("marginal_big");
+}
+
+static int check_qubit_list(const qs_state* s, const int* qubits, int nq) {
+  if (nq < 0 || nq > s->n) return fail(QS_ERR_INVALID_ARG, "nq=%d outside 0..n", nq);
+  if (nq && !qubits) return fail(QS_ERR_INVALID_ARG, "qubits is NULL");
+  uint64_t seen = 0;
+  for (int j = 0; j < nq; ++j) {
+    if (qubits[j] < 0 || qubits[j] >= s->n || ((seen >> qubits[j]) & 1))
+      return fail(QS_ERR_INVALID_ARG, "bad or repeated qubit %d", qubits[j]);
+    seen |= 1ull << qubits[j];
+  }
+  return QS_OK;
+}
+
+extern "C" int qs_probs(const qs_state* cs, const int* qubits, int nq, double* out, int on_device) {
+  clear_error();
+  qs_state* s = const_cast<qs_state*>(cs);
+  QS_TRY(check_state(s));
+  QS_TRY(check_qubit_list(s, qubits, nq));
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  size_t H = (size_t)1 << nq;
+  if (on_device) return marginal_device(s, qubits, nq, out);
+  double* tmp = nullptr;
+  QS_CUDA(cudaMallocAsync(&tmp, H * sizeof(double), s->stream));
+  int rc = marginal_device(s, qubits, nq, tmp);
+  if (rc == QS_OK) {
+    cudaError_t e = cudaMemcpyAsync(out, tmp, H * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "probs readback");
+  }
+  cudaFreeAsync(tmp, s->stream);
+  return rc;
+}
+
+extern "C" int qs_probs_dict(const qs_state* cs, const int* qubits, int nq, double threshold, uint64_t* idx,
+                             double* p, size_t cap, size_t* count) {
+  clear_error();
+  qs_state* s = const_cast<qs_state*>(cs);
+  QS_TRY(check_state(s));
+  QS_TRY(check_qubit_list(s, qubits, nq));
+  if (!count || (cap && (!idx || !p))) return fail(QS_ERR_INVALID_ARG, "NULL output");
+  if (nq > 28) return fail(QS_ERR_UNSUPPORTED, "probs_dict over more than 28 qubits");
+  size_t H = (size_t)1 << nq;
+  std::vector<double> host(H);
+  QS_TRY(qs_probs(s, qubits, nq, host.data(), 0));
+  size_t c = 0;
+  for (size_t k = 0; k < H; ++k) {
+    if (host[k] > threshold) {
+      if (c < cap) {
+        idx[c] = k;
+        p[c] = host[k];
+      }
+      ++c;
+    }
+  }
+  *count = c;
+  return QS_OK;
+}
+
+extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
+  clear_error();
+  qs_state* s = const_cast<qs_state*>(cs);
+  QS_TRY(check_state(s));
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  const int n = s->n;
+  double* part = (double*)s->ws;
+  double* dres = part + (size_t)1024 * 72 - 64;
+  if (n < 8) {
+    // tiny states: marginal per qubit
+    for (int i = 0; i < n; ++i) {
+      double m2[2];
+      int q = i;
+      QS_TRY(qs_probs(s, &q, 1, m2, 0));
+      out[i] = m2[0] - m2[1];
+    }
+    return QS_OK;
+  }
+  // r = bits per CTA: at least 8 (one element per thread), at most 8 + ZMAXJ; CTAs <= 1024
+  int r = std::max(8, n - 10);
+  r = std::min(r, std::min(n, 8 + ZMAXJ));
+  int nblocks = 1 << (n - r);
+  KTimer kt(s, QS_K_REDUCE, n, 1, 0, 0, (double)(1ull << n), 5.0 * (double)(1ull << n));
+  k_expect_z<<<nblocks, 256, 0, s->stream>>>(s->amps, r, part);
+  QS_TRY(launch_check("expect_z"));
+  k_expect_z_finish<<<1, 64, 0, s->stream>>>(part, nblocks, r, n, dres);
+  QS_TRY(launch_check("expect_z_finish"));
+  return read_back(s, dres, n, out);
+}
+
+extern "C" int qs_expect_pauli(const qs_state* cs, const qs_pauli* terms, size_t nterms, double* out) {
+  clear_error();
+  qs_state* s = const_cast<qs_state*>(cs);
+  QS_TRY(check_state(s));
+  if (!out || (nterms && !terms)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  const uint64_t full = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
+  for (size_t k = 0; k < nterms; ++k)
+    if ((terms[k].xmask | terms[k].zmask) & ~full) return fail(QS_ERR_INVALID_ARG, "term %zu exceeds n", k);
+  const uint64_t N = 1ull << s->n;
+  const int nblocks = (int)std::min<uint64_t>(608, std::max<uint64_t>(1, N / 256));
+  double* part = (double*)s->ws;
+  double* dres = part + (size_t)nblocks * 8;
+  std::vector<double> vals(nterms);
+  for (size_t k0 = 0; k0 < nterms; k0 += 8) {
+    PauliArgs g;
+    g.N = N;
+    g.nt = (int)std::min<size_t>(8, nterms - k0);
+    for (int k = 0; k < g.nt; ++k) {
+      g.xm[k] = terms[k0 + k].xmask;
+      g.zm[k] = terms[k0 + k].zmask;
+      g.ny[k] = __builtin_popcountll(terms[k0 + k].xmask & terms[k0 + k].zmask) & 3;
+    }
+    KTimer kt(s, QS_K_REDUCE, s->n, g.nt, 0, 0, (double)N, 4.0 * g.nt * (double)N);
+    k_pauli<<<nblocks, 256, 0, s->stream>>>(s->amps, g, part);
+    QS_TRY(launch_check("pauli"));
+    k_pauli_finish<<<1, 32, 0, s->stream>>>(part, nblocks, g.nt, dres);
+    QS_TRY(launch_check("pauli_finish"));
+    QS_TRY(read_back(s, dres, g.nt, vals.data() + k0));
+  }
+  double e = 0.0;
+  for (size_t k = 0; k < nterms; ++k) e += terms[k].coef * vals[k];
+  *out = e;
+  return QS_OK;
+}

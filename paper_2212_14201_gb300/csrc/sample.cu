@@ -1,0 +1,153 @@
+// Computational-basis sampling (measure_all / run_with_configuration in the
+// paper's API) with a bit-reproducible definition:
+//   u_s  = (SplitMix64 output s of the stream seeded `seed` >> 11) * 2^-53
+//          (Steele, Lea & Flood 2014; counter form: state = seed + (s+1)*gamma);
+//   p_x  = re*re + im*im, each product and the sum rounded separately;
+//   L    = min(1024, 2^n); T_b = p_{bL} + ... + p_{bL+L-1} summed left to right;
+//   E_0 = 0, E_{b+1} = E_b + T_b (left to right);
+//   shot s -> smallest x in the first block b with E_{b+1} > u_s such that
+//             E_b + (left-to-right partial sum of block b up to x) > u_s;
+//             if no block qualifies, the largest x with p_x > 0.
+// Three kernels: block totals (one thread per block, sequential), the prefix
+// (one thread, sequential, staged through shared memory), and one thread per shot
+// (binary search over E, then a sequential scan of one block).
+#include <algorithm>
+
+#include "internal.h"
+
+namespace qs {
+
+__device__ __forceinline__ double p_exact(double2 a) { return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)); }
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t s) {
+  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// T[b] = left-to-right block total; lastnz[b] = largest x in block b with p_x > 0, or -1.
+__global__ void k_block_totals(const double2* __restrict__ a, int64_t nb, int64_t L, double* __restrict__ T,
+                               long long* __restrict__ lastnz) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const double2* p = a + b * L;
+    double S = 0.0;
+    long long last = -1;
+    for (int64_t j = 0; j < L; j += 4) {
+      double2 v0 = p[j], v1 = p[j + 1 < L ? j + 1 : j], v2 = p[j + 2 < L ? j + 2 : j], v3 = p[j + 3 < L ? j + 3 : j];
+      double q0 = p_exact(v0);
+      S = __dadd_rn(S, q0);
+      if (q0 > 0.0) last = b * L + j;
+      if (j + 1 < L) { double q = p_exact(v1); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 1; }
+      if (j + 2 < L) { double q = p_exact(v2); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 2; }
+      if (j + 3 < L) { double q = p_exact(v3); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 3; }
+    }
+    T[b] = S;
+    lastnz[b] = last;
+  }
+}
+
+// E[0..nb]: exclusive-then-total prefix of T, left to right; lastnz[nb] = global last nonzero.
+__global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __restrict__ E, long long* __restrict__ lastnz) {
+  __shared__ double buf[2048];
+  __shared__ long long lbuf[2048];
+  __shared__ double carry;
+  __shared__ long long lcarry;
+  if (threadIdx.x == 0) {
+    carry = 0.0;
+    lcarry = -1;
+    E[0] = 0.0;
+  }
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < nb; c0 += 2048) {
+    int64_t cnt = min((int64_t)2048, nb - c0);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      buf[i] = T[c0 + i];
+      lbuf[i] = lastnz[c0 + i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double e = carry;
+      long long l = lcarry;
+      for (int i = 0; i < cnt; ++i) {
+        e = __dadd_rn(e, buf[i]);
+        buf[i] = e;
+        if (lbuf[i] >= 0) l = lbuf[i];
+      }
+      carry = e;
+      lcarry = l;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) E[c0 + i + 1] = buf[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lastnz[nb] = lcarry < 0 ? 0 : lcarry;  // all-zero state: index 0
+}
+
+__global__ void k_sample(const double2* __restrict__ a, const double* __restrict__ E, const long long* __restrict__ lastnz,
+                         int64_t nb, int64_t L, uint64_t seed, uint64_t shots, uint64_t* __restrict__ out) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < shots; s += (uint64_t)gridDim.x * blockDim.x) {
+    double u = (double)(splitmix64(seed, s) >> 11) * (1.0 / 9007199254740992.0);
+    int64_t lo = 0, hi = nb;
+    while (lo < hi) {
+      int64_t mid = lo + ((hi - lo) >> 1);
+      if (E[mid + 1] > u) hi = mid;
+      else lo = mid + 1;
+    }
+    if (lo == nb) {
+      out[s] = (uint64_t)lastnz[nb];
+      continue;
+    }
+    const int64_t b = lo;
+    const double eb = E[b];
+    const double2* p = a + b * L;
+    double S = 0.0;
+    int64_t pick = b * L + L - 1;
+    for (int64_t j = 0; j < L; ++j) {
+      S = __dadd_rn(S, p_exact(p[j]));
+      if (__dadd_rn(eb, S) > u) {
+        pick = b * L + j;
+        break;
+      }
+    }
+    out[s] = (uint64_t)pick;
+  }
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint64_t* out, int on_device) {
+  clear_error();
+  qs_state* s = const_cast<qs_state*>(cs);
+  QS_TRY(check_state(s));
+  if (shots == 0) return QS_OK;
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  const int64_t N = (int64_t)1 << s->n;
+  const int64_t L = N < 1024 ? N : 1024;
+  const int64_t nb = N / L;
+  double* T = (double*)s->ws;
+  double* E = T + (nb + 1);
+  long long* lastnz = (long long*)(E + (nb + 1));
+  int g1 = (int)std::min<int64_t>((nb + 127) / 128, 152 * 16);
+  KTimer kt(s, QS_K_REDUCE, s->n, 3, 0, 0, (double)N, 4.0 * (double)N);
+  k_block_totals<<<g1, 128, 0, s->stream>>>(s->amps, nb, L, T, lastnz);
+  QS_TRY(launch_check("block_totals"));
+  k_prefix<<<1, 256, 0, s->stream>>>(T, nb, E, lastnz);
+  QS_TRY(launch_check("prefix"));
+  uint64_t* dout = out;
+  if (!on_device) QS_CUDA(cudaMallocAsync((void**)&dout, shots * sizeof(uint64_t), s->stream));
+  int g3 = (int)std::min<uint64_t>((shots + 127) / 128, 152 * 16);
+  k_sample<<<g3, 128, 0, s->stream>>>(s->amps, E, lastnz, nb, L, seed, shots, dout);
+  int rc = launch_check("sample");
+  if (!on_device) {
+    if (rc == QS_OK) {
+      cudaError_t e = cudaMemcpyAsync(out, dout, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "sample readback");
+    }
+    cudaFreeAsync(dout, s->stream);
+  }
+  return rc;
+}

@@ -1,0 +1,46 @@
+// Shared-memory tile pass: one HBM read and one write of the state runs every op
+// of a fusion pass (the paper's circuit fusion, Section "Quantum circuit fusion";
+// gate data in fast on-chip memory, Section "GPU optimization").
+#pragma once
+
+#include "internal.h"
+
+namespace qs {
+
+constexpr int TILE_MAX_M = 12;  // 2^12 amplitudes x 16 B = 64 KiB of shared memory per CTA
+constexpr int TILE_LOW = 3;     // qubits 0..2 are always in a tile: 128-byte contiguous runs
+constexpr int TILE_MAX_OPS = 340;
+
+enum TileOpKind : int8_t {
+  TOP_PHASE1 = OP_PHASE1,
+  TOP_DIAG = OP_DIAG,
+  TOP_ANTI = OP_ANTI,
+  TOP_REAL = OP_REAL,
+  TOP_GENERAL = OP_GENERAL,
+  TOP_SCALAR = 9,  // diagonal op whose target lies outside the tile: a per-tile scalar
+};
+
+struct TileOp {
+  double2 m[4];        // matrix (for SCALAR: m[0] = d0, m[3] = d1)
+  uint64_t ext_cmask;  // control qubits outside the tile (global bit positions)
+  uint32_t lcmask;     // control qubits inside the tile (local bit positions)
+  int8_t kind;
+  int8_t tb;           // local target bit; global target bit for SCALAR
+  int8_t code0, code1;
+};
+
+struct TileArgs {
+  uint64_t ntiles;   // 2^(n - m)
+  int n, m;          // state qubits, tile qubits
+  int nhigh;         // tile qubits above the contiguous low run
+  int qhigh[TILE_MAX_M];  // their global positions (ascending)
+  int nout;          // qubits outside the tile
+  int outpos[QS_MAX_QUBITS];  // their global positions (ascending)
+  int nops;
+  TileOp ops[TILE_MAX_OPS];
+};
+static_assert(sizeof(TileArgs) < 32000, "tile arguments must fit the kernel parameter space");
+
+int launch_tile(qs_state* s, const TileArgs& args, double flops, int ngates);
+
+}  // namespace qs

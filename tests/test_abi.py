@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every entry point include/*.h declares, the record layouts agree, and
+argument validation rejects bad input before any device work."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2212_14201_gb300 import build
+    return build()
+
+
+def declared_symbols():
+    syms = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        syms += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(qs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(syms))
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(built)
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_gate_codes_and_layouts_agree_with_header():
+    text = open(os.path.join(ROOT, "include", "qsim.h")).read()
+    for name, code in w.GATE_CODES.items():
+        m = re.search(rf"QS_{name}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == code, name
+    from paper_2212_14201_gb300 import GATE_DTYPE, PAULI_DTYPE
+    assert GATE_DTYPE == w.GATE_DTYPE and GATE_DTYPE.itemsize == 56
+    assert PAULI_DTYPE == w.PAULI_DTYPE and PAULI_DTYPE.itemsize == 24
+
+
+def test_host_validation_without_gpu(built):
+    import paper_2212_14201_gb300 as q
+    with pytest.raises(q.QsimError) as e:
+        q.qs_alloc(0)
+    assert e.value.code == -1
+    with pytest.raises(q.QsimError):
+        q.qs_alloc(q.qs_max_qubits() + 1)
+    with pytest.raises(q.QsimError) as e:
+        q.qs_plan_create(4, w.pack([w.gate("H", 4)]), q.PLAN_PLAIN, 5)
+    assert "out of range" in str(e.value)
+    with pytest.raises(q.QsimError):
+        q.qs_plan_create(4, w.pack([w.gate("CNOT", 2, 2)]), q.PLAN_PLAIN, 5)
+    with pytest.raises(q.QsimError):
+        q.qs_plan_create(4, w.pack([w.gate("X", 1, ctrl_mask=0b10)]), q.PLAN_PLAIN, 5)
+
+
+def test_gate_list_dagger_reverses_and_flips(built):
+    import paper_2212_14201_gb300 as q
+    g = w.random_circuit(5, 30, 1)
+    d = q.qs_gate_list_dagger(g)
+    assert np.array_equal(d["type"], g["type"][::-1])
+    assert np.array_equal(d["dagger"], 1 - g["dagger"][::-1])
+    assert np.array_equal(d["p"], g["p"][::-1])

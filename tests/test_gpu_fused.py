@@ -1,0 +1,128 @@
+"""GPU parity of the fused path (greedy plan: shared-memory tile passes) against
+the CPU oracle, and fused-vs-plain agreement at the full n=30 benchmark size."""
+import numpy as np
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2212_14201_gb300 as q
+    q.build()
+    return q
+
+
+def fused(q, n, gates, params=None, init=None):
+    p = q.qs_plan_create(n, gates, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc(n)
+    try:
+        if init is not None:
+            q.qs_set_state(h, np.ascontiguousarray(init, dtype=np.complex128))
+        q.qs_apply(h, gates, params, p)
+        return q.qs_get_state(h), q.qs_plan_get_stats(p)
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(p)
+
+
+@pytest.mark.parametrize("n,ng,seed,p2", [(1, 30, 0, None), (3, 80, 1, None), (7, 200, 2, None), (12, 200, 0, None),
+                                          (13, 400, 3, 0.4), (15, 500, 4, 0.4), (19, 600, 5, 0.4), (22, 400, 6, 0.4)])
+def test_fused_random_circuits(q, orc, n, ng, seed, p2):
+    g = w.random_circuit(n, ng, seed, two_qubit_prob=p2)
+    psi, st = fused(q, n, g)
+    assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
+
+
+@pytest.mark.parametrize("n", [12, 14, 17, 21])
+def test_fused_brickwork(q, orc, n):
+    g = w.layered_u3_cz(n, 20, 1)
+    psi, st = fused(q, n, g)
+    assert st["n_tile_passes"] >= 1
+    assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
+
+
+def test_fused_controls_outside_tiles(q, orc):
+    n = 18
+    rng = w.SplitMix64(7)
+    recs = []
+    for i in range(400):
+        t = rng.below(n)
+        c = (t + 1 + rng.below(n - 1)) % n
+        d = (c + 1 + rng.below(n - 2)) % n
+        if d == t:
+            d = (d + 1) % n
+        k = i % 6
+        if k == 0:
+            recs.append(w.gate("X", t, ctrl_mask=(1 << c) | (1 << d)))
+        elif k == 1:
+            recs.append(w.gate("CR", c, t, theta=rng.angle()))
+        elif k == 2:
+            recs.append(w.gate("U3", t, theta=rng.angle(), phi=rng.angle(), lam=rng.angle(), ctrl_mask=1 << c))
+        elif k == 3:
+            recs.append(w.gate("T", t, ctrl_mask=1 << d, dagger=1))
+        elif k == 4:
+            recs.append(w.gate("Y", t, ctrl_mask=1 << c))
+        else:
+            recs.append(w.gate("RX", t, theta=rng.angle()))
+    g = w.pack(recs)
+    init = w.random_state_fast(n, 3)
+    init /= np.linalg.norm(init)
+    psi, _ = fused(q, n, g, init=init.view(np.complex128))
+    ref = orc.as_complex(orc.apply_circuit(init.copy(), n, g))
+    assert np.max(np.abs(psi - ref)) < TOL
+
+
+def test_fused_parametrised_plan_reused_across_params(q, orc):
+    n = 14
+    g, npar = w.hea_ansatz(n, 4)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc(n)
+    try:
+        for seed in (1, 2):
+            th = w.uniform_angles(npar, seed)
+            q.qs_set_zero(h)
+            q.qs_apply(h, g, th, p)
+            assert np.max(np.abs(q.qs_get_state(h) - orc.as_complex(orc.run(n, g, th)))) < TOL
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(p)
+
+
+def test_full_size_fused_vs_plain_and_invariants(q):
+    """n=30, depth-20 brickwork (the benchmark workload, its launch configuration):
+    fused and plain agree amplitude by amplitude on a sample; the norm stays 1;
+    after one layer <Z_i> = cos(theta_i) (CZ commutes with Z)."""
+    import torch
+    n = 30
+    g = w.layered_u3_cz(n, 20, 1)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    a = q.qs_alloc(n)
+    try:
+        q.qs_apply(a, g[:45], None, None)
+        ez = q.qs_expect_z_all(a)
+        assert np.max(np.abs(ez - np.cos(g["p"][:n, 0]))) < TOL
+        q.qs_set_zero(a)
+        q.qs_apply(a, g, None, p)
+        assert abs(q.qs_probs(a, [])[0] - 1.0) < TOL
+        idx = torch.randint(0, 1 << n, (1 << 16,), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+        amps = torch.empty(2 << n, dtype=torch.float64, device="cuda")
+        q.qs_get_state(a, amps)
+        fz = amps.view(torch.complex128)[idx].clone()
+        del amps
+        torch.cuda.empty_cache()
+        q.qs_set_zero(a)
+        q.qs_apply(a, g, None, None)
+        amps = torch.empty(2 << n, dtype=torch.float64, device="cuda")
+        q.qs_get_state(a, amps)
+        pl = amps.view(torch.complex128)[idx]
+        assert float((fz - pl).abs().max()) < TOL
+        del amps
+    finally:
+        q.qs_free(a)
+        q.qs_plan_free(p)
