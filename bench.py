@@ -37,6 +37,8 @@ SAMPLE_SEED = 11
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+# Integer multiply-add peak (Q60 engine): 152 SMs x 64 IMAD(.WIDE)/clk/SM x 2.07 GHz.
+INT_PEAK_OPS = 152 * 64 * 2.07e9
 
 
 def parse():
@@ -168,29 +170,38 @@ def roofline(records, hbm_peak_gbs):
     """Dominant kernel class by total device time; algorithmic bytes and flops per launch."""
     by = {}
     for r in records:
-        d = by.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0})
+        d = by.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0, "iops": 0.0})
         d["ms"] += r["ms"]
         d["launches"] += 1
         rw = 1 if r["kind"] == 20 else 2   # reductions read only; gate kernels read and write
         d["bytes"] += r["items"] * 16.0 * rw
         d["flops"] += r["flops"]
+        d["iops"] += r["int_ops"]
     kind, d = max(by.items(), key=lambda kv: kv[1]["ms"])
     per_ms = d["ms"] / d["launches"]
     bpl = d["bytes"] / d["launches"]
     fpl = d["flops"] / d["launches"]
+    ipl = d["iops"] / d["launches"]
     t_hbm = bpl / (hbm_peak_gbs * 1e9)
     t_fp = fpl / FP64_PEAK_FLOPS
+    t_int = ipl / INT_PEAK_OPS
     total = sum(v["ms"] for v in by.values())
-    if t_fp > t_hbm:
+    if t_fp > max(t_hbm, t_int):
         ach = fpl / (per_ms * 1e-3) / 1e12
         out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s (fp64)",
                "frac": ach / (FP64_PEAK_FLOPS / 1e12)}
+    elif t_int > t_hbm:
+        ach = ipl / (per_ms * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": INT_PEAK_OPS / 1e12, "unit": "Tmad/s (int32 multiply-add)",
+               "frac": ach / (INT_PEAK_OPS / 1e12)}
     else:
         ach = bpl / (per_ms * 1e-3) / 1e9
         out = {"bound": "hbm", "achieved": ach, "peak": hbm_peak_gbs, "unit": "GB/s", "frac": ach / hbm_peak_gbs}
     out.update({"kernel_kind": kind, "launches": d["launches"], "avg_launch_ms": per_ms,
                 "share_of_kernel_time": d["ms"] / total if total else None,
                 "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": fpl,
+                "algorithmic_int_mads_per_launch": ipl,
+                "hbm_frac": (bpl / (per_ms * 1e-3) / 1e9) / hbm_peak_gbs,
                 "traffic": traffic_for(kind)})
     return out
 
@@ -303,12 +314,21 @@ def run_ours(args, world, rank, local, pg):
     step_gate_ms = sum(r["ms"] for r in recs if r["kind"] in (1, 2, 3, 4, 5, 10, 11)) / args.steps
 
     plain = None
+    plain_fp64 = None
     if plan is not None and not args.no_plain:
-        pms, precs, _, _ = timed(None, max(1, args.steps - 1), 1)
+        ksteps = max(1, args.steps - 1)
+        pms, precs, _, _ = timed(None, ksteps, 1)
         pb = sum(r["items"] * 32.0 for r in precs if r["kind"] in (1, 2, 3, 4, 5))
-        pg_ms = sum(r["ms"] for r in precs if r["kind"] in (1, 2, 3, 4, 5)) / max(1, args.steps - 1)
+        pg_ms = sum(r["ms"] for r in precs if r["kind"] in (1, 2, 3, 4, 5)) / ksteps
         plain = {"value": world * amp_updates / (pms * 1e-3), "ms_per_step": pms,
-                 "hbm_gbs_algorithmic": pb / max(1, args.steps - 1) / (pg_ms * 1e-3) / 1e9}
+                 "hbm_gbs_algorithmic": pb / ksteps / (pg_ms * 1e-3) / 1e9,
+                 "roofline": roofline(precs, hbm_peak)}
+        # the same per-gate kernels with IEEE FP64 arithmetic (context: the FP64 pipe bound)
+        q.qs_set_arith(h, q.ARITH_FP64)
+        fms, frecs, _, _ = timed(None, 1, 1)
+        q.qs_set_arith(h, q.ARITH_AUTO)
+        plain_fp64 = {"value": world * amp_updates / (fms * 1e-3), "ms_per_step": fms,
+                      "roofline": roofline(frecs, hbm_peak)}
 
     # end to end through the public API: host gate list in, norm and samples out to host
     host_samples = np.empty(SHOTS, dtype=np.uint64)
@@ -341,7 +361,10 @@ def run_ours(args, world, rank, local, pg):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "int64",
+        "dtype_note": "complex128 state in HBM; gate arithmetic in Q60 fixed point (int64 limbs, 2^-60 "
+                      "resolution) on the integer pipe; reductions and sampling in f64",
+        "data": "synthetic",
         "config": {"workload": f"layered U3+CZ brickwork, n={n}, depth {args.depth} ({ng} gates), "
                                f"norm + {SHOTS} samples", "n": n, "gates": ng, "shots": SHOTS,
                    "mode": "fused" if plan is not None else "plain", "plan": plan_stats,
@@ -350,6 +373,7 @@ def run_ours(args, world, rank, local, pg):
         "hbm_gbs_note": "algorithmic bytes of the gate kernels / their device time",
         "norm2": norm2,
         "plain": plain,
+        "plain_fp64": plain_fp64,
         "roofline": roof,
         "peak_source": {"hbm": peak_src, "fp64": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
         "cpu_baseline": cpu,

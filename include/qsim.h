@@ -127,6 +127,27 @@ int qs_get_state(const qs_state* s, double* dst, int on_device);
 /* Wait for all work queued on the state's stream. */
 int qs_sync(const qs_state* s);
 
+/* Arithmetic of the gate kernels.  The state is complex128 in memory either way.
+ *   QS_ARITH_AUTO  (default) Q60 fixed point when every |re|, |im| is known to
+ *                  be <= 1.5 (true for any state of norm <= 1.5), else FP64;
+ *   QS_ARITH_FP64  IEEE double arithmetic on the FP64 pipe;
+ *   QS_ARITH_FIXED Q60 fixed point on the integer pipe: each component is
+ *                  rounded to a multiple of 2^-60 while a kernel holds it and
+ *                  products are exact to 2^-58; a state whose norm exceeds 1.5
+ *                  makes qs_apply return UNSUPPORTED.
+ * The bound is known after qs_alloc / qs_set_zero and is kept by qs_apply
+ * (unitary gates preserve the norm).  After qs_set_state, qs_alloc_external,
+ * qs_apply_matrix or qs_state_modified it is re-established by the next
+ * qs_apply from the squared norm (one reduction and one stream synchronisation). */
+#define QS_ARITH_AUTO 0
+#define QS_ARITH_FP64 1
+#define QS_ARITH_FIXED 2
+int qs_set_arith(qs_state* s, int mode);
+
+/* Tell the library that the amplitudes were written outside its calls (for
+ * example through the torch tensor of qs_alloc_external). */
+int qs_state_modified(qs_state* s);
+
 /* ---- gate application (directly_run; Section "High-performance simulation":
  * a circuit is an iteration of gates, each a map on the state vector) --------- */
 
@@ -237,7 +258,8 @@ typedef struct qs_timing_record {
   uint64_t qubit_mask; /* qubits the launch acts on (targets; tile qubits) */
   uint64_t ctrl_mask;  /* control qubits */
   double items;        /* amplitudes the launch reads (and writes) */
-  double flops;        /* floating-point operations the launch's arithmetic needs */
+  double flops;        /* floating-point operations the launch's arithmetic needs (FP64 engine) */
+  double int_ops;      /* 32x32->64 integer multiply-adds it needs (Q60 engine: 3 per real product) */
   double ms;           /* device time between the bracketing events */
 } qs_timing_record;
 

@@ -42,7 +42,7 @@ class PlanStats(ctypes.Structure):
 class TimingRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("k", ctypes.c_int32), ("n_ops", ctypes.c_int32),
                 ("qubit_mask", ctypes.c_uint64), ("ctrl_mask", ctypes.c_uint64), ("items", ctypes.c_double),
-                ("flops", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("int_ops", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
 K_PHASE1, K_DIAG, K_ANTI, K_REAL, K_GENERAL, K_DENSE, K_TILE, K_REDUCE, K_ADJOINT, K_OTHER = 1, 2, 3, 4, 5, 10, 11, 20, 30, 40
@@ -65,6 +65,8 @@ SIGNATURES = {
     "qs_set_state": (I32, [P, P, I32]),
     "qs_get_state": (I32, [P, P, I32]),
     "qs_sync": (I32, [P]),
+    "qs_set_arith": (I32, [P, I32]),
+    "qs_state_modified": (I32, [P]),
     "qs_apply": (I32, [P, P, SZ, P, P]),
     "qs_apply_matrix": (I32, [P, P, I32, U64, P]),
     "qs_gate_list_dagger": (I32, [P, SZ, P]),
@@ -90,7 +92,7 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
-                raise QsimError(-3, f"{LIB_PATH} is missing: build it with paper_2212_14201_gb300.build.build()")
+                raise QsimError(-3, f"{LIB_PATH} is missing: build it with paper_2212_14201_gb300.build()")
             l = ctypes.CDLL(LIB_PATH)
             for name, (res, args) in SIGNATURES.items():
                 f = getattr(l, name)
@@ -202,6 +204,17 @@ def qs_get_state(h: int, out=None):
 
 def qs_sync(h: int):
     _chk(lib().qs_sync(h))
+
+
+ARITH_AUTO, ARITH_FP64, ARITH_FIXED = 0, 1, 2
+
+
+def qs_set_arith(h: int, mode: int):
+    _chk(lib().qs_set_arith(h, mode))
+
+
+def qs_state_modified(h: int):
+    _chk(lib().qs_state_modified(h))
 
 
 def qs_apply(h: int, gates, params=None, plan: int | None = None):

@@ -13,6 +13,7 @@
 // vector and a Toffoli a quarter.
 #include <algorithm>
 
+#include "fixed.h"
 #include "internal.h"
 
 namespace qs {
@@ -92,25 +93,160 @@ __global__ void __launch_bounds__(256) k_op1(double2* __restrict__ a, const OpAr
   }
 }
 
+// ---- Q60 fixed-point variant (arithmetic on the integer pipe; see fixed.h) --------
+struct OpArgsFx {
+  QC u[4];
+  uint64_t cmask;
+  int64_t items;
+  int t, nfix;
+  int fix[16];
+  int code0, code1;
+};
+
+struct QV {
+  int64_t re, im;
+};
+
+__device__ __forceinline__ QV q_load(const double2& a) { return {q60_from_double(a.x), q60_from_double(a.y)}; }
+__device__ __forceinline__ double2 q_store(QV v) { return make_double2(q60_to_double(v.re), q60_to_double(v.im)); }
+
+// u0*a0 + u1*a1 (complex), a as limbs
+__device__ __forceinline__ QV q_mv2(const QC& u0, QL a0r, QL a0i, const QC& u1, QL a1r, QL a1i) {
+  QAcc re{0, 0}, im{0, 0};
+  qacc_add(re, u0.re, a0r);
+  qacc_add(re, u0.nim, a0i);
+  qacc_add(re, u1.re, a1r);
+  qacc_add(re, u1.nim, a1i);
+  qacc_add(im, u0.re, a0i);
+  qacc_add(im, u0.im, a0r);
+  qacc_add(im, u1.re, a1i);
+  qacc_add(im, u1.im, a1r);
+  return {qacc_result(re), qacc_result(im)};
+}
+
+// u*a (complex)
+__device__ __forceinline__ QV q_mul(const QC& u, QL ar, QL ai) {
+  QAcc re{0, 0}, im{0, 0};
+  qacc_add(re, u.re, ar);
+  qacc_add(re, u.nim, ai);
+  qacc_add(im, u.re, ai);
+  qacc_add(im, u.im, ar);
+  return {qacc_result(re), qacc_result(im)};
+}
+
+// real 2x2: u0.re*a0 + u1.re*a1
+__device__ __forceinline__ QV q_real2(const QC& u0, QL a0r, QL a0i, const QC& u1, QL a1r, QL a1i) {
+  QAcc re{0, 0}, im{0, 0};
+  qacc_add(re, u0.re, a0r);
+  qacc_add(re, u1.re, a1r);
+  qacc_add(im, u0.re, a0i);
+  qacc_add(im, u1.re, a1i);
+  return {qacc_result(re), qacc_result(im)};
+}
+
+__device__ __forceinline__ double2 fx_mul(double2 a, int code, const QC& u) {
+  if (code != U_GENERAL) return mul_unit(a, code);
+  QV v = q_load(a);
+  return q_store(q_mul(u, q60_split(v.re), q60_split(v.im)));
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(256) k_op1_fx(double2* __restrict__ a, const OpArgsFx g) {
+  const uint64_t tb = 1ull << g.t;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (uint64_t)g.items; i += stride) {
+    uint64_t x0 = i;
+    for (int k = 0; k < g.nfix; ++k) {
+      int f = g.fix[k];
+      x0 = ((x0 >> f) << (f + 1)) | (x0 & ((1ull << f) - 1));
+    }
+    x0 |= g.cmask;
+    const uint64_t x1 = x0 | tb;
+    if (CLS == OP_PHASE1) {
+      a[x1] = fx_mul(a[x1], g.code1, g.u[3]);
+    } else if (CLS == OP_DIAG) {
+      double2 a0 = a[x0], a1 = a[x1];
+      a[x0] = fx_mul(a0, g.code0, g.u[0]);
+      a[x1] = fx_mul(a1, g.code1, g.u[3]);
+    } else if (CLS == OP_ANTI) {
+      double2 a0 = a[x0], a1 = a[x1];
+      a[x0] = fx_mul(a1, g.code0, g.u[1]);
+      a[x1] = fx_mul(a0, g.code1, g.u[2]);
+    } else {
+      QV v0 = q_load(a[x0]), v1 = q_load(a[x1]);
+      QL r0 = q60_split(v0.re), i0 = q60_split(v0.im), r1 = q60_split(v1.re), i1 = q60_split(v1.im);
+      QV b0, b1;
+      if (CLS == OP_REAL) {
+        b0 = q_real2(g.u[0], r0, i0, g.u[1], r1, i1);
+        b1 = q_real2(g.u[2], r0, i0, g.u[3], r1, i1);
+      } else {
+        b0 = q_mv2(g.u[0], r0, i0, g.u[1], r1, i1);
+        b1 = q_mv2(g.u[2], r0, i0, g.u[3], r1, i1);
+      }
+      a[x0] = q_store(b0);
+      a[x1] = q_store(b1);
+    }
+  }
+}
+
 static int grid_for(int64_t items, int threads) {
   int64_t b = (items + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
 }
 
-int launch_op1(qs_state* s, const Op1& op) {
+static bool needs_arith(const Op1& op) {
+  if (op.cls == OP_REAL || op.cls == OP_GENERAL) return true;
+  if (op.cls == OP_PHASE1) return op.code1 == U_GENERAL;
+  return op.code0 == U_GENERAL || op.code1 == U_GENERAL;
+}
+
+int launch_op1(qs_state* s, const Op1& op, bool fixed) {
   if (op.cls == OP_IDENTITY) return QS_OK;
+  if (fixed && needs_arith(op)) {
+    OpArgsFx g;
+    for (int i = 0; i < 4; ++i) g.u[i] = qc_make(op.m.m[i].re, op.m.m[i].im);
+    g.cmask = op.cmask;
+    g.t = op.target;
+    g.code0 = op.code0;
+    g.code1 = op.code1;
+    uint64_t fx = op.cmask | (1ull << op.target);
+    int nf = __builtin_popcountll(fx);
+    if (nf > 16) return fail(QS_ERR_UNSUPPORTED, "more than 15 controls");
+    g.nfix = 0;
+    for (int b = 0; b < 64; ++b)
+      if ((fx >> b) & 1) g.fix[g.nfix++] = b;
+    g.items = (int64_t)1 << (s->n - nf);
+    const int T = 256;
+    int grid = grid_for(g.items, T);
+    double amps = op.cls == OP_PHASE1 ? (double)g.items : 2.0 * (double)g.items;
+    // algorithmic limb products: 3 per real product; a general 2x2 needs 8 real
+    // products per amplitude, a real 2x2 4, a general phase 4
+    double ipa = op.cls == OP_GENERAL ? 24.0 : op.cls == OP_REAL ? 12.0 : 0.0;
+    if (op.cls == OP_PHASE1) ipa = 12.0;
+    if (op.cls == OP_DIAG || op.cls == OP_ANTI)
+      ipa = 6.0 * ((op.code0 == U_GENERAL ? 1.0 : 0.0) + (op.code1 == U_GENERAL ? 1.0 : 0.0));
+    KTimer kt(s, op.cls, 1, 1, 1ull << op.target, op.cmask, amps, 0.0, ipa * amps);
+    switch (op.cls) {
+      case OP_PHASE1: k_op1_fx<OP_PHASE1><<<grid, T, 0, s->stream>>>(s->amps, g); break;
+      case OP_DIAG: k_op1_fx<OP_DIAG><<<grid, T, 0, s->stream>>>(s->amps, g); break;
+      case OP_ANTI: k_op1_fx<OP_ANTI><<<grid, T, 0, s->stream>>>(s->amps, g); break;
+      case OP_REAL: k_op1_fx<OP_REAL><<<grid, T, 0, s->stream>>>(s->amps, g); break;
+      default: k_op1_fx<OP_GENERAL><<<grid, T, 0, s->stream>>>(s->amps, g); break;
+    }
+    return launch_check("op1 fixed-point kernel");
+  }
   OpArgs g;
   for (int i = 0; i < 4; ++i) g.m[i] = make_double2(op.m.m[i].re, op.m.m[i].im);
   g.cmask = op.cmask;
   g.t = op.target;
   g.code0 = op.code0;
   g.code1 = op.code1;
-  uint64_t fixed = op.cmask | (1ull << op.target);
-  int nf = __builtin_popcountll(fixed);
+  uint64_t fixbits = op.cmask | (1ull << op.target);
+  int nf = __builtin_popcountll(fixbits);
   if (nf > 16) return fail(QS_ERR_UNSUPPORTED, "more than 15 controls");
   g.nfix = 0;
   for (int b = 0; b < 64; ++b)
-    if ((fixed >> b) & 1) g.fix[g.nfix++] = b;
+    if ((fixbits >> b) & 1) g.fix[g.nfix++] = b;
   g.items = (int64_t)1 << (s->n - nf);
   const int T = 256;
   int grid = grid_for(g.items, T);
@@ -219,20 +355,23 @@ int launch_dense(qs_state* s, const int* targets, int k, uint64_t cmask, const C
 
 using namespace qs;
 
-int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan);
+int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan,
+                  bool fixed);
 
 extern "C" int qs_apply(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan) {
   clear_error();
   QS_TRY(check_state(s));
   QS_TRY(validate_gates(gates, ng, s->n, params));
-  if (plan) return qs_apply_plan(s, gates, ng, params, plan);
+  bool fixed = false;
+  QS_TRY(choose_fixed(s, &fixed));
+  if (plan) return qs_apply_plan(s, gates, ng, params, plan, fixed);
   for (size_t k = 0; k < ng; ++k) {
     int t;
     uint64_t cm;
     Mat2 m;
     QS_TRY(gate_qubits(gates[k], s->n, &t, &cm));
     QS_TRY(gate_matrix(gates[k], params, &m));
-    QS_TRY(launch_op1(s, classify(t, cm, m)));
+    QS_TRY(launch_op1(s, classify(t, cm, m), fixed));
   }
   return QS_OK;
 }
@@ -250,5 +389,6 @@ extern "C" int qs_apply_matrix(qs_state* s, const int* targets, int k, uint64_t 
     tm |= 1ull << targets[j];
   }
   if ((ctrl_mask & ~full) || (ctrl_mask & tm)) return fail(QS_ERR_INVALID_ARG, "bad control mask");
+  s->bound = 0;  // the matrix need not be unitary
   return launch_dense(s, targets, k, ctrl_mask, (const C2*)mat);
 }

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 
+#include "fixed.h"
 #include "internal.h"
 
 namespace qs {
@@ -78,7 +79,8 @@ static cudaEvent_t take_event(qs_state* s) {
   return e;
 }
 
-KTimer::KTimer(qs_state* st, int kind, int k, int n_ops, uint64_t qmask, uint64_t cmask, double items, double flops)
+KTimer::KTimer(qs_state* st, int kind, int k, int n_ops, uint64_t qmask, uint64_t cmask, double items, double flops,
+               double int_ops)
     : s(st), on(st->timing) {
   note_launch(1);
   if (!on) return;
@@ -90,6 +92,7 @@ KTimer::KTimer(qs_state* st, int kind, int k, int n_ops, uint64_t qmask, uint64_
   pt.rec.ctrl_mask = cmask;
   pt.rec.items = items;
   pt.rec.flops = flops;
+  pt.rec.int_ops = int_ops;
   pt.rec.ms = 0.0;
   pt.e0 = take_event(st);
   pt.e1 = take_event(st);
@@ -257,6 +260,7 @@ static int create(int n, void* dev, void* stream, qs_state** out) {
   if (dev) {
     s->amps = (double2*)dev;
     s->owns = false;
+    s->bound = 0;
   } else {
     cudaError_t e = cudaMalloc(&s->amps, bytes);
     if (e != cudaSuccess) {
@@ -282,8 +286,43 @@ extern "C" int qs_set_zero(qs_state* s) {
   int blocks = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
   KTimer kt(s, QS_K_OTHER, 0, 0, 0, 0, (double)N, 0.0);
   k_set_zero<<<blocks, 256, 0, s->stream>>>(s->amps, N);
+  s->bound = 1;
   return launch_check("set_zero");
 }
+
+extern "C" int qs_set_arith(qs_state* s, int mode) {
+  QS_TRY(check_state(s));
+  if (mode != QS_ARITH_AUTO && mode != QS_ARITH_FP64 && mode != QS_ARITH_FIXED)
+    return fail(QS_ERR_INVALID_ARG, "arith mode %d", mode);
+  s->arith = mode;
+  return QS_OK;
+}
+
+extern "C" int qs_state_modified(qs_state* s) {
+  QS_TRY(check_state(s));
+  s->bound = 0;
+  return QS_OK;
+}
+
+namespace qs {
+int choose_fixed(qs_state* s, bool* fixed) {
+  *fixed = false;
+  if (s->arith == QS_ARITH_FP64) return QS_OK;
+  if (s->bound == 0) {
+    double norm2 = 0.0;
+    QS_TRY(qs_probs(s, nullptr, 0, &norm2, 0));
+    // every component is at most the norm; unitary gates keep the norm
+    s->bound = (norm2 <= Q60_MAX_ABS * Q60_MAX_ABS) ? 1 : 2;
+  }
+  if (s->bound == 1) {
+    *fixed = true;
+    return QS_OK;
+  }
+  if (s->arith == QS_ARITH_FIXED)
+    return fail(QS_ERR_UNSUPPORTED, "Q60 arithmetic needs a state of norm <= %.2f", Q60_MAX_ABS);
+  return QS_OK;
+}
+}  // namespace qs
 
 extern "C" int qs_alloc(int n, void* stream, qs_state** out) {
   QS_TRY(create(n, nullptr, stream, out));
@@ -334,6 +373,7 @@ extern "C" int qs_set_state(qs_state* s, const double* amps, int on_device) {
   QS_CUDA(cudaMemcpyAsync(s->amps, amps, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           s->stream));
   if (!on_device) QS_CUDA(cudaStreamSynchronize(s->stream));
+  s->bound = 0;
   return QS_OK;
 }
 

@@ -1,0 +1,153 @@
+// Q60 fixed-point arithmetic for gate application on the integer pipe.
+//
+// GB300 issues FP64 at 1/74 of its FP32 rate (measured: 5.0e11 DFMA/s against
+// 1.8e13 32x32->64 integer multiply-adds/s), so a complex128 2x2 gate costs
+// ~3x its HBM time in FP64.  The state stays complex128 in memory; inside a
+// kernel each real component v (|v| <= 1.5) is converted to V = round(v * 2^60),
+// a signed 64-bit integer, and gate matrices (|u| <= 1) likewise.  A product
+// U*A is formed from 32-bit limbs, V = h * 2^32 + l with l signed:
+//   U*A * 2^-60 = Uh*Ah * 2^4 + (Uh*Al + Ul*Ah) * 2^-28 + Ul*Al * 2^-60,
+// the first two terms accumulated exactly in two int64 registers with
+// mad.wide.s32, the last (|.| < 2^-58 per product) dropped.  One output
+// component of a 2x2 complex matvec (four products) carries at most
+// 4 * 2^-58 + 2^-61 absolute error before the final rounding back to double
+// (which adds the same <= 2^-53 relative error an FP64 kernel has).
+// Bounds for |components| <= 1.5: |h| <= 1.5 * 2^28, |l| <= 2^31, so the hi
+// accumulator stays below 2^59 and the mid accumulator below 2^63.
+#pragma once
+
+#include <stdint.h>
+#include <string.h>
+
+#ifdef __CUDACC__
+#define QS_HD __host__ __device__ __forceinline__
+#else
+#define QS_HD inline
+#endif
+
+namespace qs {
+
+constexpr double Q60_MAX_ABS = 1.5;  // component bound under which the accumulators cannot overflow
+
+QS_HD uint64_t q_bits(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(v);
+#else
+  uint64_t b;
+  memcpy(&b, &v, 8);
+  return b;
+#endif
+}
+
+QS_HD double q_from_bits(uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double v;
+  memcpy(&v, &b, 8);
+  return v;
+#endif
+}
+
+QS_HD int q_clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// round(v * 2^60), ties away from zero; |v| must be < 8.  Integer operations only.
+QS_HD int64_t q60_from_double(double v) {
+  const uint64_t b = q_bits(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;  // zero or subnormal (< 2^-1022): rounds to 0
+  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = e - 1015;  // V = mant * 2^(e - 1075 + 60)
+  uint64_t mag;
+  if (sh >= 0) {
+    mag = mant << sh;  // exact (sh <= 9 for |v| < 8)
+  } else if (sh > -54) {
+    mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+  } else {
+    mag = 0;
+  }
+  return (b >> 63) ? -(int64_t)mag : (int64_t)mag;
+}
+
+// Nearest double to V * 2^-60 (round half to even).  Integer operations only.
+QS_HD double q60_to_double(int64_t V) {
+  if (V == 0) return 0.0;
+  const uint64_t sign = (uint64_t)V >> 63;
+  uint64_t a = sign ? (uint64_t)0 - (uint64_t)V : (uint64_t)V;
+  int msb = 63 - q_clz64(a);
+  uint64_t mant;
+  if (msb <= 52) {
+    mant = a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    mant = a >> sh;
+    const uint64_t rem = a & ((1ull << sh) - 1);
+    const uint64_t half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++msb;
+      }
+    }
+  }
+  const uint64_t e = (uint64_t)(msb - 60 + 1023);
+  return q_from_bits((sign << 63) | (e << 52) | (mant & 0xFFFFFFFFFFFFFull));
+}
+
+// Limb split V = h * 2^32 + l, l the signed low 32 bits.
+struct QL {
+  int32_t h, l;
+};
+
+QS_HD QL q60_split(int64_t V) {
+  const int32_t l = (int32_t)(uint32_t)(uint64_t)V;
+  return {(int32_t)((V - (int64_t)l) >> 32), l};
+}
+
+QS_HD int64_t madw(int32_t a, int32_t b, int64_t c) {
+#ifdef __CUDA_ARCH__
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"((long long)c));
+  return (int64_t)d;
+#else
+  return c + (int64_t)a * (int64_t)b;
+#endif
+}
+
+// Accumulator pair of a sum of products (see the header comment).
+struct QAcc {
+  int64_t hi, mid;
+};
+
+QS_HD void qacc_add(QAcc& acc, QL u, QL a) {
+  acc.hi = madw(u.h, a.h, acc.hi);
+  acc.mid = madw(u.h, a.l, acc.mid);
+  acc.mid = madw(u.l, a.h, acc.mid);
+}
+
+QS_HD int64_t qacc_result(const QAcc& acc) {
+  return (int64_t)((uint64_t)acc.hi << 4) + ((acc.mid + (1ll << 27)) >> 28);
+}
+
+// A Q60 complex number as limbs, plus its negated imaginary part (so that
+// re = ur*ar - ui*ai needs only additions).
+struct QC {
+  QL re, im, nim;
+};
+
+QS_HD QC qc_make(double re, double im) {
+  QC c;
+  c.re = q60_split(q60_from_double(re));
+  c.im = q60_split(q60_from_double(im));
+  c.nim = q60_split(-q60_from_double(im));
+  return c;
+}
+
+}  // namespace qs

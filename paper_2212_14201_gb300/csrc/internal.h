@@ -28,6 +28,11 @@ struct qs_state {
   // Pinned host staging for small reduction results.
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
+  // Arithmetic of the gate kernels (QS_ARITH_*) and what is known about the
+  // magnitude of the amplitudes: 1 = every |re|, |im| <= 1.5 (the Q60 engine is
+  // safe), 2 = possibly larger, 0 = unknown (checked on the next apply).
+  int arith = 0;
+  int bound = 1;
   // Per-kernel timing log (qs_timing_enable / qs_timing_fetch).
   bool timing = false;
   std::vector<qs_pending_timing> pending;
@@ -92,7 +97,10 @@ Op1 classify(int target, uint64_t cmask, const Mat2& m);
 int unit_code(const C2& z);
 
 // ---- kernels (launchers) --------------------------------------------------------
-int launch_op1(qs_state* s, const Op1& op);
+// Whether the next gate kernels of this state run in Q60 fixed point (may
+// synchronise once to bound an unknown state's magnitude).
+int choose_fixed(qs_state* s, bool* fixed);
+int launch_op1(qs_state* s, const Op1& op, bool fixed);
 int launch_dense(qs_state* s, const int* targets, int k, uint64_t cmask, const C2* mat);
 
 // ---- instrumentation -------------------------------------------------------------
@@ -103,7 +111,8 @@ struct KTimer {
   qs_state* s;
   qs_pending_timing pt;
   bool on;
-  KTimer(qs_state* s, int kind, int k, int n_ops, uint64_t qmask, uint64_t cmask, double items, double flops);
+  KTimer(qs_state* s, int kind, int k, int n_ops, uint64_t qmask, uint64_t cmask, double items, double flops,
+         double int_ops = 0.0);
   ~KTimer();
 };
 

@@ -82,6 +82,16 @@ double op_flops_per_amp(int type) {
   }
 }
 
+// Q60 engine: limb products (3 per real product) per touched amplitude.
+double op_int_ops_per_amp(const Op1& op) {
+  switch (op.cls) {
+    case OP_GENERAL: return 24.0;
+    case OP_REAL: return 12.0;
+    case OP_PHASE1: return op.code1 == U_GENERAL ? 12.0 : 0.0;
+    default: return 6.0 * ((op.code0 == U_GENERAL ? 1.0 : 0.0) + (op.code1 == U_GENERAL ? 1.0 : 0.0));
+  }
+}
+
 double op_touch_fraction(const qs_gate& g, uint64_t cmask) {
   double f = 1.0 / (double)(1ull << __builtin_popcountll(cmask));
   if (g.type == QS_Z || g.type == QS_S || g.type == QS_T || g.type == QS_P || g.type == QS_CZ || g.type == QS_CR)
@@ -221,7 +231,7 @@ extern "C" int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint6
   return QS_OK;
 }
 
-static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params) {
+static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed) {
   const int n = s->n;
   TileArgs* g = new (std::nothrow) TileArgs;
   if (!g) return fail(QS_ERR_OOM, "host allocation failed");
@@ -243,7 +253,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   for (int b = 0; b < n; ++b)
     if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
   g->nops = 0;
-  double flops = 0.0;
+  double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
   int rc = QS_OK;
   for (uint32_t k : ps.gates) {
@@ -255,7 +265,10 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     Op1 op = classify(t, cm, mat);
     if (op.cls == OP_IDENTITY) continue;
     TileOp& to = g->ops[g->nops];
-    for (int i = 0; i < 4; ++i) to.m[i] = make_double2(mat.m[i].re, mat.m[i].im);
+    if (fixed)
+      for (int i = 0; i < 4; ++i) to.q[i] = qc_make(mat.m[i].re, mat.m[i].im);
+    else
+      for (int i = 0; i < 4; ++i) to.m[i] = make_double2(mat.m[i].re, mat.m[i].im);
     to.code0 = (int8_t)op.code0;
     to.code1 = (int8_t)op.code1;
     uint32_t lcm = 0;
@@ -279,14 +292,17 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       to.tb = (int8_t)t;
     }
     flops += N * op_touch_fraction(gates[k], cm) * op_flops_per_amp(gates[k].type);
+    int_ops += N * op_touch_fraction(gates[k], cm) * op_int_ops_per_amp(op);
     ++g->nops;
   }
-  if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, flops, (int)ps.gates.size());
+  if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,
+                                                   (int)ps.gates.size(), fixed);
   delete g;
   return rc;
 }
 
-int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan) {
+int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan,
+                  bool fixed) {
   if (plan->n != s->n || plan->ng != ng || plan->fingerprint != fingerprint(gates, ng))
     return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
   for (const PlanPass& ps : plan->passes) {
@@ -297,9 +313,9 @@ int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* pa
       Mat2 m;
       QS_TRY(gate_qubits(g, s->n, &t, &cm));
       QS_TRY(gate_matrix(g, params, &m));
-      QS_TRY(launch_op1(s, classify(t, cm, m)));
+      QS_TRY(launch_op1(s, classify(t, cm, m), fixed));
     } else {
-      QS_TRY(run_tile_pass(s, ps, gates, params));
+      QS_TRY(run_tile_pass(s, ps, gates, params, fixed));
     }
   }
   return QS_OK;

@@ -8,29 +8,13 @@
 //     tiles where one of them is 0;
 //   - a diagonal op whose target lies outside the tile is a scalar for the tile.
 // Gate matrices travel in the kernel parameters (constant bank).
+// Two arithmetic engines share the structure: FP64 (tile of double2) and Q60
+// fixed point (tile of int64 pairs, converted once on load and once on store).
 #include <algorithm>
 
 #include "tile.h"
 
 namespace qs {
-
-__device__ __forceinline__ double tneg(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
-}
-
-__device__ __forceinline__ double2 tmul_unit(double2 a, int code) {
-  switch (code) {
-    case U_ONE: return a;
-    case U_I: return make_double2(tneg(a.y), a.x);
-    case U_MINUS_ONE: return make_double2(tneg(a.x), tneg(a.y));
-    default: return make_double2(a.y, tneg(a.x));
-  }
-}
-
-__device__ __forceinline__ double2 tmul(double2 a, int code, double2 u) {
-  if (code != U_GENERAL) return tmul_unit(a, code);
-  return make_double2(fma(u.x, a.x, -u.y * a.y), fma(u.x, a.y, u.y * a.x));
-}
 
 // Insert zero bits at the set positions of `fixed` (ascending), then OR `set`.
 __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint32_t set) {
@@ -42,15 +26,112 @@ __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint
   return i | set;
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tile_f64(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
+// ---- FP64 engine -------------------------------------------------------------------
+struct EngF64 {
+  using T = double2;
+  static __device__ __forceinline__ double neg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+  }
+  static __device__ __forceinline__ T load(const double2& a) { return a; }
+  static __device__ __forceinline__ double2 store(const T& a) { return a; }
+  static __device__ __forceinline__ T unit(T a, int code) {
+    switch (code) {
+      case U_ONE: return a;
+      case U_I: return make_double2(neg(a.y), a.x);
+      case U_MINUS_ONE: return make_double2(neg(a.x), neg(a.y));
+      default: return make_double2(a.y, neg(a.x));
+    }
+  }
+  static __device__ __forceinline__ T mul(T a, int code, const TileOp& op, int e) {
+    if (code != U_GENERAL) return unit(a, code);
+    const double2 u = op.m[e];
+    return make_double2(fma(u.x, a.x, -u.y * a.y), fma(u.x, a.y, u.y * a.x));
+  }
+  static __device__ __forceinline__ void real2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
+    b0 = make_double2(fma(op.m[0].x, a0.x, op.m[1].x * a1.x), fma(op.m[0].x, a0.y, op.m[1].x * a1.y));
+    b1 = make_double2(fma(op.m[2].x, a0.x, op.m[3].x * a1.x), fma(op.m[2].x, a0.y, op.m[3].x * a1.y));
+  }
+  static __device__ __forceinline__ void general2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
+    const double2 u0 = op.m[0], u1 = op.m[1], u2 = op.m[2], u3 = op.m[3];
+    b0.x = fma(u0.x, a0.x, fma(-u0.y, a0.y, fma(u1.x, a1.x, -u1.y * a1.y)));
+    b0.y = fma(u0.x, a0.y, fma(u0.y, a0.x, fma(u1.x, a1.y, u1.y * a1.x)));
+    b1.x = fma(u2.x, a0.x, fma(-u2.y, a0.y, fma(u3.x, a1.x, -u3.y * a1.y)));
+    b1.y = fma(u2.x, a0.y, fma(u2.y, a0.x, fma(u3.x, a1.y, u3.y * a1.x)));
+  }
+};
+
+// ---- Q60 fixed-point engine ----------------------------------------------------------
+struct EngQ60 {
+  using T = longlong2;
+  static __device__ __forceinline__ T load(const double2& a) {
+    return make_longlong2(q60_from_double(a.x), q60_from_double(a.y));
+  }
+  static __device__ __forceinline__ double2 store(const T& a) {
+    return make_double2(q60_to_double(a.x), q60_to_double(a.y));
+  }
+  static __device__ __forceinline__ T unit(T a, int code) {
+    switch (code) {
+      case U_ONE: return a;
+      case U_I: return make_longlong2(-a.y, a.x);
+      case U_MINUS_ONE: return make_longlong2(-a.x, -a.y);
+      default: return make_longlong2(a.y, -a.x);
+    }
+  }
+  static __device__ __forceinline__ T mul(T a, int code, const TileOp& op, int e) {
+    if (code != U_GENERAL) return unit(a, code);
+    const QC& u = op.q[e];
+    const QL ar = q60_split(a.x), ai = q60_split(a.y);
+    QAcc re{0, 0}, im{0, 0};
+    qacc_add(re, u.re, ar);
+    qacc_add(re, u.nim, ai);
+    qacc_add(im, u.re, ai);
+    qacc_add(im, u.im, ar);
+    return make_longlong2(qacc_result(re), qacc_result(im));
+  }
+  static __device__ __forceinline__ void real2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
+    const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+    QAcc x{0, 0}, y{0, 0}, z{0, 0}, w{0, 0};
+    qacc_add(x, op.q[0].re, r0);
+    qacc_add(x, op.q[1].re, r1);
+    qacc_add(y, op.q[0].re, i0);
+    qacc_add(y, op.q[1].re, i1);
+    qacc_add(z, op.q[2].re, r0);
+    qacc_add(z, op.q[3].re, r1);
+    qacc_add(w, op.q[2].re, i0);
+    qacc_add(w, op.q[3].re, i1);
+    b0 = make_longlong2(qacc_result(x), qacc_result(y));
+    b1 = make_longlong2(qacc_result(z), qacc_result(w));
+  }
+  static __device__ __forceinline__ void general2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
+    const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const QC& u0 = op.q[2 * row];
+      const QC& u1 = op.q[2 * row + 1];
+      QAcc re{0, 0}, im{0, 0};
+      qacc_add(re, u0.re, r0);
+      qacc_add(re, u0.nim, i0);
+      qacc_add(re, u1.re, r1);
+      qacc_add(re, u1.nim, i1);
+      qacc_add(im, u0.re, i0);
+      qacc_add(im, u0.im, r0);
+      qacc_add(im, u1.re, i1);
+      qacc_add(im, u1.im, r1);
+      (row == 0 ? b0 : b1) = make_longlong2(qacc_result(re), qacc_result(im));
+    }
+  }
+};
+
+template <class E, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tile(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
+  using T = typename E::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = g.m;
   const int L = m - g.nhigh;
-  const uint32_t T = 1u << m;
+  const uint32_t TS = 1u << m;
   const uint32_t H = 1u << g.nhigh;
   uint64_t* offs = reinterpret_cast<uint64_t*>(smem_raw);  // [H] offsets of the high tile bits
-  double2* tile = reinterpret_cast<double2*>(smem_raw + ((H * sizeof(uint64_t) + 15) & ~(size_t)15));
+  T* tile = reinterpret_cast<T*>(smem_raw + ((H * sizeof(uint64_t) + 15) & ~(size_t)15));
   for (uint32_t h = threadIdx.x; h < H; h += THREADS) {
     uint64_t o = 0;
     for (int b = 0; b < g.nhigh; ++b) o |= (uint64_t)((h >> b) & 1u) << g.qhigh[b];
@@ -61,7 +142,7 @@ __global__ void __launch_bounds__(THREADS) k_tile_f64(double2* __restrict__ a, c
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
     __syncthreads();  // offs ready / previous tile stored
-    for (uint32_t j = threadIdx.x; j < T; j += THREADS) tile[j] = a[base + offs[j >> L] + (j & lowmask)];
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
     __syncthreads();
     for (int k = 0; k < g.nops; ++k) {
       const TileOp& op = g.ops[k];
@@ -71,40 +152,35 @@ __global__ void __launch_bounds__(THREADS) k_tile_f64(double2* __restrict__ a, c
         const bool one = (base >> op.tb) & 1ull;
         const int code = one ? op.code1 : op.code0;
         if (code == U_ONE) continue;
-        const double2 d = one ? op.m[3] : op.m[0];
-        const uint32_t cnt = T >> __popc(lcm);
+        const int e = one ? 3 : 0;
+        const uint32_t cnt = TS >> __popc(lcm);
         for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
           uint32_t j = tile_expand(i, lcm, lcm);
-          tile[j] = tmul(tile[j], code, d);
+          tile[j] = E::mul(tile[j], code, op, e);
         }
       } else {
         const uint32_t tb = 1u << op.tb;
         const uint32_t fixed = lcm | tb;
-        const uint32_t cnt = T >> __popc(fixed);
+        const uint32_t cnt = TS >> __popc(fixed);
         if (op.kind == TOP_PHASE1) {
           for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
             uint32_t j = tile_expand(i, fixed, lcm) | tb;
-            tile[j] = tmul(tile[j], op.code1, op.m[3]);
+            tile[j] = E::mul(tile[j], op.code1, op, 3);
           }
         } else {
           for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
             uint32_t j0 = tile_expand(i, fixed, lcm), j1 = j0 | tb;
-            double2 a0 = tile[j0], a1 = tile[j1], b0, b1;
+            T a0 = tile[j0], a1 = tile[j1], b0, b1;
             if (op.kind == TOP_DIAG) {
-              b0 = tmul(a0, op.code0, op.m[0]);
-              b1 = tmul(a1, op.code1, op.m[3]);
+              b0 = E::mul(a0, op.code0, op, 0);
+              b1 = E::mul(a1, op.code1, op, 3);
             } else if (op.kind == TOP_ANTI) {
-              b0 = tmul(a1, op.code0, op.m[1]);
-              b1 = tmul(a0, op.code1, op.m[2]);
+              b0 = E::mul(a1, op.code0, op, 1);
+              b1 = E::mul(a0, op.code1, op, 2);
             } else if (op.kind == TOP_REAL) {
-              b0 = make_double2(fma(op.m[0].x, a0.x, op.m[1].x * a1.x), fma(op.m[0].x, a0.y, op.m[1].x * a1.y));
-              b1 = make_double2(fma(op.m[2].x, a0.x, op.m[3].x * a1.x), fma(op.m[2].x, a0.y, op.m[3].x * a1.y));
+              E::real2(op, a0, a1, b0, b1);
             } else {
-              const double2 u0 = op.m[0], u1 = op.m[1], u2 = op.m[2], u3 = op.m[3];
-              b0.x = fma(u0.x, a0.x, fma(-u0.y, a0.y, fma(u1.x, a1.x, -u1.y * a1.y)));
-              b0.y = fma(u0.x, a0.y, fma(u0.y, a0.x, fma(u1.x, a1.y, u1.y * a1.x)));
-              b1.x = fma(u2.x, a0.x, fma(-u2.y, a0.y, fma(u3.x, a1.x, -u3.y * a1.y)));
-              b1.y = fma(u2.x, a0.y, fma(u2.y, a0.x, fma(u3.x, a1.y, u3.y * a1.x)));
+              E::general2(op, a0, a1, b0, b1);
             }
             tile[j0] = b0;
             tile[j1] = b1;
@@ -113,28 +189,33 @@ __global__ void __launch_bounds__(THREADS) k_tile_f64(double2* __restrict__ a, c
       }
       __syncthreads();
     }
-    for (uint32_t j = threadIdx.x; j < T; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = tile[j];
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[j]);
   }
 }
 
-int launch_tile(qs_state* s, const TileArgs& g, double flops, int ngates) {
+template <class E>
+static int launch_engine(qs_state* s, const TileArgs& g, size_t smem) {
   constexpr int THREADS = 256;
-  size_t H = (size_t)1 << g.nhigh;
-  size_t smem = ((H * sizeof(uint64_t) + 15) & ~(size_t)15) + ((size_t)sizeof(double2) << g.m);
   static bool attr_set = false;
   if (!attr_set) {
-    QS_CUDA(cudaFuncSetAttribute(k_tile_f64<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    QS_CUDA(cudaFuncSetAttribute(k_tile<E, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   int per_sm = (int)std::max<size_t>(1, (220 * 1024) / (smem + 1024));
   per_sm = std::min(per_sm, 8);
   uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)152 * per_sm);
+  k_tile<E, THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
+  return launch_check("tile kernel");
+}
+
+int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, int ngates, bool fixed) {
+  size_t H = (size_t)1 << g.nhigh;
+  size_t smem = ((H * sizeof(uint64_t) + 15) & ~(size_t)15) + ((size_t)16 << g.m);
   uint64_t qmask = 0;
   for (int b = 0; b < g.m - g.nhigh; ++b) qmask |= 1ull << b;
   for (int b = 0; b < g.nhigh; ++b) qmask |= 1ull << g.qhigh[b];
-  KTimer kt(s, QS_K_TILE, g.m, ngates, qmask, 0, (double)(1ull << g.n), flops);
-  k_tile_f64<THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
-  return launch_check("tile kernel");
+  KTimer kt(s, QS_K_TILE, g.m, ngates, qmask, 0, (double)(1ull << g.n), flops, int_ops);
+  return fixed ? launch_engine<EngQ60>(s, g, smem) : launch_engine<EngF64>(s, g, smem);
 }
 
 }  // namespace qs

@@ -3,13 +3,14 @@
 // gate data in fast on-chip memory, Section "GPU optimization").
 #pragma once
 
+#include "fixed.h"
 #include "internal.h"
 
 namespace qs {
 
 constexpr int TILE_MAX_M = 12;  // 2^12 amplitudes x 16 B = 64 KiB of shared memory per CTA
 constexpr int TILE_LOW = 3;     // qubits 0..2 are always in a tile: 128-byte contiguous runs
-constexpr int TILE_MAX_OPS = 340;
+constexpr int TILE_MAX_OPS = 276;
 
 enum TileOpKind : int8_t {
   TOP_PHASE1 = OP_PHASE1,
@@ -21,7 +22,10 @@ enum TileOpKind : int8_t {
 };
 
 struct TileOp {
-  double2 m[4];        // matrix (for SCALAR: m[0] = d0, m[3] = d1)
+  union {
+    double2 m[4];      // FP64 engine: matrix (for SCALAR: m[0] = d0, m[3] = d1)
+    QC q[4];           // Q60 engine: the same entries as limbs
+  };
   uint64_t ext_cmask;  // control qubits outside the tile (global bit positions)
   uint32_t lcmask;     // control qubits inside the tile (local bit positions)
   int8_t kind;
@@ -41,6 +45,6 @@ struct TileArgs {
 };
 static_assert(sizeof(TileArgs) < 32000, "tile arguments must fit the kernel parameter space");
 
-int launch_tile(qs_state* s, const TileArgs& args, double flops, int ngates);
+int launch_tile(qs_state* s, const TileArgs& args, double flops, double int_ops, int ngates, bool fixed);
 
 }  // namespace qs

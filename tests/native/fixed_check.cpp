@@ -1,0 +1,20 @@
+// Host-side harness for the Q60 helpers of the CUDA library (compiled by the
+// test suite with g++; exercises the same inline functions the kernels use).
+#include "fixed.h"
+
+extern "C" {
+long long fc_from_double(double v) { return (long long)qs::q60_from_double(v); }
+double fc_to_double(long long V) { return qs::q60_to_double((int64_t)V); }
+// out = u0 * a0 + u1 * a1 for Q60 reals given as int64, via the limb accumulator
+long long fc_dot2(long long u0, long long a0, long long u1, long long a1) {
+  qs::QAcc acc{0, 0};
+  qs::qacc_add(acc, qs::q60_split(u0), qs::q60_split(a0));
+  qs::qacc_add(acc, qs::q60_split(u1), qs::q60_split(a1));
+  return (long long)qs::qacc_result(acc);
+}
+long long fc_dot4(const long long* u, const long long* a) {
+  qs::QAcc acc{0, 0};
+  for (int i = 0; i < 4; ++i) qs::qacc_add(acc, qs::q60_split(u[i]), qs::q60_split(a[i]));
+  return (long long)qs::qacc_result(acc);
+}
+}

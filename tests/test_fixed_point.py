@@ -1,0 +1,96 @@
+"""The Q60 fixed-point helpers the gate kernels use (csrc/fixed.h), compiled
+for the host and checked against exact integer / rational arithmetic."""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fc():
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "fixed_check.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+                    "-I", os.path.join(ROOT, "paper_2212_14201_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "native", "fixed_check.cpp"), "-o", so], check=True)
+    lib = ctypes.CDLL(so)
+    lib.fc_from_double.restype = ctypes.c_longlong
+    lib.fc_from_double.argtypes = [ctypes.c_double]
+    lib.fc_to_double.restype = ctypes.c_double
+    lib.fc_to_double.argtypes = [ctypes.c_longlong]
+    lib.fc_dot2.restype = ctypes.c_longlong
+    lib.fc_dot2.argtypes = [ctypes.c_longlong] * 4
+    lib.fc_dot4.restype = ctypes.c_longlong
+    lib.fc_dot4.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    return lib
+
+
+def exact_q60(v: float) -> int:
+    """round(v * 2^60), ties away from zero, from the exact rational value."""
+    f = Fraction(v) * (1 << 60)
+    mag = abs(f)
+    r = math.floor(mag + Fraction(1, 2))
+    return r if f >= 0 else -r
+
+
+def values(seed, count):
+    g = np.random.Generator(np.random.PCG64(seed))
+    v = list(g.uniform(-1.5, 1.5, count)) + list(g.uniform(-1, 1, count) * 2.0 ** -g.integers(0, 70, count))
+    v += [0.0, -0.0, 1.0, -1.0, 1.5, -1.5, 2.0 ** -60, -2.0 ** -61, 2.0 ** -62, 3 * 2.0 ** -62, 5e-324,
+          1 / math.sqrt(2), math.cos(1.0), 2.0 ** -8, 2.0 ** -8 * (1 + 2 ** -52)]
+    return v
+
+
+def test_from_double_is_correctly_rounded(fc):
+    for v in values(1, 3000):
+        assert fc.fc_from_double(v) == exact_q60(v), v
+
+
+def test_to_double_is_correctly_rounded(fc):
+    g = np.random.Generator(np.random.PCG64(2))
+    Vs = [int(x) for x in g.integers(-(1 << 61), 1 << 61, 3000, dtype=np.int64)]
+    Vs += [int(x) >> int(s) for x, s in zip(g.integers(-(1 << 61), 1 << 61, 2000, dtype=np.int64),
+                                            g.integers(0, 60, 2000))]
+    Vs += [0, 1, -1, 2, (1 << 53) + 1, (1 << 54) + 2, (1 << 54) + 6, (1 << 60), -(1 << 60), (1 << 61) - 1]
+    for V in Vs:
+        got = fc.fc_to_double(V)
+        want = float(Fraction(V, 1 << 60))   # Python's int/Fraction -> float is correctly rounded (half even)
+        assert got == want, V
+
+
+def test_roundtrip_exact_for_large_values(fc):
+    for v in values(3, 2000):
+        if abs(v) >= 2.0 ** -8:
+            assert fc.fc_to_double(fc.fc_from_double(v)) == v
+
+
+def test_limb_products_error_bound(fc):
+    g = np.random.Generator(np.random.PCG64(4))
+    for _ in range(3000):
+        u = [int(x) for x in g.integers(-(1 << 60), (1 << 60) + 1, 4, dtype=np.int64)]
+        a = [int(x) for x in g.integers(-int(1.5 * (1 << 60)), int(1.5 * (1 << 60)), 4, dtype=np.int64)]
+        exact = Fraction(sum(x * y for x, y in zip(u, a)), 1 << 60)
+        ua = (ctypes.c_longlong * 4)(*u)
+        aa = (ctypes.c_longlong * 4)(*a)
+        got = fc.fc_dot4(ua, aa)
+        # four dropped low-limb products (< 2^62 each in 2^-120 units -> < 2^2 in Q60 units) + rounding
+        assert abs(got - exact) <= 4 * 4 + 1
+        got2 = fc.fc_dot2(u[0], a[0], u[1], a[1])
+        assert abs(got2 - Fraction(u[0] * a[0] + u[1] * a[1], 1 << 60)) <= 2 * 4 + 1
+
+
+def test_extreme_limbs_do_not_overflow(fc):
+    M = int(1.5 * (1 << 60))
+    for u in ([1 << 60] * 4, [-(1 << 60)] * 4):
+        for a in ([M] * 4, [-M] * 4, [M, -M, M, -M]):
+            ua = (ctypes.c_longlong * 4)(*u)
+            aa = (ctypes.c_longlong * 4)(*a)
+            exact = Fraction(sum(x * y for x, y in zip(u, a)), 1 << 60)
+            assert abs(fc.fc_dot4(ua, aa) - exact) <= 17

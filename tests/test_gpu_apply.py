@@ -21,9 +21,16 @@ def q():
     return q
 
 
-def gpu_run(q, n, gates, params=None, plan=None, init=None):
+@pytest.fixture(params=["fp64", "q60"])
+def arith(request, q):
+    return {"fp64": q.ARITH_FP64, "q60": q.ARITH_FIXED}[request.param]
+
+
+def gpu_run(q, n, gates, params=None, plan=None, init=None, arith=None):
     h = q.qs_alloc(n)
     try:
+        if arith is not None:
+            q.qs_set_arith(h, arith)
         if init is not None:
             q.qs_set_state(h, np.ascontiguousarray(init, dtype=np.complex128))
         q.qs_apply(h, gates, params, plan)
@@ -45,19 +52,19 @@ def test_worked_example_on_gpu(q):
 
 
 @pytest.mark.parametrize("name", ["H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "U3", "P"])
-def test_every_one_qubit_gate_every_target(q, orc, name):
+def test_every_one_qubit_gate_every_target(q, arith, orc, name):
     n = 9
     init = w.random_state(n, 21)
     for t in range(n):
         for dag in (0, 1):
             g = w.pack([w.gate(name, t, theta=0.3 + t, phi=1.1, lam=-0.7, dagger=dag)])
             ref = orc.as_complex(orc.apply_circuit(init.copy(), n, g))
-            got = gpu_run(q, n, g, init=init.view(np.complex128))
+            got = gpu_run(q, n, g, init=init.view(np.complex128), arith=arith)
             assert max_err(got, ref) < TOL, (name, t, dag)
 
 
 @pytest.mark.parametrize("name", ["CNOT", "CZ", "CR"])
-def test_two_qubit_gates_every_pair(q, orc, name):
+def test_two_qubit_gates_every_pair(q, arith, orc, name):
     n = 6
     init = w.random_state(n, 22)
     for c in range(n):
@@ -66,11 +73,11 @@ def test_two_qubit_gates_every_pair(q, orc, name):
                 continue
             g = w.pack([w.gate(name, c, t, theta=0.9 + c - t)])
             ref = orc.as_complex(orc.apply_circuit(init.copy(), n, g))
-            got = gpu_run(q, n, g, init=init.view(np.complex128))
+            got = gpu_run(q, n, g, init=init.view(np.complex128), arith=arith)
             assert max_err(got, ref) < TOL, (name, c, t)
 
 
-def test_multi_controlled_gates(q, orc):
+def test_multi_controlled_gates(q, arith, orc):
     n = 10
     init = w.random_state(n, 23)
     recs = [w.gate("X", 4, ctrl_mask=0b1000000011), w.gate("U3", 0, theta=1.0, phi=2.0, lam=3.0, ctrl_mask=0b0110000000),
@@ -78,40 +85,40 @@ def test_multi_controlled_gates(q, orc):
             w.gate("S", 5, ctrl_mask=0b1111000000, dagger=1), w.gate("Y", 1, ctrl_mask=0b0000001000)]
     g = w.pack(recs)
     ref = orc.as_complex(orc.apply_circuit(init.copy(), n, g))
-    assert max_err(gpu_run(q, n, g, init=init.view(np.complex128)), ref) < TOL
+    assert max_err(gpu_run(q, n, g, init=init.view(np.complex128), arith=arith), ref) < TOL
 
 
 @pytest.mark.parametrize("n,ng,seed", [(1, 20, 0), (2, 50, 1), (5, 200, 2), (12, 200, 0), (16, 400, 3), (20, 300, 4)])
-def test_random_circuits(q, orc, n, ng, seed):
+def test_random_circuits(q, arith, orc, n, ng, seed):
     g = w.random_circuit(n, ng, seed)
     ref = orc.as_complex(orc.run(n, g))
-    assert max_err(gpu_run(q, n, g), ref) < TOL
+    assert max_err(gpu_run(q, n, g, arith=arith), ref) < TOL
 
 
-def test_forty_percent_two_qubit_mix(q, orc):
+def test_forty_percent_two_qubit_mix(q, arith, orc):
     n = 18
     g = w.random_circuit(n, 500, 2, two_qubit_prob=0.4)
-    assert max_err(gpu_run(q, n, g), orc.as_complex(orc.run(n, g))) < TOL
+    assert max_err(gpu_run(q, n, g, arith=arith), orc.as_complex(orc.run(n, g))) < TOL
 
 
-def test_layered_brickwork(q, orc):
+def test_layered_brickwork(q, arith, orc):
     n = 16
     g = w.layered_u3_cz(n, 20, 1)
-    assert max_err(gpu_run(q, n, g), orc.as_complex(orc.run(n, g))) < TOL
+    assert max_err(gpu_run(q, n, g, arith=arith), orc.as_complex(orc.run(n, g))) < TOL
 
 
-def test_parametrised_records(q, orc):
+def test_parametrised_records(q, arith, orc):
     n = 8
     g, npar = w.hea_ansatz(n, 3)
     th = w.uniform_angles(npar, 4)
-    assert max_err(gpu_run(q, n, g, params=th), orc.as_complex(orc.run(n, g, th))) < TOL
+    assert max_err(gpu_run(q, n, g, params=th, arith=arith), orc.as_complex(orc.run(n, g, th))) < TOL
 
 
-def test_dagger_roundtrip_identity(q):
+def test_dagger_roundtrip_identity(q, arith):
     n = 14
     g = w.random_circuit(n, 300, 9)
     both = np.concatenate([g, q.qs_gate_list_dagger(g)])
-    psi = gpu_run(q, n, both)
+    psi = gpu_run(q, n, both, arith=arith)
     want = np.zeros(1 << n, dtype=np.complex128)
     want[0] = 1
     assert max_err(psi, want) < TOL
@@ -291,3 +298,28 @@ def test_statevector_class_on_torch_memory(q, orc):
     t = sv.amps.view(torch.complex128).cpu().numpy()
     assert max_err(t, orc.as_complex(ref)) < TOL
     sv.close()
+
+
+def test_arith_modes_and_bound_tracking(q, orc):
+    n = 10
+    g = w.random_circuit(n, 150, 12)
+    ref = orc.as_complex(orc.run(n, g))
+    big = np.zeros(1 << n, dtype=np.complex128)
+    big[5] = 3.0   # norm 3: beyond the Q60 range
+    h = q.qs_alloc(n)
+    try:
+        for mode in (q.ARITH_AUTO, q.ARITH_FP64, q.ARITH_FIXED):
+            q.qs_set_arith(h, mode)
+            q.qs_set_zero(h)
+            q.qs_apply(h, g)
+            assert max_err(q.qs_get_state(h), ref) < TOL
+        q.qs_set_state(h, big)
+        q.qs_set_arith(h, q.ARITH_FIXED)
+        with pytest.raises(q.QsimError):
+            q.qs_apply(h, g)
+        q.qs_set_arith(h, q.ARITH_AUTO)   # falls back to FP64 for the large state
+        q.qs_apply(h, g)
+        want = orc.as_complex(orc.apply_circuit(big.copy().view(np.float64), n, g))
+        assert max_err(q.qs_get_state(h), want) < 4 * TOL
+    finally:
+        q.qs_free(h)

@@ -18,10 +18,17 @@ def q():
     return q
 
 
-def fused(q, n, gates, params=None, init=None):
+@pytest.fixture(params=["fp64", "q60"])
+def arith(request, q):
+    return {"fp64": q.ARITH_FP64, "q60": q.ARITH_FIXED}[request.param]
+
+
+def fused(q, n, gates, params=None, init=None, arith=None):
     p = q.qs_plan_create(n, gates, q.PLAN_GREEDY, 5)
     h = q.qs_alloc(n)
     try:
+        if arith is not None:
+            q.qs_set_arith(h, arith)
         if init is not None:
             q.qs_set_state(h, np.ascontiguousarray(init, dtype=np.complex128))
         q.qs_apply(h, gates, params, p)
@@ -33,21 +40,21 @@ def fused(q, n, gates, params=None, init=None):
 
 @pytest.mark.parametrize("n,ng,seed,p2", [(1, 30, 0, None), (3, 80, 1, None), (7, 200, 2, None), (12, 200, 0, None),
                                           (13, 400, 3, 0.4), (15, 500, 4, 0.4), (19, 600, 5, 0.4), (22, 400, 6, 0.4)])
-def test_fused_random_circuits(q, orc, n, ng, seed, p2):
+def test_fused_random_circuits(q, orc, arith, n, ng, seed, p2):
     g = w.random_circuit(n, ng, seed, two_qubit_prob=p2)
-    psi, st = fused(q, n, g)
+    psi, st = fused(q, n, g, arith=arith)
     assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
 
 
 @pytest.mark.parametrize("n", [12, 14, 17, 21])
-def test_fused_brickwork(q, orc, n):
+def test_fused_brickwork(q, orc, arith, n):
     g = w.layered_u3_cz(n, 20, 1)
-    psi, st = fused(q, n, g)
+    psi, st = fused(q, n, g, arith=arith)
     assert st["n_tile_passes"] >= 1
     assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
 
 
-def test_fused_controls_outside_tiles(q, orc):
+def test_fused_controls_outside_tiles(q, orc, arith):
     n = 18
     rng = w.SplitMix64(7)
     recs = []
@@ -73,7 +80,7 @@ def test_fused_controls_outside_tiles(q, orc):
     g = w.pack(recs)
     init = w.random_state_fast(n, 3)
     init /= np.linalg.norm(init)
-    psi, _ = fused(q, n, g, init=init.view(np.complex128))
+    psi, _ = fused(q, n, g, init=init.view(np.complex128), arith=arith)
     ref = orc.as_complex(orc.apply_circuit(init.copy(), n, g))
     assert np.max(np.abs(psi - ref)) < TOL
 
