@@ -233,6 +233,25 @@ int qs_expect_pauli(const qs_state* s, const qs_pauli* terms, size_t nterms, dou
 int qs_sample(const qs_state* s, uint64_t seed, uint64_t shots, uint64_t* out, int on_device);
 
 
+/* ---- gradients (the paper's variational circuits and qop expectations, Section
+ * "Variational quantum circuit"; the paper does not say how gradients are taken:
+ * this is the adjoint recursion of Jones & Gacon, arXiv:2009.02823) ----------- */
+
+/* Energy E = <psi|H|psi> of psi = U_G ... U_1 |0> (gates[0..ng-1] with angles
+ * from params[0..np-1], host memory) for H = terms[0..nterms-1], and its gradient
+ * dE/dparams[j] (host, np entries): the sum over every record with param_idx == j
+ * of Im <lambda_k| G_k |psi_k>, lambda_k = U_{k+1}^dag ... U_G^dag H psi,
+ * psi_k = U_k ... U_1 |0>, G_k the generator (U = exp(-i theta G / 2)):
+ * RX -> X, RY -> Y, RZ -> Z, P and CR -> -2|1><1| on the target, times the
+ * projector on the control qubits; a dagger record flips the sign.
+ * The state `s` (n qubits) is used as the psi buffer and is overwritten; a
+ * second vector and the partial sums are allocated on the state's stream for the
+ * call.  Synchronous (returns results in host memory).
+ * Errors: INVALID_ARG (bad record, param_idx >= np, term outside n),
+ * UNSUPPORTED (a parametrised record other than RX, RY, RZ, P, CR), OOM, CUDA. */
+int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, const double* params, size_t np,
+                    const qs_pauli* terms, size_t nterms, double* energy, double* grad);
+
 /* ---- instrumentation ---------------------------------------------------------------
  * Per-kernel timing log of one state: when enabled, every kernel the library
  * queues for the state is bracketed by CUDA events on the state's stream.

@@ -80,6 +80,7 @@ SIGNATURES = {
     "qs_expect_z_all": (I32, [P, P]),
     "qs_expect_pauli": (I32, [P, P, SZ, ctypes.POINTER(DBL)]),
     "qs_sample": (I32, [P, U64, U64, P, I32]),
+    "qs_adjoint_grad": (I32, [P, P, SZ, P, SZ, P, SZ, ctypes.POINTER(DBL), P]),
     "qs_timing_enable": (I32, [P, I32]),
     "qs_timing_fetch": (I32, [P, ctypes.POINTER(TimingRecord), SZ, ctypes.POINTER(SZ)]),
     "qs_launch_count": (U64, []),
@@ -335,3 +336,16 @@ def qs_timing_fetch(h: int) -> list[dict]:
 
 def qs_launch_count() -> int:
     return int(lib().qs_launch_count())
+
+
+def qs_adjoint_grad(h: int, gates, params, terms):
+    """(energy, gradient) of <psi(params)|H|psi(params)>; overwrites the state."""
+    g = as_gates(gates)
+    pr = np.ascontiguousarray(params, dtype=np.float64)
+    t = as_paulis(terms)
+    e = ctypes.c_double()
+    grad = np.empty(len(pr), dtype=np.float64)
+    _chk(lib().qs_adjoint_grad(h, g.ctypes.data if len(g) else None, len(g), pr.ctypes.data if len(pr) else None,
+                               len(pr), t.ctypes.data if len(t) else None, len(t), ctypes.byref(e),
+                               grad.ctypes.data if len(pr) else None))
+    return e.value, grad
