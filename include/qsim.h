@@ -218,6 +218,29 @@ int qs_probs_dict(const qs_state* s, const int* qubits, int nq, double threshold
 /* <Z_i> for every qubit i into out[0..n-1] (host memory). */
 int qs_expect_z_all(const qs_state* s, double* out);
 
+/* <Z_i> for every qubit i, for callers that cannot allocate memory.  The paper
+ * has no counterpart; this is a service entry point of this library.
+ * Some callers cannot call cudaMalloc: code whose device memory all belongs to
+ * another allocator (a framework's caching allocator, or a pool reserved at
+ * start-up, where an extra allocation can fail or fragment it), and code on
+ * latency-critical paths, where cudaMalloc / cudaFree would synchronise the
+ * device.  This entry point allocates nothing, on the device or the host:
+ *   device_amps  2^n complex128 amplitudes, interleaved, 16-byte aligned, device
+ *                memory owned by the caller (read only);
+ *   device_out   n doubles, device memory owned by the caller: out[i] = <Z_i>;
+ *   stream       cudaStream_t the two kernels are queued on (NULL = legacy default);
+ *   8 <= n <= 34, otherwise INVALID_ARG with a message naming the range.
+ * Asynchronous: results are in device_out once `stream` reaches this point.
+ * The partial sums live in one file-scope device array (25,600 doubles,
+ * 200 KiB), which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents, which no call reads before rewriting; calls whose kernels overlap on
+ * the GPU (other streams, other host threads) race on it and must be ordered by
+ * the caller. */
+int qs_expect_z_all_noalloc(const double* device_amps, int n, double* device_out, void* stream);
+
 /* <psi| sum_k coef_k P_k |psi> into *out (host).  Each term's masks must lie
  * within the n qubits. */
 int qs_expect_pauli(const qs_state* s, const qs_pauli* terms, size_t nterms, double* out);

@@ -81,6 +81,7 @@ SIGNATURES = {
     "qs_expect_pauli": (I32, [P, P, SZ, ctypes.POINTER(DBL)]),
     "qs_sample": (I32, [P, U64, U64, P, I32]),
     "qs_adjoint_grad": (I32, [P, P, SZ, P, SZ, P, SZ, ctypes.POINTER(DBL), P]),
+    "qs_expect_z_all_noalloc": (I32, [P, I32, P, P]),
     "qs_timing_enable": (I32, [P, I32]),
     "qs_timing_fetch": (I32, [P, ctypes.POINTER(TimingRecord), SZ, ctypes.POINTER(SZ)]),
     "qs_launch_count": (U64, []),

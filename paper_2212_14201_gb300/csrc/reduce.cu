@@ -7,6 +7,7 @@
 // warp-shuffle tree, CTA partials go to the workspace in CTA order and one
 // final CTA adds them in that order.  Results do not depend on timing.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -392,4 +393,58 @@ extern "C" int qs_expect_pauli(const qs_state* cs, const qs_pauli* terms, size_t
   for (size_t k = 0; k < nterms; ++k) e += terms[k].coef * vals[k];
   *out = e;
   return QS_OK;
+}
+
+// ---- <Z_i> without any allocation ------------------------------------------------------
+// For callers that cannot allocate device memory (see the declaration in qsim.h):
+// the per-CTA partial sums live in this file-scope device array instead of a
+// state's workspace.  Its size covers the largest launch of k_expect_z:
+// at most 1024 CTAs, each writing r + 1 <= 25 values for n <= 34.
+#define QS_NOALLOC_EZ_MIN_QUBITS 8
+#define QS_NOALLOC_EZ_MAX_QUBITS 34
+#define QS_NOALLOC_EZ_SLOTS (1024 * 25)
+static __device__ __align__(256) double g_noalloc_ez_partials[QS_NOALLOC_EZ_SLOTS];
+
+// Device address of g_noalloc_ez_partials, looked up once per device (the name
+// itself is only a host-side stand-in and must not be passed to a kernel).
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {nullptr};
+
+static int noalloc_scratch(double** out) {
+  int dev = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(QS_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ez_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_ez_partials)");
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QS_OK;
+}
+
+extern "C" int qs_expect_z_all_noalloc(const double* device_amps, int n, double* device_out, void* stream) {
+  clear_error();
+  if (!device_amps || !device_out) return fail(QS_ERR_INVALID_ARG, "NULL device pointer");
+  if (n < QS_NOALLOC_EZ_MIN_QUBITS || n > QS_NOALLOC_EZ_MAX_QUBITS)
+    return fail(QS_ERR_INVALID_ARG, "qs_expect_z_all_noalloc supports %d <= n <= %d qubits (got n=%d)",
+                QS_NOALLOC_EZ_MIN_QUBITS, QS_NOALLOC_EZ_MAX_QUBITS, n);
+  if ((uintptr_t)device_amps & 15) return fail(QS_ERR_INVALID_ARG, "amplitudes not 16-byte aligned");
+  double* part = nullptr;
+  QS_TRY(noalloc_scratch(&part));
+  int r = std::max(8, n - 10);
+  r = std::min(r, std::min(n, 8 + ZMAXJ));
+  const int nblocks = 1 << (n - r);
+  if ((size_t)nblocks * (size_t)(r + 1) > QS_NOALLOC_EZ_SLOTS)
+    return fail(QS_ERR_INVALID_ARG, "n=%d needs more scratch than the static array holds", n);
+  cudaStream_t st = (cudaStream_t)stream;
+  note_launch(2);
+  // every partial that k_expect_z_finish reads is written first by k_expect_z, so
+  // nothing left over from an earlier call is read
+  k_expect_z<<<nblocks, 256, 0, st>>>((const double2*)device_amps, r, part);
+  QS_TRY(launch_check("expect_z (no-alloc)"));
+  k_expect_z_finish<<<1, 64, 0, st>>>(part, nblocks, r, n, device_out);
+  return launch_check("expect_z_finish (no-alloc)");
 }
