@@ -61,6 +61,9 @@ def _load():
                 "or_sample": (i32, [P, i32, u64, i64, P]),
                 "or_adjoint_grad": (i32, [i32, P, i64, P, i64, P, i64, P, P]),
                 "or_energy": (i32, [i32, P, i64, P, P, i64, P]),
+                "or_mlp_nweights": (i64, [i32, i32]),
+                "or_mlp_forward": (i32, [i32, i32, P, P, i64, P]),
+                "or_mlp_loss_grad": (i32, [i32, i32, P, P, P, i64, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -212,6 +215,29 @@ def energy(n: int, gates: np.ndarray, params: np.ndarray, terms: np.ndarray) -> 
     _chk(_load().or_energy(n, _ptr(gates), len(gates), params.ctypes.data, _ptr(terms), len(terms),
                            ctypes.byref(e)), "energy")
     return e.value
+
+
+def mlp_nweights(F: int, H: int) -> int:
+    return int(_load().or_mlp_nweights(F, H))
+
+
+def mlp_forward(F: int, H: int, w: np.ndarray, x: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, F)
+    y = np.empty(len(x), dtype=np.float64)
+    _chk(_load().or_mlp_forward(F, H, w.ctypes.data, x.ctypes.data, len(x), y.ctypes.data), "mlp_forward")
+    return y
+
+
+def mlp_loss_grad(F: int, H: int, w: np.ndarray, x: np.ndarray, t: np.ndarray):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, F)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    loss = ctypes.c_double()
+    g = np.empty_like(w)
+    _chk(_load().or_mlp_loss_grad(F, H, w.ctypes.data, x.ctypes.data, t.ctypes.data, len(x), ctypes.byref(loss),
+                                  g.ctypes.data), "mlp_loss_grad")
+    return loss.value, g
 
 
 def as_complex(state: np.ndarray) -> np.ndarray:

@@ -502,3 +502,96 @@ int or_energy(int n, const or_gate* gates, int64_t ng, const double* params,
   free(psi);
   return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Fusion cost model: a 3-layer perceptron (not in the paper; the learned      */
+/* planner's network).  Inputs x (F features), hidden width H, tanh:           */
+/*   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = w3 . h2 + b3.            */
+/* Weights flattened as W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3.           */
+/* Loss over a batch of B samples: (1/B) sum_s (y_s - t_s)^2 / 2.              */
+/* ------------------------------------------------------------------------- */
+int64_t or_mlp_nweights(int F, int H) { return (int64_t)H * F + H + (int64_t)H * H + H + H + 1; }
+
+static void mlp_layers(int F, int H, const double* w, const double* x, double* z1, double* h1, double* z2,
+                       double* h2, double* y) {
+  const double* W1 = w;
+  const double* b1 = W1 + (int64_t)H * F;
+  const double* W2 = b1 + H;
+  const double* b2 = W2 + (int64_t)H * H;
+  const double* w3 = b2 + H;
+  const double b3 = w3[H];
+  for (int i = 0; i < H; ++i) {
+    double s = b1[i];
+    for (int j = 0; j < F; ++j) s += W1[(int64_t)i * F + j] * x[j];
+    z1[i] = s;
+    h1[i] = tanh(s);
+  }
+  for (int i = 0; i < H; ++i) {
+    double s = b2[i];
+    for (int j = 0; j < H; ++j) s += W2[(int64_t)i * H + j] * h1[j];
+    z2[i] = s;
+    h2[i] = tanh(s);
+  }
+  double s = b3;
+  for (int i = 0; i < H; ++i) s += w3[i] * h2[i];
+  *y = s;
+}
+
+int or_mlp_forward(int F, int H, const double* w, const double* x, int64_t B, double* y) {
+  if (F < 1 || H < 1) return OR_EINVAL;
+  double* buf = (double*)malloc(sizeof(double) * 4 * H);
+  if (!buf) return OR_ENOMEM;
+  for (int64_t s = 0; s < B; ++s) mlp_layers(F, H, w, x + s * F, buf, buf + H, buf + 2 * H, buf + 3 * H, &y[s]);
+  free(buf);
+  return OR_OK;
+}
+
+/* Loss and its gradient with respect to every weight (same layout), by the
+ * chain rule through the three layers, summed over the batch in sample order. */
+int or_mlp_loss_grad(int F, int H, const double* w, const double* x, const double* t, int64_t B, double* loss,
+                     double* grad) {
+  if (F < 1 || H < 1 || B < 1) return OR_EINVAL;
+  const int64_t NW = or_mlp_nweights(F, H);
+  double* z1 = (double*)malloc(sizeof(double) * 6 * H);
+  if (!z1) return OR_ENOMEM;
+  double *h1 = z1 + H, *z2 = z1 + 2 * H, *h2 = z1 + 3 * H, *d2 = z1 + 4 * H, *d1 = z1 + 5 * H;
+  const double* W2 = w + (int64_t)H * F + H;
+  const double* w3 = W2 + (int64_t)H * H + H;
+  double* gW1 = grad;
+  double* gb1 = gW1 + (int64_t)H * F;
+  double* gW2 = gb1 + H;
+  double* gb2 = gW2 + (int64_t)H * H;
+  double* gw3 = gb2 + H;
+  double* gb3 = gw3 + H;
+  for (int64_t k = 0; k < NW; ++k) grad[k] = 0.0;
+  double L = 0.0;
+  for (int64_t s = 0; s < B; ++s) {
+    const double* xs = x + s * F;
+    double y;
+    mlp_layers(F, H, w, xs, z1, h1, z2, h2, &y);
+    const double r = y - t[s];
+    L += 0.5 * r * r;
+    const double dy = r / (double)B;
+    *gb3 += dy;
+    for (int i = 0; i < H; ++i) {
+      gw3[i] += dy * h2[i];
+      d2[i] = dy * w3[i] * (1.0 - h2[i] * h2[i]);
+    }
+    for (int i = 0; i < H; ++i) {
+      gb2[i] += d2[i];
+      for (int j = 0; j < H; ++j) gW2[(int64_t)i * H + j] += d2[i] * h1[j];
+    }
+    for (int j = 0; j < H; ++j) {
+      double s2 = 0.0;
+      for (int i = 0; i < H; ++i) s2 += W2[(int64_t)i * H + j] * d2[i];
+      d1[j] = s2 * (1.0 - h1[j] * h1[j]);
+    }
+    for (int i = 0; i < H; ++i) {
+      gb1[i] += d1[i];
+      for (int j = 0; j < F; ++j) gW1[(int64_t)i * F + j] += d1[i] * xs[j];
+    }
+  }
+  *loss = L / (double)B;
+  free(z1);
+  return OR_OK;
+}
