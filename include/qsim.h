@@ -193,6 +193,10 @@ int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, q
 int qs_plan_free(qs_plan* p);
 int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
 
+/* Greedy plan with an explicit tile width: tiles of tile_qubits (4..12) qubits,
+ * the "block size" of the fusion.  qs_plan_create(GREEDY) uses 12. */
+int qs_plan_create_tiled(int n, const qs_gate* gates, size_t ng, int tile_qubits, qs_plan** out);
+
 /* Pass `pass` of a plan (0 <= pass < n_passes): *kind (0 = one plain gate,
  * 1 = shared-memory tile pass), *qmask (tile qubits, or the gate's target),
  * and the indices of its gates into the program in execution order (up to cap
@@ -200,6 +204,42 @@ int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
  * order applies the same unitary as the program. */
 int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask, uint32_t* gates, size_t cap,
                       size_t* ngates);
+
+/* ---- learned fusion cost model (not in the paper, whose fusion has no cost
+ * model): a 3-layer tanh perceptron h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),
+ * y = w3 . h2 + b3 predicting log(milliseconds) of one pass from its features,
+ * trained on the GPU by the library's own kernels from its own kernel timings.
+ * Weights are flattened W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3 (doubles).
+ * Every call below is synchronous and uses the model's private stream. ------ */
+
+typedef struct qs_mlp qs_mlp; /* opaque */
+
+/* n_in features (1..64), n_hidden units (1..128); weights (host) or NULL for a
+ * seeded uniform +-1/sqrt(fan-in) initialisation (biases 0). */
+int qs_mlp_create(int n_in, int n_hidden, const double* weights, uint64_t seed, qs_mlp** out);
+int qs_mlp_free(qs_mlp* m);
+int qs_mlp_num_weights(const qs_mlp* m, size_t* out);
+int qs_mlp_get_weights(const qs_mlp* m, double* out);
+int qs_mlp_set_weights(qs_mlp* m, const double* w);
+/* y[s] for the B feature rows x[s*F .. s*F+F) (host arrays). */
+int qs_mlp_forward(qs_mlp* m, const double* x, size_t B, double* y);
+/* loss = (1/B) sum_s (y_s - t_s)^2 / 2 and its gradient for every weight. */
+int qs_mlp_loss_grad(qs_mlp* m, const double* x, const double* t, size_t B, double* loss, double* grad);
+/* `epochs` full-batch Adam steps (lr; beta 0.9 / 0.999) on the GPU; *final_loss
+ * (may be NULL) receives the loss of the final weights. */
+int qs_mlp_train(qs_mlp* m, const double* x, const double* t, size_t B, int epochs, double lr, double* final_loss);
+
+/* Features of every pass of a plan (QS_PASS_FEATURES doubles per pass, in pass
+ * order; `gates` must be the plan's program): pass kind, tile qubits, state
+ * qubits, outside qubits, and counts of general, real, general-diagonal,
+ * unit-factor, in-tile-controlled and outside-target ops. */
+#define QS_PASS_FEATURES 10
+int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out);
+
+/* Learned plan: greedy plans for every tile width 4..12 are scored by the model
+ * (sum over passes of exp(predicted log ms)) and the cheapest is kept; its
+ * est_seconds is the model's prediction.  The model needs QS_PASS_FEATURES inputs. */
+int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs_mlp* model, qs_plan** out);
 
 /* ---- reductions (prob_run_list / prob_run_dict, expectation tools) ------------- */
 
@@ -274,6 +314,40 @@ int qs_sample(const qs_state* s, uint64_t seed, uint64_t shots, uint64_t* out, i
  * UNSUPPORTED (a parametrised record other than RX, RY, RZ, P, CR), OOM, CUDA. */
 int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, const double* params, size_t np,
                     const qs_pauli* terms, size_t nterms, double* energy, double* grad);
+
+/* ---- batched variational evaluation (the hybrid quantum-classical loop of
+ * Sections "Support hybrid quantum-classical algorithm" and "Variational
+ * quantum circuit": many parameter sets evaluated per optimiser step) -------- */
+
+typedef struct qs_batch qs_batch; /* opaque */
+
+/* Describe nsets independent energy+gradient problems, set s having:
+ *   n_per_set[s] qubits (1..24);
+ *   gates[gate_offsets[s] .. gate_offsets[s+1]) (param_idx relative to the set);
+ *   params[param_offsets[s] .. param_offsets[s+1]) in the run's params array;
+ *   terms[term_offsets[s] .. term_offsets[s+1]) its Pauli sum.
+ * All arrays are host memory, read during the call (offset arrays have nsets+1
+ * entries, non-decreasing).  The batch owns device copies, per-set psi and
+ * lambda buffers (32 bytes x 2^n per set), pinned staging and a private stream.
+ * Errors: INVALID_ARG, UNSUPPORTED (parametrised record other than RX, RY, RZ,
+ * P, CR), OOM, CUDA. */
+int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate* gates, const size_t* gate_offsets,
+                    const size_t* param_offsets, const qs_pauli* terms, const size_t* term_offsets,
+                    qs_batch** out);
+
+/* Evaluate every set for params (param_offsets[nsets] values): energies[s] and
+ * grads (same layout as params), each as qs_adjoint_grad defines them, in ONE
+ * persistent kernel launch (CTAs take whole sets from a device work counter,
+ * largest first; no CTA waits for another).  on_device == 0: host arrays; the
+ * copy-in, the launch and the copy-out are a CUDA graph captured on the first
+ * such call and replayed after.  on_device != 0: device arrays, no graph.
+ * Synchronous. */
+int qs_batch_run(qs_batch* b, const double* params, double* energies, double* grads, int on_device);
+
+/* Device time (ms) of the persistent kernel in the last run; launch shape. */
+int qs_batch_last_ms(const qs_batch* b, double* ms);
+int qs_batch_info(const qs_batch* b, int* grid, int* threads, size_t* smem_bytes);
+int qs_batch_free(qs_batch* b);
 
 /* ---- instrumentation ---------------------------------------------------------------
  * Per-kernel timing log of one state: when enabled, every kernel the library

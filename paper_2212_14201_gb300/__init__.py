@@ -11,7 +11,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import (ARITH_AUTO, ARITH_FIXED, ARITH_FP64, qs_adjoint_grad, qs_set_arith,  # noqa: F401
+from ._lib import (qs_plan_create_tiled, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_last_ms, qs_batch_run,  # noqa: F401
+                   ARITH_AUTO, ARITH_FIXED, ARITH_FP64, qs_adjoint_grad, qs_set_arith,
                    qs_state_modified,
                    GATE_DTYPE, PAULI_DTYPE, PLAN_GREEDY, PLAN_LEARNED, PLAN_PLAIN, QsimError,  # noqa: F401
                    qs_alloc, qs_alloc_external, qs_apply, qs_apply_matrix, qs_device_ptr, qs_expect_pauli,

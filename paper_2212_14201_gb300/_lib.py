@@ -72,6 +72,7 @@ SIGNATURES = {
     "qs_gate_list_dagger": (I32, [P, SZ, P]),
     "qs_plan_create": (I32, [I32, P, SZ, I32, I32, PP]),
     "qs_plan_free": (I32, [P]),
+    "qs_plan_create_tiled": (I32, [I32, P, SZ, I32, PP]),
     "qs_plan_get_stats": (I32, [P, ctypes.POINTER(PlanStats)]),
     "qs_plan_pass_info": (I32, [P, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64), P, SZ,
                                 ctypes.POINTER(SZ)]),
@@ -82,6 +83,11 @@ SIGNATURES = {
     "qs_sample": (I32, [P, U64, U64, P, I32]),
     "qs_adjoint_grad": (I32, [P, P, SZ, P, SZ, P, SZ, ctypes.POINTER(DBL), P]),
     "qs_expect_z_all_noalloc": (I32, [P, I32, P, P]),
+    "qs_batch_create": (I32, [SZ, P, P, P, P, P, P, PP]),
+    "qs_batch_run": (I32, [P, P, P, P, I32]),
+    "qs_batch_last_ms": (I32, [P, ctypes.POINTER(DBL)]),
+    "qs_batch_info": (I32, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SZ)]),
+    "qs_batch_free": (I32, [P]),
     "qs_timing_enable": (I32, [P, I32]),
     "qs_timing_fetch": (I32, [P, ctypes.POINTER(TimingRecord), SZ, ctypes.POINTER(SZ)]),
     "qs_launch_count": (U64, []),
@@ -246,6 +252,13 @@ def qs_plan_create(n: int, gates, mode: int = PLAN_GREEDY, kmax: int = 5) -> int
     return h.value
 
 
+def qs_plan_create_tiled(n: int, gates, tile_qubits: int) -> int:
+    g = as_gates(gates)
+    h = ctypes.c_void_p()
+    _chk(lib().qs_plan_create_tiled(n, g.ctypes.data if len(g) else None, len(g), tile_qubits, ctypes.byref(h)))
+    return h.value
+
+
 def qs_plan_free(p: int):
     _chk(lib().qs_plan_free(p))
 
@@ -337,6 +350,53 @@ def qs_timing_fetch(h: int) -> list[dict]:
 
 def qs_launch_count() -> int:
     return int(lib().qs_launch_count())
+
+
+def qs_batch_create(n_per_set, gate_lists, n_params, term_lists) -> int:
+    """Batch of sets: gate_lists[s] (records, param_idx relative to the set),
+    n_params[s] parameters, term_lists[s] Pauli terms."""
+    ns = len(n_per_set)
+    nq = np.ascontiguousarray(n_per_set, dtype=np.int32)
+    gates = as_gates(np.concatenate([as_gates(g) for g in gate_lists]) if ns else np.empty(0, GATE_DTYPE))
+    terms = as_paulis(np.concatenate([as_paulis(t) for t in term_lists]) if ns else np.empty(0, PAULI_DTYPE))
+    go = np.zeros(ns + 1, dtype=np.uint64)
+    go[1:] = np.cumsum([len(g) for g in gate_lists])
+    po = np.zeros(ns + 1, dtype=np.uint64)
+    po[1:] = np.cumsum(n_params)
+    to = np.zeros(ns + 1, dtype=np.uint64)
+    to[1:] = np.cumsum([len(t) for t in term_lists])
+    h = ctypes.c_void_p()
+    _chk(lib().qs_batch_create(ns, nq.ctypes.data, gates.ctypes.data if len(gates) else None, go.ctypes.data,
+                               po.ctypes.data, terms.ctypes.data if len(terms) else None, to.ctypes.data,
+                               ctypes.byref(h)))
+    return h.value
+
+
+def qs_batch_run(b: int, params, energies=None, grads=None):
+    """params: numpy (host path, CUDA graph) or CUDA tensor (device path)."""
+    if energies is None:
+        raise ValueError("energies output is required")
+    pp, dev = _host_or_dev(params)
+    ep, _ = _host_or_dev(energies)
+    gp, _ = _host_or_dev(grads)
+    _chk(lib().qs_batch_run(b, pp, ep, gp, dev))
+    return energies, grads
+
+
+def qs_batch_last_ms(b: int) -> float:
+    ms = ctypes.c_double()
+    _chk(lib().qs_batch_last_ms(b, ctypes.byref(ms)))
+    return ms.value
+
+
+def qs_batch_info(b: int) -> dict:
+    g, t, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _chk(lib().qs_batch_info(b, ctypes.byref(g), ctypes.byref(t), ctypes.byref(s)))
+    return {"grid": g.value, "threads": t.value, "smem_bytes": s.value}
+
+
+def qs_batch_free(b: int):
+    _chk(lib().qs_batch_free(b))
 
 
 def qs_adjoint_grad(h: int, gates, params, terms):

@@ -1,0 +1,803 @@
+// Batched variational evaluation: energy and adjoint gradient of many parameter
+// sets of possibly different qubit counts in ONE persistent launch (the
+// hybrid quantum-classical loop of the paper, Sections "Support hybrid
+// quantum-classical algorithm" and "Variational quantum circuit"; the batching
+// itself is this library's design, not the paper's).
+//
+// Each CTA repeatedly takes the next set from a device work counter (sets
+// pre-sorted by decreasing size) and evaluates it alone, so no CTA ever waits for
+// another:
+//   1. gate matrices of the set from its parameters (forward and adjoint);
+//   2. forward sweep psi = U_G ... U_1 |0> as greedy tile passes (<= 11 tile
+//      qubits, Q60 arithmetic in shared memory);
+//   3. lambda = (H / S) psi and E = S Re<psi|lambda> (FP64 gather);
+//   4. backward sweep over the passes in reverse: for every op in reverse, the
+//      generator inner product Im<lambda|G|psi> over the tile (Q60 products,
+//      FP64 accumulation, fixed reduction order), then U^dag on both tiles.
+// The host side of a run (parameters in, energies and gradients out) is
+// captured once in a CUDA graph and replayed.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "fixed.h"
+#include "internal.h"
+
+namespace qs {
+
+constexpr int BT_THREADS = 256;
+constexpr int BT_M = 11;          // tile qubits: psi and lambda tiles of 2^11 x 16 B
+constexpr int BT_MAX_OPS = 512;   // ops (and gradient slots) per pass
+constexpr int BT_MAX_N = 24;
+constexpr int BT_OFFS = 1 << (BT_M - 3);  // high-bit offset table: tiles hold qubits 0..2 (or all of n < 3)
+
+enum : int8_t { BK_SCALAR = 9 };
+enum : int8_t { BG_NONE = 0, BG_X = 1, BG_Y = 2, BG_Z = 3, BG_P = 4 };
+
+struct BSet {
+  int n, pass_begin, npasses, gate_begin, ngates, group_begin, ngroups, param_begin, nparams;
+  long long amp_off;
+  double S;
+};
+
+struct BPass {
+  int m, nhigh, nout, op_begin, op_end, nslots;
+  int qhigh[16];
+  int outpos[32];
+};
+
+struct BOp {
+  uint64_t ext;     // controls outside the tile
+  uint32_t lcm;     // controls inside the tile (local bits)
+  int gate;         // global gate index (matrix tables)
+  int param;        // global parameter index, or -1
+  double gsign;     // generator sign (-1 for a dagger record)
+  int16_t slot;     // gradient slot within the pass, or -1
+  int8_t kf, kb;    // op class forward / adjoint
+  int8_t tb;        // local target bit (global target bit for SCALAR)
+  int8_t gen;
+  int8_t c0f, c1f, c0b, c1b;
+};
+
+struct BGate {
+  int type, param, dagger;
+  double p[3];
+};
+
+struct BGroup {
+  uint64_t xm;
+  int tbegin, tend;
+};
+
+struct BTerm {
+  double c;       // coef / S, with the real sign of i^ny
+  uint64_t zm;
+  int imag;       // i^ny is imaginary
+};
+
+struct BatchArgs {
+  const BSet* sets;
+  const int* order;
+  int nsets;
+  const BPass* passes;
+  const BOp* ops;
+  const BGate* gates;
+  const BGroup* groups;
+  const BTerm* terms;
+  const double* params;
+  double* grads;
+  double* energies;
+  double2* psi;
+  double2* lam;
+  QC* matf;   // 4 per gate
+  QC* matb;   // 4 per gate
+  int* counter;
+};
+
+// ---- device helpers ------------------------------------------------------------------
+
+__device__ void bt_gate_matrix(const BGate& g, const double* params, bool flip, double2 m[4]) {
+  double th = g.param >= 0 ? params[g.param] : g.p[0];
+  double s, c;
+  sincos(0.5 * th, &s, &c);
+  const double r = 0.70710678118654752440;
+  const double2 z = make_double2(0, 0), one = make_double2(1, 0);
+  switch (g.type) {
+    case QS_H: m[0] = make_double2(r, 0); m[1] = make_double2(r, 0); m[2] = make_double2(r, 0); m[3] = make_double2(-r, 0); break;
+    case QS_X: case QS_CNOT: m[0] = z; m[1] = one; m[2] = one; m[3] = z; break;
+    case QS_Y: m[0] = z; m[1] = make_double2(0, -1); m[2] = make_double2(0, 1); m[3] = z; break;
+    case QS_Z: case QS_CZ: m[0] = one; m[1] = z; m[2] = z; m[3] = make_double2(-1, 0); break;
+    case QS_S: m[0] = one; m[1] = z; m[2] = z; m[3] = make_double2(0, 1); break;
+    case QS_T: m[0] = one; m[1] = z; m[2] = z; m[3] = make_double2(r, r); break;
+    case QS_RX: m[0] = make_double2(c, 0); m[1] = make_double2(0, -s); m[2] = make_double2(0, -s); m[3] = make_double2(c, 0); break;
+    case QS_RY: m[0] = make_double2(c, 0); m[1] = make_double2(-s, 0); m[2] = make_double2(s, 0); m[3] = make_double2(c, 0); break;
+    case QS_RZ: m[0] = make_double2(c, -s); m[1] = z; m[2] = z; m[3] = make_double2(c, s); break;
+    case QS_U3: {
+      double sl, cl, sp, cp, spl, cpl;
+      sincos(g.p[2], &sl, &cl);
+      sincos(g.p[1], &sp, &cp);
+      sincos(g.p[1] + g.p[2], &spl, &cpl);
+      m[0] = make_double2(c, 0);
+      m[1] = make_double2(-cl * s, -sl * s);
+      m[2] = make_double2(cp * s, sp * s);
+      m[3] = make_double2(cpl * c, spl * c);
+      break;
+    }
+    case QS_P: case QS_CR: {
+      double st, ct;
+      sincos(th, &st, &ct);
+      m[0] = one; m[1] = z; m[2] = z; m[3] = make_double2(ct, st);
+      break;
+    }
+    default: m[0] = one; m[1] = z; m[2] = z; m[3] = one; break;
+  }
+  if ((g.dagger != 0) != flip) {
+    double2 a = m[0], b = m[1], cc = m[2], d = m[3];
+    m[0] = make_double2(a.x, -a.y);
+    m[1] = make_double2(cc.x, -cc.y);
+    m[2] = make_double2(b.x, -b.y);
+    m[3] = make_double2(d.x, -d.y);
+  }
+}
+
+__device__ __forceinline__ longlong2 bt_unit(longlong2 a, int code) {
+  switch (code) {
+    case U_ONE: return a;
+    case U_I: return make_longlong2(-a.y, a.x);
+    case U_MINUS_ONE: return make_longlong2(-a.x, -a.y);
+    default: return make_longlong2(a.y, -a.x);
+  }
+}
+
+__device__ __forceinline__ longlong2 bt_mul(longlong2 a, int code, const QC& u) {
+  if (code != U_GENERAL) return bt_unit(a, code);
+  const QL ar = q60_split(a.x), ai = q60_split(a.y);
+  QAcc re{0, 0}, im{0, 0};
+  qacc_add(re, u.re, ar);
+  qacc_add(re, u.nim, ai);
+  qacc_add(im, u.re, ai);
+  qacc_add(im, u.im, ar);
+  return make_longlong2(qacc_result(re), qacc_result(im));
+}
+
+__device__ __forceinline__ uint32_t bt_expand(uint32_t i, uint32_t fixed, uint32_t set) {
+  while (fixed) {
+    int f = __ffs(fixed) - 1;
+    fixed &= fixed - 1;
+    i = ((i >> f) << (f + 1)) | (i & ((1u << f) - 1));
+  }
+  return i | set;
+}
+
+__device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int kind, int c0, int c1, const QC* U,
+                         uint64_t base) {
+  const uint32_t lcm = op.lcm;
+  if (kind == BK_SCALAR) {
+    const bool one = (base >> op.tb) & 1ull;
+    const int code = one ? c1 : c0;
+    if (code == U_ONE) return;
+    const QC& u = U[one ? 3 : 0];
+    const uint32_t cnt = TS >> __popc(lcm);
+    for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+      uint32_t j = bt_expand(i, lcm, lcm);
+      tile[j] = bt_mul(tile[j], code, u);
+    }
+    return;
+  }
+  const uint32_t tb = 1u << op.tb;
+  const uint32_t fixed = lcm | tb;
+  const uint32_t cnt = TS >> __popc(fixed);
+  for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+    const uint32_t j0 = bt_expand(i, fixed, lcm), j1 = j0 | tb;
+    if (kind == OP_PHASE1) {
+      tile[j1] = bt_mul(tile[j1], c1, U[3]);
+      continue;
+    }
+    longlong2 a0 = tile[j0], a1 = tile[j1], b0, b1;
+    if (kind == OP_DIAG) {
+      b0 = bt_mul(a0, c0, U[0]);
+      b1 = bt_mul(a1, c1, U[3]);
+    } else if (kind == OP_ANTI) {
+      b0 = bt_mul(a1, c0, U[1]);
+      b1 = bt_mul(a0, c1, U[2]);
+    } else {
+      const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+      int64_t out[4];
+#pragma unroll
+      for (int row = 0; row < 2; ++row) {
+        const QC& u0 = U[2 * row];
+        const QC& u1 = U[2 * row + 1];
+        QAcc re{0, 0}, im{0, 0};
+        qacc_add(re, u0.re, r0);
+        qacc_add(re, u1.re, r1);
+        qacc_add(im, u0.re, i0);
+        qacc_add(im, u1.re, i1);
+        if (kind == OP_GENERAL) {
+          qacc_add(re, u0.nim, i0);
+          qacc_add(re, u1.nim, i1);
+          qacc_add(im, u0.im, r0);
+          qacc_add(im, u1.im, r1);
+        }
+        out[2 * row] = qacc_result(re);
+        out[2 * row + 1] = qacc_result(im);
+      }
+      b0 = make_longlong2(out[0], out[1]);
+      b1 = make_longlong2(out[2], out[3]);
+    }
+    tile[j0] = b0;
+    tile[j1] = b1;
+  }
+}
+
+// sum_k s_k * l_k * p_k for four signed products of Q60 values, as a double.
+__device__ __forceinline__ double bt_dot4(const int64_t* l, const int64_t* p, const int* sg) {
+  QAcc acc{0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (sg[k] == 0) continue;
+    qacc_add(acc, q60_split(sg[k] > 0 ? l[k] : -l[k]), q60_split(p[k]));
+  }
+  return q60_to_double(qacc_result(acc));
+}
+
+// This thread's share of Im <lambda| G |psi> over the op's pairs in the tile.
+__device__ double bt_gen_partial(const longlong2* P, const longlong2* Lt, uint32_t TS, const BOp& op, uint64_t base) {
+  if (op.kf == BK_SCALAR) {
+    // diagonal generator on a qubit outside the tile: per amplitude,
+    // Z -> (-1)^bit Im(conj(l) p), P -> -2 [bit] Im(conj(l) p)
+    const bool one = (base >> op.tb) & 1ull;
+    if (op.gen == BG_P && !one) return 0.0;
+    const double w = op.gen == BG_P ? -2.0 : (one ? -1.0 : 1.0);
+    const uint32_t cnt = TS >> __popc(op.lcm);
+    double acc = 0.0;
+    for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+      const uint32_t j = bt_expand(i, op.lcm, op.lcm);
+      const int64_t l[4] = {Lt[j].x, Lt[j].y, 0, 0}, p[4] = {P[j].y, P[j].x, 0, 0};
+      const int sg[4] = {1, -1, 0, 0};
+      acc += w * bt_dot4(l, p, sg);
+    }
+    return acc;
+  }
+  const uint32_t tb = 1u << op.tb;
+  const uint32_t fixed = op.lcm | tb;
+  const uint32_t cnt = TS >> __popc(fixed);
+  double acc = 0.0;
+  for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+    const uint32_t j0 = bt_expand(i, fixed, op.lcm), j1 = j0 | tb;
+    const longlong2 p0 = P[j0], p1 = P[j1], l0 = Lt[j0], l1 = Lt[j1];
+    int64_t l[4], p[4];
+    int sg[4];
+    switch (op.gen) {
+      case BG_X:  // l0x p1y - l0y p1x + l1x p0y - l1y p0x
+        l[0] = l0.x; p[0] = p1.y; sg[0] = 1; l[1] = l0.y; p[1] = p1.x; sg[1] = -1;
+        l[2] = l1.x; p[2] = p0.y; sg[2] = 1; l[3] = l1.y; p[3] = p0.x; sg[3] = -1;
+        break;
+      case BG_Y:  // -l0x p1x - l0y p1y + l1x p0x + l1y p0y
+        l[0] = l0.x; p[0] = p1.x; sg[0] = -1; l[1] = l0.y; p[1] = p1.y; sg[1] = -1;
+        l[2] = l1.x; p[2] = p0.x; sg[2] = 1; l[3] = l1.y; p[3] = p0.y; sg[3] = 1;
+        break;
+      case BG_Z:  // l0x p0y - l0y p0x - l1x p1y + l1y p1x
+        l[0] = l0.x; p[0] = p0.y; sg[0] = 1; l[1] = l0.y; p[1] = p0.x; sg[1] = -1;
+        l[2] = l1.x; p[2] = p1.y; sg[2] = -1; l[3] = l1.y; p[3] = p1.x; sg[3] = 1;
+        break;
+      default:    // P: -2 (l1x p1y - l1y p1x)
+        l[0] = l1.x; p[0] = p1.y; sg[0] = -1; l[1] = l1.y; p[1] = p1.x; sg[1] = 1;
+        l[2] = 0; p[2] = 0; sg[2] = 0; l[3] = 0; p[3] = 0; sg[3] = 0;
+        break;
+    }
+    double v = bt_dot4(l, p, sg);
+    acc += op.gen == BG_P ? 2.0 * v : v;
+  }
+  return acc;
+}
+
+__device__ double bt_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int i = 0; i < BT_THREADS / 32; ++i) r += red[i];
+  return r;
+}
+
+__device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, double2* lam, const QC* matf,
+                            const QC* matb, bool backward, longlong2* tP, longlong2* tL, uint64_t* offs, double* acc,
+                            double* red) {
+  const int m = ps.m;
+  const int L = m - ps.nhigh;
+  const uint32_t TS = 1u << m;
+  const uint32_t H = 1u << ps.nhigh;
+  const uint32_t lowmask = (1u << L) - 1;
+  const uint64_t ntiles = 1ull << ps.nout;
+  for (uint32_t h = threadIdx.x; h < H; h += BT_THREADS) {
+    uint64_t o = 0;
+    for (int b = 0; b < ps.nhigh; ++b) o |= (uint64_t)((h >> b) & 1u) << ps.qhigh[b];
+    offs[h] = o;
+  }
+  for (int s = threadIdx.x; s < ps.nslots; s += BT_THREADS) acc[s] = 0.0;
+  for (uint64_t r = 0; r < ntiles; ++r) {
+    uint64_t base = 0;
+    for (int b = 0; b < ps.nout; ++b) base |= ((r >> b) & 1ull) << ps.outpos[b];
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+      const uint64_t x = base + offs[j >> L] + (j & lowmask);
+      const double2 a = psi[x];
+      tP[j] = make_longlong2(q60_from_double(a.x), q60_from_double(a.y));
+      if (backward) {
+        const double2 b = lam[x];
+        tL[j] = make_longlong2(q60_from_double(b.x), q60_from_double(b.y));
+      }
+    }
+    __syncthreads();
+    if (!backward) {
+      for (int k = ps.op_begin; k < ps.op_end; ++k) {
+        const BOp op = d.ops[k];
+        if ((base & op.ext) != op.ext) continue;
+        bt_apply(tP, TS, op, op.kf, op.c0f, op.c1f, matf + 4 * op.gate, base);
+        __syncthreads();
+      }
+    } else {
+      for (int k = ps.op_end - 1; k >= ps.op_begin; --k) {
+        const BOp op = d.ops[k];
+        if ((base & op.ext) != op.ext) continue;
+        if (op.slot >= 0) {
+          double part = bt_gen_partial(tP, tL, TS, op, base);
+          double sum = bt_block_sum(part, red);
+          if (threadIdx.x == 0) acc[op.slot] += sum;
+        }
+        bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, matb + 4 * op.gate, base);
+        bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, matb + 4 * op.gate, base);
+        __syncthreads();
+      }
+    }
+    for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+      const uint64_t x = base + offs[j >> L] + (j & lowmask);
+      psi[x] = make_double2(q60_to_double(tP[j].x), q60_to_double(tP[j].y));
+      if (backward) lam[x] = make_double2(q60_to_double(tL[j].x), q60_to_double(tL[j].y));
+    }
+  }
+  __syncthreads();
+  if (backward && threadIdx.x == 0) {
+    // gradient contributions in backward gate order
+    for (int k = ps.op_end - 1; k >= ps.op_begin; --k) {
+      const BOp& op = d.ops[k];
+      if (op.slot >= 0) d.grads[op.param] += acc[op.slot] * op.gsign;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(BT_THREADS) k_batch(const BatchArgs d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  longlong2* tP = reinterpret_cast<longlong2*>(smem);
+  longlong2* tL = tP + (1 << BT_M);
+  uint64_t* offs = reinterpret_cast<uint64_t*>(tL + (1 << BT_M));
+  double* acc = reinterpret_cast<double*>(offs + BT_OFFS);
+  double* red = acc + BT_MAX_OPS;
+  __shared__ int s_set;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_set = atomicAdd(d.counter, 1);
+    __syncthreads();
+    const int si = s_set;
+    if (si >= d.nsets) break;
+    const int set_id = d.order[si];
+    const BSet st = d.sets[set_id];
+    const uint64_t N = 1ull << st.n;
+    double2* psi = d.psi + st.amp_off;
+    double2* lam = d.lam + st.amp_off;
+    QC* matf = d.matf + 4 * (size_t)st.gate_begin;
+    QC* matb = d.matb + 4 * (size_t)st.gate_begin;
+    // 1. matrices (indices of ops are global gate indices; shift back by gate_begin)
+    for (int g = threadIdx.x; g < st.ngates; g += BT_THREADS) {
+      double2 m[4];
+      const BGate gt = d.gates[st.gate_begin + g];
+      bt_gate_matrix(gt, d.params, false, m);
+      for (int e = 0; e < 4; ++e) matf[4 * g + e] = qc_make(m[e].x, m[e].y);
+      bt_gate_matrix(gt, d.params, true, m);
+      for (int e = 0; e < 4; ++e) matb[4 * g + e] = qc_make(m[e].x, m[e].y);
+    }
+    for (int j = threadIdx.x; j < st.nparams; j += BT_THREADS) d.grads[st.param_begin + j] = 0.0;
+    // 2. psi = |0>
+    for (uint64_t x = threadIdx.x; x < N; x += BT_THREADS) psi[x] = make_double2(x == 0 ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    for (int p = st.pass_begin; p < st.pass_begin + st.npasses; ++p)
+      bt_run_pass(d, d.passes[p], psi, lam, matf, matb, false, tP, tL, offs, acc, red);
+    // 3. lambda = (H/S) psi, energy
+    double e = 0.0;
+    for (uint64_t y = threadIdx.x; y < N; y += BT_THREADS) {
+      double ore = 0.0, oim = 0.0;
+      for (int gi = st.group_begin; gi < st.group_begin + st.ngroups; ++gi) {
+        const BGroup grp = d.groups[gi];
+        const uint64_t x = y ^ grp.xm;
+        double dre = 0.0, dim = 0.0;
+        for (int k = grp.tbegin; k < grp.tend; ++k) {
+          const BTerm t = d.terms[k];
+          const double v = (__popcll(x & t.zm) & 1) ? -t.c : t.c;
+          if (t.imag) dim += v;
+          else dre += v;
+        }
+        const double2 pv = psi[x];
+        ore += dre * pv.x - dim * pv.y;
+        oim += dre * pv.y + dim * pv.x;
+      }
+      lam[y] = make_double2(ore, oim);
+      const double2 py = psi[y];
+      e += py.x * ore + py.y * oim;
+    }
+    const double E = bt_block_sum(e, red);
+    if (threadIdx.x == 0) d.energies[set_id] = E * st.S;
+    __syncthreads();
+    // 4. backward
+    for (int p = st.pass_begin + st.npasses - 1; p >= st.pass_begin; --p)
+      bt_run_pass(d, d.passes[p], psi, lam, matf, matb, true, tP, tL, offs, acc, red);
+    if (threadIdx.x == 0)
+      for (int j = 0; j < st.nparams; ++j) d.grads[st.param_begin + j] *= st.S;
+  }
+}
+
+size_t batch_smem_bytes() {
+  return 2 * sizeof(longlong2) * (1 << BT_M) + sizeof(uint64_t) * BT_OFFS + sizeof(double) * (BT_MAX_OPS + 8);
+}
+
+static int bt_gen(int type) {
+  switch (type) {
+    case QS_RX: return BG_X;
+    case QS_RY: return BG_Y;
+    case QS_RZ: return BG_Z;
+    case QS_P: case QS_CR: return BG_P;
+    default: return BG_NONE;
+  }
+}
+
+// Structural op class (valid for every angle) and unit codes; `adj` = adjoint.
+static void bt_class(int type, bool adj, int8_t* kind, int8_t* c0, int8_t* c1) {
+  auto conj = [&](int8_t c) -> int8_t { return adj ? (c == U_I ? U_MINUS_I : c == U_MINUS_I ? U_I : c) : c; };
+  *c0 = U_GENERAL;
+  *c1 = U_GENERAL;
+  switch (type) {
+    case QS_I: *kind = OP_IDENTITY; *c0 = U_ONE; *c1 = U_ONE; break;
+    case QS_H: case QS_RY: *kind = OP_REAL; break;
+    case QS_X: case QS_CNOT: *kind = OP_ANTI; *c0 = U_ONE; *c1 = U_ONE; break;
+    case QS_Y: *kind = OP_ANTI; *c0 = conj(U_MINUS_I); *c1 = conj(U_I); break;
+    case QS_Z: case QS_CZ: *kind = OP_PHASE1; *c0 = U_ONE; *c1 = U_MINUS_ONE; break;
+    case QS_S: *kind = OP_PHASE1; *c0 = U_ONE; *c1 = conj(U_I); break;
+    case QS_T: case QS_P: case QS_CR: *kind = OP_PHASE1; *c0 = U_ONE; break;
+    case QS_RZ: *kind = OP_DIAG; break;
+    default: *kind = OP_GENERAL; break;  // RX, U3
+  }
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+struct qs_batch {
+  size_t nsets = 0;
+  size_t total_params = 0;
+  cudaStream_t stream = nullptr;
+  BatchArgs args{};
+  std::vector<void*> dev;      // device allocations
+  double* h_params = nullptr;  // pinned staging
+  double* h_grads = nullptr;
+  double* h_energies = nullptr;
+  double* d_params = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the persistent kernel
+  int grid = 0;
+  size_t smem = 0;
+};
+
+static void batch_release(qs_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  for (void* p : b->dev) cudaFree(p);
+  if (b->h_params) cudaFreeHost(b->h_params);
+  if (b->h_grads) cudaFreeHost(b->h_grads);
+  if (b->h_energies) cudaFreeHost(b->h_energies);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+template <class T>
+static int upload(qs_batch* b, const std::vector<T>& v, const T** out) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+  QS_CUDA(cudaMalloc(&p, bytes));
+  b->dev.push_back(p);
+  if (!v.empty()) QS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = (const T*)p;
+  return QS_OK;
+}
+
+static int dev_alloc(qs_batch* b, size_t bytes, void** out) {
+  QS_CUDA(cudaMalloc(out, std::max<size_t>(bytes, 16)));
+  b->dev.push_back(*out);
+  return QS_OK;
+}
+
+extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate* gates, const size_t* gate_offsets,
+                               const size_t* param_offsets, const qs_pauli* terms, const size_t* term_offsets,
+                               qs_batch** out) {
+  clear_error();
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nsets == 0 || !n_per_set || !gate_offsets || !param_offsets || !term_offsets)
+    return fail(QS_ERR_INVALID_ARG, "NULL argument or no sets");
+  std::vector<BSet> sets(nsets);
+  std::vector<BPass> passes;
+  std::vector<BOp> ops;
+  std::vector<BGate> bgates;
+  std::vector<BGroup> groups;
+  std::vector<BTerm> bterms;
+  long long amp_off = 0;
+  for (size_t si = 0; si < nsets; ++si) {
+    const int n = n_per_set[si];
+    if (n < 1 || n > BT_MAX_N) return fail(QS_ERR_INVALID_ARG, "set %zu: n=%d outside 1..%d", si, n, BT_MAX_N);
+    const size_t g0 = gate_offsets[si], g1 = gate_offsets[si + 1];
+    const size_t p0 = param_offsets[si], p1 = param_offsets[si + 1];
+    const size_t t0 = term_offsets[si], t1 = term_offsets[si + 1];
+    if (g1 < g0 || p1 < p0 || t1 < t0) return fail(QS_ERR_INVALID_ARG, "set %zu: offsets decrease", si);
+    const size_t ng = g1 - g0, np = p1 - p0;
+    BSet& st = sets[si];
+    st.n = n;
+    st.gate_begin = (int)bgates.size();
+    st.ngates = (int)ng;
+    st.param_begin = (int)p0;
+    st.nparams = (int)np;
+    st.amp_off = amp_off;
+    amp_off += 1ll << n;
+    std::vector<int> tgt(ng);
+    std::vector<uint64_t> cms(ng);
+    for (size_t k = 0; k < ng; ++k) {
+      const qs_gate& g = gates[g0 + k];
+      int rc = gate_qubits(g, n, &tgt[k], &cms[k]);
+      if (rc) return fail(rc, "set %zu gate %zu: %s", si, k, qs_last_error());
+      if (g.param_idx >= 0) {
+        if ((size_t)g.param_idx >= np) return fail(QS_ERR_INVALID_ARG, "set %zu gate %zu: param_idx >= set size", si, k);
+        if (bt_gen(g.type) == BG_NONE)
+          return fail(QS_ERR_UNSUPPORTED, "set %zu gate %zu: gradients need RX, RY, RZ, P or CR", si, k);
+      }
+      BGate bg;
+      bg.type = g.type;
+      bg.param = g.param_idx >= 0 ? (int)(p0 + g.param_idx) : -1;
+      bg.dagger = g.dagger != 0;
+      bg.p[0] = g.p[0];
+      bg.p[1] = g.p[1];
+      bg.p[2] = g.p[2];
+      bgates.push_back(bg);
+    }
+    // Hamiltonian: groups of terms sharing an X mask, scaled by S
+    double csum = 0.0;
+    const uint64_t full = (1ull << n) - 1;
+    for (size_t k = t0; k < t1; ++k) {
+      if ((terms[k].xmask | terms[k].zmask) & ~full) return fail(QS_ERR_INVALID_ARG, "set %zu term %zu exceeds n", si, k - t0);
+      csum += fabs(terms[k].coef);
+    }
+    st.S = csum > 0 ? exp2(ceil(log2(csum))) : 1.0;
+    st.group_begin = (int)groups.size();
+    std::vector<uint64_t> xms;
+    for (size_t k = t0; k < t1; ++k)
+      if (std::find(xms.begin(), xms.end(), terms[k].xmask) == xms.end()) xms.push_back(terms[k].xmask);
+    for (uint64_t xm : xms) {
+      BGroup grp;
+      grp.xm = xm;
+      grp.tbegin = (int)bterms.size();
+      for (size_t k = t0; k < t1; ++k) {
+        if (terms[k].xmask != xm) continue;
+        const int ny = __builtin_popcountll(terms[k].xmask & terms[k].zmask) & 3;
+        BTerm bt;
+        bt.c = (ny >= 2 ? -terms[k].coef : terms[k].coef) / st.S;
+        bt.zm = terms[k].zmask;
+        bt.imag = ny & 1;
+        bterms.push_back(bt);
+      }
+      grp.tend = (int)bterms.size();
+      groups.push_back(grp);
+    }
+    st.ngroups = (int)xms.size();
+    // greedy tile passes
+    const int m = std::min(n, BT_M);
+    const uint64_t low = (1ull << std::min(n, 3)) - 1;
+    std::vector<uint32_t> remaining(ng), pass, rest;
+    for (size_t k = 0; k < ng; ++k) remaining[k] = (uint32_t)k;
+    st.pass_begin = (int)passes.size();
+    while (!remaining.empty()) {
+      uint64_t Q = greedy_pass(gates + g0, tgt, cms, remaining, m, low, BT_MAX_OPS, pass, rest);
+      BPass bp;
+      memset(&bp, 0, sizeof bp);
+      int local[64];
+      int mm = 0;
+      for (int b = 0; b < n; ++b) local[b] = ((Q >> b) & 1) ? mm++ : -1;
+      int L = 0;
+      while (L < n && ((Q >> L) & 1)) ++L;
+      bp.m = mm;
+      for (int b = L; b < n; ++b)
+        if ((Q >> b) & 1) bp.qhigh[bp.nhigh++] = b;
+      for (int b = 0; b < n; ++b)
+        if (!((Q >> b) & 1)) bp.outpos[bp.nout++] = b;
+      bp.op_begin = (int)ops.size();
+      int slot = 0;
+      for (uint32_t k : pass) {
+        const qs_gate& g = gates[g0 + k];
+        BOp op;
+        memset(&op, 0, sizeof op);
+        op.gate = (int)k;  // index within the set's matrix tables
+        op.param = g.param_idx >= 0 ? (int)(p0 + g.param_idx) : -1;
+        bt_class(g.type, g.dagger != 0, &op.kf, &op.c0f, &op.c1f);
+        bt_class(g.type, g.dagger == 0, &op.kb, &op.c0b, &op.c1b);
+        if (op.kf == OP_IDENTITY && g.param_idx < 0) continue;
+        uint32_t lcm = 0;
+        uint64_t ext = 0;
+        for (int b = 0; b < n; ++b)
+          if ((cms[k] >> b) & 1) {
+            if (local[b] >= 0) lcm |= 1u << local[b];
+            else ext |= 1ull << b;
+          }
+        op.lcm = lcm;
+        op.ext = ext;
+        if (local[tgt[k]] >= 0) {
+          op.tb = (int8_t)local[tgt[k]];
+        } else {
+          // a diagonal op whose target lies outside the tile: a per-tile scalar
+          op.tb = (int8_t)tgt[k];
+          op.kf = BK_SCALAR;
+          op.kb = BK_SCALAR;
+        }
+        op.gen = g.param_idx >= 0 ? (int8_t)bt_gen(g.type) : BG_NONE;
+        op.gsign = g.dagger ? -1.0 : 1.0;
+        op.slot = -1;
+        if (op.gen != BG_NONE) op.slot = (int16_t)slot++;
+        ops.push_back(op);
+      }
+      bp.op_end = (int)ops.size();
+      bp.nslots = slot;
+      passes.push_back(bp);
+      remaining.swap(rest);
+    }
+    st.npasses = (int)passes.size() - st.pass_begin;
+  }
+  // largest sets first
+  std::vector<int> order(nsets);
+  for (size_t i = 0; i < nsets; ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sets[a].n > sets[b].n; });
+
+  qs_batch* b = new (std::nothrow) qs_batch;
+  if (!b) return fail(QS_ERR_OOM, "host allocation failed");
+  int rc = QS_OK;
+  auto chk = [&](int r) {
+    if (rc == QS_OK) rc = r;
+    return rc == QS_OK;
+  };
+  b->nsets = nsets;
+  b->total_params = param_offsets[nsets];
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+  if (e != cudaSuccess) chk(cuda_fail(e, "cudaStreamCreate / cudaEventCreate"));
+  BatchArgs& a = b->args;
+  a.nsets = (int)nsets;
+  if (rc == QS_OK) chk(upload(b, sets, &a.sets));
+  if (rc == QS_OK) chk(upload(b, order, &a.order));
+  if (rc == QS_OK) chk(upload(b, passes, &a.passes));
+  if (rc == QS_OK) chk(upload(b, ops, &a.ops));
+  if (rc == QS_OK) chk(upload(b, bgates, &a.gates));
+  if (rc == QS_OK) chk(upload(b, groups, &a.groups));
+  if (rc == QS_OK) chk(upload(b, bterms, &a.terms));
+  void* p = nullptr;
+  const size_t np = std::max<size_t>(1, b->total_params);
+  if (rc == QS_OK && chk(dev_alloc(b, np * sizeof(double), &p))) { a.params = (const double*)p; b->d_params = (double*)p; }
+  if (rc == QS_OK && chk(dev_alloc(b, np * sizeof(double), &p))) a.grads = (double*)p;
+  if (rc == QS_OK && chk(dev_alloc(b, nsets * sizeof(double), &p))) a.energies = (double*)p;
+  if (rc == QS_OK && chk(dev_alloc(b, (size_t)amp_off * sizeof(double2), &p))) a.psi = (double2*)p;
+  if (rc == QS_OK && chk(dev_alloc(b, (size_t)amp_off * sizeof(double2), &p))) a.lam = (double2*)p;
+  if (rc == QS_OK && chk(dev_alloc(b, std::max<size_t>(1, bgates.size()) * 4 * sizeof(QC), &p))) a.matf = (QC*)p;
+  if (rc == QS_OK && chk(dev_alloc(b, std::max<size_t>(1, bgates.size()) * 4 * sizeof(QC), &p))) a.matb = (QC*)p;
+  if (rc == QS_OK && chk(dev_alloc(b, sizeof(int), &p))) a.counter = (int*)p;
+  if (rc == QS_OK) {
+    e = cudaMallocHost(&b->h_params, np * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_grads, np * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_energies, nsets * sizeof(double));
+    if (e != cudaSuccess) chk(cuda_fail(e, "cudaMallocHost"));
+  }
+  if (rc == QS_OK) {
+    b->smem = batch_smem_bytes();
+    e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT_THREADS, b->smem);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    if (e != cudaSuccess) chk(cuda_fail(e, "batch kernel set-up"));
+    b->grid = std::max(1, per_sm) * std::max(1, sms);
+  }
+  if (rc != QS_OK) {
+    batch_release(b);
+    return rc;
+  }
+  *out = b;
+  return QS_OK;
+}
+
+// Queue one evaluation: params (device) -> energies/grads (device).
+static int batch_enqueue(qs_batch* b) {
+  const BatchArgs& a = b->args;
+  QS_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), b->stream));
+  QS_CUDA(cudaEventRecord(b->ev0, b->stream));
+  k_batch<<<b->grid, BT_THREADS, b->smem, b->stream>>>(a);
+  QS_TRY(launch_check("batch kernel"));
+  QS_CUDA(cudaEventRecord(b->ev1, b->stream));
+  return QS_OK;
+}
+
+extern "C" int qs_batch_last_ms(const qs_batch* b, double* ms) {
+  if (!b || !ms) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  float f = 0.f;
+  QS_CUDA(cudaEventElapsedTime(&f, b->ev0, b->ev1));
+  *ms = f;
+  return QS_OK;
+}
+
+extern "C" int qs_batch_info(const qs_batch* b, int* grid, int* threads, size_t* smem_bytes) {
+  if (!b || !grid || !threads || !smem_bytes) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  *grid = b->grid;
+  *threads = BT_THREADS;
+  *smem_bytes = b->smem;
+  return QS_OK;
+}
+
+extern "C" int qs_batch_run(qs_batch* b, const double* params, double* energies, double* grads, int on_device) {
+  clear_error();
+  if (!b || !params || !energies || (b->total_params && !grads)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  const size_t pb = b->total_params * sizeof(double), eb = b->nsets * sizeof(double);
+  note_launch(1);
+  if (on_device) {
+    QS_CUDA(cudaMemcpyAsync(b->d_params, params, pb, cudaMemcpyDeviceToDevice, b->stream));
+    QS_TRY(batch_enqueue(b));
+    QS_CUDA(cudaMemcpyAsync(energies, b->args.energies, eb, cudaMemcpyDeviceToDevice, b->stream));
+    if (pb) QS_CUDA(cudaMemcpyAsync(grads, b->args.grads, pb, cudaMemcpyDeviceToDevice, b->stream));
+    QS_CUDA(cudaStreamSynchronize(b->stream));
+    return QS_OK;
+  }
+  if (!b->exec) {
+    // capture: staging -> device params, counter reset, the persistent kernel, results -> staging
+    QS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemcpyAsync(b->d_params, b->h_params, pb, cudaMemcpyHostToDevice, b->stream);
+    int rc = e == cudaSuccess ? batch_enqueue(b) : cuda_fail(e, "capture params");
+    if (rc == QS_OK) {
+      e = cudaMemcpyAsync(b->h_energies, b->args.energies, eb, cudaMemcpyDeviceToHost, b->stream);
+      if (e == cudaSuccess && pb) e = cudaMemcpyAsync(b->h_grads, b->args.grads, pb, cudaMemcpyDeviceToHost, b->stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "capture results");
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (rc != QS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    b->graph = g;
+    QS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+  }
+  memcpy(b->h_params, params, pb);
+  QS_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  QS_CUDA(cudaStreamSynchronize(b->stream));
+  memcpy(energies, b->h_energies, eb);
+  if (pb) memcpy(grads, b->h_grads, pb);
+  return QS_OK;
+}
+
+extern "C" int qs_batch_free(qs_batch* b) {
+  batch_release(b);
+  return QS_OK;
+}

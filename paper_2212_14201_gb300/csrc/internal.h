@@ -103,6 +103,14 @@ int choose_fixed(qs_state* s, bool* fixed);
 int launch_op1(qs_state* s, const Op1& op, bool fixed);
 int launch_dense(qs_state* s, const int* targets, int k, uint64_t cmask, const C2* mat);
 
+// ---- planning ------------------------------------------------------------------
+// One greedy fusion pass over `remaining` (indices in program order): `pass`
+// receives the gates that run in a tile of at most m qubits containing `low`,
+// `rest` the others (still in order); returns the tile's qubit mask.
+uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                     const std::vector<uint32_t>& remaining, int m, uint64_t low, int max_ops,
+                     std::vector<uint32_t>& pass, std::vector<uint32_t>& rest);
+
 // ---- instrumentation -------------------------------------------------------------
 void note_launch(int count = 1);
 // Brackets the kernels queued during its lifetime with timing events (if the

@@ -101,8 +101,40 @@ double op_touch_fraction(const qs_gate& g, uint64_t cmask) {
 
 }  // namespace
 
-extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, qs_plan** out) {
-  clear_error();
+namespace qs {
+
+uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                     const std::vector<uint32_t>& remaining, int m, uint64_t low, int max_ops,
+                     std::vector<uint32_t>& pass, std::vector<uint32_t>& rest) {
+  uint64_t Q = low;
+  uint64_t blockedN = 0, blockedD = 0;
+  pass.clear();
+  rest.clear();
+  int nops = 0;
+  for (uint32_t k : remaining) {
+    const bool diag = structurally_diagonal(gates[k].type);
+    const uint64_t Nm = diag ? 0 : (1ull << tgt[k]);
+    const uint64_t Dm = (diag ? (1ull << tgt[k]) : 0) | cms[k];
+    bool conflict = (Nm & (blockedN | blockedD)) || (Dm & blockedN) || nops >= max_ops;
+    if (!conflict && Nm && !(Q & Nm)) {
+      if (__builtin_popcountll(Q) < m) Q |= Nm;
+      else conflict = true;
+    }
+    if (conflict) {
+      rest.push_back(k);
+      blockedN |= Nm;
+      blockedD |= Dm;
+    } else {
+      pass.push_back(k);
+      ++nops;
+    }
+  }
+  return Q;
+}
+
+}  // namespace qs
+
+static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax, int mtile, qs_plan** out) {
   if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_ERR_INVALID_ARG, "n out of range");
@@ -127,7 +159,7 @@ extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, 
   p->kmax = kmax;
   p->ng = ng;
   p->fingerprint = fingerprint(gates, ng);
-  p->m = std::min(n, TILE_MAX_M);
+  p->m = std::min(n, mtile);
   const double N = (double)(1ull << n);
   const double pass_bytes = 32.0 * N;
 
@@ -150,31 +182,9 @@ extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, 
   std::vector<uint32_t> remaining(ng), rest;
   for (size_t k = 0; k < ng; ++k) remaining[k] = (uint32_t)k;
   while (!remaining.empty()) {
-    uint64_t Q = low;
-    uint64_t blockedN = 0, blockedD = 0;
     PlanPass ps;
     ps.kind = PASS_TILE;
-    rest.clear();
-    int nops = 0;
-    for (uint32_t k : remaining) {
-      const bool diag = structurally_diagonal(gates[k].type);
-      const uint64_t Nm = diag ? 0 : (1ull << tgt[k]);
-      const uint64_t Dm = (diag ? (1ull << tgt[k]) : 0) | cms[k];
-      bool conflict = (Nm & (blockedN | blockedD)) || (Dm & blockedN) || nops >= TILE_MAX_OPS;
-      if (!conflict && Nm && !(Q & Nm)) {
-        if (__builtin_popcountll(Q) < p->m) Q |= Nm;
-        else conflict = true;
-      }
-      if (conflict) {
-        rest.push_back(k);
-        blockedN |= Nm;
-        blockedD |= Dm;
-      } else {
-        ps.gates.push_back(k);
-        ++nops;
-      }
-    }
-    ps.qmask = Q;
+    ps.qmask = greedy_pass(gates, tgt, cms, remaining, p->m, low, TILE_MAX_OPS, ps.gates, rest);
     // Cost: a tile pass sweeps the whole state once; a lone gate is cheaper in the
     // plain kernel, which touches only the amplitudes it changes.
     double flops = 0.0, plain = 0.0;
@@ -202,6 +212,18 @@ extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, 
   }
   *out = p;
   return QS_OK;
+}
+
+extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, qs_plan** out) {
+  clear_error();
+  return plan_build(n, gates, ng, mode, kmax, TILE_MAX_M, out);
+}
+
+extern "C" int qs_plan_create_tiled(int n, const qs_gate* gates, size_t ng, int tile_qubits, qs_plan** out) {
+  clear_error();
+  if (tile_qubits < TILE_LOW + 1 || tile_qubits > TILE_MAX_M)
+    return fail(QS_ERR_INVALID_ARG, "tile_qubits=%d outside %d..%d", tile_qubits, TILE_LOW + 1, TILE_MAX_M);
+  return plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, tile_qubits, out);
 }
 
 extern "C" int qs_plan_free(qs_plan* p) {
