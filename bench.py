@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--depth", type=int, default=20)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-gate arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched / adjoint / n=32 side workloads")
+    ap.add_argument("--no-n32", action="store_true", help="skip the n=32 learned-vs-greedy plan comparison")
     return ap.parse_args()
 
 
@@ -248,6 +250,99 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched_vqe(q, torch, steps: int, warmup: int):
+    """1024 parameter sets, n uniform in 10..20 (seed 3), 8-layer RY/RZ + CNOT-ring
+    ansatz, TFIM h=0.7, angles uniform (seed 33): energy + adjoint gradient of every
+    set per step, one persistent launch replayed from a CUDA graph."""
+    ns = w.batch_qubit_counts(1024, 3)
+    gl, npl, tl = [], [], []
+    for n in ns:
+        g, npar = w.hea_ansatz(int(n), 8)
+        gl.append(g)
+        npl.append(npar)
+        tl.append(w.tfim(int(n), 0.7))
+    params = w.uniform_angles(int(sum(npl)), 33)
+    b = q.qs_batch_create(ns, gl, npl, tl)
+    try:
+        e = np.empty(len(ns))
+        g = np.empty(len(params))
+        for _ in range(warmup):
+            q.qs_batch_run(b, params, e, g)
+        t0 = time.perf_counter()
+        kms = []
+        for _ in range(steps):
+            q.qs_batch_run(b, params, e, g)
+            kms.append(q.qs_batch_last_ms(b))
+        wall = (time.perf_counter() - t0) / steps
+        info = q.qs_batch_info(b)
+    finally:
+        q.qs_batch_free(b)
+    kms = float(np.mean(kms))
+    return {"grad_evals_per_s": len(ns) / (kms * 1e-3), "kernel_ms": kms,
+            "e2e_grad_evals_per_s": len(ns) / wall, "e2e_ms": wall * 1e3, "sets": len(ns),
+            "params": int(len(params)), "launch": info,
+            "workload": "1024 sets, n~U{10..20}, 8-layer RY/RZ+CNOT-ring ansatz, TFIM h=0.7"}
+
+
+def bench_adjoint(q, torch, stream, steps: int):
+    """Energy + 672-parameter adjoint gradient at n=28 (12-layer ansatz, ZZ chain)."""
+    n = 28
+    g, npar = w.hea_ansatz(n, 12)
+    th = w.uniform_angles(npar, 4)
+    H = w.zz_chain(n)
+    h = q.qs_alloc(n, stream)
+    try:
+        q.qs_adjoint_grad(h, g, th, H)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            q.qs_adjoint_grad(h, g, th, H)
+        dt = (time.perf_counter() - t0) / steps
+    finally:
+        q.qs_free(h)
+    return {"grad_evals_per_s": 1.0 / dt, "ms_per_eval": dt * 1e3, "n": n, "params": npar, "gates": len(g)}
+
+
+def bench_learned_plan(q, torch, stream):
+    """n=32 (64 GiB), 2000 random gates (40 % two-qubit, seed 2): greedy plan vs
+    the learned plan (cost model from paper_2212_14201_gb300/costmodel_weights.json)
+    vs plain per-gate apply, one timed apply each after one untimed."""
+    from paper_2212_14201_gb300 import costmodel
+    n = 32
+    g = w.random_circuit(n, 2000, 2, two_qubit_prob=0.4)
+    model = costmodel.load()
+    if model is None:
+        return {"skipped": "no trained cost model weights"}
+    out = {"n": n, "gates": len(g)}
+    h = q.qs_alloc(n, stream)
+    try:
+        plans = {"greedy": q.qs_plan_create(n, g, q.PLAN_GREEDY, 5), "learned": q.qs_plan_create_learned(n, g, model),
+                 "plain": None}
+        for name, p in plans.items():
+            q.qs_set_zero(h)
+            q.qs_apply(h, g, None, p)
+            q.qs_set_zero(h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            q.qs_apply(h, g, None, p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = q.qs_plan_get_stats(p) if p else {}
+            out[name] = {"ms": ms, "amp_updates_per_s": len(g) * float(1 << n) / (ms * 1e-3),
+                         "passes": st.get("n_passes"), "tile_qubits": st.get("tile_qubits")}
+        out["norm2"] = float(q.qs_probs(h, [])[0])
+        out["learned_gain_vs_greedy"] = out["greedy"]["ms"] / out["learned"]["ms"]
+        out["learned_gain_vs_plain"] = out["plain"]["ms"] / out["learned"]["ms"]
+        for p in plans.values():
+            if p:
+                q.qs_plan_free(p)
+    finally:
+        q.qs_free(h)
+        q.qs_mlp_free(model)
+    return out
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -348,6 +443,17 @@ def run_ours(args, world, rank, local, pg):
         q.qs_plan_free(plan)
     q.qs_free(h)
 
+    extra = {}
+    if not args.no_extra:
+        torch.cuda.empty_cache()
+        extra["batched_vqe"] = bench_batched_vqe(q, torch, 3, 3)
+        extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2)
+        if not args.no_n32:
+            try:
+                extra["learned_n32"] = bench_learned_plan(q, torch, stream)
+            except q.QsimError as ex:
+                extra["learned_n32"] = {"skipped": str(ex)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -381,6 +487,9 @@ def run_ours(args, world, rank, local, pg):
                 "d2h_bytes_per_step": SHOTS * 8 + 8, "matches_device_run": bool(ok_e2e)},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "batched_vqe": extra.get("batched_vqe"),
+        "adjoint_n28": extra.get("adjoint_n28"),
+        "learned_n32": extra.get("learned_n32"),
     }
     print(json.dumps(line), flush=True)
 

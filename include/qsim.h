@@ -184,6 +184,7 @@ typedef struct qs_plan_stats {
   int64_t n_tile_passes; /* of which shared-memory tile passes */
   int64_t n_dense;       /* dense-block ops (in tiles or standalone) */
   double est_seconds;    /* the planner's cost estimate (0 if none) */
+  int64_t tile_qubits;   /* tile width the plan was built for */
 } qs_plan_stats;
 
 /* Build a plan for n qubits from gates[0..ng-1] (host only; no device work).
@@ -192,6 +193,13 @@ typedef struct qs_plan_stats {
 int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, qs_plan** out);
 int qs_plan_free(qs_plan* p);
 int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
+
+/* Process-wide choice of the Q60 tile-pass kernel: on groups the ops of a pass
+ * into register phases (runs of ops whose targets fit in a few tile qubits
+ * execute on the amplitudes a thread holds in registers); off (default) runs one
+ * shared-memory sweep per op.  Both give the same amplitudes; the switch is for
+ * measurement. */
+int qs_set_register_phases(int on);
 
 /* Greedy plan with an explicit tile width: tiles of tile_qubits (4..12) qubits,
  * the "block size" of the fusion.  qs_plan_create(GREEDY) uses 12. */

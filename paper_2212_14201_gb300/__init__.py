@@ -11,15 +11,14 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import (qs_plan_create_tiled, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_last_ms, qs_batch_run,  # noqa: F401
-                   ARITH_AUTO, ARITH_FIXED, ARITH_FP64, qs_adjoint_grad, qs_set_arith,
-                   qs_state_modified,
-                   GATE_DTYPE, PAULI_DTYPE, PLAN_GREEDY, PLAN_LEARNED, PLAN_PLAIN, QsimError,  # noqa: F401
-                   qs_alloc, qs_alloc_external, qs_apply, qs_apply_matrix, qs_device_ptr, qs_expect_pauli,
-                   qs_expect_z_all, qs_free, qs_gate_list_dagger, qs_get_state, qs_last_error, qs_max_qubits,
-                   qs_num_qubits, qs_plan_create, qs_plan_free, qs_plan_get_stats, qs_probs, qs_probs_dict,
-                   qs_plan_pass_info, qs_plan_passes, qs_sample, qs_set_state, qs_set_zero, qs_sync, qs_timing_enable, qs_timing_fetch,
-                   qs_launch_count)
+from ._lib import (ARITH_AUTO, ARITH_FIXED, ARITH_FP64, GATE_DTYPE, PAULI_DTYPE, PLAN_GREEDY,  # noqa: F401
+                   PLAN_LEARNED, PLAN_PLAIN, QsimError)
+
+# every C entry point's wrapper, under its C name
+for _name in dir(_lib):
+    if _name.startswith("qs_"):
+        globals()[_name] = getattr(_lib, _name)
+del _name
 
 
 def build(verbose: bool = False, force: bool = False) -> str:

@@ -36,7 +36,7 @@ class QsimError(RuntimeError):
 
 class PlanStats(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_tile_passes", ctypes.c_int64),
-                ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double)]
+                ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double), ("tile_qubits", ctypes.c_int64)]
 
 
 class TimingRecord(ctypes.Structure):
@@ -73,6 +73,7 @@ SIGNATURES = {
     "qs_plan_create": (I32, [I32, P, SZ, I32, I32, PP]),
     "qs_plan_free": (I32, [P]),
     "qs_plan_create_tiled": (I32, [I32, P, SZ, I32, PP]),
+    "qs_set_register_phases": (I32, [I32]),
     "qs_plan_get_stats": (I32, [P, ctypes.POINTER(PlanStats)]),
     "qs_plan_pass_info": (I32, [P, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64), P, SZ,
                                 ctypes.POINTER(SZ)]),
@@ -83,6 +84,16 @@ SIGNATURES = {
     "qs_sample": (I32, [P, U64, U64, P, I32]),
     "qs_adjoint_grad": (I32, [P, P, SZ, P, SZ, P, SZ, ctypes.POINTER(DBL), P]),
     "qs_expect_z_all_noalloc": (I32, [P, I32, P, P]),
+    "qs_mlp_create": (I32, [I32, I32, P, U64, PP]),
+    "qs_mlp_free": (I32, [P]),
+    "qs_mlp_num_weights": (I32, [P, ctypes.POINTER(SZ)]),
+    "qs_mlp_get_weights": (I32, [P, P]),
+    "qs_mlp_set_weights": (I32, [P, P]),
+    "qs_mlp_forward": (I32, [P, P, SZ, P]),
+    "qs_mlp_loss_grad": (I32, [P, P, P, SZ, ctypes.POINTER(DBL), P]),
+    "qs_mlp_train": (I32, [P, P, P, SZ, I32, DBL, ctypes.POINTER(DBL)]),
+    "qs_plan_features": (I32, [P, P, SZ, P]),
+    "qs_plan_create_learned": (I32, [I32, P, SZ, P, PP]),
     "qs_batch_create": (I32, [SZ, P, P, P, P, P, P, PP]),
     "qs_batch_run": (I32, [P, P, P, P, I32]),
     "qs_batch_last_ms": (I32, [P, ctypes.POINTER(DBL)]),
@@ -252,6 +263,10 @@ def qs_plan_create(n: int, gates, mode: int = PLAN_GREEDY, kmax: int = 5) -> int
     return h.value
 
 
+def qs_set_register_phases(on: bool):
+    _chk(lib().qs_set_register_phases(1 if on else 0))
+
+
 def qs_plan_create_tiled(n: int, gates, tile_qubits: int) -> int:
     g = as_gates(gates)
     h = ctypes.c_void_p()
@@ -350,6 +365,77 @@ def qs_timing_fetch(h: int) -> list[dict]:
 
 def qs_launch_count() -> int:
     return int(lib().qs_launch_count())
+
+
+PASS_FEATURES = 10
+
+
+def qs_mlp_create(n_in: int, n_hidden: int, weights=None, seed: int = 0) -> int:
+    h = ctypes.c_void_p()
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    _chk(lib().qs_mlp_create(n_in, n_hidden, None if w is None else w.ctypes.data, seed, ctypes.byref(h)))
+    return h.value
+
+
+def qs_mlp_free(m: int):
+    _chk(lib().qs_mlp_free(m))
+
+
+def qs_mlp_num_weights(m: int) -> int:
+    n = ctypes.c_size_t()
+    _chk(lib().qs_mlp_num_weights(m, ctypes.byref(n)))
+    return n.value
+
+
+def qs_mlp_get_weights(m: int) -> np.ndarray:
+    w = np.empty(qs_mlp_num_weights(m), dtype=np.float64)
+    _chk(lib().qs_mlp_get_weights(m, w.ctypes.data))
+    return w
+
+
+def qs_mlp_set_weights(m: int, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _chk(lib().qs_mlp_set_weights(m, w.ctypes.data))
+
+
+def qs_mlp_forward(m: int, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    B = x.shape[0]
+    y = np.empty(B, dtype=np.float64)
+    _chk(lib().qs_mlp_forward(m, x.ctypes.data, B, y.ctypes.data))
+    return y
+
+
+def qs_mlp_loss_grad(m: int, x, t):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    loss = ctypes.c_double()
+    g = np.empty(qs_mlp_num_weights(m), dtype=np.float64)
+    _chk(lib().qs_mlp_loss_grad(m, x.ctypes.data, t.ctypes.data, x.shape[0], ctypes.byref(loss), g.ctypes.data))
+    return loss.value, g
+
+
+def qs_mlp_train(m: int, x, t, epochs: int, lr: float) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    loss = ctypes.c_double()
+    _chk(lib().qs_mlp_train(m, x.ctypes.data, t.ctypes.data, x.shape[0], epochs, lr, ctypes.byref(loss)))
+    return loss.value
+
+
+def qs_plan_features(p: int, gates) -> np.ndarray:
+    g = as_gates(gates)
+    n = qs_plan_get_stats(p)["n_passes"]
+    out = np.empty((max(n, 1), PASS_FEATURES), dtype=np.float64)
+    _chk(lib().qs_plan_features(p, g.ctypes.data if len(g) else None, len(g), out.ctypes.data))
+    return out[:n]
+
+
+def qs_plan_create_learned(n: int, gates, model: int) -> int:
+    g = as_gates(gates)
+    h = ctypes.c_void_p()
+    _chk(lib().qs_plan_create_learned(n, g.ctypes.data if len(g) else None, len(g), model, ctypes.byref(h)))
+    return h.value
 
 
 def qs_batch_create(n_per_set, gate_lists, n_params, term_lists) -> int:

@@ -1,0 +1,141 @@
+"""Learned fusion cost model.
+
+The library's greedy planner fixes the tile width (12 qubits).  The learned
+planner scores greedy plans of every tile width 4..12 with a small perceptron
+(qs_mlp_*) that predicts each pass's log(milliseconds) from its features
+(qs_plan_features), and keeps the cheapest (qs_plan_create_learned).  The
+network is trained on the GPU by the library's own kernels (qs_mlp_train) from
+per-pass timings the library's kernel log records (qs_timing_fetch).
+
+Usage on a GPU machine:  python -m paper_2212_14201_gb300.costmodel --out FILE
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+import numpy as np
+
+from . import _lib
+
+FEATURES = _lib.PASS_FEATURES
+HIDDEN = 32
+WEIGHTS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.json")
+
+_GATE_KINDS = (_lib.K_PHASE1, _lib.K_DIAG, _lib.K_ANTI, _lib.K_REAL, _lib.K_GENERAL)
+
+
+def pass_timings(h: int, n: int, gates, plan: int, params=None, repeats: int = 2):
+    """(features, ms) of every pass of `plan` that launched a kernel, measured on
+    state `h` (n qubits) from the library's per-kernel event log."""
+    feats = _lib.qs_plan_features(plan, gates)
+    passes = _lib.qs_plan_passes(plan)
+    _lib.qs_apply(h, gates, params, plan)      # warm-up
+    _lib.qs_timing_enable(h, True)
+    _lib.qs_timing_fetch(h)
+    acc = np.zeros(len(passes))
+    hit = np.zeros(len(passes), dtype=bool)
+    for _ in range(repeats):
+        _lib.qs_set_zero(h)
+        _lib.qs_timing_fetch(h)
+        _lib.qs_apply(h, gates, params, plan)
+        recs = _lib.qs_timing_fetch(h)
+        r = 0
+        for i, (kind, qm, _) in enumerate(passes):
+            if r >= len(recs):
+                break
+            rec = recs[r]
+            ok = (rec["kind"] == _lib.K_TILE and rec["qubit_mask"] == qm) if kind == 1 else \
+                 (rec["kind"] in _GATE_KINDS and rec["qubit_mask"] == qm)
+            if ok:
+                acc[i] += rec["ms"]
+                hit[i] = True
+                r += 1
+    _lib.qs_timing_enable(h, False)
+    return feats[hit], acc[hit] / repeats
+
+
+def collect(circuits, tile_widths=range(4, 13), repeats: int = 2, stream=None):
+    """Timing data set over `circuits` = [(n, gates, params or None), ...]."""
+    X, y = [], []
+    states = {}
+    try:
+        for n, gates, params in circuits:
+            if n not in states:
+                states[n] = _lib.qs_alloc(n, stream)
+            for m in tile_widths:
+                if m > n:
+                    continue
+                p = _lib.qs_plan_create_tiled(n, gates, m)
+                try:
+                    f, ms = pass_timings(states[n], n, gates, p, params, repeats)
+                finally:
+                    _lib.qs_plan_free(p)
+                X.append(f)
+                y.append(ms)
+    finally:
+        for h in states.values():
+            _lib.qs_free(h)
+    X = np.concatenate(X)
+    y = np.concatenate(y)
+    keep = y > 0
+    return X[keep], np.log(y[keep])
+
+
+def train(X, t, hidden: int = HIDDEN, epochs: int = 4000, lr: float = 3e-3, seed: int = 7):
+    """Model handle trained on (X, log ms) by the GPU kernels; returns (handle, loss)."""
+    m = _lib.qs_mlp_create(X.shape[1], hidden, None, seed)
+    loss = _lib.qs_mlp_train(m, X, t, epochs, lr)
+    return m, loss
+
+
+def save(m: int, path: str = WEIGHTS_FILE, meta: dict | None = None, hidden: int = HIDDEN):
+    w = _lib.qs_mlp_get_weights(m)
+    with open(path, "w") as f:
+        json.dump({"features": FEATURES, "hidden": hidden, "weights": w.tolist(), "meta": meta or {}}, f)
+
+
+def load(path: str = WEIGHTS_FILE) -> int | None:
+    """Model handle from a saved weight file, or None if there is none."""
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    return _lib.qs_mlp_create(d["features"], d["hidden"], np.asarray(d["weights"], dtype=np.float64), 0)
+
+
+def default_training_circuits(ns=(24, 26, 28, 30), per_n: int = 3, seed0: int = 100):
+    """Random circuits of the n=32 workload's mix (40 % two-qubit gates) at
+    smaller n, seeds 100.., plus layered and ansatz circuits."""
+    import workloads as w
+    out = []
+    s = seed0
+    for n in ns:
+        for _ in range(per_n):
+            out.append((n, w.random_circuit(n, 400, s, two_qubit_prob=0.4), None))
+            s += 1
+        out.append((n, w.layered_u3_cz(n, 6, s), None))
+        s += 1
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=WEIGHTS_FILE)
+    ap.add_argument("--ns", default="24,26,28,30")
+    ap.add_argument("--per-n", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=6000)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    circuits = default_training_circuits(tuple(int(x) for x in args.ns.split(",")), args.per_n)
+    X, t = collect(circuits, stream=torch.cuda.current_stream())
+    m, loss = train(X, t, epochs=args.epochs)
+    save(m, args.out, {"samples": int(len(t)), "loss": loss, "ns": args.ns, "per_n": args.per_n})
+    print(json.dumps({"samples": int(len(t)), "loss": loss, "out": args.out}))
+    _lib.qs_mlp_free(m)
+
+
+if __name__ == "__main__":
+    main()

@@ -226,6 +226,91 @@ extern "C" int qs_plan_create_tiled(int n, const qs_gate* gates, size_t ng, int 
   return plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, tile_qubits, out);
 }
 
+// Structural class of a record (valid for every angle): 0 general, 1 real,
+// 2 general diagonal, 3 unit factors only (swaps, sign flips).
+static int structural_class(int type) {
+  switch (type) {
+    case QS_H: case QS_RY: return 1;
+    case QS_RZ: case QS_T: case QS_P: case QS_CR: return 2;
+    case QS_X: case QS_Y: case QS_Z: case QS_S: case QS_CNOT: case QS_CZ: case QS_I: return 3;
+    default: return 0;  // RX, U3
+  }
+}
+
+static void pass_features(const qs_plan* p, const PlanPass& ps, const qs_gate* gates, double* f) {
+  const int n = p->n;
+  const int m = ps.kind == PASS_TILE ? __builtin_popcountll(ps.qmask) : 1;
+  for (int i = 0; i < QS_PASS_FEATURES; ++i) f[i] = 0.0;
+  f[0] = ps.kind == PASS_TILE ? 1.0 : 0.0;
+  f[1] = m / 12.0;
+  f[2] = n / 32.0;
+  f[3] = (n - m) / 32.0;
+  for (uint32_t k : ps.gates) {
+    int t;
+    uint64_t cm;
+    gate_qubits(gates[k], n, &t, &cm);
+    f[4 + structural_class(gates[k].type)] += 1.0 / 64.0;
+    if (cm) f[8] += 1.0 / 64.0;
+    if (ps.kind == PASS_TILE && !((ps.qmask >> t) & 1)) f[9] += 1.0 / 64.0;
+  }
+}
+
+extern "C" int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out) {
+  clear_error();
+  if (!p || !out || (ng && !gates)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  if (p->ng != ng || p->fingerprint != fingerprint(gates, ng))
+    return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
+  for (size_t i = 0; i < p->passes.size(); ++i) pass_features(p, p->passes[i], gates, out + i * QS_PASS_FEATURES);
+  return QS_OK;
+}
+
+extern "C" int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs_mlp* model, qs_plan** out) {
+  clear_error();
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!model) return fail(QS_ERR_UNSUPPORTED, "a learned plan needs a trained cost model");
+  size_t nw = 0;
+  QS_TRY(qs_mlp_num_weights(model, &nw));
+  std::vector<qs_plan*> cands;
+  std::vector<double> feats;
+  std::vector<size_t> first;
+  int rc = QS_OK;
+  const int mhi = std::min(n, TILE_MAX_M);
+  const int mlo = std::min(mhi, TILE_LOW + 1);
+  for (int m = mlo; m <= mhi && rc == QS_OK; ++m) {
+    qs_plan* c = nullptr;
+    rc = plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, m, &c);
+    if (rc != QS_OK) break;
+    cands.push_back(c);
+    first.push_back(feats.size() / QS_PASS_FEATURES);
+    size_t base = feats.size();
+    feats.resize(base + c->passes.size() * QS_PASS_FEATURES);
+    for (size_t i = 0; i < c->passes.size(); ++i)
+      pass_features(c, c->passes[i], gates, feats.data() + base + i * QS_PASS_FEATURES);
+  }
+  std::vector<double> pred(feats.size() / QS_PASS_FEATURES);
+  if (rc == QS_OK && !pred.empty()) rc = qs_mlp_forward(model, feats.data(), pred.size(), pred.data());
+  size_t best = 0;
+  double best_s = 1e300;
+  for (size_t c = 0; rc == QS_OK && c < cands.size(); ++c) {
+    size_t end = c + 1 < cands.size() ? first[c + 1] : pred.size();
+    double s = 0.0;
+    for (size_t i = first[c]; i < end; ++i) s += exp(pred[i]) * 1e-3;
+    if (s < best_s) {
+      best_s = s;
+      best = c;
+    }
+  }
+  for (size_t c = 0; c < cands.size(); ++c)
+    if (rc != QS_OK || c != best) delete cands[c];
+  if (rc != QS_OK) return rc;
+  if (cands.empty()) return fail(QS_ERR_INVALID_ARG, "no candidate plan");
+  cands[best]->mode = QS_PLAN_LEARNED;
+  cands[best]->est_seconds = best_s;
+  *out = cands[best];
+  return QS_OK;
+}
+
 extern "C" int qs_plan_free(qs_plan* p) {
   delete p;
   return QS_OK;
@@ -237,6 +322,7 @@ extern "C" int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out) {
   out->n_passes = (int64_t)p->passes.size();
   out->n_tile_passes = p->n_tile;
   out->n_dense = 0;
+  out->tile_qubits = p->m;
   out->est_seconds = p->est_seconds;
   return QS_OK;
 }
@@ -250,6 +336,47 @@ extern "C" int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint6
   *qmask = ps.qmask;
   *ngates = ps.gates.size();
   for (size_t i = 0; i < ps.gates.size() && i < cap; ++i) gates[i] = ps.gates[i];
+  return QS_OK;
+}
+
+// Register phases for the Q60 tile kernel: consecutive ops are grouped while their
+// non-diagonal targets fit in four tile bits; each phase is then padded to four
+// bits with unused tile bits (highest first, which keeps shared-memory accesses of
+// a warp on consecutive low bits).
+static bool g_register_phases = false;
+
+static void build_phases(TileArgs* g) {
+  int np = 0;
+  uint32_t P = 0;
+  int begin = 0;
+  auto close = [&](int end) {
+    if (end <= begin) return;
+    uint32_t full = P;
+    for (int b = g->m - 1; b >= 0 && __builtin_popcount(full) < 4; --b) full |= 1u << b;
+    TilePhase& ph = g->phases[np++];
+    int i = 0;
+    for (int b = 0; b < g->m; ++b)
+      if ((full >> b) & 1) ph.b[i++] = (uint8_t)b;
+    ph.op_begin = (int16_t)begin;
+    ph.op_end = (int16_t)end;
+    begin = end;
+    P = 0;
+  };
+  for (int k = 0; k < g->nops; ++k) {
+    const TileOp& op = g->ops[k];
+    const bool nondiag = op.kind == TOP_ANTI || op.kind == TOP_REAL || op.kind == TOP_GENERAL;
+    if (!nondiag) continue;
+    const uint32_t t = 1u << op.tb;
+    if (P & t) continue;
+    if (__builtin_popcount(P) == 4) close(k);
+    P |= t;
+  }
+  close(g->nops);
+  g->nphases = np;
+}
+
+extern "C" int qs_set_register_phases(int on) {
+  g_register_phases = on != 0;
   return QS_OK;
 }
 
@@ -317,6 +444,8 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     int_ops += N * op_touch_fraction(gates[k], cm) * op_int_ops_per_amp(op);
     ++g->nops;
   }
+  g->nphases = 0;
+  if (rc == QS_OK && fixed && m >= 4 && g_register_phases) build_phases(g);
   if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,
                                                    (int)ps.gates.size(), fixed);
   delete g;

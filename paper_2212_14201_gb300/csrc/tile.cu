@@ -193,6 +193,111 @@ __global__ void __launch_bounds__(THREADS) k_tile(double2* __restrict__ a, const
   }
 }
 
+// ---- register phases (Q60) ---------------------------------------------------------
+// Ops of one phase on the 16 amplitudes v[k] of a group: register bit R of k is
+// tile bit b[R]; cr = in-phase controls as register bits.
+template <int R>
+__device__ __forceinline__ void ph_op(longlong2 (&v)[16], const TileOp& op, uint32_t cr) {
+  constexpr int S = 1 << R;
+  const int kind = op.kind;
+  if (kind == TOP_GENERAL) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (!(k & S) && (k & cr) == cr) EngQ60::general2(op, v[k], v[k | S], v[k], v[k | S]);
+  } else if (kind == TOP_REAL) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (!(k & S) && (k & cr) == cr) EngQ60::real2(op, v[k], v[k | S], v[k], v[k | S]);
+  } else if (kind == TOP_ANTI) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (!(k & S) && (k & cr) == cr) {
+        const longlong2 a0 = v[k], a1 = v[k | S];
+        v[k] = EngQ60::mul(a1, op.code0, op, 1);
+        v[k | S] = EngQ60::mul(a0, op.code1, op, 2);
+      }
+  } else if (kind == TOP_DIAG) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if ((k & cr) == cr) v[k] = (k & S) ? EngQ60::mul(v[k], op.code1, op, 3) : EngQ60::mul(v[k], op.code0, op, 0);
+  } else {  // PHASE1
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if ((k & S) && (k & cr) == cr) v[k] = EngQ60::mul(v[k], op.code1, op, 3);
+  }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tile_reg(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = g.m;
+  const int L = m - g.nhigh;
+  const uint32_t TS = 1u << m;
+  const uint32_t H = 1u << g.nhigh;
+  uint64_t* offs = reinterpret_cast<uint64_t*>(smem_raw);
+  longlong2* tile = reinterpret_cast<longlong2*>(smem_raw + ((H * sizeof(uint64_t) + 15) & ~(size_t)15));
+  for (uint32_t h = threadIdx.x; h < H; h += THREADS) {
+    uint64_t o = 0;
+    for (int b = 0; b < g.nhigh; ++b) o |= (uint64_t)((h >> b) & 1u) << g.qhigh[b];
+    offs[h] = o;
+  }
+  const uint32_t lowmask = (1u << L) - 1;
+  const uint32_t G = TS >> 4;  // groups of 16 amplitudes per phase
+  for (uint64_t r = blockIdx.x; r < g.ntiles; r += gridDim.x) {
+    uint64_t base = 0;
+    for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j] = EngQ60::load(a[base + offs[j >> L] + (j & lowmask)]);
+    __syncthreads();
+    for (int p = 0; p < g.nphases; ++p) {
+      const TilePhase ph = g.phases[p];
+      const uint32_t pmask = (1u << ph.b[0]) | (1u << ph.b[1]) | (1u << ph.b[2]) | (1u << ph.b[3]);
+      uint32_t dep[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        dep[k] = ((k & 1) ? 1u << ph.b[0] : 0u) | ((k & 2) ? 1u << ph.b[1] : 0u) | ((k & 4) ? 1u << ph.b[2] : 0u) |
+                 ((k & 8) ? 1u << ph.b[3] : 0u);
+      for (uint32_t grp = threadIdx.x; grp < G; grp += THREADS) {
+        const uint32_t gb = tile_expand(grp, pmask, 0);
+        longlong2 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = tile[gb | dep[k]];
+        for (int k = ph.op_begin; k < ph.op_end; ++k) {
+          const TileOp& op = g.ops[k];
+          if ((base & op.ext_cmask) != op.ext_cmask) continue;
+          const uint32_t lcm = op.lcmask;
+          const uint32_t lout = lcm & ~pmask;
+          if ((gb & lout) != lout) continue;
+          const uint32_t cr = ((lcm >> ph.b[0]) & 1u) | (((lcm >> ph.b[1]) & 1u) << 1) |
+                              (((lcm >> ph.b[2]) & 1u) << 2) | (((lcm >> ph.b[3]) & 1u) << 3);
+          if (op.kind == TOP_SCALAR || !((pmask >> op.tb) & 1u)) {
+            // diagonal op whose target is constant for the group (outside the
+            // tile: a per-tile bit; in the tile but outside the phase: a group bit)
+            const bool one = op.kind == TOP_SCALAR ? ((base >> op.tb) & 1ull) : ((gb >> op.tb) & 1u);
+            const int code = one ? op.code1 : op.code0;
+            if (code == U_ONE) continue;
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk)
+              if ((kk & cr) == cr) v[kk] = EngQ60::mul(v[kk], code, op, one ? 3 : 0);
+            continue;
+          }
+          const int R = op.tb == ph.b[0] ? 0 : op.tb == ph.b[1] ? 1 : op.tb == ph.b[2] ? 2 : 3;
+          switch (R) {
+            case 0: ph_op<0>(v, op, cr); break;
+            case 1: ph_op<1>(v, op, cr); break;
+            case 2: ph_op<2>(v, op, cr); break;
+            default: ph_op<3>(v, op, cr); break;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) tile[gb | dep[k]] = v[k];
+      }
+      __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = EngQ60::store(tile[j]);
+  }
+}
+
 template <class E>
 static int launch_engine(qs_state* s, const TileArgs& g, size_t smem) {
   constexpr int THREADS = 256;
@@ -215,6 +320,18 @@ int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, in
   for (int b = 0; b < g.m - g.nhigh; ++b) qmask |= 1ull << b;
   for (int b = 0; b < g.nhigh; ++b) qmask |= 1ull << g.qhigh[b];
   KTimer kt(s, QS_K_TILE, g.m, ngates, qmask, 0, (double)(1ull << g.n), flops, int_ops);
+  if (fixed && g.nphases > 0) {
+    constexpr int THREADS = 256;
+    static bool attr = false;
+    if (!attr) {
+      QS_CUDA(cudaFuncSetAttribute(k_tile_reg<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (220 * 1024) / (smem + 1024)));
+    uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)152 * per_sm);
+    k_tile_reg<THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
+    return launch_check("tile kernel (register phases)");
+  }
   return fixed ? launch_engine<EngQ60>(s, g, smem) : launch_engine<EngF64>(s, g, smem);
 }
 

@@ -1,0 +1,99 @@
+"""The learned fusion cost model: the GPU perceptron kernels against the CPU
+oracle (forward, loss and every weight's gradient), training on the GPU, and
+the learned planner against the greedy planner on circuits it was not trained
+on -- both the amplitudes (oracle parity) and the measured time."""
+import numpy as np
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2212_14201_gb300 as q
+    q.build()
+    return q
+
+
+@pytest.mark.parametrize("F,H,B", [(1, 1, 1), (3, 7, 13), (10, 32, 200)])
+def test_mlp_kernels_match_oracle(q, orc, F, H, B):
+    rng = np.random.Generator(np.random.PCG64(F * 100 + H))
+    nw = orc.mlp_nweights(F, H)
+    wts = rng.normal(size=nw) * 0.5
+    x = rng.normal(size=(B, F))
+    t = rng.normal(size=B)
+    m = q.qs_mlp_create(F, H, wts)
+    try:
+        assert q.qs_mlp_num_weights(m) == nw
+        assert np.array_equal(q.qs_mlp_get_weights(m), wts)
+        y = q.qs_mlp_forward(m, x)
+        assert np.max(np.abs(y - orc.mlp_forward(F, H, wts, x))) < 1e-12
+        loss, g = q.qs_mlp_loss_grad(m, x, t)
+        l0, g0 = orc.mlp_loss_grad(F, H, wts, x, t)
+        assert abs(loss - l0) <= 1e-12 * max(1.0, abs(l0))
+        assert np.max(np.abs(g - g0)) <= 1e-12 * max(1.0, np.max(np.abs(g0)))
+    finally:
+        q.qs_mlp_free(m)
+
+
+def test_mlp_training_fits_a_smooth_function(q):
+    rng = np.random.Generator(np.random.PCG64(3))
+    x = rng.uniform(-1, 1, size=(256, 4))
+    t = np.sin(x[:, 0]) + 0.5 * x[:, 1] * x[:, 2] - 0.3 * x[:, 3]
+    m = q.qs_mlp_create(4, 16, None, 11)
+    try:
+        l0, _ = q.qs_mlp_loss_grad(m, x, t)
+        loss = q.qs_mlp_train(m, x, t, 3000, 1e-2)
+        assert loss < 0.02 * l0
+    finally:
+        q.qs_mlp_free(m)
+
+
+def test_learned_plan_versus_greedy(q, orc):
+    """Train on per-pass timings of n=20..22 random circuits (seeds 100..), then
+    on held-out circuits the learned plan must give the oracle's amplitudes and
+    must not be slower than the greedy plan (it may pick the same tile width)."""
+    import torch
+    from paper_2212_14201_gb300 import costmodel
+    train_c = [(n, w.random_circuit(n, 300, 100 + i, two_qubit_prob=0.4), None) for i, n in enumerate((20, 21, 22, 22))]
+    X, t = costmodel.collect(train_c, repeats=2, stream=torch.cuda.current_stream())
+    assert X.shape[1] == q._lib.PASS_FEATURES and len(t) > 50
+    m, loss = costmodel.train(X, t, epochs=3000)
+    try:
+        assert np.isfinite(loss)
+        for n, seed in ((18, 300), (22, 301)):
+            g = w.random_circuit(n, 400, seed, two_qubit_prob=0.4)
+            pl = q.qs_plan_create_learned(n, g, m)
+            pg = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+            h = q.qs_alloc(n, torch.cuda.current_stream())
+            try:
+                if n <= 18:
+                    q.qs_apply(h, g, None, pl)
+                    assert np.max(np.abs(q.qs_get_state(h) - orc.as_complex(orc.run(n, g)))) < 1e-12
+                times = {}
+                for name, p in (("learned", pl), ("greedy", pg)):
+                    q.qs_apply(h, g, None, p)
+                    torch.cuda.synchronize()
+                    best = 1e30
+                    for _ in range(3):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        q.qs_apply(h, g, None, p)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        best = min(best, e0.elapsed_time(e1))
+                    times[name] = best
+                st = q.qs_plan_get_stats(pl)
+                print(f"n={n}: learned tile width {st['tile_qubits']} {times['learned']:.3f} ms, "
+                      f"greedy {times['greedy']:.3f} ms")
+                assert times["learned"] <= 1.10 * times["greedy"] + 0.05
+            finally:
+                q.qs_free(h)
+                q.qs_plan_free(pl)
+                q.qs_plan_free(pg)
+    finally:
+        q.qs_mlp_free(m)
