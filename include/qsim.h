@@ -129,11 +129,11 @@ int qs_sync(const qs_state* s);
 
 /* Arithmetic of the gate kernels.  The state is complex128 in memory either way.
  *   QS_ARITH_AUTO  (default) Q60 fixed point when every |re|, |im| is known to
- *                  be <= 1.5 (true for any state of norm <= 1.5), else FP64;
+ *                  be <= 1.25 (true for any state of norm <= 1.25), else FP64;
  *   QS_ARITH_FP64  IEEE double arithmetic on the FP64 pipe;
  *   QS_ARITH_FIXED Q60 fixed point on the integer pipe: each component is
  *                  rounded to a multiple of 2^-60 while a kernel holds it and
- *                  products are exact to 2^-58; a state whose norm exceeds 1.5
+ *                  products are exact to 2^-60; a state whose norm exceeds 1.25
  *                  makes qs_apply return UNSUPPORTED.
  * The bound is known after qs_alloc / qs_set_zero and is kept by qs_apply
  * (unitary gates preserve the norm).  After qs_set_state, qs_alloc_external,
@@ -194,12 +194,12 @@ int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, q
 int qs_plan_free(qs_plan* p);
 int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
 
-/* Process-wide choice of the Q60 tile-pass kernel: on groups the ops of a pass
- * into register phases (runs of ops whose targets fit in a few tile qubits
- * execute on the amplitudes a thread holds in registers); off (default) runs one
- * shared-memory sweep per op.  Both give the same amplitudes; the switch is for
- * measurement. */
-int qs_set_register_phases(int on);
+/* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops
+ * of a pass into register phases (runs of ops whose targets fit in `bits` tile
+ * qubits execute on the 2^bits amplitudes a thread holds in registers); 0
+ * (default) runs one shared-memory sweep per op.  All give the same amplitudes;
+ * the switch is for measurement.  Errors: INVALID_ARG for other values. */
+int qs_set_register_phases(int bits);
 
 /* Greedy plan with an explicit tile width: tiles of tile_qubits (4..12) qubits,
  * the "block size" of the fusion.  qs_plan_create(GREEDY) uses 12. */
@@ -244,7 +244,7 @@ int qs_mlp_train(qs_mlp* m, const double* x, const double* t, size_t B, int epoc
 #define QS_PASS_FEATURES 10
 int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out);
 
-/* Learned plan: greedy plans for every tile width 4..12 are scored by the model
+/* Learned plan: greedy plans for every tile width 8..12 are scored by the model
  * (sum over passes of exp(predicted log ms)) and the cheapest is kept; its
  * est_seconds is the model's prediction.  The model needs QS_PASS_FEATURES inputs. */
 int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs_mlp* model, qs_plan** out);

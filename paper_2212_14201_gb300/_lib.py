@@ -263,8 +263,8 @@ def qs_plan_create(n: int, gates, mode: int = PLAN_GREEDY, kmax: int = 5) -> int
     return h.value
 
 
-def qs_set_register_phases(on: bool):
-    _chk(lib().qs_set_register_phases(1 if on else 0))
+def qs_set_register_phases(bits: int):
+    _chk(lib().qs_set_register_phases(int(bits)))
 
 
 def qs_plan_create_tiled(n: int, gates, tile_qubits: int) -> int:

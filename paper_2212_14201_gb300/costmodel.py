@@ -1,7 +1,7 @@
 """Learned fusion cost model.
 
 The library's greedy planner fixes the tile width (12 qubits).  The learned
-planner scores greedy plans of every tile width 4..12 with a small perceptron
+planner scores greedy plans of every tile width 8..12 with a small perceptron
 (qs_mlp_*) that predicts each pass's log(milliseconds) from its features
 (qs_plan_features), and keeps the cheapest (qs_plan_create_learned).  The
 network is trained on the GPU by the library's own kernels (qs_mlp_train) from
@@ -56,7 +56,7 @@ def pass_timings(h: int, n: int, gates, plan: int, params=None, repeats: int = 2
     return feats[hit], acc[hit] / repeats
 
 
-def collect(circuits, tile_widths=range(4, 13), repeats: int = 2, stream=None):
+def collect(circuits, tile_widths=range(8, 13), repeats: int = 2, stream=None):
     """Timing data set over `circuits` = [(n, gates, params or None), ...]."""
     X, y = [], []
     states = {}
@@ -105,7 +105,7 @@ def load(path: str = WEIGHTS_FILE) -> int | None:
     return _lib.qs_mlp_create(d["features"], d["hidden"], np.asarray(d["weights"], dtype=np.float64), 0)
 
 
-def default_training_circuits(ns=(24, 26, 28, 30), per_n: int = 3, seed0: int = 100):
+def default_training_circuits(ns=(24, 26, 28, 30), per_n: int = 2, seed0: int = 100):
     """Random circuits of the n=32 workload's mix (40 % two-qubit gates) at
     smaller n, seeds 100.., plus layered and ansatz circuits."""
     import workloads as w
@@ -124,7 +124,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=WEIGHTS_FILE)
     ap.add_argument("--ns", default="24,26,28,30")
-    ap.add_argument("--per-n", type=int, default=3)
+    ap.add_argument("--per-n", type=int, default=2)
     ap.add_argument("--epochs", type=int, default=6000)
     args = ap.parse_args()
     import torch

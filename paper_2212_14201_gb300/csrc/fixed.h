@@ -3,17 +3,18 @@
 // GB300 issues FP64 at 1/74 of its FP32 rate (measured: 5.0e11 DFMA/s against
 // 1.8e13 32x32->64 integer multiply-adds/s), so a complex128 2x2 gate costs
 // ~3x its HBM time in FP64.  The state stays complex128 in memory; inside a
-// kernel each real component v (|v| <= 1.5) is converted to V = round(v * 2^60),
+// kernel each real component v (|v| <= 1.25) is converted to V = round(v * 2^60),
 // a signed 64-bit integer, and gate matrices (|u| <= 1) likewise.  A product
-// U*A is formed from 32-bit limbs, V = h * 2^32 + l with l signed:
-//   U*A * 2^-60 = Uh*Ah * 2^4 + (Uh*Al + Ul*Ah) * 2^-28 + Ul*Al * 2^-60,
+// U*A is formed from limbs V = h * 2^30 + l with 0 <= l < 2^30:
+//   U*A * 2^-60 = Uh*Ah + (Uh*Al + Ul*Ah) * 2^-30 + Ul*Al * 2^-60,
 // the first two terms accumulated exactly in two int64 registers with
-// mad.wide.s32, the last (|.| < 2^-58 per product) dropped.  One output
+// mad.wide.s32, the last (< 2^-60 per product) dropped.  One output
 // component of a 2x2 complex matvec (four products) carries at most
-// 4 * 2^-58 + 2^-61 absolute error before the final rounding back to double
+// 4 * 2^-60 + 2^-61 absolute error before the final rounding back to double
 // (which adds the same <= 2^-53 relative error an FP64 kernel has).
-// Bounds for |components| <= 1.5: |h| <= 1.5 * 2^28, |l| <= 2^31, so the hi
-// accumulator stays below 2^59 and the mid accumulator below 2^63.
+// Bounds: the real and imaginary parts of one row of a unitary 2x2 sum to at
+// most 2 in absolute value, so with |components| <= 1.25 the hi accumulator
+// stays below 2.5 * 2^60 and the mid accumulator below 7 * 2^60 < 2^63.
 #pragma once
 
 #include <stdint.h>
@@ -27,7 +28,7 @@
 
 namespace qs {
 
-constexpr double Q60_MAX_ABS = 1.5;  // component bound under which the accumulators cannot overflow
+constexpr double Q60_MAX_ABS = 1.25;  // component bound under which the accumulators cannot overflow
 
 QS_HD uint64_t q_bits(double v) {
 #ifdef __CUDA_ARCH__
@@ -101,14 +102,13 @@ QS_HD double q60_to_double(int64_t V) {
   return q_from_bits((sign << 63) | (e << 52) | (mant & 0xFFFFFFFFFFFFFull));
 }
 
-// Limb split V = h * 2^32 + l, l the signed low 32 bits.
+// Limb split V = h * 2^30 + l with 0 <= l < 2^30 (h = floor(V / 2^30)).
 struct QL {
   int32_t h, l;
 };
 
 QS_HD QL q60_split(int64_t V) {
-  const int32_t l = (int32_t)(uint32_t)(uint64_t)V;
-  return {(int32_t)((V - (int64_t)l) >> 32), l};
+  return {(int32_t)(V >> 30), (int32_t)(V & ((1ll << 30) - 1))};
 }
 
 QS_HD int64_t madw(int32_t a, int32_t b, int64_t c) {
@@ -133,7 +133,7 @@ QS_HD void qacc_add(QAcc& acc, QL u, QL a) {
 }
 
 QS_HD int64_t qacc_result(const QAcc& acc) {
-  return (int64_t)((uint64_t)acc.hi << 4) + ((acc.mid + (1ll << 27)) >> 28);
+  return acc.hi + ((acc.mid + (1ll << 29)) >> 30);
 }
 
 // A Q60 complex number as limbs, plus its negated imaginary part (so that

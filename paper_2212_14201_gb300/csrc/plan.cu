@@ -275,8 +275,9 @@ extern "C" int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs
   std::vector<double> feats;
   std::vector<size_t> first;
   int rc = QS_OK;
+  // candidate tile widths 8..12: narrower tiles leave most of a CTA idle per op
   const int mhi = std::min(n, TILE_MAX_M);
-  const int mlo = std::min(mhi, TILE_LOW + 1);
+  const int mlo = std::min(mhi, 8);
   for (int m = mlo; m <= mhi && rc == QS_OK; ++m) {
     qs_plan* c = nullptr;
     rc = plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, m, &c);
@@ -340,19 +341,20 @@ extern "C" int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint6
 }
 
 // Register phases for the Q60 tile kernel: consecutive ops are grouped while their
-// non-diagonal targets fit in four tile bits; each phase is then padded to four
+// non-diagonal targets fit in `rb` tile bits; each phase is then padded to rb
 // bits with unused tile bits (highest first, which keeps shared-memory accesses of
-// a warp on consecutive low bits).
-static bool g_register_phases = false;
+// a warp on consecutive low bits).  g_register_bits = 0 disables the phases.
+static int g_register_bits = 0;
 
-static void build_phases(TileArgs* g) {
+static void build_phases(TileArgs* g, int rb) {
   int np = 0;
   uint32_t P = 0;
   int begin = 0;
+  g->reg_bits = rb;
   auto close = [&](int end) {
     if (end <= begin) return;
     uint32_t full = P;
-    for (int b = g->m - 1; b >= 0 && __builtin_popcount(full) < 4; --b) full |= 1u << b;
+    for (int b = g->m - 1; b >= 0 && __builtin_popcount(full) < rb; --b) full |= 1u << b;
     TilePhase& ph = g->phases[np++];
     int i = 0;
     for (int b = 0; b < g->m; ++b)
@@ -368,15 +370,16 @@ static void build_phases(TileArgs* g) {
     if (!nondiag) continue;
     const uint32_t t = 1u << op.tb;
     if (P & t) continue;
-    if (__builtin_popcount(P) == 4) close(k);
+    if (__builtin_popcount(P) == rb) close(k);
     P |= t;
   }
   close(g->nops);
   g->nphases = np;
 }
 
-extern "C" int qs_set_register_phases(int on) {
-  g_register_phases = on != 0;
+extern "C" int qs_set_register_phases(int bits) {
+  if (bits != 0 && bits != 3 && bits != 4) return fail(QS_ERR_INVALID_ARG, "register bits %d: use 0, 3 or 4", bits);
+  g_register_bits = bits;
   return QS_OK;
 }
 
@@ -445,7 +448,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     ++g->nops;
   }
   g->nphases = 0;
-  if (rc == QS_OK && fixed && m >= 4 && g_register_phases) build_phases(g);
+  if (rc == QS_OK && fixed && g_register_bits && m >= g_register_bits) build_phases(g, g_register_bits);
   if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,
                                                    (int)ps.gates.size(), fixed);
   delete g;

@@ -36,6 +36,23 @@ __device__ double block_sum256(double v, double* sh) {
 }
 
 // ---- full probability vector -------------------------------------------------------
+// per-CTA partial sums of |a_x|^2 (four interleaved accumulators per thread)
+__global__ void __launch_bounds__(256) k_norm2(const double2* __restrict__ a, uint64_t N, double* __restrict__ part) {
+  __shared__ double sh[8];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < N; i += 4 * stride) {
+    s0 += prob(a[i]);
+    s1 += prob(a[i + stride]);
+    s2 += prob(a[i + 2 * stride]);
+    s3 += prob(a[i + 3 * stride]);
+  }
+  for (; i < N; i += stride) s0 += prob(a[i]);
+  const double t = block_sum256((s0 + s1) + (s2 + s3), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 __global__ void k_probs_full(const double2* __restrict__ a, double* __restrict__ p, uint64_t N) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) p[i] = prob(a[i]);
@@ -237,6 +254,14 @@ static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout)
   if (identity) {
     k_probs_full<<<(int)std::min<uint64_t>((N + 255) / 256, 152 * 32), 256, 0, s->stream>>>(s->amps, dout, N);
     return launch_check("probs_full");
+  }
+  if (nq == 0) {  // squared norm: per-thread sums, a fixed shuffle tree, CTA partials in order
+    const int nblocks = (int)std::min<uint64_t>(608, std::max<uint64_t>(1, N / 1024));
+    double* part = (double*)s->ws;
+    k_norm2<<<nblocks, 256, 0, s->stream>>>(s->amps, N, part);
+    QS_TRY(launch_check("norm2"));
+    k_marginal_finish<<<1, 32, 0, s->stream>>>(part, nblocks, 1, dout);
+    return launch_check("norm2 finish");
   }
   if (nq <= 10) {  // 8 warp-private histograms of 2^nq doubles fit in shared memory
     MargArgs g;

@@ -53,6 +53,7 @@ __global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __res
   __shared__ long long lbuf[2048];
   __shared__ double carry;
   __shared__ long long lcarry;
+  __shared__ long long wmax[32];
   if (threadIdx.x == 0) {
     carry = 0.0;
     lcarry = -1;
@@ -66,16 +67,36 @@ __global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __res
       lbuf[i] = lastnz[c0 + i];
     }
     __syncthreads();
+    // the largest nonzero index so far: a max over the chunk (any order gives the same)
+    long long lm = -1;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) lm = max(lm, lbuf[i]);
+    for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lm;
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double e = carry;
       long long l = lcarry;
-      for (int i = 0; i < cnt; ++i) {
+      for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) l = max(l, wmax[wv]);
+      lcarry = l;
+      // the left-to-right sum itself: operands staged in registers eight at a time
+      double e = carry;
+      int i = 0;
+      for (; i + 8 <= cnt; i += 8) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = buf[i + k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          e = __dadd_rn(e, v[k]);
+          v[k] = e;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) buf[i + k] = v[k];
+      }
+      for (; i < cnt; ++i) {
         e = __dadd_rn(e, buf[i]);
         buf[i] = e;
-        if (lbuf[i] >= 0) l = lbuf[i];
       }
       carry = e;
-      lcarry = l;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) E[c0 + i + 1] = buf[i];

@@ -122,6 +122,34 @@ struct EngQ60 {
   }
 };
 
+// All pairs (j, j | tb) of one op in the tile, the op class fixed at compile time;
+// unrolled so that a thread has several independent pairs in flight.
+template <class E, int KIND, int THREADS>
+__device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uint32_t fixed, uint32_t lcm, uint32_t tb,
+                                          const TileOp& op) {
+  using T = typename E::T;
+#pragma unroll 4
+  for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
+    // without in-tile controls the insertion of one zero bit is a mask and an add
+    const uint32_t j0 = lcm ? tile_expand(i, fixed, lcm) : i + (i & ~(tb - 1)), j1 = j0 | tb;
+    const T a0 = tile[j0], a1 = tile[j1];
+    T b0, b1;
+    if (KIND == TOP_DIAG) {
+      b0 = E::mul(a0, op.code0, op, 0);
+      b1 = E::mul(a1, op.code1, op, 3);
+    } else if (KIND == TOP_ANTI) {
+      b0 = E::mul(a1, op.code0, op, 1);
+      b1 = E::mul(a0, op.code1, op, 2);
+    } else if (KIND == TOP_REAL) {
+      E::real2(op, a0, a1, b0, b1);
+    } else {
+      E::general2(op, a0, a1, b0, b1);
+    }
+    tile[j0] = b0;
+    tile[j1] = b1;
+  }
+}
+
 template <class E, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_tile(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
@@ -167,24 +195,14 @@ __global__ void __launch_bounds__(THREADS) k_tile(double2* __restrict__ a, const
             uint32_t j = tile_expand(i, fixed, lcm) | tb;
             tile[j] = E::mul(tile[j], op.code1, op, 3);
           }
+        } else if (op.kind == TOP_GENERAL) {
+          pair_loop<E, TOP_GENERAL, THREADS>(tile, cnt, fixed, lcm, tb, op);
+        } else if (op.kind == TOP_REAL) {
+          pair_loop<E, TOP_REAL, THREADS>(tile, cnt, fixed, lcm, tb, op);
+        } else if (op.kind == TOP_ANTI) {
+          pair_loop<E, TOP_ANTI, THREADS>(tile, cnt, fixed, lcm, tb, op);
         } else {
-          for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
-            uint32_t j0 = tile_expand(i, fixed, lcm), j1 = j0 | tb;
-            T a0 = tile[j0], a1 = tile[j1], b0, b1;
-            if (op.kind == TOP_DIAG) {
-              b0 = E::mul(a0, op.code0, op, 0);
-              b1 = E::mul(a1, op.code1, op, 3);
-            } else if (op.kind == TOP_ANTI) {
-              b0 = E::mul(a1, op.code0, op, 1);
-              b1 = E::mul(a0, op.code1, op, 2);
-            } else if (op.kind == TOP_REAL) {
-              E::real2(op, a0, a1, b0, b1);
-            } else {
-              E::general2(op, a0, a1, b0, b1);
-            }
-            tile[j0] = b0;
-            tile[j1] = b1;
-          }
+          pair_loop<E, TOP_DIAG, THREADS>(tile, cnt, fixed, lcm, tb, op);
         }
       }
       __syncthreads();
@@ -194,23 +212,24 @@ __global__ void __launch_bounds__(THREADS) k_tile(double2* __restrict__ a, const
 }
 
 // ---- register phases (Q60) ---------------------------------------------------------
-// Ops of one phase on the 16 amplitudes v[k] of a group: register bit R of k is
-// tile bit b[R]; cr = in-phase controls as register bits.
-template <int R>
-__device__ __forceinline__ void ph_op(longlong2 (&v)[16], const TileOp& op, uint32_t cr) {
+// Ops of one phase on the 2^RB amplitudes v[k] of a group: register bit R of k
+// is tile bit b[R]; cr = in-phase controls as register bits.
+template <int RB, int R>
+__device__ __forceinline__ void ph_op(longlong2 (&v)[1 << RB], const TileOp& op, uint32_t cr) {
   constexpr int S = 1 << R;
+  constexpr int K = 1 << RB;
   const int kind = op.kind;
   if (kind == TOP_GENERAL) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < K; ++k)
       if (!(k & S) && (k & cr) == cr) EngQ60::general2(op, v[k], v[k | S], v[k], v[k | S]);
   } else if (kind == TOP_REAL) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < K; ++k)
       if (!(k & S) && (k & cr) == cr) EngQ60::real2(op, v[k], v[k | S], v[k], v[k | S]);
   } else if (kind == TOP_ANTI) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < K; ++k)
       if (!(k & S) && (k & cr) == cr) {
         const longlong2 a0 = v[k], a1 = v[k | S];
         v[k] = EngQ60::mul(a1, op.code0, op, 1);
@@ -218,17 +237,18 @@ __device__ __forceinline__ void ph_op(longlong2 (&v)[16], const TileOp& op, uint
       }
   } else if (kind == TOP_DIAG) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < K; ++k)
       if ((k & cr) == cr) v[k] = (k & S) ? EngQ60::mul(v[k], op.code1, op, 3) : EngQ60::mul(v[k], op.code0, op, 0);
   } else {  // PHASE1
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < K; ++k)
       if ((k & S) && (k & cr) == cr) v[k] = EngQ60::mul(v[k], op.code1, op, 3);
   }
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tile_reg(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
+template <int RB, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_tile_reg(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
+  constexpr int K = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = g.m;
   const int L = m - g.nhigh;
@@ -242,7 +262,7 @@ __global__ void __launch_bounds__(THREADS) k_tile_reg(double2* __restrict__ a, c
     offs[h] = o;
   }
   const uint32_t lowmask = (1u << L) - 1;
-  const uint32_t G = TS >> 4;  // groups of 16 amplitudes per phase
+  const uint32_t G = TS >> RB;  // groups of 2^RB amplitudes per phase
   for (uint64_t r = blockIdx.x; r < g.ntiles; r += gridDim.x) {
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
@@ -251,25 +271,32 @@ __global__ void __launch_bounds__(THREADS) k_tile_reg(double2* __restrict__ a, c
     __syncthreads();
     for (int p = 0; p < g.nphases; ++p) {
       const TilePhase ph = g.phases[p];
-      const uint32_t pmask = (1u << ph.b[0]) | (1u << ph.b[1]) | (1u << ph.b[2]) | (1u << ph.b[3]);
-      uint32_t dep[16];
+      uint32_t pmask = 0;
 #pragma unroll
-      for (int k = 0; k < 16; ++k)
-        dep[k] = ((k & 1) ? 1u << ph.b[0] : 0u) | ((k & 2) ? 1u << ph.b[1] : 0u) | ((k & 4) ? 1u << ph.b[2] : 0u) |
-                 ((k & 8) ? 1u << ph.b[3] : 0u);
+      for (int i = 0; i < RB; ++i) pmask |= 1u << ph.b[i];
+      uint32_t dep[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        uint32_t dk = 0;
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+          if (k & (1 << i)) dk |= 1u << ph.b[i];
+        dep[k] = dk;
+      }
       for (uint32_t grp = threadIdx.x; grp < G; grp += THREADS) {
         const uint32_t gb = tile_expand(grp, pmask, 0);
-        longlong2 v[16];
+        longlong2 v[K];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = tile[gb | dep[k]];
+        for (int k = 0; k < K; ++k) v[k] = tile[gb | dep[k]];
         for (int k = ph.op_begin; k < ph.op_end; ++k) {
           const TileOp& op = g.ops[k];
           if ((base & op.ext_cmask) != op.ext_cmask) continue;
           const uint32_t lcm = op.lcmask;
           const uint32_t lout = lcm & ~pmask;
           if ((gb & lout) != lout) continue;
-          const uint32_t cr = ((lcm >> ph.b[0]) & 1u) | (((lcm >> ph.b[1]) & 1u) << 1) |
-                              (((lcm >> ph.b[2]) & 1u) << 2) | (((lcm >> ph.b[3]) & 1u) << 3);
+          uint32_t cr = 0;
+#pragma unroll
+          for (int i = 0; i < RB; ++i) cr |= ((lcm >> ph.b[i]) & 1u) << i;
           if (op.kind == TOP_SCALAR || !((pmask >> op.tb) & 1u)) {
             // diagonal op whose target is constant for the group (outside the
             // tile: a per-tile bit; in the tile but outside the phase: a group bit)
@@ -277,27 +304,29 @@ __global__ void __launch_bounds__(THREADS) k_tile_reg(double2* __restrict__ a, c
             const int code = one ? op.code1 : op.code0;
             if (code == U_ONE) continue;
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk)
+            for (int kk = 0; kk < K; ++kk)
               if ((kk & cr) == cr) v[kk] = EngQ60::mul(v[kk], code, op, one ? 3 : 0);
             continue;
           }
-          const int R = op.tb == ph.b[0] ? 0 : op.tb == ph.b[1] ? 1 : op.tb == ph.b[2] ? 2 : 3;
+          int R = RB - 1;
+#pragma unroll
+          for (int i = RB - 2; i >= 0; --i)
+            if (op.tb == ph.b[i]) R = i;
           switch (R) {
-            case 0: ph_op<0>(v, op, cr); break;
-            case 1: ph_op<1>(v, op, cr); break;
-            case 2: ph_op<2>(v, op, cr); break;
-            default: ph_op<3>(v, op, cr); break;
+            case 0: ph_op<RB, 0>(v, op, cr); break;
+            case 1: if (RB > 1) ph_op<RB, (RB > 1 ? 1 : 0)>(v, op, cr); break;
+            case 2: if (RB > 2) ph_op<RB, (RB > 2 ? 2 : 0)>(v, op, cr); break;
+            default: if (RB > 3) ph_op<RB, (RB > 3 ? 3 : 0)>(v, op, cr); break;
           }
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) tile[gb | dep[k]] = v[k];
+        for (int k = 0; k < K; ++k) tile[gb | dep[k]] = v[k];
       }
       __syncthreads();
     }
     for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = EngQ60::store(tile[j]);
   }
 }
-
 template <class E>
 static int launch_engine(qs_state* s, const TileArgs& g, size_t smem) {
   constexpr int THREADS = 256;
@@ -322,14 +351,22 @@ int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, in
   KTimer kt(s, QS_K_TILE, g.m, ngates, qmask, 0, (double)(1ull << g.n), flops, int_ops);
   if (fixed && g.nphases > 0) {
     constexpr int THREADS = 256;
-    static bool attr = false;
-    if (!attr) {
-      QS_CUDA(cudaFuncSetAttribute(k_tile_reg<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
     int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (220 * 1024) / (smem + 1024)));
     uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)152 * per_sm);
-    k_tile_reg<THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
+    static bool attr3 = false, attr4 = false;
+    if (g.reg_bits == 4) {
+      if (!attr4) {
+        QS_CUDA(cudaFuncSetAttribute(k_tile_reg<4, THREADS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr4 = true;
+      }
+      k_tile_reg<4, THREADS, 1><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
+    } else {
+      if (!attr3) {
+        QS_CUDA(cudaFuncSetAttribute(k_tile_reg<3, THREADS, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr3 = true;
+      }
+      k_tile_reg<3, THREADS, 3><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
+    }
     return launch_check("tile kernel (register phases)");
   }
   return fixed ? launch_engine<EngQ60>(s, g, smem) : launch_engine<EngF64>(s, g, smem);

@@ -53,6 +53,7 @@ struct TileArgs {
   int outpos[QS_MAX_QUBITS];  // their global positions (ascending)
   int nops;
   int nphases;       // > 0: run the register-phase kernel (Q60 engine, m >= 4)
+  int reg_bits;      // register bits per phase (3 or 4)
   TileOp ops[TILE_MAX_OPS];
   TilePhase phases[TILE_MAX_PHASES];
 };

@@ -71,26 +71,35 @@ def test_roundtrip_exact_for_large_values(fc):
             assert fc.fc_to_double(fc.fc_from_double(v)) == v
 
 
+def unitary_row(g):
+    """Real and imaginary parts of one row of a random 2x2 unitary, as Q60
+    integers (their absolute values sum to at most 2)."""
+    z = g.normal(size=2) + 1j * g.normal(size=2)
+    z /= np.linalg.norm(z)
+    return [int(round(v * (1 << 60))) for v in (z[0].real, -z[0].imag, z[1].real, -z[1].imag)]
+
+
 def test_limb_products_error_bound(fc):
     g = np.random.Generator(np.random.PCG64(4))
     for _ in range(3000):
-        u = [int(x) for x in g.integers(-(1 << 60), (1 << 60) + 1, 4, dtype=np.int64)]
-        a = [int(x) for x in g.integers(-int(1.5 * (1 << 60)), int(1.5 * (1 << 60)), 4, dtype=np.int64)]
+        u = unitary_row(g)
+        a = [int(x) for x in g.integers(-int(1.25 * (1 << 60)), int(1.25 * (1 << 60)), 4, dtype=np.int64)]
         exact = Fraction(sum(x * y for x, y in zip(u, a)), 1 << 60)
         ua = (ctypes.c_longlong * 4)(*u)
         aa = (ctypes.c_longlong * 4)(*a)
         got = fc.fc_dot4(ua, aa)
-        # four dropped low-limb products (< 2^62 each in 2^-120 units -> < 2^2 in Q60 units) + rounding
-        assert abs(got - exact) <= 4 * 4 + 1
+        # four dropped low-limb products (< 2^60 each in 2^-120 units -> < 1 in Q60 units) + rounding
+        assert abs(got - exact) <= 4 + 1
         got2 = fc.fc_dot2(u[0], a[0], u[1], a[1])
-        assert abs(got2 - Fraction(u[0] * a[0] + u[1] * a[1], 1 << 60)) <= 2 * 4 + 1
+        assert abs(got2 - Fraction(u[0] * a[0] + u[1] * a[1], 1 << 60)) <= 2 + 1
 
 
 def test_extreme_limbs_do_not_overflow(fc):
-    M = int(1.5 * (1 << 60))
-    for u in ([1 << 60] * 4, [-(1 << 60)] * 4):
-        for a in ([M] * 4, [-M] * 4, [M, -M, M, -M]):
+    M = int(1.25 * (1 << 60))
+    h = 1 << 59   # four entries of 1/2: the largest sum of absolute values a unitary row allows
+    for u in ([h] * 4, [-h] * 4, [h, -h, h, -h]):
+        for a in ([M] * 4, [-M] * 4, [M, -M, M, -M], [M - 1] * 4):
             ua = (ctypes.c_longlong * 4)(*u)
             aa = (ctypes.c_longlong * 4)(*a)
             exact = Fraction(sum(x * y for x, y in zip(u, a)), 1 << 60)
-            assert abs(fc.fc_dot4(ua, aa) - exact) <= 17
+            assert abs(fc.fc_dot4(ua, aa) - exact) <= 5

@@ -133,3 +133,18 @@ def test_full_size_fused_vs_plain_and_invariants(q):
     finally:
         q.qs_free(a)
         q.qs_plan_free(p)
+
+
+@pytest.mark.parametrize("bits", [3, 4])
+def test_register_phase_kernels(q, orc, bits):
+    """The register-phase tile kernels (runs of ops on 2^bits amplitudes per thread)
+    against the oracle on random circuits with controls and on the brickwork."""
+    q.qs_set_register_phases(bits)
+    try:
+        for n, g in ((13, w.random_circuit(13, 400, 3, two_qubit_prob=0.4)), (17, w.layered_u3_cz(17, 12, 1)),
+                     (16, w.random_circuit(16, 300, 8))):
+            psi, st = fused(q, n, g, arith=q.ARITH_FIXED)
+            assert st["n_tile_passes"] >= 1
+            assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
+    finally:
+        q.qs_set_register_phases(0)
