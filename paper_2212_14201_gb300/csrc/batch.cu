@@ -733,11 +733,14 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
 static int batch_enqueue(qs_batch* b) {
   const BatchArgs& a = b->args;
   QS_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), b->stream));
-  // external records: inside a captured graph they become timing event nodes
-  QS_CUDA(cudaEventRecordWithFlags(b->ev0, b->stream, cudaEventRecordExternal));
+  // while capturing, external records become timing event nodes of the graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  QS_CUDA(cudaStreamIsCapturing(b->stream, &cs));
+  const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  QS_CUDA(cudaEventRecordWithFlags(b->ev0, b->stream, flags));
   k_batch<<<b->grid, BT_THREADS, b->smem, b->stream>>>(a);
   QS_TRY(launch_check("batch kernel"));
-  QS_CUDA(cudaEventRecordWithFlags(b->ev1, b->stream, cudaEventRecordExternal));
+  QS_CUDA(cudaEventRecordWithFlags(b->ev1, b->stream, flags));
   return QS_OK;
 }
 
