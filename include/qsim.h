@@ -323,6 +323,13 @@ int qs_sample(const qs_state* s, uint64_t seed, uint64_t shots, uint64_t* out, i
 int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, const double* params, size_t np,
                     const qs_pauli* terms, size_t nterms, double* energy, double* grad);
 
+/* Process-wide choice of the backward sweep of qs_adjoint_grad under Q60
+ * arithmetic: on (default) runs it as shared-memory tile passes over psi and
+ * lambda together (the reversed, daggered program planned greedily); off runs one
+ * fused kernel per gate.  Same results up to rounding; the switch is for
+ * measurement. */
+int qs_set_adjoint_fused(int on);
+
 /* ---- batched variational evaluation (the hybrid quantum-classical loop of
  * Sections "Support hybrid quantum-classical algorithm" and "Variational
  * quantum circuit": many parameter sets evaluated per optimiser step) -------- */

@@ -84,6 +84,7 @@ SIGNATURES = {
     "qs_sample": (I32, [P, U64, U64, P, I32]),
     "qs_adjoint_grad": (I32, [P, P, SZ, P, SZ, P, SZ, ctypes.POINTER(DBL), P]),
     "qs_expect_z_all_noalloc": (I32, [P, I32, P, P]),
+    "qs_set_adjoint_fused": (I32, [I32]),
     "qs_mlp_create": (I32, [I32, I32, P, U64, PP]),
     "qs_mlp_free": (I32, [P]),
     "qs_mlp_num_weights": (I32, [P, ctypes.POINTER(SZ)]),
@@ -261,6 +262,10 @@ def qs_plan_create(n: int, gates, mode: int = PLAN_GREEDY, kmax: int = 5) -> int
     h = ctypes.c_void_p()
     _chk(lib().qs_plan_create(n, g.ctypes.data if len(g) else None, len(g), mode, kmax, ctypes.byref(h)))
     return h.value
+
+
+def qs_set_adjoint_fused(on: bool):
+    _chk(lib().qs_set_adjoint_fused(1 if on else 0))
 
 
 def qs_set_register_phases(bits: int):

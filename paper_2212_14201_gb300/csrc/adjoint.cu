@@ -16,6 +16,7 @@
 
 #include "fixed.h"
 #include "internal.h"
+#include "q60tile.cuh"
 
 namespace qs {
 
@@ -238,6 +239,208 @@ __global__ void k_slot_sums(const double* __restrict__ part, int nslots, int nbl
   }
 }
 
+// ---- fused backward sweep (Q60): tile passes over psi and lambda at once --------------
+// The backward sweep applies U_G^dag .. U_1^dag, so it is the forward sweep of the
+// reversed, daggered program; greedy tile passes over that list only reorder ops
+// that commute, and an op that commutes with U_k also commutes with U_k's
+// generator (same qubits, same diagonal structure), so every generator inner
+// product is taken on the same (psi, lambda) as in the gate-by-gate sweep.
+constexpr int ADJ_GRID_STRIDE = 608;  // partial-sum slots per gradient (>= CTAs of any pass)
+
+struct AdjPassArgs {
+  BPass ps;
+  const BOp* ops;   // ops of this pass (device), in execution order
+  const QC* mats;   // 4 entries per op (device)
+  double* part;     // [slot][ADJ_GRID_STRIDE]
+  int slot_base;
+};
+
+__global__ void __launch_bounds__(BT_THREADS) k_adj_pass(double2* __restrict__ psi, double2* __restrict__ lam,
+                                                         const AdjPassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BPass& ps = a.ps;
+  const int m = ps.m;
+  const int L = m - ps.nhigh;
+  const uint32_t TS = 1u << m;
+  const uint32_t H = 1u << ps.nhigh;
+  longlong2* tP = reinterpret_cast<longlong2*>(smem);
+  longlong2* tL = tP + TS;
+  uint64_t* offs = reinterpret_cast<uint64_t*>(tL + TS);
+  double* wacc = reinterpret_cast<double*>(offs + H);  // [warps][nslots]
+  for (uint32_t h = threadIdx.x; h < H; h += BT_THREADS) {
+    uint64_t o = 0;
+    for (int b = 0; b < ps.nhigh; ++b) o |= (uint64_t)((h >> b) & 1u) << ps.qhigh[b];
+    offs[h] = o;
+  }
+  for (int s = threadIdx.x; s < ps.nslots * (BT_THREADS / 32); s += BT_THREADS) wacc[s] = 0.0;
+  const uint32_t lowmask = (1u << L) - 1;
+  const uint64_t ntiles = 1ull << ps.nout;
+  for (uint64_t r = blockIdx.x; r < ntiles; r += gridDim.x) {
+    uint64_t base = 0;
+    for (int b = 0; b < ps.nout; ++b) base |= ((r >> b) & 1ull) << ps.outpos[b];
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+      const uint64_t x = base + offs[j >> L] + (j & lowmask);
+      const double2 u = psi[x], v = lam[x];
+      tP[j] = make_longlong2(q60_from_double(u.x), q60_from_double(u.y));
+      tL[j] = make_longlong2(q60_from_double(v.x), q60_from_double(v.y));
+    }
+    __syncthreads();
+    for (int k = ps.op_begin; k < ps.op_end; ++k) {
+      const BOp op = a.ops[k];
+      if ((base & op.ext) != op.ext) continue;
+      // each thread reads and then rewrites only its own pairs of this op, so the
+      // generator partial and the update need no barrier between them
+      if (op.slot >= 0) bt_warp_accumulate(bt_gen_partial(tP, tL, TS, op, base), wacc, ps.nslots, op.slot);
+      bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
+      bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
+      __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+      const uint64_t x = base + offs[j >> L] + (j & lowmask);
+      psi[x] = make_double2(q60_to_double(tP[j].x), q60_to_double(tP[j].y));
+      lam[x] = make_double2(q60_to_double(tL[j].x), q60_to_double(tL[j].y));
+    }
+  }
+  __syncthreads();
+  for (int k = ps.op_begin + threadIdx.x; k < ps.op_end; k += BT_THREADS) {
+    const BOp& op = a.ops[k];
+    if (op.slot >= 0)
+      a.part[(size_t)(a.slot_base + op.slot) * ADJ_GRID_STRIDE + blockIdx.x] =
+          bt_warp_total(wacc, ps.nslots, op.slot) * op.gsign;
+  }
+}
+
+static int gen_of(const qs_gate& g);
+
+// Backward sweep as tile passes; slot_param receives, per gradient slot in
+// execution order, the parameter it belongs to.
+static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_t ng, const double* params,
+                          double* part, std::vector<int>& slot_param) {
+  const int n = s->n;
+  std::vector<qs_gate> R(ng);
+  std::vector<int> tgt(ng);
+  std::vector<uint64_t> cms(ng);
+  for (size_t i = 0; i < ng; ++i) {
+    R[i] = gates[ng - 1 - i];
+    R[i].dagger = !R[i].dagger;
+    QS_TRY(gate_qubits(R[i], n, &tgt[i], &cms[i]));
+  }
+  const int m = std::min(n, BT_M);
+  const uint64_t low = (1ull << std::min(n, 3)) - 1;
+  std::vector<uint32_t> remaining(ng), pass, rest;
+  for (size_t i = 0; i < ng; ++i) remaining[i] = (uint32_t)i;
+  std::vector<BOp> ops;
+  std::vector<QC> mats;
+  std::vector<BPass> passes;
+  int slot_base = 0;
+  std::vector<int> slot_bases;
+  while (!remaining.empty()) {
+    const uint64_t Q = greedy_pass(R.data(), tgt, cms, remaining, m, low, BT_MAX_OPS, pass, rest);
+    BPass bp;
+    memset(&bp, 0, sizeof bp);
+    int local[64];
+    int mm = 0;
+    for (int b = 0; b < n; ++b) local[b] = ((Q >> b) & 1) ? mm++ : -1;
+    int L = 0;
+    while (L < n && ((Q >> L) & 1)) ++L;
+    bp.m = mm;
+    for (int b = L; b < n; ++b)
+      if ((Q >> b) & 1) bp.qhigh[bp.nhigh++] = b;
+    for (int b = 0; b < n; ++b)
+      if (!((Q >> b) & 1)) bp.outpos[bp.nout++] = b;
+    bp.op_begin = (int)ops.size();
+    int slot = 0;
+    for (uint32_t i : pass) {
+      const qs_gate& orig = gates[ng - 1 - i];
+      Mat2 mt;
+      QS_TRY(gate_matrix(R[i], params, &mt));
+      Op1 o1 = classify(tgt[i], cms[i], mt);
+      BOp op;
+      memset(&op, 0, sizeof op);
+      op.gen = orig.param_idx >= 0 ? (int8_t)gen_of(orig) : (int8_t)BG_NONE;
+      if (o1.cls == OP_IDENTITY && op.gen == BG_NONE) continue;
+      op.kb = op.kf = (int8_t)o1.cls;
+      op.c0b = (int8_t)o1.code0;
+      op.c1b = (int8_t)o1.code1;
+      uint32_t lcm = 0;
+      uint64_t ext = 0;
+      for (int b = 0; b < n; ++b)
+        if ((cms[i] >> b) & 1) {
+          if (local[b] >= 0) lcm |= 1u << local[b];
+          else ext |= 1ull << b;
+        }
+      op.lcm = lcm;
+      op.ext = ext;
+      if (local[tgt[i]] >= 0) {
+        op.tb = (int8_t)local[tgt[i]];
+        if (o1.cls == OP_IDENTITY) op.kb = op.kf = OP_PHASE1;  // identity matrix, kept for its gradient slot
+      } else {
+        op.tb = (int8_t)tgt[i];
+        op.kb = op.kf = BK_SCALAR;
+      }
+      op.gsign = orig.dagger ? -1.0 : 1.0;
+      op.slot = -1;
+      op.param = orig.param_idx;
+      if (op.gen != BG_NONE) {
+        op.slot = (int16_t)slot++;
+        slot_param.push_back(orig.param_idx);
+      }
+      ops.push_back(op);
+      for (int e = 0; e < 4; ++e) mats.push_back(qc_make(mt.m[e].re, mt.m[e].im));
+    }
+    bp.op_end = (int)ops.size();
+    bp.nslots = slot;
+    passes.push_back(bp);
+    slot_bases.push_back(slot_base);
+    slot_base += slot;
+    remaining.swap(rest);
+  }
+  BOp* d_ops = nullptr;
+  QC* d_mats = nullptr;
+  QS_CUDA(cudaMallocAsync((void**)&d_ops, sizeof(BOp) * std::max<size_t>(1, ops.size()), s->stream));
+  cudaError_t e = cudaMallocAsync((void**)&d_mats, sizeof(QC) * std::max<size_t>(4, mats.size()), s->stream);
+  if (e == cudaSuccess && !ops.empty())
+    e = cudaMemcpyAsync(d_ops, ops.data(), sizeof(BOp) * ops.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && !mats.empty())
+    e = cudaMemcpyAsync(d_mats, mats.data(), sizeof(QC) * mats.size(), cudaMemcpyHostToDevice, s->stream);
+  int rc = e == cudaSuccess ? QS_OK : cuda_fail(e, "adjoint op tables");
+  static bool attr = false;
+  if (rc == QS_OK && !attr) {
+    e = cudaFuncSetAttribute(k_adj_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    if (e != cudaSuccess) rc = cuda_fail(e, "adjoint pass attribute");
+    attr = true;
+  }
+  for (size_t p = 0; rc == QS_OK && p < passes.size(); ++p) {
+    AdjPassArgs a;
+    a.ps = passes[p];
+    a.ops = d_ops;
+    a.mats = d_mats;
+    a.part = part;
+    a.slot_base = slot_bases[p];
+    const uint32_t TS = 1u << a.ps.m;
+    const size_t smem = 2 * sizeof(longlong2) * TS + sizeof(uint64_t) * ((size_t)1 << a.ps.nhigh) +
+                        sizeof(double) * ((size_t)a.ps.nslots * (BT_THREADS / 32) + 8);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (220 * 1024) / (smem + 1024)));
+    const uint64_t grid = std::min<uint64_t>(1ull << a.ps.nout, (uint64_t)std::min(ADJ_GRID_STRIDE, 152 * per_sm));
+    {
+      KTimer kt(s, QS_K_ADJOINT, a.ps.m, a.ps.op_end - a.ps.op_begin, 0, 0, 2.0 * (double)(1ull << n), 0.0);
+      k_adj_pass<<<(unsigned)grid, BT_THREADS, smem, s->stream>>>(s->amps, lam, a);
+    }
+    rc = launch_check("adjoint pass");
+  }
+  cudaFreeAsync(d_ops, s->stream);
+  cudaFreeAsync(d_mats, s->stream);
+  return rc;
+}
+
+static bool g_adj_fused = true;
+
+extern "C" int qs_set_adjoint_fused(int on) {
+  g_adj_fused = on != 0;
+  return QS_OK;
+}
+
 static int gen_of(const qs_gate& g) {
   switch (g.type) {
     case QS_RX: return GEN_X;
@@ -368,7 +571,12 @@ extern "C" int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, con
   // backward
   std::vector<int> slot_param;
   size_t slot = 0;
-  for (size_t kk = ng; rc == QS_OK && kk-- > 0;) {
+  const bool fused = fixed && g_adj_fused;
+  if (rc == QS_OK && fused) {
+    e = cudaMemsetAsync(part, 0, sizeof(double) * nblocks * nslots, s->stream);
+    rc = e == cudaSuccess ? backward_fused(s, lam, gates, ng, params, part, slot_param) : cuda_fail(e, "memset");
+  }
+  for (size_t kk = fused ? 0 : ng; rc == QS_OK && kk-- > 0;) {
     const qs_gate& g = gates[kk];
     qs_gate inv = g;
     inv.dagger = !g.dagger;

@@ -136,6 +136,26 @@ QS_HD int64_t qacc_result(const QAcc& acc) {
   return acc.hi + ((acc.mid + (1ll << 29)) >> 30);
 }
 
+// Accumulator that keeps the low x low limb products too (exact up to the final
+// rounding, no bias): for sums that are later added up over a whole state
+// vector, such as inner products, where a dropped non-negative term per product
+// would accumulate.
+struct QAccF {
+  int64_t hi, mid;
+  uint64_t lo;
+};
+
+QS_HD void qaccf_add(QAccF& acc, QL u, QL a) {
+  acc.hi = madw(u.h, a.h, acc.hi);
+  acc.mid = madw(u.h, a.l, acc.mid);
+  acc.mid = madw(u.l, a.h, acc.mid);
+  acc.lo += (uint64_t)(uint32_t)u.l * (uint64_t)(uint32_t)a.l;  // < 2^60 per product
+}
+
+QS_HD int64_t qaccf_result(const QAccF& acc) {
+  return acc.hi + ((acc.mid + (int64_t)(acc.lo >> 30) + (1ll << 29)) >> 30);
+}
+
 // A Q60 complex number as limbs, plus its negated imaginary part (so that
 // re = ur*ar - ui*ai needs only additions).
 struct QC {

@@ -1,0 +1,222 @@
+// Shared Q60 tile machinery of the batched and the single-state adjoint passes:
+// op descriptors in global memory, tile ops on int64 (Q60) amplitude pairs, and the
+// generator inner product Im <lambda| G |psi> over a tile.
+#pragma once
+
+#include "fixed.h"
+#include "internal.h"
+
+namespace qs {
+
+constexpr int BT_THREADS = 256;
+constexpr int BT_M = 11;          // tile qubits: psi and lambda tiles of 2^11 x 16 B
+constexpr int BT_MAX_OPS = 128;   // ops (and gradient slots) per pass: keeps 3 CTAs per SM
+constexpr int BT_MAX_N = 24;
+constexpr int BT_OFFS = 1 << (BT_M - 3);  // high-bit offset table: tiles hold qubits 0..2 (or all of n < 3)
+
+enum : int8_t { BK_SCALAR = 9 };
+enum : int8_t { BG_NONE = 0, BG_X = 1, BG_Y = 2, BG_Z = 3, BG_P = 4 };
+
+struct BPass {
+  int m, nhigh, nout, op_begin, op_end, nslots;
+  int qhigh[16];
+  int outpos[32];
+};
+
+struct BOp {
+  uint64_t ext;     // controls outside the tile
+  uint32_t lcm;     // controls inside the tile (local bits)
+  int gate;         // global gate index (matrix tables)
+  int param;        // global parameter index, or -1
+  double gsign;     // generator sign (-1 for a dagger record)
+  int16_t slot;     // gradient slot within the pass, or -1
+  int8_t kf, kb;    // op class forward / adjoint
+  int8_t tb;        // local target bit (global target bit for SCALAR)
+  int8_t gen;
+  int8_t c0f, c1f, c0b, c1b;
+};
+
+
+__device__ __forceinline__ longlong2 bt_unit(longlong2 a, int code) {
+  switch (code) {
+    case U_ONE: return a;
+    case U_I: return make_longlong2(-a.y, a.x);
+    case U_MINUS_ONE: return make_longlong2(-a.x, -a.y);
+    default: return make_longlong2(a.y, -a.x);
+  }
+}
+
+__device__ __forceinline__ longlong2 bt_mul(longlong2 a, int code, const QC& u) {
+  if (code != U_GENERAL) return bt_unit(a, code);
+  const QL ar = q60_split(a.x), ai = q60_split(a.y);
+  QAcc re{0, 0}, im{0, 0};
+  qacc_add(re, u.re, ar);
+  qacc_add(re, u.nim, ai);
+  qacc_add(im, u.re, ai);
+  qacc_add(im, u.im, ar);
+  return make_longlong2(qacc_result(re), qacc_result(im));
+}
+
+__device__ __forceinline__ uint32_t bt_expand(uint32_t i, uint32_t fixed, uint32_t set) {
+  while (fixed) {
+    int f = __ffs(fixed) - 1;
+    fixed &= fixed - 1;
+    i = ((i >> f) << (f + 1)) | (i & ((1u << f) - 1));
+  }
+  return i | set;
+}
+
+static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int kind, int c0, int c1, const QC* U,
+                         uint64_t base) {
+  const uint32_t lcm = op.lcm;
+  if (kind == BK_SCALAR) {
+    const bool one = (base >> op.tb) & 1ull;
+    const int code = one ? c1 : c0;
+    if (code == U_ONE) return;
+    const QC& u = U[one ? 3 : 0];
+    const uint32_t cnt = TS >> __popc(lcm);
+    for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+      uint32_t j = bt_expand(i, lcm, lcm);
+      tile[j] = bt_mul(tile[j], code, u);
+    }
+    return;
+  }
+  const uint32_t tb = 1u << op.tb;
+  const uint32_t fixed = lcm | tb;
+  const uint32_t cnt = TS >> __popc(fixed);
+  for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+    const uint32_t j0 = bt_expand(i, fixed, lcm), j1 = j0 | tb;
+    if (kind == OP_PHASE1) {
+      tile[j1] = bt_mul(tile[j1], c1, U[3]);
+      continue;
+    }
+    longlong2 a0 = tile[j0], a1 = tile[j1], b0, b1;
+    if (kind == OP_DIAG) {
+      b0 = bt_mul(a0, c0, U[0]);
+      b1 = bt_mul(a1, c1, U[3]);
+    } else if (kind == OP_ANTI) {
+      b0 = bt_mul(a1, c0, U[1]);
+      b1 = bt_mul(a0, c1, U[2]);
+    } else {
+      const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+      int64_t out[4];
+#pragma unroll
+      for (int row = 0; row < 2; ++row) {
+        const QC& u0 = U[2 * row];
+        const QC& u1 = U[2 * row + 1];
+        QAcc re{0, 0}, im{0, 0};
+        qacc_add(re, u0.re, r0);
+        qacc_add(re, u1.re, r1);
+        qacc_add(im, u0.re, i0);
+        qacc_add(im, u1.re, i1);
+        if (kind == OP_GENERAL) {
+          qacc_add(re, u0.nim, i0);
+          qacc_add(re, u1.nim, i1);
+          qacc_add(im, u0.im, r0);
+          qacc_add(im, u1.im, r1);
+        }
+        out[2 * row] = qacc_result(re);
+        out[2 * row + 1] = qacc_result(im);
+      }
+      b0 = make_longlong2(out[0], out[1]);
+      b1 = make_longlong2(out[2], out[3]);
+    }
+    tile[j0] = b0;
+    tile[j1] = b1;
+  }
+}
+
+// sum_k s_k * l_k * p_k for four signed products of Q60 values, as a double.
+// (all four limb products kept: these terms are summed over the whole state)
+__device__ __forceinline__ double bt_dot4(const int64_t* l, const int64_t* p, const int* sg) {
+  QAccF acc{0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (sg[k] == 0) continue;
+    qaccf_add(acc, q60_split(sg[k] > 0 ? l[k] : -l[k]), q60_split(p[k]));
+  }
+  return q60_to_double(qaccf_result(acc));
+}
+
+// This thread's share of Im <lambda| G |psi> over the op's pairs in the tile.
+static __device__ double bt_gen_partial(const longlong2* P, const longlong2* Lt, uint32_t TS, const BOp& op, uint64_t base) {
+  if (op.kf == BK_SCALAR) {
+    // diagonal generator on a qubit outside the tile: per amplitude,
+    // Z -> (-1)^bit Im(conj(l) p), P -> -2 [bit] Im(conj(l) p)
+    const bool one = (base >> op.tb) & 1ull;
+    if (op.gen == BG_P && !one) return 0.0;
+    const double w = op.gen == BG_P ? -2.0 : (one ? -1.0 : 1.0);
+    const uint32_t cnt = TS >> __popc(op.lcm);
+    double acc = 0.0;
+    for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+      const uint32_t j = bt_expand(i, op.lcm, op.lcm);
+      const int64_t l[4] = {Lt[j].x, Lt[j].y, 0, 0}, p[4] = {P[j].y, P[j].x, 0, 0};
+      const int sg[4] = {1, -1, 0, 0};
+      acc += w * bt_dot4(l, p, sg);
+    }
+    return acc;
+  }
+  const uint32_t tb = 1u << op.tb;
+  const uint32_t fixed = op.lcm | tb;
+  const uint32_t cnt = TS >> __popc(fixed);
+  double acc = 0.0;
+  for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+    const uint32_t j0 = bt_expand(i, fixed, op.lcm), j1 = j0 | tb;
+    const longlong2 p0 = P[j0], p1 = P[j1], l0 = Lt[j0], l1 = Lt[j1];
+    int64_t l[4], p[4];
+    int sg[4];
+    switch (op.gen) {
+      case BG_X:  // l0x p1y - l0y p1x + l1x p0y - l1y p0x
+        l[0] = l0.x; p[0] = p1.y; sg[0] = 1; l[1] = l0.y; p[1] = p1.x; sg[1] = -1;
+        l[2] = l1.x; p[2] = p0.y; sg[2] = 1; l[3] = l1.y; p[3] = p0.x; sg[3] = -1;
+        break;
+      case BG_Y:  // -l0x p1x - l0y p1y + l1x p0x + l1y p0y
+        l[0] = l0.x; p[0] = p1.x; sg[0] = -1; l[1] = l0.y; p[1] = p1.y; sg[1] = -1;
+        l[2] = l1.x; p[2] = p0.x; sg[2] = 1; l[3] = l1.y; p[3] = p0.y; sg[3] = 1;
+        break;
+      case BG_Z:  // l0x p0y - l0y p0x - l1x p1y + l1y p1x
+        l[0] = l0.x; p[0] = p0.y; sg[0] = 1; l[1] = l0.y; p[1] = p0.x; sg[1] = -1;
+        l[2] = l1.x; p[2] = p1.y; sg[2] = -1; l[3] = l1.y; p[3] = p1.x; sg[3] = 1;
+        break;
+      default:    // P: -2 (l1x p1y - l1y p1x)
+        l[0] = l1.x; p[0] = p1.y; sg[0] = -1; l[1] = l1.y; p[1] = p1.x; sg[1] = 1;
+        l[2] = 0; p[2] = 0; sg[2] = 0; l[3] = 0; p[3] = 0; sg[3] = 0;
+        break;
+    }
+    double v = bt_dot4(l, p, sg);
+    acc += op.gen == BG_P ? 2.0 * v : v;
+  }
+  return acc;
+}
+
+// Adds this thread's partial to its warp's accumulator of `slot` without a CTA
+// barrier: the warp reduces by shuffles and lane 0 owns the warp's row, so the
+// order of additions is fixed.  wacc holds (BT_THREADS / 32) rows of nslots.
+__device__ __forceinline__ void bt_warp_accumulate(double v, double* wacc, int nslots, int slot) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wacc[(threadIdx.x >> 5) * nslots + slot] += v;
+}
+
+// After a barrier: the CTA's total of `slot`, warps added in warp order.
+__device__ __forceinline__ double bt_warp_total(const double* wacc, int nslots, int slot) {
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < BT_THREADS / 32; ++w) t += wacc[w * nslots + slot];
+  return t;
+}
+
+static __device__ double bt_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int i = 0; i < BT_THREADS / 32; ++i) r += red[i];
+  return r;
+}
+
+}  // namespace qs

@@ -12,6 +12,11 @@ long long fc_dot2(long long u0, long long a0, long long u1, long long a1) {
   qs::qacc_add(acc, qs::q60_split(u1), qs::q60_split(a1));
   return (long long)qs::qacc_result(acc);
 }
+long long fc_dot4_full(const long long* u, const long long* a) {
+  qs::QAccF acc{0, 0, 0};
+  for (int i = 0; i < 4; ++i) qs::qaccf_add(acc, qs::q60_split(u[i]), qs::q60_split(a[i]));
+  return (long long)qs::qaccf_result(acc);
+}
 long long fc_dot4(const long long* u, const long long* a) {
   qs::QAcc acc{0, 0};
   for (int i = 0; i < 4; ++i) qs::qacc_add(acc, qs::q60_split(u[i]), qs::q60_split(a[i]));

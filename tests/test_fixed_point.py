@@ -29,6 +29,8 @@ def fc():
     lib.fc_dot2.argtypes = [ctypes.c_longlong] * 4
     lib.fc_dot4.restype = ctypes.c_longlong
     lib.fc_dot4.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.fc_dot4_full.restype = ctypes.c_longlong
+    lib.fc_dot4_full.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -92,6 +94,22 @@ def test_limb_products_error_bound(fc):
         assert abs(got - exact) <= 4 + 1
         got2 = fc.fc_dot2(u[0], a[0], u[1], a[1])
         assert abs(got2 - Fraction(u[0] * a[0] + u[1] * a[1], 1 << 60)) <= 2 + 1
+
+
+def test_full_limb_products_are_correctly_rounded(fc):
+    """The inner-product accumulator keeps all four limb products: its result is
+    the exact sum rounded to the nearest multiple of 2^-60 (ties upward), with no
+    bias to accumulate over 2^n terms."""
+    g = np.random.Generator(np.random.PCG64(5))
+    errs = []
+    for _ in range(3000):
+        u = [int(x) for x in g.integers(-(1 << 59), 1 << 59, 4, dtype=np.int64)]
+        a = [int(x) for x in g.integers(-int(1.25 * (1 << 60)), int(1.25 * (1 << 60)), 4, dtype=np.int64)]
+        exact = Fraction(sum(x * y for x, y in zip(u, a)), 1 << 60)
+        got = fc.fc_dot4_full((ctypes.c_longlong * 4)(*u), (ctypes.c_longlong * 4)(*a))
+        assert abs(got - exact) <= Fraction(1, 2)
+        errs.append(float(got - exact))
+    assert abs(np.mean(errs)) < 0.05
 
 
 def test_extreme_limbs_do_not_overflow(fc):

@@ -147,3 +147,18 @@ def test_full_size_adjoint_invariants(q):
         assert abs(grad[k] - shift) <= 1e-9 * max(1.0, abs(shift))
     finally:
         q.qs_free(h)
+
+
+@pytest.mark.parametrize("n,layers", [(9, 3), (13, 4)])
+def test_per_gate_backward_path(q, orc, n, layers):
+    """The gate-by-gate backward sweep (qs_set_adjoint_fused(0)) against the oracle."""
+    g, npar = w.hea_ansatz(n, layers)
+    th = w.uniform_angles(npar, 40 + n)
+    H = w.tfim(n, 0.7)
+    q.qs_set_adjoint_fused(False)
+    try:
+        e, grad = gpu_grad(q, n, g, th, H)
+    finally:
+        q.qs_set_adjoint_fused(True)
+    e0, g0 = orc.adjoint_grad(n, g, th, H)
+    assert abs(e - e0) < 1e-12 and rel_close(grad, g0)
