@@ -352,16 +352,29 @@ int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate* gates, co
 
 /* Evaluate every set for params (param_offsets[nsets] values): energies[s] and
  * grads (same layout as params), each as qs_adjoint_grad defines them, in ONE
- * persistent kernel launch (CTAs take whole sets from a device work counter,
- * largest first; no CTA waits for another).  on_device == 0: host arrays; the
+ * persistent kernel launch in thread-block clusters: each cluster takes work
+ * items from a device counter, most expensive first; an item is one set with at
+ * least as many 2^11-amplitude tiles per pass as the cluster has CTAs (the CTAs
+ * share its tiles, with cluster barriers between passes) or up to one small set
+ * per CTA.  No CTA waits on a CTA of another cluster.  Results are
+ * deterministic for a given batch (fixed summation orders).  on_device == 0: host arrays; the
  * copy-in, the launch and the copy-out are a CUDA graph captured on the first
  * such call and replayed after.  on_device != 0: device arrays, no graph.
  * Synchronous. */
 int qs_batch_run(qs_batch* b, const double* params, double* energies, double* grads, int on_device);
 
-/* Device time (ms) of the persistent kernel in the last run; launch shape. */
+/* Device time (ms) of the persistent kernel in the last run; launch shape
+ * (grid in CTAs); CTAs per cluster. */
 int qs_batch_last_ms(const qs_batch* b, double* ms);
 int qs_batch_info(const qs_batch* b, int* grid, int* threads, size_t* smem_bytes);
+int qs_batch_cluster(const qs_batch* b, int* ctas);
+
+/* Cluster size of batches created after the call: 1, 2, 4 or 8 CTAs, or 0
+ * (default) to choose per batch the size whose longest-processing-time schedule
+ * of the work items over the resident clusters has the shortest estimated
+ * makespan (set cost ~ 2^n x gates).  Not thread-safe against a concurrent
+ * qs_batch_create.  Errors: INVALID_ARG. */
+int qs_set_batch_cluster(int ctas);
 int qs_batch_free(qs_batch* b);
 
 /* ---- instrumentation ---------------------------------------------------------------

@@ -99,6 +99,8 @@ SIGNATURES = {
     "qs_batch_run": (I32, [P, P, P, P, I32]),
     "qs_batch_last_ms": (I32, [P, ctypes.POINTER(DBL)]),
     "qs_batch_info": (I32, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SZ)]),
+    "qs_batch_cluster": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
+    "qs_set_batch_cluster": (I32, [I32]),
     "qs_batch_free": (I32, [P]),
     "qs_timing_enable": (I32, [P, I32]),
     "qs_timing_fetch": (I32, [P, ctypes.POINTER(TimingRecord), SZ, ctypes.POINTER(SZ)]),
@@ -483,7 +485,19 @@ def qs_batch_last_ms(b: int) -> float:
 def qs_batch_info(b: int) -> dict:
     g, t, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
     _chk(lib().qs_batch_info(b, ctypes.byref(g), ctypes.byref(t), ctypes.byref(s)))
-    return {"grid": g.value, "threads": t.value, "smem_bytes": s.value}
+    c = ctypes.c_int()
+    _chk(lib().qs_batch_cluster(b, ctypes.byref(c)))
+    return {"grid": g.value, "threads": t.value, "smem_bytes": s.value, "cluster": c.value}
+
+
+def qs_batch_cluster(b: int) -> int:
+    c = ctypes.c_int()
+    _chk(lib().qs_batch_cluster(b, ctypes.byref(c)))
+    return c.value
+
+
+def qs_set_batch_cluster(ctas: int):
+    _chk(lib().qs_set_batch_cluster(int(ctas)))
 
 
 def qs_batch_free(b: int):

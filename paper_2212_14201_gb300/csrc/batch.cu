@@ -4,9 +4,12 @@
 // quantum-classical algorithm" and "Variational quantum circuit"; the batching
 // itself is this library's design, not the paper's).
 //
-// Each CTA repeatedly takes the next set from a device work counter (sets
-// pre-sorted by decreasing size) and evaluates it alone, so no CTA ever waits for
-// another:
+// The kernel runs in clusters of c CTAs (c = 1, 2, 4 or 8, chosen per batch).
+// Each cluster repeatedly takes the next work item from a device counter (items
+// pre-sorted by decreasing cost): one large set (at least c tiles of 2^11
+// amplitudes per pass), whose tiles the c CTAs share with hardware cluster
+// barriers between passes, or up to c small sets, one per CTA.  No CTA waits on
+// a CTA outside its own cluster.  Per set:
 //   1. gate matrices of the set from its parameters (forward and adjoint);
 //   2. forward sweep psi = U_G ... U_1 |0> as greedy tile passes (<= 11 tile
 //      qubits, Q60 arithmetic in shared memory);
@@ -22,9 +25,23 @@
 #include <new>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "q60tile.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace qs {
+
+constexpr int BT_CLUSTER = 8;  // largest cluster (portable size); the launch uses 1, 2, 4 or 8
+static_assert(BT_CLUSTER <= BT_THREADS / 32, "cluster rows must fit the warp-row accumulator");
+static_assert(BT_MAX_OPS <= BT_THREADS, "one thread per gradient slot");
+
+struct BItem {
+  int cluster;               // 1: sets[0] on the whole cluster; 0: sets[r] on CTA r
+  int nsets;
+  int sets[BT_CLUSTER];
+};
 
 
 struct BSet {
@@ -51,8 +68,9 @@ struct BTerm {
 
 struct BatchArgs {
   const BSet* sets;
-  const int* order;
-  int nsets;
+  const BItem* items;
+  int nitems;
+  int csize;   // CTAs per cluster
   const BPass* passes;
   const BOp* ops;
   const BGate* gates;
@@ -115,9 +133,23 @@ __device__ void bt_gate_matrix(const BGate& g, const double* params, bool flip, 
 }
 
 
+// Cluster barrier that also publishes this CTA's global writes (psi, lambda,
+// gradients) to the other CTAs of the cluster.  A hardware barrier: every CTA of
+// the cluster is resident for the whole launch, and every CTA reaches the same
+// sequence of these barriers (work items are taken per cluster, not per CTA).
+__device__ __forceinline__ void bt_cluster_sync() {
+  __threadfence();
+  cg::this_cluster().sync();
+}
+
+// One pass over the tiles r = rank, rank + nr, ... of the set's state (nr CTAs
+// of a cluster share the set; nr = 1: this CTA alone).  Forward: U on psi.
+// Backward: for every op in reverse, the generator term then U^dag on psi and
+// lambda; gradient contributions are added in backward op order, per slot the
+// warps of a CTA in warp order, then the CTAs in rank order.
 __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, double2* lam, const QC* matf,
                             const QC* matb, bool backward, longlong2* tP, longlong2* tL, uint64_t* offs, double* acc,
-                            double* red) {
+                            int rank, int nr) {
   const int m = ps.m;
   const int L = m - ps.nhigh;
   const uint32_t TS = 1u << m;
@@ -130,7 +162,7 @@ __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, d
     offs[h] = o;
   }
   for (int s = threadIdx.x; s < ps.nslots * (BT_THREADS / 32); s += BT_THREADS) acc[s] = 0.0;
-  for (uint64_t r = 0; r < ntiles; ++r) {
+  for (uint64_t r = rank; r < ntiles; r += nr) {
     uint64_t base = 0;
     for (int b = 0; b < ps.nout; ++b) base |= ((r >> b) & 1ull) << ps.outpos[b];
     __syncthreads();
@@ -169,82 +201,137 @@ __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, d
     }
   }
   __syncthreads();
-  if (backward && threadIdx.x == 0) {
-    // gradient contributions in backward gate order
+  if (nr == 1) {
+    if (backward && threadIdx.x == 0) {
+      for (int k = ps.op_end - 1; k >= ps.op_begin; --k) {
+        const BOp& op = d.ops[k];
+        if (op.slot >= 0) d.grads[op.param] += bt_warp_total(acc, ps.nslots, op.slot) * op.gsign;
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  if (!backward) {
+    bt_cluster_sync();  // the next pass reads tiles other CTAs wrote
+    return;
+  }
+  // per-CTA slot totals -> rows [rank][slot] of rank 0's accumulator (distributed
+  // shared memory), then rank 0 adds them in rank order
+  const double v = threadIdx.x < ps.nslots ? bt_warp_total(acc, ps.nslots, threadIdx.x) : 0.0;
+  bt_cluster_sync();
+  if (threadIdx.x < ps.nslots) cg::this_cluster().map_shared_rank(acc, 0)[rank * ps.nslots + threadIdx.x] = v;
+  bt_cluster_sync();
+  if (rank == 0 && threadIdx.x == 0) {
     for (int k = ps.op_end - 1; k >= ps.op_begin; --k) {
       const BOp& op = d.ops[k];
-      if (op.slot >= 0) d.grads[op.param] += bt_warp_total(acc, ps.nslots, op.slot) * op.gsign;
+      if (op.slot < 0) continue;
+      double t = 0.0;
+      for (int q = 0; q < nr; ++q) t += acc[q * ps.nslots + op.slot];
+      d.grads[op.param] += t * op.gsign;
     }
   }
   __syncthreads();
 }
 
+// Energy and gradient of one set, by CTA `rank` of `nr` cooperating CTAs.
+__device__ void bt_eval_set(const BatchArgs& d, int set_id, int rank, int nr, longlong2* tP, longlong2* tL,
+                            uint64_t* offs, double* acc, double* red, double* epart) {
+  const BSet st = d.sets[set_id];
+  const uint64_t N = 1ull << st.n;
+  double2* psi = d.psi + st.amp_off;
+  double2* lam = d.lam + st.amp_off;
+  QC* matf = d.matf + 4 * (size_t)st.gate_begin;
+  QC* matb = d.matb + 4 * (size_t)st.gate_begin;
+  const int t0 = rank * BT_THREADS + threadIdx.x, ts = nr * BT_THREADS;
+  // 1. matrices (indices of ops are global gate indices; shift back by gate_begin)
+  for (int g = t0; g < st.ngates; g += ts) {
+    double2 m[4];
+    const BGate gt = d.gates[st.gate_begin + g];
+    bt_gate_matrix(gt, d.params, false, m);
+    for (int e = 0; e < 4; ++e) matf[4 * g + e] = qc_make(m[e].x, m[e].y);
+    bt_gate_matrix(gt, d.params, true, m);
+    for (int e = 0; e < 4; ++e) matb[4 * g + e] = qc_make(m[e].x, m[e].y);
+  }
+  for (int j = t0; j < st.nparams; j += ts) d.grads[st.param_begin + j] = 0.0;
+  // 2. psi = |0>, forward passes
+  for (uint64_t x = t0; x < N; x += ts) psi[x] = make_double2(x == 0 ? 1.0 : 0.0, 0.0);
+  if (nr == 1) __syncthreads();
+  else bt_cluster_sync();
+  for (int p = st.pass_begin; p < st.pass_begin + st.npasses; ++p)
+    bt_run_pass(d, d.passes[p], psi, lam, matf, matb, false, tP, tL, offs, acc, rank, nr);
+  // 3. lambda = (H/S) psi, energy
+  double e = 0.0;
+  for (uint64_t y = t0; y < N; y += ts) {
+    double ore = 0.0, oim = 0.0;
+    for (int gi = st.group_begin; gi < st.group_begin + st.ngroups; ++gi) {
+      const BGroup grp = d.groups[gi];
+      const uint64_t x = y ^ grp.xm;
+      double dre = 0.0, dim = 0.0;
+      for (int k = grp.tbegin; k < grp.tend; ++k) {
+        const BTerm t = d.terms[k];
+        const double v = (__popcll(x & t.zm) & 1) ? -t.c : t.c;
+        if (t.imag) dim += v;
+        else dre += v;
+      }
+      const double2 pv = psi[x];
+      ore += dre * pv.x - dim * pv.y;
+      oim += dre * pv.y + dim * pv.x;
+    }
+    lam[y] = make_double2(ore, oim);
+    const double2 py = psi[y];
+    e += py.x * ore + py.y * oim;
+  }
+  const double E = bt_block_sum(e, red);
+  if (nr == 1) {
+    if (threadIdx.x == 0) d.energies[set_id] = E * st.S;
+    __syncthreads();
+  } else {
+    if (threadIdx.x == 0) cg::this_cluster().map_shared_rank(epart, 0)[rank] = E;
+    bt_cluster_sync();  // also publishes lambda
+    if (rank == 0 && threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < nr; ++q) t += epart[q];
+      d.energies[set_id] = t * st.S;
+    }
+  }
+  // 4. backward
+  for (int p = st.pass_begin + st.npasses - 1; p >= st.pass_begin; --p)
+    bt_run_pass(d, d.passes[p], psi, lam, matf, matb, true, tP, tL, offs, acc, rank, nr);
+  if (rank == 0 && threadIdx.x == 0)
+    for (int j = 0; j < st.nparams; ++j) d.grads[st.param_begin + j] *= st.S;
+}
+
+// The persistent kernel, launched in clusters of d.csize CTAs.  Rank 0 of a
+// cluster takes the next work item from the device counter (items pre-sorted by
+// decreasing estimated cost); the item is either one large set shared by the whole
+// cluster or up to d.csize small sets, one per CTA.
 __global__ void __launch_bounds__(BT_THREADS) k_batch(const BatchArgs d) {
   extern __shared__ __align__(16) unsigned char smem[];
   longlong2* tP = reinterpret_cast<longlong2*>(smem);
   longlong2* tL = tP + (1 << BT_M);
   uint64_t* offs = reinterpret_cast<uint64_t*>(tL + (1 << BT_M));
-  double* acc = reinterpret_cast<double*>(offs + BT_OFFS);  // [warps][slots]
+  double* acc = reinterpret_cast<double*>(offs + BT_OFFS);  // [warps][slots]; [rank][slot] across the cluster
   double* red = acc + BT_MAX_OPS * (BT_THREADS / 32);
-  __shared__ int s_set;
+  __shared__ int s_item;
+  __shared__ double s_epart[BT_CLUSTER];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_set = atomicAdd(d.counter, 1);
-    __syncthreads();
-    const int si = s_set;
-    if (si >= d.nsets) break;
-    const int set_id = d.order[si];
-    const BSet st = d.sets[set_id];
-    const uint64_t N = 1ull << st.n;
-    double2* psi = d.psi + st.amp_off;
-    double2* lam = d.lam + st.amp_off;
-    QC* matf = d.matf + 4 * (size_t)st.gate_begin;
-    QC* matb = d.matb + 4 * (size_t)st.gate_begin;
-    // 1. matrices (indices of ops are global gate indices; shift back by gate_begin)
-    for (int g = threadIdx.x; g < st.ngates; g += BT_THREADS) {
-      double2 m[4];
-      const BGate gt = d.gates[st.gate_begin + g];
-      bt_gate_matrix(gt, d.params, false, m);
-      for (int e = 0; e < 4; ++e) matf[4 * g + e] = qc_make(m[e].x, m[e].y);
-      bt_gate_matrix(gt, d.params, true, m);
-      for (int e = 0; e < 4; ++e) matb[4 * g + e] = qc_make(m[e].x, m[e].y);
+    if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(d.counter, 1);
+    cl.sync();
+    const int it = *cl.map_shared_rank(&s_item, 0);
+    cl.sync();  // read by all before rank 0 may exit or take the next item
+    if (it >= d.nitems) break;
+    const BItem& item = d.items[it];
+    int set_id = -1, r = 0, nr = 1;
+    if (item.cluster) {
+      set_id = item.sets[0];
+      r = rank;
+      nr = d.csize;
+    } else if (rank < item.nsets) {
+      set_id = item.sets[rank];
     }
-    for (int j = threadIdx.x; j < st.nparams; j += BT_THREADS) d.grads[st.param_begin + j] = 0.0;
-    // 2. psi = |0>
-    for (uint64_t x = threadIdx.x; x < N; x += BT_THREADS) psi[x] = make_double2(x == 0 ? 1.0 : 0.0, 0.0);
-    __syncthreads();
-    for (int p = st.pass_begin; p < st.pass_begin + st.npasses; ++p)
-      bt_run_pass(d, d.passes[p], psi, lam, matf, matb, false, tP, tL, offs, acc, red);
-    // 3. lambda = (H/S) psi, energy
-    double e = 0.0;
-    for (uint64_t y = threadIdx.x; y < N; y += BT_THREADS) {
-      double ore = 0.0, oim = 0.0;
-      for (int gi = st.group_begin; gi < st.group_begin + st.ngroups; ++gi) {
-        const BGroup grp = d.groups[gi];
-        const uint64_t x = y ^ grp.xm;
-        double dre = 0.0, dim = 0.0;
-        for (int k = grp.tbegin; k < grp.tend; ++k) {
-          const BTerm t = d.terms[k];
-          const double v = (__popcll(x & t.zm) & 1) ? -t.c : t.c;
-          if (t.imag) dim += v;
-          else dre += v;
-        }
-        const double2 pv = psi[x];
-        ore += dre * pv.x - dim * pv.y;
-        oim += dre * pv.y + dim * pv.x;
-      }
-      lam[y] = make_double2(ore, oim);
-      const double2 py = psi[y];
-      e += py.x * ore + py.y * oim;
-    }
-    const double E = bt_block_sum(e, red);
-    if (threadIdx.x == 0) d.energies[set_id] = E * st.S;
-    __syncthreads();
-    // 4. backward
-    for (int p = st.pass_begin + st.npasses - 1; p >= st.pass_begin; --p)
-      bt_run_pass(d, d.passes[p], psi, lam, matf, matb, true, tP, tL, offs, acc, red);
-    if (threadIdx.x == 0)
-      for (int j = 0; j < st.nparams; ++j) d.grads[st.param_begin + j] *= st.S;
+    if (set_id >= 0) bt_eval_set(d, set_id, r, nr, tP, tL, offs, acc, red, s_epart);
   }
 }
 
@@ -299,6 +386,7 @@ struct qs_batch {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the persistent kernel
   int grid = 0;
+  int csize = 1;
   size_t smem = 0;
 };
 
@@ -332,6 +420,70 @@ static int dev_alloc(qs_batch* b, size_t bytes, void** out) {
   QS_CUDA(cudaMalloc(out, std::max<size_t>(bytes, 16)));
   b->dev.push_back(*out);
   return QS_OK;
+}
+
+static int g_batch_cluster = 0;  // 0: chosen per batch
+
+// Work items for clusters of c CTAs, most expensive first (longest-processing-time
+// order), and the makespan of their greedy schedule over `nclusters` clusters in
+// units of one CTA's time for one gate on 2^n amplitudes.  Cost of a set ~
+// 2^n (gates + 1); a set with at least c tiles per pass is one item for a whole
+// cluster (cost / c); smaller sets go c to an item (cost of the largest member).
+static double plan_items(const std::vector<BSet>& sets, int c, int nclusters, std::vector<BItem>* out) {
+  auto cost = [&](int i) { return std::ldexp((double)sets[i].ngates + 1.0, sets[i].n); };
+  std::vector<int> small;
+  std::vector<std::pair<double, BItem>> its;
+  for (size_t i = 0; i < sets.size(); ++i) {
+    if (c > 1 && sets[i].n >= BT_M && (1 << (sets[i].n - BT_M)) >= c) {
+      BItem it{};
+      it.cluster = 1;
+      it.nsets = 1;
+      it.sets[0] = (int)i;
+      its.push_back({cost((int)i) / c, it});
+    } else {
+      small.push_back((int)i);
+    }
+  }
+  std::stable_sort(small.begin(), small.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  for (size_t k = 0; k < small.size(); k += c) {
+    BItem it{};
+    it.cluster = 0;
+    it.nsets = (int)std::min<size_t>(c, small.size() - k);
+    for (int r = 0; r < it.nsets; ++r) it.sets[r] = small[k + r];
+    its.push_back({cost(small[k]), it});
+  }
+  std::stable_sort(its.begin(), its.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<double> finish(nclusters, 0.0);  // small heap-free scan: nclusters is a few hundred
+  double span = 0.0;
+  out->clear();
+  for (auto& pr : its) {
+    size_t k = std::min_element(finish.begin(), finish.end()) - finish.begin();
+    finish[k] += pr.first;
+    span = std::max(span, finish[k]);
+    out->push_back(pr.second);
+  }
+  return span;
+}
+
+extern "C" int qs_set_batch_cluster(int ctas) {
+  clear_error();
+  if (ctas != 0 && ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8)
+    return fail(QS_ERR_INVALID_ARG, "cluster size %d not in {0, 1, 2, 4, 8}", ctas);
+  g_batch_cluster = ctas;
+  return QS_OK;
+}
+
+static void batch_config(const qs_batch* b, int grid, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = b->args.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->gridDim = dim3(grid);
+  cfg->blockDim = dim3(BT_THREADS);
+  cfg->dynamicSmemBytes = b->smem;
+  cfg->stream = b->stream;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
 }
 
 extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate* gates, const size_t* gate_offsets,
@@ -475,11 +627,6 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
     }
     st.npasses = (int)passes.size() - st.pass_begin;
   }
-  // largest sets first
-  std::vector<int> order(nsets);
-  for (size_t i = 0; i < nsets; ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sets[a].n > sets[b].n; });
-
   qs_batch* b = new (std::nothrow) qs_batch;
   if (!b) return fail(QS_ERR_OOM, "host allocation failed");
   int rc = QS_OK;
@@ -494,9 +641,7 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
   if (e != cudaSuccess) chk(cuda_fail(e, "cudaStreamCreate / cudaEventCreate"));
   BatchArgs& a = b->args;
-  a.nsets = (int)nsets;
   if (rc == QS_OK) chk(upload(b, sets, &a.sets));
-  if (rc == QS_OK) chk(upload(b, order, &a.order));
   if (rc == QS_OK) chk(upload(b, passes, &a.passes));
   if (rc == QS_OK) chk(upload(b, ops, &a.ops));
   if (rc == QS_OK) chk(upload(b, bgates, &a.gates));
@@ -521,12 +666,39 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
   if (rc == QS_OK) {
     b->smem = batch_smem_bytes();
     e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-    int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT_THREADS, b->smem);
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     if (e != cudaSuccess) chk(cuda_fail(e, "batch kernel set-up"));
-    b->grid = std::max(1, per_sm) * std::max(1, sms);
+    // cluster size: the forced one, else the one whose LPT schedule of the items
+    // over the resident clusters has the shortest estimated makespan
+    std::vector<BItem> items;
+    double best = 0.0;
+    for (int c = BT_CLUSTER; c >= 1 && rc == QS_OK; c >>= 1) {
+      if (g_batch_cluster && c != g_batch_cluster) continue;
+      b->args.csize = c;
+      cudaLaunchConfig_t cfg{};
+      cudaLaunchAttribute attr[1];
+      batch_config(b, c * std::max(1, sms), &cfg, attr);
+      int nclusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&nclusters, k_batch, &cfg);
+      if (e != cudaSuccess) {
+        chk(cuda_fail(e, "cudaOccupancyMaxActiveClusters"));
+        break;
+      }
+      if (nclusters < 1) continue;
+      std::vector<BItem> its;
+      const double span = plan_items(sets, c, nclusters, &its);
+      if (items.empty() || span < best) {
+        best = span;
+        items.swap(its);
+        b->grid = nclusters * c;
+        b->csize = c;
+      }
+    }
+    if (rc == QS_OK && items.empty()) chk(fail(QS_ERR_UNSUPPORTED, "no cluster of the batch kernel fits the device"));
+    a.csize = b->csize;
+    a.nitems = (int)items.size();
+    if (rc == QS_OK) chk(upload(b, items, &a.items));
   }
   if (rc != QS_OK) {
     batch_release(b);
@@ -545,7 +717,10 @@ static int batch_enqueue(qs_batch* b) {
   QS_CUDA(cudaStreamIsCapturing(b->stream, &cs));
   const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   QS_CUDA(cudaEventRecordWithFlags(b->ev0, b->stream, flags));
-  k_batch<<<b->grid, BT_THREADS, b->smem, b->stream>>>(a);
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  batch_config(b, b->grid, &cfg, attr);
+  QS_CUDA(cudaLaunchKernelEx(&cfg, k_batch, a));
   QS_TRY(launch_check("batch kernel"));
   QS_CUDA(cudaEventRecordWithFlags(b->ev1, b->stream, flags));
   return QS_OK;
@@ -556,6 +731,12 @@ extern "C" int qs_batch_last_ms(const qs_batch* b, double* ms) {
   float f = 0.f;
   QS_CUDA(cudaEventElapsedTime(&f, b->ev0, b->ev1));
   *ms = f;
+  return QS_OK;
+}
+
+extern "C" int qs_batch_cluster(const qs_batch* b, int* ctas) {
+  if (!b || !ctas) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  *ctas = b->csize;
   return QS_OK;
 }
 

@@ -61,6 +61,38 @@ def test_batch_matches_oracle(q, orc, ham):
         assert rel_close(gs, g0), s
 
 
+@pytest.mark.parametrize("ctas", [0, 1, 2, 4, 8])
+def test_cluster_and_single_cta_items_together(q, orc, ctas):
+    """Sets with at least c tiles per pass are shared by a cluster of c CTAs
+    (tiles split over the cluster, gradient partials summed across it); smaller
+    sets run one per CTA.  Both kinds in one launch, for every cluster size,
+    against the oracle, and bit-identical on a rerun."""
+    ns = [17, 10, 15, 14, 12, 16, 13, 11, 14, 9]
+    gl, npl, tl, params = make_sets(ns, 3, 21, "rand")
+    q.qs_set_batch_cluster(ctas)
+    try:
+        b = q.qs_batch_create(ns, gl, npl, tl)
+    finally:
+        q.qs_set_batch_cluster(0)
+    try:
+        if ctas:
+            assert q.qs_batch_cluster(b) == ctas
+        outs = []
+        for _ in range(2):
+            e = np.empty(len(ns))
+            g = np.empty(len(params))
+            q.qs_batch_run(b, params, e, g)
+            outs.append((e, g))
+    finally:
+        q.qs_batch_free(b)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    e, g = outs[0]
+    for s, (n, gates, terms, th, gs) in enumerate(zip(ns, gl, tl, split(params, npl), split(g, npl))):
+        e0, g0 = orc.adjoint_grad(n, gates, th, terms)
+        assert abs(e[s] - e0) < 1e-12, s
+        assert rel_close(gs, g0), s
+
+
 def test_batch_general_records(q, orc):
     """Controls, dagger records, shared parameters, parametrised diagonal gates
     whose target falls outside a tile (n=16 > 11 tile qubits)."""
