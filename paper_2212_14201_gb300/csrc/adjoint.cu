@@ -86,12 +86,12 @@ __device__ __forceinline__ void adj_pair(const AdjArgs& g, double2& a0, double2&
   auto qmul = [](double2 a, int code, const QC& u) {
     if (code != U_GENERAL) return adj_unit(a, code);
     const QL ar = q60_split(q60_from_double(a.x)), ai = q60_split(q60_from_double(a.y));
-    QAcc re{0, 0}, im{0, 0};
+    QAcc re = qacc_new(), im = qacc_new();
     qacc_add(re, u.re, ar);
     qacc_add(re, u.nim, ai);
     qacc_add(im, u.re, ai);
     qacc_add(im, u.im, ar);
-    return make_double2(q60_to_double(qacc_result(re)), q60_to_double(qacc_result(im)));
+    return make_double2(q60_to_double(qacc_round(re)), q60_to_double(qacc_round(im)));
   };
   if (cls == OP_PHASE1) {
     a1 = qmul(a1, g.code1, g.q[3]);
@@ -110,7 +110,7 @@ __device__ __forceinline__ void adj_pair(const AdjArgs& g, double2& a0, double2&
     for (int row = 0; row < 2; ++row) {
       const QC& u0 = g.q[2 * row];
       const QC& u1 = g.q[2 * row + 1];
-      QAcc re{0, 0}, im{0, 0};
+      QAcc re = qacc_new(), im = qacc_new();
       qacc_add(re, u0.re, r0);
       qacc_add(re, u1.re, r1);
       qacc_add(im, u0.re, i0);
@@ -121,8 +121,8 @@ __device__ __forceinline__ void adj_pair(const AdjArgs& g, double2& a0, double2&
         qacc_add(im, u0.im, r0);
         qacc_add(im, u1.im, r1);
       }
-      out[2 * row] = qacc_result(re);
-      out[2 * row + 1] = qacc_result(im);
+      out[2 * row] = qacc_round(re);
+      out[2 * row + 1] = qacc_round(im);
     }
     a0 = make_double2(q60_to_double(out[0]), q60_to_double(out[1]));
     a1 = make_double2(q60_to_double(out[2]), q60_to_double(out[3]));

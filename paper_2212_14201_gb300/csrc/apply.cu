@@ -112,7 +112,7 @@ __device__ __forceinline__ double2 q_store(QV v) { return make_double2(q60_to_do
 
 // u0*a0 + u1*a1 (complex), a as limbs
 __device__ __forceinline__ QV q_mv2(const QC& u0, QL a0r, QL a0i, const QC& u1, QL a1r, QL a1i) {
-  QAcc re{0, 0}, im{0, 0};
+  QAcc re = qacc_new(), im = qacc_new();
   qacc_add(re, u0.re, a0r);
   qacc_add(re, u0.nim, a0i);
   qacc_add(re, u1.re, a1r);
@@ -121,27 +121,27 @@ __device__ __forceinline__ QV q_mv2(const QC& u0, QL a0r, QL a0i, const QC& u1, 
   qacc_add(im, u0.im, a0r);
   qacc_add(im, u1.re, a1i);
   qacc_add(im, u1.im, a1r);
-  return {qacc_result(re), qacc_result(im)};
+  return {qacc_round(re), qacc_round(im)};
 }
 
 // u*a (complex)
 __device__ __forceinline__ QV q_mul(const QC& u, QL ar, QL ai) {
-  QAcc re{0, 0}, im{0, 0};
+  QAcc re = qacc_new(), im = qacc_new();
   qacc_add(re, u.re, ar);
   qacc_add(re, u.nim, ai);
   qacc_add(im, u.re, ai);
   qacc_add(im, u.im, ar);
-  return {qacc_result(re), qacc_result(im)};
+  return {qacc_round(re), qacc_round(im)};
 }
 
 // real 2x2: u0.re*a0 + u1.re*a1
 __device__ __forceinline__ QV q_real2(const QC& u0, QL a0r, QL a0i, const QC& u1, QL a1r, QL a1i) {
-  QAcc re{0, 0}, im{0, 0};
+  QAcc re = qacc_new(), im = qacc_new();
   qacc_add(re, u0.re, a0r);
   qacc_add(re, u1.re, a1r);
   qacc_add(im, u0.re, a0i);
   qacc_add(im, u1.re, a1i);
-  return {qacc_result(re), qacc_result(im)};
+  return {qacc_round(re), qacc_round(im)};
 }
 
 __device__ __forceinline__ double2 fx_mul(double2 a, int code, const QC& u) {

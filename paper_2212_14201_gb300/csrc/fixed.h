@@ -136,6 +136,12 @@ QS_HD int64_t qacc_result(const QAcc& acc) {
   return acc.hi + ((acc.mid + (1ll << 29)) >> 30);
 }
 
+// The same result with the rounding half (2^29 in mid units) added up front:
+// start from qacc_new(), finish with qacc_round() (one shift and one add fewer
+// per result; identical value, since integer addition is associative).
+QS_HD QAcc qacc_new() { return {0, 1ll << 29}; }
+QS_HD int64_t qacc_round(const QAcc& acc) { return acc.hi + (acc.mid >> 30); }
+
 // Accumulator that keeps the low x low limb products too (exact up to the final
 // rounding, no bias): for sums that are later added up over a whole state
 // vector, such as inner products, where a dropped non-negative term per product
@@ -168,6 +174,36 @@ QS_HD QC qc_make(double re, double im) {
   c.im = q60_split(q60_from_double(im));
   c.nim = q60_split(-q60_from_double(im));
   return c;
+}
+
+// Gauss (three-multiplication) form of an entry c + i d, for the product
+// (a + i b)(c + i d) = [c (a + b) - b (c + d)] + i [c (a + b) + a (d - c)]:
+// re = c, im = d - c, nim = c + d, each from the Q60-rounded c and d, so the
+// represented matrix is exactly the one qc_make() gives.  |c +- d| <= sqrt(2)|u|.
+QS_HD QC qc_make_gauss(double re, double im) {
+  const int64_t c = q60_from_double(re), d = q60_from_double(im);
+  QC q;
+  q.re = q60_split(c);
+  q.im = q60_split(d - c);
+  q.nim = q60_split(c + d);
+  return q;
+}
+
+// One output of a general 2x2 complex row in Gauss form:
+//   out = u0 (r0 + i i0) + u1 (r1 + i i1),  s_e = r_e + i_e (as Q60, split),
+// u_e from qc_make_gauss().  Needs |s_e| < 2 (true for |amplitude| <= 1.25).
+// Six limb products (18 wide multiply-adds) instead of eight.
+QS_HD void q60_gauss_row(const QC& u0, const QC& u1, QL r0, QL i0, QL s0, QL r1, QL i1, QL s1, int64_t* re,
+                         int64_t* im) {
+  QAcc k1 = qacc_new(), k2{0, 0}, k3{0, 0};
+  qacc_add(k1, u0.re, s0);
+  qacc_add(k1, u1.re, s1);
+  qacc_add(k2, u0.im, r0);
+  qacc_add(k2, u1.im, r1);
+  qacc_add(k3, u0.nim, i0);
+  qacc_add(k3, u1.nim, i1);
+  *re = qacc_round(QAcc{k1.hi - k3.hi, k1.mid - k3.mid});
+  *im = qacc_round(QAcc{k1.hi + k2.hi, k1.mid + k2.mid});
 }
 
 }  // namespace qs

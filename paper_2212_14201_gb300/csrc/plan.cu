@@ -417,7 +417,9 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     Op1 op = classify(t, cm, mat);
     if (op.cls == OP_IDENTITY) continue;
     TileOp& to = g->ops[g->nops];
-    if (fixed)
+    if (fixed && op.cls == OP_GENERAL)  // three limb products per complex product
+      for (int i = 0; i < 4; ++i) to.q[i] = qc_make_gauss(mat.m[i].re, mat.m[i].im);
+    else if (fixed)
       for (int i = 0; i < 4; ++i) to.q[i] = qc_make(mat.m[i].re, mat.m[i].im);
     else
       for (int i = 0; i < 4; ++i) to.m[i] = make_double2(mat.m[i].re, mat.m[i].im);

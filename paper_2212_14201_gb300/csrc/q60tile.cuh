@@ -49,12 +49,12 @@ __device__ __forceinline__ longlong2 bt_unit(longlong2 a, int code) {
 __device__ __forceinline__ longlong2 bt_mul(longlong2 a, int code, const QC& u) {
   if (code != U_GENERAL) return bt_unit(a, code);
   const QL ar = q60_split(a.x), ai = q60_split(a.y);
-  QAcc re{0, 0}, im{0, 0};
+  QAcc re = qacc_new(), im = qacc_new();
   qacc_add(re, u.re, ar);
   qacc_add(re, u.nim, ai);
   qacc_add(im, u.re, ai);
   qacc_add(im, u.im, ar);
-  return make_longlong2(qacc_result(re), qacc_result(im));
+  return make_longlong2(qacc_round(re), qacc_round(im));
 }
 
 __device__ __forceinline__ uint32_t bt_expand(uint32_t i, uint32_t fixed, uint32_t set) {
@@ -104,7 +104,7 @@ static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int
       for (int row = 0; row < 2; ++row) {
         const QC& u0 = U[2 * row];
         const QC& u1 = U[2 * row + 1];
-        QAcc re{0, 0}, im{0, 0};
+        QAcc re = qacc_new(), im = qacc_new();
         qacc_add(re, u0.re, r0);
         qacc_add(re, u1.re, r1);
         qacc_add(im, u0.re, i0);
@@ -115,8 +115,8 @@ static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int
           qacc_add(im, u0.im, r0);
           qacc_add(im, u1.im, r1);
         }
-        out[2 * row] = qacc_result(re);
-        out[2 * row + 1] = qacc_result(im);
+        out[2 * row] = qacc_round(re);
+        out[2 * row + 1] = qacc_round(im);
       }
       b0 = make_longlong2(out[0], out[1]);
       b1 = make_longlong2(out[2], out[3]);

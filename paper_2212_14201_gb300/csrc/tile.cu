@@ -81,16 +81,16 @@ struct EngQ60 {
     if (code != U_GENERAL) return unit(a, code);
     const QC& u = op.q[e];
     const QL ar = q60_split(a.x), ai = q60_split(a.y);
-    QAcc re{0, 0}, im{0, 0};
+    QAcc re = qacc_new(), im = qacc_new();
     qacc_add(re, u.re, ar);
     qacc_add(re, u.nim, ai);
     qacc_add(im, u.re, ai);
     qacc_add(im, u.im, ar);
-    return make_longlong2(qacc_result(re), qacc_result(im));
+    return make_longlong2(qacc_round(re), qacc_round(im));
   }
   static __device__ __forceinline__ void real2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
     const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
-    QAcc x{0, 0}, y{0, 0}, z{0, 0}, w{0, 0};
+    QAcc x = qacc_new(), y = qacc_new(), z = qacc_new(), w = qacc_new();
     qacc_add(x, op.q[0].re, r0);
     qacc_add(x, op.q[1].re, r1);
     qacc_add(y, op.q[0].re, i0);
@@ -99,26 +99,19 @@ struct EngQ60 {
     qacc_add(z, op.q[3].re, r1);
     qacc_add(w, op.q[2].re, i0);
     qacc_add(w, op.q[3].re, i1);
-    b0 = make_longlong2(qacc_result(x), qacc_result(y));
-    b1 = make_longlong2(qacc_result(z), qacc_result(w));
+    b0 = make_longlong2(qacc_round(x), qacc_round(y));
+    b1 = make_longlong2(qacc_round(z), qacc_round(w));
   }
   static __device__ __forceinline__ void general2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
     const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
-#pragma unroll
-    for (int row = 0; row < 2; ++row) {
-      const QC& u0 = op.q[2 * row];
-      const QC& u1 = op.q[2 * row + 1];
-      QAcc re{0, 0}, im{0, 0};
-      qacc_add(re, u0.re, r0);
-      qacc_add(re, u0.nim, i0);
-      qacc_add(re, u1.re, r1);
-      qacc_add(re, u1.nim, i1);
-      qacc_add(im, u0.re, i0);
-      qacc_add(im, u0.im, r0);
-      qacc_add(im, u1.re, i1);
-      qacc_add(im, u1.im, r1);
-      (row == 0 ? b0 : b1) = make_longlong2(qacc_result(re), qacc_result(im));
-    }
+    // Gauss form: K1 = sum c (a + b), K2 = sum a (d - c), K3 = sum b (c + d);
+    // re = K1 - K3, im = K1 + K2 (three limb products per complex product)
+    const QL s0 = q60_split(a0.x + a0.y), s1 = q60_split(a1.x + a1.y);
+    int64_t re, im;
+    q60_gauss_row(op.q[0], op.q[1], r0, i0, s0, r1, i1, s1, &re, &im);
+    b0 = make_longlong2(re, im);
+    q60_gauss_row(op.q[2], op.q[3], r0, i0, s0, r1, i1, s1, &re, &im);
+    b1 = make_longlong2(re, im);
   }
 };
 
@@ -329,15 +322,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tile_reg(double2* __restrict_
 }
 template <class E>
 static int launch_engine(qs_state* s, const TileArgs& g, size_t smem) {
-  constexpr int THREADS = 256;
+  constexpr int THREADS = 256;  // measured at n=30: 512 (2 CTAs/SM) and 1024 (1/SM) are 2-6% slower
   static bool attr_set = false;
+  static int sms = 0;
   if (!attr_set) {
     QS_CUDA(cudaFuncSetAttribute(k_tile<E, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
     attr_set = true;
   }
-  int per_sm = (int)std::max<size_t>(1, (220 * 1024) / (smem + 1024));
-  per_sm = std::min(per_sm, 8);
-  uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)152 * per_sm);
+  int per_sm = 0;
+  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<E, THREADS>, THREADS, smem));
+  const uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)std::max(1, sms) * std::max(1, per_sm));
   k_tile<E, THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
   return launch_check("tile kernel");
 }

@@ -29,6 +29,10 @@ def fc():
     lib.fc_dot2.argtypes = [ctypes.c_longlong] * 4
     lib.fc_dot4.restype = ctypes.c_longlong
     lib.fc_dot4.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.fc_dot4_kernel.restype = ctypes.c_longlong
+    lib.fc_dot4_kernel.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.fc_gauss_row.restype = None
+    lib.fc_gauss_row.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc_dot4_full.restype = ctypes.c_longlong
     lib.fc_dot4_full.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     return lib
@@ -90,6 +94,7 @@ def test_limb_products_error_bound(fc):
         ua = (ctypes.c_longlong * 4)(*u)
         aa = (ctypes.c_longlong * 4)(*a)
         got = fc.fc_dot4(ua, aa)
+        assert fc.fc_dot4_kernel(ua, aa) == got   # pre-biased accumulator: identical value
         # four dropped low-limb products (< 2^60 each in 2^-120 units -> < 1 in Q60 units) + rounding
         assert abs(got - exact) <= 4 + 1
         got2 = fc.fc_dot2(u[0], a[0], u[1], a[1])
@@ -121,3 +126,26 @@ def test_extreme_limbs_do_not_overflow(fc):
             aa = (ctypes.c_longlong * 4)(*a)
             exact = Fraction(sum(x * y for x, y in zip(u, a)), 1 << 60)
             assert abs(fc.fc_dot4(ua, aa) - exact) <= 5
+
+
+def test_gauss_row_error_bound(fc):
+    """A general 2x2 row in the three-product (Gauss) form: u0 a0 + u1 a1 for a
+    row of a random unitary and amplitudes of modulus up to 1.25 (the Q60 state
+    bound), against exact rational arithmetic on the same Q60-rounded inputs:
+    six dropped low-limb products plus the final rounding."""
+    g = np.random.Generator(np.random.PCG64(6))
+    for trial in range(3000):
+        z = g.normal(size=2) + 1j * g.normal(size=2)
+        z /= np.linalg.norm(z)
+        u = [z[0].real, z[0].imag, z[1].real, z[1].imag]
+        amp = g.normal(size=2) + 1j * g.normal(size=2)
+        amp *= 1.25 / np.abs(amp) if trial % 3 == 0 else 1.0 / max(1.0, np.max(np.abs(amp)))
+        a = [int(round(v * (1 << 60))) for v in (amp[0].real, amp[0].imag, amp[1].real, amp[1].imag)]
+        a = [max(min(v, int(1.25 * (1 << 60))), -int(1.25 * (1 << 60))) for v in a]
+        out = (ctypes.c_longlong * 2)()
+        fc.fc_gauss_row((ctypes.c_double * 4)(*u), (ctypes.c_longlong * 4)(*a), out)
+        uq = [fc.fc_from_double(v) for v in u]
+        ex_re = Fraction(uq[0] * a[0] - uq[1] * a[1] + uq[2] * a[2] - uq[3] * a[3], 1 << 60)
+        ex_im = Fraction(uq[0] * a[1] + uq[1] * a[0] + uq[2] * a[3] + uq[3] * a[2], 1 << 60)
+        assert abs(out[0] - ex_re) <= 7, trial
+        assert abs(out[1] - ex_im) <= 7, trial
