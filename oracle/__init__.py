@@ -22,7 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, EINVAL, ENOMEM, EUNSUPPORTED = 0, -1, -2, -5
+OK, EINVAL, ENOMEM, ELIMIT, EUNSUPPORTED = 0, -1, -2, -4, -5
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +64,8 @@ def _load():
                 "or_mlp_nweights": (i64, [i32, i32]),
                 "or_mlp_forward": (i32, [i32, i32, P, P, i64, P]),
                 "or_mlp_loss_grad": (i32, [i32, i32, P, P, P, i64, P, P]),
+                "or_measure": (i32, [P, i32, i32, ctypes.c_double, P, P]),
+                "or_run_program": (i32, [P, i32, P, i64, P, i64, P, u64, u64, P, i64, P, i64, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -242,3 +244,31 @@ def mlp_loss_grad(F: int, H: int, w: np.ndarray, x: np.ndarray, t: np.ndarray):
 
 def as_complex(state: np.ndarray) -> np.ndarray:
     return _state(state).view(np.complex128)
+
+
+def measure(state: np.ndarray, n: int, qubit: int, u: float):
+    """Projective measurement of one qubit with the draw u in [0, 1): returns
+    (outcome, p1 / (p0 + p1), collapsed state)."""
+    st = _state(state).copy()
+    o = ctypes.c_int()
+    p1 = ctypes.c_double()
+    _chk(_load().or_measure(st.ctypes.data, n, qubit, u, ctypes.byref(o), ctypes.byref(p1)), "or_measure")
+    return o.value, p1.value, st
+
+
+def run_program(n: int, prog: np.ndarray, gates: np.ndarray, params=None, seed: int = 0,
+                max_iters: int = 1 << 20, cbits=None, ncbits: int = 8, state=None, record_cap: int = 4096):
+    """Runs a structured program (measurements, classical registers, if/while)
+    from |0...0> (or `state`).  Returns (state, cbits, record of p1 per measurement)."""
+    st = zero_state(n) if state is None else _state(state).copy()
+    cb = np.zeros(ncbits, dtype=np.int64) if cbits is None else np.array(cbits, dtype=np.int64)
+    rec = np.zeros(record_cap, dtype=np.float64)
+    nm = ctypes.c_uint64()
+    prog = np.ascontiguousarray(prog)
+    gates = np.ascontiguousarray(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    rc = _load().or_run_program(st.ctypes.data, n, _ptr(prog), len(prog), _ptr(gates) if len(gates) else None,
+                                len(gates), _ptr(pr), seed, max_iters, cb.ctypes.data, len(cb), rec.ctypes.data,
+                                record_cap, ctypes.byref(nm))
+    _chk(rc, "or_run_program")
+    return st, cb, rec[:min(nm.value, record_cap)].copy()

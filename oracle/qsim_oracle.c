@@ -26,6 +26,7 @@
 #define OR_EINVAL -1
 #define OR_ENOMEM -2
 #define OR_EUNSUPPORTED -5
+#define OR_ELIMIT -4
 
 enum {
   OR_I = 0, OR_H = 1, OR_X = 2, OR_Y = 3, OR_Z = 4, OR_S = 5, OR_T = 6,
@@ -594,4 +595,194 @@ int or_mlp_loss_grad(int F, int H, const double* w, const double* x, const doubl
   *loss = L / (double)B;
   free(z1);
   return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Mid-circuit measurement and classical control (the paper's QMeasure,      */
+/* QIf, QWhile and ClassicalProg nodes, Section "Core" with its QIf / QWhile  */
+/* listings, and Section "Qif and QWhile": classical bits take +, -, *, /,   */
+/* XOR, logical and/or and comparisons).  The paper fixes neither the random */
+/* draw nor the decision rule; the readings shared with the GPU library:     */
+/*   draw k (0-based count of measurements in one run) u_k = u01(SplitMix64  */
+/*   number k of the stream seeded `seed`), the sampler's mapping;           */
+/*   p0, p1 = sums of |a_x|^2 over x with bit q = 0 / 1;                     */
+/*   outcome = 0 if u_k * (p0 + p1) < p0, else 1;                            */
+/*   collapse: a_x = 0 where bit q != outcome, a_x *= 1 / sqrt(p_outcome)    */
+/*   elsewhere (Born rule and projective collapse, Nielsen & Chuang 2.2.3).  */
+/* ------------------------------------------------------------------------- */
+int or_measure(double* state, int n, int q, double u, int* outcome, double* p1_out) {
+  if (q < 0 || q >= n) return OR_EINVAL;
+  cplx* psi = (cplx*)state;
+  const int64_t N = (int64_t)1 << n;
+  double p0 = 0.0, p1 = 0.0;
+  for (int64_t x = 0; x < N; ++x) {
+    if ((x >> q) & 1) p1 += prob_of(psi[x]);
+    else p0 += prob_of(psi[x]);
+  }
+  if (!(p0 + p1 > 0.0)) return OR_EINVAL;
+  const int o = (u * (p0 + p1) < p0) ? 0 : 1;
+  const double scale = 1.0 / sqrt(o ? p1 : p0);
+  for (int64_t x = 0; x < N; ++x) {
+    if ((int)((x >> q) & 1) == o) {
+      psi[x].re *= scale;
+      psi[x].im *= scale;
+    } else {
+      psi[x].re = 0.0;
+      psi[x].im = 0.0;
+    }
+  }
+  *outcome = o;
+  if (p1_out) *p1_out = p1 / (p0 + p1);
+  return OR_OK;
+}
+
+enum { OR_PI_GATES = 0, OR_PI_MEASURE = 1, OR_PI_ASSIGN = 2, OR_PI_IF = 3, OR_PI_WHILE = 4 };
+enum {
+  OR_CA_MOV = 0, OR_CA_ADD, OR_CA_SUB, OR_CA_MUL, OR_CA_DIV, OR_CA_AND, OR_CA_OR, OR_CA_XOR,
+  OR_CA_LT, OR_CA_LE, OR_CA_GT, OR_CA_GE, OR_CA_EQ, OR_CA_NE, OR_CA_NOT
+};
+
+typedef struct {
+  int32_t op, qubit, dst, alu, lhs, rhs;
+  int64_t imm;
+  uint32_t n_then, n_else;
+  uint64_t gate_begin, gate_end;
+} or_pinstr;
+
+typedef struct {
+  double* state;
+  int n;
+  const or_pinstr* prog;
+  const or_gate* gates;
+  int64_t ng;
+  const double* params;
+  uint64_t seed, max_iters, nmeas;
+  int64_t* cbits;
+  int64_t ncbits;
+  double* record;
+  int64_t record_cap;
+} or_run;
+
+static int operand(const or_run* r, int32_t idx, int64_t imm, int64_t* v) {
+  if (idx < 0) { *v = imm; return OR_OK; }
+  if (idx >= r->ncbits) return OR_EINVAL;
+  *v = r->cbits[idx];
+  return OR_OK;
+}
+
+/* two's-complement wrap for + - * (computed in unsigned arithmetic) */
+static int alu_eval(int alu, int64_t a, int64_t b, int64_t* out) {
+  switch (alu) {
+    case OR_CA_MOV: *out = a; return OR_OK;
+    case OR_CA_ADD: *out = (int64_t)((uint64_t)a + (uint64_t)b); return OR_OK;
+    case OR_CA_SUB: *out = (int64_t)((uint64_t)a - (uint64_t)b); return OR_OK;
+    case OR_CA_MUL: *out = (int64_t)((uint64_t)a * (uint64_t)b); return OR_OK;
+    case OR_CA_DIV:
+      if (b == 0 || (a == INT64_MIN && b == -1)) return OR_EINVAL;
+      *out = a / b;
+      return OR_OK;
+    case OR_CA_AND: *out = (a != 0) && (b != 0); return OR_OK;
+    case OR_CA_OR: *out = (a != 0) || (b != 0); return OR_OK;
+    case OR_CA_XOR: *out = a ^ b; return OR_OK;
+    case OR_CA_LT: *out = a < b; return OR_OK;
+    case OR_CA_LE: *out = a <= b; return OR_OK;
+    case OR_CA_GT: *out = a > b; return OR_OK;
+    case OR_CA_GE: *out = a >= b; return OR_OK;
+    case OR_CA_EQ: *out = a == b; return OR_OK;
+    case OR_CA_NE: *out = a != b; return OR_OK;
+    case OR_CA_NOT: *out = a == 0; return OR_OK;
+    default: return OR_EINVAL;
+  }
+}
+
+/* Runs instructions [begin, end) of the program; blocks nest by length. */
+static int run_block(or_run* r, int64_t begin, int64_t end) {
+  int64_t i = begin;
+  while (i < end) {
+    const or_pinstr* in = &r->prog[i];
+    int rc = OR_OK;
+    switch (in->op) {
+      case OR_PI_GATES:
+        if (in->gate_begin > in->gate_end || (int64_t)in->gate_end > r->ng) return OR_EINVAL;
+        rc = or_apply_circuit(r->state, r->n, r->gates + in->gate_begin,
+                              (int64_t)(in->gate_end - in->gate_begin), r->params);
+        if (rc) return rc;
+        ++i;
+        break;
+      case OR_PI_MEASURE: {
+        if (in->dst < 0 || in->dst >= r->ncbits) return OR_EINVAL;
+        const double u = u01(or_splitmix64(r->seed, r->nmeas));
+        int o;
+        double p1;
+        rc = or_measure(r->state, r->n, in->qubit, u, &o, &p1);
+        if (rc) return rc;
+        if ((int64_t)r->nmeas < r->record_cap && r->record) r->record[r->nmeas] = p1;
+        r->nmeas++;
+        r->cbits[in->dst] = o;
+        ++i;
+        break;
+      }
+      case OR_PI_ASSIGN: {
+        int64_t a, b, v;
+        if (in->dst < 0 || in->dst >= r->ncbits) return OR_EINVAL;
+        if ((rc = operand(r, in->lhs, in->imm, &a)) || (rc = operand(r, in->rhs, in->imm, &b))) return rc;
+        if ((rc = alu_eval(in->alu, a, b, &v))) return rc;
+        r->cbits[in->dst] = v;
+        ++i;
+        break;
+      }
+      case OR_PI_IF: {
+        const int64_t t0 = i + 1, t1 = t0 + in->n_then, e1 = t1 + in->n_else;
+        if (e1 > end) return OR_EINVAL;
+        int64_t c;
+        if ((rc = operand(r, in->lhs, in->imm, &c))) return rc;
+        rc = c != 0 ? run_block(r, t0, t1) : run_block(r, t1, e1);
+        if (rc) return rc;
+        i = e1;
+        break;
+      }
+      case OR_PI_WHILE: {
+        const int64_t b0 = i + 1, b1 = b0 + in->n_then;
+        if (b1 > end || in->n_else != 0) return OR_EINVAL;
+        uint64_t iters = 0;
+        for (;;) {
+          int64_t c;
+          if ((rc = operand(r, in->lhs, in->imm, &c))) return rc;
+          if (c == 0) break;
+          if (iters++ >= r->max_iters) return OR_ELIMIT;
+          if ((rc = run_block(r, b0, b1))) return rc;
+        }
+        i = b1;
+        break;
+      }
+      default:
+        return OR_EINVAL;
+    }
+  }
+  return OR_OK;
+}
+
+/* Runs a program with classical control on `state` (in place).  cbits (ncbits
+ * int64 values, in/out) are the classical register; record[k] receives
+ * p1 / (p0 + p1) of measurement k (up to record_cap); *nmeasured the count. */
+int or_run_program(double* state, int n, const or_pinstr* prog, int64_t nprog, const or_gate* gates, int64_t ng,
+                   const double* params, uint64_t seed, uint64_t max_iters, int64_t* cbits, int64_t ncbits,
+                   double* record, int64_t record_cap, uint64_t* nmeasured) {
+  or_run r;
+  r.state = state;
+  r.n = n;
+  r.prog = prog;
+  r.gates = gates;
+  r.ng = ng;
+  r.params = params;
+  r.seed = seed;
+  r.max_iters = max_iters;
+  r.nmeas = 0;
+  r.cbits = cbits;
+  r.ncbits = ncbits;
+  r.record = record;
+  r.record_cap = record_cap;
+  const int rc = run_block(&r, 0, nprog);
+  if (nmeasured) *nmeasured = r.nmeas;
+  return rc;
 }

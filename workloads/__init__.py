@@ -232,3 +232,136 @@ def random_matrix(k: int, seed: int) -> np.ndarray:
     for i in range(2 * d * d):
         m[i] = (2.0 * rng.uniform() - 1.0) * 2.0 ** (-k / 2.0)
     return m
+
+
+# ---- programs with measurement and classical control ---------------------------------
+# Instruction layout (56 bytes), read by the oracle and the CUDA library alike:
+#   int32 op       PROGRAM_OPS
+#   int32 qubit    MEASURE: measured qubit
+#   int32 dst      MEASURE / ASSIGN: classical bit (int64 register) written
+#   int32 alu      ASSIGN: CLASSICAL_OPS
+#   int32 lhs, rhs operands: register index, or -1 for the immediate
+#   int64 imm      the immediate
+#   uint32 n_then  IF: length of the then-block that follows; WHILE: body length
+#   uint32 n_else  IF: length of the else-block after the then-block; WHILE: 0
+#   uint64 gate_begin, gate_end   GATES: range of the program's gate array
+# IF and WHILE test their lhs operand for != 0; a WHILE re-tests before every pass.
+PROGRAM_OPS = {"GATES": 0, "MEASURE": 1, "ASSIGN": 2, "IF": 3, "WHILE": 4}
+CLASSICAL_OPS = {"MOV": 0, "ADD": 1, "SUB": 2, "MUL": 3, "DIV": 4, "AND": 5, "OR": 6, "XOR": 7,
+                 "LT": 8, "LE": 9, "GT": 10, "GE": 11, "EQ": 12, "NE": 13, "NOT": 14}
+
+PINSTR_DTYPE = np.dtype([
+    ("op", "<i4"), ("qubit", "<i4"), ("dst", "<i4"), ("alu", "<i4"), ("lhs", "<i4"), ("rhs", "<i4"),
+    ("imm", "<i8"), ("n_then", "<u4"), ("n_else", "<u4"), ("gate_begin", "<u8"), ("gate_end", "<u8"),
+], align=True)
+assert PINSTR_DTYPE.itemsize == 56
+
+
+class Program:
+    """Builder of a structured program: gate runs, measurements into classical
+    registers, register assignments, if/else and while blocks (nested by length)."""
+
+    def __init__(self):
+        self.instrs = []
+        self.gates = []
+
+    def _emit(self, **kw):
+        rec = dict(op=0, qubit=-1, dst=-1, alu=0, lhs=-1, rhs=-1, imm=0, n_then=0, n_else=0,
+                   gate_begin=0, gate_end=0)
+        rec.update(kw)
+        self.instrs.append(rec)
+        return len(self.instrs) - 1
+
+    def apply(self, records):
+        b = len(self.gates)
+        self.gates.extend(list(np.asarray(records, dtype=GATE_DTYPE)))
+        return self._emit(op=0, gate_begin=b, gate_end=len(self.gates))
+
+    def measure(self, qubit: int, dst: int):
+        return self._emit(op=1, qubit=qubit, dst=dst)
+
+    def assign(self, dst: int, alu: str, lhs: int = -1, rhs: int = -1, imm: int = 0):
+        return self._emit(op=2, dst=dst, alu=CLASSICAL_OPS[alu], lhs=lhs, rhs=rhs, imm=imm)
+
+    def if_(self, cond: int, then_fn, else_fn=None):
+        i = self._emit(op=3, lhs=cond)
+        t0 = len(self.instrs)
+        then_fn(self)
+        t1 = len(self.instrs)
+        if else_fn is not None:
+            else_fn(self)
+        self.instrs[i]["n_then"] = t1 - t0
+        self.instrs[i]["n_else"] = len(self.instrs) - t1
+
+    def while_(self, cond: int, body_fn):
+        i = self._emit(op=4, lhs=cond)
+        b0 = len(self.instrs)
+        body_fn(self)
+        self.instrs[i]["n_then"] = len(self.instrs) - b0
+
+    def pack(self):
+        prog = np.zeros(len(self.instrs), dtype=PINSTR_DTYPE)
+        for k, rec in enumerate(self.instrs):
+            for f, v in rec.items():
+                prog[k][f] = v
+        gates = np.array(self.gates, dtype=GATE_DTYPE) if self.gates else np.zeros(0, dtype=GATE_DTYPE)
+        return prog, gates
+
+
+def random_program(n: int, seed: int, segments: int = 6, gates_per_segment: int = 40, ncbits: int = 8):
+    """Random structured program: gate runs drawn as random_circuit, measurements
+    of random qubits, classical arithmetic on the registers, if/else on
+    registers, and bounded while loops (a counter register caps each loop at 4
+    passes).  Registers 0..ncbits-1; the last two are loop scratch."""
+    rng = SplitMix64(seed)
+    p = Program()
+    cnt, flag = ncbits - 1, ncbits - 2
+    data = ncbits - 2
+    alus = ["MOV", "ADD", "SUB", "MUL", "DIV", "AND", "OR", "XOR", "LT", "LE", "GT", "GE", "EQ", "NE", "NOT"]
+
+    def gates(pp):
+        pp.apply(random_circuit(n, 1 + rng.below(gates_per_segment), rng.next_u64() & 0xFFFFFFFF))
+
+    def measure(pp):
+        pp.measure(rng.below(n), rng.below(data))
+
+    def arith(pp):
+        alu = alus[rng.below(len(alus))]
+        if alu == "DIV":
+            pp.assign(rng.below(data), alu, rng.below(data), -1, 1 + rng.below(3))
+        elif rng.below(2):
+            pp.assign(rng.below(data), alu, rng.below(data), rng.below(data))
+        else:
+            pp.assign(rng.below(data), alu, rng.below(data), -1, rng.below(5) - 2)
+
+    def block(pp, depth):
+        for _ in range(1 + rng.below(3)):
+            k = rng.below(6 if depth < 2 else 3)
+            if k == 0:
+                gates(pp)
+            elif k == 1:
+                measure(pp)
+            elif k == 2:
+                arith(pp)
+            elif k == 3:
+                c = rng.below(data)
+                if rng.below(2):
+                    pp.if_(c, lambda q: block(q, depth + 1), lambda q: block(q, depth + 1))
+                else:
+                    pp.if_(c, lambda q: block(q, depth + 1))
+            else:
+                q = rng.below(n)
+
+                def body(bb):
+                    block(bb, depth + 1)
+                    bb.assign(cnt, "ADD", cnt, -1, 1)
+                    bb.measure(q, flag)
+                    bb.assign(data - 1, "LT", cnt, -1, 4 * (depth + 1))
+                    bb.assign(flag, "AND", flag, data - 1)
+                pp.assign(flag, "MOV", -1, -1, 1)
+                pp.while_(flag, body)
+
+    for _ in range(segments):
+        block(p, 0)
+        gates(p)
+    return p.pack()
