@@ -303,6 +303,42 @@ def bench_adjoint(q, torch, stream, steps: int):
     return {"grad_evals_per_s": 1.0 / dt, "ms_per_eval": dt * 1e3, "n": n, "params": npar, "gates": len(g)}
 
 
+def bench_measure(q, torch, stream, hbm_peak: float):
+    """Mid-circuit measurement at n=30 (16 GiB): the one-qubit marginal pass and
+    the collapse pass of qs_measure, on the state after one U3 layer and the CZ
+    brickwork, five qubits measured in turn.  Algorithmic bytes: marginal 16 B per
+    amplitude read; collapse 8 B per amplitude read (the kept half) + 16 B written."""
+    n = 30
+    g = w.layered_u3_cz(n, 1, 1)
+    h = q.qs_alloc(n, stream)
+    try:
+        q.qs_apply(h, g, None, None)
+        q.qs_measure(h, 0, 0.5)
+        q.qs_timing_enable(h, True)
+        q.qs_timing_fetch(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qubits = (29, 3, 17, 11, 24)
+        for k, qb in enumerate(qubits):
+            q.qs_measure(h, qb, 0.2 * k + 0.1)
+        dt = (time.perf_counter() - t0) / len(qubits)
+        recs = q.qs_timing_fetch(h)
+        q.qs_timing_enable(h, False)
+    finally:
+        q.qs_free(h)
+    N = float(1 << n)
+    red = [r["ms"] for r in recs if r["kind"] == q.K_REDUCE]
+    col = [r["ms"] for r in recs if r["kind"] == q.K_OTHER]
+    out = {"n": n, "ms_per_measurement": dt * 1e3, "measurements_per_s": 1.0 / dt}
+    if red:
+        ms = float(np.mean(red))
+        out["marginal"] = {"avg_ms": ms, "gbs": 16 * N / (ms * 1e-3) / 1e9, "frac_of_hbm": 16 * N / (ms * 1e-3) / 1e9 / hbm_peak}
+    if col:
+        ms = float(np.mean(col))
+        out["collapse"] = {"avg_ms": ms, "gbs": 24 * N / (ms * 1e-3) / 1e9, "frac_of_hbm": 24 * N / (ms * 1e-3) / 1e9 / hbm_peak}
+    return out
+
+
 def bench_learned_plan(q, torch, stream):
     """n=32 (64 GiB), 2000 random gates (40 % two-qubit, seed 2): greedy plan vs
     the learned plan (cost model from paper_2212_14201_gb300/costmodel_weights.json)
@@ -448,6 +484,7 @@ def run_ours(args, world, rank, local, pg):
         torch.cuda.empty_cache()
         extra["batched_vqe"] = bench_batched_vqe(q, torch, 3, 3)
         extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2)
+        extra["measure_n30"] = bench_measure(q, torch, stream, hbm_peak)
         if not args.no_n32:
             try:
                 extra["learned_n32"] = bench_learned_plan(q, torch, stream)

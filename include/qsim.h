@@ -34,7 +34,7 @@ extern "C" {
 #define QS_ERR_INVALID_ARG (-1)  /* bad qubit index, overlapping targets/controls, size out of range */
 #define QS_ERR_OOM (-2)          /* a device or host allocation failed */
 #define QS_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed */
-#define QS_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
+#define QS_ERR_TIMEOUT (-4)      /* a bounded wait or loop gave up */
 #define QS_ERR_UNSUPPORTED (-5)  /* well-formed request outside what is implemented */
 
 /* ---- gate codes: the paper's gate set (API keyword list and the "Performance
@@ -329,6 +329,60 @@ int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, const double* 
  * fused kernel per gate.  Same results up to rounding; the switch is for
  * measurement. */
 int qs_set_adjoint_fused(int on);
+
+/* ---- mid-circuit measurement and classical control (QMeasure, QIf, QWhile and
+ * ClassicalProg of Section "Core" and its QIf / QWhile listings; classical
+ * operators per Section "Qif and QWhile") ----------------------------------- */
+
+/* Projective measurement of `qubit` with the caller's draw u in [0, 1):
+ * p0, p1 = squared norms of the parts of the state with the qubit 0 / 1;
+ * *outcome = 0 if u (p0 + p1) < p0, else 1; the state collapses in place (the
+ * other part set to 0, the kept part scaled by 1 / sqrt(p_outcome)).  *p1
+ * (nullable) receives p1 / (p0 + p1).  Two passes over the state (reduction,
+ * collapse); synchronous.  Errors: INVALID_ARG (qubit, u, zero state), CUDA. */
+int qs_measure(qs_state* s, int qubit, double u, int* outcome, double* p1);
+
+/* One instruction of a structured program (56 bytes).  Blocks nest by length:
+ * an IF at index i owns the n_then instructions after it (then-block) and the
+ * n_else after those (else-block); a WHILE owns the n_then after it (body).
+ * Operands lhs / rhs name a classical register (int64), or -1 for `imm`.       */
+typedef struct qs_pinstr {
+  int32_t op;        /* QS_PI_* */
+  int32_t qubit;     /* MEASURE: measured qubit */
+  int32_t dst;       /* MEASURE / ASSIGN: register written */
+  int32_t alu;       /* ASSIGN: QS_CA_* */
+  int32_t lhs, rhs;  /* operands (register index or -1) */
+  int64_t imm;       /* immediate operand */
+  uint32_t n_then;   /* IF: then-block length; WHILE: body length */
+  uint32_t n_else;   /* IF: else-block length; WHILE: 0 */
+  uint64_t gate_begin, gate_end; /* GATES: gates[gate_begin .. gate_end) */
+} qs_pinstr;
+
+enum { QS_PI_GATES = 0, QS_PI_MEASURE = 1, QS_PI_ASSIGN = 2, QS_PI_IF = 3, QS_PI_WHILE = 4 };
+/* ASSIGN: dst = lhs OP rhs.  ADD/SUB/MUL wrap (two's complement); DIV truncates
+ * toward zero (division by zero or INT64_MIN / -1 is an error); AND/OR are
+ * logical (result 0/1); XOR bitwise; comparisons give 0/1; NOT = (lhs == 0);
+ * MOV = lhs.  IF and WHILE test lhs != 0, WHILE before every pass. */
+enum {
+  QS_CA_MOV = 0, QS_CA_ADD = 1, QS_CA_SUB = 2, QS_CA_MUL = 3, QS_CA_DIV = 4, QS_CA_AND = 5, QS_CA_OR = 6,
+  QS_CA_XOR = 7, QS_CA_LT = 8, QS_CA_LE = 9, QS_CA_GT = 10, QS_CA_GE = 11, QS_CA_EQ = 12, QS_CA_NE = 13,
+  QS_CA_NOT = 14
+};
+
+/* Run prog[0 .. nprog) on the current contents of s.  GATES applies a range of
+ * `gates` (params as in qs_apply) per gate (fuse == 0) or through a greedy
+ * fusion plan built on the instruction's first execution (fuse != 0).
+ * Measurement k of the run (0-based, in execution order) uses the draw
+ * u_k = (SplitMix64 output k of the stream seeded `seed` >> 11) * 2^-53, as
+ * qs_measure does with that u, and writes the outcome (0/1) to register dst.
+ * cbits: ncbits registers (host, in/out).  record (host, nullable): p1/(p0+p1)
+ * of measurements 0 .. record_cap-1.  *nmeasured (nullable): measurements made
+ * (also on error).  A WHILE that would start pass max_iters+1 stops the run with
+ * TIMEOUT.  Synchronous.  Errors: INVALID_ARG (malformed program, register or
+ * qubit out of range, bad division), TIMEOUT, the errors of qs_apply. */
+int qs_run_program(qs_state* s, const qs_pinstr* prog, size_t nprog, const qs_gate* gates, size_t ngates,
+                   const double* params, int fuse, uint64_t seed, uint64_t max_iters, int64_t* cbits,
+                   size_t ncbits, double* record, size_t record_cap, uint64_t* nmeasured);
 
 /* ---- batched variational evaluation (the hybrid quantum-classical loop of
  * Sections "Support hybrid quantum-classical algorithm" and "Variational

@@ -26,6 +26,10 @@ GATE_DTYPE = np.dtype([
     ("ctrl_mask", "<u8"), ("p", "<f8", (3,)), ("dagger", "<i4"), ("reserved", "<i4"),
 ], align=True)
 PAULI_DTYPE = np.dtype([("coef", "<f8"), ("xmask", "<u8"), ("zmask", "<u8")], align=True)
+PINSTR_DTYPE = np.dtype([
+    ("op", "<i4"), ("qubit", "<i4"), ("dst", "<i4"), ("alu", "<i4"), ("lhs", "<i4"), ("rhs", "<i4"),
+    ("imm", "<i8"), ("n_then", "<u4"), ("n_else", "<u4"), ("gate_begin", "<u8"), ("gate_end", "<u8"),
+], align=True)
 
 
 class QsimError(RuntimeError):
@@ -100,6 +104,8 @@ SIGNATURES = {
     "qs_batch_last_ms": (I32, [P, ctypes.POINTER(DBL)]),
     "qs_batch_info": (I32, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SZ)]),
     "qs_batch_cluster": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
+    "qs_measure": (I32, [P, I32, DBL, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(DBL)]),
+    "qs_run_program": (I32, [P, P, SZ, P, SZ, P, I32, U64, U64, P, SZ, P, SZ, ctypes.POINTER(U64)]),
     "qs_set_batch_cluster": (I32, [I32]),
     "qs_batch_free": (I32, [P]),
     "qs_timing_enable": (I32, [P, I32]),
@@ -244,6 +250,32 @@ def qs_apply(h: int, gates, params=None, plan: int | None = None):
     pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
     _chk(lib().qs_apply(h, g.ctypes.data if len(g) else None, len(g),
                         None if pr is None else pr.ctypes.data, plan))
+
+
+def qs_measure(h: int, qubit: int, u: float):
+    """Projective measurement with the draw u: (outcome, p1 / (p0 + p1))."""
+    o, p1 = ctypes.c_int(), ctypes.c_double()
+    _chk(lib().qs_measure(h, qubit, u, ctypes.byref(o), ctypes.byref(p1)))
+    return o.value, p1.value
+
+
+def qs_run_program(h: int, prog, gates, params=None, fuse: bool = False, seed: int = 0,
+                   max_iters: int = 1 << 20, cbits=None, ncbits: int = 8, record_cap: int = 4096):
+    """Runs a structured program on the state: returns (cbits, record of p1 per
+    measurement)."""
+    pg = np.ascontiguousarray(prog)
+    if pg.dtype != PINSTR_DTYPE:
+        pg = pg.astype(PINSTR_DTYPE)
+    g = as_gates(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    cb = np.zeros(ncbits, dtype=np.int64) if cbits is None else np.array(cbits, dtype=np.int64)
+    rec = np.zeros(record_cap, dtype=np.float64)
+    nm = ctypes.c_uint64()
+    _chk(lib().qs_run_program(h, pg.ctypes.data if len(pg) else None, len(pg), g.ctypes.data if len(g) else None,
+                              len(g), None if pr is None else pr.ctypes.data, 1 if fuse else 0, seed, max_iters,
+                              cb.ctypes.data if len(cb) else None, len(cb), rec.ctypes.data, record_cap,
+                              ctypes.byref(nm)))
+    return cb, rec[:min(nm.value, record_cap)].copy()
 
 
 def qs_apply_matrix(h: int, targets, mat, ctrl_mask: int = 0):

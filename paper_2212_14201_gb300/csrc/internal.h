@@ -41,6 +41,18 @@ struct qs_state {
 
 namespace qs {
 
+// SplitMix64 output number s (0-based) of the stream seeded `seed`, in counter
+// form state = seed + (s + 1) * gamma (Steele, Lea & Flood, OOPSLA 2014), and its
+// mapping to [0, 1): the random draws of sampling and of measurement.
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t s) {
+  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ inline double u01_of(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+
+
 // ---- errors -------------------------------------------------------------------
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);

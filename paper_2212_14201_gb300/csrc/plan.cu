@@ -82,10 +82,11 @@ double op_flops_per_amp(int type) {
   }
 }
 
-// Q60 engine: limb products (3 per real product) per touched amplitude.
+// Q60 tile engine: limb products (3 per real product) per touched amplitude; a
+// general 2x2 row takes its complex products in three real products (Gauss).
 double op_int_ops_per_amp(const Op1& op) {
   switch (op.cls) {
-    case OP_GENERAL: return 24.0;
+    case OP_GENERAL: return 18.0;
     case OP_REAL: return 12.0;
     case OP_PHASE1: return op.code1 == U_GENERAL ? 12.0 : 0.0;
     default: return 6.0 * ((op.code0 == U_GENERAL ? 1.0 : 0.0) + (op.code1 == U_GENERAL ? 1.0 : 0.0));

@@ -19,13 +19,6 @@ namespace qs {
 
 __device__ __forceinline__ double p_exact(double2 a) { return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)); }
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t s) {
-  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 // T[b] = left-to-right block total; lastnz[b] = largest x in block b with p_x > 0, or -1.
 __global__ void k_block_totals(const double2* __restrict__ a, int64_t nb, int64_t L, double* __restrict__ T,
                                long long* __restrict__ lastnz) {
@@ -108,7 +101,7 @@ __global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __res
 __global__ void k_sample(const double2* __restrict__ a, const double* __restrict__ E, const long long* __restrict__ lastnz,
                          int64_t nb, int64_t L, uint64_t seed, uint64_t shots, uint64_t* __restrict__ out) {
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < shots; s += (uint64_t)gridDim.x * blockDim.x) {
-    double u = (double)(splitmix64(seed, s) >> 11) * (1.0 / 9007199254740992.0);
+    double u = u01_of(splitmix64(seed, s));
     int64_t lo = 0, hi = nb;
     while (lo < hi) {
       int64_t mid = lo + ((hi - lo) >> 1);

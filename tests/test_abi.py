@@ -4,6 +4,7 @@ argument validation rejects bad input before any device work."""
 import ctypes
 import glob
 import os
+import subprocess
 import re
 
 import numpy as np
@@ -45,6 +46,28 @@ def test_gate_codes_and_layouts_agree_with_header():
     from paper_2212_14201_gb300 import GATE_DTYPE, PAULI_DTYPE
     assert GATE_DTYPE == w.GATE_DTYPE and GATE_DTYPE.itemsize == 56
     assert PAULI_DTYPE == w.PAULI_DTYPE and PAULI_DTYPE.itemsize == 24
+
+
+def test_program_codes_and_layout_agree_with_header(tmp_path):
+    text = open(os.path.join(ROOT, "include", "qsim.h")).read()
+    for name, code in w.PROGRAM_OPS.items():
+        m = re.search(rf"QS_PI_{name}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == code, name
+    for name, code in w.CLASSICAL_OPS.items():
+        m = re.search(rf"QS_CA_{name}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == code, name
+    from paper_2212_14201_gb300 import PINSTR_DTYPE
+    assert PINSTR_DTYPE == w.PINSTR_DTYPE
+    # the C compiler's layout of qs_pinstr against the numpy record
+    src = tmp_path / "lay.c"
+    fields = ["op", "qubit", "dst", "alu", "lhs", "rhs", "imm", "n_then", "n_else", "gate_begin", "gate_end"]
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "qsim.h"\nint main(void){printf("%zu'
+                   + "".join(" %zu" for _ in fields) + '\\n", sizeof(qs_pinstr)'
+                   + "".join(f", offsetof(qs_pinstr, {f})" for f in fields) + ");return 0;}\n")
+    exe = tmp_path / "lay"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [w.PINSTR_DTYPE.itemsize] + [w.PINSTR_DTYPE.fields[f][1] for f in fields]
 
 
 def test_host_validation_without_gpu(built):
