@@ -327,8 +327,9 @@ def bench_measure(q, torch, stream, hbm_peak: float):
     finally:
         q.qs_free(h)
     N = float(1 << n)
-    red = [r["ms"] for r in recs if r["kind"] == q.K_REDUCE]
-    col = [r["ms"] for r in recs if r["kind"] == q.K_OTHER]
+    from paper_2212_14201_gb300 import _lib
+    red = [r["ms"] for r in recs if r["kind"] == _lib.K_REDUCE]
+    col = [r["ms"] for r in recs if r["kind"] == _lib.K_OTHER]
     out = {"n": n, "ms_per_measurement": dt * 1e3, "measurements_per_s": 1.0 / dt}
     if red:
         ms = float(np.mean(red))
@@ -527,6 +528,7 @@ def run_ours(args, world, rank, local, pg):
         "batched_vqe": extra.get("batched_vqe"),
         "adjoint_n28": extra.get("adjoint_n28"),
         "learned_n32": extra.get("learned_n32"),
+        "measure_n30": extra.get("measure_n30"),
     }
     print(json.dumps(line), flush=True)
 
