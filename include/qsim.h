@@ -194,6 +194,16 @@ int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, q
 int qs_plan_free(qs_plan* p);
 int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
 
+/* Process-wide switch (default on) for gate aggregation inside tile passes (the
+ * paper's Fusion.aggregate_operations, Section "Quantum circuit fusion"): when a
+ * pass is applied, a one-qubit gate whose target and controls no other op of the
+ * pass has touched since the previous op on the same target with the same
+ * controls is multiplied into that op (later gate on the left), if the product's
+ * limb products per amplitude do not exceed the two ops' plus one op's overhead
+ * (6); an identity product is dropped.  Results agree with aggregation off
+ * within rounding (the 2x2 products are formed in double).  Always QS_OK. */
+int qs_set_aggregate(int on);
+
 /* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops
  * of a pass into register phases (runs of ops whose targets fit in `bits` tile
  * qubits execute on the 2^bits amplitudes a thread holds in registers); 0

@@ -89,6 +89,7 @@ SIGNATURES = {
     "qs_adjoint_grad": (I32, [P, P, SZ, P, SZ, P, SZ, ctypes.POINTER(DBL), P]),
     "qs_expect_z_all_noalloc": (I32, [P, I32, P, P]),
     "qs_set_adjoint_fused": (I32, [I32]),
+    "qs_set_aggregate": (I32, [I32]),
     "qs_mlp_create": (I32, [I32, I32, P, U64, PP]),
     "qs_mlp_free": (I32, [P]),
     "qs_mlp_num_weights": (I32, [P, ctypes.POINTER(SZ)]),
@@ -300,6 +301,10 @@ def qs_plan_create(n: int, gates, mode: int = PLAN_GREEDY, kmax: int = 5) -> int
 
 def qs_set_adjoint_fused(on: bool):
     _chk(lib().qs_set_adjoint_fused(1 if on else 0))
+
+
+def qs_set_aggregate(on: bool):
+    _chk(lib().qs_set_aggregate(1 if on else 0))
 
 
 def qs_set_register_phases(bits: int):

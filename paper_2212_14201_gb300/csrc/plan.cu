@@ -104,6 +104,81 @@ double op_touch_fraction(const qs_gate& g, uint64_t cmask) {
 
 namespace qs {
 
+// Class-based figures of a resolved (possibly merged) op, per touched amplitude:
+// FP64 flops and Q60 limb products, and the fraction of amplitudes it touches.
+static double class_flops_per_amp(const Op1& op) {
+  const int g0 = op.code0 == U_GENERAL, g1 = op.code1 == U_GENERAL;
+  switch (op.cls) {
+    case OP_GENERAL: return 14.0;
+    case OP_REAL: return 6.0;
+    case OP_PHASE1: return g1 ? 6.0 : 0.0;
+    default: return 3.0 * (g0 + g1);  // DIAG / ANTI: a complex multiply on the general half
+  }
+}
+
+static double class_touch_fraction(const Op1& op) {
+  const double f = 1.0 / (double)(1ull << __builtin_popcountll(op.cmask));
+  return op.cls == OP_PHASE1 ? 0.5 * f : f;
+}
+
+// Work of one op inside a tile pass in limb products per amplitude, plus the
+// fixed cost of one more op (its shared-memory sweep, barrier and limb splits),
+// in the same units: the yardstick of the merge rule below.
+constexpr double kOpOverheadPerAmp = 6.0;
+
+static Mat2 mat_mul(const Mat2& a, const Mat2& b) {  // a * b
+  Mat2 r;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      const C2 x = a.m[2 * i], y = b.m[j], u = a.m[2 * i + 1], v = b.m[2 + j];
+      r.m[2 * i + j] = {x.re * y.re - x.im * y.im + u.re * v.re - u.im * v.im,
+                        x.re * y.im + x.im * y.re + u.re * v.im + u.im * v.re};
+    }
+  return r;
+}
+
+// Aggregation of a pass's gates into fewer unitaries (the paper's
+// Fusion.aggregate_operations, Section "Quantum circuit fusion"): a one-qubit gate
+// whose target and controls no other op of the pass has touched since the last
+// op on the same target with the same controls is multiplied into that op, when
+// the product costs no more than the two ops did (counting one op's overhead).
+// Ops are kept in pass order; a product that is the identity is dropped.
+static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const double* params,
+                          std::vector<Op1>* out, int* merged) {
+  std::vector<Op1>& ops = *out;
+  ops.clear();
+  std::vector<int> last(n, -1);
+  *merged = 0;
+  for (uint32_t k : ps.gates) {
+    int t;
+    uint64_t cm;
+    Mat2 mat;
+    QS_TRY(gate_qubits(gates[k], n, &t, &cm));
+    QS_TRY(gate_matrix(gates[k], params, &mat));
+    const Op1 op = classify(t, cm, mat);
+    if (op.cls == OP_IDENTITY) continue;
+    const uint64_t touch = cm | (1ull << t);
+    const int p = last[t];
+    bool can = p >= 0 && ops[p].target == t && ops[p].cmask == cm;
+    for (uint64_t r = touch; can && r; r &= r - 1)
+      if (last[__builtin_ctzll(r)] != p) can = false;
+    if (can) {
+      const Op1 mo = classify(t, cm, mat_mul(mat, ops[p].m));
+      const double before = op_int_ops_per_amp(ops[p]) * class_touch_fraction(ops[p]) +
+                            op_int_ops_per_amp(op) * class_touch_fraction(op) + kOpOverheadPerAmp;
+      const double after = mo.cls == OP_IDENTITY ? 0.0 : op_int_ops_per_amp(mo) * class_touch_fraction(mo);
+      if (after <= before) {
+        ops[p] = mo;
+        ++*merged;
+        continue;
+      }
+    }
+    ops.push_back(op);
+    for (uint64_t r = touch; r; r &= r - 1) last[__builtin_ctzll(r)] = (int)ops.size() - 1;
+  }
+  return QS_OK;
+}
+
 uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
                      const std::vector<uint32_t>& remaining, int m, uint64_t low, int max_ops,
                      std::vector<uint32_t>& pass, std::vector<uint32_t>& rest) {
@@ -346,6 +421,12 @@ extern "C" int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint6
 // bits with unused tile bits (highest first, which keeps shared-memory accesses of
 // a warp on consecutive low bits).  g_register_bits = 0 disables the phases.
 static int g_register_bits = 0;
+static bool g_aggregate = true;
+
+extern "C" int qs_set_aggregate(int on) {
+  g_aggregate = on != 0;
+  return QS_OK;
+}
 
 static void build_phases(TileArgs* g, int rb) {
   int np = 0;
@@ -408,22 +489,33 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   g->nops = 0;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
-  int rc = QS_OK;
-  for (uint32_t k : ps.gates) {
-    int t;
-    uint64_t cm;
-    Mat2 mat;
-    if ((rc = gate_qubits(gates[k], n, &t, &cm)) != QS_OK) break;
-    if ((rc = gate_matrix(gates[k], params, &mat)) != QS_OK) break;
-    Op1 op = classify(t, cm, mat);
+  std::vector<Op1> rops;
+  int merged = 0;
+  int rc = g_aggregate ? aggregate_pass(n, ps, gates, params, &rops, &merged) : QS_OK;
+  if (!g_aggregate) {
+    for (uint32_t k : ps.gates) {
+      int t;
+      uint64_t cm;
+      Mat2 mat;
+      if ((rc = gate_qubits(gates[k], n, &t, &cm)) != QS_OK) break;
+      if ((rc = gate_matrix(gates[k], params, &mat)) != QS_OK) break;
+      const Op1 op = classify(t, cm, mat);
+      if (op.cls != OP_IDENTITY) rops.push_back(op);
+    }
+  }
+  for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
+    const Op1& op = rops[i];
     if (op.cls == OP_IDENTITY) continue;
+    const Mat2& mat = op.m;
+    const int t = op.target;
+    const uint64_t cm = op.cmask;
     TileOp& to = g->ops[g->nops];
     if (fixed && op.cls == OP_GENERAL)  // three limb products per complex product
-      for (int i = 0; i < 4; ++i) to.q[i] = qc_make_gauss(mat.m[i].re, mat.m[i].im);
+      for (int e = 0; e < 4; ++e) to.q[e] = qc_make_gauss(mat.m[e].re, mat.m[e].im);
     else if (fixed)
-      for (int i = 0; i < 4; ++i) to.q[i] = qc_make(mat.m[i].re, mat.m[i].im);
+      for (int e = 0; e < 4; ++e) to.q[e] = qc_make(mat.m[e].re, mat.m[e].im);
     else
-      for (int i = 0; i < 4; ++i) to.m[i] = make_double2(mat.m[i].re, mat.m[i].im);
+      for (int e = 0; e < 4; ++e) to.m[e] = make_double2(mat.m[e].re, mat.m[e].im);
     to.code0 = (int8_t)op.code0;
     to.code1 = (int8_t)op.code1;
     uint32_t lcm = 0;
@@ -440,14 +532,14 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       to.tb = (int8_t)local[t];
     } else {
       if (op.cls != OP_PHASE1 && op.cls != OP_DIAG) {
-        rc = fail(QS_ERR_INVALID_ARG, "plan does not match the program (non-diagonal gate %u outside its tile)", k);
+        rc = fail(QS_ERR_INVALID_ARG, "plan does not match the program (non-diagonal op on qubit %d outside its tile)", t);
         break;
       }
       to.kind = TOP_SCALAR;
       to.tb = (int8_t)t;
     }
-    flops += N * op_touch_fraction(gates[k], cm) * op_flops_per_amp(gates[k].type);
-    int_ops += N * op_touch_fraction(gates[k], cm) * op_int_ops_per_amp(op);
+    flops += N * class_touch_fraction(op) * class_flops_per_amp(op);
+    int_ops += N * class_touch_fraction(op) * op_int_ops_per_amp(op);
     ++g->nops;
   }
   g->nphases = 0;

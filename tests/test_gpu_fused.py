@@ -148,3 +148,59 @@ def test_register_phase_kernels(q, orc, bits):
             assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
     finally:
         q.qs_set_register_phases(0)
+
+
+def run_chain_circuit(n, seed):
+    """Runs of one-qubit gates on one qubit (some with the same extra control),
+    self-cancelling pairs (H H, X X, S then S-dagger) and a two-qubit gate now and
+    then: material for the aggregation of a pass's gates into fewer unitaries."""
+    rng = w.SplitMix64(seed)
+    recs = []
+    for _ in range(60):
+        t = rng.below(n)
+        c = (t + 1 + rng.below(n - 1)) % n
+        k = rng.below(8)
+        if k < 4:
+            cm = (1 << c) if k == 3 else 0
+            for _ in range(2 + rng.below(4)):
+                name = w.ONE_QUBIT[rng.below(len(w.ONE_QUBIT))]
+                recs.append(w.gate(name, t, theta=rng.angle(), phi=rng.angle(), lam=rng.angle(), ctrl_mask=cm))
+        elif k == 4:
+            name = ("H", "X", "S")[rng.below(3)]
+            recs.append(w.gate(name, t))
+            recs.append(w.gate(name, t, dagger=1))
+        elif k == 5:
+            recs.append(w.gate("RZ", t, theta=rng.angle()))
+            recs.append(w.gate("T", t))
+            recs.append(w.gate("P", t, theta=rng.angle()))
+        else:
+            recs.append(w.gate(("CNOT", "CZ", "CR")[rng.below(3)], c, t, theta=rng.angle()))
+    return w.pack(recs)
+
+
+@pytest.mark.parametrize("n", [3, 9, 14])
+def test_aggregation_matches_oracle_and_reduces_work(q, orc, arith, n):
+    """Fused apply with gate aggregation on and off against the oracle (1e-12),
+    and the aggregated passes do fewer limb products / flops (timing log)."""
+    g = run_chain_circuit(n, 40 + n)
+    ref = orc.as_complex(orc.run(n, g))
+    work = {}
+    try:
+        for on in (True, False):
+            q.qs_set_aggregate(on)
+            p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+            h = q.qs_alloc(n)
+            try:
+                q.qs_set_arith(h, arith)
+                q.qs_timing_enable(h, True)
+                q.qs_apply(h, g, None, p)
+                recs = q.qs_timing_fetch(h)
+                got = q.qs_get_state(h)
+            finally:
+                q.qs_free(h)
+                q.qs_plan_free(p)
+            assert np.max(np.abs(got - ref)) < TOL, on
+            work[on] = sum(r["int_ops"] + r["flops"] for r in recs if r["kind"] == q._lib.K_TILE)
+    finally:
+        q.qs_set_aggregate(True)
+    assert work[True] < 0.9 * work[False]
