@@ -137,18 +137,24 @@ static Mat2 mat_mul(const Mat2& a, const Mat2& b) {  // a * b
   return r;
 }
 
+static bool is_diagonal(const Op1& op) { return op.cls == OP_PHASE1 || op.cls == OP_DIAG || op.cls == OP_IDENTITY; }
+
 // Aggregation of a pass's gates into fewer unitaries (the paper's
-// Fusion.aggregate_operations, Section "Quantum circuit fusion"): a one-qubit gate
-// whose target and controls no other op of the pass has touched since the last
-// op on the same target with the same controls is multiplied into that op, when
-// the product costs no more than the two ops did (counting one op's overhead).
-// Ops are kept in pass order; a product that is the identity is dropped.
+// Fusion.aggregate_operations, Section "Quantum circuit fusion").  A one-qubit
+// gate g (target t, controls C) is multiplied into an earlier op p of the pass
+// with the same target and controls when every op between them commutes with g:
+//   - an op that touches none of t and C commutes;
+//   - if g is diagonal, so does an op that is diagonal itself or whose target is
+//     not among t and C (it uses them as controls only: block-diagonal there);
+// and the product costs no more limb products per amplitude than the two ops did,
+// plus one op's overhead.  g then moves back to p (past ops it commutes with) and
+// p becomes g * p.  Ops stay in pass order; an identity product is dropped.
 static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const double* params,
                           std::vector<Op1>* out, int* merged) {
   std::vector<Op1>& ops = *out;
   ops.clear();
-  std::vector<int> last(n, -1);
   *merged = 0;
+  (void)n;
   for (uint32_t k : ps.gates) {
     int t;
     uint64_t cm;
@@ -158,11 +164,20 @@ static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const
     const Op1 op = classify(t, cm, mat);
     if (op.cls == OP_IDENTITY) continue;
     const uint64_t touch = cm | (1ull << t);
-    const int p = last[t];
-    bool can = p >= 0 && ops[p].target == t && ops[p].cmask == cm;
-    for (uint64_t r = touch; can && r; r &= r - 1)
-      if (last[__builtin_ctzll(r)] != p) can = false;
-    if (can) {
+    const bool diag = is_diagonal(op);
+    int p = -1;
+    for (int j = (int)ops.size() - 1; j >= 0; --j) {
+      const Op1& o = ops[j];
+      const uint64_t otouch = o.cmask | (1ull << o.target);
+      if (!(otouch & touch)) continue;
+      if (o.target == t && o.cmask == cm) {
+        p = j;
+        break;
+      }
+      if (diag && (is_diagonal(o) || !((touch >> o.target) & 1))) continue;
+      break;
+    }
+    if (p >= 0) {
       const Op1 mo = classify(t, cm, mat_mul(mat, ops[p].m));
       const double before = op_int_ops_per_amp(ops[p]) * class_touch_fraction(ops[p]) +
                             op_int_ops_per_amp(op) * class_touch_fraction(op) + kOpOverheadPerAmp;
@@ -174,7 +189,6 @@ static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const
       }
     }
     ops.push_back(op);
-    for (uint64_t r = touch; r; r &= r - 1) last[__builtin_ctzll(r)] = (int)ops.size() - 1;
   }
   return QS_OK;
 }

@@ -152,8 +152,10 @@ def test_register_phase_kernels(q, orc, bits):
 
 def run_chain_circuit(n, seed):
     """Runs of one-qubit gates on one qubit (some with the same extra control),
-    self-cancelling pairs (H H, X X, S then S-dagger) and a two-qubit gate now and
-    then: material for the aggregation of a pass's gates into fewer unitaries."""
+    self-cancelling pairs (H H, X X, S then S-dagger), diagonal gates separated by
+    gates they commute with (CZ, a CNOT controlled on the same qubit) and a
+    two-qubit gate now and then: material for the aggregation of a pass's gates
+    into fewer unitaries."""
     rng = w.SplitMix64(seed)
     recs = []
     for _ in range(60):
@@ -171,6 +173,7 @@ def run_chain_circuit(n, seed):
             recs.append(w.gate(name, t, dagger=1))
         elif k == 5:
             recs.append(w.gate("RZ", t, theta=rng.angle()))
+            recs.append(w.gate("CZ", c, t) if rng.below(2) else w.gate("CNOT", t, c))
             recs.append(w.gate("T", t))
             recs.append(w.gate("P", t, theta=rng.angle()))
         else:
