@@ -345,6 +345,52 @@ def bench_measure(q, torch, stream, hbm_peak: float):
     return out
 
 
+# FP32 peak derived from unit counts and clock: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz.
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
+
+
+def bench_c64(q, torch, stream, hbm_peak: float, steps: int = 3):
+    """The complex64 variant on the config-1 circuit (n=30, 8 GiB state): greedy
+    plan, FP32 tile passes.  Algorithmic bytes per tile pass: 16 per amplitude
+    (8 read + 8 written); flops per amplitude: 14 per U3."""
+    from paper_2212_14201_gb300 import _lib
+    n = 30
+    g = w.layered_u3_cz(n, 20, 1)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc_c64(n, stream)
+    try:
+        q.qs_apply(h, g, None, p)
+        q.qs_timing_enable(h, True)
+        q.qs_timing_fetch(h)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            q.qs_set_zero(h)
+            q.qs_apply(h, g, None, p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        recs = q.qs_timing_fetch(h)
+        q.qs_timing_enable(h, False)
+        norm2 = float(q.qs_probs(h, [])[0])
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(p)
+    tiles = [r for r in recs if r["kind"] == _lib.K_TILE]
+    out = {"n": n, "gates": len(g), "ms_per_apply": ms, "amp_updates_per_s": len(g) * float(1 << n) / (ms * 1e-3),
+           "norm2": norm2}
+    if tiles:
+        tms = float(np.mean([r["ms"] for r in tiles]))
+        fl = float(np.mean([r["flops"] for r in tiles]))
+        gbs = 16.0 * float(1 << n) / (tms * 1e-3) / 1e9
+        tf = fl / (tms * 1e-3) / 1e12
+        out["tile_pass"] = {"avg_ms": tms, "launches_per_apply": len(tiles) // steps,
+                            "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                            "fp32_tflops": tf, "fp32_frac": tf / (FP32_PEAK_FLOPS / 1e12)}
+    return out
+
+
 def bench_learned_plan(q, torch, stream):
     """n=32 (64 GiB), 2000 random gates (40 % two-qubit, seed 2): greedy plan vs
     the learned plan (cost model from paper_2212_14201_gb300/costmodel_weights.json)
@@ -491,6 +537,7 @@ def run_ours(args, world, rank, local, pg):
         extra["batched_vqe"] = bench_batched_vqe(q, torch, 3, 3)
         extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2)
         extra["measure_n30"] = bench_measure(q, torch, stream, hbm_peak)
+        extra["c64_n30"] = bench_c64(q, torch, stream, hbm_peak)
         if not args.no_n32:
             try:
                 extra["learned_n32"] = bench_learned_plan(q, torch, stream)
@@ -534,6 +581,7 @@ def run_ours(args, world, rank, local, pg):
         "adjoint_n28": extra.get("adjoint_n28"),
         "learned_n32": extra.get("learned_n32"),
         "measure_n30": extra.get("measure_n30"),
+        "c64_n30": extra.get("c64_n30"),
     }
     print(json.dumps(line), flush=True)
 

@@ -107,6 +107,20 @@ int qs_alloc(int n, void* stream, qs_state** out);
  * Errors: INVALID_ARG (n out of range, NULL or misaligned pointer), OOM, CUDA. */
 int qs_alloc_external(int n, void* device_amps, void* stream, qs_state** out);
 
+/* Allocate an n-qubit complex64 state (2^n interleaved float pairs, 8 bytes
+ * per amplitude), initialised to |0...0>.  The complex64 variant of the path:
+ * gates compute in FP32 (per-gate kernels and tile passes, matrices rounded to
+ * float from their double form); probabilities, marginals, expectations, the
+ * canonical sampler and measurement widen each component to double (exact) and
+ * compute as for complex128, so sampling is the same definition on the stored
+ * state.  qs_set_state / qs_get_state move float data for these states.
+ * qs_apply_matrix, qs_adjoint_grad and QS_ARITH_FIXED return UNSUPPORTED.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int qs_alloc_c64(int n, void* stream, qs_state** out);
+
+/* *bits = 128 (complex128 state) or 64 (complex64 state). */
+int qs_state_precision(const qs_state* s, int* bits);
+
 /* Release a state (waits for its stream first).  NULL is accepted. */
 int qs_free(qs_state* s);
 
@@ -117,11 +131,13 @@ int qs_device_ptr(const qs_state* s, void** out);
 /* Reset to |0...0>. */
 int qs_set_zero(qs_state* s);
 
-/* Copy 2^n interleaved complex128 amplitudes in from `amps` (device memory if
- * on_device != 0, else host memory; synchronous for host memory). */
+/* Copy 2^n interleaved amplitudes in from `amps` (device memory if on_device !=
+ * 0, else host memory; synchronous for host memory): complex128 (double pairs),
+ * or float pairs for a complex64 state (the pointer is then read as float). */
 int qs_set_state(qs_state* s, const double* amps, int on_device);
 
-/* Copy the 2^n amplitudes out to `dst` (device or host memory). */
+/* Copy the 2^n amplitudes out to `dst` (device or host memory), in the state's
+ * own precision (float pairs for a complex64 state). */
 int qs_get_state(const qs_state* s, double* dst, int on_device);
 
 /* Wait for all work queued on the state's stream. */

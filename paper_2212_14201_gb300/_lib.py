@@ -62,6 +62,8 @@ SIGNATURES = {
     "qs_max_qubits": (I32, []),
     "qs_alloc": (I32, [I32, P, PP]),
     "qs_alloc_external": (I32, [I32, P, P, PP]),
+    "qs_alloc_c64": (I32, [I32, P, PP]),
+    "qs_state_precision": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
     "qs_free": (I32, [P]),
     "qs_num_qubits": (I32, [P]),
     "qs_device_ptr": (I32, [P, PP]),
@@ -215,17 +217,42 @@ def qs_set_zero(h: int):
     _chk(lib().qs_set_zero(h))
 
 
+def qs_alloc_c64(n: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _chk(lib().qs_alloc_c64(n, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qs_state_precision(h: int) -> int:
+    b = ctypes.c_int()
+    _chk(lib().qs_state_precision(h, ctypes.byref(b)))
+    return b.value
+
+
+def _check_amps(h: int, x):
+    """The buffer's element size must match the state's precision and length."""
+    n = qs_num_qubits(h)
+    bits = qs_state_precision(h)
+    item = x.itemsize if isinstance(x, np.ndarray) else x.element_size()
+    numel = x.size if isinstance(x, np.ndarray) else x.numel()
+    comp = 8 if bits == 128 else 4            # bytes per real component
+    if item not in (comp, 2 * comp) or numel * item != (2 << n) * comp:
+        raise ValueError(f"buffer does not hold 2^{n} complex{bits} amplitudes")
+
+
 def qs_set_state(h: int, amps):
+    _check_amps(h, amps)
     ptr, dev = _host_or_dev(amps)
     _chk(lib().qs_set_state(h, ptr, dev))
 
 
 def qs_get_state(h: int, out=None):
-    """Copy the amplitudes into `out` (numpy float64 / complex128 array or device
-    tensor); with out=None returns a new numpy complex128 array."""
+    """Copy the amplitudes into `out` (numpy array or device tensor of the state's
+    precision); with out=None returns a new numpy complex128 (or complex64) array."""
     if out is None:
         n = qs_num_qubits(h)
-        out = np.empty(1 << n, dtype=np.complex128)
+        out = np.empty(1 << n, dtype=np.complex64 if qs_state_precision(h) == 64 else np.complex128)
+    _check_amps(h, out)
     ptr, dev = _host_or_dev(out)
     _chk(lib().qs_get_state(h, ptr, dev))
     return out

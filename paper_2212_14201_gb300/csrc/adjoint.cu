@@ -516,6 +516,7 @@ extern "C" int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, con
                                const qs_pauli* terms, size_t nterms, double* energy, double* grad) {
   clear_error();
   QS_TRY(check_state(s));
+  if (s->prec == 64) return fail(QS_ERR_UNSUPPORTED, "adjoint gradients need a complex128 state");
   if (!energy || (np && !grad) || (nterms && !terms)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
   QS_TRY(validate_gates(gates, ng, s->n, params));
   const uint64_t full = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);

@@ -93,6 +93,68 @@ __global__ void __launch_bounds__(256) k_op1(double2* __restrict__ a, const OpAr
   }
 }
 
+// ---- complex64 states: the same ops in FP32 ----------------------------------------
+struct OpArgs32 {
+  float2 m[4];
+  uint64_t cmask;
+  int64_t items;
+  int t;
+  int nfix;
+  int fix[16];
+  int code0, code1;
+};
+
+__device__ __forceinline__ float2 mul_unit32(float2 a, int code) {
+  switch (code) {
+    case U_ONE: return a;
+    case U_I: return make_float2(-a.y, a.x);
+    case U_MINUS_ONE: return make_float2(-a.x, -a.y);
+    default: return make_float2(a.y, -a.x);
+  }
+}
+
+__device__ __forceinline__ float2 mul_code32(float2 a, int code, float2 u) {
+  return code == U_GENERAL ? make_float2(fmaf(u.x, a.x, -u.y * a.y), fmaf(u.x, a.y, u.y * a.x)) : mul_unit32(a, code);
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(256) k_op1_c64(float2* __restrict__ a, const OpArgs32 g) {
+  const uint64_t tb = 1ull << g.t;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (uint64_t)g.items; i += stride) {
+    uint64_t x0 = i;
+    for (int k = 0; k < g.nfix; ++k) {
+      const int f = g.fix[k];
+      x0 = ((x0 >> f) << (f + 1)) | (x0 & ((1ull << f) - 1));
+    }
+    x0 |= g.cmask;
+    const uint64_t x1 = x0 | tb;
+    if (CLS == OP_PHASE1) {
+      a[x1] = mul_code32(a[x1], g.code1, g.m[3]);
+      continue;
+    }
+    const float2 a0 = a[x0], a1 = a[x1];
+    float2 b0, b1;
+    if (CLS == OP_DIAG) {
+      b0 = mul_code32(a0, g.code0, g.m[0]);
+      b1 = mul_code32(a1, g.code1, g.m[3]);
+    } else if (CLS == OP_ANTI) {
+      b0 = mul_code32(a1, g.code0, g.m[1]);
+      b1 = mul_code32(a0, g.code1, g.m[2]);
+    } else if (CLS == OP_REAL) {
+      b0 = make_float2(fmaf(g.m[0].x, a0.x, g.m[1].x * a1.x), fmaf(g.m[0].x, a0.y, g.m[1].x * a1.y));
+      b1 = make_float2(fmaf(g.m[2].x, a0.x, g.m[3].x * a1.x), fmaf(g.m[2].x, a0.y, g.m[3].x * a1.y));
+    } else {
+      b0.x = fmaf(g.m[0].x, a0.x, fmaf(-g.m[0].y, a0.y, fmaf(g.m[1].x, a1.x, -g.m[1].y * a1.y)));
+      b0.y = fmaf(g.m[0].x, a0.y, fmaf(g.m[0].y, a0.x, fmaf(g.m[1].x, a1.y, g.m[1].y * a1.x)));
+      b1.x = fmaf(g.m[2].x, a0.x, fmaf(-g.m[2].y, a0.y, fmaf(g.m[3].x, a1.x, -g.m[3].y * a1.y)));
+      b1.y = fmaf(g.m[2].x, a0.y, fmaf(g.m[2].y, a0.x, fmaf(g.m[3].x, a1.y, g.m[3].y * a1.x)));
+    }
+    a[x0] = b0;
+    a[x1] = b1;
+  }
+}
+
 // ---- Q60 fixed-point variant (arithmetic on the integer pipe; see fixed.h) --------
 struct OpArgsFx {
   QC u[4];
@@ -200,8 +262,43 @@ static bool needs_arith(const Op1& op) {
   return op.code0 == U_GENERAL || op.code1 == U_GENERAL;
 }
 
+static int launch_op1_c64(qs_state* s, const Op1& op) {
+  OpArgs32 g;
+  for (int i = 0; i < 4; ++i) g.m[i] = make_float2((float)op.m.m[i].re, (float)op.m.m[i].im);
+  g.cmask = op.cmask;
+  g.t = op.target;
+  g.code0 = op.code0;
+  g.code1 = op.code1;
+  const uint64_t fixbits = op.cmask | (1ull << op.target);
+  const int nf = __builtin_popcountll(fixbits);
+  if (nf > 16) return fail(QS_ERR_UNSUPPORTED, "more than 15 controls");
+  g.nfix = 0;
+  for (int b = 0; b < 64; ++b)
+    if ((fixbits >> b) & 1) g.fix[g.nfix++] = b;
+  g.items = (int64_t)1 << (s->n - nf);
+  const int T = 256;
+  const int grid = grid_for(g.items, T);
+  const double amps = op.cls == OP_PHASE1 ? (double)g.items : 2.0 * (double)g.items;
+  double fpa = 0.0;
+  if (op.cls == OP_GENERAL) fpa = 14.0;
+  else if (op.cls == OP_REAL) fpa = 6.0;
+  else if (op.cls == OP_PHASE1) fpa = op.code1 == U_GENERAL ? 6.0 : 0.0;
+  else fpa = 0.5 * ((op.code0 == U_GENERAL ? 6.0 : 0.0) + (op.code1 == U_GENERAL ? 6.0 : 0.0));
+  KTimer kt(s, op.cls, 1, 1, 1ull << op.target, op.cmask, amps, fpa * amps);
+  float2* a = reinterpret_cast<float2*>(s->amps);
+  switch (op.cls) {
+    case OP_PHASE1: k_op1_c64<OP_PHASE1><<<grid, T, 0, s->stream>>>(a, g); break;
+    case OP_DIAG: k_op1_c64<OP_DIAG><<<grid, T, 0, s->stream>>>(a, g); break;
+    case OP_ANTI: k_op1_c64<OP_ANTI><<<grid, T, 0, s->stream>>>(a, g); break;
+    case OP_REAL: k_op1_c64<OP_REAL><<<grid, T, 0, s->stream>>>(a, g); break;
+    default: k_op1_c64<OP_GENERAL><<<grid, T, 0, s->stream>>>(a, g); break;
+  }
+  return launch_check("op1 kernel (complex64)");
+}
+
 int launch_op1(qs_state* s, const Op1& op, bool fixed) {
   if (op.cls == OP_IDENTITY) return QS_OK;
+  if (s->prec == 64) return launch_op1_c64(s, op);
   if (fixed && needs_arith(op)) {
     OpArgsFx g;
     for (int i = 0; i < 4; ++i) g.u[i] = qc_make(op.m.m[i].re, op.m.m[i].im);
@@ -380,6 +477,7 @@ extern "C" int qs_apply_matrix(qs_state* s, const int* targets, int k, uint64_t 
   clear_error();
   QS_TRY(check_state(s));
   if (!targets || !mat) return fail(QS_ERR_INVALID_ARG, "NULL targets or matrix");
+  if (s->prec == 64) return fail(QS_ERR_UNSUPPORTED, "dense k-qubit matrices need a complex128 state");
   if (k < 1 || k > 5 || k > s->n) return fail(QS_ERR_INVALID_ARG, "k=%d outside 1..min(5, n)", k);
   uint64_t full = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
   uint64_t tm = 0;

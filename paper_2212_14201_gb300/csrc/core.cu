@@ -245,7 +245,13 @@ __global__ void k_set_zero(double2* __restrict__ a, size_t N) {
   for (; i < N; i += stride) a[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
 }
 
-static int create(int n, void* dev, void* stream, qs_state** out) {
+__global__ void k_set_zero(float2* __restrict__ a, size_t N) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < N; i += stride) a[i] = make_float2(i == 0 ? 1.0f : 0.0f, 0.0f);
+}
+
+static int create(int n, void* dev, void* stream, qs_state** out, int prec = 128) {
   clear_error();
   if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -254,9 +260,10 @@ static int create(int n, void* dev, void* stream, qs_state** out) {
   qs_state* s = new (std::nothrow) qs_state;
   if (!s) return fail(QS_ERR_OOM, "host allocation failed");
   s->n = n;
+  s->prec = prec;
   s->stream = (cudaStream_t)stream;
   cudaGetDevice(&s->device);
-  size_t bytes = ((size_t)1 << n) * sizeof(double2);
+  size_t bytes = ((size_t)1 << n) * amp_bytes(s);
   if (dev) {
     s->amps = (double2*)dev;
     s->owns = false;
@@ -285,7 +292,10 @@ extern "C" int qs_set_zero(qs_state* s) {
   size_t N = (size_t)1 << s->n;
   int blocks = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
   KTimer kt(s, QS_K_OTHER, 0, 0, 0, 0, (double)N, 0.0);
-  k_set_zero<<<blocks, 256, 0, s->stream>>>(s->amps, N);
+  with_amps(s, [&](auto* a) {
+    k_set_zero<<<blocks, 256, 0, s->stream>>>(a, N);
+    return QS_OK;
+  });
   s->bound = 1;
   return launch_check("set_zero");
 }
@@ -294,6 +304,8 @@ extern "C" int qs_set_arith(qs_state* s, int mode) {
   QS_TRY(check_state(s));
   if (mode != QS_ARITH_AUTO && mode != QS_ARITH_FP64 && mode != QS_ARITH_FIXED)
     return fail(QS_ERR_INVALID_ARG, "arith mode %d", mode);
+  if (s->prec == 64 && mode == QS_ARITH_FIXED)
+    return fail(QS_ERR_UNSUPPORTED, "complex64 states compute in FP32 (no Q60 engine)");
   s->arith = mode;
   return QS_OK;
 }
@@ -307,7 +319,7 @@ extern "C" int qs_state_modified(qs_state* s) {
 namespace qs {
 int choose_fixed(qs_state* s, bool* fixed) {
   *fixed = false;
-  if (s->arith == QS_ARITH_FP64) return QS_OK;
+  if (s->arith == QS_ARITH_FP64 || s->prec == 64) return QS_OK;
   if (s->bound == 0) {
     double norm2 = 0.0;
     QS_TRY(qs_probs(s, nullptr, 0, &norm2, 0));
@@ -332,6 +344,23 @@ extern "C" int qs_alloc(int n, void* stream, qs_state** out) {
     *out = nullptr;
   }
   return rc;
+}
+
+extern "C" int qs_alloc_c64(int n, void* stream, qs_state** out) {
+  QS_TRY(create(n, nullptr, stream, out, 64));
+  int rc = qs_set_zero(*out);
+  if (rc) {
+    qs_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+extern "C" int qs_state_precision(const qs_state* s, int* bits) {
+  QS_TRY(check_state(s));
+  if (!bits) return fail(QS_ERR_INVALID_ARG, "bits is NULL");
+  *bits = s->prec;
+  return QS_OK;
 }
 
 extern "C" int qs_alloc_external(int n, void* device_amps, void* stream, qs_state** out) {
@@ -369,7 +398,7 @@ extern "C" int qs_device_ptr(const qs_state* s, void** out) {
 extern "C" int qs_set_state(qs_state* s, const double* amps, int on_device) {
   QS_TRY(check_state(s));
   if (!amps) return fail(QS_ERR_INVALID_ARG, "amps is NULL");
-  size_t bytes = ((size_t)1 << s->n) * sizeof(double2);
+  size_t bytes = ((size_t)1 << s->n) * amp_bytes(s);
   QS_CUDA(cudaMemcpyAsync(s->amps, amps, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           s->stream));
   if (!on_device) QS_CUDA(cudaStreamSynchronize(s->stream));
@@ -380,7 +409,7 @@ extern "C" int qs_set_state(qs_state* s, const double* amps, int on_device) {
 extern "C" int qs_get_state(const qs_state* s, double* dst, int on_device) {
   QS_TRY(check_state(s));
   if (!dst) return fail(QS_ERR_INVALID_ARG, "dst is NULL");
-  size_t bytes = ((size_t)1 << s->n) * sizeof(double2);
+  size_t bytes = ((size_t)1 << s->n) * amp_bytes(s);
   QS_CUDA(cudaMemcpyAsync(dst, s->amps, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           s->stream));
   if (!on_device) QS_CUDA(cudaStreamSynchronize(s->stream));

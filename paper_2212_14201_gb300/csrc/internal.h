@@ -18,7 +18,10 @@ struct qs_pending_timing {
 
 struct qs_state {
   int n = 0;
-  double2* amps = nullptr;  // 2^n amplitudes, device
+  // 2^n amplitudes, device: complex128 (double2) when prec == 128, complex64
+  // (float2, same pointer reinterpreted) when prec == 64
+  double2* amps = nullptr;
+  int prec = 128;
   bool owns = false;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -52,6 +55,21 @@ __host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t s) {
 }
 __host__ __device__ inline double u01_of(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
 
+
+// Amplitude access for kernels templated on the stored element type: complex128
+// or complex64, read as a double2 (float -> double is exact).
+__device__ __forceinline__ double2 ld_amp(const double2* a, uint64_t i) { return a[i]; }
+__device__ __forceinline__ double2 ld_amp(const float2* a, uint64_t i) {
+  const float2 v = a[i];
+  return make_double2((double)v.x, (double)v.y);
+}
+inline size_t amp_bytes(const qs_state* s) { return s->prec == 64 ? sizeof(float2) : sizeof(double2); }
+// Calls f with the state's amplitude pointer typed by its precision.
+template <class F>
+int with_amps(const qs_state* s, F&& f) {
+  if (s->prec == 64) return f(reinterpret_cast<float2*>(s->amps));
+  return f(s->amps);
+}
 
 // ---- errors -------------------------------------------------------------------
 int fail(int code, const char* fmt, ...);
@@ -112,7 +130,7 @@ int unit_code(const C2& z);
 // Whether the next gate kernels of this state run in Q60 fixed point (may
 // synchronise once to bound an unknown state's magnitude).
 int choose_fixed(qs_state* s, bool* fixed);
-int launch_op1(qs_state* s, const Op1& op, bool fixed);
+int launch_op1(qs_state* s, const Op1& op, bool fixed);  // complex64 states: FP32 arithmetic
 int launch_dense(qs_state* s, const int* targets, int k, uint64_t cmask, const C2* mat);
 
 // ---- planning ------------------------------------------------------------------

@@ -524,7 +524,9 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     const int t = op.target;
     const uint64_t cm = op.cmask;
     TileOp& to = g->ops[g->nops];
-    if (fixed && op.cls == OP_GENERAL)  // three limb products per complex product
+    if (s->prec == 64)
+      for (int e = 0; e < 4; ++e) to.f[e] = make_float2((float)mat.m[e].re, (float)mat.m[e].im);
+    else if (fixed && op.cls == OP_GENERAL)  // three limb products per complex product
       for (int e = 0; e < 4; ++e) to.q[e] = qc_make_gauss(mat.m[e].re, mat.m[e].im);
     else if (fixed)
       for (int e = 0; e < 4; ++e) to.q[e] = qc_make(mat.m[e].re, mat.m[e].im);

@@ -20,15 +20,18 @@
 
 namespace qs {
 
-// a_x *= scale where (x & mask) == want; a_x = 0 elsewhere.
-__global__ void k_collapse(double2* __restrict__ a, uint64_t N, uint64_t mask, uint64_t want, double scale) {
+// a_x *= scale where (x & mask) == want; a_x = 0 elsewhere (complex128, or
+// complex64 scaled in double and rounded once).
+__device__ __forceinline__ double2 scaled(double2 v, double c) { return make_double2(v.x * c, v.y * c); }
+__device__ __forceinline__ float2 scaled(float2 v, double c) {
+  return make_float2((float)((double)v.x * c), (float)((double)v.y * c));
+}
+
+template <class A>
+__global__ void k_collapse(A* __restrict__ a, uint64_t N, uint64_t mask, uint64_t want, double scale) {
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
-    if ((x & mask) == want) {
-      const double2 v = a[x];
-      a[x] = make_double2(v.x * scale, v.y * scale);
-    } else {
-      a[x] = make_double2(0.0, 0.0);
-    }
+    if ((x & mask) == want) a[x] = scaled(a[x], scale);
+    else a[x] = A{};
   }
 }
 
@@ -39,7 +42,10 @@ static int collapse(qs_state* s, uint64_t mask, uint64_t want, double scale) {
   QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
   const uint64_t grid = std::min<uint64_t>((N + T - 1) / T, (uint64_t)std::max(1, sms) * 16);
   KTimer kt(s, QS_K_OTHER, 0, 1, mask, 0, (double)N, 2.0 * (double)(N >> __builtin_popcountll(mask)));
-  k_collapse<<<(unsigned)grid, T, 0, s->stream>>>(s->amps, N, mask, want, scale);
+  with_amps(s, [&](auto* a) {
+    k_collapse<<<(unsigned)grid, T, 0, s->stream>>>(a, N, mask, want, scale);
+    return QS_OK;
+  });
   return launch_check("collapse kernel");
 }
 

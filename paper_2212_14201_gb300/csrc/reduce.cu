@@ -8,6 +8,7 @@
 // final CTA adds them in that order.  Results do not depend on timing.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -15,6 +16,7 @@
 namespace qs {
 
 __device__ __forceinline__ double prob(double2 a) { return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)); }
+__device__ __forceinline__ double acc_prob(double2 a, double s) { return fma(a.y, a.y, fma(a.x, a.x, s)); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -37,25 +39,29 @@ __device__ double block_sum256(double v, double* sh) {
 
 // ---- full probability vector -------------------------------------------------------
 // per-CTA partial sums of |a_x|^2 (four interleaved accumulators per thread)
-__global__ void __launch_bounds__(256) k_norm2(const double2* __restrict__ a, uint64_t N, double* __restrict__ part) {
+template <class T>
+__global__ void __launch_bounds__(256) k_norm2(const T* __restrict__ a, uint64_t N, double* __restrict__ part) {
   __shared__ double sh[8];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  // |a|^2 accumulated as two fused multiply-adds (two FP64 instructions per
+  // amplitude: the FP64 pipe, not HBM, bounds this kernel on GB300)
   for (; i + 3 * stride < N; i += 4 * stride) {
-    s0 += prob(a[i]);
-    s1 += prob(a[i + stride]);
-    s2 += prob(a[i + 2 * stride]);
-    s3 += prob(a[i + 3 * stride]);
+    s0 = acc_prob(ld_amp(a, i), s0);
+    s1 = acc_prob(ld_amp(a, i + stride), s1);
+    s2 = acc_prob(ld_amp(a, i + 2 * stride), s2);
+    s3 = acc_prob(ld_amp(a, i + 3 * stride), s3);
   }
-  for (; i < N; i += stride) s0 += prob(a[i]);
+  for (; i < N; i += stride) s0 = acc_prob(ld_amp(a, i), s0);
   const double t = block_sum256((s0 + s1) + (s2 + s3), sh);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-__global__ void k_probs_full(const double2* __restrict__ a, double* __restrict__ p, uint64_t N) {
+template <class T>
+__global__ void k_probs_full(const T* __restrict__ a, double* __restrict__ p, uint64_t N) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) p[i] = prob(a[i]);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) p[i] = prob(ld_amp(a, i));
 }
 
 // ---- marginal over nq <= 12 qubits: per-CTA shared histogram ---------------------
@@ -75,7 +81,8 @@ __device__ __forceinline__ uint32_t extract_bits(uint64_t x, const MargArgs& g) 
 // elements into a shared histogram with shared-memory atomics would make the sum
 // order timing-dependent, so instead each warp owns a private histogram slice
 // and adds its lanes' values in lane order.
-__global__ void __launch_bounds__(256) k_marginal_small(const double2* __restrict__ a, double* __restrict__ part,
+template <class T>
+__global__ void __launch_bounds__(256) k_marginal_small(const T* __restrict__ a, double* __restrict__ part,
                                                          const MargArgs g, uint64_t per_cta) {
   extern __shared__ double hist[];  // [8 warps][2^nq]
   const int H = 1 << g.nq;
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(256) k_marginal_small(const double2* __restric
   double* mine = hist + w * H;
   for (uint64_t base = begin + (uint64_t)w * 32; base < end; base += 256) {
     uint64_t x = base + l;
-    double p = x < end ? prob(a[x]) : 0.0;
+    double p = x < end ? prob(ld_amp(a, x)) : 0.0;
     uint32_t k = extract_bits(x, g);
     // lanes add in lane order (deterministic)
     for (int src = 0; src < 32; ++src) {
@@ -100,6 +107,35 @@ __global__ void __launch_bounds__(256) k_marginal_small(const double2* __restric
     double s = 0.0;
     for (int ww = 0; ww < 8; ++ww) s += hist[ww * H + i];
     part[(size_t)blockIdx.x * H + i] = s;
+  }
+}
+
+// Marginal over nq <= 3 qubits (a measured qubit, a few bits): every thread keeps
+// one partial per outcome over its grid-stride elements, the CTA adds them with
+// the fixed shuffle tree, CTA partials go to part[cta][outcome] (then
+// k_marginal_finish in CTA order).
+template <class T, int NQ>
+__global__ void __launch_bounds__(256) k_marginal_tiny(const T* __restrict__ a, double* __restrict__ part,
+                                                        const MargArgs g) {
+  __shared__ double sh[8];
+  constexpr int H = 1 << NQ;
+  double acc[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) acc[k] = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < g.N; x += stride) {
+    const double2 v = ld_amp(a, x);
+    uint32_t kb = 0;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) kb |= (uint32_t)((x >> g.q[j]) & 1) << j;
+#pragma unroll
+    for (int k = 0; k < H; ++k)
+      if (k == (int)kb) acc[k] = acc_prob(v, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const double t = block_sum256(acc[k], sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * H + k] = t;
   }
 }
 
@@ -120,7 +156,8 @@ struct MargBigArgs {
   int r[QS_MAX_QUBITS];   // remaining qubits, ascending
 };
 
-__global__ void k_marginal_big(const double2* __restrict__ a, double* __restrict__ out, const MargBigArgs g) {
+template <class T>
+__global__ void k_marginal_big(const T* __restrict__ a, double* __restrict__ out, const MargBigArgs g) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.H; k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t xb = 0;
     for (int j = 0; j < g.nq; ++j) xb |= ((k >> j) & 1ull) << g.q[j];
@@ -128,7 +165,7 @@ __global__ void k_marginal_big(const double2* __restrict__ a, double* __restrict
     for (uint64_t r = 0; r < g.R; ++r) {
       uint64_t x = xb;
       for (int j = 0; j < g.nr; ++j) x |= ((r >> j) & 1ull) << g.r[j];
-      s += prob(a[x]);
+      s += prob(ld_amp(a, x));
     }
     out[k] = s;
   }
@@ -140,7 +177,8 @@ __global__ void k_marginal_big(const double2* __restrict__ a, double* __restrict
 // Each thread keeps its total and, for every bit of j, the sum over its elements
 // with that bit set; the CTA combines them into S_i = sum_{x_i = 1} p_x.
 constexpr int ZMAXJ = 26;
-__global__ void __launch_bounds__(256) k_expect_z(const double2* __restrict__ a, int r, double* __restrict__ part) {
+template <class A>
+__global__ void __launch_bounds__(256) k_expect_z(const A* __restrict__ a, int r, double* __restrict__ part) {
   __shared__ double sh[8];
   const int jbits = r - 8;
   const uint64_t base = (uint64_t)blockIdx.x << r;
@@ -150,7 +188,7 @@ __global__ void __launch_bounds__(256) k_expect_z(const double2* __restrict__ a,
   for (int b = 0; b < ZMAXJ; ++b) bs[b] = 0.0;
   const uint64_t J = 1ull << jbits;
   for (uint64_t j = 0; j < J; ++j) {
-    double p = prob(a[base + threadIdx.x + (j << 8)]);
+    double p = prob(ld_amp(a, base + threadIdx.x + (j << 8)));
     tot += p;
 #pragma unroll
     for (int b = 0; b < ZMAXJ; ++b)
@@ -199,18 +237,19 @@ struct PauliArgs {
   int ny[8];
 };
 
-__global__ void __launch_bounds__(256) k_pauli(const double2* __restrict__ a, const PauliArgs g, double* __restrict__ part) {
+template <class T>
+__global__ void __launch_bounds__(256) k_pauli(const T* __restrict__ a, const PauliArgs g, double* __restrict__ part) {
   __shared__ double sh[8];
   double acc[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < g.N; x += stride) {
-    double2 v = a[x];
+    double2 v = ld_amp(a, x);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       if (k >= g.nt) break;
-      double2 u = a[x ^ g.xm[k]];
+      double2 u = ld_amp(a, x ^ g.xm[k]);
       // w = conj(u) * v ; term = Re(i^ny * w) with sign (-1)^{popcount(x & zm)}
       double w;
       if (g.ny[k] & 1) w = fma(u.y, v.x, -u.x * v.y);   // Re(i*w) = -Im(w) = u.y v.x - u.x v.y
@@ -252,16 +291,44 @@ static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout)
   for (int j = 0; j < nq && identity; ++j) identity = qubits[j] == j;
   KTimer kt(s, QS_K_REDUCE, nq, 1, 0, 0, (double)N, 3.0 * (double)N);
   if (identity) {
-    k_probs_full<<<(int)std::min<uint64_t>((N + 255) / 256, 152 * 32), 256, 0, s->stream>>>(s->amps, dout, N);
+    with_amps(s, [&](auto* a) {
+      k_probs_full<<<(int)std::min<uint64_t>((N + 255) / 256, 152 * 32), 256, 0, s->stream>>>(a, dout, N);
+      return QS_OK;
+    });
     return launch_check("probs_full");
   }
   if (nq == 0) {  // squared norm: per-thread sums, a fixed shuffle tree, CTA partials in order
     const int nblocks = (int)std::min<uint64_t>(608, std::max<uint64_t>(1, N / 1024));
     double* part = (double*)s->ws;
-    k_norm2<<<nblocks, 256, 0, s->stream>>>(s->amps, N, part);
+    with_amps(s, [&](auto* a) {
+      k_norm2<<<nblocks, 256, 0, s->stream>>>(a, N, part);
+      return QS_OK;
+    });
     QS_TRY(launch_check("norm2"));
     k_marginal_finish<<<1, 32, 0, s->stream>>>(part, nblocks, 1, dout);
     return launch_check("norm2 finish");
+  }
+  if (nq <= 3) {
+    MargArgs g;
+    g.N = N;
+    g.nq = nq;
+    for (int j = 0; j < nq; ++j) g.q[j] = qubits[j];
+    const int nblocks = (int)std::min<uint64_t>(608, std::max<uint64_t>(1, N / 1024));
+    double* part = (double*)s->ws;
+    with_amps(s, [&](auto* a) {
+      using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
+      const T* ca = a;
+      switch (nq) {
+        case 1: k_marginal_tiny<T, 1><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+        case 2: k_marginal_tiny<T, 2><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+        default: k_marginal_tiny<T, 3><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+      }
+      return QS_OK;
+    });
+    QS_TRY(launch_check("marginal_tiny"));
+    const int H = 1 << nq;
+    k_marginal_finish<<<1, 32, 0, s->stream>>>(part, nblocks, H, dout);
+    return launch_check("marginal_finish");
   }
   if (nq <= 10) {  // 8 warp-private histograms of 2^nq doubles fit in shared memory
     MargArgs g;
@@ -273,10 +340,14 @@ static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout)
     per = (per + 255) / 256 * 256;
     nblocks = (int)((N + per - 1) / per);
     size_t smem = (size_t)8 * (1 << nq) * sizeof(double);
-    if (smem > 48 * 1024)
-      QS_CUDA(cudaFuncSetAttribute(k_marginal_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     double* part = (double*)s->ws;
-    k_marginal_small<<<nblocks, 256, smem, s->stream>>>(s->amps, part, g, per);
+    QS_TRY(with_amps(s, [&](auto* a) {
+      using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
+      if (smem > 48 * 1024)
+        QS_CUDA(cudaFuncSetAttribute(k_marginal_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_marginal_small<<<nblocks, 256, smem, s->stream>>>((const T*)a, part, g, per);
+      return QS_OK;
+    }));
     QS_TRY(launch_check("marginal_small"));
     int H = 1 << nq;
     k_marginal_finish<<<(H + 255) / 256, 256, 0, s->stream>>>(part, nblocks, H, dout);
@@ -294,7 +365,10 @@ static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout)
   g.nr = 0;
   for (int b = 0; b < n; ++b)
     if (!((used >> b) & 1)) g.r[g.nr++] = b;
-  k_marginal_big<<<(int)std::min<uint64_t>((g.H + 255) / 256, 152 * 32), 256, 0, s->stream>>>(s->amps, dout, g);
+  with_amps(s, [&](auto* a) {
+    k_marginal_big<<<(int)std::min<uint64_t>((g.H + 255) / 256, 152 * 32), 256, 0, s->stream>>>(a, dout, g);
+    return QS_OK;
+  });
   return launch_check("marginal_big");
 }
 
@@ -378,7 +452,10 @@ extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
   r = std::min(r, std::min(n, 8 + ZMAXJ));
   int nblocks = 1 << (n - r);
   KTimer kt(s, QS_K_REDUCE, n, 1, 0, 0, (double)(1ull << n), 5.0 * (double)(1ull << n));
-  k_expect_z<<<nblocks, 256, 0, s->stream>>>(s->amps, r, part);
+  with_amps(s, [&](auto* a) {
+    k_expect_z<<<nblocks, 256, 0, s->stream>>>(a, r, part);
+    return QS_OK;
+  });
   QS_TRY(launch_check("expect_z"));
   k_expect_z_finish<<<1, 64, 0, s->stream>>>(part, nblocks, r, n, dres);
   QS_TRY(launch_check("expect_z_finish"));
@@ -408,7 +485,10 @@ extern "C" int qs_expect_pauli(const qs_state* cs, const qs_pauli* terms, size_t
       g.ny[k] = __builtin_popcountll(terms[k0 + k].xmask & terms[k0 + k].zmask) & 3;
     }
     KTimer kt(s, QS_K_REDUCE, s->n, g.nt, 0, 0, (double)N, 4.0 * g.nt * (double)N);
-    k_pauli<<<nblocks, 256, 0, s->stream>>>(s->amps, g, part);
+    with_amps(s, [&](auto* a) {
+      k_pauli<<<nblocks, 256, 0, s->stream>>>(a, g, part);
+      return QS_OK;
+    });
     QS_TRY(launch_check("pauli"));
     k_pauli_finish<<<1, 32, 0, s->stream>>>(part, nblocks, g.nt, dres);
     QS_TRY(launch_check("pauli_finish"));

@@ -20,14 +20,16 @@ namespace qs {
 __device__ __forceinline__ double p_exact(double2 a) { return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)); }
 
 // T[b] = left-to-right block total; lastnz[b] = largest x in block b with p_x > 0, or -1.
-__global__ void k_block_totals(const double2* __restrict__ a, int64_t nb, int64_t L, double* __restrict__ T,
+template <class A>
+__global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, double* __restrict__ T,
                                long long* __restrict__ lastnz) {
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
-    const double2* p = a + b * L;
+    const A* p = a + b * L;
     double S = 0.0;
     long long last = -1;
     for (int64_t j = 0; j < L; j += 4) {
-      double2 v0 = p[j], v1 = p[j + 1 < L ? j + 1 : j], v2 = p[j + 2 < L ? j + 2 : j], v3 = p[j + 3 < L ? j + 3 : j];
+      double2 v0 = ld_amp(p, j), v1 = ld_amp(p, j + 1 < L ? j + 1 : j), v2 = ld_amp(p, j + 2 < L ? j + 2 : j),
+              v3 = ld_amp(p, j + 3 < L ? j + 3 : j);
       double q0 = p_exact(v0);
       S = __dadd_rn(S, q0);
       if (q0 > 0.0) last = b * L + j;
@@ -98,7 +100,8 @@ __global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __res
   if (threadIdx.x == 0) lastnz[nb] = lcarry < 0 ? 0 : lcarry;  // all-zero state: index 0
 }
 
-__global__ void k_sample(const double2* __restrict__ a, const double* __restrict__ E, const long long* __restrict__ lastnz,
+template <class A>
+__global__ void k_sample(const A* __restrict__ a, const double* __restrict__ E, const long long* __restrict__ lastnz,
                          int64_t nb, int64_t L, uint64_t seed, uint64_t shots, uint64_t* __restrict__ out) {
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < shots; s += (uint64_t)gridDim.x * blockDim.x) {
     double u = u01_of(splitmix64(seed, s));
@@ -114,11 +117,11 @@ __global__ void k_sample(const double2* __restrict__ a, const double* __restrict
     }
     const int64_t b = lo;
     const double eb = E[b];
-    const double2* p = a + b * L;
+    const A* p = a + b * L;
     double S = 0.0;
     int64_t pick = b * L + L - 1;
     for (int64_t j = 0; j < L; ++j) {
-      S = __dadd_rn(S, p_exact(p[j]));
+      S = __dadd_rn(S, p_exact(ld_amp(p, j)));
       if (__dadd_rn(eb, S) > u) {
         pick = b * L + j;
         break;
@@ -146,14 +149,20 @@ extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint
   long long* lastnz = (long long*)(E + (nb + 1));
   int g1 = (int)std::min<int64_t>((nb + 127) / 128, 152 * 16);
   KTimer kt(s, QS_K_REDUCE, s->n, 3, 0, 0, (double)N, 4.0 * (double)N);
-  k_block_totals<<<g1, 128, 0, s->stream>>>(s->amps, nb, L, T, lastnz);
+  with_amps(s, [&](auto* a) {
+    k_block_totals<<<g1, 128, 0, s->stream>>>(a, nb, L, T, lastnz);
+    return QS_OK;
+  });
   QS_TRY(launch_check("block_totals"));
   k_prefix<<<1, 256, 0, s->stream>>>(T, nb, E, lastnz);
   QS_TRY(launch_check("prefix"));
   uint64_t* dout = out;
   if (!on_device) QS_CUDA(cudaMallocAsync((void**)&dout, shots * sizeof(uint64_t), s->stream));
   int g3 = (int)std::min<uint64_t>((shots + 127) / 128, 152 * 16);
-  k_sample<<<g3, 128, 0, s->stream>>>(s->amps, E, lastnz, nb, L, seed, shots, dout);
+  with_amps(s, [&](auto* a) {
+    k_sample<<<g3, 128, 0, s->stream>>>(a, E, lastnz, nb, L, seed, shots, dout);
+    return QS_OK;
+  });
   int rc = launch_check("sample");
   if (!on_device) {
     if (rc == QS_OK) {

@@ -28,7 +28,8 @@ __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint
 
 // ---- FP64 engine -------------------------------------------------------------------
 struct EngF64 {
-  using T = double2;
+  using T = double2;  // shared-memory element
+  using G = double2;  // global element
   static __device__ __forceinline__ double neg(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
   }
@@ -63,6 +64,7 @@ struct EngF64 {
 // ---- Q60 fixed-point engine ----------------------------------------------------------
 struct EngQ60 {
   using T = longlong2;
+  using G = double2;
   static __device__ __forceinline__ T load(const double2& a) {
     return make_longlong2(q60_from_double(a.x), q60_from_double(a.y));
   }
@@ -115,6 +117,41 @@ struct EngQ60 {
   }
 };
 
+// ---- FP32 engine (complex64 states) -------------------------------------------------
+// The op's matrix arrives rounded to float by the host (no conversion on the FP64 pipe).
+struct EngF32 {
+  using T = float2;
+  using G = float2;
+  static __device__ __forceinline__ T load(const float2& a) { return a; }
+  static __device__ __forceinline__ float2 store(const T& a) { return a; }
+  static __device__ __forceinline__ float2 u(const TileOp& op, int e) { return op.f[e]; }
+  static __device__ __forceinline__ T unit(T a, int code) {
+    switch (code) {
+      case U_ONE: return a;
+      case U_I: return make_float2(-a.y, a.x);
+      case U_MINUS_ONE: return make_float2(-a.x, -a.y);
+      default: return make_float2(a.y, -a.x);
+    }
+  }
+  static __device__ __forceinline__ T mul(T a, int code, const TileOp& op, int e) {
+    if (code != U_GENERAL) return unit(a, code);
+    const float2 w = u(op, e);
+    return make_float2(fmaf(w.x, a.x, -w.y * a.y), fmaf(w.x, a.y, w.y * a.x));
+  }
+  static __device__ __forceinline__ void real2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
+    const float m0 = op.f[0].x, m1 = op.f[1].x, m2 = op.f[2].x, m3 = op.f[3].x;
+    b0 = make_float2(fmaf(m0, a0.x, m1 * a1.x), fmaf(m0, a0.y, m1 * a1.y));
+    b1 = make_float2(fmaf(m2, a0.x, m3 * a1.x), fmaf(m2, a0.y, m3 * a1.y));
+  }
+  static __device__ __forceinline__ void general2(const TileOp& op, T a0, T a1, T& b0, T& b1) {
+    const float2 u0 = u(op, 0), u1 = u(op, 1), u2 = u(op, 2), u3 = u(op, 3);
+    b0.x = fmaf(u0.x, a0.x, fmaf(-u0.y, a0.y, fmaf(u1.x, a1.x, -u1.y * a1.y)));
+    b0.y = fmaf(u0.x, a0.y, fmaf(u0.y, a0.x, fmaf(u1.x, a1.y, u1.y * a1.x)));
+    b1.x = fmaf(u2.x, a0.x, fmaf(-u2.y, a0.y, fmaf(u3.x, a1.x, -u3.y * a1.y)));
+    b1.y = fmaf(u2.x, a0.y, fmaf(u2.y, a0.x, fmaf(u3.x, a1.y, u3.y * a1.x)));
+  }
+};
+
 // All pairs (j, j | tb) of one op in the tile, the op class fixed at compile time;
 // unrolled so that a thread has several independent pairs in flight.
 template <class E, int KIND, int THREADS>
@@ -144,7 +181,7 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
 }
 
 template <class E, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tile(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
+__global__ void __launch_bounds__(THREADS) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = g.m;
@@ -321,7 +358,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tile_reg(double2* __restrict_
   }
 }
 template <class E>
-static int launch_engine(qs_state* s, const TileArgs& g, size_t smem) {
+static int launch_engine(qs_state* s, const TileArgs& g) {
+  const size_t H = (size_t)1 << g.nhigh;
+  const size_t smem = ((H * sizeof(uint64_t) + 15) & ~(size_t)15) + (sizeof(typename E::T) << g.m);
   constexpr int THREADS = 256;  // measured at n=30: 512 (2 CTAs/SM) and 1024 (1/SM) are 2-6% slower
   static bool attr_set = false;
   static int sms = 0;
@@ -333,7 +372,7 @@ static int launch_engine(qs_state* s, const TileArgs& g, size_t smem) {
   int per_sm = 0;
   QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<E, THREADS>, THREADS, smem));
   const uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)std::max(1, sms) * std::max(1, per_sm));
-  k_tile<E, THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
+  k_tile<E, THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(reinterpret_cast<typename E::G*>(s->amps), g);
   return launch_check("tile kernel");
 }
 
@@ -364,7 +403,8 @@ int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, in
     }
     return launch_check("tile kernel (register phases)");
   }
-  return fixed ? launch_engine<EngQ60>(s, g, smem) : launch_engine<EngF64>(s, g, smem);
+  if (s->prec == 64) return launch_engine<EngF32>(s, g);
+  return fixed ? launch_engine<EngQ60>(s, g) : launch_engine<EngF64>(s, g);
 }
 
 }  // namespace qs

@@ -36,6 +36,7 @@ struct TileOp {
   union {
     double2 m[4];      // FP64 engine: matrix (for SCALAR: m[0] = d0, m[3] = d1)
     QC q[4];           // Q60 engine: the same entries as limbs (GENERAL ops: Gauss form)
+    float2 f[4];       // FP32 engine (complex64 states): the entries rounded to float
   };
   uint64_t ext_cmask;  // control qubits outside the tile (global bit positions)
   uint32_t lcmask;     // control qubits inside the tile (local bit positions)
