@@ -65,6 +65,10 @@ def _load():
                 "or_mlp_forward": (i32, [i32, i32, P, P, i64, P]),
                 "or_mlp_loss_grad": (i32, [i32, i32, P, P, P, i64, P, P]),
                 "or_measure": (i32, [P, i32, i32, ctypes.c_double, P, P]),
+                "or_kraus": (i32, [i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]),
+                "or_run_noisy": (i32, [P, i32, P, i64, P, P, i64, ctypes.c_double, u64, P]),
+                "or_readout": (None, [P, i64, i32, ctypes.c_double, ctypes.c_double, u64]),
+                "or_dm_run": (i32, [P, i32, P, i64, P, P, i64]),
                 "or_run_program": (i32, [P, i32, P, i64, P, i64, P, u64, u64, P, i64, P, i64, P]),
             }
             for name, (res, args) in sig.items():
@@ -272,3 +276,46 @@ def run_program(n: int, prog: np.ndarray, gates: np.ndarray, params=None, seed: 
                                 record_cap, ctypes.byref(nm))
     _chk(rc, "or_run_program")
     return st, cb, rec[:min(nm.value, record_cap)].copy()
+
+
+def kraus(model: int, p: float = 0.0, t1: float = 0.0, t2: float = 0.0, tgate: float = 0.0):
+    """(list of 2x2 complex Kraus matrices, unital flag) of a noise model."""
+    K = np.zeros(32, dtype=np.float64)
+    un = ctypes.c_int()
+    m = _load().or_kraus(model, p, t1, t2, tgate, K.ctypes.data, ctypes.byref(un))
+    if m == 0:
+        raise OracleError("or_kraus: bad noise model or parameters")
+    Kc = K.view(np.complex128).reshape(4, 2, 2)[:m].copy()
+    return list(Kc), bool(un.value)
+
+
+def run_noisy(n: int, gates: np.ndarray, rules: np.ndarray, params=None, rot_err: float = 0.0, seed: int = 0,
+              state=None):
+    """One Monte-Carlo trajectory from |0...0> (or `state`): (state, draws used)."""
+    st = zero_state(n) if state is None else _state(state).copy()
+    gates = np.ascontiguousarray(gates)
+    rules = np.ascontiguousarray(rules)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    nd = ctypes.c_uint64()
+    rc = _load().or_run_noisy(st.ctypes.data, n, _ptr(gates) if len(gates) else None, len(gates), _ptr(pr),
+                              _ptr(rules) if len(rules) else None, len(rules), rot_err, seed, ctypes.byref(nd))
+    _chk(rc, "or_run_noisy")
+    return st, nd.value
+
+
+def readout(samples: np.ndarray, n: int, f0: float, f1: float, seed: int) -> np.ndarray:
+    out = np.ascontiguousarray(samples, dtype=np.uint64).copy()
+    _load().or_readout(out.ctypes.data, len(out), n, f0, f1, seed)
+    return out
+
+
+def dm_run(n: int, gates: np.ndarray, rules: np.ndarray, params=None) -> np.ndarray:
+    """Density matrix after the noisy circuit (exact channel average), 2^n x 2^n."""
+    N = 1 << n
+    rho = np.empty(2 * N * N, dtype=np.float64)
+    gates = np.ascontiguousarray(gates)
+    rules = np.ascontiguousarray(rules)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    _chk(_load().or_dm_run(rho.ctypes.data, n, _ptr(gates) if len(gates) else None, len(gates), _ptr(pr),
+                           _ptr(rules) if len(rules) else None, len(rules)), "or_dm_run")
+    return rho.view(np.complex128).reshape(N, N)

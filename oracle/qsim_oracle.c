@@ -786,3 +786,285 @@ int or_run_program(double* state, int n, const or_pinstr* prog, int64_t nprog, c
   if (nmeasured) *nmeasured = r.nmeas;
   return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Noise (the paper's NoiseQVM, Section "Multi-simulation methods", noise     */
+/* simulation method): one-qubit Kraus channels attached to gate types, a     */
+/* readout confusion matrix and a rotation error.                             */
+/* Kraus sets, as printed in the paper (row-major 2x2):                       */
+/*   DAMPING       K1 = [[1,0],[0,sqrt(1-p)]], K2 = [[0,sqrt(p)],[0,0]]        */
+/*   DEPHASING     K1 = sqrt(1-p) I, K2 = sqrt(p) Z                            */
+/*   DECOHERENCE   K_ij = Kdamp_i Kdeph_j (i, j = 1, 2; K1 = K11, K2 = K12,    */
+/*                 K3 = K21, K4 = K22) with p_damp = 1 - exp(-tg/T1) and       */
+/*                 p_deph = (1 - exp(-(tg/T2 - tg/(2 T1)))) / 2                */
+/*   DEPOLARIZING  sqrt(1 - 3p/4) I, sqrt(p)/2 X, sqrt(p)/2 Y, sqrt(p)/2 Z      */
+/*   BITFLIP       sqrt(1-p) I, sqrt(p) X                                      */
+/*   BITPHASEFLIP  sqrt(1-p) I, sqrt(p) Y   (the matrix the paper prints for    */
+/*                 its "bit or phase flip" operator)                           */
+/*   PHASEFLIP     sqrt(1-p) I, sqrt(p) Z                                      */
+/*   PHASE_DAMPING K1 = [[1,0],[0,sqrt(1-p)]], K2 = [[0,0],[0,sqrt(p)]]        */
+/* ------------------------------------------------------------------------- */
+enum {
+  OR_NOISE_DAMPING = 0, OR_NOISE_DEPHASING = 1, OR_NOISE_DECOHERENCE = 2, OR_NOISE_DEPOLARIZING = 3,
+  OR_NOISE_BITFLIP = 4, OR_NOISE_BITPHASEFLIP = 5, OR_NOISE_PHASEFLIP = 6, OR_NOISE_PHASE_DAMPING = 7
+};
+
+typedef struct {
+  int32_t model, gate_type, q0, q1;
+  double p, t1, t2, tgate;
+} or_noise_rule;
+
+static void set2(cplx K[4], double a, double b, double c, double d) {
+  K[0] = c_make(a, 0); K[1] = c_make(b, 0); K[2] = c_make(c, 0); K[3] = c_make(d, 0);
+}
+
+static void mul2(const cplx A[4], const cplx B[4], cplx C[4]) {
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      C[2 * i + j] = c_add(c_mul(A[2 * i], B[j]), c_mul(A[2 * i + 1], B[2 + j]));
+}
+
+/* Kraus operators of a rule into K (up to 4 x 4 entries); returns their count,
+ * or 0 for a bad rule.  *unital: 1 when every operator is a scaled unitary (the
+ * choice weights are the squared scales, independent of the state). */
+int or_kraus(int model, double p, double t1, double t2, double tg, double* K8x4, int* unital) {
+  cplx* K = (cplx*)K8x4;
+  const double s = sqrt(p), r = sqrt(1.0 - p);
+  *unital = 1;
+  switch (model) {
+    case OR_NOISE_DAMPING:
+      set2(K, 1, 0, 0, r); set2(K + 4, 0, s, 0, 0); *unital = 0; return 2;
+    case OR_NOISE_PHASE_DAMPING:
+      set2(K, 1, 0, 0, r); set2(K + 4, 0, 0, 0, s); *unital = 0; return 2;
+    case OR_NOISE_DEPHASING:
+    case OR_NOISE_PHASEFLIP:
+      set2(K, r, 0, 0, r); set2(K + 4, s, 0, 0, -s); return 2;
+    case OR_NOISE_BITFLIP:
+      set2(K, r, 0, 0, r); set2(K + 4, 0, s, s, 0); return 2;
+    case OR_NOISE_BITPHASEFLIP:
+      set2(K, r, 0, 0, r);
+      K[4] = c_make(0, 0); K[5] = c_make(0, -s); K[6] = c_make(0, s); K[7] = c_make(0, 0);
+      return 2;
+    case OR_NOISE_DEPOLARIZING: {
+      const double a = sqrt(1.0 - 0.75 * p), h = 0.5 * s;
+      set2(K, a, 0, 0, a);
+      set2(K + 4, 0, h, h, 0);
+      K[8] = c_make(0, 0); K[9] = c_make(0, -h); K[10] = c_make(0, h); K[11] = c_make(0, 0);
+      set2(K + 12, h, 0, 0, -h);
+      return 4;
+    }
+    case OR_NOISE_DECOHERENCE: {
+      if (!(t1 > 0) || !(t2 > 0) || !(tg >= 0)) return 0;
+      const double pa = 1.0 - exp(-tg / t1), pd = 0.5 * (1.0 - exp(-(tg / t2 - tg / (2.0 * t1))));
+      cplx D[2][4], P[2][4];
+      set2(D[0], 1, 0, 0, sqrt(1.0 - pa)); set2(D[1], 0, sqrt(pa), 0, 0);
+      set2(P[0], sqrt(1.0 - pd), 0, 0, sqrt(1.0 - pd)); set2(P[1], sqrt(pd), 0, 0, -sqrt(pd));
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) mul2(D[i], P[j], K + 4 * (2 * i + j));
+      *unital = 0;
+      return 4;
+    }
+    default:
+      return 0;
+  }
+}
+
+/* The weights w_j = || K_j psi ||^2 on qubit q (from the state), or the squared
+ * scales of a scaled-unitary set (independent of the state). */
+static void kraus_weights(const cplx* psi, int n, int q, const cplx* K, int m, int unital, double* w) {
+  for (int j = 0; j < m; ++j) {
+    if (unital) {
+      const cplx* k = K + 4 * j;
+      /* a scaled unitary c U has |column|^2 = c^2 */
+      w[j] = k[0].re * k[0].re + k[0].im * k[0].im + k[2].re * k[2].re + k[2].im * k[2].im;
+      continue;
+    }
+    double s = 0.0;
+    const int64_t N = (int64_t)1 << n, b = (int64_t)1 << q;
+    for (int64_t x = 0; x < N; ++x) {
+      if (x & b) continue;
+      const cplx a0 = psi[x], a1 = psi[x | b];
+      const cplx y0 = c_add(c_mul(K[4 * j], a0), c_mul(K[4 * j + 1], a1));
+      const cplx y1 = c_add(c_mul(K[4 * j + 2], a0), c_mul(K[4 * j + 3], a1));
+      s += prob_of(y0) + prob_of(y1);
+    }
+    w[j] = s;
+  }
+}
+
+static int is_rotation(int type) {
+  return type == OR_RX || type == OR_RY || type == OR_RZ || type == OR_U3 || type == OR_P || type == OR_CR;
+}
+
+/* One Monte-Carlo trajectory.  For every gate in order:
+ *   1. a rotation gate's theta gets e * (2u - 1) added (one draw, if e > 0);
+ *   2. the gate is applied;
+ *   3. for every rule that matches it (gate type, or -1 for all; q0/q1 the
+ *      gate's first / second qubit, -1 = any), in rule order, and every qubit
+ *      the gate acts on (controls, then target, ascending), one draw u picks
+ *      the smallest j with u * W < w_1 + ... + w_j (W = sum of weights), and
+ *      psi <- K_j psi / sqrt(w_j).
+ * Draw k of the trajectory is u01(SplitMix64 output k of the stream seeded
+ * `seed`).  *ndraws receives the draws used. */
+int or_run_noisy(double* state, int n, const or_gate* gates, int64_t ng, const double* params,
+                 const or_noise_rule* rules, int64_t nrules, double rot_err, uint64_t seed, uint64_t* ndraws) {
+  cplx* psi = (cplx*)state;
+  uint64_t k = 0;
+  double* pv = NULL;
+  int64_t np = 0;
+  for (int64_t g = 0; g < ng; ++g)
+    if (gates[g].param_idx >= 0 && gates[g].param_idx + 1 > np) np = gates[g].param_idx + 1;
+  if (np) {
+    pv = (double*)malloc(sizeof(double) * np);
+    if (!pv) return OR_ENOMEM;
+  }
+  int rc = OR_OK;
+  for (int64_t g = 0; g < ng && rc == OR_OK; ++g) {
+    or_gate gate = gates[g];
+    const double* prm = params;
+    if (rot_err > 0.0 && is_rotation(gate.type)) {
+      const double d = rot_err * (2.0 * u01(or_splitmix64(seed, k++)) - 1.0);
+      if (gate.param_idx >= 0) {
+        memcpy(pv, params, sizeof(double) * np);
+        pv[gate.param_idx] += d;
+        prm = pv;
+      } else {
+        gate.p[0] += d;
+      }
+    }
+    if ((rc = or_apply_gate(state, n, &gate, prm)) != OR_OK) break;
+    int t;
+    uint64_t cm;
+    if ((rc = qubits_of(&gate, n, &t, &cm)) != OR_OK) break;
+    const int first = gate.q0;
+    const int second = is_two_qubit(gate.type) ? gate.q1 : -1;
+    for (int64_t r = 0; r < nrules && rc == OR_OK; ++r) {
+      const or_noise_rule* R = &rules[r];
+      if (R->gate_type >= 0 && R->gate_type != gate.type) continue;
+      if (R->q0 >= 0 && R->q0 != first) continue;
+      if (R->q1 >= 0 && R->q1 != second) continue;
+      double K8[32];
+      int unital = 0;
+      const int m = or_kraus(R->model, R->p, R->t1, R->t2, R->tgate, K8, &unital);
+      if (!m) { rc = OR_EINVAL; break; }
+      const uint64_t touched = cm | (1ull << t);
+      for (int q = 0; q < n; ++q) {
+        if (!((touched >> q) & 1)) continue;
+        double w[4] = {0.0, 0.0, 0.0, 0.0}, W = 0.0;
+        kraus_weights(psi, n, q, (const cplx*)K8, m, unital, w);
+        for (int j = 0; j < m; ++j) W += w[j];
+        const double u = u01(or_splitmix64(seed, k++));
+        int pick = m - 1;
+        double c = 0.0;
+        for (int j = 0; j < m; ++j) {
+          c += w[j];
+          if (u * W < c) { pick = j; break; }
+        }
+        if (!(w[pick] > 0.0)) { rc = OR_EINVAL; break; }
+        const cplx* Kp = (const cplx*)K8 + 4 * pick;
+        const double sc = 1.0 / sqrt(w[pick]);
+        const int64_t N = (int64_t)1 << n, b = (int64_t)1 << q;
+        for (int64_t x = 0; x < N; ++x) {
+          if (x & b) continue;
+          const cplx a0 = psi[x], a1 = psi[x | b];
+          const cplx y0 = c_add(c_mul(Kp[0], a0), c_mul(Kp[1], a1));
+          const cplx y1 = c_add(c_mul(Kp[2], a0), c_mul(Kp[3], a1));
+          psi[x] = c_make(y0.re * sc, y0.im * sc);
+          psi[x | b] = c_make(y1.re * sc, y1.im * sc);
+        }
+      }
+    }
+  }
+  free(pv);
+  if (ndraws) *ndraws = k;
+  return rc;
+}
+
+/* Readout error on sampled basis indices: bit i of shot s reads wrong with
+ * probability 1 - f0 (true bit 0) or 1 - f1 (true bit 1), the confusion matrix
+ * [[f0, 1-f0], [1-f1, f1]] of the paper's set_readout_error; draw
+ * u = u01(SplitMix64 output s*n + i of the stream seeded `seed`) flips the bit
+ * when u >= f_bit. */
+void or_readout(uint64_t* samples, int64_t shots, int n, double f0, double f1, uint64_t seed) {
+  for (int64_t s = 0; s < shots; ++s)
+    for (int i = 0; i < n; ++i) {
+      const int bit = (int)((samples[s] >> i) & 1);
+      const double u = u01(or_splitmix64(seed, (uint64_t)s * (uint64_t)n + (uint64_t)i));
+      if (u >= (bit ? f1 : f0)) samples[s] ^= 1ull << i;
+    }
+}
+
+/* ---- density-matrix reference (n <= 8): rho -> U rho U^dag per gate, then
+ * rho -> sum_j K_j rho K_j^dag for every matching rule and touched qubit, as
+ * above but averaged instead of sampled (no rotation error). rho is 2^n x 2^n
+ * complex, row-major, interleaved. ------------------------------------------ */
+static void dm_left(cplx* rho, int n, int q, uint64_t cm, const cplx M[4]) {  /* rho <- M_q rho */
+  const int64_t N = (int64_t)1 << n, b = (int64_t)1 << q;
+  for (int64_t c = 0; c < N; ++c)
+    for (int64_t x = 0; x < N; ++x) {
+      if ((x & b) || (x & cm) != (int64_t)cm) continue;
+      const cplx a0 = rho[x * N + c], a1 = rho[(x | b) * N + c];
+      rho[x * N + c] = c_add(c_mul(M[0], a0), c_mul(M[1], a1));
+      rho[(x | b) * N + c] = c_add(c_mul(M[2], a0), c_mul(M[3], a1));
+    }
+}
+
+static void dm_right(cplx* rho, int n, int q, uint64_t cm, const cplx M[4]) {  /* rho <- rho M_q^dag */
+  const int64_t N = (int64_t)1 << n, b = (int64_t)1 << q;
+  const cplx Mc[4] = {c_conj(M[0]), c_conj(M[1]), c_conj(M[2]), c_conj(M[3])};
+  for (int64_t r = 0; r < N; ++r)
+    for (int64_t x = 0; x < N; ++x) {
+      if ((x & b) || (x & cm) != (int64_t)cm) continue;
+      const cplx a0 = rho[r * N + x], a1 = rho[r * N + (x | b)];
+      rho[r * N + x] = c_add(c_mul(a0, Mc[0]), c_mul(a1, Mc[1]));
+      rho[r * N + (x | b)] = c_add(c_mul(a0, Mc[2]), c_mul(a1, Mc[3]));
+    }
+}
+
+int or_dm_run(double* rho_out, int n, const or_gate* gates, int64_t ng, const double* params,
+              const or_noise_rule* rules, int64_t nrules) {
+  if (n < 1 || n > 8) return OR_EINVAL;
+  const int64_t N = (int64_t)1 << n;
+  cplx* rho = (cplx*)rho_out;
+  cplx* acc = (cplx*)malloc(sizeof(cplx) * N * N);
+  cplx* tmp = (cplx*)malloc(sizeof(cplx) * N * N);
+  if (!acc || !tmp) { free(acc); free(tmp); return OR_ENOMEM; }
+  for (int64_t i = 0; i < N * N; ++i) rho[i] = c_make(0, 0);
+  rho[0] = c_make(1, 0);
+  int rc = OR_OK;
+  for (int64_t g = 0; g < ng && rc == OR_OK; ++g) {
+    int t;
+    uint64_t cm;
+    cplx U[4];
+    if ((rc = resolve(&gates[g], n, params, &t, &cm, U)) != OR_OK) break;
+    dm_left(rho, n, t, cm, U);
+    dm_right(rho, n, t, cm, U);
+    const int first = gates[g].q0;
+    const int second = is_two_qubit(gates[g].type) ? gates[g].q1 : -1;
+    for (int64_t r = 0; r < nrules && rc == OR_OK; ++r) {
+      const or_noise_rule* R = &rules[r];
+      if (R->gate_type >= 0 && R->gate_type != gates[g].type) continue;
+      if (R->q0 >= 0 && R->q0 != first) continue;
+      if (R->q1 >= 0 && R->q1 != second) continue;
+      double K8[32];
+      int unital = 0;
+      const int m = or_kraus(R->model, R->p, R->t1, R->t2, R->tgate, K8, &unital);
+      if (!m) { rc = OR_EINVAL; break; }
+      const uint64_t touched = cm | (1ull << t);
+      for (int q = 0; q < n; ++q) {
+        if (!((touched >> q) & 1)) continue;
+        for (int64_t i = 0; i < N * N; ++i) acc[i] = c_make(0, 0);
+        for (int j = 0; j < m; ++j) {
+          memcpy(tmp, rho, sizeof(cplx) * N * N);
+          dm_left(tmp, n, q, 0, (const cplx*)K8 + 4 * j);
+          dm_right(tmp, n, q, 0, (const cplx*)K8 + 4 * j);
+          for (int64_t i = 0; i < N * N; ++i) acc[i] = c_add(acc[i], tmp[i]);
+        }
+        memcpy(rho, acc, sizeof(cplx) * N * N);
+      }
+    }
+  }
+  free(acc);
+  free(tmp);
+  return rc;
+}

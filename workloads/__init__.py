@@ -365,3 +365,23 @@ def random_program(n: int, seed: int, segments: int = 6, gates_per_segment: int 
         block(p, 0)
         gates(p)
     return p.pack()
+
+
+
+# ---- noise rules -----------------------------------------------------------------------
+# Rule layout (48 bytes): int32 model, int32 gate_type (-1: every gate), int32 q0,
+# int32 q1 (the gate's first / second qubit, -1: any), f64 p, f64 t1, f64 t2, f64 tgate.
+NOISE_MODELS = {"DAMPING": 0, "DEPHASING": 1, "DECOHERENCE": 2, "DEPOLARIZING": 3, "BITFLIP": 4,
+                "BITPHASEFLIP": 5, "PHASEFLIP": 6, "PHASE_DAMPING": 7}
+NOISE_DTYPE = np.dtype([("model", "<i4"), ("gate_type", "<i4"), ("q0", "<i4"), ("q1", "<i4"),
+                        ("p", "<f8"), ("t1", "<f8"), ("t2", "<f8"), ("tgate", "<f8")], align=True)
+assert NOISE_DTYPE.itemsize == 48
+
+
+def noise_rule(model: str, gate: str | None = None, p: float = 0.0, q0: int = -1, q1: int = -1,
+               t1: float = 0.0, t2: float = 0.0, tgate: float = 0.0):
+    return (NOISE_MODELS[model], -1 if gate is None else GATE_CODES[gate], q0, q1, p, t1, t2, tgate)
+
+
+def noise_rules(rules) -> np.ndarray:
+    return np.array(list(rules), dtype=NOISE_DTYPE)
