@@ -391,6 +391,42 @@ def bench_c64(q, torch, stream, hbm_peak: float, steps: int = 3):
     return out
 
 
+def bench_noisy(q, torch, stream):
+    """Noise trajectories on the n=28 brickwork (depth 20, 830 gates): depolarizing
+    p=1e-3 on every gate (scaled-unitary channel: Paulis join the fused gate
+    stream), then the same plus amplitude damping p=1e-3 on every CZ (one weight
+    reduction and one renormalised Kraus pass per touched qubit)."""
+    n = 28
+    g = w.layered_u3_cz(n, 20, 1)
+    out = {"n": n, "gates": len(g)}
+    cases = {"depolarizing": w.noise_rules([w.noise_rule("DEPOLARIZING", None, 1e-3)]),
+             "depolarizing+damping": w.noise_rules([w.noise_rule("DEPOLARIZING", None, 1e-3),
+                                                    w.noise_rule("DAMPING", "CZ", 1e-3)])}
+    h = q.qs_alloc(n, stream)
+    try:
+        for name, rules in cases.items():
+            q.qs_run_noisy(h, g, rules, seed=0)
+            ts = []
+            for seed in (1, 2):
+                q.qs_set_zero(h)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                nd = q.qs_run_noisy(h, g, rules, seed=seed)
+                ts.append(time.perf_counter() - t0)
+            out[name] = {"ms_per_trajectory": 1e3 * float(np.mean(ts)), "draws": nd}
+        p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+        q.qs_set_zero(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.qs_apply(h, g, None, p)
+        torch.cuda.synchronize()
+        out["noiseless_fused_ms"] = 1e3 * (time.perf_counter() - t0)
+        q.qs_plan_free(p)
+    finally:
+        q.qs_free(h)
+    return out
+
+
 def bench_learned_plan(q, torch, stream):
     """n=32 (64 GiB), 2000 random gates (40 % two-qubit, seed 2): greedy plan vs
     the learned plan (cost model from paper_2212_14201_gb300/costmodel_weights.json)
@@ -538,6 +574,7 @@ def run_ours(args, world, rank, local, pg):
         extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2)
         extra["measure_n30"] = bench_measure(q, torch, stream, hbm_peak)
         extra["c64_n30"] = bench_c64(q, torch, stream, hbm_peak)
+        extra["noisy_n28"] = bench_noisy(q, torch, stream)
         if not args.no_n32:
             try:
                 extra["learned_n32"] = bench_learned_plan(q, torch, stream)
@@ -582,6 +619,7 @@ def run_ours(args, world, rank, local, pg):
         "learned_n32": extra.get("learned_n32"),
         "measure_n30": extra.get("measure_n30"),
         "c64_n30": extra.get("c64_n30"),
+        "noisy_n28": extra.get("noisy_n28"),
     }
     print(json.dumps(line), flush=True)
 

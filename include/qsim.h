@@ -410,6 +410,55 @@ int qs_run_program(qs_state* s, const qs_pinstr* prog, size_t nprog, const qs_ga
                    const double* params, int fuse, uint64_t seed, uint64_t max_iters, int64_t* cbits,
                    size_t ncbits, double* record, size_t record_cap, uint64_t* nmeasured);
 
+/* ---- noisy simulation by Monte-Carlo trajectories (NoiseQVM, Section
+ * "Multi-simulation methods": Kraus operator noise models, set_noise_model,
+ * set_readout_error, set_rotation_error) --------------------------------------- */
+
+enum {
+  QS_NOISE_DAMPING = 0, QS_NOISE_DEPHASING = 1, QS_NOISE_DECOHERENCE = 2, QS_NOISE_DEPOLARIZING = 3,
+  QS_NOISE_BITFLIP = 4, QS_NOISE_BITPHASEFLIP = 5, QS_NOISE_PHASEFLIP = 6, QS_NOISE_PHASE_DAMPING = 7
+};
+
+/* A noise rule (48 bytes): after every gate of type gate_type (-1: every gate)
+ * whose first qubit is q0 and second qubit q1 (-1: any; for CNOT/CZ/CR the
+ * control and the target), the one-qubit channel `model` acts on each qubit the
+ * gate touches.  Kraus sets as the paper prints them:
+ *   DAMPING [[1,0],[0,sqrt(1-p)]], [[0,sqrt(p)],[0,0]];
+ *   DEPHASING and PHASEFLIP sqrt(1-p) I, sqrt(p) Z;  BITFLIP sqrt(1-p) I, sqrt(p) X;
+ *   BITPHASEFLIP sqrt(1-p) I, sqrt(p) Y;
+ *   DEPOLARIZING sqrt(1-3p/4) I, sqrt(p)/2 {X, Y, Z};
+ *   PHASE_DAMPING [[1,0],[0,sqrt(1-p)]], [[0,0],[0,sqrt(p)]];
+ *   DECOHERENCE Kdamp_i Kdeph_j with p_damp = 1 - exp(-tgate/t1) and
+ *   p_deph = (1 - exp(-(tgate/t2 - tgate/(2 t1)))) / 2 (p unused). */
+typedef struct qs_noise_rule {
+  int32_t model, gate_type, q0, q1;
+  double p, t1, t2, tgate;
+} qs_noise_rule;
+
+/* One trajectory of the noisy circuit on the current contents of s.  Gate by
+ * gate: a rotation (RX, RY, RZ, U3, P, CR) gets theta += rotation_error (2u - 1)
+ * (one draw, if rotation_error > 0); the gate is applied; then for each matching
+ * rule in order and each touched qubit in ascending order, one draw u picks the
+ * smallest j with u W < w_1 + ... + w_j (w_j = ||K_j psi||^2, W their sum) and
+ * psi <- K_j psi / sqrt(w_j).  Draw k is (SplitMix64 output k of the stream
+ * seeded `seed` >> 11) * 2^-53; *ndraws (nullable) receives the count.
+ * Stretches without damping-type channels run as one gate list (fused with a
+ * greedy plan if fuse != 0); damping-type channels take one reduction pass for
+ * their weights.  Synchronous.  Errors: INVALID_ARG (rule, probability,
+ * decoherence times), the errors of qs_apply. */
+int qs_run_noisy(qs_state* s, const qs_gate* gates, size_t ng, const double* params,
+                 const qs_noise_rule* rules, size_t nrules, double rotation_error, uint64_t seed, int fuse,
+                 uint64_t* ndraws);
+
+/* Readout error on sampled basis indices (set_readout_error's confusion matrix
+ * [[f0, 1-f0], [1-f1, f1]] on every qubit): bit i of shot s flips when
+ * u = u01(SplitMix64 output s*n + i of the stream seeded `seed`) >= f0 (bit 0)
+ * or f1 (bit 1).  samples: shots indices in device (on_device != 0, on
+ * `stream`) or host memory, rewritten in place.  Synchronous.
+ * Errors: INVALID_ARG, CUDA. */
+int qs_readout_error(uint64_t* samples, size_t shots, int n, double f0, double f1, uint64_t seed, int on_device,
+                     void* stream);
+
 /* ---- batched variational evaluation (the hybrid quantum-classical loop of
  * Sections "Support hybrid quantum-classical algorithm" and "Variational
  * quantum circuit": many parameter sets evaluated per optimiser step) -------- */

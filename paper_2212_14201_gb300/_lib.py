@@ -26,6 +26,8 @@ GATE_DTYPE = np.dtype([
     ("ctrl_mask", "<u8"), ("p", "<f8", (3,)), ("dagger", "<i4"), ("reserved", "<i4"),
 ], align=True)
 PAULI_DTYPE = np.dtype([("coef", "<f8"), ("xmask", "<u8"), ("zmask", "<u8")], align=True)
+NOISE_DTYPE = np.dtype([("model", "<i4"), ("gate_type", "<i4"), ("q0", "<i4"), ("q1", "<i4"),
+                        ("p", "<f8"), ("t1", "<f8"), ("t2", "<f8"), ("tgate", "<f8")], align=True)
 PINSTR_DTYPE = np.dtype([
     ("op", "<i4"), ("qubit", "<i4"), ("dst", "<i4"), ("alu", "<i4"), ("lhs", "<i4"), ("rhs", "<i4"),
     ("imm", "<i8"), ("n_then", "<u4"), ("n_else", "<u4"), ("gate_begin", "<u8"), ("gate_end", "<u8"),
@@ -108,6 +110,8 @@ SIGNATURES = {
     "qs_batch_info": (I32, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SZ)]),
     "qs_batch_cluster": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
     "qs_measure": (I32, [P, I32, DBL, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(DBL)]),
+    "qs_run_noisy": (I32, [P, P, SZ, P, P, SZ, DBL, U64, I32, ctypes.POINTER(U64)]),
+    "qs_readout_error": (I32, [P, SZ, I32, DBL, DBL, U64, I32, P]),
     "qs_run_program": (I32, [P, P, SZ, P, SZ, P, I32, U64, U64, P, SZ, P, SZ, ctypes.POINTER(U64)]),
     "qs_set_batch_cluster": (I32, [I32]),
     "qs_batch_free": (I32, [P]),
@@ -304,6 +308,29 @@ def qs_run_program(h: int, prog, gates, params=None, fuse: bool = False, seed: i
                               cb.ctypes.data if len(cb) else None, len(cb), rec.ctypes.data, record_cap,
                               ctypes.byref(nm)))
     return cb, rec[:min(nm.value, record_cap)].copy()
+
+
+def qs_run_noisy(h: int, gates, rules, params=None, rotation_error: float = 0.0, seed: int = 0,
+                 fuse: bool = True) -> int:
+    """One noise trajectory on the state; returns the number of draws used."""
+    g = as_gates(gates)
+    r = np.ascontiguousarray(rules)
+    if r.dtype != NOISE_DTYPE:
+        r = r.astype(NOISE_DTYPE)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    nd = ctypes.c_uint64()
+    _chk(lib().qs_run_noisy(h, g.ctypes.data if len(g) else None, len(g), None if pr is None else pr.ctypes.data,
+                            r.ctypes.data if len(r) else None, len(r), rotation_error, seed, 1 if fuse else 0,
+                            ctypes.byref(nd)))
+    return nd.value
+
+
+def qs_readout_error(samples, n: int, f0: float, f1: float, seed: int, stream=None):
+    """Readout error in place on sampled indices (numpy uint64 array or CUDA tensor)."""
+    ptr, dev = _host_or_dev(samples)
+    count = samples.size if isinstance(samples, np.ndarray) else samples.numel()
+    _chk(lib().qs_readout_error(ptr, count, n, f0, f1, seed, dev, _stream_ptr(stream)))
+    return samples
 
 
 def qs_apply_matrix(h: int, targets, mat, ctrl_mask: int = 0):

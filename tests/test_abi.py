@@ -70,6 +70,24 @@ def test_program_codes_and_layout_agree_with_header(tmp_path):
     assert got == [w.PINSTR_DTYPE.itemsize] + [w.PINSTR_DTYPE.fields[f][1] for f in fields]
 
 
+def test_noise_codes_and_layout_agree_with_header(tmp_path):
+    text = open(os.path.join(ROOT, "include", "qsim.h")).read()
+    for name, code in w.NOISE_MODELS.items():
+        m = re.search(rf"QS_NOISE_{name}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == code, name
+    from paper_2212_14201_gb300 import NOISE_DTYPE
+    assert NOISE_DTYPE == w.NOISE_DTYPE
+    src = tmp_path / "lay.c"
+    fields = ["model", "gate_type", "q0", "q1", "p", "t1", "t2", "tgate"]
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "qsim.h"\nint main(void){printf("%zu'
+                   + "".join(" %zu" for _ in fields) + '\\n", sizeof(qs_noise_rule)'
+                   + "".join(f", offsetof(qs_noise_rule, {f})" for f in fields) + ");return 0;}\n")
+    exe = tmp_path / "lay"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [w.NOISE_DTYPE.itemsize] + [w.NOISE_DTYPE.fields[f][1] for f in fields]
+
+
 def test_host_validation_without_gpu(built):
     import paper_2212_14201_gb300 as q
     with pytest.raises(q.QsimError) as e:
