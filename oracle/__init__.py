@@ -69,6 +69,7 @@ def _load():
                 "or_run_noisy": (i32, [P, i32, P, i64, P, P, i64, ctypes.c_double, u64, P]),
                 "or_readout": (None, [P, i64, i32, ctypes.c_double, ctypes.c_double, u64]),
                 "or_dm_run": (i32, [P, i32, P, i64, P, P, i64]),
+                "or_partial_amplitudes": (i32, [i32, P, i64, P, i32, P, i64, P, P]),
                 "or_run_program": (i32, [P, i32, P, i64, P, i64, P, u64, u64, P, i64, P, i64, P]),
             }
             for name, (res, args) in sig.items():
@@ -319,3 +320,17 @@ def dm_run(n: int, gates: np.ndarray, rules: np.ndarray, params=None) -> np.ndar
     _chk(_load().or_dm_run(rho.ctypes.data, n, _ptr(gates) if len(gates) else None, len(gates), _ptr(pr),
                            _ptr(rules) if len(rules) else None, len(rules)), "or_dm_run")
     return rho.view(np.complex128).reshape(N, N)
+
+
+def partial_amplitudes(n: int, gates: np.ndarray, n_low: int, indices, params=None):
+    """Amplitudes <x|U|0...0> for the listed x by cutting the gates that cross the
+    split (qubits < n_low | the rest): (complex array, number of paths)."""
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    out = np.empty(2 * len(idx), dtype=np.float64)
+    gates = np.ascontiguousarray(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    npaths = ctypes.c_uint64()
+    _chk(_load().or_partial_amplitudes(n, _ptr(gates) if len(gates) else None, len(gates), _ptr(pr), n_low,
+                                       idx.ctypes.data, len(idx), out.ctypes.data, ctypes.byref(npaths)),
+         "or_partial_amplitudes")
+    return out.view(np.complex128).copy(), npaths.value

@@ -1068,3 +1068,83 @@ int or_dm_run(double* rho_out, int n, const or_gate* gates, int64_t ng, const do
   free(tmp);
   return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Partial amplitudes (the paper's PartialAmpQVM, Section "Multi-simulation   */
+/* methods", noise-free simulation method): the qubits are split into a low   */
+/* block (0 .. n_low-1) and a high block; every gate with qubits in both      */
+/* blocks is cut.  A controlled gate with target t, controls C_t in t's block */
+/* and C_o in the other block is                                              */
+/*   P(C_o all 1) (x) [U on t controlled by C_t]  +  (I - P(C_o all 1)) (x) I */
+/* so k cut gates turn the circuit into 2^k products of block circuits; path  */
+/* bit i = 1 takes the first term of cut i.  <x|psi> = sum over paths of      */
+/* <x_low|lo_path> <x_high|hi_path>.                                          */
+/* ------------------------------------------------------------------------- */
+static void project_ones(cplx* psi, int n, uint64_t mask, int keep_all_ones) {
+  const int64_t N = (int64_t)1 << n;
+  for (int64_t x = 0; x < N; ++x) {
+    const int all = ((uint64_t)x & mask) == mask;
+    if (all != keep_all_ones) psi[x] = c_make(0, 0);
+  }
+}
+
+int or_partial_amplitudes(int n, const or_gate* gates, int64_t ng, const double* params, int n_low,
+                          const uint64_t* idx, int64_t count, double* out_amps, uint64_t* npaths) {
+  if (n_low < 1 || n_low >= n || n > 24) return OR_EINVAL;
+  const int nh = n - n_low;
+  const uint64_t lowmask = ((uint64_t)1 << n_low) - 1;
+  /* cut gates */
+  int64_t k = 0;
+  for (int64_t g = 0; g < ng; ++g) {
+    int t;
+    uint64_t cm;
+    int rc = qubits_of(&gates[g], n, &t, &cm);
+    if (rc) return rc;
+    const uint64_t all = cm | ((uint64_t)1 << t);
+    if ((all & lowmask) && (all & ~lowmask)) ++k;
+  }
+  if (k > 20) return OR_EUNSUPPORTED;
+  cplx* lo = (cplx*)malloc(sizeof(cplx) << n_low);
+  cplx* hi = (cplx*)malloc(sizeof(cplx) << nh);
+  cplx* out = (cplx*)out_amps;
+  if (!lo || !hi) { free(lo); free(hi); return OR_ENOMEM; }
+  for (int64_t i = 0; i < count; ++i) out[i] = c_make(0, 0);
+  int rc = OR_OK;
+  for (uint64_t path = 0; path < ((uint64_t)1 << k) && rc == OR_OK; ++path) {
+    or_init_zero((double*)lo, n_low);
+    or_init_zero((double*)hi, nh);
+    int64_t cut = 0;
+    for (int64_t g = 0; g < ng && rc == OR_OK; ++g) {
+      int t;
+      uint64_t cm;
+      cplx U[4];
+      if ((rc = resolve(&gates[g], n, params, &t, &cm, U)) != OR_OK) break;
+      const uint64_t all = cm | ((uint64_t)1 << t);
+      const int t_low = t < n_low;
+      if (!((all & lowmask) && (all & ~lowmask))) {     /* inside one block */
+        if (t_low) apply_2x2(lo, n_low, t, cm, U);
+        else apply_2x2(hi, nh, t - n_low, cm >> n_low, U);
+        continue;
+      }
+      const int bit = (int)((path >> cut) & 1);
+      ++cut;
+      const uint64_t c_low = cm & lowmask, c_high = cm >> n_low;
+      if (t_low) {
+        if (bit) apply_2x2(lo, n_low, t, c_low, U);
+        project_ones(hi, nh, c_high, bit);
+      } else {
+        if (bit) apply_2x2(hi, nh, t - n_low, c_high, U);
+        project_ones(lo, n_low, c_low, bit);
+      }
+    }
+    for (int64_t i = 0; i < count && rc == OR_OK; ++i) {
+      const uint64_t x = idx[i];
+      if (x >> n) { rc = OR_EINVAL; break; }
+      out[i] = c_add(out[i], c_mul(lo[x & lowmask], hi[x >> n_low]));
+    }
+  }
+  free(lo);
+  free(hi);
+  if (npaths) *npaths = (uint64_t)1 << k;
+  return rc;
+}
