@@ -427,6 +427,21 @@ def bench_noisy(q, torch, stream):
     return out
 
 
+def bench_partial(q, torch):
+    """Partial amplitudes at n=40 (a 16 TiB state): the depth-20 brickwork cut
+    between qubits 19 and 20 (10 CZ cuts, 1024 paths of two 20-qubit blocks),
+    10^6 random basis indices (seed 5)."""
+    n = 40
+    g = w.layered_u3_cz(n, 20, 1)
+    idx = np.random.Generator(np.random.PCG64(5)).integers(0, 1 << n, 1_000_000, dtype=np.uint64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    amps, paths = q.qs_partial_amplitudes(n, g, 20, idx)
+    dt = time.perf_counter() - t0
+    return {"n": n, "gates": len(g), "paths": paths, "amplitudes": len(idx), "s": dt,
+            "amplitudes_per_s": len(idx) / dt, "mean_p_times_2n": float(np.mean(np.abs(amps) ** 2)) * 2.0 ** n}
+
+
 def bench_learned_plan(q, torch, stream):
     """n=32 (64 GiB), 2000 random gates (40 % two-qubit, seed 2): greedy plan vs
     the learned plan (cost model from paper_2212_14201_gb300/costmodel_weights.json)
@@ -575,6 +590,7 @@ def run_ours(args, world, rank, local, pg):
         extra["measure_n30"] = bench_measure(q, torch, stream, hbm_peak)
         extra["c64_n30"] = bench_c64(q, torch, stream, hbm_peak)
         extra["noisy_n28"] = bench_noisy(q, torch, stream)
+        extra["partial_n40"] = bench_partial(q, torch)
         if not args.no_n32:
             try:
                 extra["learned_n32"] = bench_learned_plan(q, torch, stream)
@@ -620,6 +636,7 @@ def run_ours(args, world, rank, local, pg):
         "measure_n30": extra.get("measure_n30"),
         "c64_n30": extra.get("c64_n30"),
         "noisy_n28": extra.get("noisy_n28"),
+        "partial_n40": extra.get("partial_n40"),
     }
     print(json.dumps(line), flush=True)
 

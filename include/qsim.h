@@ -459,6 +459,27 @@ int qs_run_noisy(qs_state* s, const qs_gate* gates, size_t ng, const double* par
 int qs_readout_error(uint64_t* samples, size_t shots, int n, double f0, double f1, uint64_t seed, int on_device,
                      void* stream);
 
+/* ---- partial amplitudes (PartialAmpQVM, Section "Multi-simulation methods":
+ * cut the two-qubit gates across a bisection into sums of products and simulate
+ * the two halves) ---------------------------------------------------------------- */
+
+/* Amplitudes <x|U|0...0> of an n-qubit program (2 <= n <= 64) for the count
+ * basis indices in `indices` (host), written to out (host, count interleaved
+ * complex128), without the 2^n state.  Qubits 0 .. n_low-1 form the low block,
+ * the rest the high block (each at most qs_max_qubits()).  Every gate with
+ * qubits in both blocks is cut: with target t, controls C_t in t's block and C_o
+ * in the other, it is P(C_o all 1) (x) [U on t, controls C_t] + (I - P(C_o all
+ * 1)) (x) I.  k cuts give 2^k paths (k <= 30); each path simulates both blocks
+ * (fused per uncut stretch if fuse != 0), and the amplitude is the sum over paths
+ * of <x_low|lo> <x_high|hi>, added in a fixed path order.  Consecutive paths share
+ * their early cuts, so a block resumes from a snapshot before its first changed
+ * cut (device memory: one block state per cut item of that block).  *npaths
+ * (nullable) receives 2^k.  Runs on `stream`; synchronous.
+ * Errors: INVALID_ARG, UNSUPPORTED (block too large, more than 30 cuts), OOM, CUDA. */
+int qs_partial_amplitudes(int n, const qs_gate* gates, size_t ng, const double* params, int n_low,
+                          const uint64_t* indices, size_t count, double* out, int fuse, void* stream,
+                          uint64_t* npaths);
+
 /* ---- batched variational evaluation (the hybrid quantum-classical loop of
  * Sections "Support hybrid quantum-classical algorithm" and "Variational
  * quantum circuit": many parameter sets evaluated per optimiser step) -------- */

@@ -112,6 +112,7 @@ SIGNATURES = {
     "qs_measure": (I32, [P, I32, DBL, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(DBL)]),
     "qs_run_noisy": (I32, [P, P, SZ, P, P, SZ, DBL, U64, I32, ctypes.POINTER(U64)]),
     "qs_readout_error": (I32, [P, SZ, I32, DBL, DBL, U64, I32, P]),
+    "qs_partial_amplitudes": (I32, [I32, P, SZ, P, I32, P, SZ, P, I32, P, ctypes.POINTER(U64)]),
     "qs_run_program": (I32, [P, P, SZ, P, SZ, P, I32, U64, U64, P, SZ, P, SZ, ctypes.POINTER(U64)]),
     "qs_set_batch_cluster": (I32, [I32]),
     "qs_batch_free": (I32, [P]),
@@ -331,6 +332,22 @@ def qs_readout_error(samples, n: int, f0: float, f1: float, seed: int, stream=No
     count = samples.size if isinstance(samples, np.ndarray) else samples.numel()
     _chk(lib().qs_readout_error(ptr, count, n, f0, f1, seed, dev, _stream_ptr(stream)))
     return samples
+
+
+def qs_partial_amplitudes(n: int, gates, n_low: int, indices, params=None, fuse: bool = True, stream=None):
+    """Selected amplitudes of an n-qubit program by cutting the gates across the
+    split at n_low: (complex128 array, number of paths)."""
+    g = as_gates(gates)
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    out = np.empty(len(idx), dtype=np.complex128)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    npaths = ctypes.c_uint64()
+    _chk(lib().qs_partial_amplitudes(n, g.ctypes.data if len(g) else None, len(g),
+                                     None if pr is None else pr.ctypes.data, n_low,
+                                     idx.ctypes.data if len(idx) else None, len(idx),
+                                     out.ctypes.data if len(idx) else None, 1 if fuse else 0,
+                                     _stream_ptr(stream), ctypes.byref(npaths)))
+    return out, npaths.value
 
 
 def qs_apply_matrix(h: int, targets, mat, ctrl_mask: int = 0):
