@@ -227,8 +227,9 @@ int qs_set_aggregate(int on);
  * the switch is for measurement.  Errors: INVALID_ARG for other values. */
 int qs_set_register_phases(int bits);
 
-/* Greedy plan with an explicit tile width: tiles of tile_qubits (4..12) qubits,
- * the "block size" of the fusion.  qs_plan_create(GREEDY) uses 12. */
+/* Greedy plan with an explicit tile width: tiles of tile_qubits (4..13) qubits,
+ * the "block size" of the fusion (13: 128 KiB tiles, one 512-thread CTA per SM).
+ * qs_plan_create(GREEDY) uses 12. */
 int qs_plan_create_tiled(int n, const qs_gate* gates, size_t ng, int tile_qubits, qs_plan** out);
 
 /* Pass `pass` of a plan (0 <= pass < n_passes): *kind (0 = one plain gate,

@@ -34,7 +34,7 @@ struct qs_plan {
   int n = 0;
   int mode = 0;
   int kmax = 1;
-  int m = TILE_MAX_M;
+  int m = TILE_DEFAULT_M;
   size_t ng = 0;
   uint64_t fingerprint = 0;
   std::vector<PlanPass> passes;
@@ -306,7 +306,7 @@ static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax
 
 extern "C" int qs_plan_create(int n, const qs_gate* gates, size_t ng, int mode, int kmax, qs_plan** out) {
   clear_error();
-  return plan_build(n, gates, ng, mode, kmax, TILE_MAX_M, out);
+  return plan_build(n, gates, ng, mode, kmax, TILE_DEFAULT_M, out);
 }
 
 extern "C" int qs_plan_create_tiled(int n, const qs_gate* gates, size_t ng, int tile_qubits, qs_plan** out) {
@@ -366,7 +366,7 @@ extern "C" int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs
   std::vector<size_t> first;
   int rc = QS_OK;
   // candidate tile widths 8..12: narrower tiles leave most of a CTA idle per op
-  const int mhi = std::min(n, TILE_MAX_M);
+  const int mhi = std::min(n, TILE_DEFAULT_M);
   const int mlo = std::min(mhi, 8);
   for (int m = mlo; m <= mhi && rc == QS_OK; ++m) {
     qs_plan* c = nullptr;

@@ -357,11 +357,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tile_reg(double2* __restrict_
     for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = EngQ60::store(tile[j]);
   }
 }
-template <class E>
-static int launch_engine(qs_state* s, const TileArgs& g) {
-  const size_t H = (size_t)1 << g.nhigh;
-  const size_t smem = ((H * sizeof(uint64_t) + 15) & ~(size_t)15) + (sizeof(typename E::T) << g.m);
-  constexpr int THREADS = 256;  // measured at n=30: 512 (2 CTAs/SM) and 1024 (1/SM) are 2-6% slower
+template <class E, int THREADS>
+static int launch_engine_t(qs_state* s, const TileArgs& g, size_t smem) {
   static bool attr_set = false;
   static int sms = 0;
   if (!attr_set) {
@@ -374,6 +371,17 @@ static int launch_engine(qs_state* s, const TileArgs& g) {
   const uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)std::max(1, sms) * std::max(1, per_sm));
   k_tile<E, THREADS><<<(unsigned)grid, THREADS, smem, s->stream>>>(reinterpret_cast<typename E::G*>(s->amps), g);
   return launch_check("tile kernel");
+}
+
+// 256 threads per CTA (measured at n=30, 12-qubit tiles: 512 threads with 2 CTAs
+// per SM and 1024 with one are 2-6 % slower); a 13-qubit tile (one CTA per SM)
+// runs 512 threads.
+template <class E>
+static int launch_engine(qs_state* s, const TileArgs& g) {
+  const size_t H = (size_t)1 << g.nhigh;
+  const size_t smem = ((H * sizeof(uint64_t) + 15) & ~(size_t)15) + (sizeof(typename E::T) << g.m);
+  if (g.m >= 13) return launch_engine_t<E, 512>(s, g, smem);
+  return launch_engine_t<E, 256>(s, g, smem);
 }
 
 int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, int ngates, bool fixed) {

@@ -8,7 +8,8 @@
 
 namespace qs {
 
-constexpr int TILE_MAX_M = 12;  // 2^12 amplitudes x 16 B = 64 KiB of shared memory per CTA
+constexpr int TILE_MAX_M = 13;      // widest tile: 2^13 x 16 B = 128 KiB of shared memory per CTA
+constexpr int TILE_DEFAULT_M = 12;  // greedy plans: 2^12 x 16 B = 64 KiB, 3 CTAs per SM
 constexpr int TILE_LOW = 3;     // qubits 0..2 are always in a tile: 128-byte contiguous runs
 constexpr int TILE_MAX_OPS = 256;
 constexpr int TILE_MAX_PHASES = 256;
