@@ -220,6 +220,18 @@ int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out);
  * within rounding (the 2x2 products are formed in double).  Always QS_OK. */
 int qs_set_aggregate(int on);
 
+/* Process-wide switch (default on) for phase tables in Q60 tile passes.  An
+ * uncontrolled general one-qubit op factors exactly as diag R diag with R real
+ * (the ZYZ Euler form); within a pass the diagonal factors of many qubits, and
+ * the plain diagonal gates between them, commute into one table op
+ * a_j *= Tlo[j_lo] Thi[j_hi] (tables of 64 and 128 phases over the tile's low
+ * and high bits), leaving real rotations: 12 instead of 18 limb products per
+ * amplitude.  A table is built only where at least three general ops become
+ * real.  The tables are staged through pinned memory per pass, so a qs_apply
+ * with a plan is not stream-capturable while this is on.  Results agree with
+ * the switch off within rounding (factors formed in double).  Always QS_OK. */
+int qs_set_phase_tables(int on);
+
 /* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops
  * of a pass into register phases (runs of ops whose targets fit in `bits` tile
  * qubits execute on the 2^bits amplitudes a thread holds in registers); 0
@@ -239,6 +251,27 @@ int qs_plan_create_tiled(int n, const qs_gate* gates, size_t ng, int tile_qubits
  * order applies the same unitary as the program. */
 int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask, uint32_t* gates, size_t cap,
                       size_t* ngates);
+
+/* The op list a tile pass runs (introspection; host only, no device work): the
+ * pass's gates after aggregation (qs_set_aggregate) and, when q60 != 0 and
+ * phase tables are on (qs_set_phase_tables), after the general ops were split
+ * into real rotations and phase tables.  Applying the ops in order is the pass's
+ * gates in order (up to rounding).  Kind 0: the 2x2 matrix m (row-major,
+ * interleaved complex) on `target` with controls ctrl_mask.  Kind 1: phase table
+ * `table`: amplitude x gets Tlo[j & (2^nlo - 1)] * Thi[j >> nlo], j = the bits of
+ * x at the pass's qubits in ascending order; tables[t] holds 64 + 128 complex
+ * (interleaved) entries, Tlo first.  *count / *ntables receive the totals (only
+ * the first cap ops and table_cap tables are written). */
+typedef struct qs_pass_op {
+  int32_t kind;
+  int32_t target;
+  uint64_t ctrl_mask;
+  double m[8];
+  int32_t table, nlo;
+} qs_pass_op;
+int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
+                     int q60, qs_pass_op* ops, size_t cap, size_t* count, double* tables, size_t table_cap,
+                     size_t* ntables);
 
 /* ---- learned fusion cost model (not in the paper, whose fusion has no cost
  * model): a 3-layer tanh perceptron h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),

@@ -45,6 +45,11 @@ class PlanStats(ctypes.Structure):
                 ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double), ("tile_qubits", ctypes.c_int64)]
 
 
+class PassOp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("target", ctypes.c_int32), ("ctrl_mask", ctypes.c_uint64),
+                ("m", ctypes.c_double * 8), ("table", ctypes.c_int32), ("nlo", ctypes.c_int32)]
+
+
 class TimingRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("k", ctypes.c_int32), ("n_ops", ctypes.c_int32),
                 ("qubit_mask", ctypes.c_uint64), ("ctrl_mask", ctypes.c_uint64), ("items", ctypes.c_double),
@@ -94,6 +99,9 @@ SIGNATURES = {
     "qs_expect_z_all_noalloc": (I32, [P, I32, P, P]),
     "qs_set_adjoint_fused": (I32, [I32]),
     "qs_set_aggregate": (I32, [I32]),
+    "qs_set_phase_tables": (I32, [I32]),
+    "qs_plan_pass_ops": (I32, [P, SZ, P, SZ, P, I32, ctypes.POINTER(PassOp), SZ, ctypes.POINTER(SZ), P, SZ,
+                               ctypes.POINTER(SZ)]),
     "qs_mlp_create": (I32, [I32, I32, P, U64, PP]),
     "qs_mlp_free": (I32, [P]),
     "qs_mlp_num_weights": (I32, [P, ctypes.POINTER(SZ)]),
@@ -378,6 +386,10 @@ def qs_set_aggregate(on: bool):
     _chk(lib().qs_set_aggregate(1 if on else 0))
 
 
+def qs_set_phase_tables(on: bool):
+    _chk(lib().qs_set_phase_tables(1 if on else 0))
+
+
 def qs_set_register_phases(bits: int):
     _chk(lib().qs_set_register_phases(int(bits)))
 
@@ -407,6 +419,29 @@ def qs_plan_pass_info(p: int, i: int):
     _chk(lib().qs_plan_pass_info(p, i, ctypes.byref(kind), ctypes.byref(qm), idx.ctypes.data, cnt.value,
                                  ctypes.byref(cnt)))
     return kind.value, qm.value, idx[:cnt.value].copy()
+
+
+def qs_plan_pass_ops(p: int, i: int, gates, params=None, q60: bool = True):
+    """(ops, tables) a tile pass runs: ops as dicts (kind 0: target, ctrl_mask,
+    2x2 complex matrix; kind 1: table index, nlo), tables as (64 + 128) complex
+    arrays."""
+    g = as_gates(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    cnt, nt = ctypes.c_size_t(), ctypes.c_size_t()
+    args = (p, i, g.ctypes.data if len(g) else None, len(g), None if pr is None else pr.ctypes.data, 1 if q60 else 0)
+    _chk(lib().qs_plan_pass_ops(*args, None, 0, ctypes.byref(cnt), None, 0, ctypes.byref(nt)))
+    ops = (PassOp * max(1, cnt.value))()
+    tab = np.zeros(max(1, nt.value) * 2 * 192, dtype=np.float64)
+    _chk(lib().qs_plan_pass_ops(*args, ops, cnt.value, ctypes.byref(cnt), tab.ctypes.data, nt.value, ctypes.byref(nt)))
+    out = []
+    for o in ops[:cnt.value]:
+        if o.kind == 1:
+            out.append({"kind": 1, "table": o.table, "nlo": o.nlo})
+        else:
+            m = np.array(o.m[:]).view(np.complex128).reshape(2, 2)
+            out.append({"kind": 0, "target": o.target, "ctrl_mask": o.ctrl_mask, "m": m})
+    tables = tab.view(np.complex128).reshape(-1, 192)[:nt.value].copy()
+    return out, tables
 
 
 def qs_plan_passes(p: int) -> list:

@@ -206,4 +206,15 @@ QS_HD void q60_gauss_row(const QC& u0, const QC& u1, QL r0, QL i0, QL s0, QL r1,
   *im = qacc_round(QAcc{k1.hi + k2.hi, k1.mid + k2.mid});
 }
 
+// One complex product u * a in Gauss form (u from qc_make_gauss), a = r + i i,
+// s = r + i (split): three limb products.
+QS_HD void q60_gauss_mul(const QC& u, QL r, QL i, QL s, int64_t* re, int64_t* im) {
+  QAcc k1 = qacc_new(), k2{0, 0}, k3{0, 0};
+  qacc_add(k1, u.re, s);
+  qacc_add(k2, u.im, r);
+  qacc_add(k3, u.nim, i);
+  *re = qacc_round(QAcc{k1.hi - k3.hi, k1.mid - k3.mid});
+  *im = qacc_round(QAcc{k1.hi + k2.hi, k1.mid + k2.mid});
+}
+
 }  // namespace qs

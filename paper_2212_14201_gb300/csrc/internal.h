@@ -40,6 +40,13 @@ struct qs_state {
   bool timing = false;
   std::vector<qs_pending_timing> pending;
   std::vector<cudaEvent_t> event_pool;
+  // Phase tables of tile passes: device copy, pinned staging, and the event of the
+  // last upload (the staging buffer is rewritten only after that copy ran).
+  void* tables = nullptr;
+  size_t tables_bytes = 0;
+  void* tables_pinned = nullptr;
+  size_t tables_pinned_bytes = 0;
+  cudaEvent_t tables_ev = nullptr;
 };
 
 namespace qs {

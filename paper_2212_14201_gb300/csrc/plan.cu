@@ -14,6 +14,8 @@
 // pass (their target may lie outside Q: a per-tile scalar).
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -191,6 +193,233 @@ static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const
     ops.push_back(op);
   }
   return QS_OK;
+}
+
+// ---- phase tables ----------------------------------------------------------------
+// An uncontrolled general one-qubit unitary U = [[a, b], [c, d]] (all entries
+// nonzero) factors exactly as diag(p1, p2) R diag(1, q2) with R = [[|a|, -|c|],
+// [|c|, |a|]] real (the ZYZ Euler form): p1 = a/|a|, p2 = c/|c|, q2 = d/(p2 |a|).
+// Diagonals commute with each other, with diagonal gates and with gates that use
+// their qubit only as a control, so within a tile pass the phases of many qubits
+// collect into one table op, diag(prod_q d_q(j_q)) = Tlo[j_lo] Thi[j_hi], and the
+// general ops shrink to real rotations (12 instead of 18 limb products per
+// amplitude).  A flush emits the pending phases before an op that does not
+// commute with them, pulling forward the right factors of the next general op of
+// every qubit (and the plain diagonal gates before it); it builds a table only
+// when at least kTableMinPulls general ops become real, else the pending phase of
+// the op's qubit is folded into that op (or emitted as a diagonal op).
+constexpr int kTableMinPulls = 3;
+static bool g_phase_tables = true;
+
+extern "C" int qs_set_phase_tables(int on) {
+  g_phase_tables = on != 0;
+  return QS_OK;
+}
+
+static C2 cmul2(C2 x, C2 y) { return {x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re}; }
+static C2 cdiv2(C2 x, C2 y) {
+  const double d = y.re * y.re + y.im * y.im;
+  return {(x.re * y.re + x.im * y.im) / d, (x.im * y.re - x.re * y.im) / d};
+}
+
+struct Zyz {
+  C2 p1, p2, q2;
+  Mat2 R;
+};
+
+static Zyz zyz(const Mat2& U) {
+  Zyz z;
+  const double aa = std::hypot(U.m[0].re, U.m[0].im), cc = std::hypot(U.m[2].re, U.m[2].im);
+  z.p1 = {U.m[0].re / aa, U.m[0].im / aa};
+  z.p2 = {U.m[2].re / cc, U.m[2].im / cc};
+  z.q2 = cdiv2(U.m[3], {z.p2.re * aa, z.p2.im * aa});
+  z.R.m[0] = {aa, 0.0};
+  z.R.m[1] = {-cc, 0.0};
+  z.R.m[2] = {cc, 0.0};
+  z.R.m[3] = {aa, 0.0};
+  return z;
+}
+
+struct PhaseTable {
+  int nlo;
+  C2 lo[DTABLE_LO], hi[DTABLE_HI];
+};
+
+// Rewrites ops (one pass, pass order) into real rotations, phase-table markers
+// (cls = kTableMark, target = table index) and the other ops unchanged.
+constexpr int kTableMark = 100;
+
+static bool diag_cls(int c) { return c == OP_DIAG || c == OP_PHASE1 || c == OP_IDENTITY; }
+
+static void extract_phases(const std::vector<Op1>& ops, const int* local, int n, int m, std::vector<Op1>* out,
+                           std::vector<PhaseTable>* tables) {
+  const size_t N = ops.size();
+  out->clear();
+  std::vector<char> consumed(N, 0), pulled(N, 0);
+  std::vector<Zyz> z(N);
+  std::vector<char> elig(N, 0);
+  for (size_t i = 0; i < N; ++i)
+    if (ops[i].cls == OP_GENERAL && ops[i].cmask == 0 && local[ops[i].target] >= 0) {
+      elig[i] = 1;
+      z[i] = zyz(ops[i].m);
+    }
+  C2 d0[TILE_MAX_M], d1[TILE_MAX_M];
+  bool has[TILE_MAX_M];
+  int gq[TILE_MAX_M];  // tile bit -> global qubit (local[] is defined for qubits 0..n-1)
+  for (int b = 0; b < TILE_MAX_M; ++b) gq[b] = 0;
+  for (int b = 0; b < n; ++b)
+    if (local[b] >= 0 && local[b] < m) gq[local[b]] = b;
+  auto reset = [&](int b) {
+    d0[b] = {1.0, 0.0};
+    d1[b] = {1.0, 0.0};
+    has[b] = false;
+  };
+  for (int b = 0; b < m; ++b) reset(b);
+  auto absorb = [&](int b, C2 e0, C2 e1) {
+    d0[b] = cmul2(d0[b], e0);
+    d1[b] = cmul2(d1[b], e1);
+    has[b] = true;
+  };
+  auto diag_of = [&](const Op1& o, C2* e0, C2* e1) {
+    *e0 = o.cls == OP_PHASE1 ? C2{1.0, 0.0} : o.m.m[0];
+    *e1 = o.m.m[3];
+  };
+  auto emit_diag = [&](int b) {
+    if (!has[b]) return;
+    Mat2 M;
+    M.m[0] = d0[b];
+    M.m[1] = {0.0, 0.0};
+    M.m[2] = {0.0, 0.0};
+    M.m[3] = d1[b];
+    const Op1 o = classify(gq[b], 0, M);
+    if (o.cls != OP_IDENTITY) out->push_back(o);
+    reset(b);
+  };
+  // candidate pulls for a flush before op i: per tile bit, the diagonal gates
+  // before its next general op, and that op
+  struct Pull {
+    std::vector<size_t> diags;
+    long gen = -1;
+  };
+  auto plan_pulls = [&](size_t i, Pull* P) {
+    int count = 0;
+    for (int b = 0; b < m; ++b) {
+      P[b] = Pull();
+      const int q = gq[b];
+      for (size_t j = i; j < N; ++j) {
+        if (consumed[j] || ops[j].cls == OP_IDENTITY) continue;
+        const Op1& o = ops[j];
+        if (o.target != q) continue;  // untouched, or q only a control: commutes
+        if (diag_cls(o.cls)) {
+          if (o.cmask == 0) P[b].diags.push_back(j);
+          continue;
+        }
+        if (elig[j] && !pulled[j]) {
+          P[b].gen = (long)j;
+          ++count;
+        }
+        break;
+      }
+    }
+    return count;
+  };
+  auto commit = [&](Pull* P) {
+    for (int b = 0; b < m; ++b) {
+      for (size_t j : P[b].diags) {
+        C2 e0, e1;
+        diag_of(ops[j], &e0, &e1);
+        absorb(b, e0, e1);
+        consumed[j] = 1;
+      }
+      if (P[b].gen >= 0) {
+        absorb(b, {1.0, 0.0}, z[P[b].gen].q2);
+        pulled[P[b].gen] = 1;
+      }
+    }
+    int cnt = 0;
+    for (int b = 0; b < m; ++b) cnt += has[b];
+    if (cnt < 2) {
+      for (int b = 0; b < m; ++b) emit_diag(b);
+      return;
+    }
+    PhaseTable t{};
+    t.nlo = std::min(m, 6);
+    const int nhi = m - t.nlo;
+    for (int j = 0; j < (1 << t.nlo); ++j) {
+      C2 v = {1.0, 0.0};
+      for (int b = 0; b < t.nlo; ++b) v = cmul2(v, ((j >> b) & 1) ? d1[b] : d0[b]);
+      t.lo[j] = v;
+    }
+    for (int j = 0; j < (1 << nhi); ++j) {
+      C2 v = {1.0, 0.0};
+      for (int b = 0; b < nhi; ++b) v = cmul2(v, ((j >> b) & 1) ? d1[t.nlo + b] : d0[t.nlo + b]);
+      t.hi[j] = v;
+    }
+    Op1 mark{};
+    mark.cls = kTableMark;
+    mark.target = (int)tables->size();
+    tables->push_back(t);
+    out->push_back(mark);
+    for (int b = 0; b < m; ++b) reset(b);
+  };
+  std::vector<Pull> P(m);
+  for (size_t i = 0; i < N; ++i) {
+    if (consumed[i] || ops[i].cls == OP_IDENTITY) continue;
+    const Op1& o = ops[i];
+    const int b = local[o.target];
+    if (b < 0) {  // diagonal on a qubit outside the tile: commutes with every table
+      out->push_back(o);
+      continue;
+    }
+    if (diag_cls(o.cls)) {
+      if (o.cmask == 0) {
+        C2 e0, e1;
+        diag_of(o, &e0, &e1);
+        absorb(b, e0, e1);
+      } else {
+        out->push_back(o);
+      }
+      continue;
+    }
+    if (elig[i] && pulled[i]) {  // its right factor is already in a table
+      emit_diag(b);                // (nothing is pending here: a pull takes every diagonal before it)
+      out->push_back(classify(o.target, 0, z[i].R));
+      absorb(b, z[i].p1, z[i].p2);
+      continue;
+    }
+    // o does not commute with the pending phase of its target
+    if (plan_pulls(i, P.data()) >= kTableMinPulls) {
+      commit(P.data());
+      if (elig[i]) {  // pulled by the commit
+        out->push_back(classify(o.target, 0, z[i].R));
+        absorb(b, z[i].p1, z[i].p2);
+        continue;
+      }
+      out->push_back(o);
+      continue;
+    }
+    if (has[b] && elig[i]) {  // fold the pending phase into the op: U diag(d0, d1)
+      Mat2 M = o.m;
+      M.m[0] = cmul2(M.m[0], d0[b]);
+      M.m[2] = cmul2(M.m[2], d0[b]);
+      M.m[1] = cmul2(M.m[1], d1[b]);
+      M.m[3] = cmul2(M.m[3], d1[b]);
+      reset(b);
+      out->push_back(classify(o.target, o.cmask, M));
+      continue;
+    }
+    emit_diag(b);
+    out->push_back(o);
+  }
+  // what is left at the end of the pass
+  int cnt = 0;
+  for (int b = 0; b < m; ++b) cnt += has[b];
+  if (cnt >= 2) {
+    std::vector<Pull> none(m);
+    commit(none.data());
+  } else {
+    for (int b = 0; b < m; ++b) emit_diag(b);
+  }
 }
 
 uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
@@ -430,6 +659,66 @@ extern "C" int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint6
   return QS_OK;
 }
 
+static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const double* params, bool tables_ok,
+                          std::vector<Op1>* rops, std::vector<PhaseTable>* ptables, int* local, int* m_out);
+
+extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
+                                int q60, qs_pass_op* ops, size_t cap, size_t* count, double* tables,
+                                size_t table_cap, size_t* ntables) {
+  clear_error();
+  if (!p || !count || !ntables || (cap && !ops) || (table_cap && !tables))
+    return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  if (pass >= p->passes.size()) return fail(QS_ERR_INVALID_ARG, "pass %zu of %zu", pass, p->passes.size());
+  if (p->ng != ng || p->fingerprint != fingerprint(gates, ng)) return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
+  QS_TRY(validate_gates(gates, ng, p->n, params));
+  const PlanPass& ps = p->passes[pass];
+  std::vector<Op1> rops;
+  std::vector<PhaseTable> pt;
+  int local[64];
+  int m = 0;
+  if (ps.kind == PASS_TILE) {
+    QS_TRY(build_pass_ops(p->n, ps, gates, params, q60 != 0, &rops, &pt, local, &m));
+  } else {
+    int t;
+    uint64_t cm;
+    Mat2 mat;
+    QS_TRY(gate_qubits(gates[ps.gates[0]], p->n, &t, &cm));
+    QS_TRY(gate_matrix(gates[ps.gates[0]], params, &mat));
+    rops.push_back(classify(t, cm, mat));
+  }
+  *count = rops.size();
+  *ntables = pt.size();
+  for (size_t i = 0; i < rops.size() && i < cap; ++i) {
+    qs_pass_op& o = ops[i];
+    memset(&o, 0, sizeof o);
+    if (rops[i].cls == kTableMark) {
+      o.kind = 1;
+      o.table = rops[i].target;
+      o.nlo = pt[rops[i].target].nlo;
+      continue;
+    }
+    o.kind = 0;
+    o.target = rops[i].target;
+    o.ctrl_mask = rops[i].cmask;
+    for (int e = 0; e < 4; ++e) {
+      o.m[2 * e] = rops[i].m.m[e].re;
+      o.m[2 * e + 1] = rops[i].m.m[e].im;
+    }
+  }
+  for (size_t t = 0; t < pt.size() && t < table_cap; ++t) {
+    double* d = tables + t * 2 * (DTABLE_LO + DTABLE_HI);
+    for (int k = 0; k < DTABLE_LO; ++k) {
+      d[2 * k] = pt[t].lo[k].re;
+      d[2 * k + 1] = pt[t].lo[k].im;
+    }
+    for (int k = 0; k < DTABLE_HI; ++k) {
+      d[2 * (DTABLE_LO + k)] = pt[t].hi[k].re;
+      d[2 * (DTABLE_LO + k) + 1] = pt[t].hi[k].im;
+    }
+  }
+  return QS_OK;
+}
+
 // Register phases for the Q60 tile kernel: consecutive ops are grouped while their
 // non-diagonal targets fit in `rb` tile bits; each phase is then padded to rb
 // bits with unused tile bits (highest first, which keeps shared-memory accesses of
@@ -479,6 +768,82 @@ extern "C" int qs_set_register_phases(int bits) {
   return QS_OK;
 }
 
+// Copies a pass's phase tables (Gauss form) to the device: pinned staging, one
+// asynchronous copy on the state's stream, an event so that the staging buffer is
+// rewritten only after that copy has run (the host waits, the stream does not).
+static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const QC** dev) {
+  const size_t per = DTABLE_LO + DTABLE_HI;
+  const size_t bytes = pt.size() * per * sizeof(QC);
+  if (!s->tables_ev) QS_CUDA(cudaEventCreateWithFlags(&s->tables_ev, cudaEventDisableTiming));
+  QS_CUDA(cudaEventSynchronize(s->tables_ev));
+  if (s->tables_pinned_bytes < bytes) {
+    if (s->tables_pinned) cudaFreeHost(s->tables_pinned);
+    s->tables_pinned = nullptr;
+    s->tables_pinned_bytes = 0;
+    QS_CUDA(cudaMallocHost(&s->tables_pinned, bytes));
+    s->tables_pinned_bytes = bytes;
+  }
+  if (s->tables_bytes < bytes) {
+    if (s->tables) {
+      QS_CUDA(cudaStreamSynchronize(s->stream));
+      cudaFree(s->tables);
+    }
+    s->tables = nullptr;
+    s->tables_bytes = 0;
+    QS_CUDA(cudaMalloc(&s->tables, bytes));
+    s->tables_bytes = bytes;
+  }
+  QC* host = (QC*)s->tables_pinned;
+  for (size_t t = 0; t < pt.size(); ++t) {
+    QC* dst = host + t * per;
+    for (int j = 0; j < DTABLE_LO; ++j) dst[j] = qc_make_gauss(pt[t].lo[j].re, pt[t].lo[j].im);
+    for (int j = 0; j < DTABLE_HI; ++j) dst[DTABLE_LO + j] = qc_make_gauss(pt[t].hi[j].re, pt[t].hi[j].im);
+  }
+  QS_CUDA(cudaMemcpyAsync(s->tables, host, bytes, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(cudaEventRecord(s->tables_ev, s->stream));
+  *dev = (const QC*)s->tables;
+  return QS_OK;
+}
+
+// The host op list of one tile pass (shared by the kernel path and
+// qs_plan_pass_ops): the pass's gates aggregated into fewer unitaries, then (Q60
+// engine) general ops split into real rotations and phase tables.  local[b] is
+// the tile bit of qubit b (-1 outside the tile), *m the tile width.
+static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const double* params, bool tables_ok,
+                          std::vector<Op1>* rops, std::vector<PhaseTable>* ptables, int* local, int* m_out) {
+  int m = 0;
+  for (int b = 0; b < 64; ++b) local[b] = -1;
+  for (int b = 0; b < n; ++b)
+    if ((ps.qmask >> b) & 1) local[b] = m++;
+  *m_out = m;
+  rops->clear();
+  ptables->clear();
+  int merged = 0;
+  if (g_aggregate) {
+    QS_TRY(aggregate_pass(n, ps, gates, params, rops, &merged));
+  } else {
+    for (uint32_t k : ps.gates) {
+      int t;
+      uint64_t cm;
+      Mat2 mat;
+      QS_TRY(gate_qubits(gates[k], n, &t, &cm));
+      QS_TRY(gate_matrix(gates[k], params, &mat));
+      const Op1 op = classify(t, cm, mat);
+      if (op.cls != OP_IDENTITY) rops->push_back(op);
+    }
+  }
+  if (tables_ok && g_aggregate && g_phase_tables && g_register_bits == 0) {
+    std::vector<Op1> x;
+    std::vector<PhaseTable> t;
+    extract_phases(*rops, local, n, m, &x, &t);
+    if (x.size() <= (size_t)TILE_MAX_OPS) {  // else keep the aggregated list (it fits: the plan capped it)
+      rops->swap(x);
+      ptables->swap(t);
+    }
+  }
+  return QS_OK;
+}
+
 static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed) {
   const int n = s->n;
   TileArgs* g = new (std::nothrow) TileArgs;
@@ -486,9 +851,9 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   const uint64_t Q = ps.qmask;
   int local[64];
   int m = 0;
-  for (int b = 0; b < n; ++b)
-    if ((Q >> b) & 1) local[b] = m++;
-    else local[b] = -1;
+  std::vector<Op1> rops;
+  std::vector<PhaseTable> ptables;
+  int rc = build_pass_ops(n, ps, gates, params, fixed && s->prec == 128, &rops, &ptables, local, &m);
   int L = 0;
   while (L < n && ((Q >> L) & 1)) ++L;
   g->n = n;
@@ -501,24 +866,22 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   for (int b = 0; b < n; ++b)
     if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
   g->nops = 0;
+  g->tables = nullptr;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
-  std::vector<Op1> rops;
-  int merged = 0;
-  int rc = g_aggregate ? aggregate_pass(n, ps, gates, params, &rops, &merged) : QS_OK;
-  if (!g_aggregate) {
-    for (uint32_t k : ps.gates) {
-      int t;
-      uint64_t cm;
-      Mat2 mat;
-      if ((rc = gate_qubits(gates[k], n, &t, &cm)) != QS_OK) break;
-      if ((rc = gate_matrix(gates[k], params, &mat)) != QS_OK) break;
-      const Op1 op = classify(t, cm, mat);
-      if (op.cls != OP_IDENTITY) rops.push_back(op);
-    }
-  }
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
+    if (op.cls == kTableMark) {
+      TileOp& to = g->ops[g->nops];
+      to.kind = TOP_DTABLE;
+      to.tb = (int8_t)ptables[op.target].nlo;
+      to.lcmask = (uint32_t)op.target;
+      to.ext_cmask = 0;
+      to.code0 = to.code1 = U_GENERAL;
+      int_ops += N * 18.0;  // two complex products (Gauss: 9 limb products each) per amplitude
+      ++g->nops;
+      continue;
+    }
     if (op.cls == OP_IDENTITY) continue;
     const Mat2& mat = op.m;
     const int t = op.target;
@@ -558,6 +921,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     int_ops += N * class_touch_fraction(op) * op_int_ops_per_amp(op);
     ++g->nops;
   }
+  if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables);
   g->nphases = 0;
   if (rc == QS_OK && fixed && g_register_bits && m >= g_register_bits) build_phases(g, g_register_bits);
   if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,

@@ -11,6 +11,7 @@
 // Two arithmetic engines share the structure: FP64 (tile of double2) and Q60
 // fixed point (tile of int64 pairs, converted once on load and once on store).
 #include <algorithm>
+#include <type_traits>
 
 #include "tile.h"
 
@@ -206,6 +207,24 @@ __global__ void __launch_bounds__(THREADS) k_tile(typename E::G* __restrict__ a,
       const TileOp& op = g.ops[k];
       if ((base & op.ext_cmask) != op.ext_cmask) continue;  // uniform across the CTA
       const uint32_t lcm = op.lcmask;
+      if constexpr (std::is_same<E, EngQ60>::value) {
+        if (op.kind == TOP_DTABLE) {
+          const QC* tl = g.tables + (size_t)lcm * (DTABLE_LO + DTABLE_HI);
+          const QC* th = tl + DTABLE_LO;
+          const int nlo = op.tb;
+          const uint32_t lm = (1u << nlo) - 1;
+          for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
+            const longlong2 a = tile[j];
+            int64_t re, im;
+            q60_gauss_mul(tl[j & lm], q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
+            int64_t re2, im2;
+            q60_gauss_mul(th[j >> nlo], q60_split(re), q60_split(im), q60_split(re + im), &re2, &im2);
+            tile[j] = make_longlong2(re2, im2);
+          }
+          __syncthreads();
+          continue;
+        }
+      }
       if (op.kind == TOP_SCALAR) {
         const bool one = (base >> op.tb) & 1ull;
         const int code = one ? op.code1 : op.code0;

@@ -31,7 +31,12 @@ enum TileOpKind : int8_t {
   TOP_REAL = OP_REAL,
   TOP_GENERAL = OP_GENERAL,
   TOP_SCALAR = 9,  // diagonal op whose target lies outside the tile: a per-tile scalar
+  TOP_DTABLE = 10, // Q60 only: a_j *= Tlo[j & (2^tb - 1)] * Thi[j >> tb], a diagonal over the
+                   // tile's qubits as a product of two tables (table index in lcmask)
 };
+
+constexpr int DTABLE_LO = 64;   // entries of the low table (tile bits 0..5)
+constexpr int DTABLE_HI = 128;  // entries of the high table (tile bits 6..12)
 
 struct TileOp {
   union {
@@ -56,6 +61,7 @@ struct TileArgs {
   int nops;
   int nphases;       // > 0: run the register-phase kernel (Q60 engine, m >= 4)
   int reg_bits;      // register bits per phase (3 or 4)
+  const QC* tables;  // DTABLE ops: (DTABLE_LO + DTABLE_HI) Gauss-form entries per table
   TileOp ops[TILE_MAX_OPS];
   TilePhase phases[TILE_MAX_PHASES];
 };

@@ -207,3 +207,35 @@ def test_aggregation_matches_oracle_and_reduces_work(q, orc, arith, n):
     finally:
         q.qs_set_aggregate(True)
     assert work[True] < 0.9 * work[False]
+
+
+@pytest.mark.parametrize("n,kind", [(13, "brick"), (14, "rand"), (12, "hea"), (9, "chain")])
+def test_phase_tables_match_oracle_and_cut_work(q, orc, n, kind):
+    """Q60 tile passes with the general ops split into real rotations and phase
+    tables, against the oracle (1e-12) and against the switch off; on the
+    brickwork the limb products per step drop."""
+    g = {"brick": lambda: w.layered_u3_cz(n, 12, 4), "rand": lambda: w.random_circuit(n, 400, 11),
+         "hea": lambda: w.hea_ansatz(n, 4)[0], "chain": lambda: run_chain_circuit(n, 77)}[kind]()
+    params = w.uniform_angles(400, 3)
+    ref = orc.as_complex(orc.run(n, g, params))
+    work = {}
+    try:
+        for on in (True, False):
+            q.qs_set_phase_tables(on)
+            p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+            h = q.qs_alloc(n)
+            try:
+                q.qs_set_arith(h, q.ARITH_FIXED)
+                q.qs_timing_enable(h, True)
+                q.qs_apply(h, g, params, p)
+                recs = q.qs_timing_fetch(h)
+                got = q.qs_get_state(h)
+            finally:
+                q.qs_free(h)
+                q.qs_plan_free(p)
+            assert np.max(np.abs(got - ref)) < TOL, on
+            work[on] = sum(r["int_ops"] for r in recs if r["kind"] == q._lib.K_TILE)
+    finally:
+        q.qs_set_phase_tables(True)
+    if kind == "brick":
+        assert work[True] < 0.85 * work[False]

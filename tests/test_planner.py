@@ -91,3 +91,97 @@ def test_plan_rejects_other_program(q):
             q.qs_apply(0, w.random_circuit(6, 40, 2), None, p)   # NULL state is rejected first
     finally:
         q.qs_plan_free(p)
+
+
+def apply_pass_ops(orc, st, n, qmask, ops, tables):
+    """Applies a pass's op list (qs_plan_pass_ops) to a state on the host: 2x2 ops
+    through the oracle, phase tables by their definition."""
+    st = orc.as_complex(st).copy()
+    qs_ = [b for b in range(n) if (qmask >> b) & 1]
+    x = np.arange(1 << n)
+    j = np.zeros(1 << n, dtype=np.int64)
+    for pos, b in enumerate(qs_):
+        j |= ((x >> b) & 1) << pos
+    for o in ops:
+        if o["kind"] == 0:
+            st = orc.as_complex(orc.apply_matrix(st, n, [o["target"]], o["m"], o["ctrl_mask"]))
+        else:
+            t = tables[o["table"]]
+            lo, hi = t[:64], t[64:]
+            st = st * lo[j & ((1 << o["nlo"]) - 1)] * hi[j >> o["nlo"]]
+    return st
+
+
+def chain_circuit(n, seed):
+    rng = w.SplitMix64(seed)
+    recs = []
+    for _ in range(50):
+        t = rng.below(n)
+        c = (t + 1 + rng.below(n - 1)) % n
+        k = rng.below(6)
+        if k < 3:
+            for _ in range(2 + rng.below(3)):
+                name = w.ONE_QUBIT[rng.below(len(w.ONE_QUBIT))]
+                recs.append(w.gate(name, t, theta=rng.angle(), phi=rng.angle(), lam=rng.angle(),
+                                   ctrl_mask=(1 << c) if k == 2 else 0))
+        elif k == 3:
+            recs.append(w.gate("RZ", t, theta=rng.angle()))
+            recs.append(w.gate("CZ", c, t) if rng.below(2) else w.gate("CNOT", t, c))
+            recs.append(w.gate("T", t))
+        else:
+            recs.append(w.gate(("CNOT", "CZ", "CR")[rng.below(3)], c, t, theta=rng.angle()))
+    return w.pack(recs)
+
+
+@pytest.mark.parametrize("tables", [True, False])
+@pytest.mark.parametrize("aggregate", [True, False])
+def test_pass_op_lists_compose_to_their_passes(q, orc, tables, aggregate):
+    """Every tile pass's op list (after aggregation and the split of general ops
+    into real rotations and phase tables) applied to a random state equals the
+    pass's gates applied in order (oracle), 1e-13."""
+    cases = [(10, w.layered_u3_cz(10, 8, 2), None), (9, w.random_circuit(9, 300, 4), None),
+             (8, chain_circuit(8, 5), None), (7, w.hea_ansatz(7, 3)[0], w.uniform_angles(200, 6)),
+             (5, w.random_circuit(5, 200, 8, two_qubit_prob=0.4), None), (3, chain_circuit(3, 9), None)]
+    q.qs_set_phase_tables(tables)
+    q.qs_set_aggregate(aggregate)
+    try:
+        for n, g, params in cases:
+            p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+            try:
+                st = w.random_state(n, 17 + n)
+                st = st / np.sqrt(np.sum(st * st))
+                for i, (kind, qm, idx) in enumerate(q.qs_plan_passes(p)):
+                    ops, tabs = q.qs_plan_pass_ops(p, i, g, params)
+                    want = orc.as_complex(orc.apply_circuit(st.copy(), n, g[idx], params))
+                    got = apply_pass_ops(orc, st, n, qm if kind == 1 else 0, ops, tabs)
+                    assert np.max(np.abs(got - want)) < 1e-13, (n, i)
+                    st = want.view(np.float64).copy()
+            finally:
+                q.qs_plan_free(p)
+    finally:
+        q.qs_set_phase_tables(True)
+        q.qs_set_aggregate(True)
+
+
+def _general(m):
+    return np.all(np.abs(m) > 0) and np.any(np.abs(m.imag) > 0)
+
+
+def test_phase_tables_turn_brickwork_layers_real(q):
+    """On the brickwork every uncontrolled general op of a tile pass becomes a
+    real rotation, with about one phase table per layer."""
+    n = 12
+    g = w.layered_u3_cz(n, 10, 3)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    try:
+        tables = general = real = 0
+        for i, (kind, qm, idx) in enumerate(q.qs_plan_passes(p)):
+            ops, tabs = q.qs_plan_pass_ops(p, i, g)
+            tables += sum(1 for o in ops if o["kind"] == 1)
+            for o in ops:
+                if o["kind"] == 0 and o["ctrl_mask"] == 0:
+                    general += _general(o["m"])
+                    real += bool(np.all(np.abs(o["m"].imag) == 0) and np.all(np.abs(o["m"]) > 0))
+        assert general == 0 and real >= 10 * n * 0.9 and 5 <= tables <= 15
+    finally:
+        q.qs_plan_free(p)
