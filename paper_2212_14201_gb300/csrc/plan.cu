@@ -70,9 +70,23 @@ bool structurally_diagonal(int type) {
 }
 
 // Cost model of the greedy planner (seconds): a pass costs the larger of its HBM
-// time and its arithmetic time.
+// time and its arithmetic time.  Rates of the Q60 engine measured at n=30: a
+// tile pass runs ~5.2e12 limb products per second, a per-gate kernel streams at
+// ~60 % of HBM.  (kFp64FlopPerS serves the FP64 estimate of PLAIN plans.)
 constexpr double kHbmBytesPerS = 6.6e12;
 constexpr double kFp64FlopPerS = 1.0e12;
+constexpr double kTileLimbPerS = 5.2e12;
+constexpr double kPlainHbmFraction = 0.6;
+
+// Limb products per touched amplitude of a gate inside a tile pass, by type.
+static double op_q60_per_amp(int type) {
+  switch (type) {
+    case QS_U3: case QS_RX: return 18.0;
+    case QS_H: case QS_RY: case QS_RZ: return 12.0;
+    case QS_T: case QS_P: case QS_CR: return 12.0;
+    default: return 0.0;
+  }
+}
 
 double op_flops_per_amp(int type) {
   switch (type) {
@@ -196,9 +210,14 @@ static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const
 }
 
 // ---- phase tables ----------------------------------------------------------------
-// An uncontrolled general one-qubit unitary U = [[a, b], [c, d]] (all entries
-// nonzero) factors exactly as diag(p1, p2) R diag(1, q2) with R = [[|a|, -|c|],
-// [|c|, |a|]] real (the ZYZ Euler form): p1 = a/|a|, p2 = c/|c|, q2 = d/(p2 |a|).
+// An uncontrolled general one-qubit unitary U = [[a, b], [c, d]] factors exactly
+// as diag(p1, p2) R diag(1, q2), R = [[cs, -sn], [sn, cs]] real (the ZYZ Euler
+// form): a = p1 cs, c = p2 sn, d = p2 cs q2, b = -p1 sn q2, with p1, p2, q2 unit
+// phases.  Rounding can leave entries that are zero in exact arithmetic at 1e-17
+// (and differently on platforms that fuse multiply-adds), so every phase is
+// taken from an entry that is large where it matters: cs, sn from the averaged
+// moduli, q2 from d when |d| >= |b|, else from -b; a noisy p1 (tiny |a|) or p2
+// (tiny |c|) only multiplies a tiny entry.
 // Diagonals commute with each other, with diagonal gates and with gates that use
 // their qubit only as a control, so within a tile pass the phases of many qubits
 // collect into one table op, diag(prod_q d_q(j_q)) = Tlo[j_lo] Thi[j_hi], and the
@@ -217,9 +236,10 @@ extern "C" int qs_set_phase_tables(int on) {
 }
 
 static C2 cmul2(C2 x, C2 y) { return {x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re}; }
-static C2 cdiv2(C2 x, C2 y) {
-  const double d = y.re * y.re + y.im * y.im;
-  return {(x.re * y.re + x.im * y.im) / d, (x.im * y.re - x.re * y.im) / d};
+static C2 cconj2(C2 x) { return {x.re, -x.im}; }
+static C2 phase_of(C2 x) {
+  const double r = std::hypot(x.re, x.im);
+  return r > 0.0 ? C2{x.re / r, x.im / r} : C2{1.0, 0.0};
 }
 
 struct Zyz {
@@ -229,14 +249,20 @@ struct Zyz {
 
 static Zyz zyz(const Mat2& U) {
   Zyz z;
-  const double aa = std::hypot(U.m[0].re, U.m[0].im), cc = std::hypot(U.m[2].re, U.m[2].im);
-  z.p1 = {U.m[0].re / aa, U.m[0].im / aa};
-  z.p2 = {U.m[2].re / cc, U.m[2].im / cc};
-  z.q2 = cdiv2(U.m[3], {z.p2.re * aa, z.p2.im * aa});
-  z.R.m[0] = {aa, 0.0};
-  z.R.m[1] = {-cc, 0.0};
-  z.R.m[2] = {cc, 0.0};
-  z.R.m[3] = {aa, 0.0};
+  const C2 a = U.m[0], b = U.m[1], c = U.m[2], d = U.m[3];
+  const double na = std::hypot(a.re, a.im), nb = std::hypot(b.re, b.im);
+  const double nc = std::hypot(c.re, c.im), nd = std::hypot(d.re, d.im);
+  double cs = 0.5 * (na + nd), sn = 0.5 * (nb + nc);
+  const double r = std::hypot(cs, sn);
+  cs /= r;
+  sn /= r;
+  z.p1 = phase_of(a);
+  z.p2 = phase_of(c);
+  z.q2 = nd >= nb ? cmul2(phase_of(d), cconj2(z.p2)) : cmul2(phase_of({-b.re, -b.im}), cconj2(z.p1));
+  z.R.m[0] = {cs, 0.0};
+  z.R.m[1] = {-sn, 0.0};
+  z.R.m[2] = {sn, 0.0};
+  z.R.m[3] = {cs, 0.0};
   return z;
 }
 
@@ -504,15 +530,17 @@ static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax
     PlanPass ps;
     ps.kind = PASS_TILE;
     ps.qmask = greedy_pass(gates, tgt, cms, remaining, p->m, low, TILE_MAX_OPS, ps.gates, rest);
-    // Cost: a tile pass sweeps the whole state once; a lone gate is cheaper in the
-    // plain kernel, which touches only the amplitudes it changes.
-    double flops = 0.0, plain = 0.0;
+    // Cost: a tile pass sweeps the whole state once and is bound by its limb
+    // products; a per-gate kernel touches only the amplitudes it changes and is
+    // bound by HBM.  A lone gate, or a pass of cheap data-movement gates (CZ,
+    // CNOT), can be cheaper gate by gate.
+    double limbs = 0.0, plain = 0.0;
     for (uint32_t k : ps.gates) {
-      double f = op_touch_fraction(gates[k], cms[k]);
-      flops += N * f * op_flops_per_amp(gates[k].type);
-      plain += std::max(pass_bytes * f / kHbmBytesPerS, N * f * op_flops_per_amp(gates[k].type) / kFp64FlopPerS);
+      const double f = op_touch_fraction(gates[k], cms[k]);
+      limbs += N * f * op_q60_per_amp(gates[k].type);
+      plain += pass_bytes * f / (kPlainHbmFraction * kHbmBytesPerS);
     }
-    double tile_cost = std::max(pass_bytes / kHbmBytesPerS, flops / kFp64FlopPerS);
+    const double tile_cost = std::max(pass_bytes / kHbmBytesPerS, limbs / kTileLimbPerS);
     if (ps.gates.size() == 1 || plain <= tile_cost) {
       for (uint32_t k : ps.gates) {
         PlanPass g1;

@@ -185,3 +185,43 @@ def test_phase_tables_turn_brickwork_layers_real(q):
         assert general == 0 and real >= 10 * n * 0.9 and 5 <= tables <= 15
     finally:
         q.qs_plan_free(p)
+
+
+def u3_params(M):
+    """(theta, phi, lambda) of the U3 equal to the 2x2 unitary M up to a global phase."""
+    th = 2 * np.arctan2(abs(M[1, 0]), abs(M[0, 0]))
+    g0 = np.angle(M[0, 0]) if abs(M[0, 0]) > 1e-12 else np.angle(-M[0, 1]) if abs(M[0, 1]) > 0 else 0.0
+    phi = np.angle(M[1, 0]) - g0 if abs(M[1, 0]) > 1e-12 else 0.0
+    lam = np.angle(-M[0, 1]) - g0 if abs(M[0, 1]) > 1e-12 else np.angle(M[1, 1]) - g0 - phi
+    return th, phi, lam
+
+
+def test_nearly_antidiagonal_products_split_exactly(q, orc):
+    """Pairs of U3 gates whose product is X (or Y) up to a phase: the aggregated op
+    has diagonal entries that are rounding noise, independent in a and d.  Its
+    split into phases and a real rotation must still reproduce it (1e-13)."""
+    n = 5
+    rng = np.random.Generator(np.random.PCG64(3))
+    recs = []
+    for rep in range(3):
+        for k in range(n):
+            th, ph, la = rng.uniform(0.1, 3.0, 3)
+            V = orc.gate_matrix(w.pack([w.gate("U3", 0, theta=th, phi=ph, lam=la)])[0], 1)[2]
+            T = np.array([[0, 1], [1, 0]]) if (k + rep) % 2 else np.array([[0, -1j], [1j, 0]])
+            W = T @ V.conj().T
+            recs.append(w.gate("U3", k, theta=th, phi=ph, lam=la))
+            recs.append(w.gate("U3", k, *[], **dict(zip(("theta", "phi", "lam"), u3_params(W)))))
+        recs += [w.gate("CZ", k, k + 1) for k in range(rep % 2, n - 1, 2)]
+    g = w.pack(recs)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    try:
+        st = w.random_state(n, 4)
+        st = st / np.sqrt(np.sum(st * st))
+        for i, (kind, qm, idx) in enumerate(q.qs_plan_passes(p)):
+            ops, tabs = q.qs_plan_pass_ops(p, i, g)
+            want = orc.as_complex(orc.apply_circuit(st.copy(), n, g[idx]))
+            got = apply_pass_ops(orc, st, n, qm if kind == 1 else 0, ops, tabs)
+            assert np.max(np.abs(got - want)) < 1e-13, i
+            st = want.view(np.float64).copy()
+    finally:
+        q.qs_plan_free(p)
