@@ -224,10 +224,10 @@ int qs_set_aggregate(int on);
  * uncontrolled general one-qubit op factors exactly as diag R diag with R real
  * (the ZYZ Euler form); within a pass the diagonal factors of many qubits, and
  * the plain diagonal gates between them, commute into one table op
- * a_j *= Tlo[j_lo] Thi[j_hi] (tables of 64 and 128 phases over the tile's low
- * and high bits), leaving real rotations: 12 instead of 18 limb products per
- * amplitude.  A table is built only where at least three general ops become
- * real.  The tables are staged through pinned memory per pass, so a qs_apply
+ * a_j *= Tlo[j_lo] Thi[j_hi] (tables of 256 and 32 phases over the tile's
+ * low 8 and high bits), leaving real rotations: 12 instead of 18 limb products
+ * per amplitude.  A table is built where the general ops it makes real and the
+ * pending phases it absorbs outweigh its own cost.  The tables are staged through pinned memory per pass, so a qs_apply
  * with a plan is not stream-capturable while this is on.  Results agree with
  * the switch off within rounding (factors formed in double).  Always QS_OK. */
 int qs_set_phase_tables(int on);
@@ -259,7 +259,7 @@ int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask,
  * gates in order (up to rounding).  Kind 0: the 2x2 matrix m (row-major,
  * interleaved complex) on `target` with controls ctrl_mask.  Kind 1: phase table
  * `table`: amplitude x gets Tlo[j & (2^nlo - 1)] * Thi[j >> nlo], j = the bits of
- * x at the pass's qubits in ascending order; tables[t] holds 64 + 128 complex
+ * x at the pass's qubits in ascending order; tables[t] holds 256 + 32 complex
  * (interleaved) entries, Tlo first.  *count / *ntables receive the totals (only
  * the first cap ops and table_cap tables are written). */
 typedef struct qs_pass_op {

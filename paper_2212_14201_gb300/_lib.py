@@ -423,7 +423,7 @@ def qs_plan_pass_info(p: int, i: int):
 
 def qs_plan_pass_ops(p: int, i: int, gates, params=None, q60: bool = True):
     """(ops, tables) a tile pass runs: ops as dicts (kind 0: target, ctrl_mask,
-    2x2 complex matrix; kind 1: table index, nlo), tables as (64 + 128) complex
+    2x2 complex matrix; kind 1: table index, nlo), tables as (256 + 32) complex
     arrays."""
     g = as_gates(gates)
     pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
@@ -431,7 +431,7 @@ def qs_plan_pass_ops(p: int, i: int, gates, params=None, q60: bool = True):
     args = (p, i, g.ctypes.data if len(g) else None, len(g), None if pr is None else pr.ctypes.data, 1 if q60 else 0)
     _chk(lib().qs_plan_pass_ops(*args, None, 0, ctypes.byref(cnt), None, 0, ctypes.byref(nt)))
     ops = (PassOp * max(1, cnt.value))()
-    tab = np.zeros(max(1, nt.value) * 2 * 192, dtype=np.float64)
+    tab = np.zeros(max(1, nt.value) * 2 * 288, dtype=np.float64)
     _chk(lib().qs_plan_pass_ops(*args, ops, cnt.value, ctypes.byref(cnt), tab.ctypes.data, nt.value, ctypes.byref(nt)))
     out = []
     for o in ops[:cnt.value]:
@@ -440,7 +440,7 @@ def qs_plan_pass_ops(p: int, i: int, gates, params=None, q60: bool = True):
         else:
             m = np.array(o.m[:]).view(np.complex128).reshape(2, 2)
             out.append({"kind": 0, "target": o.target, "ctrl_mask": o.ctrl_mask, "m": m})
-    tables = tab.view(np.complex128).reshape(-1, 192)[:nt.value].copy()
+    tables = tab.view(np.complex128).reshape(-1, 288)[:nt.value].copy()
     return out, tables
 
 

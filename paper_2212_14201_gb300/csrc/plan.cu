@@ -224,10 +224,16 @@ static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const
 // general ops shrink to real rotations (12 instead of 18 limb products per
 // amplitude).  A flush emits the pending phases before an op that does not
 // commute with them, pulling forward the right factors of the next general op of
-// every qubit (and the plain diagonal gates before it); it builds a table only
-// when at least kTableMinPulls general ops become real, else the pending phase of
-// the op's qubit is folded into that op (or emitted as a diagonal op).
-constexpr int kTableMinPulls = 3;
+// every qubit (and the plain diagonal gates before it); it builds a table when
+// the general ops made real and the pending phases it absorbs outweigh the table
+// op (kTableCost), else the pending phase of the op's qubit is folded into that
+// op (or emitted as a diagonal op).
+// Limb products per amplitude: a table op (two complex products) plus an op's
+// overhead, against 6 saved per general op made real and 12 + overhead per
+// pending phase that needs no diagonal op of its own.
+constexpr double kTableCost = 18.0 + 6.0;
+constexpr double kPullGain = 6.0;
+constexpr double kPhaseGain = 12.0 + 6.0;
 static bool g_phase_tables = true;
 
 extern "C" int qs_set_phase_tables(int on) {
@@ -369,7 +375,7 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       return;
     }
     PhaseTable t{};
-    t.nlo = std::min(m, 6);
+    t.nlo = std::min(m, 8);
     const int nhi = m - t.nlo;
     for (int j = 0; j < (1 << t.nlo); ++j) {
       C2 v = {1.0, 0.0};
@@ -413,8 +419,15 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       absorb(b, z[i].p1, z[i].p2);
       continue;
     }
-    // o does not commute with the pending phase of its target
-    if (plan_pulls(i, P.data()) >= kTableMinPulls) {
+    // o does not commute with the pending phase of its target.  A table now pays
+    // for itself through the general ops it turns real and through the pending
+    // phases that would otherwise become separate diagonal ops (qubits whose
+    // next non-commuting op is not a general op, like this one).
+    const int pulls = plan_pulls(i, P.data());
+    int lone = 0;
+    for (int bb = 0; bb < m; ++bb)
+      if (has[bb] && P[bb].gen < 0) ++lone;
+    if (kPullGain * pulls + kPhaseGain * lone >= kTableCost) {
       commit(P.data());
       if (elig[i]) {  // pulled by the commit
         out->push_back(classify(o.target, 0, z[i].R));

@@ -211,12 +211,16 @@ __global__ void __launch_bounds__(THREADS) k_tile(typename E::G* __restrict__ a,
         if (op.kind == TOP_DTABLE) {
           const QC* tl = g.tables + (size_t)lcm * (DTABLE_LO + DTABLE_HI);
           const QC* th = tl + DTABLE_LO;
+          // THREADS is a multiple of 256 >= 2^nlo: j & lm is the thread's own entry,
+          // j >> nlo the same for the whole warp in each iteration
+          static_assert(THREADS % DTABLE_LO == 0, "one low-table entry per thread");
           const int nlo = op.tb;
           const uint32_t lm = (1u << nlo) - 1;
+          const QC ulo = tl[threadIdx.x & lm];
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             const longlong2 a = tile[j];
             int64_t re, im;
-            q60_gauss_mul(tl[j & lm], q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
+            q60_gauss_mul(ulo, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
             int64_t re2, im2;
             q60_gauss_mul(th[j >> nlo], q60_split(re), q60_split(im), q60_split(re + im), &re2, &im2);
             tile[j] = make_longlong2(re2, im2);

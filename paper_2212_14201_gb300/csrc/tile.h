@@ -35,8 +35,8 @@ enum TileOpKind : int8_t {
                    // tile's qubits as a product of two tables (table index in lcmask)
 };
 
-constexpr int DTABLE_LO = 64;   // entries of the low table (tile bits 0..5)
-constexpr int DTABLE_HI = 128;  // entries of the high table (tile bits 6..12)
+constexpr int DTABLE_LO = 256;  // entries of the low table (tile bits 0..7: fixed per thread)
+constexpr int DTABLE_HI = 32;   // entries of the high table (tile bits 8..12: uniform per warp)
 
 struct TileOp {
   union {

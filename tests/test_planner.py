@@ -107,7 +107,7 @@ def apply_pass_ops(orc, st, n, qmask, ops, tables):
             st = orc.as_complex(orc.apply_matrix(st, n, [o["target"]], o["m"], o["ctrl_mask"]))
         else:
             t = tables[o["table"]]
-            lo, hi = t[:64], t[64:]
+            lo, hi = t[:256], t[256:]
             st = st * lo[j & ((1 << o["nlo"]) - 1)] * hi[j >> o["nlo"]]
     return st
 
