@@ -542,7 +542,19 @@ static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax
   while (!remaining.empty()) {
     PlanPass ps;
     ps.kind = PASS_TILE;
-    ps.qmask = greedy_pass(gates, tgt, cms, remaining, p->m, low, TILE_MAX_OPS, ps.gates, rest);
+    // leave op slots for the phase tables a pass may gain
+    ps.qmask = greedy_pass(gates, tgt, cms, remaining, p->m, low, TILE_MAX_OPS - 32, ps.gates, rest);
+    // Pad the tile to the full width: a pass of diagonal gates needs few tile
+    // qubits, but a narrow tile means many small tiles (a CTA pass and a barrier
+    // per op for a few amplitudes).  Qubits the pass's gates touch come first
+    // (their diagonal ops and controls become in-tile), then the lowest.
+    {
+      uint64_t touched = 0;
+      for (uint32_t k : ps.gates) touched |= cms[k] | (1ull << tgt[k]);
+      for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < p->m; ++b)
+        if (((touched >> b) & 1) && !((ps.qmask >> b) & 1)) ps.qmask |= 1ull << b;
+      for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < p->m; ++b) ps.qmask |= 1ull << b;
+    }
     // Cost: a tile pass sweeps the whole state once and is bound by its limb
     // products; a per-gate kernel touches only the amplitudes it changes and is
     // bound by HBM.  A lone gate, or a pass of cheap data-movement gates (CZ,
