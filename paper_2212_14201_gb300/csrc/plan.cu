@@ -862,6 +862,33 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
 // qs_plan_pass_ops): the pass's gates aggregated into fewer unitaries, then (Q60
 // engine) general ops split into real rotations and phase tables.  local[b] is
 // the tile bit of qubit b (-1 outside the tile), *m the tile width.
+// Estimated time of a tile pass's op list on the Q60 engine, in units of one
+// uncontrolled general op over the tile (measured at n=24: a real rotation 0.67,
+// a general-phase diagonal 0.78, a phase table 1.28); used to keep the phase
+// table rewrite only for passes it makes cheaper.
+static double est_op(const Op1& o) {
+  if (o.cls == kTableMark) return 1.28;
+  const double f = 1.0 / (double)(1ull << __builtin_popcountll(o.cmask));
+  const int g0 = o.code0 == U_GENERAL, g1 = o.code1 == U_GENERAL;
+  double c;
+  switch (o.cls) {
+    case OP_GENERAL: c = 1.0; break;
+    case OP_REAL: c = 0.67; break;
+    case OP_DIAG: c = 0.2 + 0.29 * (g0 + g1); break;
+    case OP_PHASE1: c = g1 ? 0.45 : 0.15; break;
+    case OP_ANTI: c = 0.2 + 0.2 * (g0 + g1); break;
+    default: c = 0.0; break;
+  }
+  return 0.05 + c * f;
+}
+
+static double est_ops(const std::vector<Op1>& ops) {
+  double t = 0.0;
+  for (const Op1& o : ops)
+    if (o.cls != OP_IDENTITY) t += est_op(o);
+  return t;
+}
+
 static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const double* params, bool tables_ok,
                           std::vector<Op1>* rops, std::vector<PhaseTable>* ptables, int* local, int* m_out) {
   int m = 0;
@@ -889,7 +916,8 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
     std::vector<Op1> x;
     std::vector<PhaseTable> t;
     extract_phases(*rops, local, n, m, &x, &t);
-    if (x.size() <= (size_t)TILE_MAX_OPS) {  // else keep the aggregated list (it fits: the plan capped it)
+    // keep the rewrite where it is estimated cheaper (and fits the op table)
+    if (x.size() <= (size_t)TILE_MAX_OPS && est_ops(x) < 0.98 * est_ops(*rops)) {
       rops->swap(x);
       ptables->swap(t);
     }
