@@ -56,9 +56,6 @@ size_t workspace_bytes(int n) {
 int ensure_pinned(qs_state* s, size_t bytes) {
   if (s->pinned_bytes >= bytes) return QS_OK;
   if (s->pinned) cudaFreeHost(s->pinned);
-  if (s->tables) cudaFree(s->tables);
-  if (s->tables_pinned) cudaFreeHost(s->tables_pinned);
-  if (s->tables_ev) cudaEventDestroy(s->tables_ev);
   s->pinned = nullptr;
   s->pinned_bytes = 0;
   QS_CUDA(cudaMallocHost(&s->pinned, bytes));
@@ -377,6 +374,9 @@ extern "C" int qs_free(qs_state* s) {
   if (s->owns && s->amps) cudaFree(s->amps);
   if (s->ws) cudaFree(s->ws);
   if (s->pinned) cudaFreeHost(s->pinned);
+  if (s->tables) cudaFree(s->tables);
+  if (s->tables_pinned) cudaFreeHost(s->tables_pinned);
+  if (s->tables_ev) cudaEventDestroy(s->tables_ev);
   for (auto& p : s->pending) {
     cudaEventDestroy(p.e0);
     cudaEventDestroy(p.e1);

@@ -1002,6 +1002,11 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     int_ops += N * class_touch_fraction(op) * op_int_ops_per_amp(op);
     ++g->nops;
   }
+  for (int k = 0; rc == QS_OK && k < g->nops; ++k)
+    if (g->ops[k].kind == TOP_DTABLE &&
+        (g->ops[k].lcmask >= ptables.size() || g->ops[k].tb < 0 || g->ops[k].tb > 8 || (1 << g->ops[k].tb) > DTABLE_LO ||
+         (m - g->ops[k].tb) > 5))
+      rc = fail(QS_ERR_INVALID_ARG, "internal: malformed phase-table op");
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables);
   g->nphases = 0;
   if (rc == QS_OK && fixed && g_register_bits && m >= g_register_bits) build_phases(g, g_register_bits);

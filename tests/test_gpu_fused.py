@@ -239,3 +239,27 @@ def test_phase_tables_match_oracle_and_cut_work(q, orc, n, kind):
         q.qs_set_phase_tables(True)
     if kind == "brick":
         assert work[True] < 0.85 * work[False]
+
+
+def test_phase_tables_survive_host_buffer_growth(q, orc):
+    """Per-state resources of the table upload (device copy, pinned staging, event)
+    stay valid across a reduction that grows the state's pinned result buffer: a
+    fused apply with tables, a 12-qubit marginal (4096 results), a second fused
+    apply, each against the oracle."""
+    n = 14
+    g = w.layered_u3_cz(n, 12, 4)
+    ref1 = orc.run(n, g)
+    ref2 = orc.apply_circuit(ref1.copy(), n, g)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc(n)
+    try:
+        q.qs_set_arith(h, q.ARITH_FIXED)
+        q.qs_apply(h, g, None, p)
+        assert np.max(np.abs(q.qs_get_state(h) - orc.as_complex(ref1))) < TOL
+        qs12 = list(range(12))
+        assert np.max(np.abs(q.qs_probs(h, qs12) - orc.marginal(ref1, n, qs12))) < 1e-12
+        q.qs_apply(h, g, None, p)
+        assert np.max(np.abs(q.qs_get_state(h) - orc.as_complex(ref2))) < TOL
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(p)
