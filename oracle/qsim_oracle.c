@@ -344,7 +344,11 @@ int or_apply_pauli_sum(const double* state, int n, const or_pauli* terms, int64_
 /*   p_x   = re*re + im*im (two rounded products, one rounded sum);             */
 /*   L     = min(1024, 2^n); block b holds x in [bL, bL + L);                   */
 /*   S_b(j)= p_{bL} + ... + p_{bL+j}, summed left to right;                     */
-/*   E_0 = 0, E_{b+1} = E_b + S_b(L-1)      (left to right over blocks);        */
+/*   T_b   = S_b(L-1);  G = min(1024, N/L); superblock c holds blocks            */
+/*           [cG, cG + G); F_c(i) = T_{cG} + ... + T_{cG+i} left to right;       */
+/*   P_0 = 0, P_{c+1} = P_c + F_c(G-1)      (left to right over superblocks);   */
+/*   E_0 = 0, E_{cG+i+1} = P_c + F_c(i)     (for N <= 2^20 there is one         */
+/*           superblock and E_{b+1} = E_b + T_b);                               */
 /*   C_x   = E_b + S_b(x - bL);                                                 */
 /*   shot s -> the smallest x with C_x > u_s; if there is none (rounding left   */
 /*   the total <= u_s) the largest x with p_x > 0.                              */
@@ -364,11 +368,19 @@ int or_block_prefix(const double* state, int n, double* E /* nblocks + 1 */) {
   const int64_t N = (int64_t)1 << n;
   const int64_t L = N < 1024 ? N : 1024;
   const int64_t nb = N / L;
+  const int64_t G = nb < 1024 ? nb : 1024;
+  double P = 0.0; /* P_c */
   E[0] = 0.0;
-  for (int64_t b = 0; b < nb; ++b) {
-    double S = 0.0;
-    for (int64_t j = 0; j < L; ++j) S += prob_of(psi[b * L + j]);
-    E[b + 1] = E[b] + S;
+  for (int64_t c = 0; c < nb / G; ++c) {
+    double F = 0.0; /* F_c(i) */
+    for (int64_t i = 0; i < G; ++i) {
+      const int64_t b = c * G + i;
+      double T = 0.0;
+      for (int64_t j = 0; j < L; ++j) T += prob_of(psi[b * L + j]);
+      F += T;
+      E[b + 1] = P + F;
+    }
+    P = P + F;
   }
   return OR_OK;
 }

@@ -41,13 +41,14 @@ int check_state(const qs_state* s) {
   return QS_OK;
 }
 
-// Workspace: per-1024-amplitude block sums and prefixes for the sampler, plus
-// per-CTA partial results of the reductions.
+// Workspace: per-1024-amplitude block sums and prefixes for the sampler (and per
+// superblock of 1024 blocks), plus per-CTA partial results of the reductions.
 size_t workspace_bytes(int n) {
   size_t N = (size_t)1 << n;
   size_t L = N < 1024 ? N : 1024;
   size_t nb = N / L;
-  size_t sampler = (2 * (nb + 1)) * sizeof(double) + (nb + 1) * sizeof(long long) + 256;
+  size_t nsb = nb < 1024 ? 1 : nb / 1024;
+  size_t sampler = (2 * (nb + 1) + 2 * (nsb + 1)) * sizeof(double) + (nb + 1 + 2 * (nsb + 1)) * sizeof(long long) + 256;
   size_t reduce = (size_t)1024 * 72 * sizeof(double) + 256;  // up to 1024 CTAs x (n + 2) values
   size_t hist = (size_t)304 * 4096 * sizeof(double);          // marginal histograms
   return std::max(sampler, std::max(reduce, hist)) + 4096;

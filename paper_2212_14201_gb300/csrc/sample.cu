@@ -4,13 +4,17 @@
 //          (Steele, Lea & Flood 2014; counter form: state = seed + (s+1)*gamma);
 //   p_x  = re*re + im*im, each product and the sum rounded separately;
 //   L    = min(1024, 2^n); T_b = p_{bL} + ... + p_{bL+L-1} summed left to right;
-//   E_0 = 0, E_{b+1} = E_b + T_b (left to right);
+//   G    = min(1024, number of blocks); superblock c holds blocks [cG, cG + G);
+//   F_c(i) = T_{cG} + ... + T_{cG+i} left to right; P_0 = 0, P_{c+1} = P_c + F_c(G-1);
+//   E_0 = 0, E_{cG+i+1} = P_c + F_c(i)  (for n <= 20: E_{b+1} = E_b + T_b);
 //   shot s -> smallest x in the first block b with E_{b+1} > u_s such that
 //             E_b + (left-to-right partial sum of block b up to x) > u_s;
 //             if no block qualifies, the largest x with p_x > 0.
-// Three kernels: block totals (one thread per block, sequential), the prefix
-// (one thread, sequential, staged through shared memory), and one thread per shot
-// (binary search over E, then a sequential scan of one block).
+// Kernels: block totals (one thread per block, sequential), the superblock
+// prefixes (one CTA per superblock, its sequential sum staged through shared
+// memory), the prefix of the superblock totals (one CTA), the offset of every
+// superblock's prefixes, and one thread per shot (binary search over E, then a
+// sequential scan of one block).
 #include <algorithm>
 
 #include "internal.h"
@@ -42,37 +46,29 @@ __global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, d
   }
 }
 
-// E[0..nb]: exclusive-then-total prefix of T, left to right; lastnz[nb] = global last nonzero.
-__global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __restrict__ E, long long* __restrict__ lastnz) {
-  __shared__ double buf[2048];
-  __shared__ long long lbuf[2048];
-  __shared__ double carry;
-  __shared__ long long lcarry;
+// One CTA per segment c of G entries of T (a superblock of blocks, or the
+// superblock totals): out[c*G + i + 1] = T[c*G] + ... + T[c*G + i], left to right;
+// tot[c] = the segment's total; lmax[c] = max of lastnz over the segment.  CTA 0
+// also writes out[0] = 0.  The operands are staged through shared memory in
+// chunks so the one thread that adds waits only on its own additions.
+constexpr int kSegMax = 1024;
+__global__ void k_seg_prefix(const double* __restrict__ T, int64_t G, double* __restrict__ out,
+                             double* __restrict__ tot, const long long* __restrict__ lastnz,
+                             long long* __restrict__ lmax) {
+  __shared__ double buf[kSegMax];
   __shared__ long long wmax[32];
-  if (threadIdx.x == 0) {
-    carry = 0.0;
-    lcarry = -1;
-    E[0] = 0.0;
-  }
-  __syncthreads();
-  for (int64_t c0 = 0; c0 < nb; c0 += 2048) {
-    int64_t cnt = min((int64_t)2048, nb - c0);
+  __shared__ double carry;
+  const int64_t c0 = (int64_t)blockIdx.x * G;
+  long long lm = -1;
+  if (threadIdx.x == 0) carry = 0.0;
+  for (int64_t k0 = 0; k0 < G; k0 += kSegMax) {
+    const int cnt = (int)min((int64_t)kSegMax, G - k0);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      buf[i] = T[c0 + i];
-      lbuf[i] = lastnz[c0 + i];
+      buf[i] = T[c0 + k0 + i];
+      lm = max(lm, lastnz[c0 + k0 + i]);
     }
     __syncthreads();
-    // the largest nonzero index so far: a max over the chunk (any order gives the same)
-    long long lm = -1;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) lm = max(lm, lbuf[i]);
-    for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lm;
-    __syncthreads();
     if (threadIdx.x == 0) {
-      long long l = lcarry;
-      for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) l = max(l, wmax[wv]);
-      lcarry = l;
-      // the left-to-right sum itself: operands staged in registers eight at a time
       double e = carry;
       int i = 0;
       for (; i + 8 <= cnt; i += 8) {
@@ -94,10 +90,29 @@ __global__ void k_prefix(const double* __restrict__ T, int64_t nb, double* __res
       carry = e;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) E[c0 + i + 1] = buf[i];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[c0 + k0 + i + 1] = buf[i];
     __syncthreads();
   }
-  if (threadIdx.x == 0) lastnz[nb] = lcarry < 0 ? 0 : lcarry;  // all-zero state: index 0
+  // the largest nonzero index: a max (any order gives the same)
+  for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long l = -1;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) l = max(l, wmax[wv]);
+    lmax[blockIdx.x] = l;
+    tot[blockIdx.x] = carry;
+    if (blockIdx.x == 0) out[0] = 0.0;
+  }
+}
+
+// E[b + 1] = P[b / G] + E[b + 1] for the blocks of superblocks 1, 2, ... (superblock
+// 0 has P = 0); lastnz[nb] = the last nonzero index (0 for the zero vector).
+__global__ void k_seg_offset(double* __restrict__ E, int64_t nb, int G, const double* __restrict__ P,
+                             const long long* __restrict__ lall, long long* __restrict__ lastnz) {
+  for (int64_t b = G + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+    E[b + 1] = __dadd_rn(P[b / G], E[b + 1]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) lastnz[nb] = lall[0] < 0 ? 0 : lall[0];
 }
 
 template <class A>
@@ -144,18 +159,30 @@ extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint
   const int64_t N = (int64_t)1 << s->n;
   const int64_t L = N < 1024 ? N : 1024;
   const int64_t nb = N / L;
+  const int64_t G = nb < kSegMax ? nb : kSegMax;  // blocks per superblock
+  const int64_t nsb = nb / G;                      // superblocks (nb, G powers of two)
   double* T = (double*)s->ws;
   double* E = T + (nb + 1);
   long long* lastnz = (long long*)(E + (nb + 1));
+  double* Ssb = (double*)(lastnz + (nb + 1));  // superblock totals
+  double* P = Ssb + (nsb + 1);                 // superblock prefixes
+  long long* lsb = (long long*)(P + (nsb + 1));
+  long long* lall = lsb + (nsb + 1);
   int g1 = (int)std::min<int64_t>((nb + 127) / 128, 152 * 16);
   KTimer kt(s, QS_K_REDUCE, s->n, 3, 0, 0, (double)N, 4.0 * (double)N);
+  note_launch(4);
   with_amps(s, [&](auto* a) {
     k_block_totals<<<g1, 128, 0, s->stream>>>(a, nb, L, T, lastnz);
     return QS_OK;
   });
   QS_TRY(launch_check("block_totals"));
-  k_prefix<<<1, 256, 0, s->stream>>>(T, nb, E, lastnz);
-  QS_TRY(launch_check("prefix"));
+  k_seg_prefix<<<(unsigned)nsb, 128, 0, s->stream>>>(T, G, E, Ssb, lastnz, lsb);
+  QS_TRY(launch_check("superblock prefix"));
+  k_seg_prefix<<<1, 128, 0, s->stream>>>(Ssb, nsb, P, Ssb + nsb, lsb, lall);
+  QS_TRY(launch_check("superblock totals prefix"));
+  const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 152 * 8));
+  k_seg_offset<<<g2, 256, 0, s->stream>>>(E, nb, (int)G, P, lall, lastnz);
+  QS_TRY(launch_check("superblock offset"));
   uint64_t* dout = out;
   if (!on_device) QS_CUDA(cudaMallocAsync((void**)&dout, shots * sizeof(uint64_t), s->stream));
   int g3 = (int)std::min<uint64_t>((shots + 127) / 128, 152 * 16);

@@ -242,7 +242,7 @@ def test_pauli_expectations(q, orc, n, nt, seed):
 
 # ---- sampler: bit-exact on the same state array -----------------------------------------
 
-@pytest.mark.parametrize("n,seed", [(1, 1), (4, 2), (10, 3), (12, 0), (15, 5), (20, 6)])
+@pytest.mark.parametrize("n,seed", [(1, 1), (4, 2), (10, 3), (12, 0), (15, 5), (20, 6), (21, 7), (24, 8)])
 def test_sampler_bit_exact(q, orc, n, seed):
     g = w.random_circuit(n, 100, seed)
     h = q.qs_alloc(n)

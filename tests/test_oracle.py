@@ -343,6 +343,59 @@ def test_sampler_norm_deficit_and_point_mass(orc):
     assert (got == 5).sum() > 200
 
 
+def _two_level_cumulative(psi_f, n):
+    """C_x of the canonical sampler built with numpy's cumulative sums, which add
+    left to right: block sums, then per-superblock prefixes of the block totals,
+    offset by the prefix of the superblock totals."""
+    v = cvec(psi_f)
+    p = v.real * v.real + v.imag * v.imag
+    N = 1 << n
+    L = min(1024, N)
+    nb = N // L
+    G = min(1024, nb)
+    S = np.cumsum(p.reshape(nb, L), axis=1)          # S_b(j)
+    T = S[:, -1]
+    F = np.cumsum(T.reshape(nb // G, G), axis=1)     # F_c(i)
+    P = np.concatenate([[0.0], np.cumsum(F[:, -1])])[:-1]
+    Eend = (P[:, None] + F).reshape(nb)              # E_{b+1}
+    E = np.concatenate([[0.0], Eend])
+    C = E[:-1, None] + S                             # E_b + S_b(x - bL)
+    return E, C.reshape(N), p
+
+
+def test_sampler_superblocks(orc):
+    """n=21: two superblocks of 1024 blocks.  The oracle's block prefixes equal the
+    definition rebuilt from numpy's left-to-right cumulative sums; they never
+    decrease, end at the exact total within the summation bound, and every shot is
+    the first x with C_x above its draw."""
+    n = 21
+    psi = w.random_state_fast(n, 5)   # generic values: the two-level sums round differently
+    psi /= math.sqrt(math.fsum((psi * psi).tolist()))
+    E = orc.block_prefix(psi, n)
+    E2, C, p = _two_level_cumulative(psi, n)
+    assert np.array_equal(E, E2)
+    one_level = np.concatenate([[0.0], np.cumsum(np.cumsum(p.reshape(-1, 1024), axis=1)[:, -1])])
+    assert not np.array_equal(E, one_level)   # the case distinguishes the two definitions
+    assert E[0] == 0.0 and np.all(np.diff(E) >= 0.0)
+    total = math.fsum(p.tolist())
+    assert abs(E[-1] - total) <= (1024 + 1024 + 2 + 2) * 2.0 ** -53 * total
+    # the second superblock starts from the first one's total: its first prefix is
+    # that total plus the next block total, rounded once
+    T1024 = float(np.cumsum(p[1024 * 1024:1025 * 1024])[-1])
+    assert E[1025] == E[1024] + T1024
+    seed, shots = 17, 2000
+    got = orc.sample(psi, n, seed, shots)
+    u = np.array([(orc.splitmix64(seed, s) >> 11) * 2.0 ** -53 for s in range(shots)])
+    want = np.searchsorted(C, u, side="right")
+    last = int(np.nonzero(p > 0)[0].max())
+    want = np.where(want >= len(C), last, want).astype(np.uint64)
+    assert np.array_equal(got, want)
+    # both superblocks are drawn in proportion to their mass
+    hi = float(p[1 << 20:].sum())
+    frac = float(np.mean(got >= (1 << 20)))
+    assert abs(frac - hi) < 5 * math.sqrt(hi * (1 - hi) / shots)
+
+
 def test_sampler_chi_square(orc):
     from scipy.stats import chisquare
     n = 12
