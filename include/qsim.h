@@ -222,14 +222,16 @@ int qs_set_aggregate(int on);
 
 /* Process-wide switch (default on) for phase tables in Q60 tile passes.  An
  * uncontrolled general one-qubit op factors exactly as diag R diag with R real
- * (the ZYZ Euler form); within a pass the diagonal factors of many qubits, and
- * the plain diagonal gates between them, commute into one table op
- * a_j *= Tlo[j_lo] Thi[j_hi] (tables of 256 and 32 phases over the tile's
- * low 8 and high bits), leaving real rotations: 12 instead of 18 limb products
- * per amplitude.  A table is built where the general ops it makes real and the
- * pending phases it absorbs outweigh its own cost.  The tables are staged through pinned memory per pass, so a qs_apply
- * with a plan is not stream-capturable while this is on.  Results agree with
- * the switch off within rounding (factors formed in double).  Always QS_OK. */
+ * (the ZYZ Euler form); within a pass the diagonal factors of many qubits, the
+ * plain diagonal gates between them and the controlled diagonal gates among the
+ * tile's qubits (CZ, CR, ...) commute into one table op a_j *= T[j], a diagonal
+ * over the tile (2^m phases in device memory, one complex product per
+ * amplitude), leaving real rotations: 12 instead of 18 limb products per
+ * amplitude.  A table is built where the general ops it makes real and the
+ * diagonals it absorbs outweigh its own cost.  The tables are staged through
+ * pinned memory per pass, so a qs_apply with a plan is not stream-capturable
+ * while this is on.  Results agree with the switch off within rounding (table
+ * entries formed in double).  Always QS_OK. */
 int qs_set_phase_tables(int on);
 
 /* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops
@@ -258,16 +260,17 @@ int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask,
  * into real rotations and phase tables.  Applying the ops in order is the pass's
  * gates in order (up to rounding).  Kind 0: the 2x2 matrix m (row-major,
  * interleaved complex) on `target` with controls ctrl_mask.  Kind 1: phase table
- * `table`: amplitude x gets Tlo[j & (2^nlo - 1)] * Thi[j >> nlo], j = the bits of
- * x at the pass's qubits in ascending order; tables[t] holds 256 + 32 complex
- * (interleaved) entries, Tlo first.  *count / *ntables receive the totals (only
+ * `table`, a diagonal over the pass's `bits` qubits: amplitude x gets T[j], j =
+ * the bits of x at the pass's qubits in ascending order; the tables are written
+ * one after another, 2^bits complex (interleaved) entries each (every table of a
+ * pass has the pass's tile width).  *count / *ntables receive the totals (only
  * the first cap ops and table_cap tables are written). */
 typedef struct qs_pass_op {
   int32_t kind;
   int32_t target;
   uint64_t ctrl_mask;
   double m[8];
-  int32_t table, nlo;
+  int32_t table, bits;
 } qs_pass_op;
 int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
                      int q60, qs_pass_op* ops, size_t cap, size_t* count, double* tables, size_t table_cap,

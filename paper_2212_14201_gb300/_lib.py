@@ -47,7 +47,7 @@ class PlanStats(ctypes.Structure):
 
 class PassOp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("target", ctypes.c_int32), ("ctrl_mask", ctypes.c_uint64),
-                ("m", ctypes.c_double * 8), ("table", ctypes.c_int32), ("nlo", ctypes.c_int32)]
+                ("m", ctypes.c_double * 8), ("table", ctypes.c_int32), ("bits", ctypes.c_int32)]
 
 
 class TimingRecord(ctypes.Structure):
@@ -423,24 +423,26 @@ def qs_plan_pass_info(p: int, i: int):
 
 def qs_plan_pass_ops(p: int, i: int, gates, params=None, q60: bool = True):
     """(ops, tables) a tile pass runs: ops as dicts (kind 0: target, ctrl_mask,
-    2x2 complex matrix; kind 1: table index, nlo), tables as (256 + 32) complex
-    arrays."""
+    2x2 complex matrix; kind 1: table index, bits), tables as an array of
+    2^bits complex entries per table (entry j: tile index j)."""
     g = as_gates(gates)
     pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
     cnt, nt = ctypes.c_size_t(), ctypes.c_size_t()
     args = (p, i, g.ctypes.data if len(g) else None, len(g), None if pr is None else pr.ctypes.data, 1 if q60 else 0)
     _chk(lib().qs_plan_pass_ops(*args, None, 0, ctypes.byref(cnt), None, 0, ctypes.byref(nt)))
     ops = (PassOp * max(1, cnt.value))()
-    tab = np.zeros(max(1, nt.value) * 2 * 288, dtype=np.float64)
+    _chk(lib().qs_plan_pass_ops(*args, ops, cnt.value, ctypes.byref(cnt), None, 0, ctypes.byref(nt)))
+    bits = max([o.bits for o in ops[:cnt.value] if o.kind == 1], default=0)
+    tab = np.zeros(max(1, nt.value) * 2 << bits, dtype=np.float64)
     _chk(lib().qs_plan_pass_ops(*args, ops, cnt.value, ctypes.byref(cnt), tab.ctypes.data, nt.value, ctypes.byref(nt)))
     out = []
     for o in ops[:cnt.value]:
         if o.kind == 1:
-            out.append({"kind": 1, "table": o.table, "nlo": o.nlo})
+            out.append({"kind": 1, "table": o.table, "bits": o.bits})
         else:
             m = np.array(o.m[:]).view(np.complex128).reshape(2, 2)
             out.append({"kind": 0, "target": o.target, "ctrl_mask": o.ctrl_mask, "m": m})
-    tables = tab.view(np.complex128).reshape(-1, 288)[:nt.value].copy()
+    tables = tab.view(np.complex128).reshape(-1, 1 << bits)[:nt.value].copy()
     return out, tables
 
 

@@ -219,26 +219,55 @@ static int aggregate_pass(int n, const PlanPass& ps, const qs_gate* gates, const
 // moduli, q2 from d when |d| >= |b|, else from -b; a noisy p1 (tiny |a|) or p2
 // (tiny |c|) only multiplies a tiny entry.
 // Diagonals commute with each other, with diagonal gates and with gates that use
-// their qubit only as a control, so within a tile pass the phases of many qubits
-// collect into one table op, diag(prod_q d_q(j_q)) = Tlo[j_lo] Thi[j_hi], and the
-// general ops shrink to real rotations (12 instead of 18 limb products per
-// amplitude).  A flush emits the pending phases before an op that does not
+// their qubit only as a control, so within a tile pass the phases of many qubits,
+// and the controlled diagonal gates (CZ, CR, ...) among the tile's qubits, collect
+// into one diagonal over the tile, applied as one table op a_j *= T[j] (one
+// complex product per amplitude, T in global memory and shared by every tile), and
+// the general ops shrink to real rotations (12 instead of 18 limb products per
+// amplitude).  A flush emits the pending diagonals before an op that does not
 // commute with them, pulling forward the right factors of the next general op of
-// every qubit (and the plain diagonal gates before it); it builds a table when
-// the general ops made real and the pending phases it absorbs outweigh the table
-// op (kTableCost), else the pending phase of the op's qubit is folded into that
-// op (or emitted as a diagonal op).
-// Limb products per amplitude: a table op (two complex products) plus an op's
-// overhead, against 6 saved per general op made real and 12 + overhead per
-// pending phase that needs no diagonal op of its own.
-constexpr double kTableCost = 18.0 + 6.0;
-constexpr double kPullGain = 6.0;
-constexpr double kPhaseGain = 12.0 + 6.0;
+// every qubit (and the plain diagonal gates before it); it builds a table when the
+// general ops made real, the pending phases and the controlled diagonal gates it
+// absorbs outweigh the table op, else the pending phase of the op's qubit is
+// folded into that op (or emitted as a diagonal op) and the pending controlled
+// diagonal gates on that qubit are emitted as they are.
+// Gains and costs in units of one uncontrolled general op over the tile (est_op).
+constexpr double kTableCost = 0.62;  // a table op
+constexpr double kPullGain = 0.33;   // a general op made real
+constexpr double kPhaseGain = 0.5;   // a pending phase that needs no op of its own
 static bool g_phase_tables = true;
 
 extern "C" int qs_set_phase_tables(int on) {
   g_phase_tables = on != 0;
   return QS_OK;
+}
+
+// Estimated time of an op on the Q60 tile engine, in units of one uncontrolled
+// general op over the tile (measured at n=24: a real rotation 0.67, a
+// general-phase diagonal 0.78); used to decide on tables and to keep the phase
+// table rewrite only for passes it makes cheaper.
+constexpr int kTableMark = 100;
+static double est_op(const Op1& o) {
+  if (o.cls == kTableMark) return kTableCost;
+  const double f = 1.0 / (double)(1ull << __builtin_popcountll(o.cmask));
+  const int g0 = o.code0 == U_GENERAL, g1 = o.code1 == U_GENERAL;
+  double c;
+  switch (o.cls) {
+    case OP_GENERAL: c = 1.0; break;
+    case OP_REAL: c = 0.67; break;
+    case OP_DIAG: c = 0.2 + 0.29 * (g0 + g1); break;
+    case OP_PHASE1: c = g1 ? 0.45 : 0.15; break;
+    case OP_ANTI: c = 0.2 + 0.2 * (g0 + g1); break;
+    default: c = 0.0; break;
+  }
+  return 0.05 + c * f;
+}
+
+static double est_ops(const std::vector<Op1>& ops) {
+  double t = 0.0;
+  for (const Op1& o : ops)
+    if (o.cls != OP_IDENTITY) t += est_op(o);
+  return t;
 }
 
 static C2 cmul2(C2 x, C2 y) { return {x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re}; }
@@ -272,15 +301,14 @@ static Zyz zyz(const Mat2& U) {
   return z;
 }
 
+// A diagonal over the tile: entry j for tile index j (bit b of j = tile bit b).
 struct PhaseTable {
-  int nlo;
-  C2 lo[DTABLE_LO], hi[DTABLE_HI];
+  int m = 0;
+  std::vector<C2> t;
 };
 
 // Rewrites ops (one pass, pass order) into real rotations, phase-table markers
 // (cls = kTableMark, target = table index) and the other ops unchanged.
-constexpr int kTableMark = 100;
-
 static bool diag_cls(int c) { return c == OP_DIAG || c == OP_PHASE1 || c == OP_IDENTITY; }
 
 static void extract_phases(const std::vector<Op1>& ops, const int* local, int n, int m, std::vector<Op1>* out,
@@ -301,6 +329,15 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
   for (int b = 0; b < TILE_MAX_M; ++b) gq[b] = 0;
   for (int b = 0; b < n; ++b)
     if (local[b] >= 0 && local[b] < m) gq[local[b]] = b;
+  // pending controlled diagonal gates with every qubit in the tile
+  struct Term {
+    uint32_t touch;  // tile bits of its controls and target
+    uint32_t lmask;  // tile bits of its controls
+    int tb;          // tile bit of its target
+    C2 e0, e1;
+    Op1 op;
+  };
+  std::vector<Term> terms;
   auto reset = [&](int b) {
     d0[b] = {1.0, 0.0};
     d1[b] = {1.0, 0.0};
@@ -326,6 +363,15 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
     const Op1 o = classify(gq[b], 0, M);
     if (o.cls != OP_IDENTITY) out->push_back(o);
     reset(b);
+  };
+  // the pending controlled diagonal gates on tile bit b, as they are
+  auto emit_terms = [&](int b) {
+    size_t k = 0;
+    for (size_t i = 0; i < terms.size(); ++i) {
+      if ((terms[i].touch >> b) & 1) out->push_back(terms[i].op);
+      else terms[k++] = terms[i];
+    }
+    terms.resize(k);
   };
   // candidate pulls for a flush before op i: per tile bit, the diagonal gates
   // before its next general op, and that op
@@ -355,6 +401,8 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
     }
     return count;
   };
+  // applies every pending diagonal (and the pulls): one table if two or more
+  // things are pending, else each as its own op
   auto commit = [&](Pull* P) {
     for (int b = 0; b < m; ++b) {
       for (size_t j : P[b].diags) {
@@ -368,29 +416,34 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
         pulled[P[b].gen] = 1;
       }
     }
-    int cnt = 0;
+    int cnt = (int)terms.size();
     for (int b = 0; b < m; ++b) cnt += has[b];
     if (cnt < 2) {
-      for (int b = 0; b < m; ++b) emit_diag(b);
+      for (int b = 0; b < m; ++b) {
+        emit_diag(b);
+        emit_terms(b);
+      }
       return;
     }
-    PhaseTable t{};
-    t.nlo = std::min(m, 8);
-    const int nhi = m - t.nlo;
-    for (int j = 0; j < (1 << t.nlo); ++j) {
-      C2 v = {1.0, 0.0};
-      for (int b = 0; b < t.nlo; ++b) v = cmul2(v, ((j >> b) & 1) ? d1[b] : d0[b]);
-      t.lo[j] = v;
+    PhaseTable t;
+    t.m = m;
+    t.t.assign((size_t)1 << m, C2{1.0, 0.0});
+    // product over tile bits, doubling the filled prefix once per bit
+    for (int b = 0; b < m; ++b) {
+      const size_t h = (size_t)1 << b;
+      for (size_t j = 0; j < h; ++j) {
+        t.t[j + h] = cmul2(t.t[j], d1[b]);
+        t.t[j] = cmul2(t.t[j], d0[b]);
+      }
     }
-    for (int j = 0; j < (1 << nhi); ++j) {
-      C2 v = {1.0, 0.0};
-      for (int b = 0; b < nhi; ++b) v = cmul2(v, ((j >> b) & 1) ? d1[t.nlo + b] : d0[t.nlo + b]);
-      t.hi[j] = v;
-    }
+    for (const Term& tm : terms)
+      for (size_t j = 0; j < t.t.size(); ++j)
+        if ((j & tm.lmask) == tm.lmask) t.t[j] = cmul2(t.t[j], ((j >> tm.tb) & 1) ? tm.e1 : tm.e0);
+    terms.clear();
     Op1 mark{};
     mark.cls = kTableMark;
     mark.target = (int)tables->size();
-    tables->push_back(t);
+    tables->push_back(std::move(t));
     out->push_back(mark);
     for (int b = 0; b < m; ++b) reset(b);
   };
@@ -404,30 +457,39 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       continue;
     }
     if (diag_cls(o.cls)) {
-      if (o.cmask == 0) {
-        C2 e0, e1;
-        diag_of(o, &e0, &e1);
-        absorb(b, e0, e1);
-      } else {
-        out->push_back(o);
+      C2 e0, e1;
+      diag_of(o, &e0, &e1);
+      uint32_t lm = 0;
+      bool inside = true;
+      for (uint64_t c = o.cmask; c; c &= c - 1) {
+        const int q = __builtin_ctzll(c);
+        if (local[q] < 0) inside = false;
+        else lm |= 1u << local[q];
       }
+      if (o.cmask == 0) absorb(b, e0, e1);
+      else if (inside) terms.push_back(Term{lm | (1u << b), lm, b, e0, e1, o});
+      else out->push_back(o);  // a control outside the tile: stays an op (it commutes with the pending ones)
       continue;
     }
     if (elig[i] && pulled[i]) {  // its right factor is already in a table
       emit_diag(b);                // (nothing is pending here: a pull takes every diagonal before it)
+      emit_terms(b);
       out->push_back(classify(o.target, 0, z[i].R));
       absorb(b, z[i].p1, z[i].p2);
       continue;
     }
-    // o does not commute with the pending phase of its target.  A table now pays
-    // for itself through the general ops it turns real and through the pending
-    // phases that would otherwise become separate diagonal ops (qubits whose
-    // next non-commuting op is not a general op, like this one).
+    // o does not commute with the pending diagonals on its target.  A table now
+    // pays for itself through the general ops it turns real, the pending phases
+    // that would otherwise become separate diagonal ops (qubits whose next
+    // non-commuting op is not a general op, like this one) and the pending
+    // controlled diagonal gates it absorbs.
     const int pulls = plan_pulls(i, P.data());
     int lone = 0;
     for (int bb = 0; bb < m; ++bb)
       if (has[bb] && P[bb].gen < 0) ++lone;
-    if (kPullGain * pulls + kPhaseGain * lone >= kTableCost) {
+    double term_gain = 0.0;
+    for (const Term& tm : terms) term_gain += est_op(tm.op);
+    if (kPullGain * pulls + kPhaseGain * lone + term_gain >= kTableCost) {
       commit(P.data());
       if (elig[i]) {  // pulled by the commit
         out->push_back(classify(o.target, 0, z[i].R));
@@ -437,6 +499,7 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       out->push_back(o);
       continue;
     }
+    emit_terms(b);
     if (has[b] && elig[i]) {  // fold the pending phase into the op: U diag(d0, d1)
       Mat2 M = o.m;
       M.m[0] = cmul2(M.m[0], d0[b]);
@@ -451,14 +514,8 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
     out->push_back(o);
   }
   // what is left at the end of the pass
-  int cnt = 0;
-  for (int b = 0; b < m; ++b) cnt += has[b];
-  if (cnt >= 2) {
-    std::vector<Pull> none(m);
-    commit(none.data());
-  } else {
-    for (int b = 0; b < m; ++b) emit_diag(b);
-  }
+  std::vector<Pull> none(m);
+  commit(none.data());
 }
 
 uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
@@ -747,7 +804,7 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
     if (rops[i].cls == kTableMark) {
       o.kind = 1;
       o.table = rops[i].target;
-      o.nlo = pt[rops[i].target].nlo;
+      o.bits = pt[rops[i].target].m;
       continue;
     }
     o.kind = 0;
@@ -759,14 +816,10 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
     }
   }
   for (size_t t = 0; t < pt.size() && t < table_cap; ++t) {
-    double* d = tables + t * 2 * (DTABLE_LO + DTABLE_HI);
-    for (int k = 0; k < DTABLE_LO; ++k) {
-      d[2 * k] = pt[t].lo[k].re;
-      d[2 * k + 1] = pt[t].lo[k].im;
-    }
-    for (int k = 0; k < DTABLE_HI; ++k) {
-      d[2 * (DTABLE_LO + k)] = pt[t].hi[k].re;
-      d[2 * (DTABLE_LO + k) + 1] = pt[t].hi[k].im;
+    double* d = tables + t * 2 * pt[t].t.size();
+    for (size_t k = 0; k < pt[t].t.size(); ++k) {
+      d[2 * k] = pt[t].t[k].re;
+      d[2 * k + 1] = pt[t].t[k].im;
     }
   }
   return QS_OK;
@@ -821,12 +874,17 @@ extern "C" int qs_set_register_phases(int bits) {
   return QS_OK;
 }
 
-// Copies a pass's phase tables (Gauss form) to the device: pinned staging, one
-// asynchronous copy on the state's stream, an event so that the staging buffer is
-// rewritten only after that copy has run (the host waits, the stream does not).
-static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const QC** dev) {
-  const size_t per = DTABLE_LO + DTABLE_HI;
-  const size_t bytes = pt.size() * per * sizeof(QC);
+// Copies a pass's phase tables to the device in the layout the tile kernel reads:
+// per table three arrays of 2^m limb pairs (the Gauss-form parts re, im, nim of
+// qc_make_gauss), so that a warp's loads of one part are consecutive.  Pinned
+// staging, one asynchronous copy on the state's stream, an event so that the
+// staging buffer is rewritten only after that copy has run (the host waits, the
+// stream does not); the device buffer is rewritten in stream order, after the
+// previous pass's kernel.
+static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const QL** dev) {
+  size_t per = 0;
+  for (const PhaseTable& t : pt) per = std::max(per, t.t.size());
+  const size_t bytes = pt.size() * 3 * per * sizeof(QL);
   if (!s->tables_ev) QS_CUDA(cudaEventCreateWithFlags(&s->tables_ev, cudaEventDisableTiming));
   QS_CUDA(cudaEventSynchronize(s->tables_ev));
   if (s->tables_pinned_bytes < bytes) {
@@ -846,15 +904,21 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
     QS_CUDA(cudaMalloc(&s->tables, bytes));
     s->tables_bytes = bytes;
   }
-  QC* host = (QC*)s->tables_pinned;
+  QL* host = (QL*)s->tables_pinned;
   for (size_t t = 0; t < pt.size(); ++t) {
-    QC* dst = host + t * per;
-    for (int j = 0; j < DTABLE_LO; ++j) dst[j] = qc_make_gauss(pt[t].lo[j].re, pt[t].lo[j].im);
-    for (int j = 0; j < DTABLE_HI; ++j) dst[DTABLE_LO + j] = qc_make_gauss(pt[t].hi[j].re, pt[t].hi[j].im);
+    QL* re = host + t * 3 * per;
+    QL* im = re + per;
+    QL* nim = im + per;
+    for (size_t j = 0; j < pt[t].t.size(); ++j) {
+      const QC c = qc_make_gauss(pt[t].t[j].re, pt[t].t[j].im);
+      re[j] = c.re;
+      im[j] = c.im;
+      nim[j] = c.nim;
+    }
   }
   QS_CUDA(cudaMemcpyAsync(s->tables, host, bytes, cudaMemcpyHostToDevice, s->stream));
   QS_CUDA(cudaEventRecord(s->tables_ev, s->stream));
-  *dev = (const QC*)s->tables;
+  *dev = (const QL*)s->tables;
   return QS_OK;
 }
 
@@ -862,33 +926,6 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
 // qs_plan_pass_ops): the pass's gates aggregated into fewer unitaries, then (Q60
 // engine) general ops split into real rotations and phase tables.  local[b] is
 // the tile bit of qubit b (-1 outside the tile), *m the tile width.
-// Estimated time of a tile pass's op list on the Q60 engine, in units of one
-// uncontrolled general op over the tile (measured at n=24: a real rotation 0.67,
-// a general-phase diagonal 0.78, a phase table 1.28); used to keep the phase
-// table rewrite only for passes it makes cheaper.
-static double est_op(const Op1& o) {
-  if (o.cls == kTableMark) return 1.28;
-  const double f = 1.0 / (double)(1ull << __builtin_popcountll(o.cmask));
-  const int g0 = o.code0 == U_GENERAL, g1 = o.code1 == U_GENERAL;
-  double c;
-  switch (o.cls) {
-    case OP_GENERAL: c = 1.0; break;
-    case OP_REAL: c = 0.67; break;
-    case OP_DIAG: c = 0.2 + 0.29 * (g0 + g1); break;
-    case OP_PHASE1: c = g1 ? 0.45 : 0.15; break;
-    case OP_ANTI: c = 0.2 + 0.2 * (g0 + g1); break;
-    default: c = 0.0; break;
-  }
-  return 0.05 + c * f;
-}
-
-static double est_ops(const std::vector<Op1>& ops) {
-  double t = 0.0;
-  for (const Op1& o : ops)
-    if (o.cls != OP_IDENTITY) t += est_op(o);
-  return t;
-}
-
 static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const double* params, bool tables_ok,
                           std::vector<Op1>* rops, std::vector<PhaseTable>* ptables, int* local, int* m_out) {
   int m = 0;
@@ -955,11 +992,11 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     if (op.cls == kTableMark) {
       TileOp& to = g->ops[g->nops];
       to.kind = TOP_DTABLE;
-      to.tb = (int8_t)ptables[op.target].nlo;
+      to.tb = (int8_t)ptables[op.target].m;
       to.lcmask = (uint32_t)op.target;
       to.ext_cmask = 0;
       to.code0 = to.code1 = U_GENERAL;
-      int_ops += N * 18.0;  // two complex products (Gauss: 9 limb products each) per amplitude
+      int_ops += N * 9.0;  // one complex product (Gauss: 9 limb products) per amplitude
       ++g->nops;
       continue;
     }
@@ -1004,8 +1041,8 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   }
   for (int k = 0; rc == QS_OK && k < g->nops; ++k)
     if (g->ops[k].kind == TOP_DTABLE &&
-        (g->ops[k].lcmask >= ptables.size() || g->ops[k].tb < 0 || g->ops[k].tb > 8 || (1 << g->ops[k].tb) > DTABLE_LO ||
-         (m - g->ops[k].tb) > 5))
+        (g->ops[k].lcmask >= ptables.size() || g->ops[k].tb != m ||
+         ptables[g->ops[k].lcmask].t.size() != ((size_t)1 << m)))
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed phase-table op");
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables);
   g->nphases = 0;

@@ -209,21 +209,19 @@ __global__ void __launch_bounds__(THREADS) k_tile(typename E::G* __restrict__ a,
       const uint32_t lcm = op.lcmask;
       if constexpr (std::is_same<E, EngQ60>::value) {
         if (op.kind == TOP_DTABLE) {
-          const QC* tl = g.tables + (size_t)lcm * (DTABLE_LO + DTABLE_HI);
-          const QC* th = tl + DTABLE_LO;
-          // THREADS is a multiple of 256 >= 2^nlo: j & lm is the thread's own entry,
-          // j >> nlo the same for the whole warp in each iteration
-          static_assert(THREADS % DTABLE_LO == 0, "one low-table entry per thread");
-          const int nlo = op.tb;
-          const uint32_t lm = (1u << nlo) - 1;
-          const QC ulo = tl[threadIdx.x & lm];
+          // one table entry per amplitude, read through the read-only path (every
+          // tile reads the same table: it stays in L2)
+          const int2* tre = reinterpret_cast<const int2*>(g.tables) + (size_t)lcm * 3 * TS;
+          const int2* tim = tre + TS;
+          const int2* tnim = tim + TS;
+#pragma unroll 4
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
+            const int2 ur = __ldg(tre + j), ui = __ldg(tim + j), un = __ldg(tnim + j);
+            const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
             const longlong2 a = tile[j];
             int64_t re, im;
-            q60_gauss_mul(ulo, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
-            int64_t re2, im2;
-            q60_gauss_mul(th[j >> nlo], q60_split(re), q60_split(im), q60_split(re + im), &re2, &im2);
-            tile[j] = make_longlong2(re2, im2);
+            q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
+            tile[j] = make_longlong2(re, im);
           }
           __syncthreads();
           continue;

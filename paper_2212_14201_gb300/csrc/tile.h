@@ -31,12 +31,9 @@ enum TileOpKind : int8_t {
   TOP_REAL = OP_REAL,
   TOP_GENERAL = OP_GENERAL,
   TOP_SCALAR = 9,  // diagonal op whose target lies outside the tile: a per-tile scalar
-  TOP_DTABLE = 10, // Q60 only: a_j *= Tlo[j & (2^tb - 1)] * Thi[j >> tb], a diagonal over the
-                   // tile's qubits as a product of two tables (table index in lcmask)
+  TOP_DTABLE = 10, // Q60 only: a_j *= T[j], a diagonal over the tile's 2^tb amplitudes
+                   // (table index in lcmask; TileArgs::tables)
 };
-
-constexpr int DTABLE_LO = 256;  // entries of the low table (tile bits 0..7: fixed per thread)
-constexpr int DTABLE_HI = 32;   // entries of the high table (tile bits 8..12: uniform per warp)
 
 struct TileOp {
   union {
@@ -61,7 +58,7 @@ struct TileArgs {
   int nops;
   int nphases;       // > 0: run the register-phase kernel (Q60 engine, m >= 4)
   int reg_bits;      // register bits per phase (3 or 4)
-  const QC* tables;  // DTABLE ops: (DTABLE_LO + DTABLE_HI) Gauss-form entries per table
+  const QL* tables;  // DTABLE ops: per table the Gauss-form parts re, im, nim, 2^m limb pairs each
   TileOp ops[TILE_MAX_OPS];
   TilePhase phases[TILE_MAX_PHASES];
 };

@@ -106,9 +106,8 @@ def apply_pass_ops(orc, st, n, qmask, ops, tables):
         if o["kind"] == 0:
             st = orc.as_complex(orc.apply_matrix(st, n, [o["target"]], o["m"], o["ctrl_mask"]))
         else:
-            t = tables[o["table"]]
-            lo, hi = t[:256], t[256:]
-            st = st * lo[j & ((1 << o["nlo"]) - 1)] * hi[j >> o["nlo"]]
+            assert o["bits"] == len(qs_)
+            st = st * tables[o["table"]][j]
     return st
 
 
