@@ -234,6 +234,14 @@ int qs_set_aggregate(int on);
  * entries formed in double).  Always QS_OK. */
 int qs_set_phase_tables(int on);
 
+/* Process-wide switch (default on): in Q60 tile passes, two consecutive real
+ * one-qubit ops on different tile qubits (the real rotations the phase tables
+ * leave, RY, ...) run as one real 4x4 op on amplitude quads.  The multiply-adds
+ * are the same; the limb splits, roundings, shared-memory round trips and
+ * barriers halve.  Results agree with the switch off within the Q60 rounding
+ * (one rounding per output instead of two).  For measurement.  Always QS_OK. */
+int qs_set_rotation_pairs(int on);
+
 /* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops
  * of a pass into register phases (runs of ops whose targets fit in `bits` tile
  * qubits execute on the 2^bits amplitudes a thread holds in registers); 0

@@ -100,6 +100,7 @@ SIGNATURES = {
     "qs_set_adjoint_fused": (I32, [I32]),
     "qs_set_aggregate": (I32, [I32]),
     "qs_set_phase_tables": (I32, [I32]),
+    "qs_set_rotation_pairs": (I32, [I32]),
     "qs_plan_pass_ops": (I32, [P, SZ, P, SZ, P, I32, ctypes.POINTER(PassOp), SZ, ctypes.POINTER(SZ), P, SZ,
                                ctypes.POINTER(SZ)]),
     "qs_mlp_create": (I32, [I32, I32, P, U64, PP]),
@@ -388,6 +389,10 @@ def qs_set_aggregate(on: bool):
 
 def qs_set_phase_tables(on: bool):
     _chk(lib().qs_set_phase_tables(1 if on else 0))
+
+def qs_set_rotation_pairs(on: bool):
+    """Process-wide: run pairs of real rotations as one 4x4 op on quads (Q60 tiles)."""
+    _chk(lib().qs_set_rotation_pairs(1 if on else 0))
 
 
 def qs_set_register_phases(bits: int):

@@ -831,6 +831,12 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
 // a warp on consecutive low bits).  g_register_bits = 0 disables the phases.
 static int g_register_bits = 0;
 static bool g_aggregate = true;
+static bool g_rotation_pairs = true;
+
+extern "C" int qs_set_rotation_pairs(int on) {
+  g_rotation_pairs = on != 0;
+  return QS_OK;
+}
 
 extern "C" int qs_set_aggregate(int on) {
   g_aggregate = on != 0;
@@ -987,8 +993,36 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   g->tables = nullptr;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
+  const bool pairs = fixed && s->prec == 128 && g_rotation_pairs && g_register_bits == 0;
+  auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
+    if (pairs && i + 1 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
+        rops[i + 1].target != op.target) {
+      // two real rotations on different tile qubits: one 4x4 op on quads (two slots)
+      const Mat2& ra = op.m;
+      const Mat2& rb = rops[i + 1].m;
+      TileOp& t0 = g->ops[g->nops];
+      TileOp& t1 = g->ops[g->nops + 1];
+      memset(&t0, 0, sizeof t0);
+      memset(&t1, 0, sizeof t1);
+      t0.kind = TOP_REAL2;
+      t0.tb = (int8_t)local[op.target];
+      t0.code0 = (int8_t)local[rops[i + 1].target];
+      t1.kind = TOP_CONT;
+      QL* e0 = reinterpret_cast<QL*>(t0.q);
+      QL* e1 = reinterpret_cast<QL*>(t1.q);
+      for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 4; ++c) {
+          const double v = rb.m[2 * (k >> 1) + (c >> 1)].re * ra.m[2 * (k & 1) + (c & 1)].re;
+          const int e = 4 * k + c;
+          (e < 12 ? e0[e] : e1[e - 12]) = q60_split(q60_from_double(v));
+        }
+      int_ops += N * 24.0;  // two real rotations: 12 limb products per amplitude each
+      g->nops += 2;
+      ++i;
+      continue;
+    }
     if (op.cls == kTableMark) {
       TileOp& to = g->ops[g->nops];
       to.kind = TOP_DTABLE;

@@ -181,8 +181,46 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
   }
 }
 
+// Two real rotations on tile bits a (low) and b as one real 4x4 matrix M on the
+// quads (j, j|a, j|b, j|a|b): each output component sums four products in one
+// accumulator pair, so a quad costs the same 96 wide multiply-adds as the two
+// rotations apart but half the limb splits, roundings, shared-memory round trips
+// and barriers.  Every row of M (a Kronecker product of two rotations) has an L1
+// norm of at most 2, the bound the accumulators were sized for.
+template <int THREADS>
+__device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* m0,
+                                          const QL* m1) {
+  const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
+  const uint32_t cnt = TS >> 2;
+#pragma unroll 2
+  for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
+    uint32_t j = i + (i & ~(lo - 1));  // insert a zero bit at lo, then at hi
+    j = j + (j & ~(hi - 1));
+    const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
+    QL r[4], im[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const longlong2 v = tile[jj[c]];
+      r[c] = q60_split(v.x);
+      im[c] = q60_split(v.y);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      QAcc xr = qacc_new(), xi = qacc_new();
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int e = 4 * k + c;
+        const QL u = e < 12 ? m0[e] : m1[e - 12];
+        qacc_add(xr, u, r[c]);
+        qacc_add(xi, u, im[c]);
+      }
+      tile[jj[k]] = make_longlong2(qacc_round(xr), qacc_round(xi));
+    }
+  }
+}
+
 template <class E, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = g.m;
@@ -223,6 +261,13 @@ __global__ void __launch_bounds__(THREADS) k_tile(typename E::G* __restrict__ a,
             q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
             tile[j] = make_longlong2(re, im);
           }
+          __syncthreads();
+          continue;
+        }
+        if (op.kind == TOP_REAL2) {
+          quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
+                             reinterpret_cast<const QL*>(g.ops[k + 1].q));
+          ++k;  // the continuation slot
           __syncthreads();
           continue;
         }
