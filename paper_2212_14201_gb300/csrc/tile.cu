@@ -31,6 +31,7 @@ __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint
 struct EngF64 {
   using T = double2;  // shared-memory element
   using G = double2;  // global element
+  static constexpr int kMinBlocks = 3;  // CTAs per SM the register budget must allow (256 threads; 64 KiB tiles)
   static __device__ __forceinline__ double neg(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
   }
@@ -66,6 +67,7 @@ struct EngF64 {
 struct EngQ60 {
   using T = longlong2;
   using G = double2;
+  static constexpr int kMinBlocks = 3;  // 64 KiB tiles: three per SM; registers must not cut that
   static __device__ __forceinline__ T load(const double2& a) {
     return make_longlong2(q60_from_double(a.x), q60_from_double(a.y));
   }
@@ -123,6 +125,7 @@ struct EngQ60 {
 struct EngF32 {
   using T = float2;
   using G = float2;
+  static constexpr int kMinBlocks = 6;  // 32 KiB tiles: up to seven per SM
   static __device__ __forceinline__ T load(const float2& a) { return a; }
   static __device__ __forceinline__ float2 store(const T& a) { return a; }
   static __device__ __forceinline__ float2 u(const TileOp& op, int e) { return op.f[e]; }
@@ -220,7 +223,7 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
 }
 
 template <class E, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = g.m;
