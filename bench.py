@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched / adjoint / n=32 side workloads")
     ap.add_argument("--no-n32", action="store_true", help="skip the n=32 learned-vs-greedy plan comparison")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="profiling aid: run only the batched VQE workload and print its result")
+    ap.add_argument("--batch-sets", type=int, default=1024, help="parameter sets of the batched VQE workload")
     return ap.parse_args()
 
 
@@ -255,11 +258,12 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
-def bench_batched_vqe(q, torch, steps: int, warmup: int):
+def bench_batched_vqe(q, torch, steps: int, warmup: int, sets: int = 1024):
     """1024 parameter sets, n uniform in 10..20 (seed 3), 8-layer RY/RZ + CNOT-ring
     ansatz, TFIM h=0.7, angles uniform (seed 33): energy + adjoint gradient of every
-    set per step, one persistent launch replayed from a CUDA graph."""
-    ns = w.batch_qubit_counts(1024, 3)
+    set per step, one persistent launch replayed from a CUDA graph.  (`sets` < 1024
+    takes a smaller batch of the same recipe, for profiling.)"""
+    ns = w.batch_qubit_counts(sets, 3)
     gl, npl, tl = [], [], []
     for n in ns:
         g, npar = w.hea_ansatz(int(n), 8)
@@ -286,7 +290,7 @@ def bench_batched_vqe(q, torch, steps: int, warmup: int):
     return {"grad_evals_per_s": len(ns) / (kms * 1e-3), "kernel_ms": kms,
             "e2e_grad_evals_per_s": len(ns) / wall, "e2e_ms": wall * 1e3, "sets": len(ns),
             "params": int(len(params)), "launch": info,
-            "workload": "1024 sets, n~U{10..20}, 8-layer RY/RZ+CNOT-ring ansatz, TFIM h=0.7"}
+            "workload": f"{sets} sets, n~U{{10..20}}, 8-layer RY/RZ+CNOT-ring ansatz, TFIM h=0.7"}
 
 
 def bench_adjoint(q, torch, stream, steps: int):
@@ -489,6 +493,10 @@ def run_ours(args, world, rank, local, pg):
     q.build()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
+    if args.only_batch:
+        if rank == 0:
+            print(json.dumps({"batched_vqe": bench_batched_vqe(q, torch, args.steps, args.warmup, args.batch_sets)}))
+        return
     n = args.n
     gates = w.layered_u3_cz(n, args.depth, 1)
     ng = len(gates)

@@ -387,7 +387,7 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
         slot_param.push_back(orig.param_idx);
       }
       ops.push_back(op);
-      for (int e = 0; e < 4; ++e) mats.push_back(qc_make(mt.m[e].re, mt.m[e].im));
+      for (int e = 0; e < 4; ++e) mats.push_back(qc_make_gauss(mt.m[e].re, mt.m[e].im));  // bt_apply's form
     }
     bp.op_end = (int)ops.size();
     bp.nslots = slot;

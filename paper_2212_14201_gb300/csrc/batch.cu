@@ -81,8 +81,8 @@ struct BatchArgs {
   double* energies;
   double2* psi;
   double2* lam;
-  QC* matf;   // 4 per gate
-  QC* matb;   // 4 per gate
+  QC* matf;   // 4 per gate (Gauss form)
+  QC* matb;   // 4 per gate (Gauss form)
   int* counter;
 };
 
@@ -248,9 +248,9 @@ __device__ void bt_eval_set(const BatchArgs& d, int set_id, int rank, int nr, lo
     double2 m[4];
     const BGate gt = d.gates[st.gate_begin + g];
     bt_gate_matrix(gt, d.params, false, m);
-    for (int e = 0; e < 4; ++e) matf[4 * g + e] = qc_make(m[e].x, m[e].y);
+    for (int e = 0; e < 4; ++e) matf[4 * g + e] = qc_make_gauss(m[e].x, m[e].y);
     bt_gate_matrix(gt, d.params, true, m);
-    for (int e = 0; e < 4; ++e) matb[4 * g + e] = qc_make(m[e].x, m[e].y);
+    for (int e = 0; e < 4; ++e) matb[4 * g + e] = qc_make_gauss(m[e].x, m[e].y);
   }
   for (int j = t0; j < st.nparams; j += ts) d.grads[st.param_begin + j] = 0.0;
   // 2. psi = |0>, forward passes
@@ -305,7 +305,7 @@ __device__ void bt_eval_set(const BatchArgs& d, int set_id, int rank, int nr, lo
 // cluster takes the next work item from the device counter (items pre-sorted by
 // decreasing estimated cost); the item is either one large set shared by the whole
 // cluster or up to d.csize small sets, one per CTA.
-__global__ void __launch_bounds__(BT_THREADS) k_batch(const BatchArgs d) {
+__global__ void __launch_bounds__(BT_THREADS, 3) k_batch(const BatchArgs d) {
   extern __shared__ __align__(16) unsigned char smem[];
   longlong2* tP = reinterpret_cast<longlong2*>(smem);
   longlong2* tL = tP + (1 << BT_M);

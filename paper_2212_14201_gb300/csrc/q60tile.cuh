@@ -46,15 +46,13 @@ __device__ __forceinline__ longlong2 bt_unit(longlong2 a, int code) {
   }
 }
 
+// Matrices of these passes are in Gauss form (qc_make_gauss): u * a with three
+// limb products; a real entry keeps its value in u.re.
 __device__ __forceinline__ longlong2 bt_mul(longlong2 a, int code, const QC& u) {
   if (code != U_GENERAL) return bt_unit(a, code);
-  const QL ar = q60_split(a.x), ai = q60_split(a.y);
-  QAcc re = qacc_new(), im = qacc_new();
-  qacc_add(re, u.re, ar);
-  qacc_add(re, u.nim, ai);
-  qacc_add(im, u.re, ai);
-  qacc_add(im, u.im, ar);
-  return make_longlong2(qacc_round(re), qacc_round(im));
+  int64_t re, im;
+  q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
+  return make_longlong2(re, im);
 }
 
 __device__ __forceinline__ uint32_t bt_expand(uint32_t i, uint32_t fixed, uint32_t set) {
@@ -97,7 +95,15 @@ static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int
     } else if (kind == OP_ANTI) {
       b0 = bt_mul(a1, c0, U[1]);
       b1 = bt_mul(a0, c1, U[2]);
-    } else {
+    } else if (kind == OP_GENERAL) {
+      const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+      const QL s0 = q60_split(a0.x + a0.y), s1 = q60_split(a1.x + a1.y);
+      int64_t re, im;
+      q60_gauss_row(U[0], U[1], r0, i0, s0, r1, i1, s1, &re, &im);
+      b0 = make_longlong2(re, im);
+      q60_gauss_row(U[2], U[3], r0, i0, s0, r1, i1, s1, &re, &im);
+      b1 = make_longlong2(re, im);
+    } else {  // real entries: u.re of the Gauss form
       const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
       int64_t out[4];
 #pragma unroll
@@ -109,12 +115,6 @@ static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int
         qacc_add(re, u1.re, r1);
         qacc_add(im, u0.re, i0);
         qacc_add(im, u1.re, i1);
-        if (kind == OP_GENERAL) {
-          qacc_add(re, u0.nim, i0);
-          qacc_add(re, u1.nim, i1);
-          qacc_add(im, u0.im, r0);
-          qacc_add(im, u1.im, r1);
-        }
         out[2 * row] = qacc_round(re);
         out[2 * row + 1] = qacc_round(im);
       }
