@@ -83,7 +83,8 @@ static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int
   const uint32_t fixed = lcm | tb;
   const uint32_t cnt = TS >> __popc(fixed);
   for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
-    const uint32_t j0 = bt_expand(i, fixed, lcm), j1 = j0 | tb;
+    // without in-tile controls the insertion of one zero bit is a mask and an add
+    const uint32_t j0 = lcm ? bt_expand(i, fixed, lcm) : i + (i & ~(tb - 1)), j1 = j0 | tb;
     if (kind == OP_PHASE1) {
       tile[j1] = bt_mul(tile[j1], c1, U[3]);
       continue;
@@ -126,28 +127,35 @@ static __device__ void bt_apply(longlong2* tile, uint32_t TS, const BOp& op, int
   }
 }
 
-// sum_k s_k * l_k * p_k for four signed products of Q60 values, as a double.
-// (all four limb products kept: these terms are summed over the whole state)
-__device__ __forceinline__ double bt_dot4(const int64_t* l, const int64_t* p, const int* sg) {
+// sum_k s_k * l_k * p_k for four signed products of Q60 values, in Q60 units
+// (all four limb products kept, one rounding: these terms are summed over the
+// whole state).
+__device__ __forceinline__ int64_t bt_dot4(const int64_t* l, const int64_t* p, const int* sg) {
   QAccF acc{0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (sg[k] == 0) continue;
     qaccf_add(acc, q60_split(sg[k] > 0 ? l[k] : -l[k]), q60_split(p[k]));
   }
-  return q60_to_double(qaccf_result(acc));
+  return qaccf_result(acc);
 }
 
-// This thread's share of Im <lambda| G |psi> over the op's pairs in the tile.
-static __device__ double bt_gen_partial(const longlong2* P, const longlong2* Lt, uint32_t TS, const BOp& op, uint64_t base) {
+// This thread's share of Im <lambda| G |psi> over the op's pairs in the tile, in
+// Q60 units, summed exactly in an int64: every partial sum is bounded by
+// sum |l_x| |p_y| over distinct pairs (x, y) times the generator's largest
+// weight (2), i.e. by 2 ||lambda|| ||psi|| <= 2 * 1.25^2 < 4 (Cauchy-Schwarz),
+// so it stays below 2^62.  No FP64 arithmetic per pair (GB300 issues FP64 at
+// 1/74 of its FP32 rate).
+static __device__ int64_t bt_gen_partial(const longlong2* P, const longlong2* Lt, uint32_t TS, const BOp& op,
+                                         uint64_t base) {
   if (op.kf == BK_SCALAR) {
     // diagonal generator on a qubit outside the tile: per amplitude,
     // Z -> (-1)^bit Im(conj(l) p), P -> -2 [bit] Im(conj(l) p)
     const bool one = (base >> op.tb) & 1ull;
-    if (op.gen == BG_P && !one) return 0.0;
-    const double w = op.gen == BG_P ? -2.0 : (one ? -1.0 : 1.0);
+    if (op.gen == BG_P && !one) return 0;
+    const int64_t w = op.gen == BG_P ? -2 : (one ? -1 : 1);
     const uint32_t cnt = TS >> __popc(op.lcm);
-    double acc = 0.0;
+    int64_t acc = 0;
     for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
       const uint32_t j = bt_expand(i, op.lcm, op.lcm);
       const int64_t l[4] = {Lt[j].x, Lt[j].y, 0, 0}, p[4] = {P[j].y, P[j].x, 0, 0};
@@ -159,9 +167,9 @@ static __device__ double bt_gen_partial(const longlong2* P, const longlong2* Lt,
   const uint32_t tb = 1u << op.tb;
   const uint32_t fixed = op.lcm | tb;
   const uint32_t cnt = TS >> __popc(fixed);
-  double acc = 0.0;
+  int64_t acc = 0;
   for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
-    const uint32_t j0 = bt_expand(i, fixed, op.lcm), j1 = j0 | tb;
+    const uint32_t j0 = op.lcm ? bt_expand(i, fixed, op.lcm) : i + (i & ~(tb - 1)), j1 = j0 | tb;
     const longlong2 p0 = P[j0], p1 = P[j1], l0 = Lt[j0], l1 = Lt[j1];
     int64_t l[4], p[4];
     int sg[4];
@@ -183,19 +191,21 @@ static __device__ double bt_gen_partial(const longlong2* P, const longlong2* Lt,
         l[2] = 0; p[2] = 0; sg[2] = 0; l[3] = 0; p[3] = 0; sg[3] = 0;
         break;
     }
-    double v = bt_dot4(l, p, sg);
-    acc += op.gen == BG_P ? 2.0 * v : v;
+    const int64_t v = bt_dot4(l, p, sg);
+    acc += op.gen == BG_P ? 2 * v : v;
   }
   return acc;
 }
 
-// Adds this thread's partial to its warp's accumulator of `slot` without a CTA
-// barrier: the warp reduces by shuffles and lane 0 owns the warp's row, so the
-// order of additions is fixed.  wacc holds (BT_THREADS / 32) rows of nslots.
-__device__ __forceinline__ void bt_warp_accumulate(double v, double* wacc, int nslots, int slot) {
+// Adds this thread's partial (Q60 units) to its warp's accumulator of `slot`
+// without a CTA barrier: the warp sums exactly by integer shuffles (the bound of
+// bt_gen_partial holds for the warp's total too), lane 0 converts once and owns
+// the warp's row, so the order of the FP64 additions is fixed.  wacc holds
+// (BT_THREADS / 32) rows of nslots.
+__device__ __forceinline__ void bt_warp_accumulate(int64_t v, double* wacc, int nslots, int slot) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) wacc[(threadIdx.x >> 5) * nslots + slot] += v;
+  for (int o = 16; o > 0; o >>= 1) v += (int64_t)__shfl_xor_sync(0xffffffffu, (long long)v, o);
+  if ((threadIdx.x & 31) == 0) wacc[(threadIdx.x >> 5) * nslots + slot] += q60_to_double(v);
 }
 
 // After a barrier: the CTA's total of `slot`, warps added in warp order.
