@@ -80,6 +80,9 @@ int with_amps(const qs_state* s, F&& f) {
 
 // ---- errors -------------------------------------------------------------------
 int fail(int code, const char* fmt, ...);
+// Marginal probabilities of `qubits` into host memory (qs_probs); allow_exact =
+// false forces the FP64 reduction kernels.
+int marginal_host(qs_state* s, const int* qubits, int nq, double* out, bool allow_exact);
 int cuda_fail(cudaError_t e, const char* what);
 void clear_error();
 #define QS_CUDA(call)                                      \

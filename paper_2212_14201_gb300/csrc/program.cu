@@ -51,7 +51,10 @@ static int collapse(qs_state* s, uint64_t mask, uint64_t want, double scale) {
 
 static int measure_one(qs_state* s, int qubit, double u, int* outcome, double* p1_out) {
   double p[2] = {0.0, 0.0};
-  QS_TRY(qs_probs(s, &qubit, 1, p, 0));
+  QS_TRY(marginal_host(s, &qubit, 1, p, true));
+  // the exact integer marginal is accurate to 2^-45 absolute: for a small branch
+  // (whose probability scales the collapse) take the FP64 sums instead
+  if (std::min(p[0], p[1]) < 0x1p-20) QS_TRY(marginal_host(s, &qubit, 1, p, false));
   const double tot = p[0] + p[1];
   if (!(tot > 0.0)) return fail(QS_ERR_INVALID_ARG, "measurement of a zero state");
   const int o = (u * tot < p[0]) ? 0 : 1;

@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "fixed.h"
 #include "internal.h"
 
 namespace qs {
@@ -136,6 +137,89 @@ __global__ void __launch_bounds__(256) k_marginal_tiny(const T* __restrict__ a, 
   for (int k = 0; k < H; ++k) {
     const double t = block_sum256(acc[k], sh);
     if (threadIdx.x == 0) part[(size_t)blockIdx.x * H + k] = t;
+  }
+}
+
+// ---- exact integer marginals over at most three qubits (and the squared norm) ------
+// For states whose components are known to lie within the Q60 bound (norm <= 1.25,
+// e.g. |0> after unitary gates): each component is rounded once to Q60 (2^-60
+// resolution, |error| <= 2^-61) and its square is summed exactly as a 128-bit
+// integer in units of 2^-120, so the only errors are those roundings (a total below
+// 2^-60 sum |a_x| <= 2^-45 for n <= 30) and one final conversion to double.  Integer
+// arithmetic runs on pipes that GB300 issues at full rate; the FP64 form above is
+// bound by the FP64 pipe (1/74 of the FP32 rate) rather than by HBM.
+// The sum of all squares is at most 1.5625 * 2^120 < 2^128.
+using u128 = unsigned __int128;
+
+__device__ __forceinline__ u128 sq120(double2 v) {
+  const int64_t r = q60_from_double(v.x), i = q60_from_double(v.y);
+  const uint64_t ur = (uint64_t)(r < 0 ? -r : r), ui = (uint64_t)(i < 0 ? -i : i);
+  return (u128)ur * ur + (u128)ui * ui;
+}
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)(v >> 64), o);
+  return ((u128)hi << 64) | lo;
+}
+
+// per-CTA exact partials: part[(block * H + k) * 2 + {0, 1}] = low and high words
+template <class T, int NQ>
+__global__ void __launch_bounds__(256) k_marginal_exact(const T* __restrict__ a, uint64_t* __restrict__ part,
+                                                         const MargArgs g) {
+  constexpr int H = 1 << NQ;
+  __shared__ uint64_t sh[8][H][2];
+  u128 acc[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) acc[k] = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  auto add = [&](uint64_t x, u128 p) {
+    uint32_t kb = 0;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) kb |= (uint32_t)((x >> g.q[j]) & 1) << j;
+#pragma unroll
+    for (int k = 0; k < H; ++k)
+      if (k == (int)kb) acc[k] += p;
+  };
+  uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  // four independent loads in flight per thread (the loop is otherwise bound by
+  // the latency of one 16-byte load per iteration)
+  for (; x + 3 * stride < g.N; x += 4 * stride) {
+    const double2 v0 = ld_amp(a, x), v1 = ld_amp(a, x + stride), v2 = ld_amp(a, x + 2 * stride),
+                  v3 = ld_amp(a, x + 3 * stride);
+    add(x, sq120(v0));
+    add(x + stride, sq120(v1));
+    add(x + 2 * stride, sq120(v2));
+    add(x + 3 * stride, sq120(v3));
+  }
+  for (; x < g.N; x += stride) add(x, sq120(ld_amp(a, x)));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    u128 v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+    if (l == 0) {
+      sh[w][k][0] = (uint64_t)v;
+      sh[w][k][1] = (uint64_t)(v >> 64);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < H) {
+    u128 t = 0;
+    for (int i = 0; i < 8; ++i) t += ((u128)sh[i][threadIdx.x][1] << 64) | sh[i][threadIdx.x][0];
+    part[((size_t)blockIdx.x * H + threadIdx.x) * 2] = (uint64_t)t;
+    part[((size_t)blockIdx.x * H + threadIdx.x) * 2 + 1] = (uint64_t)(t >> 64);
+  }
+}
+
+__global__ void k_exact_finish(const uint64_t* __restrict__ part, int nblocks, int H, double* __restrict__ out) {
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    u128 t = 0;
+    for (int b = 0; b < nblocks; ++b)
+      t += ((u128)part[((size_t)b * H + i) * 2 + 1] << 64) | part[((size_t)b * H + i) * 2];
+    const double v = (double)(uint64_t)(t >> 64) * 18446744073709551616.0 + (double)(uint64_t)t;
+    out[i] = v * 0x1p-120;
   }
 }
 
@@ -284,7 +368,7 @@ static int read_back(qs_state* s, const double* dev, size_t count, double* host)
   return QS_OK;
 }
 
-static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout) {
+static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout, bool allow_exact = true) {
   const int n = s->n;
   const uint64_t N = 1ull << n;
   bool identity = nq == n;
@@ -296,6 +380,29 @@ static int marginal_device(qs_state* s, const int* qubits, int nq, double* dout)
       return QS_OK;
     });
     return launch_check("probs_full");
+  }
+  if (nq <= 3 && s->bound == 1 && allow_exact) {  // exact integer sums (see k_marginal_exact)
+    MargArgs g;
+    g.N = N;
+    g.nq = nq;
+    for (int j = 0; j < nq; ++j) g.q[j] = qubits[j];
+    const int nblocks = (int)std::min<uint64_t>(1216, std::max<uint64_t>(1, N / 1024));
+    uint64_t* part = (uint64_t*)s->ws;
+    note_launch(1);
+    with_amps(s, [&](auto* a) {
+      using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
+      const T* ca = a;
+      switch (nq) {
+        case 0: k_marginal_exact<T, 0><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+        case 1: k_marginal_exact<T, 1><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+        case 2: k_marginal_exact<T, 2><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+        default: k_marginal_exact<T, 3><<<nblocks, 256, 0, s->stream>>>(ca, part, g); break;
+      }
+      return QS_OK;
+    });
+    QS_TRY(launch_check("marginal_exact"));
+    k_exact_finish<<<1, 32, 0, s->stream>>>(part, nblocks, 1 << nq, dout);
+    return launch_check("marginal_exact finish");
   }
   if (nq == 0) {  // squared norm: per-thread sums, a fixed shuffle tree, CTA partials in order
     const int nblocks = (int)std::min<uint64_t>(608, std::max<uint64_t>(1, N / 1024));
@@ -383,6 +490,25 @@ static int check_qubit_list(const qs_state* s, const int* qubits, int nq) {
   }
   return QS_OK;
 }
+
+namespace qs {
+// Marginal probabilities into host memory; allow_exact = false forces the FP64
+// kernels (relative accuracy for tiny probabilities, where the exact integer form
+// is only accurate to 2^-45 absolute).
+int marginal_host(qs_state* s, const int* qubits, int nq, double* out, bool allow_exact) {
+  size_t H = (size_t)1 << nq;
+  double* tmp = nullptr;
+  QS_CUDA(cudaMallocAsync(&tmp, H * sizeof(double), s->stream));
+  int rc = marginal_device(s, qubits, nq, tmp, allow_exact);
+  if (rc == QS_OK) {
+    cudaError_t e = cudaMemcpyAsync(out, tmp, H * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "probs readback");
+  }
+  cudaFreeAsync(tmp, s->stream);
+  return rc;
+}
+}  // namespace qs
 
 extern "C" int qs_probs(const qs_state* cs, const int* qubits, int nq, double* out, int on_device) {
   clear_error();

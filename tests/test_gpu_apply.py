@@ -323,3 +323,31 @@ def test_arith_modes_and_bound_tracking(q, orc):
         assert max_err(q.qs_get_state(h), want) < 4 * TOL
     finally:
         q.qs_free(h)
+
+
+def test_exact_marginals_match_fp64_and_oracle(q, orc):
+    """A state reached from |0> by gates has known-bounded components, so its
+    squared norm and marginals over <= 3 qubits are summed exactly in integers;
+    a state loaded with qs_set_state takes the FP64 kernels.  Both agree with the
+    oracle on the same amplitudes (1e-13), and a zero branch is exactly zero."""
+    n = 14
+    g = w.random_circuit(n, 200, 9)
+    h = q.qs_alloc(n)
+    h2 = q.qs_alloc(n)
+    try:
+        q.qs_apply(h, g)
+        st = q.qs_get_state(h)
+        q.qs_set_state(h2, st)
+        ref_st = st.view(np.float64)
+        for qs_ in ([], [0], [13], [3, 7], [1, 5, 12]):
+            exact = q.qs_probs(h, qs_)
+            fp64 = q.qs_probs(h2, qs_)
+            ref = orc.marginal(ref_st, n, qs_)
+            assert np.max(np.abs(exact - ref)) < 1e-13, qs_
+            assert np.max(np.abs(fp64 - ref)) < 1e-13, qs_
+        q.qs_set_zero(h)
+        p = q.qs_probs(h, [4, 9])
+        assert p[0] == 1.0 and np.all(p[1:] == 0.0)
+    finally:
+        q.qs_free(h)
+        q.qs_free(h2)
