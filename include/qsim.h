@@ -238,8 +238,10 @@ int qs_set_phase_tables(int on);
  * one-qubit ops on different tile qubits (the real rotations the phase tables
  * leave, RY, ...) run as one real 4x4 op on amplitude quads.  The multiply-adds
  * are the same; the limb splits, roundings, shared-memory round trips and
- * barriers halve.  Results agree with the switch off within the Q60 rounding
- * (one rounding per output instead of two).  For measurement.  Always QS_OK. */
+ * barriers halve.  A phase table op just before a pair runs inside the pair's
+ * quad loop.  Results agree with the switch off within the Q60 rounding (one
+ * rounding per output instead of two).  For measurement: on = 1 (default) pairs
+ * with tables fused, 2 pairs without table fusion, 0 neither.  Always QS_OK. */
 int qs_set_rotation_pairs(int on);
 
 /* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops

@@ -390,9 +390,10 @@ def qs_set_aggregate(on: bool):
 def qs_set_phase_tables(on: bool):
     _chk(lib().qs_set_phase_tables(1 if on else 0))
 
-def qs_set_rotation_pairs(on: bool):
-    """Process-wide: run pairs of real rotations as one 4x4 op on quads (Q60 tiles)."""
-    _chk(lib().qs_set_rotation_pairs(1 if on else 0))
+def qs_set_rotation_pairs(on):
+    """Process-wide: run pairs of real rotations as one 4x4 op on quads (Q60 tiles);
+    True/1 with phase tables fused into the following pair, 2 without, False/0 off."""
+    _chk(lib().qs_set_rotation_pairs(int(on)))
 
 
 def qs_set_register_phases(bits: int):

@@ -832,9 +832,11 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
 static int g_register_bits = 0;
 static bool g_aggregate = true;
 static bool g_rotation_pairs = true;
+static bool g_fuse_tables = true;
 
 extern "C" int qs_set_rotation_pairs(int on) {
   g_rotation_pairs = on != 0;
+  g_fuse_tables = on > 0 && on != 2;
   return QS_OK;
 }
 
@@ -1002,6 +1004,13 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       // two real rotations on different tile qubits: one 4x4 op on quads (two slots)
       const Mat2& ra = op.m;
       const Mat2& rb = rops[i + 1].m;
+      // a phase table op just before the pair runs inside the pair's quad loop
+      int tab = -1;
+      if (g_fuse_tables && i > 0 && rops[i - 1].cls == kTableMark && g->nops > 0 &&
+          g->ops[g->nops - 1].kind == TOP_DTABLE && g->ops[g->nops - 1].lcmask < 128) {
+        --g->nops;
+        tab = (int)g->ops[g->nops].lcmask;
+      }
       TileOp& t0 = g->ops[g->nops];
       TileOp& t1 = g->ops[g->nops + 1];
       memset(&t0, 0, sizeof t0);
@@ -1009,6 +1018,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       t0.kind = TOP_REAL2;
       t0.tb = (int8_t)local[op.target];
       t0.code0 = (int8_t)local[rops[i + 1].target];
+      t0.code1 = (int8_t)tab;
       t1.kind = TOP_CONT;
       QL* e0 = reinterpret_cast<QL*>(t0.q);
       QL* e1 = reinterpret_cast<QL*>(t1.q);
@@ -1073,11 +1083,14 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     int_ops += N * class_touch_fraction(op) * op_int_ops_per_amp(op);
     ++g->nops;
   }
-  for (int k = 0; rc == QS_OK && k < g->nops; ++k)
-    if (g->ops[k].kind == TOP_DTABLE &&
-        (g->ops[k].lcmask >= ptables.size() || g->ops[k].tb != m ||
-         ptables[g->ops[k].lcmask].t.size() != ((size_t)1 << m)))
+  for (int k = 0; rc == QS_OK && k < g->nops; ++k) {
+    const TileOp& o = g->ops[k];
+    if (o.kind == TOP_DTABLE && (o.lcmask >= ptables.size() || o.tb != m || ptables[o.lcmask].t.size() != ((size_t)1 << m)))
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed phase-table op");
+    if (o.kind == TOP_REAL2 && (k + 1 >= g->nops || g->ops[k + 1].kind != TOP_CONT ||
+                                (o.code1 >= 0 && (size_t)o.code1 >= ptables.size())))
+      rc = fail(QS_ERR_INVALID_ARG, "internal: malformed rotation-pair op");
+  }
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables);
   g->nphases = 0;
   if (rc == QS_OK && fixed && g_register_bits && m >= g_register_bits) build_phases(g, g_register_bits);

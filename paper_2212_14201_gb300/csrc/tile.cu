@@ -190,9 +190,12 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
 // rotations apart but half the limb splits, roundings, shared-memory round trips
 // and barriers.  Every row of M (a Kronecker product of two rotations) has an L1
 // norm of at most 2, the bound the accumulators were sized for.
+// With a phase table (tab != nullptr, the table op just before the pair): every
+// amplitude of the quad is first multiplied by its table entry, which saves the
+// table op's own shared-memory round trip, index arithmetic and barrier.
 template <int THREADS>
 __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* m0,
-                                          const QL* m1) {
+                                          const QL* m1, const int2* tab) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
@@ -203,7 +206,14 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
     QL r[4], im[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const longlong2 v = tile[jj[c]];
+      longlong2 v = tile[jj[c]];
+      if (tab) {
+        const int2 ur = __ldg(tab + jj[c]), ui = __ldg(tab + TS + jj[c]), un = __ldg(tab + 2 * TS + jj[c]);
+        const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
+        int64_t vr, vi;
+        q60_gauss_mul(u, q60_split(v.x), q60_split(v.y), q60_split(v.x + v.y), &vr, &vi);
+        v = make_longlong2(vr, vi);
+      }
       r[c] = q60_split(v.x);
       im[c] = q60_split(v.y);
     }
@@ -268,8 +278,14 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           continue;
         }
         if (op.kind == TOP_REAL2) {
-          quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
-                             reinterpret_cast<const QL*>(g.ops[k + 1].q));
+          const int2* tab = op.code1 >= 0 ? reinterpret_cast<const int2*>(g.tables) + (size_t)op.code1 * 3 * TS
+                                          : nullptr;
+          if (tab)
+            quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
+                               reinterpret_cast<const QL*>(g.ops[k + 1].q), tab);
+          else
+            quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
+                               reinterpret_cast<const QL*>(g.ops[k + 1].q), nullptr);
           ++k;  // the continuation slot
           __syncthreads();
           continue;

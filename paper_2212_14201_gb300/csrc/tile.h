@@ -35,7 +35,8 @@ enum TileOpKind : int8_t {
                    // (table index in lcmask; TileArgs::tables)
   TOP_REAL2 = 11,  // Q60 only: two real rotations on tile bits tb and code0 as one real 4x4
                    // matrix on amplitude quads; its 16 entries (row-major, quad index
-                   // 2*bit(code0) + bit(tb)) fill q[] of this slot (12) and the next (4)
+                   // 2*bit(code0) + bit(tb)) fill q[] of this slot (12) and the next (4);
+                   // code1 >= 0: phase table code1 applied first (the op before the pair)
   TOP_CONT = 12,   // continuation slot of the op before it (never run on its own)
 };
 

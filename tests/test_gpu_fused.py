@@ -267,16 +267,16 @@ def test_phase_tables_survive_host_buffer_growth(q, orc):
 
 @pytest.mark.parametrize("n,kind", [(9, "brick"), (14, "brick"), (12, "rand"), (13, "hea")])
 def test_rotation_pairs_match_oracle(q, orc, n, kind):
-    """Q60 tile passes with pairs of real rotations run as 4x4 ops on quads, against
-    the oracle (1e-12) with the switch on and off; the limb products per step are
-    the same both ways."""
+    """Q60 tile passes with pairs of real rotations run as 4x4 ops on quads (with
+    and without the preceding phase table fused into the pair), against the oracle
+    (1e-12) and with the switch off; the limb products per step are the same."""
     g = {"brick": lambda: w.layered_u3_cz(n, 12, 4), "rand": lambda: w.random_circuit(n, 400, 12),
          "hea": lambda: w.hea_ansatz(n, 4)[0]}[kind]()
     params = w.uniform_angles(400, 5)
     ref = orc.as_complex(orc.run(n, g, params))
     work = {}
     try:
-        for on in (True, False):
+        for on in (1, 2, 0):
             q.qs_set_rotation_pairs(on)
             p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
             h = q.qs_alloc(n)
@@ -293,4 +293,4 @@ def test_rotation_pairs_match_oracle(q, orc, n, kind):
             work[on] = sum(r["int_ops"] for r in recs if r["kind"] == q._lib.K_TILE)
     finally:
         q.qs_set_rotation_pairs(True)
-    assert work[True] == work[False]
+    assert work[1] == work[2] == work[0]
