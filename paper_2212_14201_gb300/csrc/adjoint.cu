@@ -251,6 +251,7 @@ struct AdjPassArgs {
   BPass ps;
   const BOp* ops;   // ops of this pass (device), in execution order
   const QC* mats;   // 4 entries per op (device)
+  const QC* dgm;    // 16 entries per diagonal group (device)
   double* part;     // [slot][ADJ_GRID_STRIDE]
   int slot_base;
 };
@@ -288,9 +289,20 @@ __global__ void __launch_bounds__(BT_THREADS) k_adj_pass(double2* __restrict__ p
     __syncthreads();
     for (int k = ps.op_begin; k < ps.op_end; ++k) {
       const BOp op = a.ops[k];
-      if ((base & op.ext) != op.ext) continue;
-      // each thread reads and then rewrites only its own pairs of this op, so the
-      // generator partial and the update need no barrier between them
+      if (op.kb == BK_MEMBER || (base & op.ext) != op.ext) continue;
+      // each thread reads and then rewrites only its own pairs (amplitudes) of this
+      // op, so the generator partial and the update need no barrier between them
+      if (op.kb == BK_DGROUP) {
+        int64_t gp[BT_DG_MAX];
+        const BOp* mem = a.ops + k + 1;
+        bt_gen_dgroup(tP, tL, TS, mem, op.nmem, gp);
+        for (int mm = 0; mm < op.nmem; ++mm)
+          if (mem[mm].slot >= 0) bt_warp_accumulate(gp[mm], wacc, ps.nslots, mem[mm].slot);
+        bt_apply_dgroup(tP, TS, mem, op.nmem, a.dgm + 16 * op.gate);
+        bt_apply_dgroup(tL, TS, mem, op.nmem, a.dgm + 16 * op.gate);
+        __syncthreads();
+        continue;
+      }
       if (op.slot >= 0) bt_warp_accumulate(bt_gen_partial(tP, tL, TS, op, base), wacc, ps.nslots, op.slot);
       bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
       bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
@@ -331,7 +343,10 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   std::vector<uint32_t> remaining(ng), pass, rest;
   for (size_t i = 0; i < ng; ++i) remaining[i] = (uint32_t)i;
   std::vector<BOp> ops;
+  std::vector<Mat2> opm;  // each op's matrix (double), parallel to ops
   std::vector<QC> mats;
+  std::vector<QC> dgm;    // 16 Gauss-form entries per diagonal group
+  std::vector<int> dgheads, dgsrc;
   std::vector<BPass> passes;
   int slot_base = 0;
   std::vector<int> slot_bases;
@@ -387,7 +402,33 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
         slot_param.push_back(orig.param_idx);
       }
       ops.push_back(op);
-      for (int e = 0; e < 4; ++e) mats.push_back(qc_make_gauss(mt.m[e].re, mt.m[e].im));  // bt_apply's form
+      opm.push_back(mt);
+    }
+    // runs of diagonal ops -> diagonal groups; then the matrix tables in op order
+    const size_t ng0 = dgheads.size();
+    group_diagonals(ops, bp.op_begin, &dgheads, &dgsrc);
+    std::vector<Mat2> pm(dgsrc.size());
+    for (size_t k = 0; k < dgsrc.size(); ++k) {
+      if (dgsrc[k] >= 0) pm[k] = opm[dgsrc[k]];
+      else pm[k] = Mat2{};
+    }
+    opm.resize(bp.op_begin);
+    opm.insert(opm.end(), pm.begin(), pm.end());
+    for (size_t k = bp.op_begin; k < ops.size(); ++k)
+      for (int e = 0; e < 4; ++e) mats.push_back(qc_make_gauss(opm[k].m[e].re, opm[k].m[e].im));  // bt_apply's form
+    for (size_t gi = ng0; gi < dgheads.size(); ++gi) {
+      const int head = dgheads[gi];
+      const int nm = ops[head].nmem;
+      for (int idx = 0; idx < 16; ++idx) {
+        double re = 1.0, im = 0.0;
+        for (int mm = 0; mm < nm && idx < (1 << nm); ++mm) {
+          const C2 u = opm[head + 1 + mm].m[((idx >> mm) & 1) ? 3 : 0];
+          const double r2 = re * u.re - im * u.im, i2 = re * u.im + im * u.re;
+          re = r2;
+          im = i2;
+        }
+        dgm.push_back(qc_make_gauss(re, im));
+      }
     }
     bp.op_end = (int)ops.size();
     bp.nslots = slot;
@@ -398,12 +439,16 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   }
   BOp* d_ops = nullptr;
   QC* d_mats = nullptr;
+  QC* d_dgm = nullptr;
   QS_CUDA(cudaMallocAsync((void**)&d_ops, sizeof(BOp) * std::max<size_t>(1, ops.size()), s->stream));
   cudaError_t e = cudaMallocAsync((void**)&d_mats, sizeof(QC) * std::max<size_t>(4, mats.size()), s->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_dgm, sizeof(QC) * std::max<size_t>(16, dgm.size()), s->stream);
   if (e == cudaSuccess && !ops.empty())
     e = cudaMemcpyAsync(d_ops, ops.data(), sizeof(BOp) * ops.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && !mats.empty())
     e = cudaMemcpyAsync(d_mats, mats.data(), sizeof(QC) * mats.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && !dgm.empty())
+    e = cudaMemcpyAsync(d_dgm, dgm.data(), sizeof(QC) * dgm.size(), cudaMemcpyHostToDevice, s->stream);
   int rc = e == cudaSuccess ? QS_OK : cuda_fail(e, "adjoint op tables");
   static bool attr = false;
   if (rc == QS_OK && !attr) {
@@ -416,6 +461,7 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
     a.ps = passes[p];
     a.ops = d_ops;
     a.mats = d_mats;
+    a.dgm = d_dgm;
     a.part = part;
     a.slot_base = slot_bases[p];
     const uint32_t TS = 1u << a.ps.m;
@@ -431,6 +477,7 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   }
   cudaFreeAsync(d_ops, s->stream);
   cudaFreeAsync(d_mats, s->stream);
+  cudaFreeAsync(d_dgm, s->stream);
   return rc;
 }
 

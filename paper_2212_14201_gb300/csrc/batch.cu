@@ -46,6 +46,7 @@ struct BItem {
 
 struct BSet {
   int n, pass_begin, npasses, gate_begin, ngates, group_begin, ngroups, param_begin, nparams;
+  int dg_begin, ndg;  // diagonal groups (BK_DGROUP heads) of the set's passes
   long long amp_off;
   double S;
 };
@@ -83,6 +84,9 @@ struct BatchArgs {
   double2* lam;
   QC* matf;   // 4 per gate (Gauss form)
   QC* matb;   // 4 per gate (Gauss form)
+  const int* dghead;  // per diagonal group: global index of its head op
+  QC* dgf;    // 16 per diagonal group (Gauss form), forward
+  QC* dgb;    // 16 per diagonal group, adjoint
   int* counter;
 };
 
@@ -179,15 +183,27 @@ __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, d
     if (!backward) {
       for (int k = ps.op_begin; k < ps.op_end; ++k) {
         const BOp op = d.ops[k];
-        if ((base & op.ext) != op.ext) continue;
-        bt_apply(tP, TS, op, op.kf, op.c0f, op.c1f, matf + 4 * op.gate, base);
+        if (op.kf == BK_MEMBER || (base & op.ext) != op.ext) continue;
+        if (op.kf == BK_DGROUP) bt_apply_dgroup(tP, TS, d.ops + k + 1, op.nmem, d.dgf + 16 * op.gate);
+        else bt_apply(tP, TS, op, op.kf, op.c0f, op.c1f, matf + 4 * op.gate, base);
         __syncthreads();
       }
     } else {
       for (int k = ps.op_end - 1; k >= ps.op_begin; --k) {
         const BOp op = d.ops[k];
-        if ((base & op.ext) != op.ext) continue;
-        // each thread reads and then rewrites only its own pairs of this op
+        if (op.kb == BK_MEMBER || (base & op.ext) != op.ext) continue;
+        // each thread reads and then rewrites only its own pairs (amplitudes) of this op
+        if (op.kb == BK_DGROUP) {
+          int64_t part[BT_DG_MAX];
+          const BOp* mem = d.ops + k + 1;
+          bt_gen_dgroup(tP, tL, TS, mem, op.nmem, part);
+          for (int mm = 0; mm < op.nmem; ++mm)
+            if (mem[mm].slot >= 0) bt_warp_accumulate(part[mm], acc, ps.nslots, mem[mm].slot);
+          bt_apply_dgroup(tP, TS, mem, op.nmem, d.dgb + 16 * op.gate);
+          bt_apply_dgroup(tL, TS, mem, op.nmem, d.dgb + 16 * op.gate);
+          __syncthreads();
+          continue;
+        }
         if (op.slot >= 0) bt_warp_accumulate(bt_gen_partial(tP, tL, TS, op, base), acc, ps.nslots, op.slot);
         bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, matb + 4 * op.gate, base);
         bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, matb + 4 * op.gate, base);
@@ -251,6 +267,34 @@ __device__ void bt_eval_set(const BatchArgs& d, int set_id, int rank, int nr, lo
     for (int e = 0; e < 4; ++e) matf[4 * g + e] = qc_make_gauss(m[e].x, m[e].y);
     bt_gate_matrix(gt, d.params, true, m);
     for (int e = 0; e < 4; ++e) matb[4 * g + e] = qc_make_gauss(m[e].x, m[e].y);
+  }
+  // diagonal groups: E = product of the members' diagonals (forward and adjoint)
+  for (int gi = t0; gi < st.ndg; gi += ts) {
+    const int head = d.dghead[st.dg_begin + gi];
+    const int nm = d.ops[head].nmem;
+    double2 df[BT_DG_MAX][2], db[BT_DG_MAX][2];
+    for (int mm = 0; mm < nm; ++mm) {
+      const BGate gt = d.gates[st.gate_begin + d.ops[head + 1 + mm].gate];
+      double2 mt[4];
+      bt_gate_matrix(gt, d.params, false, mt);
+      df[mm][0] = mt[0];
+      df[mm][1] = mt[3];
+      bt_gate_matrix(gt, d.params, true, mt);
+      db[mm][0] = mt[0];
+      db[mm][1] = mt[3];
+    }
+    QC* ef = d.dgf + 16 * (size_t)(st.dg_begin + gi);
+    QC* eb = d.dgb + 16 * (size_t)(st.dg_begin + gi);
+    for (int idx = 0; idx < (1 << nm); ++idx) {
+      double2 f = make_double2(1.0, 0.0), b = make_double2(1.0, 0.0);
+      for (int mm = 0; mm < nm; ++mm) {
+        const double2 u = df[mm][(idx >> mm) & 1], v = db[mm][(idx >> mm) & 1];
+        f = make_double2(f.x * u.x - f.y * u.y, f.x * u.y + f.y * u.x);
+        b = make_double2(b.x * v.x - b.y * v.y, b.x * v.y + b.y * v.x);
+      }
+      ef[idx] = qc_make_gauss(f.x, f.y);
+      eb[idx] = qc_make_gauss(b.x, b.y);
+    }
   }
   for (int j = t0; j < st.nparams; j += ts) d.grads[st.param_begin + j] = 0.0;
   // 2. psi = |0>, forward passes
@@ -500,6 +544,7 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
   std::vector<BGate> bgates;
   std::vector<BGroup> groups;
   std::vector<BTerm> bterms;
+  std::vector<int> dgheads, dgsrc;
   long long amp_off = 0;
   for (size_t si = 0; si < nsets; ++si) {
     const int n = n_per_set[si];
@@ -567,6 +612,7 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
     }
     st.ngroups = (int)xms.size();
     // greedy tile passes
+    const int dg_first = (int)dgheads.size();
     const int m = std::min(n, BT_M);
     const uint64_t low = (1ull << std::min(n, 3)) - 1;
     std::vector<uint32_t> remaining(ng), pass, rest;
@@ -620,12 +666,15 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
         if (op.gen != BG_NONE) op.slot = (int16_t)slot++;
         ops.push_back(op);
       }
+      group_diagonals(ops, bp.op_begin, &dgheads, &dgsrc);
       bp.op_end = (int)ops.size();
       bp.nslots = slot;
       passes.push_back(bp);
       remaining.swap(rest);
     }
     st.npasses = (int)passes.size() - st.pass_begin;
+    st.dg_begin = dg_first;
+    st.ndg = (int)dgheads.size() - dg_first;
   }
   qs_batch* b = new (std::nothrow) qs_batch;
   if (!b) return fail(QS_ERR_OOM, "host allocation failed");
@@ -641,12 +690,16 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
   if (e != cudaSuccess) chk(cuda_fail(e, "cudaStreamCreate / cudaEventCreate"));
   BatchArgs& a = b->args;
+  void* p0dg = nullptr;
   if (rc == QS_OK) chk(upload(b, sets, &a.sets));
   if (rc == QS_OK) chk(upload(b, passes, &a.passes));
   if (rc == QS_OK) chk(upload(b, ops, &a.ops));
   if (rc == QS_OK) chk(upload(b, bgates, &a.gates));
   if (rc == QS_OK) chk(upload(b, groups, &a.groups));
   if (rc == QS_OK) chk(upload(b, bterms, &a.terms));
+  if (rc == QS_OK) chk(upload(b, dgheads, &a.dghead));
+  if (rc == QS_OK && chk(dev_alloc(b, std::max<size_t>(1, dgheads.size()) * 16 * sizeof(QC), &p0dg))) a.dgf = (QC*)p0dg;
+  if (rc == QS_OK && chk(dev_alloc(b, std::max<size_t>(1, dgheads.size()) * 16 * sizeof(QC), &p0dg))) a.dgb = (QC*)p0dg;
   void* p = nullptr;
   const size_t np = std::max<size_t>(1, b->total_params);
   if (rc == QS_OK && chk(dev_alloc(b, np * sizeof(double), &p))) { a.params = (const double*)p; b->d_params = (double*)p; }

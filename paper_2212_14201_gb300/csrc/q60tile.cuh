@@ -3,6 +3,10 @@
 // generator inner product Im <lambda| G |psi> over a tile.
 #pragma once
 
+#include <string.h>
+
+#include <vector>
+
 #include "fixed.h"
 #include "internal.h"
 
@@ -14,7 +18,13 @@ constexpr int BT_MAX_OPS = 128;   // ops (and gradient slots) per pass: keeps 3 
 constexpr int BT_MAX_N = 24;
 constexpr int BT_OFFS = 1 << (BT_M - 3);  // high-bit offset table: tiles hold qubits 0..2 (or all of n < 3)
 
-enum : int8_t { BK_SCALAR = 9 };
+// BK_DGROUP: a group of up to four uncontrolled diagonal gates on distinct tile
+// qubits, run as one op: amplitude j gets E[idx], idx = the member target bits
+// of j (member m at bit m), E = the product of the members' diagonals (16 entries
+// per group, Gauss form).  The members follow the head as BK_MEMBER records
+// (nothing to run on their own) and keep their generator slots.
+enum : int8_t { BK_SCALAR = 9, BK_DGROUP = 10, BK_MEMBER = 11 };
+constexpr int BT_DG_MAX = 4;  // members per group
 enum : int8_t { BG_NONE = 0, BG_X = 1, BG_Y = 2, BG_Z = 3, BG_P = 4 };
 
 struct BPass {
@@ -34,7 +44,55 @@ struct BOp {
   int8_t tb;        // local target bit (global target bit for SCALAR)
   int8_t gen;
   int8_t c0f, c1f, c0b, c1b;
+  int8_t nmem;      // BK_DGROUP head: members following it (gate = group index)
 };
+
+// Diagonal group (see BK_DGROUP): a_j *= E[idx(j)].
+static __device__ void bt_apply_dgroup(longlong2* tile, uint32_t TS, const BOp* mem, int nm, const QC* E) {
+  int tbs[BT_DG_MAX];
+#pragma unroll
+  for (int m = 0; m < BT_DG_MAX; ++m) tbs[m] = m < nm ? mem[m].tb : 0;
+  for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+    uint32_t idx = 0;
+#pragma unroll
+    for (int m = 0; m < BT_DG_MAX; ++m)
+      if (m < nm) idx |= ((j >> tbs[m]) & 1u) << m;
+    const QC u = E[idx];
+    const longlong2 a = tile[j];
+    int64_t re, im;
+    q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
+    tile[j] = make_longlong2(re, im);
+  }
+}
+
+// Generator partials of every member of a diagonal group on the same tiles, in
+// Q60 units: w_j = Im(conj(l_j) p_j) once per amplitude, then per member Z:
+// (-1)^bit w_j, P: -2 [bit] w_j (the members commute with each other and with
+// each other's generators, so every term may be taken before the group runs).
+// Bounds as in bt_gen_partial.
+static __device__ void bt_gen_dgroup(const longlong2* P, const longlong2* Lt, uint32_t TS, const BOp* mem, int nm,
+                                     int64_t* out) {
+  int tbs[BT_DG_MAX], gens[BT_DG_MAX];
+#pragma unroll
+  for (int m = 0; m < BT_DG_MAX; ++m) {
+    out[m] = 0;
+    tbs[m] = m < nm ? mem[m].tb : 0;
+    gens[m] = m < nm ? mem[m].gen : BG_NONE;
+  }
+  for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+    const longlong2 p = P[j], l = Lt[j];
+    QAccF acc{0, 0, 0};
+    qaccf_add(acc, q60_split(l.x), q60_split(p.y));
+    qaccf_add(acc, q60_split(-l.y), q60_split(p.x));
+    const int64_t w = qaccf_result(acc);
+#pragma unroll
+    for (int m = 0; m < BT_DG_MAX; ++m) {
+      const bool one = (j >> tbs[m]) & 1u;
+      if (gens[m] == BG_Z) out[m] += one ? -w : w;
+      else if (gens[m] == BG_P && one) out[m] -= 2 * w;
+    }
+  }
+}
 
 
 __device__ __forceinline__ longlong2 bt_unit(longlong2 a, int code) {
@@ -227,6 +285,56 @@ static __device__ double bt_block_sum(double v, double* red) {
 #pragma unroll
   for (int i = 0; i < BT_THREADS / 32; ++i) r += red[i];
   return r;
+}
+
+// Runs of up to BT_DG_MAX consecutive uncontrolled diagonal ops (forward and
+// adjoint class) on distinct tile qubits, with a Z, P or no generator, of the
+// ops [begin, end) become diagonal groups: a BK_DGROUP head (gate = group index,
+// nmem members) is inserted before the members, which turn into BK_MEMBER
+// records.  Heads are appended to `heads` (their index in the new op list);
+// src[i - begin] receives the old index of new op i (-1 for a head).
+static inline void group_diagonals(std::vector<BOp>& ops, size_t begin, std::vector<int>* heads,
+                                   std::vector<int>* src) {
+  auto eligible = [](const BOp& o) {
+    const bool df = o.kf == OP_DIAG || o.kf == OP_PHASE1, db = o.kb == OP_DIAG || o.kb == OP_PHASE1;
+    return df && db && o.lcm == 0 && o.ext == 0 && (o.gen == BG_NONE || o.gen == BG_Z || o.gen == BG_P);
+  };
+  std::vector<BOp> out(ops.begin(), ops.begin() + begin);
+  src->clear();
+  size_t i = begin;
+  while (i < ops.size()) {
+    size_t j = i;
+    uint32_t bits = 0;
+    while (j < ops.size() && j - i < (size_t)BT_DG_MAX && eligible(ops[j]) && !((bits >> ops[j].tb) & 1)) {
+      bits |= 1u << ops[j].tb;
+      ++j;
+    }
+    if (j - i >= 2) {
+      BOp h;
+      memset(&h, 0, sizeof h);
+      h.kf = h.kb = BK_DGROUP;
+      h.nmem = (int8_t)(j - i);
+      h.gate = (int)heads->size();
+      h.slot = -1;
+      h.param = -1;
+      h.gen = BG_NONE;
+      heads->push_back((int)out.size());
+      out.push_back(h);
+      src->push_back(-1);
+      for (size_t k = i; k < j; ++k) {
+        BOp mo = ops[k];
+        mo.kf = mo.kb = BK_MEMBER;
+        out.push_back(mo);
+        src->push_back((int)k);
+      }
+      i = j;
+    } else {
+      out.push_back(ops[i]);
+      src->push_back((int)i);
+      ++i;
+    }
+  }
+  ops.swap(out);
 }
 
 }  // namespace qs
