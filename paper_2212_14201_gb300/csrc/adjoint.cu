@@ -252,11 +252,12 @@ struct AdjPassArgs {
   const BOp* ops;   // ops of this pass (device), in execution order
   const QC* mats;   // 4 entries per op (device)
   const QC* dgm;    // 16 entries per diagonal group (device)
+  const QL* rpm;    // 16 entries per real pair (device)
   double* part;     // [slot][ADJ_GRID_STRIDE]
   int slot_base;
 };
 
-__global__ void __launch_bounds__(BT_THREADS) k_adj_pass(double2* __restrict__ psi, double2* __restrict__ lam,
+__global__ void __launch_bounds__(BT_THREADS, 3) k_adj_pass(double2* __restrict__ psi, double2* __restrict__ lam,
                                                          const AdjPassArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BPass& ps = a.ps;
@@ -303,6 +304,16 @@ __global__ void __launch_bounds__(BT_THREADS) k_adj_pass(double2* __restrict__ p
         __syncthreads();
         continue;
       }
+      if (op.kb == BK_RPAIR) {
+        const BOp* mem = a.ops + k + 1;
+        int64_t ga, gb;
+        bt_rpair_back(tP, tL, TS, 1u << mem[0].tb, 1u << mem[1].tb, mem[0].gen, mem[1].gen, a.rpm + 16 * op.gate,
+                      &ga, &gb);
+        if (mem[0].slot >= 0) bt_warp_accumulate(ga, wacc, ps.nslots, mem[0].slot);
+        if (mem[1].slot >= 0) bt_warp_accumulate(gb, wacc, ps.nslots, mem[1].slot);
+        __syncthreads();
+        continue;
+      }
       if (op.slot >= 0) bt_warp_accumulate(bt_gen_partial(tP, tL, TS, op, base), wacc, ps.nslots, op.slot);
       bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
       bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
@@ -346,7 +357,8 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   std::vector<Mat2> opm;  // each op's matrix (double), parallel to ops
   std::vector<QC> mats;
   std::vector<QC> dgm;    // 16 Gauss-form entries per diagonal group
-  std::vector<int> dgheads, dgsrc;
+  std::vector<int> dgheads, dgsrc, rpheads;
+  std::vector<QL> rpm;    // 16 limb pairs per real pair
   std::vector<BPass> passes;
   int slot_base = 0;
   std::vector<int> slot_bases;
@@ -405,8 +417,8 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
       opm.push_back(mt);
     }
     // runs of diagonal ops -> diagonal groups; then the matrix tables in op order
-    const size_t ng0 = dgheads.size();
-    group_diagonals(ops, bp.op_begin, &dgheads, &dgsrc);
+    const size_t ng0 = dgheads.size(), np0 = rpheads.size();
+    group_diagonals(ops, bp.op_begin, &dgheads, &dgsrc, &rpheads);
     std::vector<Mat2> pm(dgsrc.size());
     for (size_t k = 0; k < dgsrc.size(); ++k) {
       if (dgsrc[k] >= 0) pm[k] = opm[dgsrc[k]];
@@ -430,6 +442,13 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
         dgm.push_back(qc_make_gauss(re, im));
       }
     }
+    for (size_t pi = np0; pi < rpheads.size(); ++pi) {  // M = R_b (x) R_a, a = first member
+      const Mat2& ra = opm[rpheads[pi] + 1];
+      const Mat2& rb = opm[rpheads[pi] + 2];
+      for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 4; ++c)
+          rpm.push_back(q60_split(q60_from_double(rb.m[2 * (k >> 1) + (c >> 1)].re * ra.m[2 * (k & 1) + (c & 1)].re)));
+    }
     bp.op_end = (int)ops.size();
     bp.nslots = slot;
     passes.push_back(bp);
@@ -440,9 +459,13 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   BOp* d_ops = nullptr;
   QC* d_mats = nullptr;
   QC* d_dgm = nullptr;
+  QL* d_rpm = nullptr;
   QS_CUDA(cudaMallocAsync((void**)&d_ops, sizeof(BOp) * std::max<size_t>(1, ops.size()), s->stream));
   cudaError_t e = cudaMallocAsync((void**)&d_mats, sizeof(QC) * std::max<size_t>(4, mats.size()), s->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_dgm, sizeof(QC) * std::max<size_t>(16, dgm.size()), s->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_rpm, sizeof(QL) * std::max<size_t>(16, rpm.size()), s->stream);
+  if (e == cudaSuccess && !rpm.empty())
+    e = cudaMemcpyAsync(d_rpm, rpm.data(), sizeof(QL) * rpm.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && !ops.empty())
     e = cudaMemcpyAsync(d_ops, ops.data(), sizeof(BOp) * ops.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && !mats.empty())
@@ -462,6 +485,7 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
     a.ops = d_ops;
     a.mats = d_mats;
     a.dgm = d_dgm;
+    a.rpm = d_rpm;
     a.part = part;
     a.slot_base = slot_bases[p];
     const uint32_t TS = 1u << a.ps.m;
@@ -478,6 +502,7 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   cudaFreeAsync(d_ops, s->stream);
   cudaFreeAsync(d_mats, s->stream);
   cudaFreeAsync(d_dgm, s->stream);
+  cudaFreeAsync(d_rpm, s->stream);
   return rc;
 }
 

@@ -666,7 +666,9 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
         if (op.gen != BG_NONE) op.slot = (int16_t)slot++;
         ops.push_back(op);
       }
-      group_diagonals(ops, bp.op_begin, &dgheads, &dgsrc);
+      // (no real pairs here: their quad code alone pushes the batch kernel past its
+      // 80-register budget for three CTAs per SM; measured 847 -> 879 ms)
+      group_diagonals(ops, bp.op_begin, &dgheads, &dgsrc, nullptr);
       bp.op_end = (int)ops.size();
       bp.nslots = slot;
       passes.push_back(bp);

@@ -23,7 +23,12 @@ constexpr int BT_OFFS = 1 << (BT_M - 3);  // high-bit offset table: tiles hold q
 // of j (member m at bit m), E = the product of the members' diagonals (16 entries
 // per group, Gauss form).  The members follow the head as BK_MEMBER records
 // (nothing to run on their own) and keep their generator slots.
-enum : int8_t { BK_SCALAR = 9, BK_DGROUP = 10, BK_MEMBER = 11 };
+// BK_RPAIR: two uncontrolled real ops on distinct tile qubits a (first member)
+// and b, run as one real 4x4 M = R_b (x) R_a on the quads (j, j|a, j|b, j|a|b)
+// (entries row-major, quad index 2*bit(b) + bit(a); 16 limb pairs per pair,
+// gate = pair index); in the backward sweep the op also takes both members'
+// generator terms from the quads it has loaded.
+enum : int8_t { BK_SCALAR = 9, BK_DGROUP = 10, BK_MEMBER = 11, BK_RPAIR = 12 };
 constexpr int BT_DG_MAX = 4;  // members per group
 enum : int8_t { BG_NONE = 0, BG_X = 1, BG_Y = 2, BG_Z = 3, BG_P = 4 };
 
@@ -63,6 +68,94 @@ static __device__ void bt_apply_dgroup(longlong2* tile, uint32_t TS, const BOp* 
     q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
     tile[j] = make_longlong2(re, im);
   }
+}
+
+// One output component of the 4x4 real M (row k) on four split inputs.
+__device__ __forceinline__ int64_t bt_row4(const QL* M, int k, const QL* x) {
+  QAcc acc = qacc_new();
+#pragma unroll
+  for (int c = 0; c < 4; ++c) qacc_add(acc, M[4 * k + c], x[c]);
+  return qacc_round(acc);
+}
+
+// Generator term of one pair (amplitudes 0 and 1 of the pair) for generator `gen`,
+// as the signed products of bt_gen_partial, exactly in Q60 units.
+__device__ __forceinline__ int64_t bt_pair_gen(int gen, QL l0x, QL l0y, QL l1x, QL l1y, QL p0x, QL p0y, QL p1x,
+                                               QL p1y) {
+  QAccF pos{0, 0, 0}, neg{0, 0, 0};
+  switch (gen) {
+    case BG_X:  // l0x p1y - l0y p1x + l1x p0y - l1y p0x
+      qaccf_add(pos, l0x, p1y); qaccf_add(neg, l0y, p1x); qaccf_add(pos, l1x, p0y); qaccf_add(neg, l1y, p0x);
+      break;
+    case BG_Y:  // -l0x p1x - l0y p1y + l1x p0x + l1y p0y
+      qaccf_add(neg, l0x, p1x); qaccf_add(neg, l0y, p1y); qaccf_add(pos, l1x, p0x); qaccf_add(pos, l1y, p0y);
+      break;
+    case BG_Z:  // l0x p0y - l0y p0x - l1x p1y + l1y p1x
+      qaccf_add(pos, l0x, p0y); qaccf_add(neg, l0y, p0x); qaccf_add(neg, l1x, p1y); qaccf_add(pos, l1y, p1x);
+      break;
+    case BG_P:  // -2 (l1x p1y - l1y p1x)
+      qaccf_add(neg, l1x, p1y); qaccf_add(pos, l1y, p1x);
+      return 2 * (qaccf_result(pos) - qaccf_result(neg));
+    default:
+      return 0;
+  }
+  return qaccf_result(pos) - qaccf_result(neg);
+}
+
+// Real pair forward: the quads of the tile through M.
+static __device__ void bt_rpair(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* __restrict__ M) {
+  const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
+  for (uint32_t i = threadIdx.x; i < (TS >> 2); i += BT_THREADS) {
+    uint32_t j = i + (i & ~(lo - 1));
+    j = j + (j & ~(hi - 1));
+    const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
+    QL r[4], im[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const longlong2 v = tile[jj[c]];
+      r[c] = q60_split(v.x);
+      im[c] = q60_split(v.y);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tile[jj[k]] = make_longlong2(bt_row4(M, k, r), bt_row4(M, k, im));
+  }
+}
+
+// Real pair backward: both members' generator terms (member a on the pairs
+// (0,1), (2,3) of the quad, member b on (0,2), (1,3)), then M on both tiles.
+static __device__ void bt_rpair_back(longlong2* P, longlong2* Lt, uint32_t TS, uint32_t ta, uint32_t tbb, int gen_a,
+                                     int gen_b, const QL* __restrict__ M, int64_t* out_a, int64_t* out_b) {
+  int64_t sa = 0, sb = 0;
+  const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
+  for (uint32_t i = threadIdx.x; i < (TS >> 2); i += BT_THREADS) {
+    uint32_t j = i + (i & ~(lo - 1));
+    j = j + (j & ~(hi - 1));
+    const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
+    QL pr[4], pi[4], lr[4], li[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const longlong2 v = P[jj[c]], w = Lt[jj[c]];
+      pr[c] = q60_split(v.x);
+      pi[c] = q60_split(v.y);
+      lr[c] = q60_split(w.x);
+      li[c] = q60_split(w.y);
+    }
+    if (gen_a != BG_NONE) {
+      sa += bt_pair_gen(gen_a, lr[0], li[0], lr[1], li[1], pr[0], pi[0], pr[1], pi[1]);
+      sa += bt_pair_gen(gen_a, lr[2], li[2], lr[3], li[3], pr[2], pi[2], pr[3], pi[3]);
+    }
+    if (gen_b != BG_NONE) {
+      sb += bt_pair_gen(gen_b, lr[0], li[0], lr[2], li[2], pr[0], pi[0], pr[2], pi[2]);
+      sb += bt_pair_gen(gen_b, lr[1], li[1], lr[3], li[3], pr[1], pi[1], pr[3], pi[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      P[jj[k]] = make_longlong2(bt_row4(M, k, pr), bt_row4(M, k, pi));
+      Lt[jj[k]] = make_longlong2(bt_row4(M, k, lr), bt_row4(M, k, li));
+    }
+  }
+  *out_a = sa;
+  *out_b = sb;
 }
 
 // Generator partials of every member of a diagonal group on the same tiles, in
@@ -293,16 +386,40 @@ static __device__ double bt_block_sum(double v, double* red) {
 // nmem members) is inserted before the members, which turn into BK_MEMBER
 // records.  Heads are appended to `heads` (their index in the new op list);
 // src[i - begin] receives the old index of new op i (-1 for a head).
+// Consecutive uncontrolled real ops on distinct tile qubits become real pairs
+// the same way (a BK_RPAIR head, gate = index into `pairs`, two BK_MEMBER records).
 static inline void group_diagonals(std::vector<BOp>& ops, size_t begin, std::vector<int>* heads,
-                                   std::vector<int>* src) {
+                                   std::vector<int>* src, std::vector<int>* pairs = nullptr) {
   auto eligible = [](const BOp& o) {
     const bool df = o.kf == OP_DIAG || o.kf == OP_PHASE1, db = o.kb == OP_DIAG || o.kb == OP_PHASE1;
     return df && db && o.lcm == 0 && o.ext == 0 && (o.gen == BG_NONE || o.gen == BG_Z || o.gen == BG_P);
   };
+  auto real = [](const BOp& o) { return o.kf == OP_REAL && o.kb == OP_REAL && o.lcm == 0 && o.ext == 0; };
   std::vector<BOp> out(ops.begin(), ops.begin() + begin);
   src->clear();
   size_t i = begin;
   while (i < ops.size()) {
+    if (pairs && i + 1 < ops.size() && real(ops[i]) && real(ops[i + 1]) && ops[i].tb != ops[i + 1].tb) {
+      BOp h;
+      memset(&h, 0, sizeof h);
+      h.kf = h.kb = BK_RPAIR;
+      h.nmem = 2;
+      h.gate = (int)pairs->size();
+      h.slot = -1;
+      h.param = -1;
+      h.gen = BG_NONE;
+      pairs->push_back((int)out.size());
+      out.push_back(h);
+      src->push_back(-1);
+      for (size_t k = i; k < i + 2; ++k) {
+        BOp mo = ops[k];
+        mo.kf = mo.kb = BK_MEMBER;
+        out.push_back(mo);
+        src->push_back((int)k);
+      }
+      i += 2;
+      continue;
+    }
     size_t j = i;
     uint32_t bits = 0;
     while (j < ops.size() && j - i < (size_t)BT_DG_MAX && eligible(ops[j]) && !((bits >> ops[j].tb) & 1)) {
