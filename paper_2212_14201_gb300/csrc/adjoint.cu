@@ -314,6 +314,11 @@ __global__ void __launch_bounds__(BT_THREADS, 3) k_adj_pass(double2* __restrict_
         __syncthreads();
         continue;
       }
+      if (op.slot >= 0 && op.kb == OP_REAL) {  // one pass over the pairs
+        bt_warp_accumulate(bt_back_real(tP, tL, TS, op, a.mats + 4 * k), wacc, ps.nslots, op.slot);
+        __syncthreads();
+        continue;
+      }
       if (op.slot >= 0) bt_warp_accumulate(bt_gen_partial(tP, tL, TS, op, base), wacc, ps.nslots, op.slot);
       bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);
       bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, a.mats + 4 * k, base);

@@ -204,6 +204,11 @@ __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, d
           __syncthreads();
           continue;
         }
+        if (op.slot >= 0 && op.kb == OP_REAL) {  // one pass over the pairs
+          bt_warp_accumulate(bt_back_real(tP, tL, TS, op, matb + 4 * op.gate), acc, ps.nslots, op.slot);
+          __syncthreads();
+          continue;
+        }
         if (op.slot >= 0) bt_warp_accumulate(bt_gen_partial(tP, tL, TS, op, base), acc, ps.nslots, op.slot);
         bt_apply(tP, TS, op, op.kb, op.c0b, op.c1b, matb + 4 * op.gate, base);
         bt_apply(tL, TS, op, op.kb, op.c0b, op.c1b, matb + 4 * op.gate, base);

@@ -348,6 +348,42 @@ static __device__ int64_t bt_gen_partial(const longlong2* P, const longlong2* Lt
   return acc;
 }
 
+// Backward step of a pair op of class REAL with a generator (RY, H-type rows):
+// for each of this thread's pairs, the generator term and then U on the psi pair
+// and on the lambda pair, from one load and one limb split of each (real entries
+// in u.re of the Gauss form).  Returns the thread's partial.
+static __device__ int64_t bt_back_real(longlong2* P, longlong2* Lt, uint32_t TS, const BOp& op,
+                                       const QC* __restrict__ U) {
+  const uint32_t tb = 1u << op.tb;
+  const uint32_t fixed = op.lcm | tb;
+  const uint32_t cnt = TS >> __popc(fixed);
+  int64_t acc = 0;
+  for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+    const uint32_t j0 = op.lcm ? bt_expand(i, fixed, op.lcm) : i + (i & ~(tb - 1)), j1 = j0 | tb;
+    const longlong2 p0 = P[j0], p1 = P[j1], l0 = Lt[j0], l1 = Lt[j1];
+    const QL p0x = q60_split(p0.x), p0y = q60_split(p0.y), p1x = q60_split(p1.x), p1y = q60_split(p1.y);
+    const QL l0x = q60_split(l0.x), l0y = q60_split(l0.y), l1x = q60_split(l1.x), l1y = q60_split(l1.y);
+    acc += bt_pair_gen(op.gen, l0x, l0y, l1x, l1y, p0x, p0y, p1x, p1y);
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const QL u0 = U[2 * row].re, u1 = U[2 * row + 1].re;
+      QAcc pr = qacc_new(), pi = qacc_new(), lr = qacc_new(), li = qacc_new();
+      qacc_add(pr, u0, p0x);
+      qacc_add(pr, u1, p1x);
+      qacc_add(pi, u0, p0y);
+      qacc_add(pi, u1, p1y);
+      qacc_add(lr, u0, l0x);
+      qacc_add(lr, u1, l1x);
+      qacc_add(li, u0, l0y);
+      qacc_add(li, u1, l1y);
+      const uint32_t jr = row ? j1 : j0;
+      P[jr] = make_longlong2(qacc_round(pr), qacc_round(pi));
+      Lt[jr] = make_longlong2(qacc_round(lr), qacc_round(li));
+    }
+  }
+  return acc;
+}
+
 // Adds this thread's partial (Q60 units) to its warp's accumulator of `slot`
 // without a CTA barrier: the warp sums exactly by integer shuffles (the bound of
 // bt_gen_partial holds for the warp's total too), lane 0 converts once and owns
