@@ -296,11 +296,9 @@ __global__ void __launch_bounds__(BT_THREADS, 3) k_adj_pass(double2* __restrict_
       if (op.kb == BK_DGROUP) {
         int64_t gp[BT_DG_MAX];
         const BOp* mem = a.ops + k + 1;
-        bt_gen_dgroup(tP, tL, TS, mem, op.nmem, gp);
+        bt_back_dgroup(tP, tL, TS, mem, op.nmem, a.dgm + 16 * op.gate, gp);
         for (int mm = 0; mm < op.nmem; ++mm)
           if (mem[mm].slot >= 0) bt_warp_accumulate(gp[mm], wacc, ps.nslots, mem[mm].slot);
-        bt_apply_dgroup(tP, TS, mem, op.nmem, a.dgm + 16 * op.gate);
-        bt_apply_dgroup(tL, TS, mem, op.nmem, a.dgm + 16 * op.gate);
         __syncthreads();
         continue;
       }

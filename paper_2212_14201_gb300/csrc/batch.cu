@@ -196,11 +196,9 @@ __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, d
         if (op.kb == BK_DGROUP) {
           int64_t part[BT_DG_MAX];
           const BOp* mem = d.ops + k + 1;
-          bt_gen_dgroup(tP, tL, TS, mem, op.nmem, part);
+          bt_back_dgroup(tP, tL, TS, mem, op.nmem, d.dgb + 16 * op.gate, part);
           for (int mm = 0; mm < op.nmem; ++mm)
             if (mem[mm].slot >= 0) bt_warp_accumulate(part[mm], acc, ps.nslots, mem[mm].slot);
-          bt_apply_dgroup(tP, TS, mem, op.nmem, d.dgb + 16 * op.gate);
-          bt_apply_dgroup(tL, TS, mem, op.nmem, d.dgb + 16 * op.gate);
           __syncthreads();
           continue;
         }

@@ -158,6 +158,41 @@ static __device__ void bt_rpair_back(longlong2* P, longlong2* Lt, uint32_t TS, u
   *out_b = sb;
 }
 
+// Backward step of a diagonal group in one sweep: per amplitude the members'
+// generator terms (as bt_gen_dgroup) and then E on psi and on lambda.
+static __device__ void bt_back_dgroup(longlong2* P, longlong2* Lt, uint32_t TS, const BOp* mem, int nm,
+                                      const QC* __restrict__ E, int64_t* out) {
+  int tbs[BT_DG_MAX], gens[BT_DG_MAX];
+#pragma unroll
+  for (int m = 0; m < BT_DG_MAX; ++m) {
+    out[m] = 0;
+    tbs[m] = m < nm ? mem[m].tb : 0;
+    gens[m] = m < nm ? mem[m].gen : BG_NONE;
+  }
+  for (uint32_t j = threadIdx.x; j < TS; j += BT_THREADS) {
+    const longlong2 p = P[j], l = Lt[j];
+    const QL px = q60_split(p.x), py = q60_split(p.y), lx = q60_split(l.x), ly = q60_split(l.y);
+    QAccF pos{0, 0, 0}, neg{0, 0, 0};
+    qaccf_add(pos, lx, py);
+    qaccf_add(neg, ly, px);
+    const int64_t w = qaccf_result(pos) - qaccf_result(neg);
+    uint32_t idx = 0;
+#pragma unroll
+    for (int m = 0; m < BT_DG_MAX; ++m) {
+      const bool one = (j >> tbs[m]) & 1u;
+      if (m < nm) idx |= (uint32_t)one << m;
+      if (gens[m] == BG_Z) out[m] += one ? -w : w;
+      else if (gens[m] == BG_P && one) out[m] -= 2 * w;
+    }
+    const QC u = E[idx];
+    int64_t re, im;
+    q60_gauss_mul(u, px, py, q60_split(p.x + p.y), &re, &im);
+    P[j] = make_longlong2(re, im);
+    q60_gauss_mul(u, lx, ly, q60_split(l.x + l.y), &re, &im);
+    Lt[j] = make_longlong2(re, im);
+  }
+}
+
 // Generator partials of every member of a diagonal group on the same tiles, in
 // Q60 units: w_j = Im(conj(l_j) p_j) once per amplitude, then per member Z:
 // (-1)^bit w_j, P: -2 [bit] w_j (the members commute with each other and with
