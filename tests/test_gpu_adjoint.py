@@ -162,3 +162,18 @@ def test_per_gate_backward_path(q, orc, n, layers):
         q.qs_set_adjoint_fused(True)
     e0, g0 = orc.adjoint_grad(n, g, th, H)
     assert abs(e - e0) < 1e-12 and rel_close(grad, g0)
+
+
+@pytest.mark.parametrize("n,layers", [(3, 2), (8, 3), (13, 3)])
+def test_fused_backward_groups_and_pairs(q, orc, n, layers):
+    """Diagonal groups (Z and P generators, members with and without parameters,
+    a parameter shared inside a group) and real pairs (Y generators, dagger flags,
+    pairs without generators) against the oracle's adjoint recursion, fused
+    backward (Q60) and the per-gate path (FP64)."""
+    g, npar = w.mixed_layers_circuit(n, layers, 5 + n)
+    th = w.uniform_angles(npar, 9 + n)
+    H = w.random_paulis(n, 12, 4)
+    e0, g0 = orc.adjoint_grad(n, g, th, H)
+    for arith in (q.ARITH_FIXED, q.ARITH_FP64):
+        e, grad = gpu_grad(q, n, g, th, H, arith)
+        assert abs(e - e0) < 1e-12 and rel_close(grad, g0), arith

@@ -186,3 +186,27 @@ def test_full_batch_matches_single_state_adjoint(q):
     finally:
         for h in hs.values():
             q.qs_free(h)
+
+
+def test_batch_groups_and_fused_backward_steps(q, orc):
+    """Sets built to exercise diagonal groups (Z and P generators, members with and
+    without parameters, a parameter shared inside a group) and the one-sweep
+    backward of real ops, against the oracle's adjoint recursion."""
+    sets = [(n, *w.mixed_layers_circuit(n, 3, 20 + n)) for n in (4, 9, 13)]
+    ns = [s[0] for s in sets]
+    nps = [s[2] for s in sets]
+    params = w.uniform_angles(int(sum(nps)), 21)
+    terms = [w.random_paulis(n, 8, n) for n in ns]
+    b = q.qs_batch_create(ns, [s[1] for s in sets], nps, terms)
+    try:
+        e = np.empty(len(ns))
+        g = np.empty(len(params))
+        q.qs_batch_run(b, params, e, g)
+    finally:
+        q.qs_batch_free(b)
+    off = 0
+    for i, (n, gates, npar) in enumerate(sets):
+        e0, g0 = orc.adjoint_grad(n, gates, params[off:off + npar], terms[i])
+        assert abs(e[i] - e0) < 1e-12
+        assert rel_close(g[off:off + npar], g0)
+        off += npar

@@ -166,6 +166,43 @@ def hea_ansatz(n: int, layers: int) -> tuple[np.ndarray, int]:
     return pack(recs), k
 
 
+def mixed_layers_circuit(n: int, layers: int, seed: int) -> tuple[np.ndarray, int]:
+    """Parametrised layers mixing gate kinds: an H layer; per layer RY on every
+    qubit (every third daggered), then per qubit one of RZ (on a parameter shared
+    within the layer), P (alternately daggered), an unparametrised S, T or Z, or
+    RZ on its own parameter, with one controlled RZ in the middle of the run; a
+    CNOT ring (control (i+1) mod n, target i); H on even qubits.
+    Returns (records, parameter count)."""
+    rng = SplitMix64(seed)
+    recs = [gate("H", qq) for qq in range(n)]
+    p = 0
+    for layer in range(layers):
+        for qq in range(n):
+            recs.append(gate("RY", qq, param_idx=p, dagger=int((qq + layer) % 3 == 0)))
+            p += 1
+        shared = p
+        p += 1
+        for qq in range(n):
+            k = rng.below(5)
+            if k == 0:
+                recs.append(gate("RZ", qq, param_idx=shared))
+            elif k == 1:
+                recs.append(gate("P", qq, param_idx=p, dagger=qq & 1))
+                p += 1
+            elif k == 2:
+                recs.append(gate(("S", "T", "Z")[rng.below(3)], qq))
+            else:
+                recs.append(gate("RZ", qq, param_idx=p))
+                p += 1
+            if qq == n // 2 and n > 1:
+                recs.append(gate("RZ", qq, param_idx=p, ctrl_mask=1 << ((qq + 1) % n)))
+                p += 1
+        if n > 1:
+            recs += [gate("CNOT", (qq + 1) % n, qq) for qq in range(n)]
+        recs += [gate("H", qq) for qq in range(0, n, 2)]
+    return pack(recs), p
+
+
 def uniform_angles(count: int, seed: int) -> np.ndarray:
     rng = SplitMix64(seed)
     return np.array([rng.angle() for _ in range(count)], dtype=np.float64)
