@@ -312,6 +312,11 @@ __global__ void __launch_bounds__(BT_THREADS, 3) k_adj_pass(double2* __restrict_
         __syncthreads();
         continue;
       }
+      if (op.slot < 0 && op.kb == OP_ANTI && op.c0b != U_GENERAL && op.c1b != U_GENERAL) {
+        bt_anti_both(tP, tL, TS, op, op.c0b, op.c1b);  // psi and lambda in one sweep
+        __syncthreads();
+        continue;
+      }
       if (op.slot >= 0 && op.kb == OP_REAL) {  // one pass over the pairs
         bt_warp_accumulate(bt_back_real(tP, tL, TS, op, a.mats + 4 * k), wacc, ps.nslots, op.slot);
         __syncthreads();

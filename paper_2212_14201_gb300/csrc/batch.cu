@@ -202,6 +202,11 @@ __device__ void bt_run_pass(const BatchArgs& d, const BPass& ps, double2* psi, d
           __syncthreads();
           continue;
         }
+        if (op.slot < 0 && op.kb == OP_ANTI && op.c0b != U_GENERAL && op.c1b != U_GENERAL) {
+          bt_anti_both(tP, tL, TS, op, op.c0b, op.c1b);  // psi and lambda in one sweep
+          __syncthreads();
+          continue;
+        }
         if (op.slot >= 0 && op.kb == OP_REAL) {  // one pass over the pairs
           bt_warp_accumulate(bt_back_real(tP, tL, TS, op, matb + 4 * op.gate), acc, ps.nslots, op.slot);
           __syncthreads();

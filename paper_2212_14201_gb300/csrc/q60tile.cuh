@@ -419,6 +419,22 @@ static __device__ int64_t bt_back_real(longlong2* P, longlong2* Lt, uint32_t TS,
   return acc;
 }
 
+// An antidiagonal op with unit factors (X, CNOT, Y, Toffoli) on psi and lambda in
+// one sweep over the pairs: swaps with sign or i factors, no arithmetic.
+static __device__ void bt_anti_both(longlong2* P, longlong2* Lt, uint32_t TS, const BOp& op, int c0, int c1) {
+  const uint32_t tb = 1u << op.tb;
+  const uint32_t fixed = op.lcm | tb;
+  const uint32_t cnt = TS >> __popc(fixed);
+  for (uint32_t i = threadIdx.x; i < cnt; i += BT_THREADS) {
+    const uint32_t j0 = op.lcm ? bt_expand(i, fixed, op.lcm) : i + (i & ~(tb - 1)), j1 = j0 | tb;
+    const longlong2 p0 = P[j0], p1 = P[j1], l0 = Lt[j0], l1 = Lt[j1];
+    P[j0] = bt_unit(p1, c0);
+    P[j1] = bt_unit(p0, c1);
+    Lt[j0] = bt_unit(l1, c0);
+    Lt[j1] = bt_unit(l0, c1);
+  }
+}
+
 // Adds this thread's partial (Q60 units) to its warp's accumulator of `slot`
 // without a CTA barrier: the warp sums exactly by integer shuffles (the bound of
 // bt_gen_partial holds for the warp's total too), lane 0 converts once and owns
