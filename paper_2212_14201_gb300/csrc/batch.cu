@@ -63,6 +63,7 @@ struct BGroup {
 
 struct BTerm {
   double c;       // coef / S, with the real sign of i^ny
+  int64_t cq;     // the same in Q60 (|c| <= 1)
   uint64_t zm;
   int imag;       // i^ny is imaginary
 };
@@ -311,27 +312,39 @@ __device__ void bt_eval_set(const BatchArgs& d, int set_id, int rank, int nr, lo
   else bt_cluster_sync();
   for (int p = st.pass_begin; p < st.pass_begin + st.npasses; ++p)
     bt_run_pass(d, d.passes[p], psi, lam, matf, matb, false, tP, tL, offs, acc, rank, nr);
-  // 3. lambda = (H/S) psi, energy
+  // 3. lambda = (H/S) psi, energy, in Q60 integers (GB300's FP64 pipe would bound
+  // this loop): per group of terms sharing an X mask the signed coefficient sums
+  // d = sum_t (-1)^popc(x & zm_t) c_t are exact in int64 (sum |c_t| <= 1), the
+  // group's product d * psi_x is rounded once, and lambda_y = sum over groups
+  // (|lambda_y| <= |psi|_inf <= 1.25: every partial fits).
   double e = 0.0;
   for (uint64_t y = t0; y < N; y += ts) {
-    double ore = 0.0, oim = 0.0;
+    int64_t ore = 0, oim = 0;
     for (int gi = st.group_begin; gi < st.group_begin + st.ngroups; ++gi) {
       const BGroup grp = d.groups[gi];
       const uint64_t x = y ^ grp.xm;
-      double dre = 0.0, dim = 0.0;
+      int64_t dre = 0, dim = 0;
       for (int k = grp.tbegin; k < grp.tend; ++k) {
-        const BTerm t = d.terms[k];
-        const double v = (__popcll(x & t.zm) & 1) ? -t.c : t.c;
+        const BTerm& t = d.terms[k];
+        const int64_t v = (__popcll(x & t.zm) & 1) ? -t.cq : t.cq;
         if (t.imag) dim += v;
         else dre += v;
       }
       const double2 pv = psi[x];
-      ore += dre * pv.x - dim * pv.y;
-      oim += dre * pv.y + dim * pv.x;
+      const QL px = q60_split(q60_from_double(pv.x)), py = q60_split(q60_from_double(pv.y));
+      const QL qr = q60_split(dre), qi = q60_split(dim), nqi = q60_split(-dim);
+      QAcc r = qacc_new(), i = qacc_new();
+      qacc_add(r, qr, px);   // re: dre px - dim py
+      qacc_add(r, nqi, py);
+      qacc_add(i, qr, py);   // im: dre py + dim px
+      qacc_add(i, qi, px);
+      ore += qacc_round(r);
+      oim += qacc_round(i);
     }
-    lam[y] = make_double2(ore, oim);
-    const double2 py = psi[y];
-    e += py.x * ore + py.y * oim;
+    const double lr = q60_to_double(ore), li = q60_to_double(oim);
+    lam[y] = make_double2(lr, li);
+    const double2 pyv = psi[y];
+    e += pyv.x * lr + pyv.y * li;
   }
   const double E = bt_block_sum(e, red);
   if (nr == 1) {
@@ -611,6 +624,7 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
         const int ny = __builtin_popcountll(terms[k].xmask & terms[k].zmask) & 3;
         BTerm bt;
         bt.c = (ny >= 2 ? -terms[k].coef : terms[k].coef) / st.S;
+        bt.cq = q60_from_double(bt.c);
         bt.zm = terms[k].zmask;
         bt.imag = ny & 1;
         bterms.push_back(bt);
