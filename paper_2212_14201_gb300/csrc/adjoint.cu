@@ -193,25 +193,43 @@ struct HArgs {
   int gstart[HMAX + 1];
   uint64_t zm[HMAX];
   double c[HMAX];   // coef / S times the real unit of i^ny (+-1) ...
+  int64_t cq[HMAX]; // (the same in Q60)
   int imag[HMAX];   // ... placed in the imaginary part when ny is odd
 };
 
 __global__ void __launch_bounds__(256) k_apply_h(const double2* __restrict__ psi, double2* __restrict__ lam,
                                                  const __grid_constant__ HArgs h) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // Q60 integers (the FP64 pipe would bound this loop on GB300): the signed
+  // coefficient sums of a group are exact in int64 (sum |c_k| <= 1), each group's
+  // product with psi is rounded once, and the launch's total (|.| <= |psi|_inf)
+  // is converted once.
   for (uint64_t y = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; y < h.N; y += stride) {
-    double2 out = h.accumulate ? lam[y] : make_double2(0.0, 0.0);
+    int64_t ore = 0, oim = 0;
     for (int gi = 0; gi < h.ngroups; ++gi) {
       const uint64_t x = y ^ h.gxm[gi];
-      double dre = 0.0, dim = 0.0;
+      int64_t dre = 0, dim = 0;
       for (int k = h.gstart[gi]; k < h.gstart[gi + 1]; ++k) {
-        double v = (__popcll(x & h.zm[k]) & 1) ? -h.c[k] : h.c[k];
+        const int64_t v = (__popcll(x & h.zm[k]) & 1) ? -h.cq[k] : h.cq[k];
         if (h.imag[k]) dim += v;
         else dre += v;
       }
       const double2 p = psi[x];
-      out.x += dre * p.x - dim * p.y;
-      out.y += dre * p.y + dim * p.x;
+      const QL px = q60_split(q60_from_double(p.x)), py = q60_split(q60_from_double(p.y));
+      const QL qr = q60_split(dre), qi = q60_split(dim), nqi = q60_split(-dim);
+      QAcc r = qacc_new(), i = qacc_new();
+      qacc_add(r, qr, px);  // re: dre px - dim py
+      qacc_add(r, nqi, py);
+      qacc_add(i, qr, py);  // im: dre py + dim px
+      qacc_add(i, qi, px);
+      ore += qacc_round(r);
+      oim += qacc_round(i);
+    }
+    double2 out = make_double2(q60_to_double(ore), q60_to_double(oim));
+    if (h.accumulate) {
+      const double2 prev = lam[y];
+      out.x += prev.x;
+      out.y += prev.y;
     }
     lam[y] = out;
   }
@@ -565,6 +583,7 @@ static int apply_hamiltonian(qs_state* s, const double2* psi, double2* lam, cons
         double c = t.coef / S;
         h->zm[h->nterms] = t.zmask;
         h->c[h->nterms] = (ny >= 2) ? -c : c;
+        h->cq[h->nterms] = q60_from_double(h->c[h->nterms]);
         h->imag[h->nterms] = ny & 1;
         ++h->nterms;
       }
