@@ -351,3 +351,31 @@ def test_exact_marginals_match_fp64_and_oracle(q, orc):
     finally:
         q.qs_free(h)
         q.qs_free(h2)
+
+
+def test_sampler_bit_exact_n31(q, orc):
+    """n=31: 2048 superblocks of 1024 blocks, so the prefix of the superblock
+    totals runs in chunks; 20000 shots against the oracle on the same 32 GiB of
+    amplitudes (skipped without room for the host copy)."""
+    import os
+    import torch
+    n = 31
+    need = (16 << n) * 2.2
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 0
+    free_dev, _ = torch.cuda.mem_get_info()
+    if avail < need or free_dev < (16 << n) * 1.1:
+        pytest.skip("not enough host or device memory for a 32 GiB state and its copy")
+    g = w.random_circuit(n, 60, 31)
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc(n)
+    try:
+        q.qs_apply(h, g, None, p)
+        got = q.qs_sample(h, 77, 20000)
+        st = q.qs_get_state(h).view(np.float64)
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(p)
+    assert np.array_equal(got, orc.sample(st, n, 77, 20000))
