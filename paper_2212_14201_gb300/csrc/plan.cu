@@ -889,10 +889,11 @@ extern "C" int qs_set_register_phases(int bits) {
 // staging buffer is rewritten only after that copy has run (the host waits, the
 // stream does not); the device buffer is rewritten in stream order, after the
 // previous pass's kernel.
-static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const QL** dev) {
+static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const QL** dev, bool f32) {
   size_t per = 0;
   for (const PhaseTable& t : pt) per = std::max(per, t.t.size());
-  const size_t bytes = pt.size() * 3 * per * sizeof(QL);
+  // FP32 engine: one float2 per entry (table t at t * 2^m)
+  const size_t bytes = f32 ? pt.size() * per * sizeof(float2) : pt.size() * 3 * per * sizeof(QL);
   if (!s->tables_ev) QS_CUDA(cudaEventCreateWithFlags(&s->tables_ev, cudaEventDisableTiming));
   QS_CUDA(cudaEventSynchronize(s->tables_ev));
   if (s->tables_pinned_bytes < bytes) {
@@ -912,8 +913,14 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
     QS_CUDA(cudaMalloc(&s->tables, bytes));
     s->tables_bytes = bytes;
   }
+  if (f32) {
+    float2* hf = (float2*)s->tables_pinned;
+    for (size_t t = 0; t < pt.size(); ++t)
+      for (size_t j = 0; j < pt[t].t.size(); ++j)
+        hf[t * per + j] = make_float2((float)pt[t].t[j].re, (float)pt[t].t[j].im);
+  }
   QL* host = (QL*)s->tables_pinned;
-  for (size_t t = 0; t < pt.size(); ++t) {
+  for (size_t t = 0; !f32 && t < pt.size(); ++t) {
     QL* re = host + t * 3 * per;
     QL* im = re + per;
     QL* nim = im + per;
@@ -979,7 +986,8 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   int m = 0;
   std::vector<Op1> rops;
   std::vector<PhaseTable> ptables;
-  int rc = build_pass_ops(n, ps, gates, params, fixed && s->prec == 128, &rops, &ptables, local, &m);
+  const bool f32 = s->prec == 64;  // complex64 state: FP32 engine
+  int rc = build_pass_ops(n, ps, gates, params, (fixed && s->prec == 128) || f32, &rops, &ptables, local, &m);
   int L = 0;
   while (L < n && ((Q >> L) & 1)) ++L;
   g->n = n;
@@ -995,7 +1003,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   g->tables = nullptr;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
-  const bool pairs = fixed && s->prec == 128 && g_rotation_pairs && g_register_bits == 0;
+  const bool pairs = ((fixed && s->prec == 128) || f32) && g_rotation_pairs && g_register_bits == 0;
   auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
@@ -1022,13 +1030,17 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       t1.kind = TOP_CONT;
       QL* e0 = reinterpret_cast<QL*>(t0.q);
       QL* e1 = reinterpret_cast<QL*>(t1.q);
+      float* f0 = reinterpret_cast<float*>(t0.f);
+      float* f1 = reinterpret_cast<float*>(t1.f);
       for (int k = 0; k < 4; ++k)
         for (int c = 0; c < 4; ++c) {
           const double v = rb.m[2 * (k >> 1) + (c >> 1)].re * ra.m[2 * (k & 1) + (c & 1)].re;
           const int e = 4 * k + c;
-          (e < 12 ? e0[e] : e1[e - 12]) = q60_split(q60_from_double(v));
+          if (f32) (e < 8 ? f0[e] : f1[e - 8]) = (float)v;
+          else (e < 12 ? e0[e] : e1[e - 12]) = q60_split(q60_from_double(v));
         }
-      int_ops += N * 24.0;  // two real rotations: 12 limb products per amplitude each
+      if (f32) flops += N * 16.0;  // 4 real multiply-adds per output component, 2 components, per 4 amplitudes x 4 outputs
+      else int_ops += N * 24.0;    // two real rotations: 12 limb products per amplitude each
       g->nops += 2;
       ++i;
       continue;
@@ -1040,7 +1052,8 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       to.lcmask = (uint32_t)op.target;
       to.ext_cmask = 0;
       to.code0 = to.code1 = U_GENERAL;
-      int_ops += N * 9.0;  // one complex product (Gauss: 9 limb products) per amplitude
+      if (f32) flops += N * 6.0;  // one complex product per amplitude
+      else int_ops += N * 9.0;    // one complex product (Gauss: 9 limb products) per amplitude
       ++g->nops;
       continue;
     }
@@ -1091,7 +1104,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
                                 (o.code1 >= 0 && (size_t)o.code1 >= ptables.size())))
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed rotation-pair op");
   }
-  if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables);
+  if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, f32);
   g->nphases = 0;
   if (rc == QS_OK && fixed && g_register_bits && m >= g_register_bits) build_phases(g, g_register_bits);
   if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,

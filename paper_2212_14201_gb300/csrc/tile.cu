@@ -125,7 +125,7 @@ struct EngQ60 {
 struct EngF32 {
   using T = float2;
   using G = float2;
-  static constexpr int kMinBlocks = 6;  // 32 KiB tiles: up to seven per SM
+  static constexpr int kMinBlocks = 5;  // 32 KiB tiles; five per SM leave the quad ops unspilled (5/6/7: 460/517/626 ms)
   static __device__ __forceinline__ T load(const float2& a) { return a; }
   static __device__ __forceinline__ float2 store(const T& a) { return a; }
   static __device__ __forceinline__ float2 u(const TileOp& op, int e) { return op.f[e]; }
@@ -232,6 +232,43 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
   }
 }
 
+// The same two ops for the FP32 engine (complex64 states): a real 4x4 on quads with
+// its 16 entries as floats in f[] of the op's two slots, optionally after a phase
+// table of float2 entries (one per amplitude of the tile).
+template <int THREADS>
+__device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const float* m0,
+                                              const float* m1, const float2* tab) {
+  const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
+  const uint32_t cnt = TS >> 2;
+#pragma unroll 2
+  for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
+    uint32_t j = i + (i & ~(lo - 1));
+    j = j + (j & ~(hi - 1));
+    const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
+    float2 v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      v[c] = tile[jj[c]];
+      if (tab) {
+        const float2 u = __ldg(tab + jj[c]);
+        v[c] = make_float2(fmaf(u.x, v[c].x, -u.y * v[c].y), fmaf(u.x, v[c].y, u.y * v[c].x));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float xr = 0.0f, xi = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int e = 4 * k + c;
+        const float u = e < 8 ? m0[e] : m1[e - 8];
+        xr = fmaf(u, v[c].x, xr);
+        xi = fmaf(u, v[c].y, xi);
+      }
+      tile[jj[k]] = make_float2(xr, xi);
+    }
+  }
+}
+
 template <class E, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
@@ -258,6 +295,26 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
       const TileOp& op = g.ops[k];
       if ((base & op.ext_cmask) != op.ext_cmask) continue;  // uniform across the CTA
       const uint32_t lcm = op.lcmask;
+      if constexpr (std::is_same<E, EngF32>::value) {
+        if (op.kind == TOP_DTABLE) {
+          const float2* tf = reinterpret_cast<const float2*>(g.tables) + (size_t)lcm * TS;
+          for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
+            const float2 u = __ldg(tf + j), v = tile[j];
+            tile[j] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
+          }
+          __syncthreads();
+          continue;
+        }
+        if (op.kind == TOP_REAL2) {
+          const float2* tab =
+              op.code1 >= 0 ? reinterpret_cast<const float2*>(g.tables) + (size_t)op.code1 * TS : nullptr;
+          quad_real_f32<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const float*>(op.f),
+                                 reinterpret_cast<const float*>(g.ops[k + 1].f), tab);
+          ++k;  // the continuation slot
+          __syncthreads();
+          continue;
+        }
+      }
       if constexpr (std::is_same<E, EngQ60>::value) {
         if (op.kind == TOP_DTABLE) {
           // one table entry per amplitude, read through the read-only path (every
