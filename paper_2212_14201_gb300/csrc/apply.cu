@@ -172,30 +172,6 @@ struct QV {
 __device__ __forceinline__ QV q_load(const double2& a) { return {q60_from_double(a.x), q60_from_double(a.y)}; }
 __device__ __forceinline__ double2 q_store(QV v) { return make_double2(q60_to_double(v.re), q60_to_double(v.im)); }
 
-// u0*a0 + u1*a1 (complex), a as limbs
-__device__ __forceinline__ QV q_mv2(const QC& u0, QL a0r, QL a0i, const QC& u1, QL a1r, QL a1i) {
-  QAcc re = qacc_new(), im = qacc_new();
-  qacc_add(re, u0.re, a0r);
-  qacc_add(re, u0.nim, a0i);
-  qacc_add(re, u1.re, a1r);
-  qacc_add(re, u1.nim, a1i);
-  qacc_add(im, u0.re, a0i);
-  qacc_add(im, u0.im, a0r);
-  qacc_add(im, u1.re, a1i);
-  qacc_add(im, u1.im, a1r);
-  return {qacc_round(re), qacc_round(im)};
-}
-
-// u*a (complex)
-__device__ __forceinline__ QV q_mul(const QC& u, QL ar, QL ai) {
-  QAcc re = qacc_new(), im = qacc_new();
-  qacc_add(re, u.re, ar);
-  qacc_add(re, u.nim, ai);
-  qacc_add(im, u.re, ai);
-  qacc_add(im, u.im, ar);
-  return {qacc_round(re), qacc_round(im)};
-}
-
 // real 2x2: u0.re*a0 + u1.re*a1
 __device__ __forceinline__ QV q_real2(const QC& u0, QL a0r, QL a0i, const QC& u1, QL a1r, QL a1i) {
   QAcc re = qacc_new(), im = qacc_new();
@@ -206,48 +182,83 @@ __device__ __forceinline__ QV q_real2(const QC& u0, QL a0r, QL a0i, const QC& u1
   return {qacc_round(re), qacc_round(im)};
 }
 
+// u * a with u in Gauss form (three limb products)
 __device__ __forceinline__ double2 fx_mul(double2 a, int code, const QC& u) {
   if (code != U_GENERAL) return mul_unit(a, code);
-  QV v = q_load(a);
-  return q_store(q_mul(u, q60_split(v.re), q60_split(v.im)));
+  const QV v = q_load(a);
+  int64_t re, im;
+  q60_gauss_mul(u, q60_split(v.re), q60_split(v.im), q60_split(v.re + v.im), &re, &im);
+  return q_store(QV{re, im});
 }
 
+// One pair (x0, x0 | tb) of the op: matrices in Gauss form (real entries in u.re).
+template <int CLS>
+__device__ __forceinline__ void fx_pair(const OpArgsFx& g, double2 a0, double2 a1, double2& b0, double2& b1) {
+  if (CLS == OP_DIAG) {
+    b0 = fx_mul(a0, g.code0, g.u[0]);
+    b1 = fx_mul(a1, g.code1, g.u[3]);
+  } else if (CLS == OP_ANTI) {
+    b0 = fx_mul(a1, g.code0, g.u[1]);
+    b1 = fx_mul(a0, g.code1, g.u[2]);
+  } else {
+    const QV v0 = q_load(a0), v1 = q_load(a1);
+    const QL r0 = q60_split(v0.re), i0 = q60_split(v0.im), r1 = q60_split(v1.re), i1 = q60_split(v1.im);
+    if (CLS == OP_REAL) {
+      b0 = q_store(q_real2(g.u[0], r0, i0, g.u[1], r1, i1));
+      b1 = q_store(q_real2(g.u[2], r0, i0, g.u[3], r1, i1));
+    } else {
+      const QL s0 = q60_split(v0.re + v0.im), s1 = q60_split(v1.re + v1.im);
+      int64_t re, im;
+      q60_gauss_row(g.u[0], g.u[1], r0, i0, s0, r1, i1, s1, &re, &im);
+      b0 = q_store(QV{re, im});
+      q60_gauss_row(g.u[2], g.u[3], r0, i0, s0, r1, i1, s1, &re, &im);
+      b1 = q_store(QV{re, im});
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t fx_index(const OpArgsFx& g, uint64_t i, uint64_t tb) {
+  if (g.nfix == 1) return i + (i & ~(tb - 1));  // no controls: one zero bit at the target
+  uint64_t x0 = i;
+  for (int k = 0; k < g.nfix; ++k) {
+    const int f = g.fix[k];
+    x0 = ((x0 >> f) << (f + 1)) | (x0 & ((1ull << f) - 1));
+  }
+  return x0 | g.cmask;
+}
+
+// Two pairs per iteration, both loaded before either is computed (four 16-byte
+// loads in flight per thread: the kernel moves the whole state through HBM).
 template <int CLS>
 __global__ void __launch_bounds__(256) k_op1_fx(double2* __restrict__ a, const OpArgsFx g) {
   const uint64_t tb = 1ull << g.t;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (uint64_t)g.items; i += stride) {
-    uint64_t x0 = i;
-    for (int k = 0; k < g.nfix; ++k) {
-      int f = g.fix[k];
-      x0 = ((x0 >> f) << (f + 1)) | (x0 & ((1ull << f) - 1));
-    }
-    x0 |= g.cmask;
-    const uint64_t x1 = x0 | tb;
-    if (CLS == OP_PHASE1) {
+  const uint64_t items = (uint64_t)g.items;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (CLS == OP_PHASE1) {
+    for (; i < items; i += stride) {
+      const uint64_t x1 = fx_index(g, i, tb) | tb;
       a[x1] = fx_mul(a[x1], g.code1, g.u[3]);
-    } else if (CLS == OP_DIAG) {
-      double2 a0 = a[x0], a1 = a[x1];
-      a[x0] = fx_mul(a0, g.code0, g.u[0]);
-      a[x1] = fx_mul(a1, g.code1, g.u[3]);
-    } else if (CLS == OP_ANTI) {
-      double2 a0 = a[x0], a1 = a[x1];
-      a[x0] = fx_mul(a1, g.code0, g.u[1]);
-      a[x1] = fx_mul(a0, g.code1, g.u[2]);
-    } else {
-      QV v0 = q_load(a[x0]), v1 = q_load(a[x1]);
-      QL r0 = q60_split(v0.re), i0 = q60_split(v0.im), r1 = q60_split(v1.re), i1 = q60_split(v1.im);
-      QV b0, b1;
-      if (CLS == OP_REAL) {
-        b0 = q_real2(g.u[0], r0, i0, g.u[1], r1, i1);
-        b1 = q_real2(g.u[2], r0, i0, g.u[3], r1, i1);
-      } else {
-        b0 = q_mv2(g.u[0], r0, i0, g.u[1], r1, i1);
-        b1 = q_mv2(g.u[2], r0, i0, g.u[3], r1, i1);
-      }
-      a[x0] = q_store(b0);
-      a[x1] = q_store(b1);
     }
+    return;
+  }
+  for (; i + stride < items; i += 2 * stride) {
+    const uint64_t p0 = fx_index(g, i, tb), q0 = fx_index(g, i + stride, tb);
+    const double2 a0 = a[p0], a1 = a[p0 | tb], c0 = a[q0], c1 = a[q0 | tb];
+    double2 b0, b1, d0, d1;
+    fx_pair<CLS>(g, a0, a1, b0, b1);
+    fx_pair<CLS>(g, c0, c1, d0, d1);
+    a[p0] = b0;
+    a[p0 | tb] = b1;
+    a[q0] = d0;
+    a[q0 | tb] = d1;
+  }
+  if (i < items) {
+    const uint64_t p0 = fx_index(g, i, tb);
+    double2 b0, b1;
+    fx_pair<CLS>(g, a[p0], a[p0 | tb], b0, b1);
+    a[p0] = b0;
+    a[p0 | tb] = b1;
   }
 }
 
@@ -301,7 +312,7 @@ int launch_op1(qs_state* s, const Op1& op, bool fixed) {
   if (s->prec == 64) return launch_op1_c64(s, op);
   if (fixed && needs_arith(op)) {
     OpArgsFx g;
-    for (int i = 0; i < 4; ++i) g.u[i] = qc_make(op.m.m[i].re, op.m.m[i].im);
+    for (int i = 0; i < 4; ++i) g.u[i] = qc_make_gauss(op.m.m[i].re, op.m.m[i].im);  // Gauss form
     g.cmask = op.cmask;
     g.t = op.target;
     g.code0 = op.code0;
