@@ -370,9 +370,12 @@ int qs_expect_pauli(const qs_state* s, const qs_pauli* terms, size_t nterms, dou
  * Canonical, bit-reproducible definition: u_s = ((SplitMix64 output number s of
  * the stream seeded `seed`) >> 11) * 2^-53; p_x = re*re + im*im rounded as two
  * products and a sum; blocks of L = min(1024, 2^n) amplitudes summed left to
- * right give the block totals, whose left-to-right prefix gives E_b; the sample
- * is the smallest x with E_b + (left-to-right partial sum of block b up to x)
- * > u_s, or, when no x qualifies, the largest x with p_x > 0.
+ * right give the block totals T_b; superblocks of G = min(1024, blocks) blocks
+ * give F_c(i) = T_cG + ... + T_cG+i (left to right) and P_0 = 0,
+ * P_c+1 = P_c + F_c(G-1); E_0 = 0 and E_cG+i+1 = P_c + F_c(i) (for n <= 20 this
+ * is the left-to-right prefix of the block totals); the sample is the smallest x
+ * with E_b + (left-to-right partial sum of block b up to x) > u_s, or, when no x
+ * qualifies, the largest x with p_x > 0.
  * out[s] (uint64, device or host memory) receives the basis index of shot s. */
 int qs_sample(const qs_state* s, uint64_t seed, uint64_t shots, uint64_t* out, int on_device);
 
