@@ -327,7 +327,11 @@ int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs_mlp* model
 /* Marginal probabilities over qubits[0..nq-1] (0 <= nq <= n; qubits[j] is bit j
  * of the output index): out has 2^nq entries, out[k] = sum of |a_x|^2 over x
  * whose listed bits spell k.  nq = 0 gives the squared norm.  out is device
- * memory if on_device != 0 (asynchronous), else host memory (synchronous). */
+ * memory if on_device != 0 (asynchronous), else host memory (synchronous).
+ * For nq <= 3 on a state known to satisfy the Q60 bound (reached from |0> by
+ * unitary gates), the squares of the Q60-rounded components are summed exactly
+ * in integers: absolute error below 2^-60 * sum_x |a_x| (2^-45 at n = 30);
+ * otherwise FP64 sums in a fixed order.  Results are deterministic either way. */
 int qs_probs(const qs_state* s, const int* qubits, int nq, double* out, int on_device);
 
 /* Entries of the marginal over qubits[0..nq-1] with probability > threshold,
@@ -415,7 +419,8 @@ int qs_set_adjoint_fused(int on);
  * *outcome = 0 if u (p0 + p1) < p0, else 1; the state collapses in place (the
  * other part set to 0, the kept part scaled by 1 / sqrt(p_outcome)).  *p1
  * (nullable) receives p1 / (p0 + p1).  Two passes over the state (reduction,
- * collapse); synchronous.  Errors: INVALID_ARG (qubit, u, zero state), CUDA. */
+ * collapse; a third, FP64 reduction when the smaller branch is below 2^-20);
+ * synchronous.  Errors: INVALID_ARG (qubit, u, zero state), CUDA. */
 int qs_measure(qs_state* s, int qubit, double u, int* outcome, double* p1);
 
 /* One instruction of a structured program (56 bytes).  Blocks nest by length:
