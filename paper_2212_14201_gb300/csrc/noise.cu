@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "fixed.h"
 #include "internal.h"
 
 namespace qs {
@@ -61,6 +62,65 @@ __global__ void __launch_bounds__(256) k_gram(const A* __restrict__ a, uint64_t 
     for (int i = 0; i < 8; ++i) t += sh[threadIdx.x][i];
     part[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
   }
+}
+
+// The same four sums exactly, for a state within the Q60 bound: components rounded
+// once to Q60 and the products summed as 128-bit integers (units of 2^-120; every
+// sum is at most the squared norm <= 1.5625 in magnitude).  Integer pipes instead
+// of GB300's 1/74-rate FP64 pipe.
+using i128 = __int128;
+
+__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int o) {
+  const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
+  const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)((unsigned __int128)v >> 64), o);
+  return (i128)(((unsigned __int128)hi << 64) | lo);
+}
+
+template <class A>
+__global__ void __launch_bounds__(256) k_gram_exact(const A* __restrict__ a, uint64_t pairs, int q,
+                                                     uint64_t* __restrict__ part) {
+  __shared__ uint64_t sh[4][8][2];
+  i128 v[4] = {0, 0, 0, 0};
+  const uint64_t b = 1ull << q;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t x0 = ((i >> q) << (q + 1)) | (i & (b - 1));
+    const double2 a0 = ld_amp(a, x0), a1 = ld_amp(a, x0 | b);
+    const int64_t r0 = q60_from_double(a0.x), i0 = q60_from_double(a0.y);
+    const int64_t r1 = q60_from_double(a1.x), i1 = q60_from_double(a1.y);
+    v[0] += (i128)r0 * r0 + (i128)i0 * i0;
+    v[1] += (i128)r1 * r1 + (i128)i1 * i1;
+    v[2] += (i128)r0 * r1 + (i128)i0 * i1;  // Re(a0 conj(a1))
+    v[3] += (i128)i0 * r1 - (i128)r0 * i1;  // Im(a0 conj(a1))
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += shfl_xor_i128(v[k], o);
+    if (l == 0) {
+      sh[k][w][0] = (uint64_t)v[k];
+      sh[k][w][1] = (uint64_t)((unsigned __int128)v[k] >> 64);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    i128 t = 0;
+    for (int i = 0; i < 8; ++i) t += (i128)(((unsigned __int128)sh[threadIdx.x][i][1] << 64) | sh[threadIdx.x][i][0]);
+    part[((size_t)blockIdx.x * 4 + threadIdx.x) * 2] = (uint64_t)t;
+    part[((size_t)blockIdx.x * 4 + threadIdx.x) * 2 + 1] = (uint64_t)((unsigned __int128)t >> 64);
+  }
+}
+
+__global__ void k_gram_exact_finish(const uint64_t* __restrict__ part, int nblocks, double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= 4) return;
+  i128 t = 0;
+  for (int c = 0; c < nblocks; ++c)
+    t += (i128)(((unsigned __int128)part[((size_t)c * 4 + k) * 2 + 1] << 64) | part[((size_t)c * 4 + k) * 2]);
+  const bool neg = t < 0;
+  const unsigned __int128 m = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+  const double d = (double)(uint64_t)(m >> 64) * 18446744073709551616.0 + (double)(uint64_t)m;
+  out[k] = (neg ? -d : d) * 0x1p-120;
 }
 
 __global__ void k_gram_finish(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
@@ -208,14 +268,27 @@ struct Trajectory {
     double* part = (double*)s->ws;
     double* dres = part + (size_t)nblocks * 4;
     KTimer kt(s, QS_K_REDUCE, 1, 1, 1ull << q, 0, (double)(pairs * 2), 8.0 * (double)pairs);
-    with_amps(s, [&](auto* a) {
-      using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
-      k_gram<<<nblocks, 256, 0, s->stream>>>((const T*)a, pairs, q, part);
-      return QS_OK;
-    });
-    QS_TRY(launch_check("gram"));
-    k_gram_finish<<<1, 32, 0, s->stream>>>(part, nblocks, dres);
-    QS_TRY(launch_check("gram finish"));
+    if (s->bound == 1) {  // components known to lie within the Q60 bound: exact integer sums
+      uint64_t* ipart = (uint64_t*)s->ws;
+      dres = (double*)(ipart + (size_t)nblocks * 8);
+      with_amps(s, [&](auto* a) {
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
+        k_gram_exact<<<nblocks, 256, 0, s->stream>>>((const T*)a, pairs, q, ipart);
+        return QS_OK;
+      });
+      QS_TRY(launch_check("gram"));
+      k_gram_exact_finish<<<1, 32, 0, s->stream>>>(ipart, nblocks, dres);
+      QS_TRY(launch_check("gram finish"));
+    } else {
+      with_amps(s, [&](auto* a) {
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
+        k_gram<<<nblocks, 256, 0, s->stream>>>((const T*)a, pairs, q, part);
+        return QS_OK;
+      });
+      QS_TRY(launch_check("gram"));
+      k_gram_finish<<<1, 32, 0, s->stream>>>(part, nblocks, dres);
+      QS_TRY(launch_check("gram finish"));
+    }
     QS_TRY(ensure_pinned(s, 4 * sizeof(double)));
     QS_CUDA(cudaMemcpyAsync(s->pinned, dres, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     QS_CUDA(cudaStreamSynchronize(s->stream));
@@ -271,8 +344,16 @@ struct Trajectory {
     Mat2 M = ks.K[pick];
     const double sc = 1.0 / sqrt(w[pick]);
     for (int e = 0; e < 4; ++e) M.m[e] = {M.m[e].re * sc, M.m[e].im * sc};
-    // a renormalised Kraus operator is not unitary: FP64 (or FP32) engine
-    return launch_op1(s, classify(q, 0, M), false);
+    // A renormalised Kraus operator is not unitary, but the state it produces is
+    // normalised: the Q60 kernel applies it when every entry has |re| + |im| < 1.9
+    // (its Gauss-form sums then stay below 2, the limb range), e.g. the usual
+    // no-decay operator of amplitude damping; otherwise (the rare jump operators,
+    // scaled by 1 / sqrt(p)) the FP64 kernel.
+    bool fixed = false;
+    QS_TRY(choose_fixed(s, &fixed));
+    for (int e = 0; e < 4 && fixed; ++e)
+      if (fabs(M.m[e].re) + fabs(M.m[e].im) >= 1.9) fixed = false;
+    return launch_op1(s, classify(q, 0, M), fixed);
   }
 };
 
