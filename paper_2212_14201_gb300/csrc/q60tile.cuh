@@ -103,7 +103,8 @@ __device__ __forceinline__ int64_t bt_pair_gen(int gen, QL l0x, QL l0y, QL l1x, 
 }
 
 // Real pair forward: the quads of the tile through M.
-static __device__ void bt_rpair(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* __restrict__ M) {
+static __device__ __noinline__ void bt_rpair(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb,
+                                             const QL* __restrict__ M) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   for (uint32_t i = threadIdx.x; i < (TS >> 2); i += BT_THREADS) {
     uint32_t j = i + (i & ~(lo - 1));
@@ -123,8 +124,9 @@ static __device__ void bt_rpair(longlong2* tile, uint32_t TS, uint32_t ta, uint3
 
 // Real pair backward: both members' generator terms (member a on the pairs
 // (0,1), (2,3) of the quad, member b on (0,2), (1,3)), then M on both tiles.
-static __device__ void bt_rpair_back(longlong2* P, longlong2* Lt, uint32_t TS, uint32_t ta, uint32_t tbb, int gen_a,
-                                     int gen_b, const QL* __restrict__ M, int64_t* out_a, int64_t* out_b) {
+static __device__ __noinline__ void bt_rpair_back(longlong2* P, longlong2* Lt, uint32_t TS, uint32_t ta,
+                                                  uint32_t tbb, int gen_a, int gen_b, const QL* __restrict__ M,
+                                                  int64_t* out_a, int64_t* out_b) {
   int64_t sa = 0, sb = 0;
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   for (uint32_t i = threadIdx.x; i < (TS >> 2); i += BT_THREADS) {
