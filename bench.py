@@ -349,6 +349,53 @@ def bench_measure(q, torch, stream, hbm_peak: float):
     return out
 
 
+def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3):
+    """Rows A6-A8 at n=30 (16 GiB) on the config-1 output state: squared norm,
+    one-qubit marginal, <Z_i> for all 30 qubits, a TFIM Pauli sum (29 ZZ + 30 X
+    terms, h = 0.7) and 10^6 samples, each timed with CUDA events on the state's
+    stream.  Algorithmic bytes: 16 B per amplitude read for the norm, marginal and
+    <Z_i>; for the Pauli sum 16 B per amplitude per distinct X mask (31 reads:
+    the Z-only group and one gather per X term)."""
+    n = 30
+    g = w.layered_u3_cz(n, 20, 1)
+    terms = w.tfim(n, 0.7)
+    h = q.qs_alloc(n, stream)
+    N = float(1 << n)
+    out = {"n": n}
+    try:
+        p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+        q.qs_apply(h, g, None, p)
+        q.qs_plan_free(p)
+        dev = torch.empty(64, dtype=torch.float64, device="cuda")
+        samples = torch.empty(1_000_000, dtype=torch.int64, device="cuda")
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        cases = {
+            "norm": (lambda: q.qs_probs(h, [], dev), 16 * N),
+            "marginal_1q": (lambda: q.qs_probs(h, [17], dev), 16 * N),
+            "expect_z_all": (lambda: q.qs_expect_z_all(h), 16 * N),
+            "expect_pauli_tfim": (lambda: q.qs_expect_pauli(h, terms), 16 * N * 31),
+            "sample_1e6": (lambda: q.qs_sample(h, 11, 1_000_000, samples), 16 * N),
+        }
+        for name, (fn, nbytes) in cases.items():
+            ms = timed(fn)
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            out[name] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / hbm_peak}
+    finally:
+        q.qs_free(h)
+    return out
+
+
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz.
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 
@@ -597,6 +644,7 @@ def run_ours(args, world, rank, local, pg):
         extra["batched_vqe"] = bench_batched_vqe(q, torch, 3, 3)
         extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2)
         extra["measure_n30"] = bench_measure(q, torch, stream, hbm_peak)
+        extra["reductions_n30"] = bench_reductions(q, torch, stream, hbm_peak)
         extra["c64_n30"] = bench_c64(q, torch, stream, hbm_peak)
         extra["noisy_n28"] = bench_noisy(q, torch, stream)
         extra["partial_n40"] = bench_partial(q, torch)
@@ -643,6 +691,7 @@ def run_ours(args, world, rank, local, pg):
         "adjoint_n28": extra.get("adjoint_n28"),
         "learned_n32": extra.get("learned_n32"),
         "measure_n30": extra.get("measure_n30"),
+        "reductions_n30": extra.get("reductions_n30"),
         "c64_n30": extra.get("c64_n30"),
         "noisy_n28": extra.get("noisy_n28"),
         "partial_n40": extra.get("partial_n40"),

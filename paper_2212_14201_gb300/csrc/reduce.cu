@@ -7,7 +7,9 @@
 // warp-shuffle tree, CTA partials go to the workspace in CTA order and one
 // final CTA adds them in that order.  Results do not depend on timing.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -296,6 +298,87 @@ __global__ void __launch_bounds__(256) k_expect_z(const A* __restrict__ a, int r
   }
 }
 
+// The same sums exactly, for a state within the Q60 bound and r - 8 <= ZEXJ loop
+// bits: squares of the Q60-rounded components as 128-bit integers (units 2^-120).
+// A thread folds its amplitudes in fours (loop bits 0 and 1 inside the four), so
+// the other loop bits take one 128-bit add per four amplitudes.  Outputs per CTA
+// as in k_expect_z, each value as two words (low, high).
+constexpr int ZEXJ = 12;
+template <class A>
+__global__ void __launch_bounds__(256) k_expect_z_exact(const A* __restrict__ a, int r, uint64_t* __restrict__ part) {
+  __shared__ uint64_t sh[8][2];
+  const int jbits = r - 8;
+  const uint64_t base = (uint64_t)blockIdx.x << r;
+  u128 tot = 0;
+  u128 bs[ZEXJ];
+#pragma unroll
+  for (int b = 0; b < ZEXJ; ++b) bs[b] = 0;
+  const uint64_t J = 1ull << jbits;
+  for (uint64_t j = 0; j < J; j += 4) {
+    const u128 p0 = sq120(ld_amp(a, base + threadIdx.x + (j << 8)));
+    const u128 p1 = sq120(ld_amp(a, base + threadIdx.x + ((j + 1) << 8)));
+    const u128 p2 = sq120(ld_amp(a, base + threadIdx.x + ((j + 2) << 8)));
+    const u128 p3 = sq120(ld_amp(a, base + threadIdx.x + ((j + 3) << 8)));
+    const u128 t4 = (p0 + p1) + (p2 + p3);
+    tot += t4;
+    bs[0] += p1 + p3;
+    bs[1] += p2 + p3;
+#pragma unroll
+    for (int b = 2; b < ZEXJ; ++b)
+      if (b < jbits && ((j >> b) & 1)) bs[b] += t4;
+  }
+  auto block_sum = [&](u128 v) {  // fixed shuffle tree, then warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+      sh[w][0] = (uint64_t)v;
+      sh[w][1] = (uint64_t)(v >> 64);
+    }
+    __syncthreads();
+    u128 t = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += ((u128)sh[i][1] << 64) | sh[i][0];
+    return t;
+  };
+  uint64_t* o = part + (size_t)blockIdx.x * (r + 1) * 2;
+  auto put = [&](int k, u128 v) {
+    if (threadIdx.x == 0) {
+      o[2 * k] = (uint64_t)v;
+      o[2 * k + 1] = (uint64_t)(v >> 64);
+    }
+  };
+  put(0, block_sum(tot));
+  for (int i = 0; i < 8; ++i) put(1 + i, block_sum(((threadIdx.x >> i) & 1) ? tot : (u128)0));
+  for (int b = 0; b < jbits; ++b) {
+    u128 v = 0;
+#pragma unroll
+    for (int bb = 0; bb < ZEXJ; ++bb)
+      if (bb == b) v = bs[bb];
+    put(1 + 8 + b, block_sum(v));
+  }
+}
+
+// out[i] = T - 2 S_i from the exact CTA partials (bits >= r: CTA index bits).
+__global__ void k_expect_z_exact_finish(const uint64_t* __restrict__ part, int nblocks, int r, int n,
+                                        double* __restrict__ out) {
+  const int i = threadIdx.x;
+  if (i >= n) return;
+  u128 T = 0, S = 0;
+  for (int c = 0; c < nblocks; ++c) {
+    const uint64_t* o = part + (size_t)c * (r + 1) * 2;
+    const u128 t = ((u128)o[1] << 64) | o[0];
+    T += t;
+    if (i < r) S += ((u128)o[2 * (1 + i) + 1] << 64) | o[2 * (1 + i)];
+    else if ((c >> (i - r)) & 1) S += t;
+  }
+  const bool neg = T < 2 * S;  // T - 2S may be negative
+  const u128 m = neg ? 2 * S - T : T - 2 * S;
+  const double d = (double)(uint64_t)(m >> 64) * 18446744073709551616.0 + (double)(uint64_t)m;
+  out[i] = (neg ? -d : d) * 0x1p-120;
+}
+
 __global__ void k_expect_z_finish(const double* __restrict__ part, int nblocks, int r, int n, double* __restrict__ out) {
   // out[i] = T - 2 S_i; thread i handles qubit i; CTA partials added in CTA order.
   int i = threadIdx.x;
@@ -354,6 +437,151 @@ __global__ void k_pauli_finish(const double* __restrict__ part, int nblocks, int
   double s = 0.0;
   for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * 8 + k];
   out[k] = s;
+}
+
+// ---- Pauli sums, exact integer form ---------------------------------------------------
+// For a state within the Q60 bound (norm <= 1.25) every term is computed from the
+// Q60-rounded amplitudes with exact 128-bit integer sums (units 2^-120).  A term
+// P = (xm, zm) with ny = popcount(xm & zm) pairs x0 with x1 = x0 ^ xm; with
+// w = conj(a_x1) a_x0 and s0 = (-1)^popcount(x0 & zm) the pair contributes
+//   ny = 0: 2 s0 Re w,  1: -2 s0 Im w,  2: -2 s0 Re w,  3: 2 s0 Im w,
+// and a term with xm = 0 contributes s0 |a_x0|^2 per index.
+//
+// One pass reads the state once, as cells {base ^ span(m1, m2)} of 2^NB amplitudes
+// (NB <= 2; m1, m2 two X masks with distinct leading bits, which the cell base
+// has clear), and serves every slot whose X mask lies in the span plus any
+// xm = 0 slots.  A slot (xm, zm, part) accumulates pos = the sum of its values v
+// (Re w, Im w or |a|^2) over pairs with s0 = +1; the term is then
+// mult * (2 pos - tot), tot = the same sum with zm = 0 (its own slot).
+constexpr int PS_MAX = 12;  // slots per pass
+struct PPass {
+  uint64_t ncells;       // 2^(n - NB)
+  uint64_t m1, m2;       // cell basis (first NB used)
+  int lo, hi;            // leading-bit positions of the basis, ascending (NB = 2), lo only (NB = 1)
+  int nt;                // slots in this pass
+  int nz;                // the first nz slots are |a|^2 slots
+  uint64_t zm[PS_MAX];
+  uint8_t xc[PS_MAX];     // pair slots: X mask = (xc & 1 ? m1 : 0) ^ (xc & 2 ? m2 : 0)
+  uint8_t im[PS_MAX];     // pair slots: 0 = Re w, 1 = Im w
+  uint8_t smask[PS_MAX];  // bit s = parity(off_s & zm), off_s = (s & 1 ? m1 : 0) ^ (s & 2 ? m2 : 0)
+};
+
+// v = h 2^31 + l with |l| <= 2^30; for |v| < 2^61 also |h| <= 2^30.
+struct Sp {
+  int32_t h, l;
+};
+__device__ __forceinline__ Sp split31(int64_t v) {
+  const int64_t h = (v + (1ll << 30)) >> 31;
+  return {(int32_t)h, (int32_t)(v - h * (1ll << 31))};
+}
+__device__ __forceinline__ Sp sp_neg(Sp v) { return {-v.h, -v.l}; }
+
+// x1 y1 + x2 y2 exactly, as a two's-complement 128-bit value: the three column
+// sums are each below 2^63 in magnitude for split inputs of |v| < 2^61.
+__device__ __forceinline__ u128 dot2(Sp x1, Sp y1, Sp x2, Sp y2) {
+  const int64_t A = (int64_t)x1.h * y1.h + (int64_t)x2.h * y2.h;
+  const int64_t B = (int64_t)x1.h * y1.l + (int64_t)x1.l * y1.h + (int64_t)x2.h * y2.l + (int64_t)x2.l * y2.h;
+  const int64_t C = (int64_t)x1.l * y1.l + (int64_t)x2.l * y2.l;
+  return ((u128)A << 62) + ((u128)B << 31) + (u128)C;
+}
+
+__device__ __forceinline__ uint64_t insert0(uint64_t c, int b) {
+  return ((c >> b) << (b + 1)) | (c & ((1ull << b) - 1));
+}
+
+template <class A, int NB>
+__global__ void __launch_bounds__(256, 2) k_pauli_exact(const A* __restrict__ a, const PPass g,
+                                                        uint64_t* __restrict__ part) {
+  constexpr int S = 1 << NB;
+  __shared__ uint64_t sh[8][PS_MAX][2];
+  u128 pos[PS_MAX];
+#pragma unroll
+  for (int k = 0; k < PS_MAX; ++k) pos[k] = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < g.ncells; c += stride) {
+    uint64_t base = c;
+    if (NB >= 1) base = insert0(base, g.lo);
+    if (NB >= 2) base = insert0(base, g.hi);
+    double2 v[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) v[s] = ld_amp(a, base ^ ((s & 1) ? g.m1 : 0) ^ ((s & 2) ? g.m2 : 0));
+    Sp r[S], i[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      r[s] = split31(q60_from_double(v[s].x));
+      i[s] = split31(q60_from_double(v[s].y));
+    }
+    u128 p[S];
+    if (g.nz > 0) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) p[s] = dot2(r[s], r[s], i[s], i[s]);
+    }
+    u128 w[S / 2 > 0 ? S / 2 : 1];
+    int key = -1;
+#pragma unroll
+    for (int k = 0; k < PS_MAX; ++k) {
+      if (k < g.nt) {
+        const int pb = __popcll(base & g.zm[k]) & 1;
+        const int sm = g.smask[k];
+        if (k < g.nz) {
+#pragma unroll
+          for (int s = 0; s < S; ++s)
+            if ((((sm >> s) & 1) ^ pb) == 0) pos[k] += p[s];
+        } else {
+          const int xc = g.xc[k], part_im = g.im[k];
+#pragma unroll
+          for (int xcc = 1; xcc < S; ++xcc) {
+            if (xc == xcc) {
+              if (xc * 2 + part_im != key) {
+                key = xc * 2 + part_im;
+#pragma unroll
+                for (int j = 0; j < S / 2; ++j) {
+                  const int s0 = xcc == 1 ? 2 * j : j, s1 = s0 ^ xcc;
+                  w[j] = part_im ? dot2(r[s1], i[s0], sp_neg(i[s1]), r[s0]) : dot2(r[s1], r[s0], i[s1], i[s0]);
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < S / 2; ++j) {
+                const int s0 = xcc == 1 ? 2 * j : j;
+                if ((((sm >> s0) & 1) ^ pb) == 0) pos[k] += w[j];
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < PS_MAX; ++k) {
+    if (k < g.nt) {
+      u128 t = pos[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += shfl_xor_u128(t, o);
+      if (l == 0) {
+        sh[wp][k][0] = (uint64_t)t;
+        sh[wp][k][1] = (uint64_t)(t >> 64);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < g.nt) {
+    u128 t = 0;
+    for (int q = 0; q < 8; ++q) t += ((u128)sh[q][threadIdx.x][1] << 64) | sh[q][threadIdx.x][0];
+    part[((size_t)blockIdx.x * PS_MAX + threadIdx.x) * 2] = (uint64_t)t;
+    part[((size_t)blockIdx.x * PS_MAX + threadIdx.x) * 2 + 1] = (uint64_t)(t >> 64);
+  }
+}
+
+// sums[slot0 + k] = the CTA partials of slot k added (modulo 2^128)
+__global__ void k_pauli_exact_finish(const uint64_t* __restrict__ part, int nblocks, int nt, uint64_t* __restrict__ sums) {
+  const int k = threadIdx.x;
+  if (k >= nt) return;
+  u128 t = 0;
+  for (int b = 0; b < nblocks; ++b)
+    t += ((u128)part[((size_t)b * PS_MAX + k) * 2 + 1] << 64) | part[((size_t)b * PS_MAX + k) * 2];
+  sums[2 * k] = (uint64_t)t;
+  sums[2 * k + 1] = (uint64_t)(t >> 64);
 }
 
 }  // namespace qs
@@ -555,6 +783,16 @@ extern "C" int qs_probs_dict(const qs_state* cs, const int* qubits, int nq, doub
   return QS_OK;
 }
 
+// Whether the state is within the Q60 bound (norm <= 1.25), measuring the norm
+// once when that is unknown (after qs_set_state or a non-unitary matrix).
+static int ensure_bound(qs_state* s) {
+  if (s->bound != 0) return QS_OK;
+  double norm2 = 0.0;
+  QS_TRY(qs_probs(s, nullptr, 0, &norm2, 0));
+  s->bound = (norm2 <= Q60_MAX_ABS * Q60_MAX_ABS) ? 1 : 2;
+  return QS_OK;
+}
+
 extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
   clear_error();
   qs_state* s = const_cast<qs_state*>(cs);
@@ -573,11 +811,27 @@ extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
     }
     return QS_OK;
   }
+  QS_TRY(ensure_bound(s));
+  KTimer kt(s, QS_K_REDUCE, n, 1, 0, 0, (double)(1ull << n), 5.0 * (double)(1ull << n));
+  if (s->bound == 1 && n >= 10 && n <= 20 + ZEXJ - 2) {  // exact integer sums (k_expect_z_exact)
+    // r bits per CTA: 2 <= r - 8 <= ZEXJ loop bits, at most 1024 CTAs
+    const int r = std::max(10, n - 10);
+    const int nblocks = 1 << (n - r);
+    uint64_t* ipart = (uint64_t*)s->ws;
+    note_launch(1);
+    with_amps(s, [&](auto* a) {
+      k_expect_z_exact<<<nblocks, 256, 0, s->stream>>>(a, r, ipart);
+      return QS_OK;
+    });
+    QS_TRY(launch_check("expect_z"));
+    k_expect_z_exact_finish<<<1, 64, 0, s->stream>>>(ipart, nblocks, r, n, dres);
+    QS_TRY(launch_check("expect_z_finish"));
+    return read_back(s, dres, n, out);
+  }
   // r = bits per CTA: at least 8 (one element per thread), at most 8 + ZMAXJ; CTAs <= 1024
   int r = std::max(8, n - 10);
   r = std::min(r, std::min(n, 8 + ZMAXJ));
   int nblocks = 1 << (n - r);
-  KTimer kt(s, QS_K_REDUCE, n, 1, 0, 0, (double)(1ull << n), 5.0 * (double)(1ull << n));
   with_amps(s, [&](auto* a) {
     k_expect_z<<<nblocks, 256, 0, s->stream>>>(a, r, part);
     return QS_OK;
@@ -588,6 +842,183 @@ extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
   return read_back(s, dres, n, out);
 }
 
+static int lead_bit(uint64_t m) { return 63 - __builtin_clzll(m); }
+
+// <sum_k coef_k P_k> with the exact passes of k_pauli_exact.  Slots are keyed by
+// (xm, zm, part); X masks are taken two at a time as a cell basis, every other
+// X mask in their span joins that pass, and |a|^2 slots fill the free places
+// (then passes of their own over cells of bits 0 and 1).
+static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double* out) {
+  const int n = s->n;
+  const size_t kChunk = 16384;  // terms per plan: at most 2 slots each
+  double e = 0.0;
+  std::vector<double> vals;
+  for (size_t t0 = 0; t0 < nterms; t0 += kChunk) {
+    const size_t nt = std::min(kChunk, nterms - t0);
+    struct Slot {
+      uint64_t xm, zm;
+      int im;
+    };
+    std::vector<Slot> slots;
+    std::map<std::tuple<uint64_t, uint64_t, int>, int> slot_of;
+    auto get = [&](uint64_t xm, uint64_t zm, int im) {
+      auto key = std::make_tuple(xm, zm, im);
+      auto it = slot_of.find(key);
+      if (it != slot_of.end()) return it->second;
+      slots.push_back({xm, zm, im});
+      return slot_of[key] = (int)slots.size() - 1;
+    };
+    std::vector<int> tslot(nt), ttot(nt), tmult(nt);
+    std::vector<uint64_t> xms;  // distinct X masks, first appearance order
+    for (size_t k = 0; k < nt; ++k) {
+      const uint64_t xm = terms[t0 + k].xmask, zm = terms[t0 + k].zmask;
+      const int ny = __builtin_popcountll(xm & zm) & 3;
+      if (xm == 0) {
+        tslot[k] = get(0, zm, 0);
+        ttot[k] = get(0, 0, 0);
+        tmult[k] = 1;
+      } else {
+        const int im = ny & 1;
+        if (!slot_of.count(std::make_tuple(xm, 0ull, 0)) && !slot_of.count(std::make_tuple(xm, 0ull, 1)))
+          xms.push_back(xm);
+        tslot[k] = get(xm, zm, im);
+        ttot[k] = get(xm, 0, im);
+        tmult[k] = (ny == 0 || ny == 3) ? 2 : -2;
+      }
+    }
+    // passes: basis, then the slot list (|a|^2 slots first, pair slots by (xc, im))
+    struct Pass {
+      int nb;
+      uint64_t m1, m2;
+      std::vector<int> sl;
+    };
+    std::vector<Pass> passes;
+    std::vector<char> done(xms.size(), 0);
+    std::map<uint64_t, std::vector<int>> by_xm;  // pair slots per X mask
+    for (int k = 0; k < (int)slots.size(); ++k)
+      if (slots[k].xm) by_xm[slots[k].xm].push_back(k);
+    for (size_t i = 0; i < xms.size(); ++i) {
+      if (done[i]) continue;
+      done[i] = 1;
+      Pass P{1, xms[i], 0, {}};
+      size_t j = i + 1;
+      while (j < xms.size() && done[j]) ++j;
+      if (j < xms.size()) {
+        done[j] = 1;
+        P.nb = 2;
+        P.m2 = xms[j];
+        if (lead_bit(P.m2) == lead_bit(P.m1)) P.m2 ^= P.m1;
+      }
+      std::vector<uint64_t> span = {P.m1};
+      if (P.nb == 2) {
+        span.push_back(P.m2);
+        span.push_back(P.m1 ^ P.m2);
+      }
+      for (size_t q = i + 1; q < xms.size(); ++q)  // every other X mask in the span
+        if (!done[q] && std::find(span.begin(), span.end(), xms[q]) != span.end()) done[q] = 1;
+      std::vector<std::pair<int, int>> keyed;  // (xc * 2 + im, slot)
+      for (size_t c = 0; c < span.size(); ++c) {
+        auto it = by_xm.find(span[c]);
+        if (it == by_xm.end()) continue;
+        for (int k : it->second) keyed.push_back({(int)(c + 1) * 2 + slots[k].im, k});
+        by_xm.erase(it);
+      }
+      std::stable_sort(keyed.begin(), keyed.end(),
+                       [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+      for (size_t c = 0; c < keyed.size(); c += PS_MAX) {
+        Pass Q = P;
+        for (size_t q = c; q < std::min(keyed.size(), c + PS_MAX); ++q) Q.sl.push_back(keyed[q].second);
+        passes.push_back(Q);
+      }
+      if (keyed.empty()) passes.push_back(P);
+    }
+    // |a|^2 slots: into free places, then passes over cells of bits 0 (and 1)
+    std::vector<int> zs;
+    for (int k = 0; k < (int)slots.size(); ++k)
+      if (!slots[k].xm) zs.push_back(k);
+    size_t zi = 0;
+    for (auto& P : passes)
+      while (zi < zs.size() && (int)P.sl.size() < PS_MAX) P.sl.insert(P.sl.begin(), zs[zi++]);
+    while (zi < zs.size()) {
+      Pass P{n >= 2 ? 2 : 1, 1, n >= 2 ? 2ull : 0ull, {}};
+      while (zi < zs.size() && (int)P.sl.size() < PS_MAX) P.sl.push_back(zs[zi++]);
+      passes.push_back(P);
+    }
+    // launch
+    const size_t nslots = slots.size();
+    std::vector<int> gidx(nslots, -1);
+    uint64_t* part = (uint64_t*)s->ws;
+    const size_t part_words = (size_t)1216 * PS_MAX * 2;
+    uint64_t* sums = part + part_words;
+    if ((part_words + 2 * nslots) * sizeof(uint64_t) > s->ws_bytes)
+      return fail(QS_ERR_UNSUPPORTED, "Pauli slot sums exceed the workspace");
+    int next = 0;
+    for (const auto& P : passes) {
+      if (P.sl.empty()) continue;
+      PPass g{};
+      g.ncells = 1ull << (n - P.nb);
+      g.m1 = P.m1;
+      g.m2 = P.nb == 2 ? P.m2 : 0;
+      if (P.nb == 2) {
+        g.lo = std::min(lead_bit(P.m1), lead_bit(P.m2));
+        g.hi = std::max(lead_bit(P.m1), lead_bit(P.m2));
+      } else {
+        g.lo = lead_bit(P.m1);
+        g.hi = -1;
+      }
+      g.nt = (int)P.sl.size();
+      g.nz = 0;
+      for (int q = 0; q < g.nt; ++q) {
+        const Slot& sl = slots[P.sl[q]];
+        gidx[P.sl[q]] = next + q;
+        g.zm[q] = sl.zm;
+        g.im[q] = (uint8_t)sl.im;
+        if (!sl.xm) {
+          ++g.nz;
+          g.xc[q] = 0;
+        } else {
+          g.xc[q] = sl.xm == P.m1 ? 1 : (sl.xm == g.m2 ? 2 : 3);
+        }
+        uint8_t sm = 0;
+        for (int t = 0; t < (1 << P.nb); ++t) {
+          const uint64_t off = ((t & 1) ? g.m1 : 0) ^ ((t & 2) ? g.m2 : 0);
+          sm |= (uint8_t)((__builtin_popcountll(off & sl.zm) & 1) << t);
+        }
+        g.smask[q] = sm;
+      }
+      const int nblocks = (int)std::min<uint64_t>(1216, std::max<uint64_t>(1, g.ncells / 256));
+      KTimer kt(s, QS_K_REDUCE, n, g.nt, 0, 0, (double)(1ull << n), 8.0 * g.nt * (double)(1ull << n));
+      note_launch(2);
+      with_amps(s, [&](auto* a) {
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
+        const T* ca = a;
+        switch (P.nb) {
+          case 1: k_pauli_exact<T, 1><<<nblocks, 256, 0, s->stream>>>(ca, g, part); break;
+          default: k_pauli_exact<T, 2><<<nblocks, 256, 0, s->stream>>>(ca, g, part); break;
+        }
+        return QS_OK;
+      });
+      QS_TRY(launch_check("pauli_exact"));
+      k_pauli_exact_finish<<<1, 32, 0, s->stream>>>(part, nblocks, g.nt, sums + 2 * (size_t)next);
+      QS_TRY(launch_check("pauli_exact_finish"));
+      next += g.nt;
+    }
+    std::vector<uint64_t> hs(2 * nslots);
+    if (nslots) QS_TRY(read_back(s, (const double*)sums, 2 * nslots, (double*)hs.data()));
+    auto sum_of = [&](int k) {
+      const int g2 = gidx[k];
+      return ((unsigned __int128)hs[2 * g2 + 1] << 64) | hs[2 * g2];
+    };
+    for (size_t k = 0; k < nt; ++k) {
+      const __int128 d = (__int128)(2 * sum_of(tslot[k]) - sum_of(ttot[k]));
+      const double v = (double)tmult[k] * ((double)d * 0x1p-120);
+      e += terms[t0 + k].coef * v;
+    }
+  }
+  *out = e;
+  return QS_OK;
+}
+
 extern "C" int qs_expect_pauli(const qs_state* cs, const qs_pauli* terms, size_t nterms, double* out) {
   clear_error();
   qs_state* s = const_cast<qs_state*>(cs);
@@ -596,6 +1027,8 @@ extern "C" int qs_expect_pauli(const qs_state* cs, const qs_pauli* terms, size_t
   const uint64_t full = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
   for (size_t k = 0; k < nterms; ++k)
     if ((terms[k].xmask | terms[k].zmask) & ~full) return fail(QS_ERR_INVALID_ARG, "term %zu exceeds n", k);
+  QS_TRY(ensure_bound(s));
+  if (s->bound == 1) return pauli_exact(s, terms, nterms, out);
   const uint64_t N = 1ull << s->n;
   const int nblocks = (int)std::min<uint64_t>(608, std::max<uint64_t>(1, N / 256));
   double* part = (double*)s->ws;

@@ -185,7 +185,7 @@ def test_cfg0_probs_and_expect_z(q, orc, cfg0):
         q.qs_free(h)
 
 
-@pytest.mark.parametrize("n", [3, 7, 8, 9, 13, 17, 21])
+@pytest.mark.parametrize("n", [3, 7, 8, 9, 10, 11, 13, 17, 21, 24])
 def test_expect_z_sizes(q, orc, n):
     psi = w.random_state_fast(n, n)
     h = q.qs_alloc(n)
@@ -236,6 +236,62 @@ def test_pauli_expectations(q, orc, n, nt, seed):
         assert abs(q.qs_expect_pauli(h, terms) - orc.expect_pauli(psi, n, terms)) < TOL
         tf = w.tfim(n, 0.7)
         assert abs(q.qs_expect_pauli(h, tf) - orc.expect_pauli(psi, n, tf)) < TOL
+    finally:
+        q.qs_free(h)
+
+
+def _pauli_structure_terms(n):
+    """Terms that exercise every pass layout: the identity, Z strings beyond one
+    pass, one X mask shared by more terms than a pass holds, X masks with equal
+    leading bits and their sum, and Y counts of every residue mod 4."""
+    rows = [(0.3, 0, 0)]
+    rows += [(0.01 * (k + 1), 0, (k * 37 + 5) % (1 << n)) for k in range(15)]
+    shared = 0b101001 & ((1 << n) - 1)
+    rows += [(0.02 * (k - 9), shared, (k * 11) % (1 << n)) for k in range(17)]
+    full = (1 << n) - 1
+    a, b = ((1 << (n - 1)) | 0b110) & full, ((1 << (n - 1)) | 0b011) & full
+    rows += [(0.4, a, 0), (-0.25, b, 1 << (n - 1)), (0.15, a ^ b, 0b101 & full)]
+    for ny in range(4):  # Y on qubits 0..ny-1, X on the top two
+        ys = ((1 << ny) - 1) & full
+        rows.append((0.1 * (ny + 1), ys | (0b11 << (n - 2)), ys))
+    rows.append((-0.2, full, full))  # Y on every qubit
+    rows.append((0.05, full, 0))     # X on every qubit
+    return np.array(rows, dtype=w.PAULI_DTYPE)
+
+
+@pytest.mark.parametrize("n", [2, 9, 14])
+def test_pauli_pass_layouts(q, orc, n):
+    psi = w.random_state_fast(n, 40 + n)
+    psi /= np.linalg.norm(psi)
+    terms = _pauli_structure_terms(n)
+    h = q.qs_alloc(n)
+    try:
+        q.qs_set_state(h, psi.view(np.complex128))
+        assert abs(q.qs_expect_pauli(h, terms) - orc.expect_pauli(psi, n, terms)) < TOL
+        for t in terms:  # each term on its own
+            one = np.array([t], dtype=w.PAULI_DTYPE)
+            assert abs(q.qs_expect_pauli(h, one) - orc.expect_pauli(psi, n, one)) < TOL
+    finally:
+        q.qs_free(h)
+
+
+def test_pauli_large_state_and_fp64_fallback(q, orc):
+    """n=22 (several CTAs per pass, every cell basis) and a state of norm^2 = 2,
+    outside the fixed-point bound, which takes the FP64 kernel."""
+    n = 22
+    psi = w.random_state_fast(n, 9)
+    psi /= np.linalg.norm(psi)
+    terms = np.concatenate([w.tfim(n, 0.7), w.random_paulis(n, 25, 3)])
+    h = q.qs_alloc(n)
+    try:
+        q.qs_set_state(h, psi.view(np.complex128))
+        want = orc.expect_pauli(psi, n, terms)
+        got = q.qs_expect_pauli(h, terms)
+        assert abs(got - want) < TOL
+        assert q.qs_expect_pauli(h, terms) == got  # integer sums: identical on every call
+        big = psi * np.sqrt(2.0)
+        q.qs_set_state(h, big.view(np.complex128))
+        assert abs(q.qs_expect_pauli(h, terms) - 2.0 * want) < 4 * TOL
     finally:
         q.qs_free(h)
 
