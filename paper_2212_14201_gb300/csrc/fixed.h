@@ -76,6 +76,43 @@ QS_HD int64_t q60_from_double(double v) {
   return (b >> 63) ? -(int64_t)mag : (int64_t)mag;
 }
 
+// The same value as q60_from_double without branches, for kernels that decode
+// many amplitudes per thread: with X = mant * 2^10 (< 2^63) and k = 1025 - e,
+// V = (X + 2^(k-1)) >> k for k < 64 (X exactly for k = 0) and 0 for k >= 64
+// (zero, subnormal or below 2^-62).  |v| must be < 8 (e <= 1025).
+QS_HD int64_t q60_from_double_nb(double v) {
+  const uint64_t b = q_bits(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const uint64_t X = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+  const int k = 1025 - e;
+  const int kk = k < 0 ? 0 : (k > 63 ? 63 : k);
+  uint64_t mag = (X + ((1ull << kk) >> 1)) >> kk;
+  mag = k > 63 ? 0 : mag;
+  const uint64_t s = 0ull - (b >> 63);  // all ones when negative
+  return (int64_t)((mag ^ s) - s);
+}
+
+// Exact 128-bit sums of products of Q60 values (the exact reductions): a value
+// splits as v = h 2^31 + l with |l| <= 2^30, so for |v| < 2^61 also |h| <= 2^30,
+// and x1 y1 + x2 y2 = A 2^62 + B 2^31 + C with |A| <= 2^61, |B| <= 2^62,
+// |C| <= 2^61: three int64 column sums of 32 x 32 -> 64-bit products, combined
+// modulo 2^128 (two's complement).
+struct Sp {
+  int32_t h, l;
+};
+QS_HD Sp split31(int64_t v) {
+  const int64_t h = (v + (1ll << 30)) >> 31;
+  return {(int32_t)h, (int32_t)(v - h * (1ll << 31))};
+}
+QS_HD Sp sp_neg(Sp v) { return {-v.h, -v.l}; }
+QS_HD unsigned __int128 dot2_exact(Sp x1, Sp y1, Sp x2, Sp y2) {
+  using u128 = unsigned __int128;
+  const int64_t A = (int64_t)x1.h * y1.h + (int64_t)x2.h * y2.h;
+  const int64_t B = (int64_t)x1.h * y1.l + (int64_t)x1.l * y1.h + (int64_t)x2.h * y2.l + (int64_t)x2.l * y2.h;
+  const int64_t C = (int64_t)x1.l * y1.l + (int64_t)x2.l * y2.l;
+  return ((u128)A << 62) + ((u128)B << 31) + (u128)C;
+}
+
 // Nearest double to V * 2^-60 (round half to even).  Integer operations only.
 QS_HD double q60_to_double(int64_t V) {
   if (V == 0) return 0.0;

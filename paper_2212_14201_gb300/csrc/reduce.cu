@@ -298,34 +298,54 @@ __global__ void __launch_bounds__(256) k_expect_z(const A* __restrict__ a, int r
   }
 }
 
-// The same sums exactly, for a state within the Q60 bound and r - 8 <= ZEXJ loop
-// bits: squares of the Q60-rounded components as 128-bit integers (units 2^-120).
-// A thread folds its amplitudes in fours (loop bits 0 and 1 inside the four), so
-// the other loop bits take one 128-bit add per four amplitudes.  Outputs per CTA
-// as in k_expect_z, each value as two words (low, high).
+// The same sums exactly, for a state within the Q60 bound and 4 <= r - 8 <= ZEXJ
+// loop bits: squares of the Q60-rounded components as 128-bit integers (units
+// 2^-120).  A thread takes its amplitudes sixteen at a time (loop bits 0..3, whose
+// sums stay in registers); the sixteen-amplitude total is then added, in shared
+// memory, to the sum of every higher loop bit set in that step, the same for all
+// lanes.  Outputs per CTA as in k_expect_z, each value as two words (low, high).
 constexpr int ZEXJ = 12;
 template <class A>
-__global__ void __launch_bounds__(256) k_expect_z_exact(const A* __restrict__ a, int r, uint64_t* __restrict__ part) {
+__global__ void __launch_bounds__(256, 3) k_expect_z_exact(const A* __restrict__ a, int r, uint64_t* __restrict__ part) {
   __shared__ uint64_t sh[8][2];
+  __shared__ uint4 hs[ZEXJ - 4][256];  // per-thread sums of loop bits 4.. (low, high words)
   const int jbits = r - 8;
-  const uint64_t base = (uint64_t)blockIdx.x << r;
-  u128 tot = 0;
-  u128 bs[ZEXJ];
-#pragma unroll
-  for (int b = 0; b < ZEXJ; ++b) bs[b] = 0;
+  const uint64_t base = ((uint64_t)blockIdx.x << r) + threadIdx.x;
+  for (int b = 0; b < jbits - 4; ++b) hs[b][threadIdx.x] = make_uint4(0, 0, 0, 0);
+  u128 tot = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
   const uint64_t J = 1ull << jbits;
-  for (uint64_t j = 0; j < J; j += 4) {
-    const u128 p0 = sq120(ld_amp(a, base + threadIdx.x + (j << 8)));
-    const u128 p1 = sq120(ld_amp(a, base + threadIdx.x + ((j + 1) << 8)));
-    const u128 p2 = sq120(ld_amp(a, base + threadIdx.x + ((j + 2) << 8)));
-    const u128 p3 = sq120(ld_amp(a, base + threadIdx.x + ((j + 3) << 8)));
-    const u128 t4 = (p0 + p1) + (p2 + p3);
-    tot += t4;
-    bs[0] += p1 + p3;
-    bs[1] += p2 + p3;
+  for (uint64_t j = 0; j < J; j += 16) {
+    u128 t16 = 0;
 #pragma unroll
-    for (int b = 2; b < ZEXJ; ++b)
-      if (b < jbits && ((j >> b) & 1)) bs[b] += t4;
+    for (int h = 0; h < 16; h += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = ld_amp(a, base + ((j + h + q) << 8));
+      u128 t8 = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const u128 p = sq120(v[q]);
+        t8 += p;
+        if (q & 1) b0 += p;
+        if (q & 2) b1 += p;
+        if (q & 4) b2 += p;
+      }
+      if (h) b3 += t8;
+      t16 += t8;
+    }
+    tot += t16;
+    const uint32_t jh = (uint32_t)(j >> 4);
+    if (jh) {
+      for (int b = 0; b < jbits - 4; ++b) {
+        if ((jh >> b) & 1) {
+          uint4 c = hs[b][threadIdx.x];
+          u128 v = (((u128)(((uint64_t)c.w << 32) | c.z)) << 64) | (((uint64_t)c.y << 32) | c.x);
+          v += t16;
+          const uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+          hs[b][threadIdx.x] = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+        }
+      }
+    }
   }
   auto block_sum = [&](u128 v) {  // fixed shuffle tree, then warps in order
 #pragma unroll
@@ -351,12 +371,13 @@ __global__ void __launch_bounds__(256) k_expect_z_exact(const A* __restrict__ a,
   };
   put(0, block_sum(tot));
   for (int i = 0; i < 8; ++i) put(1 + i, block_sum(((threadIdx.x >> i) & 1) ? tot : (u128)0));
-  for (int b = 0; b < jbits; ++b) {
-    u128 v = 0;
-#pragma unroll
-    for (int bb = 0; bb < ZEXJ; ++bb)
-      if (bb == b) v = bs[bb];
-    put(1 + 8 + b, block_sum(v));
+  put(9, block_sum(b0));
+  put(10, block_sum(b1));
+  put(11, block_sum(b2));
+  put(12, block_sum(b3));
+  for (int b = 0; b < jbits - 4; ++b) {
+    const uint4 c = hs[b][threadIdx.x];
+    put(13 + b, block_sum((((u128)(((uint64_t)c.w << 32) | c.z)) << 64) | (((uint64_t)c.y << 32) | c.x)));
   }
 }
 
@@ -447,109 +468,154 @@ __global__ void k_pauli_finish(const double* __restrict__ part, int nblocks, int
 //   ny = 0: 2 s0 Re w,  1: -2 s0 Im w,  2: -2 s0 Re w,  3: 2 s0 Im w,
 // and a term with xm = 0 contributes s0 |a_x0|^2 per index.
 //
-// One pass reads the state once, as cells {base ^ span(m1, m2)} of 2^NB amplitudes
-// (NB <= 2; m1, m2 two X masks with distinct leading bits, which the cell base
-// has clear), and serves every slot whose X mask lies in the span plus any
-// xm = 0 slots.  A slot (xm, zm, part) accumulates pos = the sum of its values v
-// (Re w, Im w or |a|^2) over pairs with s0 = +1; the term is then
-// mult * (2 pos - tot), tot = the same sum with zm = 0 (its own slot).
-constexpr int PS_MAX = 12;  // slots per pass
-struct PPass {
-  uint64_t ncells;       // 2^(n - NB)
-  uint64_t m1, m2;       // cell basis (first NB used)
-  int lo, hi;            // leading-bit positions of the basis, ascending (NB = 2), lo only (NB = 1)
-  int nt;                // slots in this pass
-  int nz;                // the first nz slots are |a|^2 slots
+// One pass reads the state once, as tiles {base ^ span(bm_0 .. bm_{T-1})} of
+// 2^T <= 4096 amplitudes: the basis holds qubits 0..3 (so a tile is made of runs
+// of 16 consecutive amplitudes) and X masks reduced to distinct leading bits, which
+// every tile base has clear.  A CTA stages a tile in shared memory with cp.async,
+// decodes it to split Q60 once, serves the |a|^2 slots from the decoded values,
+// then every pair slot whose X mask lies in the span from shared memory.  A slot
+// (xm, zm, part) accumulates pos = the sum of its values v (Re w, Im w or |a|^2)
+// over pairs with s0 = +1; the term is mult * (2 pos - tot), tot = the same sum
+// with zm = 0 (its own slot).
+constexpr int PT_TMAX = 12;  // tile coordinates
+constexpr int PS_MAX = 12;   // slots per pass
+struct PTile {
+  uint64_t ntiles;          // 2^(n - T)
+  int T;                    // tile coordinates, ordered by leading bit
+  int lead[PT_TMAX];        // leading bit of each basis vector (ascending)
+  uint64_t bm[PT_TMAX];     // basis vector of each coordinate
+  int nt, nz;               // slots in this pass; the first nz are |a|^2 slots
   uint64_t zm[PS_MAX];
-  uint8_t xc[PS_MAX];     // pair slots: X mask = (xc & 1 ? m1 : 0) ^ (xc & 2 ? m2 : 0)
-  uint8_t im[PS_MAX];     // pair slots: 0 = Re w, 1 = Im w
-  uint8_t smask[PS_MAX];  // bit s = parity(off_s & zm), off_s = (s & 1 ? m1 : 0) ^ (s & 2 ? m2 : 0)
+  uint32_t zc[PS_MAX];      // bit i = parity(bm[i] & zm)
+  uint32_t xc[PS_MAX];      // pair slots: X mask = XOR of bm[i] over the bits i of xc
+  int top[PS_MAX];          // pair slots: highest bit of xc
+  uint8_t im[PS_MAX];       // pair slots: 0 = Re w, 1 = Im w
 };
-
-// v = h 2^31 + l with |l| <= 2^30; for |v| < 2^61 also |h| <= 2^30.
-struct Sp {
-  int32_t h, l;
-};
-__device__ __forceinline__ Sp split31(int64_t v) {
-  const int64_t h = (v + (1ll << 30)) >> 31;
-  return {(int32_t)h, (int32_t)(v - h * (1ll << 31))};
-}
-__device__ __forceinline__ Sp sp_neg(Sp v) { return {-v.h, -v.l}; }
-
-// x1 y1 + x2 y2 exactly, as a two's-complement 128-bit value: the three column
-// sums are each below 2^63 in magnitude for split inputs of |v| < 2^61.
-__device__ __forceinline__ u128 dot2(Sp x1, Sp y1, Sp x2, Sp y2) {
-  const int64_t A = (int64_t)x1.h * y1.h + (int64_t)x2.h * y2.h;
-  const int64_t B = (int64_t)x1.h * y1.l + (int64_t)x1.l * y1.h + (int64_t)x2.h * y2.l + (int64_t)x2.l * y2.h;
-  const int64_t C = (int64_t)x1.l * y1.l + (int64_t)x2.l * y2.l;
-  return ((u128)A << 62) + ((u128)B << 31) + (u128)C;
-}
 
 __device__ __forceinline__ uint64_t insert0(uint64_t c, int b) {
   return ((c >> b) << (b + 1)) | (c & ((1ull << b) - 1));
 }
 
-template <class A, int NB>
-__global__ void __launch_bounds__(256, 2) k_pauli_exact(const A* __restrict__ a, const PPass g,
-                                                        uint64_t* __restrict__ part) {
-  constexpr int S = 1 << NB;
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ Sp sp_h(int4 u) { return {u.x, u.y}; }
+// acc += v when bit 0 of c is clear: a predicated 128-bit add (carry chain)
+__device__ __forceinline__ void add128_if_even(u128& acc, u128 v, uint32_t c) {
+  uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
+  asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %4, 1;\n\tsetp.eq.u32 p, t, 0;\n\t"
+      "@p add.cc.u64 %0, %0, %2;\n\t@p addc.u64 %1, %1, %3;\n\t}"
+      : "+l"(lo), "+l"(hi)
+      : "l"((uint64_t)v), "l"((uint64_t)(v >> 64)), "r"(c));
+  acc = ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ Sp sp_i(int4 u) { return {u.z, u.w}; }
+
+template <class A>
+__global__ void __launch_bounds__(256, 3) k_pauli_tile(const A* __restrict__ a, const PTile g,
+                                                       uint64_t* __restrict__ part) {
+  extern __shared__ int4 tile[];  // 2^T entries: the raw amplitude, then (r.h, r.l, i.h, i.l)
   __shared__ uint64_t sh[8][PS_MAX][2];
+  const int E = 1 << g.T;
   u128 pos[PS_MAX];
 #pragma unroll
   for (int k = 0; k < PS_MAX; ++k) pos[k] = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < g.ncells; c += stride) {
+  __shared__ uint64_t span_hi[1 << (PT_TMAX - 8)];  // span of coordinates 8.. for e >> 8
+  uint64_t span_t = 0;                              // span of this thread's coordinates 0..7
+  for (int i = 0; i < g.T && i < 8; ++i)
+    if ((threadIdx.x >> i) & 1) span_t ^= g.bm[i];
+  if (threadIdx.x < (1 << (PT_TMAX - 8))) {
+    uint64_t v = 0;
+    for (int i = 8; i < g.T; ++i)
+      if ((threadIdx.x >> (i - 8)) & 1) v ^= g.bm[i];
+    span_hi[threadIdx.x] = v;
+  }
+  // |a|^2 slots: the sign of entry e is bit k of (pbm ^ tpar ^ zub[e >> 8]), with
+  // tpar the parities of this thread's coordinates 0..7 and zub those of 8..
+  __shared__ uint32_t zub[1 << (PT_TMAX - 8)];
+  uint32_t tpar = 0;
+#pragma unroll
+  for (int k = 0; k < PS_MAX; ++k)
+    if (k < g.nz) tpar |= (uint32_t)(__popc(threadIdx.x & g.zc[k] & 0xffu) & 1) << k;
+  if (threadIdx.x < (1 << (PT_TMAX - 8))) {
+    uint32_t u = 0;
+    for (int k = 0; k < g.nz; ++k) u |= (uint32_t)(__popc(threadIdx.x & (g.zc[k] >> 8)) & 1) << k;
+    zub[threadIdx.x] = u;
+  }
+  __syncthreads();
+  for (uint64_t c = blockIdx.x; c < g.ntiles; c += gridDim.x) {
     uint64_t base = c;
-    if (NB >= 1) base = insert0(base, g.lo);
-    if (NB >= 2) base = insert0(base, g.hi);
-    double2 v[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) v[s] = ld_amp(a, base ^ ((s & 1) ? g.m1 : 0) ^ ((s & 2) ? g.m2 : 0));
-    Sp r[S], i[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      r[s] = split31(q60_from_double(v[s].x));
-      i[s] = split31(q60_from_double(v[s].y));
+    for (int i = 0; i < g.T; ++i) base = insert0(base, g.lead[i]);
+    const uint64_t bt = base ^ span_t;
+    for (int e = threadIdx.x; e < E; e += 256) {
+      const uint64_t x = bt ^ span_hi[e >> 8];
+      if (sizeof(A) == 16) cp_async16(&tile[e], a + x);
+      else cp_async8(&tile[e], a + x);
     }
-    u128 p[S];
-    if (g.nz > 0) {
+    cp_async_wait_all();  // each thread decodes the entries it copied
+    uint32_t pbm = 0;     // bit k: parity(base & zm_k)
 #pragma unroll
-      for (int s = 0; s < S; ++s) p[s] = dot2(r[s], r[s], i[s], i[s]);
+    for (int k = 0; k < PS_MAX; ++k)
+      if (k < g.nt) pbm |= (uint32_t)(__popcll(base & g.zm[k]) & 1) << k;
+    for (int e = threadIdx.x; e < E; e += 256) {
+      double re, im;
+      if (sizeof(A) == 16) {
+        const double2 v = *reinterpret_cast<const double2*>(&tile[e]);
+        re = v.x;
+        im = v.y;
+      } else {
+        const float2 v = *reinterpret_cast<const float2*>(&tile[e]);
+        re = v.x;
+        im = v.y;
+      }
+      const Sp r = split31(q60_from_double(re)), i = split31(q60_from_double(im));
+      tile[e] = make_int4(r.h, r.l, i.h, i.l);
+      if (g.nz > 0) {
+        const u128 p = dot2_exact(r, r, i, i);
+        const uint32_t m = pbm ^ tpar ^ zub[e >> 8];
+#pragma unroll
+        for (int k = 0; k < PS_MAX; ++k)
+          if (k < g.nz) add128_if_even(pos[k], p, m >> k);
+      }
     }
-    u128 w[S / 2 > 0 ? S / 2 : 1];
-    int key = -1;
+    __syncthreads();
+    // pair slots: pairs outer, slots inner (one product live, recomputed when the
+    // slot's (X mask, part) changes)
+    for (int t = threadIdx.x; t < E / 2; t += 256) {
+      int key = -1;
+      u128 wv = 0;
+      uint32_t s0 = 0;
 #pragma unroll
-    for (int k = 0; k < PS_MAX; ++k) {
-      if (k < g.nt) {
-        const int pb = __popcll(base & g.zm[k]) & 1;
-        const int sm = g.smask[k];
-        if (k < g.nz) {
-#pragma unroll
-          for (int s = 0; s < S; ++s)
-            if ((((sm >> s) & 1) ^ pb) == 0) pos[k] += p[s];
-        } else {
-          const int xc = g.xc[k], part_im = g.im[k];
-#pragma unroll
-          for (int xcc = 1; xcc < S; ++xcc) {
-            if (xc == xcc) {
-              if (xc * 2 + part_im != key) {
-                key = xc * 2 + part_im;
-#pragma unroll
-                for (int j = 0; j < S / 2; ++j) {
-                  const int s0 = xcc == 1 ? 2 * j : j, s1 = s0 ^ xcc;
-                  w[j] = part_im ? dot2(r[s1], i[s0], sp_neg(i[s1]), r[s0]) : dot2(r[s1], r[s0], i[s1], i[s0]);
-                }
-              }
-#pragma unroll
-              for (int j = 0; j < S / 2; ++j) {
-                const int s0 = xcc == 1 ? 2 * j : j;
-                if ((((sm >> s0) & 1) ^ pb) == 0) pos[k] += w[j];
-              }
-            }
+      for (int k = 0; k < PS_MAX; ++k) {
+        if (k >= g.nz && k < g.nt) {
+          const uint32_t xc = g.xc[k];
+          const int kk = (int)xc * 2 + g.im[k];
+          if (kk != key) {
+            key = kk;
+            const int top = g.top[k];
+            s0 = (((uint32_t)t >> top) << (top + 1)) | ((uint32_t)t & ((1u << top) - 1u));
+            const int4 u0 = tile[s0], u1 = tile[s0 ^ xc];
+            wv = g.im[k] ? dot2_exact(sp_h(u1), sp_i(u0), sp_neg(sp_i(u1)), sp_h(u0))
+                         : dot2_exact(sp_h(u1), sp_h(u0), sp_i(u1), sp_i(u0));
+          }
+          if (g.zc[k] == 0) {  // sign the same over the tile
+            if (((pbm >> k) & 1u) == 0) pos[k] += wv;
+          } else {
+            add128_if_even(pos[k], wv, (pbm >> k) ^ (uint32_t)__popc(s0 & g.zc[k]));
           }
         }
       }
     }
+    __syncthreads();  // the next tile's copies overwrite this one
   }
   const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
@@ -813,9 +879,9 @@ extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
   }
   QS_TRY(ensure_bound(s));
   KTimer kt(s, QS_K_REDUCE, n, 1, 0, 0, (double)(1ull << n), 5.0 * (double)(1ull << n));
-  if (s->bound == 1 && n >= 10 && n <= 20 + ZEXJ - 2) {  // exact integer sums (k_expect_z_exact)
-    // r bits per CTA: 2 <= r - 8 <= ZEXJ loop bits, at most 1024 CTAs
-    const int r = std::max(10, n - 10);
+  if (s->bound == 1 && n >= 12 && n <= 20 + ZEXJ - 2) {  // exact integer sums (k_expect_z_exact)
+    // r bits per CTA: 4 <= r - 8 <= ZEXJ loop bits, at most 1024 CTAs
+    const int r = std::max(12, n - 10);
     const int nblocks = 1 << (n - r);
     uint64_t* ipart = (uint64_t*)s->ws;
     note_launch(1);
@@ -886,53 +952,70 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
         tmult[k] = (ny == 0 || ny == 3) ? 2 : -2;
       }
     }
-    // passes: basis, then the slot list (|a|^2 slots first, pair slots by (xc, im))
+    // passes: a tile basis (qubits 0..3, then X masks reduced to new leading bits,
+    // then further single qubits up to T coordinates) and its slot list (|a|^2 slots
+    // first, pair slots ordered by (xc, im))
+    const int Tmax = std::min(PT_TMAX, n);
     struct Pass {
-      int nb;
-      uint64_t m1, m2;
+      std::vector<uint64_t> bm;  // by coordinate, ascending leading bit
       std::vector<int> sl;
     };
+    auto reduce = [](const std::vector<uint64_t>& B, uint64_t v, uint32_t* xc) {
+      // B in echelon form (distinct leading bits), any order: clear each basis
+      // vector's leading bit from v, highest leading bit first
+      std::vector<int> order(B.size());
+      for (size_t q = 0; q < B.size(); ++q) order[q] = (int)q;
+      std::sort(order.begin(), order.end(), [&](int x, int y) { return lead_bit(B[x]) > lead_bit(B[y]); });
+      uint32_t c = 0;
+      for (int q : order)
+        if ((v >> lead_bit(B[q])) & 1) {
+          v ^= B[q];
+          c |= 1u << q;
+        }
+      if (xc) *xc = c;
+      return v;
+    };
+    auto make_basis = [&](std::vector<uint64_t> B) {
+      for (int b = 0; (int)B.size() < Tmax && b < n; ++b) {  // fill with single qubits
+        bool is_lead = false;
+        for (uint64_t v : B) is_lead |= lead_bit(v) == b;
+        if (!is_lead) B.push_back(1ull << b);
+      }
+      std::sort(B.begin(), B.end(), [](uint64_t x, uint64_t y) { return lead_bit(x) < lead_bit(y); });
+      return B;
+    };
     std::vector<Pass> passes;
-    std::vector<char> done(xms.size(), 0);
     std::map<uint64_t, std::vector<int>> by_xm;  // pair slots per X mask
     for (int k = 0; k < (int)slots.size(); ++k)
       if (slots[k].xm) by_xm[slots[k].xm].push_back(k);
-    for (size_t i = 0; i < xms.size(); ++i) {
-      if (done[i]) continue;
-      done[i] = 1;
-      Pass P{1, xms[i], 0, {}};
-      size_t j = i + 1;
-      while (j < xms.size() && done[j]) ++j;
-      if (j < xms.size()) {
-        done[j] = 1;
-        P.nb = 2;
-        P.m2 = xms[j];
-        if (lead_bit(P.m2) == lead_bit(P.m1)) P.m2 ^= P.m1;
+    std::vector<char> done(xms.size(), 0);
+    for (size_t i0 = 0; i0 < xms.size(); ++i0) {
+      if (done[i0]) continue;
+      std::vector<uint64_t> B;
+      for (int b = 0; b < std::min(4, n); ++b) B.push_back(1ull << b);
+      for (size_t q = i0; q < xms.size() && (int)B.size() < Tmax; ++q) {
+        if (done[q]) continue;
+        const uint64_t v = reduce(B, xms[q], nullptr);
+        if (v) B.push_back(v);
       }
-      std::vector<uint64_t> span = {P.m1};
-      if (P.nb == 2) {
-        span.push_back(P.m2);
-        span.push_back(P.m1 ^ P.m2);
-      }
-      for (size_t q = i + 1; q < xms.size(); ++q)  // every other X mask in the span
-        if (!done[q] && std::find(span.begin(), span.end(), xms[q]) != span.end()) done[q] = 1;
-      std::vector<std::pair<int, int>> keyed;  // (xc * 2 + im, slot)
-      for (size_t c = 0; c < span.size(); ++c) {
-        auto it = by_xm.find(span[c]);
-        if (it == by_xm.end()) continue;
-        for (int k : it->second) keyed.push_back({(int)(c + 1) * 2 + slots[k].im, k});
-        by_xm.erase(it);
+      B = make_basis(B);
+      std::vector<std::pair<uint64_t, int>> keyed;  // ((xc << 1) | im, slot)
+      for (size_t q = i0; q < xms.size(); ++q) {
+        if (done[q]) continue;
+        uint32_t xc = 0;
+        if (reduce(B, xms[q], &xc)) continue;  // outside this span
+        done[q] = 1;
+        for (int k : by_xm[xms[q]]) keyed.push_back({((uint64_t)xc << 1) | (uint64_t)slots[k].im, k});
       }
       std::stable_sort(keyed.begin(), keyed.end(),
-                       [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+                       [](const std::pair<uint64_t, int>& x, const std::pair<uint64_t, int>& y) { return x.first < y.first; });
       for (size_t c = 0; c < keyed.size(); c += PS_MAX) {
-        Pass Q = P;
-        for (size_t q = c; q < std::min(keyed.size(), c + PS_MAX); ++q) Q.sl.push_back(keyed[q].second);
-        passes.push_back(Q);
+        Pass P{B, {}};
+        for (size_t q = c; q < std::min(keyed.size(), c + PS_MAX); ++q) P.sl.push_back(keyed[q].second);
+        passes.push_back(P);
       }
-      if (keyed.empty()) passes.push_back(P);
     }
-    // |a|^2 slots: into free places, then passes over cells of bits 0 (and 1)
+    // |a|^2 slots: into free places, then passes over tiles of qubits 0..T-1
     std::vector<int> zs;
     for (int k = 0; k < (int)slots.size(); ++k)
       if (!slots[k].xm) zs.push_back(k);
@@ -940,7 +1023,7 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
     for (auto& P : passes)
       while (zi < zs.size() && (int)P.sl.size() < PS_MAX) P.sl.insert(P.sl.begin(), zs[zi++]);
     while (zi < zs.size()) {
-      Pass P{n >= 2 ? 2 : 1, 1, n >= 2 ? 2ull : 0ull, {}};
+      Pass P{make_basis({}), {}};
       while (zi < zs.size() && (int)P.sl.size() < PS_MAX) P.sl.push_back(zs[zi++]);
       passes.push_back(P);
     }
@@ -952,19 +1035,19 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
     uint64_t* sums = part + part_words;
     if ((part_words + 2 * nslots) * sizeof(uint64_t) > s->ws_bytes)
       return fail(QS_ERR_UNSUPPORTED, "Pauli slot sums exceed the workspace");
+    static std::once_flag smem_once;
+    std::call_once(smem_once, [] {
+      cudaFuncSetAttribute(k_pauli_tile<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << PT_TMAX);
+      cudaFuncSetAttribute(k_pauli_tile<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << PT_TMAX);
+    });
     int next = 0;
     for (const auto& P : passes) {
-      if (P.sl.empty()) continue;
-      PPass g{};
-      g.ncells = 1ull << (n - P.nb);
-      g.m1 = P.m1;
-      g.m2 = P.nb == 2 ? P.m2 : 0;
-      if (P.nb == 2) {
-        g.lo = std::min(lead_bit(P.m1), lead_bit(P.m2));
-        g.hi = std::max(lead_bit(P.m1), lead_bit(P.m2));
-      } else {
-        g.lo = lead_bit(P.m1);
-        g.hi = -1;
+      PTile g{};
+      g.T = (int)P.bm.size();
+      g.ntiles = 1ull << (n - g.T);
+      for (int q = 0; q < g.T; ++q) {
+        g.bm[q] = P.bm[q];
+        g.lead[q] = lead_bit(P.bm[q]);
       }
       g.nt = (int)P.sl.size();
       g.nz = 0;
@@ -973,32 +1056,29 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
         gidx[P.sl[q]] = next + q;
         g.zm[q] = sl.zm;
         g.im[q] = (uint8_t)sl.im;
+        uint32_t zc = 0;
+        for (int t = 0; t < g.T; ++t) zc |= (uint32_t)(__builtin_popcountll(P.bm[t] & sl.zm) & 1) << t;
+        g.zc[q] = zc;
         if (!sl.xm) {
           ++g.nz;
           g.xc[q] = 0;
+          g.top[q] = 0;
         } else {
-          g.xc[q] = sl.xm == P.m1 ? 1 : (sl.xm == g.m2 ? 2 : 3);
+          uint32_t xc = 0;
+          reduce(P.bm, sl.xm, &xc);
+          g.xc[q] = xc;
+          g.top[q] = 31 - __builtin_clz(xc);
         }
-        uint8_t sm = 0;
-        for (int t = 0; t < (1 << P.nb); ++t) {
-          const uint64_t off = ((t & 1) ? g.m1 : 0) ^ ((t & 2) ? g.m2 : 0);
-          sm |= (uint8_t)((__builtin_popcountll(off & sl.zm) & 1) << t);
-        }
-        g.smask[q] = sm;
       }
-      const int nblocks = (int)std::min<uint64_t>(1216, std::max<uint64_t>(1, g.ncells / 256));
+      const int nblocks = (int)std::min<uint64_t>(3 * 152, g.ntiles);  // three CTAs per SM
       KTimer kt(s, QS_K_REDUCE, n, g.nt, 0, 0, (double)(1ull << n), 8.0 * g.nt * (double)(1ull << n));
       note_launch(2);
       with_amps(s, [&](auto* a) {
         using T = std::remove_cv_t<std::remove_pointer_t<decltype(a)>>;
-        const T* ca = a;
-        switch (P.nb) {
-          case 1: k_pauli_exact<T, 1><<<nblocks, 256, 0, s->stream>>>(ca, g, part); break;
-          default: k_pauli_exact<T, 2><<<nblocks, 256, 0, s->stream>>>(ca, g, part); break;
-        }
+        k_pauli_tile<T><<<nblocks, 256, (size_t)16 << g.T, s->stream>>>(a, g, part);
         return QS_OK;
       });
-      QS_TRY(launch_check("pauli_exact"));
+      QS_TRY(launch_check("pauli_tile"));
       k_pauli_exact_finish<<<1, 32, 0, s->stream>>>(part, nblocks, g.nt, sums + 2 * (size_t)next);
       QS_TRY(launch_check("pauli_exact_finish"));
       next += g.nt;

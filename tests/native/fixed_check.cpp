@@ -4,6 +4,13 @@
 
 extern "C" {
 long long fc_from_double(double v) { return (long long)qs::q60_from_double(v); }
+long long fc_from_double_nb(double v) { return (long long)qs::q60_from_double_nb(v); }
+// x1 y1 + x2 y2 of Q60 integers through the split-column exact product, as two words
+void fc_dot2_exact(long long x1, long long y1, long long x2, long long y2, unsigned long long* out) {
+  const unsigned __int128 r = qs::dot2_exact(qs::split31(x1), qs::split31(y1), qs::split31(x2), qs::split31(y2));
+  out[0] = (unsigned long long)r;
+  out[1] = (unsigned long long)(r >> 64);
+}
 double fc_to_double(long long V) { return qs::q60_to_double((int64_t)V); }
 // out = u0 * a0 + u1 * a1 for Q60 reals given as int64, via the limb accumulator
 long long fc_dot2(long long u0, long long a0, long long u1, long long a1) {

@@ -23,6 +23,10 @@ def fc():
     lib = ctypes.CDLL(so)
     lib.fc_from_double.restype = ctypes.c_longlong
     lib.fc_from_double.argtypes = [ctypes.c_double]
+    lib.fc_from_double_nb.restype = ctypes.c_longlong
+    lib.fc_from_double_nb.argtypes = [ctypes.c_double]
+    lib.fc_dot2_exact.restype = None
+    lib.fc_dot2_exact.argtypes = [ctypes.c_longlong] * 4 + [ctypes.c_void_p]
     lib.fc_to_double.restype = ctypes.c_double
     lib.fc_to_double.argtypes = [ctypes.c_longlong]
     lib.fc_dot2.restype = ctypes.c_longlong
@@ -57,6 +61,34 @@ def values(seed, count):
 def test_from_double_is_correctly_rounded(fc):
     for v in values(1, 3000):
         assert fc.fc_from_double(v) == exact_q60(v), v
+
+
+def test_branch_free_decode_matches(fc):
+    """q60_from_double_nb: the same rounding for every exponent |v| < 8 can have,
+    the largest values, ties, zeros and subnormals."""
+    vs = values(2, 3000)
+    for e in range(-75, 3):
+        for m in (1.0, 1.5, 1.0 + 2.0 ** -52, 2.0 - 2.0 ** -52):
+            vs += [m * 2.0 ** e, -m * 2.0 ** e]
+    vs += [7.999999999999999, -7.999999999999999, 2.0 ** -61 * 3, 2.0 ** -63, 2.0 ** -62, -(2.0 ** -62),
+           2.0 ** -62 * (1 + 2.0 ** -52), 5e-324, -5e-324, 2.2250738585072014e-308]
+    for v in vs:
+        assert fc.fc_from_double_nb(v) == exact_q60(v), v
+
+
+def test_exact_pair_products(fc):
+    """split31 / dot2_exact: x1 y1 + x2 y2 exactly (modulo 2^128) over the whole
+    range |v| < 2^61, including the extremes of every column sum."""
+    g = np.random.Generator(np.random.PCG64(5))
+    lim = (1 << 61) - 1
+    edge = [lim, -lim, (1 << 60) + (1 << 30), -(1 << 30), (1 << 30) - 1, 0, 1, -1, (1 << 31) + (1 << 30)]
+    cases = [tuple(int(x) for x in g.integers(-lim, lim, 4, dtype=np.int64)) for _ in range(3000)]
+    cases += [(a, b, c, d) for a in edge for b in edge for c in edge[:3] for d in edge[:3]]
+    out = (ctypes.c_ulonglong * 2)()
+    for x1, y1, x2, y2 in cases:
+        fc.fc_dot2_exact(x1, y1, x2, y2, out)
+        want = (x1 * y1 + x2 * y2) % (1 << 128)
+        assert out[0] + (out[1] << 64) == want, (x1, y1, x2, y2)
 
 
 def test_to_double_is_correctly_rounded(fc):
