@@ -353,9 +353,10 @@ def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3):
     """Rows A6-A8 at n=30 (16 GiB) on the config-1 output state: squared norm,
     one-qubit marginal, <Z_i> for all 30 qubits, a TFIM Pauli sum (29 ZZ + 30 X
     terms, h = 0.7) and 10^6 samples, each timed with CUDA events on the state's
-    stream.  Algorithmic bytes: 16 B per amplitude read for the norm, marginal and
-    <Z_i>; for the Pauli sum 16 B per amplitude per distinct X mask (31 reads:
-    the Z-only group and one gather per X term)."""
+    stream.  Bytes: 16 B per amplitude read for the norm, marginal and <Z_i>; for
+    the Pauli sum 16 B per amplitude per pass of the tile kernel, which reads the
+    state once per pass: 5 passes (tiles spanning 12, 8, 8 and 2 of the 30 X
+    masks, the 30 |a|^2 slots in the free places and one pass of their own)."""
     n = 30
     g = w.layered_u3_cz(n, 20, 1)
     terms = w.tfim(n, 0.7)
@@ -384,7 +385,7 @@ def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3):
             "norm": (lambda: q.qs_probs(h, [], dev), 16 * N),
             "marginal_1q": (lambda: q.qs_probs(h, [17], dev), 16 * N),
             "expect_z_all": (lambda: q.qs_expect_z_all(h), 16 * N),
-            "expect_pauli_tfim": (lambda: q.qs_expect_pauli(h, terms), 16 * N * 31),
+            "expect_pauli_tfim": (lambda: q.qs_expect_pauli(h, terms), 16 * N * 5),
             "sample_1e6": (lambda: q.qs_sample(h, 11, 1_000_000, samples), 16 * N),
         }
         for name, (fn, nbytes) in cases.items():
