@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--only-batch", action="store_true",
                     help="profiling aid: run only the batched VQE workload and print its result")
     ap.add_argument("--batch-sets", type=int, default=1024, help="parameter sets of the batched VQE workload")
+    ap.add_argument("--only-reductions", type=int, default=0, metavar="N",
+                    help="profiling aid: run only the reduction timings on an N-qubit state and print them")
     return ap.parse_args()
 
 
@@ -349,15 +351,14 @@ def bench_measure(q, torch, stream, hbm_peak: float):
     return out
 
 
-def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3):
-    """Rows A6-A8 at n=30 (16 GiB) on the config-1 output state: squared norm,
-    one-qubit marginal, <Z_i> for all 30 qubits, a TFIM Pauli sum (29 ZZ + 30 X
-    terms, h = 0.7) and 10^6 samples, each timed with CUDA events on the state's
-    stream.  Bytes: 16 B per amplitude read for the norm, marginal and <Z_i>; for
-    the Pauli sum 16 B per amplitude per pass of the tile kernel, which reads the
-    state once per pass: 5 passes (tiles spanning 12, 8, 8 and 2 of the 30 X
-    masks, the 30 |a|^2 slots in the free places and one pass of their own)."""
-    n = 30
+def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3, n: int = 30):
+    """Rows A6-A8 on the output state of the config-1 circuit (n=30: 16 GiB):
+    squared norm, one-qubit marginal, <Z_i> for all n qubits, a TFIM Pauli sum
+    ((n-1) ZZ + n X terms, h = 0.7) and 10^6 samples, each timed with CUDA events
+    on the state's stream.  Bytes: 16 B per amplitude read for the norm, marginal
+    and <Z_i>; for the Pauli sum 16 B per amplitude per pass of the tile kernel,
+    which reads the state once per pass (the passes are counted from the
+    library's kernel log; n=30: 5, tiles spanning 12, 8, 8 and 2 of the X masks)."""
     g = w.layered_u3_cz(n, 20, 1)
     terms = w.tfim(n, 0.7)
     h = q.qs_alloc(n, stream)
@@ -367,6 +368,11 @@ def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3):
         p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
         q.qs_apply(h, g, None, p)
         q.qs_plan_free(p)
+        q.qs_timing_enable(h, True)
+        q.qs_expect_pauli(h, terms)
+        pauli_passes = sum(1 for r in q.qs_timing_fetch(h) if r["kind"] == q._lib.K_REDUCE)
+        q.qs_timing_enable(h, False)
+        out["pauli_passes"] = pauli_passes
         dev = torch.empty(64, dtype=torch.float64, device="cuda")
         samples = torch.empty(1_000_000, dtype=torch.int64, device="cuda")
 
@@ -385,7 +391,7 @@ def bench_reductions(q, torch, stream, hbm_peak: float, reps: int = 3):
             "norm": (lambda: q.qs_probs(h, [], dev), 16 * N),
             "marginal_1q": (lambda: q.qs_probs(h, [17], dev), 16 * N),
             "expect_z_all": (lambda: q.qs_expect_z_all(h), 16 * N),
-            "expect_pauli_tfim": (lambda: q.qs_expect_pauli(h, terms), 16 * N * 5),
+            "expect_pauli_tfim": (lambda: q.qs_expect_pauli(h, terms), 16 * N * pauli_passes),
             "sample_1e6": (lambda: q.qs_sample(h, 11, 1_000_000, samples), 16 * N),
         }
         for name, (fn, nbytes) in cases.items():
@@ -544,6 +550,10 @@ def run_ours(args, world, rank, local, pg):
     if args.only_batch:
         if rank == 0:
             print(json.dumps({"batched_vqe": bench_batched_vqe(q, torch, args.steps, args.warmup, args.batch_sets)}))
+        return
+    if args.only_reductions:
+        if rank == 0:
+            print(json.dumps({"reductions": bench_reductions(q, torch, stream, peaks()[0], n=args.only_reductions)}))
         return
     n = args.n
     gates = w.layered_u3_cz(n, args.depth, 1)
