@@ -340,7 +340,12 @@ int qs_probs(const qs_state* s, const int* qubits, int nq, double* out, int on_d
 int qs_probs_dict(const qs_state* s, const int* qubits, int nq, double threshold, uint64_t* idx,
                   double* p, size_t cap, size_t* count);
 
-/* <Z_i> for every qubit i into out[0..n-1] (host memory). */
+/* <Z_i> for every qubit i into out[0..n-1] (host memory).  For 10 <= n <= 30 on
+ * a state within the Q60 bound (norm <= 1.25; a state of unknown magnitude, e.g.
+ * after qs_set_state, has its norm measured once), the squares of the Q60-rounded
+ * components are summed exactly in integers: absolute error below
+ * 2^-59 * sum_x |a_x| (about 2^-44 at n = 30).  Otherwise FP64 sums in a fixed
+ * order.  Results are deterministic either way. */
 int qs_expect_z_all(const qs_state* s, double* out);
 
 /* <Z_i> for every qubit i, for callers that cannot allocate memory.  The paper
@@ -367,7 +372,13 @@ int qs_expect_z_all(const qs_state* s, double* out);
 int qs_expect_z_all_noalloc(const double* device_amps, int n, double* device_out, void* stream);
 
 /* <psi| sum_k coef_k P_k |psi> into *out (host).  Each term's masks must lie
- * within the n qubits. */
+ * within the n qubits (else INVALID_ARG).  On a state within the Q60 bound (see
+ * qs_expect_z_all) every term is an exact integer sum over the Q60-rounded
+ * amplitudes (absolute error per term below 2^-59 * sum_x |a_x|): the terms are
+ * grouped by X mask, and each pass reads the state once in tiles of up to 4096
+ * amplitudes that serve every X mask in the span of the tile's basis (qubits
+ * 0..3 and up to eight X masks).  Otherwise FP64, eight terms per pass.  The
+ * weighted sum is formed on the host in term order; results are deterministic. */
 int qs_expect_pauli(const qs_state* s, const qs_pauli* terms, size_t nterms, double* out);
 
 /* Draw `shots` computational-basis samples (measure_all / run_with_configuration).
