@@ -15,6 +15,7 @@
 
 #include "fixed.h"
 #include "internal.h"
+#include "pauli_plan.h"
 
 namespace qs {
 
@@ -477,8 +478,6 @@ __global__ void k_pauli_finish(const double* __restrict__ part, int nblocks, int
 // (xm, zm, part) accumulates pos = the sum of its values v (Re w, Im w or |a|^2)
 // over pairs with s0 = +1; the term is mult * (2 pos - tot), tot = the same sum
 // with zm = 0 (its own slot).
-constexpr int PT_TMAX = 12;  // tile coordinates
-constexpr int PS_MAX = 12;   // slots per pass
 struct PTile {
   uint64_t ntiles;          // 2^(n - T)
   int T;                    // tile coordinates, ordered by leading bit
@@ -908,8 +907,6 @@ extern "C" int qs_expect_z_all(const qs_state* cs, double* out) {
   return read_back(s, dres, n, out);
 }
 
-static int lead_bit(uint64_t m) { return 63 - __builtin_clzll(m); }
-
 // <sum_k coef_k P_k> with the exact passes of k_pauli_exact.  Slots are keyed by
 // (xm, zm, part); X masks are taken two at a time as a cell basis, every other
 // X mask in their span joins that pass, and |a|^2 slots fill the free places
@@ -921,112 +918,17 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
   std::vector<double> vals;
   for (size_t t0 = 0; t0 < nterms; t0 += kChunk) {
     const size_t nt = std::min(kChunk, nterms - t0);
-    struct Slot {
-      uint64_t xm, zm;
-      int im;
-    };
-    std::vector<Slot> slots;
-    std::map<std::tuple<uint64_t, uint64_t, int>, int> slot_of;
-    auto get = [&](uint64_t xm, uint64_t zm, int im) {
-      auto key = std::make_tuple(xm, zm, im);
-      auto it = slot_of.find(key);
-      if (it != slot_of.end()) return it->second;
-      slots.push_back({xm, zm, im});
-      return slot_of[key] = (int)slots.size() - 1;
-    };
-    std::vector<int> tslot(nt), ttot(nt), tmult(nt);
-    std::vector<uint64_t> xms;  // distinct X masks, first appearance order
+    std::vector<uint64_t> xmv(nt), zmv(nt);
     for (size_t k = 0; k < nt; ++k) {
-      const uint64_t xm = terms[t0 + k].xmask, zm = terms[t0 + k].zmask;
-      const int ny = __builtin_popcountll(xm & zm) & 3;
-      if (xm == 0) {
-        tslot[k] = get(0, zm, 0);
-        ttot[k] = get(0, 0, 0);
-        tmult[k] = 1;
-      } else {
-        const int im = ny & 1;
-        if (!slot_of.count(std::make_tuple(xm, 0ull, 0)) && !slot_of.count(std::make_tuple(xm, 0ull, 1)))
-          xms.push_back(xm);
-        tslot[k] = get(xm, zm, im);
-        ttot[k] = get(xm, 0, im);
-        tmult[k] = (ny == 0 || ny == 3) ? 2 : -2;
-      }
+      xmv[k] = terms[t0 + k].xmask;
+      zmv[k] = terms[t0 + k].zmask;
     }
-    // passes: a tile basis (qubits 0..3, then X masks reduced to new leading bits,
-    // then further single qubits up to T coordinates) and its slot list (|a|^2 slots
-    // first, pair slots ordered by (xc, im))
-    const int Tmax = std::min(PT_TMAX, n);
-    struct Pass {
-      std::vector<uint64_t> bm;  // by coordinate, ascending leading bit
-      std::vector<int> sl;
-    };
-    auto reduce = [](const std::vector<uint64_t>& B, uint64_t v, uint32_t* xc) {
-      // B in echelon form (distinct leading bits), any order: clear each basis
-      // vector's leading bit from v, highest leading bit first
-      std::vector<int> order(B.size());
-      for (size_t q = 0; q < B.size(); ++q) order[q] = (int)q;
-      std::sort(order.begin(), order.end(), [&](int x, int y) { return lead_bit(B[x]) > lead_bit(B[y]); });
-      uint32_t c = 0;
-      for (int q : order)
-        if ((v >> lead_bit(B[q])) & 1) {
-          v ^= B[q];
-          c |= 1u << q;
-        }
-      if (xc) *xc = c;
-      return v;
-    };
-    auto make_basis = [&](std::vector<uint64_t> B) {
-      for (int b = 0; (int)B.size() < Tmax && b < n; ++b) {  // fill with single qubits
-        bool is_lead = false;
-        for (uint64_t v : B) is_lead |= lead_bit(v) == b;
-        if (!is_lead) B.push_back(1ull << b);
-      }
-      std::sort(B.begin(), B.end(), [](uint64_t x, uint64_t y) { return lead_bit(x) < lead_bit(y); });
-      return B;
-    };
-    std::vector<Pass> passes;
-    std::map<uint64_t, std::vector<int>> by_xm;  // pair slots per X mask
-    for (int k = 0; k < (int)slots.size(); ++k)
-      if (slots[k].xm) by_xm[slots[k].xm].push_back(k);
-    std::vector<char> done(xms.size(), 0);
-    for (size_t i0 = 0; i0 < xms.size(); ++i0) {
-      if (done[i0]) continue;
-      std::vector<uint64_t> B;
-      for (int b = 0; b < std::min(4, n); ++b) B.push_back(1ull << b);
-      for (size_t q = i0; q < xms.size() && (int)B.size() < Tmax; ++q) {
-        if (done[q]) continue;
-        const uint64_t v = reduce(B, xms[q], nullptr);
-        if (v) B.push_back(v);
-      }
-      B = make_basis(B);
-      std::vector<std::pair<uint64_t, int>> keyed;  // ((xc << 1) | im, slot)
-      for (size_t q = i0; q < xms.size(); ++q) {
-        if (done[q]) continue;
-        uint32_t xc = 0;
-        if (reduce(B, xms[q], &xc)) continue;  // outside this span
-        done[q] = 1;
-        for (int k : by_xm[xms[q]]) keyed.push_back({((uint64_t)xc << 1) | (uint64_t)slots[k].im, k});
-      }
-      std::stable_sort(keyed.begin(), keyed.end(),
-                       [](const std::pair<uint64_t, int>& x, const std::pair<uint64_t, int>& y) { return x.first < y.first; });
-      for (size_t c = 0; c < keyed.size(); c += PS_MAX) {
-        Pass P{B, {}};
-        for (size_t q = c; q < std::min(keyed.size(), c + PS_MAX); ++q) P.sl.push_back(keyed[q].second);
-        passes.push_back(P);
-      }
-    }
-    // |a|^2 slots: into free places, then passes over tiles of qubits 0..T-1
-    std::vector<int> zs;
-    for (int k = 0; k < (int)slots.size(); ++k)
-      if (!slots[k].xm) zs.push_back(k);
-    size_t zi = 0;
-    for (auto& P : passes)
-      while (zi < zs.size() && (int)P.sl.size() < PS_MAX) P.sl.insert(P.sl.begin(), zs[zi++]);
-    while (zi < zs.size()) {
-      Pass P{make_basis({}), {}};
-      while (zi < zs.size() && (int)P.sl.size() < PS_MAX) P.sl.push_back(zs[zi++]);
-      passes.push_back(P);
-    }
+    const PauliPlan plan = plan_pauli(n, xmv.data(), zmv.data(), nt);
+    const auto& slots = plan.slots;
+    const auto& passes = plan.passes;
+    const auto& tslot = plan.tslot;
+    const auto& ttot = plan.ttot;
+    const auto& tmult = plan.tmult;
     // launch
     const size_t nslots = slots.size();
     std::vector<int> gidx(nslots, -1);
@@ -1047,12 +949,12 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
       g.ntiles = 1ull << (n - g.T);
       for (int q = 0; q < g.T; ++q) {
         g.bm[q] = P.bm[q];
-        g.lead[q] = lead_bit(P.bm[q]);
+        g.lead[q] = pp_lead(P.bm[q]);
       }
       g.nt = (int)P.sl.size();
       g.nz = 0;
       for (int q = 0; q < g.nt; ++q) {
-        const Slot& sl = slots[P.sl[q]];
+        const PauliSlot& sl = slots[P.sl[q]];
         gidx[P.sl[q]] = next + q;
         g.zm[q] = sl.zm;
         g.im[q] = (uint8_t)sl.im;
@@ -1065,7 +967,7 @@ static int pauli_exact(qs_state* s, const qs_pauli* terms, size_t nterms, double
           g.top[q] = 0;
         } else {
           uint32_t xc = 0;
-          reduce(P.bm, sl.xm, &xc);
+          pp_reduce(P.bm, sl.xm, &xc);
           g.xc[q] = xc;
           g.top[q] = 31 - __builtin_clz(xc);
         }
