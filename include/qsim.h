@@ -391,6 +391,9 @@ int qs_expect_pauli(const qs_state* s, const qs_pauli* terms, size_t nterms, dou
  * is the left-to-right prefix of the block totals); the sample is the smallest x
  * with E_b + (left-to-right partial sum of block b up to x) > u_s, or, when no x
  * qualifies, the largest x with p_x > 0.
+ * The search within a block starts from the running sum kept after every 32
+ * amplitudes (2^n / 32 doubles of stream-ordered scratch, freed when the call
+ * returns), which continues the same left-to-right additions.
  * out[s] (uint64, device or host memory) receives the basis index of shot s. */
 int qs_sample(const qs_state* s, uint64_t seed, uint64_t shots, uint64_t* out, int on_device);
 

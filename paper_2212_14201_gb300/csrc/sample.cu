@@ -10,11 +10,14 @@
 //   shot s -> smallest x in the first block b with E_{b+1} > u_s such that
 //             E_b + (left-to-right partial sum of block b up to x) > u_s;
 //             if no block qualifies, the largest x with p_x > 0.
-// Kernels: block totals (one thread per block, sequential), the superblock
-// prefixes (one CTA per superblock, its sequential sum staged through shared
-// memory), the prefix of the superblock totals (one CTA), the offset of every
-// superblock's prefixes, and one thread per shot (binary search over E, then a
-// sequential scan of one block).
+// Kernels: block totals (one thread per block, sequential; the running sum is
+// also kept after every K = min(32, L) amplitudes), the superblock prefixes (one
+// CTA per superblock, its sequential sum staged through shared memory), the
+// prefix of the superblock totals (one CTA), the offset of every superblock's
+// prefixes, and one thread per shot (binary search over E, then over the block's
+// running-sum checkpoints, then a sequential scan of at most K amplitudes that
+// continues the block's left-to-right sum from the checkpoint before them: the
+// same additions in the same order as a scan from the block's start).
 #include <algorithm>
 
 #include "internal.h"
@@ -23,10 +26,13 @@ namespace qs {
 
 __device__ __forceinline__ double p_exact(double2 a) { return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)); }
 
-// T[b] = left-to-right block total; lastnz[b] = largest x in block b with p_x > 0, or -1.
+// T[b] = left-to-right block total; lastnz[b] = largest x in block b with p_x > 0,
+// or -1; cp[b * (L / K) + m] = the running sum after amplitude (m + 1) K - 1 of the
+// block (K = min(32, L); the last checkpoint is T[b]).
 template <class A>
-__global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, double* __restrict__ T,
-                               long long* __restrict__ lastnz) {
+__global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, int64_t K, double* __restrict__ T,
+                               long long* __restrict__ lastnz, double* __restrict__ cp) {
+  const int64_t M = L / K;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
     const A* p = a + b * L;
     double S = 0.0;
@@ -40,8 +46,10 @@ __global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, d
       if (j + 1 < L) { double q = p_exact(v1); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 1; }
       if (j + 2 < L) { double q = p_exact(v2); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 2; }
       if (j + 3 < L) { double q = p_exact(v3); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 3; }
+      if (K >= 4 && ((j + 4) & (K - 1)) == 0 && j + 4 < L) cp[b * M + (j + 4) / K - 1] = S;
     }
     T[b] = S;
+    cp[b * M + M - 1] = S;
     lastnz[b] = last;
   }
 }
@@ -117,7 +125,9 @@ __global__ void k_seg_offset(double* __restrict__ E, int64_t nb, int G, const do
 
 template <class A>
 __global__ void k_sample(const A* __restrict__ a, const double* __restrict__ E, const long long* __restrict__ lastnz,
-                         int64_t nb, int64_t L, uint64_t seed, uint64_t shots, uint64_t* __restrict__ out) {
+                         const double* __restrict__ cp, int64_t nb, int64_t L, int64_t K, uint64_t seed,
+                         uint64_t shots, uint64_t* __restrict__ out) {
+  const int64_t M = L / K;
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < shots; s += (uint64_t)gridDim.x * blockDim.x) {
     double u = u01_of(splitmix64(seed, s));
     int64_t lo = 0, hi = nb;
@@ -132,14 +142,24 @@ __global__ void k_sample(const A* __restrict__ a, const double* __restrict__ E, 
     }
     const int64_t b = lo;
     const double eb = E[b];
-    const A* p = a + b * L;
-    double S = 0.0;
+    const double* c = cp + b * M;
+    // first K-run whose end passes u (E_b + running sum is nondecreasing in x)
+    int64_t lo2 = 0, hi2 = M;
+    while (lo2 < hi2) {
+      const int64_t mid = lo2 + ((hi2 - lo2) >> 1);
+      if (__dadd_rn(eb, c[mid]) > u) hi2 = mid;
+      else lo2 = mid + 1;
+    }
     int64_t pick = b * L + L - 1;
-    for (int64_t j = 0; j < L; ++j) {
-      S = __dadd_rn(S, p_exact(ld_amp(p, j)));
-      if (__dadd_rn(eb, S) > u) {
-        pick = b * L + j;
-        break;
+    if (lo2 < M) {
+      const A* p = a + b * L;
+      double S = lo2 ? c[lo2 - 1] : 0.0;
+      for (int64_t j = lo2 * K; j < lo2 * K + K; ++j) {
+        S = __dadd_rn(S, p_exact(ld_amp(p, j)));
+        if (__dadd_rn(eb, S) > u) {
+          pick = b * L + j;
+          break;
+        }
       }
     }
     out[s] = (uint64_t)pick;
@@ -168,11 +188,21 @@ extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint
   double* P = Ssb + (nsb + 1);                 // superblock prefixes
   long long* lsb = (long long*)(P + (nsb + 1));
   long long* lall = lsb + (nsb + 1);
+  const int64_t K = L < 32 ? L : 32;  // amplitudes per running-sum checkpoint
+  struct StreamBuf {                   // freed on the stream when the call returns
+    void* p = nullptr;
+    cudaStream_t st;
+    ~StreamBuf() {
+      if (p) cudaFreeAsync(p, st);
+    }
+  } cpb{nullptr, s->stream};
+  QS_CUDA(cudaMallocAsync(&cpb.p, (size_t)(N / K) * sizeof(double), s->stream));  // 1/64 of the state's bytes
+  double* cp = (double*)cpb.p;
   int g1 = (int)std::min<int64_t>((nb + 127) / 128, 152 * 16);
   KTimer kt(s, QS_K_REDUCE, s->n, 3, 0, 0, (double)N, 4.0 * (double)N);
   note_launch(4);
   with_amps(s, [&](auto* a) {
-    k_block_totals<<<g1, 128, 0, s->stream>>>(a, nb, L, T, lastnz);
+    k_block_totals<<<g1, 128, 0, s->stream>>>(a, nb, L, K, T, lastnz, cp);
     return QS_OK;
   });
   QS_TRY(launch_check("block_totals"));
@@ -184,10 +214,13 @@ extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint
   k_seg_offset<<<g2, 256, 0, s->stream>>>(E, nb, (int)G, P, lall, lastnz);
   QS_TRY(launch_check("superblock offset"));
   uint64_t* dout = out;
-  if (!on_device) QS_CUDA(cudaMallocAsync((void**)&dout, shots * sizeof(uint64_t), s->stream));
+  if (!on_device) {
+    const cudaError_t e = cudaMallocAsync((void**)&dout, shots * sizeof(uint64_t), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(samples)");
+  }
   int g3 = (int)std::min<uint64_t>((shots + 127) / 128, 152 * 16);
   with_amps(s, [&](auto* a) {
-    k_sample<<<g3, 128, 0, s->stream>>>(a, E, lastnz, nb, L, seed, shots, dout);
+    k_sample<<<g3, 128, 0, s->stream>>>(a, E, lastnz, cp, nb, L, K, seed, shots, dout);
     return QS_OK;
   });
   int rc = launch_check("sample");
