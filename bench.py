@@ -685,7 +685,8 @@ def run_ours(args, world, rank, local, pg):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64",
         "dtype_note": "complex128 state in HBM; gate arithmetic in Q60 fixed point (int64 limbs, 2^-60 "
-                      "resolution) on the integer pipe; reductions and sampling in f64",
+                      "resolution) on the integer pipe; the squared norm as exact integer sums of the Q60 "
+                      "squares; sampling in f64 by its canonical definition",
         "data": "synthetic",
         "config": {"workload": f"layered U3+CZ brickwork, n={n}, depth {args.depth} ({ng} gates), "
                                f"norm + {SHOTS} samples", "n": n, "gates": ng, "shots": SHOTS,
