@@ -477,7 +477,7 @@ __global__ void k_pauli_finish(const double* __restrict__ part, int nblocks, int
 // then every pair slot whose X mask lies in the span from shared memory.  A slot
 // (xm, zm, part) accumulates pos = the sum of its values v (Re w, Im w or |a|^2)
 // over pairs with s0 = +1; the term is mult * (2 pos - tot), tot = the same sum
-// with zm = 0 (its own slot).
+// with zm = 0 (its own slot).  The passes are planned on the host (pauli_plan.h).
 struct PTile {
   uint64_t ntiles;          // 2^(n - T)
   int T;                    // tile coordinates, ordered by leading bit
