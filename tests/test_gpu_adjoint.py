@@ -1,12 +1,14 @@
 """GPU parity of the adjoint gradient (qs_adjoint_grad and the torch.autograd
 binding) against the CPU oracle's adjoint recursion, parameter shift and central
-finite differences.  Gradients within 1e-9 relative; energies within 1e-12."""
+finite differences.  Every gradient entry within 1e-9 relative (plus the derived
+rounding floor of tests/_tol.py for entries that vanish); energies within 1e-12."""
 import math
 
 import numpy as np
 import pytest
 
 import workloads as w
+from tests._tol import grad_close, grad_report, h1_of
 
 pytestmark = pytest.mark.gpu
 
@@ -30,9 +32,12 @@ def gpu_grad(q, n, g, th, H, arith=None):
         q.qs_free(h)
 
 
-def rel_close(a, b, rel=1e-9):
-    a, b = np.asarray(a), np.asarray(b)
-    return float(np.max(np.abs(a - b))) <= rel * max(1.0, float(np.max(np.abs(b))))
+def rel_close(a, b, n, gates, terms):
+    """Element-wise: |a - b| <= 1e-9 |b| + floor(n, G, ||H||_1)."""
+    ok = grad_close(a, b, n, len(gates), h1_of(terms))
+    if not ok:
+        print(grad_report(a, b, n, len(gates), h1_of(terms)))
+    return ok
 
 
 @pytest.mark.parametrize("arith", ["fp64", "q60"])
@@ -45,7 +50,7 @@ def test_adjoint_matches_oracle(q, orc, arith, n, layers, ham):
     e, grad = gpu_grad(q, n, g, th, H, mode)
     e0, g0 = orc.adjoint_grad(n, g, th, H)
     assert abs(e - e0) < 1e-12
-    assert rel_close(grad, g0)
+    assert rel_close(grad, g0, n, g, H)
 
 
 def test_n12_against_parameter_shift_and_finite_differences(q, orc):
@@ -63,7 +68,7 @@ def test_n12_against_parameter_shift_and_finite_differences(q, orc):
         tp[k] += math.pi / 2
         tm[k] -= math.pi / 2
         shift = 0.5 * (orc.energy(n, g, tp, H) - orc.energy(n, g, tm, H))
-        assert abs(grad[k] - shift) <= 1e-9 * max(1.0, abs(shift))
+        assert rel_close(grad[k:k + 1], [shift], n, g, H)
         h = 1e-6
         tp, tm = th.copy(), th.copy()
         tp[k] += h
@@ -84,7 +89,7 @@ def test_controlled_daggered_and_shared_parameters(q, orc):
     H = w.random_paulis(n, 9, 2)
     e, grad = gpu_grad(q, n, g, th, H)
     e0, g0 = orc.adjoint_grad(n, g, th, H)
-    assert abs(e - e0) < 1e-12 and rel_close(grad, g0)
+    assert abs(e - e0) < 1e-12 and rel_close(grad, g0, n, g, H)
 
 
 def test_rejects_unsupported_parameter(q):
@@ -110,7 +115,9 @@ def test_torch_autograd_function(q, orc):
     (2.0 * e).backward()
     e0, g0 = orc.adjoint_grad(n, g, th.detach().numpy(), H)
     assert abs(e.item() - e0) < 1e-12
-    assert rel_close(th.grad.numpy(), 2.0 * g0)
+    H2 = H.copy()
+    H2["coef"] *= 2.0  # the loss is 2 E
+    assert rel_close(th.grad.numpy(), 2.0 * g0, n, g, H2)
     f.close()
 
 
@@ -144,9 +151,25 @@ def test_full_size_adjoint_invariants(q):
         tp[k] += math.pi / 2
         tm[k] -= math.pi / 2
         shift = 0.5 * (energy(tp) - energy(tm))
-        assert abs(grad[k] - shift) <= 1e-9 * max(1.0, abs(shift))
+        assert rel_close(grad[k:k + 1], [shift], n, g, H)
     finally:
         q.qs_free(h)
+
+
+def test_config4_full_depth_against_oracle(q, orc):
+    """The adjoint workload's circuit (12 layers of RY, RZ and the CNOT ring; ZZ
+    chain) at the largest size the oracle's adjoint recursion finishes in about a
+    minute, n=24 (864 gates, 576 parameters): energy within 1e-12 and every
+    gradient entry within 1e-9 relative of the oracle's, fused backward (Q60)."""
+    n, layers = 24, 12
+    g, npar = w.hea_ansatz(n, layers)
+    th = w.uniform_angles(npar, 4)
+    H = w.zz_chain(n)
+    e, grad = gpu_grad(q, n, g, th, H)
+    e0, g0 = orc.adjoint_grad(n, g, th, H)
+    print(f"n={n} energy err {abs(e - e0):.3e}; " + grad_report(grad, g0, n, len(g), h1_of(H)))
+    assert abs(e - e0) < 1e-12
+    assert rel_close(grad, g0, n, g, H)
 
 
 @pytest.mark.parametrize("n,layers", [(9, 3), (13, 4)])
@@ -161,7 +184,7 @@ def test_per_gate_backward_path(q, orc, n, layers):
     finally:
         q.qs_set_adjoint_fused(True)
     e0, g0 = orc.adjoint_grad(n, g, th, H)
-    assert abs(e - e0) < 1e-12 and rel_close(grad, g0)
+    assert abs(e - e0) < 1e-12 and rel_close(grad, g0, n, g, H)
 
 
 @pytest.mark.parametrize("n,layers", [(3, 2), (8, 3), (13, 3)])
@@ -176,4 +199,4 @@ def test_fused_backward_groups_and_pairs(q, orc, n, layers):
     e0, g0 = orc.adjoint_grad(n, g, th, H)
     for arith in (q.ARITH_FIXED, q.ARITH_FP64):
         e, grad = gpu_grad(q, n, g, th, H, arith)
-        assert abs(e - e0) < 1e-12 and rel_close(grad, g0), arith
+        assert abs(e - e0) < 1e-12 and rel_close(grad, g0, n, g, H), arith

@@ -311,6 +311,58 @@ def test_sampler_bit_exact(q, orc, n, seed):
         q.qs_free(h)
 
 
+def _canonical_cdf(orc, st, n):
+    """The canonical sampler's decision values on a state array (interleaved f64):
+    E[b] (block prefixes, from the oracle) and C_x = E[b] + left-to-right partial
+    sum of p within x's block (numpy's accumulate is sequential, p = re*re + im*im
+    with separate roundings, as in the oracle)."""
+    E = orc.block_prefix(st, n)
+    re, im = st[0::2], st[1::2]
+    p = re * re + im * im
+    L = min(1024, 1 << n)
+    S = np.add.accumulate(p.reshape(-1, L), axis=1)
+    return E, (E[:-1, None] + S).reshape(-1)
+
+
+@pytest.mark.parametrize("n,seed,fused", [(12, 0, False), (20, 6, True)])
+def test_sampler_cross_state_explained_flips(q, orc, n, seed, fused):
+    """Samples of the GPU-computed state against samples of the oracle-computed
+    state (the same program, computed independently on both sides): a shot may
+    differ only where its draw u_s lies between the two sides' decision values at
+    a boundary between the two picks (min(C_x, C'_x) <= u_s < max(C_x, C'_x), or
+    the same for a block prefix).  Any other mismatch fails."""
+    g = w.random_circuit(n, 200, seed)
+    shots, sseed = 1_000_000, 31 + seed
+    ref = orc.run(n, g)
+    plan = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5) if fused else None
+    h = q.qs_alloc(n)
+    try:
+        q.qs_apply(h, g, None, plan)
+        got = q.qs_sample(h, sseed, shots)
+        st = q.qs_get_state(h).view(np.float64).copy()
+    finally:
+        q.qs_free(h)
+        if plan is not None:
+            q.qs_plan_free(plan)
+    # the definition on the GPU's own state: bit-exact
+    assert np.array_equal(got, orc.sample(st, n, sseed, shots))
+    want = orc.sample(ref, n, sseed, shots)
+    bad = np.nonzero(got != want)[0]
+    if bad.size:
+        Eg, Cg = _canonical_cdf(orc, st, n)
+        Eo, Co = _canonical_cdf(orc, ref, n)
+        L = min(1024, 1 << n)
+        for s in bad:
+            u = (orc.splitmix64(sseed, int(s)) >> 11) * 2.0 ** -53
+            lo, hi = sorted((int(got[s]), int(want[s])))
+            xs = np.arange(lo, hi + 1)
+            straddle = np.any((np.minimum(Cg[xs], Co[xs]) <= u) & (u < np.maximum(Cg[xs], Co[xs])))
+            bs = np.arange(lo // L, hi // L + 1)
+            straddle |= bool(np.any((np.minimum(Eg[bs + 1], Eo[bs + 1]) <= u) & (u < np.maximum(Eg[bs + 1], Eo[bs + 1]))))
+            assert straddle, f"shot {s}: GPU {got[s]} oracle {want[s]} not explained by the two states' rounding"
+    print(f"n={n}: {bad.size} explained flips in {shots} shots")
+
+
 def test_sampler_edge_states(q, orc):
     n = 5
     for amps in [np.zeros(1 << n, dtype=np.complex128), None]:

@@ -135,6 +135,52 @@ def test_full_size_fused_vs_plain_and_invariants(q):
         q.qs_plan_free(p)
 
 
+def _amp_errors(got, ref, chunk=1 << 24):
+    """max |got - ref|, and max |got - ref| / |ref| over entries with |ref| >= 2^-20,
+    in chunks (the full n=30 arrays are 16 GiB each)."""
+    mabs = 0.0
+    mrel = 0.0
+    for o in range(0, got.size, chunk):
+        a = got[o:o + chunk]
+        b = ref[o:o + chunk]
+        d = np.abs(a - b)
+        mabs = max(mabs, float(d.max()))
+        ab = np.abs(b)
+        big = ab >= 2.0 ** -20
+        if np.any(big):
+            mrel = max(mrel, float((d[big] / ab[big]).max()))
+    return mabs, mrel
+
+
+def test_config1_full_state_against_oracle_n30(q, orc):
+    """The benchmark workload at its full size (n=30, depth-20 U3 + CZ brickwork,
+    890 gates, seed 1): every one of the 2^30 amplitudes of the fused Q60 path
+    (greedy plan, the benchmark's launch configuration), of plain per-gate Q60
+    and of plain per-gate FP64 within 1e-12 of the CPU oracle's state."""
+    n = 30
+    g = w.layered_u3_cz(n, 20, 1)
+    ref = orc.as_complex(orc.run(n, g))
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc(n)
+    got = np.empty(1 << n, dtype=np.complex128)
+    try:
+        results = {}
+        for name, plan, arith in (("fused_q60", p, q.ARITH_FIXED), ("plain_q60", None, q.ARITH_FIXED),
+                                  ("plain_fp64", None, q.ARITH_FP64)):
+            q.qs_set_zero(h)
+            q.qs_set_arith(h, arith)
+            q.qs_apply(h, g, None, plan)
+            q.qs_get_state(h, got)
+            results[name] = _amp_errors(got, ref)
+            print(f"n=30 config-1 {name}: max abs err {results[name][0]:.3e}, "
+                  f"max rel err (|a|>=2^-20) {results[name][1]:.3e}")
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(p)
+    for name, (mabs, _) in results.items():
+        assert mabs < TOL, name
+
+
 @pytest.mark.parametrize("bits", [3, 4])
 def test_register_phase_kernels(q, orc, bits):
     """The register-phase tile kernels (runs of ops on 2^bits amplitudes per thread)
