@@ -244,11 +244,13 @@ int qs_set_phase_tables(int on);
  * with tables fused, 2 pairs without table fusion, 0 neither.  Always QS_OK. */
 int qs_set_rotation_pairs(int on);
 
-/* Process-wide choice of the Q60 tile-pass kernel: bits = 3 or 4 groups the ops
- * of a pass into register phases (runs of ops whose targets fit in `bits` tile
- * qubits execute on the 2^bits amplitudes a thread holds in registers); 0
- * (default) runs one shared-memory sweep per op.  All give the same amplitudes;
- * the switch is for measurement.  Errors: INVALID_ARG for other values. */
+/* Process-wide choice of the Q60 tile-pass kernel: bits = 4 (default) runs the
+ * register-phase engine (the ops of a pass grouped into phases of four tile
+ * qubits; each thread applies a phase's ops to the 16 amplitudes it holds in
+ * registers, one shared-memory exchange per phase; tiles of 4..12 qubits); 0
+ * runs one shared-memory sweep per op.  Both give the amplitudes within the Q60
+ * rounding; the switch is for measurement.  Errors: INVALID_ARG for other
+ * values. */
 int qs_set_register_phases(int bits);
 
 /* Greedy plan with an explicit tile width: tiles of tile_qubits (4..13) qubits,
@@ -285,6 +287,27 @@ typedef struct qs_pass_op {
 int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
                      int q60, qs_pass_op* ops, size_t cap, size_t* count, double* tables, size_t table_cap,
                      size_t* ntables);
+
+/* Register program of a tile pass on the Q60 register-phase engine (the
+ * kernel behind Q60 tile passes of 4..12 qubits; Section "Quantum circuit
+ * fusion" with the gate work in on-chip memory, Section "GPU optimization"),
+ * host only: the pass's op list (qs_plan_pass_ops, q60 = 1) regrouped into
+ * register phases.  A phase holds four tile qubits in registers (reg_bits, a
+ * mask over tile bits); its ops run there in order, after reordering only ops
+ * that commute.  Each step names the op(s) of the list it runs: src0 (and
+ * src1, the second rotation of a pair: kind 0), and table_src, a phase-table op
+ * that runs just before the pair inside it (-1 if none).  kind: 0 pair of real
+ * rotations, 1 real 2x2, 2 general 2x2, 3 antidiagonal, 4 diagonal, 5 |1>
+ * phase, 6 diagonal on a qubit outside the phase's registers, 7 phase table.
+ * Up to cap steps are written; *count receives the total.  Errors: INVALID_ARG
+ * (NULL pointers, pass out of range or a per-gate pass, plan/program mismatch),
+ * UNSUPPORTED (tile width outside 4..12). */
+typedef struct qs_reg_step {
+  int32_t phase, kind, src0, src1, table_src;
+  uint32_t reg_bits;
+} qs_reg_step;
+int qs_plan_pass_program(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
+                         qs_reg_step* steps, size_t cap, size_t* count);
 
 /* ---- learned fusion cost model (not in the paper, whose fusion has no cost
  * model): a 3-layer tanh perceptron h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),

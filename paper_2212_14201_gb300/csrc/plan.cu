@@ -13,6 +13,7 @@
 // common qubit commute when both touch it diagonally.  Diagonal gates join any
 // pass (their target may lie outside Q: a per-tile scalar).
 #include <math.h>
+#include <stddef.h>
 
 #include <string.h>
 
@@ -20,6 +21,7 @@
 #include <new>
 #include <vector>
 
+#include "regtile.h"
 #include "tile.h"
 
 using namespace qs;
@@ -825,11 +827,9 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
   return QS_OK;
 }
 
-// Register phases for the Q60 tile kernel: consecutive ops are grouped while their
-// non-diagonal targets fit in `rb` tile bits; each phase is then padded to rb
-// bits with unused tile bits (highest first, which keeps shared-memory accesses of
-// a warp on consecutive low bits).  g_register_bits = 0 disables the phases.
-static int g_register_bits = 0;
+// Register-phase tile engine (tile_q60.cu) for Q60 passes: 4 = on (default), 0 =
+// the per-op shared-memory engine (k_tile<EngQ60>), kept for measurement.
+static int g_register_bits = 4;
 static bool g_aggregate = true;
 static bool g_rotation_pairs = true;
 static bool g_fuse_tables = true;
@@ -845,39 +845,8 @@ extern "C" int qs_set_aggregate(int on) {
   return QS_OK;
 }
 
-static void build_phases(TileArgs* g, int rb) {
-  int np = 0;
-  uint32_t P = 0;
-  int begin = 0;
-  g->reg_bits = rb;
-  auto close = [&](int end) {
-    if (end <= begin) return;
-    uint32_t full = P;
-    for (int b = g->m - 1; b >= 0 && __builtin_popcount(full) < rb; --b) full |= 1u << b;
-    TilePhase& ph = g->phases[np++];
-    int i = 0;
-    for (int b = 0; b < g->m; ++b)
-      if ((full >> b) & 1) ph.b[i++] = (uint8_t)b;
-    ph.op_begin = (int16_t)begin;
-    ph.op_end = (int16_t)end;
-    begin = end;
-    P = 0;
-  };
-  for (int k = 0; k < g->nops; ++k) {
-    const TileOp& op = g->ops[k];
-    const bool nondiag = op.kind == TOP_ANTI || op.kind == TOP_REAL || op.kind == TOP_GENERAL;
-    if (!nondiag) continue;
-    const uint32_t t = 1u << op.tb;
-    if (P & t) continue;
-    if (__builtin_popcount(P) == rb) close(k);
-    P |= t;
-  }
-  close(g->nops);
-  g->nphases = np;
-}
-
 extern "C" int qs_set_register_phases(int bits) {
-  if (bits != 0 && bits != 3 && bits != 4) return fail(QS_ERR_INVALID_ARG, "register bits %d: use 0, 3 or 4", bits);
+  if (bits != 0 && bits != 4) return fail(QS_ERR_INVALID_ARG, "register bits %d: use 0 or 4", bits);
   g_register_bits = bits;
   return QS_OK;
 }
@@ -964,7 +933,7 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
       if (op.cls != OP_IDENTITY) rops->push_back(op);
     }
   }
-  if (tables_ok && g_aggregate && g_phase_tables && g_register_bits == 0) {
+  if (tables_ok && g_aggregate && g_phase_tables) {
     std::vector<Op1> x;
     std::vector<PhaseTable> t;
     extract_phases(*rops, local, n, m, &x, &t);
@@ -974,6 +943,322 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
       ptables->swap(t);
     }
   }
+  return QS_OK;
+}
+
+// ---- register programs (Q60 register-phase engine, tile_q60.cu) --------------------
+// The pass's op list becomes register phases (regprog.h); inside a phase,
+// consecutive uncontrolled real rotations on two register bits become one PAIR
+// (a real 4x4), and a phase table directly before such a pair runs inside it.
+// Each table use gets a copy of the table in the order its phase's threads read
+// it.  steps[] records, per emitted op, which ops of the list it runs (for the
+// host tests of qs_plan_pass_program).
+struct RtProgram {
+  std::vector<RtPhase> phases;
+  std::vector<RtOp> ops;
+  std::vector<int> ncoef;                 // coefficient limb pairs of each op
+  std::vector<QL> coef;
+  std::vector<qs_reg_step> steps;         // parallel to ops
+  std::vector<std::pair<int, int>> uses;  // (table index, phase index) of RtOp.table
+  double int_ops = 0.0;                   // limb products per amplitude of the state
+};
+
+static int build_rt_program(int n, const std::vector<Op1>& rops, const int* local, int m, RtProgram* pr) {
+  std::vector<RpIn> in;
+  std::vector<int> src;
+  for (size_t i = 0; i < rops.size(); ++i) {
+    const Op1& o = rops[i];
+    if (o.cls == OP_IDENTITY) continue;
+    RpIn x{IK_DIAG, -1, 0};
+    if (o.cls == kTableMark) {
+      x.kind = IK_TABLE;
+    } else {
+      for (int b = 0; b < n; ++b)
+        if (((o.cmask >> b) & 1) && local[b] >= 0) x.lcm |= 1u << local[b];
+      x.tb = local[o.target];
+      if (o.cls == OP_ANTI || o.cls == OP_REAL || o.cls == OP_GENERAL) {
+        if (x.tb < 0)
+          return fail(QS_ERR_INVALID_ARG, "plan does not match the program (non-diagonal op on qubit %d outside its tile)",
+                      o.target);
+        x.kind = IK_MIX;
+      }
+    }
+    in.push_back(x);
+    src.push_back((int)i);
+  }
+  const std::vector<RpPhase> phases = rp_build_phases(in, m);
+  for (size_t p = 0; p < phases.size(); ++p) {
+    const RpPhase& rp = phases[p];
+    RtPhase ph;
+    memset(&ph, 0, sizeof ph);
+    int reg[32];
+    for (int b = 0; b < 32; ++b) reg[b] = -1;
+    int r = 0;
+    for (int b = 0; b < m; ++b)
+      if ((rp.P >> b) & 1) {
+        ph.rb[r] = (uint8_t)b;
+        reg[b] = r++;
+      }
+    if (r != RP_BITS) return fail(QS_ERR_INVALID_ARG, "internal: register phase with %d bits", r);
+    rp_group_bits(rp.P, m, ph.gl);
+    ph.op_begin = (uint16_t)pr->ops.size();
+    auto src_op = [&](int k) -> const Op1& { return rops[src[rp.ops[k]]]; };
+    auto pairable = [&](size_t k) {
+      if (k + 1 >= rp.ops.size()) return false;
+      const Op1& a = src_op((int)k);
+      const Op1& b = src_op((int)k + 1);
+      return a.cls == OP_REAL && b.cls == OP_REAL && a.cmask == 0 && b.cmask == 0 && a.target != b.target;
+    };
+    auto new_op = [&](int kind, int ncoef, int s0, int s1, int tsrc) -> RtOp& {
+      RtOp o;
+      memset(&o, 0, sizeof o);
+      o.kind = (uint8_t)kind;
+      o.table = -1;
+      o.coef = (uint16_t)pr->coef.size();
+      pr->ops.push_back(o);
+      pr->ncoef.push_back(ncoef);
+      qs_reg_step st;
+      st.phase = (int32_t)p;
+      st.kind = kind;
+      st.src0 = s0;
+      st.src1 = s1;
+      st.table_src = tsrc;
+      st.reg_bits = rp.P;
+      pr->steps.push_back(st);
+      return pr->ops.back();
+    };
+    auto add_table_use = [&](int table) {
+      pr->uses.push_back({table, (int)p});
+      return (int16_t)(pr->uses.size() - 1);
+    };
+    auto qc_push = [&](const C2& z, bool gauss) {
+      const QC c = gauss ? qc_make_gauss(z.re, z.im) : qc_make(z.re, z.im);
+      pr->coef.push_back(c.re);
+      pr->coef.push_back(c.im);
+      pr->coef.push_back(c.nim);
+    };
+    for (size_t k = 0; k < rp.ops.size(); ++k) {
+      const Op1& o = src_op((int)k);
+      const int sk = src[rp.ops[k]];
+      int tab = -1, tsrc = -1;
+      if (o.cls == kTableMark) {
+        if (g_fuse_tables && pairable(k + 1)) {
+          tab = o.target;
+          tsrc = sk;
+          ++k;  // the pair follows
+        } else {
+          RtOp& t = new_op(RK_TABLE, 0, sk, -1, -1);
+          t.table = add_table_use(o.target);
+          pr->int_ops += 9.0;
+          continue;
+        }
+      }
+      const Op1& a = src_op((int)k);
+      const int sa = src[rp.ops[k]];
+      if (pairable(k) && g_rotation_pairs) {
+        const Op1& b = src_op((int)k + 1);
+        const int sb2 = src[rp.ops[k + 1]];
+        const int ra = reg[local[a.target]], rb2 = reg[local[b.target]];
+        const Op1& lo = ra < rb2 ? a : b;
+        const Op1& hi = ra < rb2 ? b : a;
+        RtOp& t = new_op(RK_PAIR, 16, sa, sb2, tsrc);
+        t.r0 = (uint8_t)std::min(ra, rb2);
+        t.r1 = (uint8_t)std::max(ra, rb2);
+        if (tab >= 0) t.table = add_table_use(tab);
+        for (int qo = 0; qo < 4; ++qo)
+          for (int qi = 0; qi < 4; ++qi) {
+            const double v = hi.m.m[2 * (qo >> 1) + (qi >> 1)].re * lo.m.m[2 * (qo & 1) + (qi & 1)].re;
+            pr->coef.push_back(q60_split(q60_from_double(v)));
+          }
+        pr->int_ops += 24.0 + (tab >= 0 ? 9.0 : 0.0);
+        ++k;
+        continue;
+      }
+      if (tab >= 0) {  // no pair after all (rotation pairs switched off): the table on its own
+        RtOp& t = new_op(RK_TABLE, 0, tsrc, -1, -1);
+        t.table = add_table_use(tab);
+        pr->int_ops += 9.0;
+      }
+      uint32_t lcm = 0;
+      uint64_t ext = 0;
+      for (int b = 0; b < n; ++b)
+        if ((a.cmask >> b) & 1) {
+          if (local[b] >= 0) lcm |= 1u << local[b];
+          else ext |= 1ull << b;
+        }
+      uint32_t cr = 0, gm = 0;
+      for (int b = 0; b < m; ++b)
+        if ((lcm >> b) & 1) {
+          if (reg[b] >= 0) cr |= 1u << reg[b];
+          else gm |= 1u << b;
+        }
+      const int tb = local[a.target];
+      int kind;
+      bool in_reg = tb >= 0 && reg[tb] >= 0;
+      switch (a.cls) {
+        case OP_REAL: kind = RK_REAL; break;
+        case OP_GENERAL: kind = RK_GEN; break;
+        case OP_ANTI: kind = RK_ANTI; break;
+        case OP_DIAG: kind = in_reg ? RK_DIAG : RK_SCAL; break;
+        default: kind = in_reg ? RK_PH1 : RK_SCAL; break;
+      }
+      RtOp& t = new_op(kind, kind == RK_REAL ? 4 : 12, sa, -1, -1);
+      t.ext = ext;
+      t.gmask = (uint16_t)gm;
+      t.cr = (uint8_t)cr;
+      t.code0 = (uint8_t)(a.cls == OP_PHASE1 ? U_ONE : a.code0);
+      t.code1 = (uint8_t)a.code1;
+      if (kind == RK_SCAL) {
+        t.sout = tb < 0 ? 1 : 0;
+        t.sbit = (uint8_t)(tb < 0 ? a.target : tb);
+      } else {
+        t.r0 = (uint8_t)reg[tb];
+      }
+      if (kind == RK_REAL) {
+        for (int e = 0; e < 4; ++e) pr->coef.push_back(q60_split(q60_from_double(a.m.m[e].re)));
+      } else {
+        for (int e = 0; e < 4; ++e) qc_push(a.m.m[e], kind == RK_GEN);
+      }
+      pr->int_ops += class_touch_fraction(a) * op_int_ops_per_amp(a);
+    }
+    ph.op_end = (uint16_t)pr->ops.size();
+    pr->phases.push_back(ph);
+  }
+  return QS_OK;
+}
+
+// Tile index of register index k of group g in a phase.
+static uint32_t rt_index(const RtPhase& ph, int m, uint32_t g, uint32_t k) {
+  uint32_t j = 0;
+  for (int i = 0; i + RP_BITS < m; ++i) j |= ((g >> i) & 1u) << ph.gl[i];
+  for (int r = 0; r < RP_BITS; ++r) j |= ((k >> r) & 1u) << ph.rb[r];
+  return j;
+}
+
+// Device copy of the program's table uses (int4 entries, thread-major), through
+// the state's pinned staging buffer (see upload_tables for the ordering rules).
+static int upload_rt_tables(qs_state* s, const RtProgram& pr, const std::vector<PhaseTable>& pt, int m,
+                            const int4** dev) {
+  const size_t per = (size_t)1 << m;
+  const size_t bytes = pr.uses.size() * per * sizeof(int4);
+  if (!s->tables_ev) QS_CUDA(cudaEventCreateWithFlags(&s->tables_ev, cudaEventDisableTiming));
+  QS_CUDA(cudaEventSynchronize(s->tables_ev));
+  if (s->tables_pinned_bytes < bytes) {
+    if (s->tables_pinned) cudaFreeHost(s->tables_pinned);
+    s->tables_pinned = nullptr;
+    s->tables_pinned_bytes = 0;
+    QS_CUDA(cudaMallocHost(&s->tables_pinned, bytes));
+    s->tables_pinned_bytes = bytes;
+  }
+  if (s->tables_bytes < bytes) {
+    if (s->tables) {
+      QS_CUDA(cudaStreamSynchronize(s->stream));
+      cudaFree(s->tables);
+    }
+    s->tables = nullptr;
+    s->tables_bytes = 0;
+    QS_CUDA(cudaMalloc(&s->tables, bytes));
+    s->tables_bytes = bytes;
+  }
+  int4* host = (int4*)s->tables_pinned;
+  const uint32_t G = (uint32_t)(per >> RP_BITS);
+  for (size_t u = 0; u < pr.uses.size(); ++u) {
+    const PhaseTable& t = pt[pr.uses[u].first];
+    const RtPhase& ph = pr.phases[pr.uses[u].second];
+    int4* out = host + u * per;
+    for (uint32_t g = 0; g < G; ++g)
+      for (uint32_t k = 0; k < 16; ++k) {
+        const C2 z = t.t[rt_index(ph, m, g, k)];
+        const QL c = q60_split(q60_from_double(z.re)), d = q60_split(q60_from_double(z.im));
+        out[g * 16 + k] = make_int4(c.h, c.l, d.h, d.l);
+      }
+  }
+  QS_CUDA(cudaMemcpyAsync(s->tables, host, bytes, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(cudaEventRecord(s->tables_ev, s->stream));
+  *dev = (const int4*)s->tables;
+  return QS_OK;
+}
+
+static int run_tile_pass_rt(qs_state* s, const PlanPass& ps, const std::vector<Op1>& rops,
+                            const std::vector<PhaseTable>& ptables, const int* local, int m) {
+  const int n = s->n;
+  RtProgram pr;
+  QS_TRY(build_rt_program(n, rops, local, m, &pr));
+  if (pr.ops.empty()) return QS_OK;
+  for (const auto& u : pr.uses)
+    if (u.first < 0 || (size_t)u.first >= ptables.size() || ptables[u.first].t.size() != ((size_t)1 << m))
+      return fail(QS_ERR_INVALID_ARG, "internal: malformed phase-table use");
+  RtArgs* g = new (std::nothrow) RtArgs;
+  if (!g) return fail(QS_ERR_OOM, "host allocation failed");
+  memset(g, 0, offsetof(RtArgs, phases));
+  const uint64_t Q = ps.qmask;
+  int L = 0;
+  while (L < n && ((Q >> L) & 1)) ++L;
+  g->n = n;
+  g->m = m;
+  g->ntiles = 1ull << (n - m);
+  for (int b = L; b < n; ++b)
+    if ((Q >> b) & 1) g->qhigh[g->nhigh++] = b;
+  for (int b = 0; b < n; ++b)
+    if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
+  int rc = QS_OK;
+  if (!pr.uses.empty()) rc = upload_rt_tables(s, pr, ptables, m, &g->tables);
+  const double N = (double)(1ull << n);
+  size_t p = 0;
+  while (rc == QS_OK && p < pr.phases.size()) {
+    g->nphases = g->nops = g->ncoef = 0;
+    double io = 0.0;
+    while (p < pr.phases.size()) {
+      const RtPhase& ph = pr.phases[p];
+      int nc = 0;
+      for (int o = ph.op_begin; o < ph.op_end; ++o) nc += pr.ncoef[o];
+      const int no = ph.op_end - ph.op_begin;
+      if (g->nphases + 1 > RT_MAX_PHASES || g->nops + no > RT_MAX_OPS || g->ncoef + nc > RT_MAX_COEF) break;
+      RtPhase& q = g->phases[g->nphases++];
+      q = ph;
+      q.op_begin = (uint16_t)g->nops;
+      for (int o = ph.op_begin; o < ph.op_end; ++o) {
+        RtOp t = pr.ops[o];
+        for (int c = 0; c < pr.ncoef[o]; ++c) g->coef[g->ncoef + c] = pr.coef[t.coef + c];
+        t.coef = (uint16_t)g->ncoef;
+        g->ncoef += pr.ncoef[o];
+        g->ops[g->nops++] = t;
+      }
+      q.op_end = (uint16_t)g->nops;
+      ++p;
+    }
+    if (g->nphases == 0) {
+      rc = fail(QS_ERR_UNSUPPORTED, "a register phase exceeds the launch limits (%d ops, %d coefficients)",
+                RT_MAX_OPS, RT_MAX_COEF);
+      break;
+    }
+    // the roofline counts of this launch: its share of the program's limb products
+    io = pr.int_ops * N * (double)g->nops / (double)pr.ops.size();
+    rc = launch_tile_q60(s, *g, io, (int)ps.gates.size(), Q);
+  }
+  delete g;
+  return rc;
+}
+
+extern "C" int qs_plan_pass_program(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng,
+                                    const double* params, qs_reg_step* steps, size_t cap, size_t* count) {
+  clear_error();
+  if (!p || !count || (cap && !steps)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  if (pass >= p->passes.size()) return fail(QS_ERR_INVALID_ARG, "pass %zu of %zu", pass, p->passes.size());
+  if (p->ng != ng || p->fingerprint != fingerprint(gates, ng)) return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
+  QS_TRY(validate_gates(gates, ng, p->n, params));
+  const PlanPass& ps = p->passes[pass];
+  if (ps.kind != PASS_TILE) return fail(QS_ERR_INVALID_ARG, "pass %zu is a per-gate pass", pass);
+  std::vector<Op1> rops;
+  std::vector<PhaseTable> pt;
+  int local[64];
+  int m = 0;
+  QS_TRY(build_pass_ops(p->n, ps, gates, params, true, &rops, &pt, local, &m));
+  if (m < RT_MIN_M || m > RT_MAX_M) return fail(QS_ERR_UNSUPPORTED, "tile width %d has no register program", m);
+  RtProgram pr;
+  QS_TRY(build_rt_program(p->n, rops, local, m, &pr));
+  *count = pr.steps.size();
+  for (size_t i = 0; i < pr.steps.size() && i < cap; ++i) steps[i] = pr.steps[i];
   return QS_OK;
 }
 
@@ -988,6 +1273,10 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   std::vector<PhaseTable> ptables;
   const bool f32 = s->prec == 64;  // complex64 state: FP32 engine
   int rc = build_pass_ops(n, ps, gates, params, (fixed && s->prec == 128) || f32, &rops, &ptables, local, &m);
+  if (rc == QS_OK && fixed && s->prec == 128 && g_register_bits == RP_BITS && m >= RT_MIN_M && m <= RT_MAX_M) {
+    delete g;
+    return run_tile_pass_rt(s, ps, rops, ptables, local, m);
+  }
   int L = 0;
   while (L < n && ((Q >> L) & 1)) ++L;
   g->n = n;
@@ -1003,7 +1292,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   g->tables = nullptr;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
-  const bool pairs = ((fixed && s->prec == 128) || f32) && g_rotation_pairs && g_register_bits == 0;
+  const bool pairs = ((fixed && s->prec == 128) || f32) && g_rotation_pairs;
   auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
@@ -1105,8 +1394,6 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed rotation-pair op");
   }
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, f32);
-  g->nphases = 0;
-  if (rc == QS_OK && fixed && g_register_bits && m >= g_register_bits) build_phases(g, g_register_bits);
   if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,
                                                    (int)ps.gates.size(), fixed);
   delete g;

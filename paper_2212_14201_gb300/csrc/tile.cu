@@ -383,122 +383,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
   }
 }
 
-// ---- register phases (Q60) ---------------------------------------------------------
-// Ops of one phase on the 2^RB amplitudes v[k] of a group: register bit R of k
-// is tile bit b[R]; cr = in-phase controls as register bits.
-template <int RB, int R>
-__device__ __forceinline__ void ph_op(longlong2 (&v)[1 << RB], const TileOp& op, uint32_t cr) {
-  constexpr int S = 1 << R;
-  constexpr int K = 1 << RB;
-  const int kind = op.kind;
-  if (kind == TOP_GENERAL) {
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (!(k & S) && (k & cr) == cr) EngQ60::general2(op, v[k], v[k | S], v[k], v[k | S]);
-  } else if (kind == TOP_REAL) {
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (!(k & S) && (k & cr) == cr) EngQ60::real2(op, v[k], v[k | S], v[k], v[k | S]);
-  } else if (kind == TOP_ANTI) {
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (!(k & S) && (k & cr) == cr) {
-        const longlong2 a0 = v[k], a1 = v[k | S];
-        v[k] = EngQ60::mul(a1, op.code0, op, 1);
-        v[k | S] = EngQ60::mul(a0, op.code1, op, 2);
-      }
-  } else if (kind == TOP_DIAG) {
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if ((k & cr) == cr) v[k] = (k & S) ? EngQ60::mul(v[k], op.code1, op, 3) : EngQ60::mul(v[k], op.code0, op, 0);
-  } else {  // PHASE1
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if ((k & S) && (k & cr) == cr) v[k] = EngQ60::mul(v[k], op.code1, op, 3);
-  }
-}
-
-template <int RB, int THREADS, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k_tile_reg(double2* __restrict__ a, const __grid_constant__ TileArgs g) {
-  constexpr int K = 1 << RB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = g.m;
-  const int L = m - g.nhigh;
-  const uint32_t TS = 1u << m;
-  const uint32_t H = 1u << g.nhigh;
-  uint64_t* offs = reinterpret_cast<uint64_t*>(smem_raw);
-  longlong2* tile = reinterpret_cast<longlong2*>(smem_raw + ((H * sizeof(uint64_t) + 15) & ~(size_t)15));
-  for (uint32_t h = threadIdx.x; h < H; h += THREADS) {
-    uint64_t o = 0;
-    for (int b = 0; b < g.nhigh; ++b) o |= (uint64_t)((h >> b) & 1u) << g.qhigh[b];
-    offs[h] = o;
-  }
-  const uint32_t lowmask = (1u << L) - 1;
-  const uint32_t G = TS >> RB;  // groups of 2^RB amplitudes per phase
-  for (uint64_t r = blockIdx.x; r < g.ntiles; r += gridDim.x) {
-    uint64_t base = 0;
-    for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j] = EngQ60::load(a[base + offs[j >> L] + (j & lowmask)]);
-    __syncthreads();
-    for (int p = 0; p < g.nphases; ++p) {
-      const TilePhase ph = g.phases[p];
-      uint32_t pmask = 0;
-#pragma unroll
-      for (int i = 0; i < RB; ++i) pmask |= 1u << ph.b[i];
-      uint32_t dep[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        uint32_t dk = 0;
-#pragma unroll
-        for (int i = 0; i < RB; ++i)
-          if (k & (1 << i)) dk |= 1u << ph.b[i];
-        dep[k] = dk;
-      }
-      for (uint32_t grp = threadIdx.x; grp < G; grp += THREADS) {
-        const uint32_t gb = tile_expand(grp, pmask, 0);
-        longlong2 v[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = tile[gb | dep[k]];
-        for (int k = ph.op_begin; k < ph.op_end; ++k) {
-          const TileOp& op = g.ops[k];
-          if ((base & op.ext_cmask) != op.ext_cmask) continue;
-          const uint32_t lcm = op.lcmask;
-          const uint32_t lout = lcm & ~pmask;
-          if ((gb & lout) != lout) continue;
-          uint32_t cr = 0;
-#pragma unroll
-          for (int i = 0; i < RB; ++i) cr |= ((lcm >> ph.b[i]) & 1u) << i;
-          if (op.kind == TOP_SCALAR || !((pmask >> op.tb) & 1u)) {
-            // diagonal op whose target is constant for the group (outside the
-            // tile: a per-tile bit; in the tile but outside the phase: a group bit)
-            const bool one = op.kind == TOP_SCALAR ? ((base >> op.tb) & 1ull) : ((gb >> op.tb) & 1u);
-            const int code = one ? op.code1 : op.code0;
-            if (code == U_ONE) continue;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk)
-              if ((kk & cr) == cr) v[kk] = EngQ60::mul(v[kk], code, op, one ? 3 : 0);
-            continue;
-          }
-          int R = RB - 1;
-#pragma unroll
-          for (int i = RB - 2; i >= 0; --i)
-            if (op.tb == ph.b[i]) R = i;
-          switch (R) {
-            case 0: ph_op<RB, 0>(v, op, cr); break;
-            case 1: if (RB > 1) ph_op<RB, (RB > 1 ? 1 : 0)>(v, op, cr); break;
-            case 2: if (RB > 2) ph_op<RB, (RB > 2 ? 2 : 0)>(v, op, cr); break;
-            default: if (RB > 3) ph_op<RB, (RB > 3 ? 3 : 0)>(v, op, cr); break;
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < K; ++k) tile[gb | dep[k]] = v[k];
-      }
-      __syncthreads();
-    }
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = EngQ60::store(tile[j]);
-  }
-}
 template <class E, int THREADS>
 static int launch_engine_t(qs_state* s, const TileArgs& g, size_t smem) {
   static bool attr_set = false;
@@ -533,26 +417,6 @@ int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, in
   for (int b = 0; b < g.m - g.nhigh; ++b) qmask |= 1ull << b;
   for (int b = 0; b < g.nhigh; ++b) qmask |= 1ull << g.qhigh[b];
   KTimer kt(s, QS_K_TILE, g.m, ngates, qmask, 0, (double)(1ull << g.n), flops, int_ops);
-  if (fixed && g.nphases > 0) {
-    constexpr int THREADS = 256;
-    int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (220 * 1024) / (smem + 1024)));
-    uint64_t grid = std::min<uint64_t>(g.ntiles, (uint64_t)152 * per_sm);
-    static bool attr3 = false, attr4 = false;
-    if (g.reg_bits == 4) {
-      if (!attr4) {
-        QS_CUDA(cudaFuncSetAttribute(k_tile_reg<4, THREADS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr4 = true;
-      }
-      k_tile_reg<4, THREADS, 1><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
-    } else {
-      if (!attr3) {
-        QS_CUDA(cudaFuncSetAttribute(k_tile_reg<3, THREADS, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr3 = true;
-      }
-      k_tile_reg<3, THREADS, 3><<<(unsigned)grid, THREADS, smem, s->stream>>>(s->amps, g);
-    }
-    return launch_check("tile kernel (register phases)");
-  }
   if (s->prec == 64) return launch_engine<EngF32>(s, g);
   return fixed ? launch_engine<EngQ60>(s, g) : launch_engine<EngF64>(s, g);
 }

@@ -12,17 +12,6 @@ constexpr int TILE_MAX_M = 13;      // widest tile: 2^13 x 16 B = 128 KiB of sha
 constexpr int TILE_DEFAULT_M = 12;  // greedy plans: 2^12 x 16 B = 64 KiB, 3 CTAs per SM
 constexpr int TILE_LOW = 3;     // qubits 0..2 are always in a tile: 128-byte contiguous runs
 constexpr int TILE_MAX_OPS = 256;
-constexpr int TILE_MAX_PHASES = 256;
-
-// A register phase: a run of consecutive ops of the pass whose non-diagonal
-// targets lie within four tile bits b[0..3] (ascending local positions).  Each
-// thread holds the 16 amplitudes of a group (the other m-4 bits fixed) in
-// registers and applies every op of the run before the next shared-memory
-// round trip.  Diagonal ops join any phase.
-struct TilePhase {
-  uint8_t b[4];
-  int16_t op_begin, op_end;
-};
 
 enum TileOpKind : int8_t {
   TOP_PHASE1 = OP_PHASE1,
@@ -61,11 +50,8 @@ struct TileArgs {
   int nout;          // qubits outside the tile
   int outpos[QS_MAX_QUBITS];  // their global positions (ascending)
   int nops;
-  int nphases;       // > 0: run the register-phase kernel (Q60 engine, m >= 4)
-  int reg_bits;      // register bits per phase (3 or 4)
   const QL* tables;  // DTABLE ops: per table the Gauss-form parts re, im, nim, 2^m limb pairs each
   TileOp ops[TILE_MAX_OPS];
-  TilePhase phases[TILE_MAX_PHASES];
 };
 static_assert(sizeof(TileArgs) < 32000, "tile arguments must fit the kernel parameter space");
 
