@@ -969,7 +969,7 @@ static int build_rt_program(int n, const std::vector<Op1>& rops, const int* loca
   for (size_t i = 0; i < rops.size(); ++i) {
     const Op1& o = rops[i];
     if (o.cls == OP_IDENTITY) continue;
-    RpIn x{IK_DIAG, -1, 0};
+    RpIn x{IK_DIAG, -1, 0, false};
     if (o.cls == kTableMark) {
       x.kind = IK_TABLE;
     } else {
@@ -981,6 +981,7 @@ static int build_rt_program(int n, const std::vector<Op1>& rops, const int* loca
           return fail(QS_ERR_INVALID_ARG, "plan does not match the program (non-diagonal op on qubit %d outside its tile)",
                       o.target);
         x.kind = IK_MIX;
+        x.pairable = o.cls == OP_REAL && o.cmask == 0;
       }
     }
     in.push_back(x);

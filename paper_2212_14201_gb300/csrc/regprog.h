@@ -8,14 +8,19 @@
 // diagonal gates, controls) run in any phase; an op that mixes amplitudes (real,
 // general, antidiagonal) needs its target among the phase's register bits.
 //
-// Phases are built greedily over the pass's op list: scan the remaining ops in
-// order; an op joins the current phase when it commutes with every op skipped so
-// far and its mixing target fits in the register set (<= R bits); otherwise it is
-// skipped.  Two ops commute unless they share a qubit on which at least one of
-// them acts non-diagonally.  The skipped ops, in order, form the rest.  A phase
-// that ends a layer therefore continues with the next layer's ops on its own
-// register bits, so a layer of rotations over m tile qubits costs about m/R - 1
-// phases instead of m/R.
+// Phases are built greedily over the pass's op list.  For a register set P, scan
+// the remaining ops in order; an op joins the phase when it commutes with every
+// op skipped so far and its mixing target lies in P; otherwise it is skipped.
+// Two ops commute unless they share a qubit on which at least one of them acts
+// non-diagonally.  The skipped ops, in order, form the rest.  P is chosen per
+// phase among the sets that contain the target of the first op that can run:
+// the one that lets the most mixing ops (then the most ops) join.  A phase that
+// ends a layer therefore continues with the next layer's ops on its own register
+// bits, so a layer of rotations over m tile qubits costs about m/R - 1 phases
+// instead of m/R, and in light-cone passes a phase spans several short layers.
+// Inside a phase, a real rotation that can be paired (uncontrolled, another
+// register bit) is moved up next to an earlier unpaired one when it commutes with
+// every op between them, so that the two run as one 4x4 on quads.
 #pragma once
 
 #include <stdint.h>
@@ -33,6 +38,7 @@ struct RpIn {
   int kind;       // IK_TABLE (diagonal over the whole tile), IK_MIX (mixes its target), IK_DIAG
   int tb;         // tile bit of the target, -1 when it lies outside the tile (IK_DIAG only)
   uint32_t lcm;   // controls inside the tile (tile-bit mask)
+  bool pairable;  // an uncontrolled real rotation (may join another as a 4x4 pair)
 };
 
 struct RpPhase {
@@ -56,29 +62,128 @@ inline void rp_touch(const RpIn& o, uint32_t full, uint32_t* N, uint32_t* D) {
   }
 }
 
+// Ops of `rem` that a phase with register set P takes (in order), the rest in
+// `rest`; returns the number of mixing ops taken.
+inline int rp_take(const std::vector<RpIn>& ops, const std::vector<int>& rem, uint32_t P, uint32_t full,
+                   std::vector<int>* take, std::vector<int>* rest) {
+  uint32_t defN = 0, defD = 0;
+  int mix = 0;
+  for (int i : rem) {
+    uint32_t N, D;
+    rp_touch(ops[i], full, &N, &D);
+    const bool blocked = (N & (defN | defD)) || (D & defN);
+    if (!blocked && (N & ~P) == 0) {
+      if (take) take->push_back(i);
+      mix += N != 0;
+      continue;
+    }
+    if (rest) rest->push_back(i);
+    defN |= N;
+    defD |= D;
+  }
+  return mix;
+}
+
+inline bool rp_commute(const RpIn& a, const RpIn& b, uint32_t full) {
+  uint32_t Na, Da, Nb, Db;
+  rp_touch(a, full, &Na, &Da);
+  rp_touch(b, full, &Nb, &Db);
+  return !(Na & (Nb | Db)) && !(Nb & Da);
+}
+
+// Moves pairable rotations next to an earlier unpaired partner (see above).
+inline void rp_pair_order(const std::vector<RpIn>& ops, uint32_t full, std::vector<int>* list) {
+  std::vector<int>& L = *list;
+  size_t i = 0;
+  while (i < L.size()) {
+    const RpIn& a = ops[L[i]];
+    if (!a.pairable) {
+      ++i;
+      continue;
+    }
+    if (i + 1 < L.size() && ops[L[i + 1]].pairable && ops[L[i + 1]].tb != a.tb) {
+      i += 2;
+      continue;
+    }
+    size_t found = 0;
+    for (size_t j = i + 1; j < L.size(); ++j) {
+      const RpIn& b = ops[L[j]];
+      if (b.pairable && b.tb != a.tb) {
+        bool ok = true;
+        for (size_t k = i + 1; k < j && ok; ++k) ok = rp_commute(b, ops[L[k]], full);
+        if (ok) found = j;
+        break;  // only the first candidate: later ones would have to pass it
+      }
+    }
+    if (found) {
+      const int b = L[found];
+      L.erase(L.begin() + (long)found);
+      L.insert(L.begin() + (long)i + 1, b);
+      i += 2;
+    } else {
+      ++i;
+    }
+  }
+}
+
 inline std::vector<RpPhase> rp_build_phases(const std::vector<RpIn>& ops, int m) {
   const int R = std::min(m, RP_BITS);
   const uint32_t full = m >= 32 ? ~0u : ((1u << m) - 1);
   std::vector<RpPhase> phases;
-  std::vector<int> rem(ops.size()), rest;
+  std::vector<int> rem(ops.size()), rest, take;
   for (size_t i = 0; i < ops.size(); ++i) rem[i] = (int)i;
   while (!rem.empty()) {
-    RpPhase ph;
-    uint32_t defN = 0, defD = 0;
-    rest.clear();
-    for (int i : rem) {
-      uint32_t N, D;
-      rp_touch(ops[i], full, &N, &D);
-      const bool blocked = (N & (defN | defD)) || (D & defN);
-      if (!blocked && rp_popc(ph.P | N) <= R) {
-        ph.P |= N;
-        ph.ops.push_back(i);
-        continue;
+    // the target of the first op that can run, and the mixing targets of the rest
+    uint32_t first = 0, bits = 0;
+    {
+      uint32_t defN = 0, defD = 0;
+      for (int i : rem) {
+        uint32_t N, D;
+        rp_touch(ops[i], full, &N, &D);
+        bits |= N;
+        const bool blocked = (N & (defN | defD)) || (D & defN);
+        if (!blocked && !N) continue;  // a diagonal op every phase takes
+        if (!blocked && !first) {
+          first = N;
+          continue;
+        }
+        defN |= N;
+        defD |= D;
       }
-      rest.push_back(i);
-      defN |= N;
-      defD |= D;
     }
+    uint32_t bestP = first;
+    if (first) {
+      int cand[32], nc = 0;
+      for (int b = 0; b < m; ++b)
+        if (((bits & ~first) >> b) & 1) cand[nc++] = b;
+      const int need = std::min(R - 1, nc);
+      int best_mix = -1, best_all = -1;
+      // every choice of `need` further bits (nc <= m - 1 <= 11, need <= 3)
+      int idx[3] = {0, 1, 2};
+      for (int k = 0; k < need; ++k) idx[k] = k;
+      while (true) {
+        uint32_t P = first;
+        for (int k = 0; k < need; ++k) P |= 1u << cand[idx[k]];
+        take.clear();
+        const int mix = rp_take(ops, rem, P, full, &take, nullptr);
+        const int all = (int)take.size();
+        if (mix > best_mix || (mix == best_mix && all > best_all)) {
+          best_mix = mix;
+          best_all = all;
+          bestP = P;
+        }
+        int k = need - 1;
+        while (k >= 0 && idx[k] == nc - need + k) --k;
+        if (k < 0) break;
+        ++idx[k];
+        for (int j = k + 1; j < need; ++j) idx[j] = idx[j - 1] + 1;
+      }
+    }
+    RpPhase ph;
+    ph.P = bestP;
+    rest.clear();
+    rp_take(ops, rem, ph.P, full, &ph.ops, &rest);
+    rp_pair_order(ops, full, &ph.ops);
     // pad the register set to R bits with the highest unused tile bits
     for (int b = m - 1; b >= 0 && rp_popc(ph.P) < R; --b) ph.P |= 1u << b;
     phases.push_back(std::move(ph));

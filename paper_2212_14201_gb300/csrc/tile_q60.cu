@@ -209,8 +209,12 @@ __device__ __forceinline__ void rt_pair_any(longlong2 (&v)[16], int r0, int r1, 
   }
 }
 
+#ifndef QS_RT_MINB
+#define QS_RT_MINB 1
+#endif
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS >= 256 ? 2 : 1)
+__global__ void __launch_bounds__(THREADS, THREADS >= 256 ? QS_RT_MINB : 1)
     k_tile_q60(double2* __restrict__ a, const __grid_constant__ RtArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = g.m;
