@@ -955,6 +955,7 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
 // host tests of qs_plan_pass_program).
 struct RtProgram {
   std::vector<RtPhase> phases;
+  std::vector<RtRun> runs;
   std::vector<RtOp> ops;
   std::vector<int> ncoef;                 // coefficient limb pairs of each op
   std::vector<QL> coef;
@@ -987,6 +988,14 @@ static int build_rt_program(int n, const std::vector<Op1>& rops, const int* loca
     in.push_back(x);
     src.push_back((int)i);
   }
+  // one emitted op before its coefficients are known: a table, a pair (a, b) or a single a
+  struct Item {
+    int kind;       // RtKind
+    int a, b;       // indices into rops (b: the pair's second rotation, -1)
+    int table;      // table index (TABLE, or a table that runs first in a PAIR), -1
+    int tsrc;       // rops index of that table op, -1
+    int ra, rb;     // register bits: the single's target (ra), the pair's two rotations (ra, rb)
+  };
   const std::vector<RpPhase> phases = rp_build_phases(in, m);
   for (size_t p = 0; p < phases.size(); ++p) {
     const RpPhase& rp = phases[p];
@@ -1002,127 +1011,167 @@ static int build_rt_program(int n, const std::vector<Op1>& rops, const int* loca
       }
     if (r != RP_BITS) return fail(QS_ERR_INVALID_ARG, "internal: register phase with %d bits", r);
     rp_group_bits(rp.P, m, ph.gl);
-    ph.op_begin = (uint16_t)pr->ops.size();
-    auto src_op = [&](int k) -> const Op1& { return rops[src[rp.ops[k]]]; };
+    // the phase's items in order: pairs of consecutive rotations, tables fused into the pair after them
+    std::vector<Item> items;
+    auto src_op = [&](size_t k) -> const Op1& { return rops[src[rp.ops[k]]]; };
     auto pairable = [&](size_t k) {
-      if (k + 1 >= rp.ops.size()) return false;
-      const Op1& a = src_op((int)k);
-      const Op1& b = src_op((int)k + 1);
-      return a.cls == OP_REAL && b.cls == OP_REAL && a.cmask == 0 && b.cmask == 0 && a.target != b.target;
-    };
-    auto new_op = [&](int kind, int ncoef, int s0, int s1, int tsrc) -> RtOp& {
-      RtOp o;
-      memset(&o, 0, sizeof o);
-      o.kind = (uint8_t)kind;
-      o.table = -1;
-      o.coef = (uint16_t)pr->coef.size();
-      pr->ops.push_back(o);
-      pr->ncoef.push_back(ncoef);
-      qs_reg_step st;
-      st.phase = (int32_t)p;
-      st.kind = kind;
-      st.src0 = s0;
-      st.src1 = s1;
-      st.table_src = tsrc;
-      st.reg_bits = rp.P;
-      pr->steps.push_back(st);
-      return pr->ops.back();
-    };
-    auto add_table_use = [&](int table) {
-      pr->uses.push_back({table, (int)p});
-      return (int16_t)(pr->uses.size() - 1);
-    };
-    auto qc_push = [&](const C2& z, bool gauss) {
-      const QC c = gauss ? qc_make_gauss(z.re, z.im) : qc_make(z.re, z.im);
-      pr->coef.push_back(c.re);
-      pr->coef.push_back(c.im);
-      pr->coef.push_back(c.nim);
+      if (!g_rotation_pairs || k + 1 >= rp.ops.size()) return false;
+      const Op1& x = src_op(k);
+      const Op1& y = src_op(k + 1);
+      return x.cls == OP_REAL && y.cls == OP_REAL && x.cmask == 0 && y.cmask == 0 && x.target != y.target;
     };
     for (size_t k = 0; k < rp.ops.size(); ++k) {
-      const Op1& o = src_op((int)k);
+      const Op1& o = src_op(k);
       const int sk = src[rp.ops[k]];
-      int tab = -1, tsrc = -1;
       if (o.cls == kTableMark) {
         if (g_fuse_tables && pairable(k + 1)) {
-          tab = o.target;
-          tsrc = sk;
-          ++k;  // the pair follows
+          const Op1& x = src_op(k + 1);
+          const Op1& y = src_op(k + 2);
+          items.push_back({RK_PAIR, src[rp.ops[k + 1]], src[rp.ops[k + 2]], o.target, sk, reg[local[x.target]],
+                           reg[local[y.target]]});
+          k += 2;
         } else {
-          RtOp& t = new_op(RK_TABLE, 0, sk, -1, -1);
-          t.table = add_table_use(o.target);
-          pr->int_ops += 9.0;
-          continue;
+          items.push_back({RK_TABLE, sk, -1, o.target, -1, -1, -1});
         }
+        continue;
       }
-      const Op1& a = src_op((int)k);
-      const int sa = src[rp.ops[k]];
-      if (pairable(k) && g_rotation_pairs) {
-        const Op1& b = src_op((int)k + 1);
-        const int sb2 = src[rp.ops[k + 1]];
-        const int ra = reg[local[a.target]], rb2 = reg[local[b.target]];
-        const Op1& lo = ra < rb2 ? a : b;
-        const Op1& hi = ra < rb2 ? b : a;
-        RtOp& t = new_op(RK_PAIR, 16, sa, sb2, tsrc);
-        t.r0 = (uint8_t)std::min(ra, rb2);
-        t.r1 = (uint8_t)std::max(ra, rb2);
-        if (tab >= 0) t.table = add_table_use(tab);
-        for (int qo = 0; qo < 4; ++qo)
-          for (int qi = 0; qi < 4; ++qi) {
-            const double v = hi.m.m[2 * (qo >> 1) + (qi >> 1)].re * lo.m.m[2 * (qo & 1) + (qi & 1)].re;
-            pr->coef.push_back(q60_split(q60_from_double(v)));
-          }
-        pr->int_ops += 24.0 + (tab >= 0 ? 9.0 : 0.0);
+      if (pairable(k)) {
+        const Op1& y = src_op(k + 1);
+        items.push_back({RK_PAIR, sk, src[rp.ops[k + 1]], -1, -1, reg[local[o.target]], reg[local[y.target]]});
         ++k;
         continue;
       }
-      if (tab >= 0) {  // no pair after all (rotation pairs switched off): the table on its own
-        RtOp& t = new_op(RK_TABLE, 0, tsrc, -1, -1);
-        t.table = add_table_use(tab);
-        pr->int_ops += 9.0;
-      }
-      uint32_t lcm = 0;
-      uint64_t ext = 0;
-      for (int b = 0; b < n; ++b)
-        if ((a.cmask >> b) & 1) {
-          if (local[b] >= 0) lcm |= 1u << local[b];
-          else ext |= 1ull << b;
-        }
-      uint32_t cr = 0, gm = 0;
-      for (int b = 0; b < m; ++b)
-        if ((lcm >> b) & 1) {
-          if (reg[b] >= 0) cr |= 1u << reg[b];
-          else gm |= 1u << b;
-        }
-      const int tb = local[a.target];
+      const int tb = local[o.target];
+      const bool in_reg = tb >= 0 && reg[tb] >= 0;
       int kind;
-      bool in_reg = tb >= 0 && reg[tb] >= 0;
-      switch (a.cls) {
+      switch (o.cls) {
         case OP_REAL: kind = RK_REAL; break;
         case OP_GENERAL: kind = RK_GEN; break;
         case OP_ANTI: kind = RK_ANTI; break;
         case OP_DIAG: kind = in_reg ? RK_DIAG : RK_SCAL; break;
         default: kind = in_reg ? RK_PH1 : RK_SCAL; break;
       }
-      RtOp& t = new_op(kind, kind == RK_REAL ? 4 : 12, sa, -1, -1);
-      t.ext = ext;
-      t.gmask = (uint16_t)gm;
-      t.cr = (uint8_t)cr;
-      t.code0 = (uint8_t)(a.cls == OP_PHASE1 ? U_ONE : a.code0);
-      t.code1 = (uint8_t)a.code1;
-      if (kind == RK_SCAL) {
-        t.sout = tb < 0 ? 1 : 0;
-        t.sbit = (uint8_t)(tb < 0 ? a.target : tb);
-      } else {
-        t.r0 = (uint8_t)reg[tb];
-      }
-      if (kind == RK_REAL) {
-        for (int e = 0; e < 4; ++e) pr->coef.push_back(q60_split(q60_from_double(a.m.m[e].re)));
-      } else {
-        for (int e = 0; e < 4; ++e) qc_push(a.m.m[e], kind == RK_GEN);
-      }
-      pr->int_ops += class_touch_fraction(a) * op_int_ops_per_amp(a);
+      items.push_back({kind, sk, -1, -1, -1, in_reg ? reg[tb] : -1, -1});
     }
-    ph.op_end = (uint16_t)pr->ops.size();
+    // runs: consecutive items on one quad structure (two register bits)
+    ph.run_begin = (uint16_t)pr->runs.size();
+    size_t it = 0;
+    while (it < items.size()) {
+      int b0 = -1, b1 = -1;
+      size_t end = it;
+      for (; end < items.size(); ++end) {
+        const Item& x = items[end];
+        bool ok = true;
+        int n0 = b0, n1 = b1;
+        auto want = [&](int bit) {  // bit must be one of the run's two
+          if (bit == n0 || bit == n1) return;
+          if (n0 < 0) n0 = bit;
+          else if (n1 < 0) n1 = bit;
+          else ok = false;
+        };
+        if (x.kind == RK_PAIR) {
+          want(x.ra);
+          want(x.rb);
+        } else if (x.kind != RK_SCAL && x.kind != RK_TABLE) {
+          want(x.ra);
+        }
+        if (!ok) break;
+        b0 = n0;
+        b1 = n1;
+      }
+      for (int f = 0; f < RP_BITS && (b0 < 0 || b1 < 0); ++f) {
+        if (f == b0 || f == b1) continue;
+        if (b0 < 0) b0 = f;
+        else b1 = f;
+      }
+      RtRun run;
+      memset(&run, 0, sizeof run);
+      run.r0 = (uint8_t)b0;
+      run.r1 = (uint8_t)b1;
+      run.op_begin = (uint16_t)pr->ops.size();
+      for (size_t j = it; j < end; ++j) {
+        const Item& x = items[j];
+        RtOp t;
+        memset(&t, 0, sizeof t);
+        t.kind = (uint8_t)x.kind;
+        t.table = -1;
+        t.coef = (uint16_t)pr->coef.size();
+        int nc = 0;
+        if (x.table >= 0) {
+          pr->uses.push_back({x.table, (int)p});
+          t.table = (int16_t)(pr->uses.size() - 1);
+          pr->int_ops += 9.0;
+        }
+        if (x.kind == RK_PAIR) {
+          // quad index bit(run.r0) + 2 bit(run.r1)
+          const Op1& oa = rops[x.a];
+          const Op1& ob = rops[x.b];
+          const Op1& on0 = x.ra == b0 ? oa : ob;  // the rotation on run bit r0
+          const Op1& on1 = x.ra == b0 ? ob : oa;
+          for (int qo = 0; qo < 4; ++qo)
+            for (int qi = 0; qi < 4; ++qi) {
+              const double v = on1.m.m[2 * (qo >> 1) + (qi >> 1)].re * on0.m.m[2 * (qo & 1) + (qi & 1)].re;
+              pr->coef.push_back(q60_split(q60_from_double(v)));
+            }
+          nc = 16;
+          pr->int_ops += 24.0;
+        } else if (x.kind != RK_TABLE) {
+          const Op1& o = rops[x.a];
+          uint32_t lcm = 0;
+          uint64_t ext = 0;
+          for (int b = 0; b < n; ++b)
+            if ((o.cmask >> b) & 1) {
+              if (local[b] >= 0) lcm |= 1u << local[b];
+              else ext |= 1ull << b;
+            }
+          uint32_t cr = 0, gm = 0;
+          for (int b = 0; b < m; ++b)
+            if ((lcm >> b) & 1) {
+              if (reg[b] >= 0) cr |= 1u << reg[b];
+              else gm |= 1u << b;
+            }
+          t.ext = ext;
+          t.gmask = (uint16_t)gm;
+          t.cr = (uint8_t)cr;
+          t.code0 = (uint8_t)(o.cls == OP_PHASE1 ? U_ONE : o.code0);
+          t.code1 = (uint8_t)o.code1;
+          if (x.kind == RK_SCAL) {
+            const int tb = local[o.target];
+            t.sout = tb < 0 ? 1 : 0;
+            t.sbit = (uint8_t)(tb < 0 ? o.target : tb);
+          } else {
+            t.role = (uint8_t)(x.ra == b0 ? 0 : 1);
+          }
+          if (x.kind == RK_REAL) {
+            for (int e = 0; e < 4; ++e) pr->coef.push_back(q60_split(q60_from_double(o.m.m[e].re)));
+            nc = 4;
+          } else {
+            for (int e = 0; e < 4; ++e) {
+              const QC c = x.kind == RK_GEN ? qc_make_gauss(o.m.m[e].re, o.m.m[e].im) : qc_make(o.m.m[e].re, o.m.m[e].im);
+              pr->coef.push_back(c.re);
+              pr->coef.push_back(c.im);
+              pr->coef.push_back(c.nim);
+            }
+            nc = 12;
+          }
+          pr->int_ops += class_touch_fraction(o) * op_int_ops_per_amp(o);
+        }
+        pr->ops.push_back(t);
+        pr->ncoef.push_back(nc);
+        qs_reg_step st;
+        st.phase = (int32_t)p;
+        st.kind = x.kind;
+        st.src0 = x.a;
+        st.src1 = x.b;
+        st.table_src = x.tsrc;
+        st.reg_bits = rp.P;
+        pr->steps.push_back(st);
+      }
+      run.op_end = (uint16_t)pr->ops.size();
+      pr->runs.push_back(run);
+      it = end;
+    }
+    ph.run_end = (uint16_t)pr->runs.size();
     pr->phases.push_back(ph);
   }
   return QS_OK;
@@ -1207,25 +1256,37 @@ static int run_tile_pass_rt(qs_state* s, const PlanPass& ps, const std::vector<O
   const double N = (double)(1ull << n);
   size_t p = 0;
   while (rc == QS_OK && p < pr.phases.size()) {
-    g->nphases = g->nops = g->ncoef = 0;
+    g->nphases = g->nruns = g->nops = g->ncoef = 0;
     double io = 0.0;
     while (p < pr.phases.size()) {
       const RtPhase& ph = pr.phases[p];
-      int nc = 0;
-      for (int o = ph.op_begin; o < ph.op_end; ++o) nc += pr.ncoef[o];
-      const int no = ph.op_end - ph.op_begin;
-      if (g->nphases + 1 > RT_MAX_PHASES || g->nops + no > RT_MAX_OPS || g->ncoef + nc > RT_MAX_COEF) break;
+      int nc = 0, no = 0;
+      for (int u = ph.run_begin; u < ph.run_end; ++u)
+        for (int o = pr.runs[u].op_begin; o < pr.runs[u].op_end; ++o) {
+          nc += pr.ncoef[o];
+          ++no;
+        }
+      const int nr = ph.run_end - ph.run_begin;
+      if (g->nphases + 1 > RT_MAX_PHASES || g->nruns + nr > RT_MAX_RUNS || g->nops + no > RT_MAX_OPS ||
+          g->ncoef + nc > RT_MAX_COEF)
+        break;
       RtPhase& q = g->phases[g->nphases++];
       q = ph;
-      q.op_begin = (uint16_t)g->nops;
-      for (int o = ph.op_begin; o < ph.op_end; ++o) {
-        RtOp t = pr.ops[o];
-        for (int c = 0; c < pr.ncoef[o]; ++c) g->coef[g->ncoef + c] = pr.coef[t.coef + c];
-        t.coef = (uint16_t)g->ncoef;
-        g->ncoef += pr.ncoef[o];
-        g->ops[g->nops++] = t;
+      q.run_begin = (uint16_t)g->nruns;
+      for (int u = ph.run_begin; u < ph.run_end; ++u) {
+        RtRun ru = pr.runs[u];
+        ru.op_begin = (uint16_t)g->nops;
+        for (int o = pr.runs[u].op_begin; o < pr.runs[u].op_end; ++o) {
+          RtOp t = pr.ops[o];
+          for (int c = 0; c < pr.ncoef[o]; ++c) g->coef[g->ncoef + c] = pr.coef[t.coef + c];
+          t.coef = (uint16_t)g->ncoef;
+          g->ncoef += pr.ncoef[o];
+          g->ops[g->nops++] = t;
+        }
+        ru.op_end = (uint16_t)g->nops;
+        g->runs[g->nruns++] = ru;
       }
-      q.op_end = (uint16_t)g->nops;
+      q.run_end = (uint16_t)g->nruns;
       ++p;
     }
     if (g->nphases == 0) {

@@ -5,13 +5,14 @@
 // For each tile (2^m amplitudes x = deposit(r, outside bits) | deposit(j, tile
 // bits)) the CTA reads the amplitudes once from HBM, converts them to Q60 (two
 // int64 per amplitude) and keeps them in shared memory at the swizzled index
-// j ^ sw(j).  Each register phase then has every thread load the 16 amplitudes
-// of its group (tile index gb | dep(k), k = 0..15 over the phase's four register
-// bits), apply the phase's ops to them in registers and store them back; one
-// barrier separates phases.  The tile is converted back and written once.
+// j ^ sw(j).  In a register phase every thread owns the 16 amplitudes of its
+// group (tile index gb | dep(k), k = 0..15 over the phase's four register bits);
+// the phase's runs stream the group's four quads through registers, each quad
+// loaded once per run and taken through every op of the run.  One barrier
+// separates phases; the tile is converted back and written once.
 //
 // Arithmetic per op (limb products, 3 wide multiply-adds each, fixed.h):
-//   PAIR  two real rotations on register bits r0 < r1 as one real 4x4 on quads:
+//   PAIR  two real rotations on the run's bits as one real 4x4 on the quad:
 //         16 products per quad and component (the same as the two apart), half the
 //         limb splits and roundings;
 //   REAL  real 2x2: 4 products per pair and component;
@@ -90,127 +91,116 @@ __device__ __forceinline__ longlong2 rt_mul(const longlong2 a, int code, const Q
   }
 }
 
-// Two real rotations on register bits R0 < R1 as a real 4x4 on the four quads of
-// the 16 registers (quad index bit(R0) + 2 bit(R1)); with TAB the table entries
-// of the quad multiply first.
-template <int R0, int R1, bool TAB>
-__device__ __forceinline__ void rt_pair(longlong2 (&v)[16], const QL* __restrict__ c, const int4* __restrict__ tab) {
-  constexpr int S0 = 1 << R0, S1 = 1 << R1;
+// A quad in registers: a[i] is register index kk[i] of the group, quad index
+// i = bit(run r0) + 2 bit(run r1).
+struct RtQuad {
+  longlong2 a[4];
+  uint32_t kk[4];
+};
+
+__device__ __forceinline__ void rt_q_pair(RtQuad& q, const QL* __restrict__ c, const int4* __restrict__ tab) {
+  QL r[4], im[4];
 #pragma unroll
-  for (int k0 = 0; k0 < 16; ++k0) {
-    if (k0 & (S0 | S1)) continue;
-    const int kk[4] = {k0, k0 | S0, k0 | S1, k0 | S0 | S1};
-    QL r[4], im[4];
+  for (int i = 0; i < 4; ++i) {
+    longlong2 x = q.a[i];
+    if (tab) x = rt_tab_mul(__ldg(tab + q.kk[i]), x);
+    r[i] = q60_split(x.x);
+    im[i] = q60_split(x.y);
+  }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      longlong2 x = v[kk[q]];
-      if (TAB) x = rt_tab_mul(__ldg(tab + kk[q]), x);
-      r[q] = q60_split(x.x);
-      im[q] = q60_split(x.y);
+  for (int row = 0; row < 4; ++row) {
+    QAcc xr = qacc_new(), xi = qacc_new();
+#pragma unroll
+    for (int col = 0; col < 4; ++col) {
+      const QL u = c[4 * row + col];
+      qacc_add(xr, u, r[col]);
+      qacc_add(xi, u, im[col]);
     }
-#pragma unroll
-    for (int row = 0; row < 4; ++row) {
-      QAcc xr = qacc_new(), xi = qacc_new();
-#pragma unroll
-      for (int col = 0; col < 4; ++col) {
-        const QL u = c[4 * row + col];
-        qacc_add(xr, u, r[col]);
-        qacc_add(xi, u, im[col]);
-      }
-      v[kk[row]] = make_longlong2(qacc_round(xr), qacc_round(xi));
-    }
+    q.a[row] = make_longlong2(qacc_round(xr), qacc_round(xi));
   }
 }
 
-template <int R>
-__device__ __forceinline__ void rt_real(longlong2 (&v)[16], const QL* __restrict__ c, uint32_t cr) {
-  constexpr int S = 1 << R;
-  const QL m00 = c[0], m01 = c[1], m10 = c[2], m11 = c[3];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (k & S) continue;
-    if (((uint32_t)k & cr) != cr) continue;
-    const longlong2 a0 = v[k], a1 = v[k | S];
-    const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
-    QAcc x = qacc_new(), y = qacc_new(), z = qacc_new(), w = qacc_new();
-    qacc_add(x, m00, r0);
-    qacc_add(x, m01, r1);
-    qacc_add(y, m00, i0);
-    qacc_add(y, m01, i1);
-    qacc_add(z, m10, r0);
-    qacc_add(z, m11, r1);
-    qacc_add(w, m10, i0);
-    qacc_add(w, m11, i1);
-    v[k] = make_longlong2(qacc_round(x), qacc_round(y));
-    v[k | S] = make_longlong2(qacc_round(z), qacc_round(w));
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void rt_gen(longlong2 (&v)[16], const QL* __restrict__ c, uint32_t cr) {
-  constexpr int S = 1 << R;
-  const QC u0{c[0], c[1], c[2]}, u1{c[3], c[4], c[5]}, u2{c[6], c[7], c[8]}, u3{c[9], c[10], c[11]};
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (k & S) continue;
-    if (((uint32_t)k & cr) != cr) continue;
-    const longlong2 a0 = v[k], a1 = v[k | S];
-    const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
-    const QL s0 = q60_split(a0.x + a0.y), s1 = q60_split(a1.x + a1.y);
-    int64_t re, im;
-    q60_gauss_row(u0, u1, r0, i0, s0, r1, i1, s1, &re, &im);
-    v[k] = make_longlong2(re, im);
-    q60_gauss_row(u2, u3, r0, i0, s0, r1, i1, s1, &re, &im);
-    v[k | S] = make_longlong2(re, im);
-  }
-}
-
-// Antidiagonal (kind 0), diagonal (1) or |1>-phase (2) op on register bit R.
-template <int R>
-__device__ __forceinline__ void rt_unit(longlong2 (&v)[16], const RtOp& op, const QL* __restrict__ c, int form) {
-  constexpr int S = 1 << R;
-  const uint32_t cr = op.cr;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (k & S) continue;
-    if (((uint32_t)k & cr) != cr) continue;
-    if (form == 0) {
-      const longlong2 a0 = v[k], a1 = v[k | S];
-      v[k] = rt_mul(a1, op.code0, c + 3);
-      v[k | S] = rt_mul(a0, op.code1, c + 6);
-    } else {
-      if (form == 1) v[k] = rt_mul(v[k], op.code0, c);
-      v[k | S] = rt_mul(v[k | S], op.code1, c + 9);
-    }
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void rt_single(longlong2 (&v)[16], const RtOp& op, const QL* __restrict__ c) {
+// A one-qubit op on the amplitude pair (a0, a1) = (bit 0, bit 1 of its target).
+__device__ __forceinline__ void rt_2x2(longlong2& a0, longlong2& a1, const RtOp& op, const QL* __restrict__ c) {
   switch (op.kind) {
-    case RK_REAL: rt_real<R>(v, c, op.cr); break;
-    case RK_GEN: rt_gen<R>(v, c, op.cr); break;
-    case RK_ANTI: rt_unit<R>(v, op, c, 0); break;
-    case RK_DIAG: rt_unit<R>(v, op, c, 1); break;
-    default: rt_unit<R>(v, op, c, 2); break;
+    case RK_REAL: {
+      const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+      QAcc x = qacc_new(), y = qacc_new(), z = qacc_new(), w = qacc_new();
+      qacc_add(x, c[0], r0);
+      qacc_add(x, c[1], r1);
+      qacc_add(y, c[0], i0);
+      qacc_add(y, c[1], i1);
+      qacc_add(z, c[2], r0);
+      qacc_add(z, c[3], r1);
+      qacc_add(w, c[2], i0);
+      qacc_add(w, c[3], i1);
+      a0 = make_longlong2(qacc_round(x), qacc_round(y));
+      a1 = make_longlong2(qacc_round(z), qacc_round(w));
+      break;
+    }
+    case RK_GEN: {
+      const QL r0 = q60_split(a0.x), i0 = q60_split(a0.y), r1 = q60_split(a1.x), i1 = q60_split(a1.y);
+      const QL s0 = q60_split(a0.x + a0.y), s1 = q60_split(a1.x + a1.y);
+      const QC u0{c[0], c[1], c[2]}, u1{c[3], c[4], c[5]}, u2{c[6], c[7], c[8]}, u3{c[9], c[10], c[11]};
+      int64_t re, im;
+      q60_gauss_row(u0, u1, r0, i0, s0, r1, i1, s1, &re, &im);
+      const longlong2 b0 = make_longlong2(re, im);
+      q60_gauss_row(u2, u3, r0, i0, s0, r1, i1, s1, &re, &im);
+      a0 = b0;
+      a1 = make_longlong2(re, im);
+      break;
+    }
+    case RK_ANTI: {
+      const longlong2 x0 = a0;
+      a0 = rt_mul(a1, op.code0, c + 3);
+      a1 = rt_mul(x0, op.code1, c + 6);
+      break;
+    }
+    case RK_DIAG:
+      a0 = rt_mul(a0, op.code0, c);
+      a1 = rt_mul(a1, op.code1, c + 9);
+      break;
+    default:  // RK_PH1
+      a1 = rt_mul(a1, op.code1, c + 9);
+      break;
   }
 }
 
-template <bool TAB>
-__device__ __forceinline__ void rt_pair_any(longlong2 (&v)[16], int r0, int r1, const QL* __restrict__ c,
-                                            const int4* __restrict__ tab) {
-  switch (r0 * 4 + r1) {
-    case 1: rt_pair<0, 1, TAB>(v, c, tab); break;
-    case 2: rt_pair<0, 2, TAB>(v, c, tab); break;
-    case 3: rt_pair<0, 3, TAB>(v, c, tab); break;
-    case 6: rt_pair<1, 2, TAB>(v, c, tab); break;
-    case 7: rt_pair<1, 3, TAB>(v, c, tab); break;
-    default: rt_pair<2, 3, TAB>(v, c, tab); break;
+__device__ __forceinline__ void rt_q_op(RtQuad& q, const RtOp& op, const QL* __restrict__ c, const int4* tab0,
+                                        uint64_t base, uint32_t gb) {
+  const uint32_t cr = op.cr;
+  switch (op.kind) {
+    case RK_PAIR:
+      rt_q_pair(q, c, op.table >= 0 ? tab0 : nullptr);
+      break;
+    case RK_TABLE: {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q.a[i] = rt_tab_mul(__ldg(tab0 + q.kk[i]), q.a[i]);
+      break;
+    }
+    case RK_SCAL: {
+      const uint32_t bit = op.sout ? (uint32_t)((base >> op.sbit) & 1ull) : ((gb >> op.sbit) & 1u);
+      const int code = bit ? op.code1 : op.code0;
+      const QL* u = c + (bit ? 9 : 0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if ((q.kk[i] & cr) == cr) q.a[i] = rt_mul(q.a[i], code, u);
+      break;
+    }
+    default:
+      if (op.role == 0) {
+        if ((q.kk[0] & cr) == cr) rt_2x2(q.a[0], q.a[1], op, c);
+        if ((q.kk[2] & cr) == cr) rt_2x2(q.a[2], q.a[3], op, c);
+      } else {
+        if ((q.kk[0] & cr) == cr) rt_2x2(q.a[0], q.a[2], op, c);
+        if ((q.kk[1] & cr) == cr) rt_2x2(q.a[1], q.a[3], op, c);
+      }
+      break;
   }
 }
 
 #ifndef QS_RT_MINB
-#define QS_RT_MINB 1
+#define QS_RT_MINB 3
 #endif
 
 template <int THREADS>
@@ -239,6 +229,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 256 ? QS_RT_MINB : 1)
     swt[h] = (uint8_t)sw;
   }
   const int ngb = m - 4;
+  // this thread's slice of every table (entry k at + k)
+  const int4* tab_t = g.tables + (size_t)tid * 16;
   for (uint64_t r = blockIdx.x; r < g.ntiles; r += gridDim.x) {
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
@@ -252,51 +244,37 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 256 ? QS_RT_MINB : 1)
         uint32_t gb = 0;
         for (int i = 0; i < ngb; ++i) gb |= ((tid >> i) & 1u) << ph.gl[i];
         const uint32_t sb = gb ^ swt[gb >> 3];
-        const uint32_t d0 = rt_bit_phys(ph.rb[0]), d1 = rt_bit_phys(ph.rb[1]), d2 = rt_bit_phys(ph.rb[2]),
-                       d3 = rt_bit_phys(ph.rb[3]);
-        longlong2 v[16];
+        const uint32_t p0 = rt_bit_phys(ph.rb[0]), p1 = rt_bit_phys(ph.rb[1]), p2 = rt_bit_phys(ph.rb[2]),
+                       p3 = rt_bit_phys(ph.rb[3]);
+        auto dsel = [&](int i) { return i == 0 ? p0 : (i == 1 ? p1 : (i == 2 ? p2 : p3)); };
+        for (int u = ph.run_begin; u < ph.run_end; ++u) {
+          const RtRun run = g.runs[u];
+          const int r0 = run.r0, r1 = run.r1;
+          const int o0 = (r0 != 0 && r1 != 0) ? 0 : ((r0 != 1 && r1 != 1) ? 1 : 2);
+          const int o1 = 6 - r0 - r1 - o0;
+          const uint32_t d0 = dsel(r0), d1 = dsel(r1), e0 = dsel(o0), e1 = dsel(o1);
+          const uint32_t k0 = 1u << r0, k1 = 1u << r1, f0 = 1u << o0, f1 = 1u << o1;
+#pragma unroll 1
+          for (int qi = 0; qi < 4; ++qi) {
+            const uint32_t ob = sb ^ ((qi & 1) ? e0 : 0u) ^ ((qi & 2) ? e1 : 0u);
+            const uint32_t kq = ((qi & 1) ? f0 : 0u) | ((qi & 2) ? f1 : 0u);
+            RtQuad q;
+            const uint32_t ad[4] = {ob, ob ^ d0, ob ^ d1, ob ^ d0 ^ d1};
+            q.kk[0] = kq;
+            q.kk[1] = kq | k0;
+            q.kk[2] = kq | k1;
+            q.kk[3] = kq | k0 | k1;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const uint32_t dk = ((k & 1) ? d0 : 0u) ^ ((k & 2) ? d1 : 0u) ^ ((k & 4) ? d2 : 0u) ^ ((k & 8) ? d3 : 0u);
-          v[k] = tile[sb ^ dk];
-        }
-        for (int o = ph.op_begin; o < ph.op_end; ++o) {
-          const RtOp& op = g.ops[o];
-          if ((base & op.ext) != op.ext) continue;  // uniform across the CTA
-          if ((gb & op.gmask) != op.gmask) continue;
-          const QL* c = g.coef + op.coef;
-          const int kind = op.kind;
-          if (kind == RK_PAIR) {
-            if (op.table >= 0)
-              rt_pair_any<true>(v, op.r0, op.r1, c, g.tables + ((size_t)op.table << m) + (size_t)tid * 16);
-            else
-              rt_pair_any<false>(v, op.r0, op.r1, c, nullptr);
-          } else if (kind == RK_TABLE) {
-            const int4* tab = g.tables + ((size_t)op.table << m) + (size_t)tid * 16;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = rt_tab_mul(__ldg(tab + k), v[k]);
-          } else if (kind == RK_SCAL) {
-            const uint32_t bit = op.sout ? (uint32_t)((base >> op.sbit) & 1ull) : ((gb >> op.sbit) & 1u);
-            const int code = bit ? op.code1 : op.code0;
-            if (code == U_ONE) continue;
-            const QL* u = c + (bit ? 9 : 0);
-            const uint32_t cr = op.cr;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-              if (((uint32_t)k & cr) == cr) v[k] = rt_mul(v[k], code, u);
-          } else {
-            switch (op.r0) {
-              case 0: rt_single<0>(v, op, c); break;
-              case 1: rt_single<1>(v, op, c); break;
-              case 2: rt_single<2>(v, op, c); break;
-              default: rt_single<3>(v, op, c); break;
+            for (int i = 0; i < 4; ++i) q.a[i] = tile[ad[i]];
+            for (int o = run.op_begin; o < run.op_end; ++o) {
+              const RtOp& op = g.ops[o];
+              if ((base & op.ext) != op.ext) continue;  // uniform across the CTA
+              if ((gb & op.gmask) != op.gmask) continue;
+              rt_q_op(q, op, g.coef + op.coef, tab_t + ((size_t)(op.table < 0 ? 0 : op.table) << m), base, gb);
             }
-          }
-        }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const uint32_t dk = ((k & 1) ? d0 : 0u) ^ ((k & 2) ? d1 : 0u) ^ ((k & 4) ? d2 : 0u) ^ ((k & 8) ? d3 : 0u);
-          tile[sb ^ dk] = v[k];
+            for (int i = 0; i < 4; ++i) tile[ad[i]] = q.a[i];
+          }
         }
       }
       __syncthreads();
