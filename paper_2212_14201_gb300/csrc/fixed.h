@@ -139,6 +139,23 @@ QS_HD double q60_to_double(int64_t V) {
   return q_from_bits((sign << 63) | (e << 52) | (mant & 0xFFFFFFFFFFFFFull));
 }
 
+// The same value as q60_to_double without branches (|V| < 2^62): normalise |V|
+// so that its leading one is bit 63, keep 53 bits rounded half to even, and
+// place the exponent so that a carry of the mantissa into bit 53 raises it.
+QS_HD double q60_to_double_nb(int64_t V) {
+  const uint64_t s = (uint64_t)(V >> 63);
+  const uint64_t a = ((uint64_t)V ^ s) - s;
+  const int lz = q_clz64(a);  // 64 for a == 0
+  const uint64_t x = a << (lz & 63);
+  uint64_t mant = x >> 11;
+  const uint32_t rem = (uint32_t)x & 0x7FFu;
+  mant += (uint64_t)((rem > 0x400u) | ((rem == 0x400u) & ((uint32_t)mant & 1u)));
+  // leading bit 63 - lz: biased exponent 1026 - lz, one of which the mantissa's
+  // leading one supplies
+  const uint64_t bits = ((uint64_t)(1025 - lz) << 52) + mant;
+  return a ? q_from_bits((s << 63) | bits) : 0.0;
+}
+
 // Limb split V = h * 2^30 + l with 0 <= l < 2^30 (h = floor(V / 2^30)).
 struct QL {
   int32_t h, l;

@@ -21,6 +21,7 @@
 #include <new>
 #include <vector>
 
+#include "q60pair.cuh"
 #include "regtile.h"
 #include "tile.h"
 
@@ -1108,13 +1109,18 @@ static int build_rt_program(int n, const std::vector<Op1>& rops, const int* loca
           const Op1& ob = rops[x.b];
           const Op1& on0 = x.ra == b0 ? oa : ob;  // the rotation on run bit r0
           const Op1& on1 = x.ra == b0 ? ob : oa;
-          for (int qo = 0; qo < 4; ++qo)
-            for (int qi = 0; qi < 4; ++qi) {
-              const double v = on1.m.m[2 * (qo >> 1) + (qi >> 1)].re * on0.m.m[2 * (qo & 1) + (qi & 1)].re;
-              pr->coef.push_back(q60_split(q60_from_double(v)));
-            }
-          nc = 16;
-          pr->int_ops += 24.0;
+          double m0[4], m1[4];
+          for (int e = 0; e < 4; ++e) {
+            m0[e] = on0.m.m[e].re;
+            m1[e] = on1.m.m[e].re;
+          }
+          QL cf[6];
+          int flags = 0;
+          q60_pair_coef(m0, m1, cf, &flags);
+          for (int e = 0; e < 6; ++e) pr->coef.push_back(cf[e]);
+          t.role = (uint8_t)flags;
+          nc = 6;
+          pr->int_ops += 12.0;  // 8 real products per quad and component: 2 x 3 x 8 / 4 per amplitude
         } else if (x.kind != RK_TABLE) {
           const Op1& o = rops[x.a];
           uint32_t lcm = 0;
@@ -1383,15 +1389,27 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       QL* e1 = reinterpret_cast<QL*>(t1.q);
       float* f0 = reinterpret_cast<float*>(t0.f);
       float* f1 = reinterpret_cast<float*>(t1.f);
-      for (int k = 0; k < 4; ++k)
-        for (int c = 0; c < 4; ++c) {
-          const double v = rb.m[2 * (k >> 1) + (c >> 1)].re * ra.m[2 * (k & 1) + (c & 1)].re;
-          const int e = 4 * k + c;
-          if (f32) (e < 8 ? f0[e] : f1[e - 8]) = (float)v;
-          else (e < 12 ? e0[e] : e1[e - 12]) = q60_split(q60_from_double(v));
+      if (f32) {
+        for (int k = 0; k < 4; ++k)
+          for (int c = 0; c < 4; ++c) {
+            const double v = rb.m[2 * (k >> 1) + (c >> 1)].re * ra.m[2 * (k & 1) + (c & 1)].re;
+            const int e = 4 * k + c;
+            (e < 8 ? f0[e] : f1[e - 8]) = (float)v;
+          }
+        flops += N * 16.0;  // 4 real multiply-adds per output component, 2 components, per 4 amplitudes x 4 outputs
+      } else {
+        // two complex products on the quad (q60pair.cuh): 6 limb pairs, reflection flags in lcmask
+        double m0[4], m1[4];
+        for (int e = 0; e < 4; ++e) {
+          m0[e] = ra.m[e].re;
+          m1[e] = rb.m[e].re;
         }
-      if (f32) flops += N * 16.0;  // 4 real multiply-adds per output component, 2 components, per 4 amplitudes x 4 outputs
-      else int_ops += N * 24.0;    // two real rotations: 12 limb products per amplitude each
+        int flags = 0;
+        q60_pair_coef(m0, m1, e0, &flags);
+        t0.lcmask = (uint32_t)flags;
+        (void)e1;
+        int_ops += N * 12.0;  // 8 real products per quad and component: 12 limb products per amplitude
+      }
       g->nops += 2;
       ++i;
       continue;

@@ -27,8 +27,8 @@ constexpr int RT_MIN_M = 4;
 constexpr int RT_MAX_M = 12;       // 2^(m-4) <= 256 threads, one group of 16 amplitudes each
 
 enum RtKind : uint8_t {
-  RK_PAIR = 0,   // real 4x4 on the quad (R (x) R' of two rotations on the run's two bits):
-                 // 16 QL, row-major, quad index bit(r0) + 2 bit(r1) of the run
+  RK_PAIR = 0,   // R1 (x) R0, two real orthogonal ops on the run's bits r0, r1, as two complex
+                 // products (q60pair.cuh): 6 QL, reflection flags in `role`
   RK_REAL = 1,   // real 2x2 on quad bit `role` (0: the run's r0, 1: its r1): 4 QL (m00 m01 m10 m11)
   RK_GEN = 2,    // general 2x2 on quad bit `role`: 4 Gauss-form entries (qc_make_gauss), 12 QL
   RK_ANTI = 3,   // antidiagonal on quad bit `role` (codes code0 / code1 of entries 01 / 10)

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "q60pair.cuh"
 #include "tile.h"
 
 namespace qs {
@@ -184,18 +185,15 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
   }
 }
 
-// Two real rotations on tile bits a (low) and b as one real 4x4 matrix M on the
-// quads (j, j|a, j|b, j|a|b): each output component sums four products in one
-// accumulator pair, so a quad costs the same 96 wide multiply-adds as the two
-// rotations apart but half the limb splits, roundings, shared-memory round trips
-// and barriers.  Every row of M (a Kronecker product of two rotations) has an L1
-// norm of at most 2, the bound the accumulators were sized for.
-// With a phase table (tab != nullptr, the table op just before the pair): every
-// amplitude of the quad is first multiplied by its table entry, which saves the
-// table op's own shared-memory round trip, index arithmetic and barrier.
+// Two real rotations on tile bits a and b on the quads (j, j|a, j|b, j|a|b), as
+// two complex products per quad and component (q60pair.cuh): 48 wide
+// multiply-adds per quad where the 4x4 matrix takes 96.  With a phase table
+// (tab != nullptr, the table op just before the pair): every amplitude of the
+// quad is first multiplied by its table entry, which saves the table op's own
+// shared-memory round trip, index arithmetic and barrier.
 template <int THREADS>
 __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* m0,
-                                          const QL* m1, const int2* tab) {
+                                          int flags, const int2* tab) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
@@ -203,32 +201,21 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
     uint32_t j = i + (i & ~(lo - 1));  // insert a zero bit at lo, then at hi
     j = j + (j & ~(hi - 1));
     const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
-    QL r[4], im[4];
+    longlong2 v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      longlong2 v = tile[jj[c]];
+      v[c] = tile[jj[c]];
       if (tab) {
         const int2 ur = __ldg(tab + jj[c]), ui = __ldg(tab + TS + jj[c]), un = __ldg(tab + 2 * TS + jj[c]);
         const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
         int64_t vr, vi;
-        q60_gauss_mul(u, q60_split(v.x), q60_split(v.y), q60_split(v.x + v.y), &vr, &vi);
-        v = make_longlong2(vr, vi);
+        q60_gauss_mul(u, q60_split(v[c].x), q60_split(v[c].y), q60_split(v[c].x + v[c].y), &vr, &vi);
+        v[c] = make_longlong2(vr, vi);
       }
-      r[c] = q60_split(v.x);
-      im[c] = q60_split(v.y);
     }
+    q60_pair_quad(v[0], v[1], v[2], v[3], m0, flags);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      QAcc xr = qacc_new(), xi = qacc_new();
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int e = 4 * k + c;
-        const QL u = e < 12 ? m0[e] : m1[e - 12];
-        qacc_add(xr, u, r[c]);
-        qacc_add(xi, u, im[c]);
-      }
-      tile[jj[k]] = make_longlong2(qacc_round(xr), qacc_round(xi));
-    }
+    for (int c = 0; c < 4; ++c) tile[jj[c]] = v[c];
   }
 }
 
@@ -339,10 +326,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
                                           : nullptr;
           if (tab)
             quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
-                               reinterpret_cast<const QL*>(g.ops[k + 1].q), tab);
+                               (int)op.lcmask, tab);
           else
             quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
-                               reinterpret_cast<const QL*>(g.ops[k + 1].q), nullptr);
+                               (int)op.lcmask, nullptr);
           ++k;  // the continuation slot
           __syncthreads();
           continue;

@@ -22,10 +22,11 @@ enum TileOpKind : int8_t {
   TOP_SCALAR = 9,  // diagonal op whose target lies outside the tile: a per-tile scalar
   TOP_DTABLE = 10, // Q60 only: a_j *= T[j], a diagonal over the tile's 2^tb amplitudes
                    // (table index in lcmask; TileArgs::tables)
-  TOP_REAL2 = 11,  // Q60 only: two real rotations on tile bits tb and code0 as one real 4x4
-                   // matrix on amplitude quads; its 16 entries (row-major, quad index
-                   // 2*bit(code0) + bit(tb)) fill q[] of this slot (12) and the next (4);
-                   // code1 >= 0: phase table code1 applied first (the op before the pair)
+  TOP_REAL2 = 11,  // two real rotations on tile bits tb and code0 on amplitude quads (quad
+                   // index 2*bit(code0) + bit(tb)): Q60, two complex products (q60pair.cuh,
+                   // 6 limb pairs in q[], reflection flags in lcmask); FP32, the real 4x4
+                   // (16 floats in f[] of this slot and the next); code1 >= 0: phase
+                   // table code1 applied first (the op before the pair)
   TOP_CONT = 12,   // continuation slot of the op before it (never run on its own)
 };
 

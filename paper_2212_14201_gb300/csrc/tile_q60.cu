@@ -12,15 +12,16 @@
 // separates phases; the tile is converted back and written once.
 //
 // Arithmetic per op (limb products, 3 wide multiply-adds each, fixed.h):
-//   PAIR  two real rotations on the run's bits as one real 4x4 on the quad:
-//         16 products per quad and component (the same as the two apart), half the
-//         limb splits and roundings;
+//   PAIR  two real rotations on the run's bits as two complex products on the
+//         quad (q60pair.cuh): 8 products per quad and component, half of what
+//         the two rotations cost apart;
 //   REAL  real 2x2: 4 products per pair and component;
 //   GEN   general 2x2, Gauss form: 6 products per output;
 //   TABLE a full-tile diagonal, one Gauss-form complex product per amplitude,
 //         entries read from L2 in the order the phase's threads use them.
 #include <algorithm>
 
+#include "q60pair.cuh"
 #include "regtile.h"
 
 namespace qs {
@@ -30,27 +31,11 @@ __constant__ uint8_t c_rt_swz[16] = {1, 2, 4, 3, 5, 6, 7, 1, 2, 4, 3, 5, 6, 7, 1
 // Physical shared-memory index of a single tile bit b.
 __device__ __forceinline__ uint32_t rt_bit_phys(int b) { return (1u << b) ^ (b < 3 ? 0u : (uint32_t)c_rt_swz[b]); }
 
-// Nearest double to V * 2^-60 (round half to even) without branches, integer
-// operations only (the FP64 pipe runs at 1/64 of the integer rate).
-__device__ __forceinline__ double rt_to_double(int64_t V) {
-  const uint64_t s = (uint64_t)(V >> 63);
-  const uint64_t a = ((uint64_t)V ^ s) - s;  // |V|; |V| < 2^62 here
-  const int lz = __clzll((long long)a);       // 64 for a == 0
-  const uint64_t x = a << (lz & 63);          // leading one at bit 63
-  uint64_t mant = x >> 11;                    // 53 bits with the leading one
-  const uint32_t rem = (uint32_t)x & 0x7FFu;
-  mant += (uint64_t)((rem > 0x400u) | ((rem == 0x400u) & (uint32_t)mant & 1u));
-  // leading bit 63 - lz of V: biased exponent 1026 - lz; the leading one of mant
-  // adds 1 to the exponent field, and a carry to 2^53 adds one more
-  const uint64_t bits = ((uint64_t)(1025 - lz) << 52) + mant;
-  return a ? __longlong_as_double((long long)((s << 63) | bits)) : 0.0;
-}
-
 __device__ __forceinline__ longlong2 rt_load(const double2& x) {
   return make_longlong2(q60_from_double_nb(x.x), q60_from_double_nb(x.y));
 }
 __device__ __forceinline__ double2 rt_store(const longlong2& v) {
-  return make_double2(rt_to_double(v.x), rt_to_double(v.y));
+  return make_double2(q60_to_double_nb(v.x), q60_to_double_nb(v.y));
 }
 
 // c + i d (table entry as Q60 limbs c.h c.l d.h d.l) times a, Gauss form:
@@ -98,26 +83,12 @@ struct RtQuad {
   uint32_t kk[4];
 };
 
-__device__ __forceinline__ void rt_q_pair(RtQuad& q, const QL* __restrict__ c, const int4* __restrict__ tab) {
-  QL r[4], im[4];
+__device__ __forceinline__ void rt_q_pair(RtQuad& q, const QL* __restrict__ c, int flags, const int4* __restrict__ tab) {
+  if (tab) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    longlong2 x = q.a[i];
-    if (tab) x = rt_tab_mul(__ldg(tab + q.kk[i]), x);
-    r[i] = q60_split(x.x);
-    im[i] = q60_split(x.y);
+    for (int i = 0; i < 4; ++i) q.a[i] = rt_tab_mul(__ldg(tab + q.kk[i]), q.a[i]);
   }
-#pragma unroll
-  for (int row = 0; row < 4; ++row) {
-    QAcc xr = qacc_new(), xi = qacc_new();
-#pragma unroll
-    for (int col = 0; col < 4; ++col) {
-      const QL u = c[4 * row + col];
-      qacc_add(xr, u, r[col]);
-      qacc_add(xi, u, im[col]);
-    }
-    q.a[row] = make_longlong2(qacc_round(xr), qacc_round(xi));
-  }
+  q60_pair_quad(q.a[0], q.a[1], q.a[2], q.a[3], c, flags);
 }
 
 // A one-qubit op on the amplitude pair (a0, a1) = (bit 0, bit 1 of its target).
@@ -171,7 +142,7 @@ __device__ __forceinline__ void rt_q_op(RtQuad& q, const RtOp& op, const QL* __r
   const uint32_t cr = op.cr;
   switch (op.kind) {
     case RK_PAIR:
-      rt_q_pair(q, c, op.table >= 0 ? tab0 : nullptr);
+      rt_q_pair(q, c, op.role, op.table >= 0 ? tab0 : nullptr);
       break;
     case RK_TABLE: {
 #pragma unroll

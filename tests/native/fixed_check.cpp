@@ -1,6 +1,7 @@
 // Host-side harness for the Q60 helpers of the CUDA library (compiled by the
 // test suite with g++; exercises the same inline functions the kernels use).
 #include "fixed.h"
+#include "q60pair.cuh"
 
 extern "C" {
 long long fc_from_double(double v) { return (long long)qs::q60_from_double(v); }
@@ -12,6 +13,35 @@ void fc_dot2_exact(long long x1, long long y1, long long x2, long long y2, unsig
   out[1] = (unsigned long long)(r >> 64);
 }
 double fc_to_double(long long V) { return qs::q60_to_double((int64_t)V); }
+double fc_to_double_nb(long long V) { return qs::q60_to_double_nb((int64_t)V); }
+// the coefficients of the pair form as Q60 integers (P.re, P.im, -P.im, Q.re,
+// Q.im, -Q.im) and the reflection flags
+int fc_pair_coef(const double* ra, const double* rb, long long* c) {
+  qs::QL q[6];
+  int flags = 0;
+  qs::q60_pair_coef(ra, rb, q, &flags);
+  for (int k = 0; k < 6; ++k) c[k] = (long long)q[k].h * (1ll << 30) + q[k].l;
+  return flags;
+}
+// two real orthogonal 2x2 ops (ra on quad bit a, rb on bit b; row-major) on one
+// component of a quad x[4] (Q60 integers, index bit(a) + 2 bit(b)), through the
+// two-complex-product form of the pair kernels
+void fc_pair_comp(const double* ra, const double* rb, long long* x) {
+  qs::QL c[6];
+  int flags = 0;
+  qs::q60_pair_coef(ra, rb, c, &flags);
+  int64_t x0 = x[0], x1 = x[1], x2 = x[2], x3 = x[3];
+  switch (flags) {
+    case 0: qs::q60_pair_comp<0>(x0, x1, x2, x3, c); break;
+    case 1: qs::q60_pair_comp<1>(x0, x1, x2, x3, c); break;
+    case 2: qs::q60_pair_comp<2>(x0, x1, x2, x3, c); break;
+    default: qs::q60_pair_comp<3>(x0, x1, x2, x3, c); break;
+  }
+  x[0] = x0;
+  x[1] = x1;
+  x[2] = x2;
+  x[3] = x3;
+}
 // out = u0 * a0 + u1 * a1 for Q60 reals given as int64, via the limb accumulator
 long long fc_dot2(long long u0, long long a0, long long u1, long long a1) {
   qs::QAcc acc{0, 0};

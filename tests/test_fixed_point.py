@@ -29,6 +29,12 @@ def fc():
     lib.fc_dot2_exact.argtypes = [ctypes.c_longlong] * 4 + [ctypes.c_void_p]
     lib.fc_to_double.restype = ctypes.c_double
     lib.fc_to_double.argtypes = [ctypes.c_longlong]
+    lib.fc_to_double_nb.restype = ctypes.c_double
+    lib.fc_to_double_nb.argtypes = [ctypes.c_longlong]
+    lib.fc_pair_coef.restype = ctypes.c_int
+    lib.fc_pair_coef.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.fc_pair_comp.restype = None
+    lib.fc_pair_comp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc_dot2.restype = ctypes.c_longlong
     lib.fc_dot2.argtypes = [ctypes.c_longlong] * 4
     lib.fc_dot4.restype = ctypes.c_longlong
@@ -181,3 +187,70 @@ def test_gauss_row_error_bound(fc):
         ex_im = Fraction(uq[0] * a[1] + uq[1] * a[0] + uq[2] * a[3] + uq[3] * a[2], 1 << 60)
         assert abs(out[0] - ex_re) <= 7, trial
         assert abs(out[1] - ex_im) <= 7, trial
+
+
+def test_branch_free_to_double_matches(fc):
+    """The branch-free conversion the register engine uses gives the same double
+    as the reference conversion (itself checked against exact rounding above)."""
+    g = np.random.Generator(np.random.PCG64(11))
+    Vs = [0, 1, -1, 2 ** 53 - 1, 2 ** 53, 2 ** 53 + 1, -(2 ** 53 + 3), 2 ** 60, -(2 ** 60), 2 ** 61 + 5, -(2 ** 61) - 7]
+    Vs += [int(x) for x in g.integers(-2 ** 61, 2 ** 61, 4000)]
+    Vs += [int(x) >> int(k) for x, k in zip(g.integers(-2 ** 61, 2 ** 61, 2000), g.integers(0, 61, 2000))]
+    # ties at the 53-bit boundary: both parities of the kept bit
+    Vs += [(m << 11) | 0x400 for m in range(2 ** 52, 2 ** 52 + 8)] + [-((m << 10) | 0x200) for m in range(2 ** 52, 2 ** 52 + 8)]
+    for V in Vs:
+        assert fc.fc_to_double_nb(V) == fc.fc_to_double(V), V
+
+
+def _orth(g, reflect):
+    t = g.uniform(0, 2 * np.pi)
+    c, s = math.cos(t), math.sin(t)
+    return np.array([c, s, s, -c] if reflect else [c, -s, s, c], dtype=np.float64)
+
+
+@pytest.mark.parametrize("fa,fb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_pair_as_two_complex_products(fc, fa, fb):
+    """R_b (x) R_a on a quad component through the two-complex-product form.
+    (1) The coefficients: u = z0 + i z1 and v = z0 - i z1 (z_b = x_b0 + i x_b1,
+    after the reflections' sign flips) scaled by P and Q, then z0 = u' + v',
+    z1 = -i (u' - v'), reproduce the 4x4 Kronecker product of the two double
+    matrices within double rounding.  (2) The limb arithmetic: the kernel's
+    outputs equal that formula evaluated exactly on the same Q60 integers (inputs
+    and the kernel's rounded P, Q) within 12 units of 2^-60."""
+    g = np.random.Generator(np.random.PCG64(20 + 2 * fa + fb))
+    sa, sb = (-1 if fa else 1), (-1 if fb else 1)
+    for _ in range(300):
+        ra, rb = _orth(g, fa), _orth(g, fb)
+        c = np.zeros(6, dtype=np.int64)
+        flags = fc.fc_pair_coef(ra.ctypes.data, rb.ctypes.data, c.ctypes.data)
+        assert flags == fa | (fb << 1)
+        P = complex(c[0], c[1]) / 2.0 ** 60
+        Q = complex(c[3], c[4]) / 2.0 ** 60
+        assert c[2] == -c[1] and c[5] == -c[4]
+
+        # (1) the matrix of the form, column by column, against kron(rb, ra)
+        K = np.kron(rb.reshape(2, 2), ra.reshape(2, 2))
+        for qi in range(4):
+            e = np.zeros(4)
+            e[qi] = 1.0
+            y = [e[0], sa * e[1], sb * e[2], sa * sb * e[3]]
+            u = complex(y[0] - y[3], y[1] + y[2])
+            v = complex(y[0] + y[3], y[1] - y[2])
+            U, V = P * u, Q * v
+            col = [U.real + V.real, U.imag + V.imag, U.imag - V.imag, V.real - U.real]
+            assert np.max(np.abs(np.array(col) - K[:, qi])) < 4e-16
+        # (2) the limb arithmetic against the exact evaluation on the same integers
+        v = g.normal(size=4)
+        v *= g.uniform(0, 1.25) / np.linalg.norm(v)
+        x = np.array([exact_q60(float(t)) for t in v], dtype=np.int64)
+        out = x.copy()
+        fc.fc_pair_comp(ra.ctypes.data, rb.ctypes.data, out.ctypes.data)
+        y = [Fraction(int(x[0])), sa * Fraction(int(x[1])), sb * Fraction(int(x[2])), sa * sb * Fraction(int(x[3]))]
+        ur, ui = y[0] - y[3], y[1] + y[2]
+        vr, vi = y[0] + y[3], y[1] - y[2]
+        pr, pi, qr, qi_ = (Fraction(int(t), 1 << 60) for t in (c[0], c[1], c[3], c[4]))
+        Ur, Ui = pr * ur - pi * ui, pi * ur + pr * ui
+        Vr, Vi = qr * vr - qi_ * vi, qi_ * vr + qr * vi
+        exact = [Ur + Vr, Ui + Vi, Ui - Vi, Vr - Ur]
+        for qo in range(4):
+            assert abs(Fraction(int(out[qo])) - exact[qo]) <= 12, (qo, float(Fraction(int(out[qo])) - exact[qo]))
