@@ -234,23 +234,27 @@ int qs_set_aggregate(int on);
  * entries formed in double).  Always QS_OK. */
 int qs_set_phase_tables(int on);
 
-/* Process-wide switch (default on): in Q60 tile passes, two consecutive real
+/* Process-wide switch (default on): in Q60 tile passes, consecutive real
  * one-qubit ops on different tile qubits (the real rotations the phase tables
- * leave, RY, ...) run as one real 4x4 op on amplitude quads.  The multiply-adds
- * are the same; the limb splits, roundings, shared-memory round trips and
- * barriers halve.  A phase table op just before a pair runs inside the pair's
- * quad loop.  Results agree with the switch off within the Q60 rounding (one
- * rounding per output instead of two).  For measurement: on = 1 (default) pairs
- * with tables fused, 2 pairs without table fusion, 0 neither.  Always QS_OK. */
+ * leave, RY, ...) run together.  Two of them run on amplitude quads as two
+ * complex products per quad and component (u = z0 + i z1 and v = z0 - i z1,
+ * z_b the complex number formed along the first qubit: both rotations act on u
+ * and v as multiplications), three on amplitude octets as four complex products
+ * (the same basis change along each further qubit): 8 and 16 real products
+ * where the rotations apart take 16 and 24.  A phase table op just before the
+ * group runs inside its loop.  Results agree with the switch off within the
+ * Q60 rounding.  For measurement: on = 1 (default) triples and pairs with
+ * tables fused, 3 pairs only with tables fused, 2 pairs without table fusion,
+ * 0 neither.  Always QS_OK. */
 int qs_set_rotation_pairs(int on);
 
-/* Process-wide choice of the Q60 tile-pass kernel: bits = 4 (default) runs the
- * register-phase engine (the ops of a pass grouped into phases of four tile
- * qubits; each thread applies a phase's ops to the 16 amplitudes it holds in
- * registers, one shared-memory exchange per phase; tiles of 4..12 qubits); 0
- * runs one shared-memory sweep per op.  Both give the amplitudes within the Q60
- * rounding; the switch is for measurement.  Errors: INVALID_ARG for other
- * values. */
+/* Process-wide choice of the Q60 tile-pass kernel: 0 (default) runs one
+ * shared-memory sweep per op; bits = 4 runs the register-phase engine (the ops
+ * of a pass grouped into phases of four tile qubits; each thread applies a
+ * phase's ops to the 16 amplitudes of its group, streaming them through
+ * registers a quad at a time; tiles of 4..12 qubits).  Both give the amplitudes
+ * within the Q60 rounding; the switch is for measurement.  Errors: INVALID_ARG
+ * for other values. */
 int qs_set_register_phases(int bits);
 
 /* Greedy plan with an explicit tile width: tiles of tile_qubits (4..13) qubits,

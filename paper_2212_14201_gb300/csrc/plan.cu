@@ -828,16 +828,19 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
   return QS_OK;
 }
 
-// Register-phase tile engine (tile_q60.cu) for Q60 passes: 4 = on (default), 0 =
-// the per-op shared-memory engine (k_tile<EngQ60>), kept for measurement.
-static int g_register_bits = 4;
+// Q60 tile engine: 0 = one shared-memory sweep per op (k_tile<EngQ60>, the
+// default), 4 = register phases (tile_q60.cu), kept for measurement.
+static int g_register_bits = 0;
 static bool g_aggregate = true;
 static bool g_rotation_pairs = true;
 static bool g_fuse_tables = true;
 
+static bool g_rotation_triples = true;
+
 extern "C" int qs_set_rotation_pairs(int on) {
   g_rotation_pairs = on != 0;
   g_fuse_tables = on > 0 && on != 2;
+  g_rotation_triples = on == 1;
   return QS_OK;
 }
 
@@ -1361,9 +1364,49 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
   const bool pairs = ((fixed && s->prec == 128) || f32) && g_rotation_pairs;
+  const bool triples = g_rotation_triples;
   auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
+    if (pairs && triples && !f32 && i + 2 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
+        in_tile_real(rops[i + 2]) && rops[i + 1].target != op.target && rops[i + 2].target != op.target &&
+        rops[i + 2].target != rops[i + 1].target) {
+      // three real rotations on different tile qubits: one op on octets (two slots)
+      int tab = -1;
+      if (g_fuse_tables && i > 0 && rops[i - 1].cls == kTableMark && g->nops > 0 &&
+          g->ops[g->nops - 1].kind == TOP_DTABLE && g->ops[g->nops - 1].lcmask < 128) {
+        --g->nops;
+        tab = (int)g->ops[g->nops].lcmask;
+      }
+      TileOp& t0 = g->ops[g->nops];
+      TileOp& t1 = g->ops[g->nops + 1];
+      memset(&t0, 0, sizeof t0);
+      memset(&t1, 0, sizeof t1);
+      t0.kind = TOP_REAL3;
+      t0.tb = (int8_t)local[op.target];
+      t0.code0 = (int8_t)local[rops[i + 1].target];
+      t0.code1 = (int8_t)tab;
+      t1.kind = TOP_CONT;
+      double m0[4], m1[4], m2[4];
+      for (int e = 0; e < 4; ++e) {
+        m0[e] = op.m.m[e].re;
+        m1[e] = rops[i + 1].m.m[e].re;
+        m2[e] = rops[i + 2].m.m[e].re;
+      }
+      QL c[8];
+      int flags = 0;
+      q60_triple_coef(m0, m1, m2, c, &flags);
+      Q3 P[4][3];
+      q60_triple_q3(c, P);
+      Q3* d0 = reinterpret_cast<Q3*>(t0.q);
+      Q3* d1 = reinterpret_cast<Q3*>(t1.q);
+      for (int e = 0; e < 12; ++e) (e < 8 ? d0[e] : d1[e - 8]) = P[e / 3][e % 3];
+      t0.lcmask = (uint32_t)flags | ((uint32_t)local[rops[i + 2].target] << 8);
+      int_ops += N * 12.0;  // 16 real products per octet and component: 12 limb products per amplitude
+      g->nops += 2;
+      i += 2;
+      continue;
+    }
     if (pairs && i + 1 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
         rops[i + 1].target != op.target) {
       // two real rotations on different tile qubits: one 4x4 op on quads (two slots)
@@ -1469,7 +1512,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     const TileOp& o = g->ops[k];
     if (o.kind == TOP_DTABLE && (o.lcmask >= ptables.size() || o.tb != m || ptables[o.lcmask].t.size() != ((size_t)1 << m)))
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed phase-table op");
-    if (o.kind == TOP_REAL2 && (k + 1 >= g->nops || g->ops[k + 1].kind != TOP_CONT ||
+    if ((o.kind == TOP_REAL2 || o.kind == TOP_REAL3) && (k + 1 >= g->nops || g->ops[k + 1].kind != TOP_CONT ||
                                 (o.code1 >= 0 && (size_t)o.code1 >= ptables.size())))
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed rotation-pair op");
   }

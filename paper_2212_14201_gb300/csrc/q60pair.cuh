@@ -101,27 +101,145 @@ __device__ __forceinline__ void q60_pair_quad(longlong2& q0, longlong2& q1, long
 }
 #endif
 
+// Three real rotations on tile bits a, b, c, applied to an amplitude octet
+// (index bit(a) + 2 bit(b) + 4 bit(c)) as four complex products.
+//
+// With z_cb = x_cb0 + i x_cb1, u_c = z_c0 + i z_c1, v_c = z_c0 - i z_c1 (the pair
+// basis along b) and U+- = u_0 +- i u_1, V+- = v_0 +- i v_1 (the same along c),
+// R_c (x) R_b (x) R_a multiplies U+ by w_a w_b w_c, U- by w_a w_b conj(w_c), V+ by
+// w_a conj(w_b) w_c and V- by w_a conj(w_b) conj(w_c) (C (x) C (x) C splits into
+// four copies of C).  The inverse is u_0 = (U+ + U-) / 2, u_1 = -i (U+ - U-) / 2,
+// the same for v, then z_c0 = (u_c + v_c) / 2, z_c1 = -i (u_c - v_c) / 2; the 1/4
+// goes into the four coefficients.  16 real products per octet and component,
+// against 24 for a pair and a single rotation.
+// |U+-|, |V+-| <= 2 |octet component| <= 2.5, so the products take the basis
+// values split as h 2^31 + l (0 <= l < 2^31): U P / 2^60 = (2 Ph) h + (Ph l +
+// (2 Pl) h) / 2^30, with Ph, Pl the 30-bit limbs of a coefficient (|P| <= 1/4).
+struct Q3 {
+  int32_t h2, h, l2;  // limbs of a coefficient for products with 31-bit-split values
+};
+QS_HD Q3 q3_of(QL p) { return Q3{p.h * 2, p.h, p.l * 2}; }
+QS_HD Q3 q3_neg(Q3 p) { return Q3{-p.h2, -p.h, -p.l2}; }
+QS_HD void q3_add(QAcc& A, Q3 p, int32_t yh, int32_t yl) {
+  A.hi = madw(p.h2, yh, A.hi);
+  A.mid = madw(p.h, yl, A.mid);
+  A.mid = madw(p.l2, yh, A.mid);
+}
+
+// One component of the octet; P[k] = (re, im, -im) of coefficient k (U+, U-, V+, V-).
+QS_HD void q60_triple_comp(int64_t (&x)[8], const Q3 (&P)[4][3]) {
+  int64_t ur[2], ui[2], vr[2], vi[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int64_t z0r = x[4 * c], z0i = x[4 * c + 1], z1r = x[4 * c + 2], z1i = x[4 * c + 3];
+    ur[c] = z0r - z1i;
+    ui[c] = z0i + z1r;
+    vr[c] = z0r + z1i;
+    vi[c] = z0i - z1r;
+  }
+  const int64_t Y[8] = {ur[0] - ui[1], ui[0] + ur[1], ur[0] + ui[1], ui[0] - ur[1],
+                        vr[0] - vi[1], vi[0] + vr[1], vr[0] + vi[1], vi[0] - vr[1]};
+  int32_t yh[8], yl[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    yh[k] = (int32_t)(Y[k] >> 31);
+    yl[k] = (int32_t)(Y[k] & 0x7FFFFFFF);
+  }
+  int64_t R[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    QAcc A = qacc_new(), B = qacc_new();
+    q3_add(A, P[k][0], yh[2 * k], yl[2 * k]);  // re = P.re Y.re - P.im Y.im
+    q3_add(A, P[k][2], yh[2 * k + 1], yl[2 * k + 1]);
+    q3_add(B, P[k][1], yh[2 * k], yl[2 * k]);  // im = P.im Y.re + P.re Y.im
+    q3_add(B, P[k][0], yh[2 * k + 1], yl[2 * k + 1]);
+    R[2 * k] = qacc_round(A);
+    R[2 * k + 1] = qacc_round(B);
+  }
+  const int64_t u0r = R[0] + R[2], u0i = R[1] + R[3], u1r = R[1] - R[3], u1i = R[2] - R[0];
+  const int64_t v0r = R[4] + R[6], v0i = R[5] + R[7], v1r = R[5] - R[7], v1i = R[6] - R[4];
+  x[0] = u0r + v0r;
+  x[1] = u0i + v0i;
+  x[2] = u0i - v0i;
+  x[3] = v0r - u0r;
+  x[4] = u1r + v1r;
+  x[5] = u1i + v1i;
+  x[6] = u1i - v1i;
+  x[7] = v1r - u1r;
+}
+
+// The coefficients in the form the products take: P[k] = (re, im, -im) of
+// coefficient k (U+, U-, V+, V-) as Q3 limbs, from (re, im) limb pairs.
+QS_HD void q60_triple_q3(const QL* c, Q3 (&P)[4][3]) {
+  for (int k = 0; k < 4; ++k) {
+    P[k][0] = q3_of(c[2 * k]);
+    P[k][1] = q3_of(c[2 * k + 1]);
+    P[k][2] = q3_neg(P[k][1]);
+  }
+}
+
+#ifdef __CUDACC__
+// The octet v[0..7]; P: the Q3 coefficients; flags bit k: rotation k (a, b, c) is
+// a reflection, whose sign flip of its bit-1 half comes first.
+__device__ __forceinline__ void q60_triple_octet(longlong2 (&v)[8], const Q3 (&P)[4][3], int flags) {
+  if (flags) {
+#pragma unroll
+    for (int k = 1; k < 8; ++k)
+      if (__popc(k & flags) & 1) v[k] = make_longlong2(-v[k].x, -v[k].y);
+  }
+  int64_t r[8], im[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    r[k] = v[k].x;
+    im[k] = v[k].y;
+  }
+  q60_triple_comp(r, P);
+  q60_triple_comp(im, P);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = make_longlong2(r[k], im[k]);
+}
+#endif
+
+// Host: rotation angle (c, s) of a real orthogonal 2x2 (row-major) and whether it
+// is a reflection R Z.
+inline int q60_orth_angle(const double* m, double* c, double* s) {
+  const double det = m[0] * m[3] - m[1] * m[2];
+  const double sg = det < 0.0 ? -1.0 : 1.0;
+  double cc = 0.5 * (m[0] + sg * m[3]), ss = 0.5 * (m[2] - sg * m[1]);
+  const double r = std::sqrt(cc * cc + ss * ss);
+  if (r > 0.0) {
+    cc /= r;
+    ss /= r;
+  } else {
+    cc = 1.0;
+    ss = 0.0;
+  }
+  *c = cc;
+  *s = ss;
+  return det < 0.0 ? 1 : 0;
+}
+
+// Host: the four coefficients (re, im limb pairs: U+, U-, V+, V-) and the flags
+// of R_c (x) R_b (x) R_a.
+inline void q60_triple_coef(const double* ra, const double* rb, const double* rc, QL out[8], int* flags) {
+  double ca, sa, cb, sb, cc, sc;
+  const int fa = q60_orth_angle(ra, &ca, &sa), fb = q60_orth_angle(rb, &cb, &sb), fc = q60_orth_angle(rc, &cc, &sc);
+  *flags = fa | (fb << 1) | (fc << 2);
+  // w_a w_b^(+-1) w_c^(+-1) / 4
+  for (int k = 0; k < 4; ++k) {
+    const double sbk = (k & 2) ? -sb : sb, sck = (k & 1) ? -sc : sc;
+    const double abr = ca * cb - sa * sbk, abi = sa * cb + ca * sbk;
+    const double re = 0.25 * (abr * cc - abi * sck), im = 0.25 * (abi * cc + abr * sck);
+    out[2 * k] = q60_split(q60_from_double(re));
+    out[2 * k + 1] = q60_split(q60_from_double(im));
+  }
+}
+
 // Host: the six limb pairs and the flags of R_b (x) R_a (a, b real orthogonal
 // 2x2 matrices, row-major m[0..3]).
 inline void q60_pair_coef(const double* ra, const double* rb, QL out[6], int* flags) {
-  auto angle = [](const double* m, double* c, double* s) {
-    const double det = m[0] * m[3] - m[1] * m[2];
-    const double sg = det < 0.0 ? -1.0 : 1.0;
-    double cc = 0.5 * (m[0] + sg * m[3]), ss = 0.5 * (m[2] - sg * m[1]);
-    const double r = std::sqrt(cc * cc + ss * ss);
-    if (r > 0.0) {
-      cc /= r;
-      ss /= r;
-    } else {
-      cc = 1.0;
-      ss = 0.0;
-    }
-    *c = cc;
-    *s = ss;
-    return det < 0.0 ? 1 : 0;
-  };
   double ca, sa, cb, sb;
-  const int fa = angle(ra, &ca, &sa), fb = angle(rb, &cb, &sb);
+  const int fa = q60_orth_angle(ra, &ca, &sa), fb = q60_orth_angle(rb, &cb, &sb);
   *flags = fa | (fb << 1);
   const double pr = 0.5 * (ca * cb - sa * sb), pi = 0.5 * (sa * cb + ca * sb);
   const double qr = 0.5 * (ca * cb + sa * sb), qi = 0.5 * (sa * cb - ca * sb);

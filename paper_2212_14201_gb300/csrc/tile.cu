@@ -219,6 +219,40 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
   }
 }
 
+// Three real rotations on tile bits ta, tb, tc on the octets (index bit(ta) +
+// 2 bit(tb) + 4 bit(tc)) as four complex products per octet and component
+// (q60pair.cuh): 16 real products per octet and component where a pair and a
+// single rotation take 24.  With a phase table, as in quad_real.
+template <int THREADS>
+__device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tb, uint32_t tc,
+                                           const Q3 (&P)[4][3], int flags, const int2* tab) {
+  const uint32_t p0 = min(ta, min(tb, tc)), p2 = max(ta, max(tb, tc));
+  const uint32_t p1 = (ta | tb | tc) & ~(p0 | p2);
+  const uint32_t cnt = TS >> 3;
+  for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
+    uint32_t j = i + (i & ~(p0 - 1));  // insert zero bits at p0 < p1 < p2
+    j = j + (j & ~(p1 - 1));
+    j = j + (j & ~(p2 - 1));
+    uint32_t jj[8];
+    longlong2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      jj[k] = j | ((k & 1) ? ta : 0u) | ((k & 2) ? tb : 0u) | ((k & 4) ? tc : 0u);
+      v[k] = tile[jj[k]];
+      if (tab) {
+        const int2 ur = __ldg(tab + jj[k]), ui = __ldg(tab + TS + jj[k]), un = __ldg(tab + 2 * TS + jj[k]);
+        const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
+        int64_t vr, vi;
+        q60_gauss_mul(u, q60_split(v[k].x), q60_split(v[k].y), q60_split(v[k].x + v[k].y), &vr, &vi);
+        v[k] = make_longlong2(vr, vi);
+      }
+    }
+    q60_triple_octet(v, P, flags);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tile[jj[k]] = v[k];
+  }
+}
+
 // The same two ops for the FP32 engine (complex64 states): a real 4x4 on quads with
 // its 16 entries as floats in f[] of the op's two slots, optionally after a phase
 // table of float2 entries (one per amplitude of the tile).
@@ -318,6 +352,25 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
             q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
             tile[j] = make_longlong2(re, im);
           }
+          __syncthreads();
+          continue;
+        }
+        if (op.kind == TOP_REAL3) {
+          const int2* tab = op.code1 >= 0 ? reinterpret_cast<const int2*>(g.tables) + (size_t)op.code1 * 3 * TS
+                                          : nullptr;
+          // 12 Q3 coefficients: 8 in this slot's q[] (96 bytes), 4 in the next slot's
+          const Q3* pq0 = reinterpret_cast<const Q3*>(op.q);
+          const Q3* pq1 = reinterpret_cast<const Q3*>(g.ops[k + 1].q);
+          Q3 P[4][3];
+#pragma unroll
+          for (int e = 0; e < 12; ++e) P[e / 3][e % 3] = e < 8 ? pq0[e] : pq1[e - 8];
+          if (tab)
+            octet_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, 1u << (op.lcmask >> 8), P,
+                                (int)(op.lcmask & 7), tab);
+          else
+            octet_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, 1u << (op.lcmask >> 8), P,
+                                (int)(op.lcmask & 7), nullptr);
+          ++k;  // the continuation slot
           __syncthreads();
           continue;
         }

@@ -28,6 +28,11 @@ enum TileOpKind : int8_t {
                    // (16 floats in f[] of this slot and the next); code1 >= 0: phase
                    // table code1 applied first (the op before the pair)
   TOP_CONT = 12,   // continuation slot of the op before it (never run on its own)
+  TOP_REAL3 = 13,  // Q60 only: three real rotations on tile bits tb, code0 and lcmask >> 8 on
+                   // amplitude octets (index bit(tb) + 2 bit(code0) + 4 bit(lcmask >> 8)) as
+                   // four complex products (q60pair.cuh); the 12 Q3 coefficients (4 x re, im,
+                   // -im): 8 in q[] of this slot, 4 in the next; reflection flags in
+                   // lcmask & 7; code1 >= 0: phase table code1 applied first
 };
 
 struct TileOp {

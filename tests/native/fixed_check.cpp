@@ -23,6 +23,22 @@ int fc_pair_coef(const double* ra, const double* rb, long long* c) {
   for (int k = 0; k < 6; ++k) c[k] = (long long)q[k].h * (1ll << 30) + q[k].l;
   return flags;
 }
+// three real orthogonal 2x2 ops on one component of an octet x[8] (Q60 integers,
+// index bit(a) + 2 bit(b) + 4 bit(c)) through the four-complex-product form;
+// coefficients (re, im of U+, U-, V+, V-) as Q60 integers into c[8]
+int fc_triple_comp(const double* ra, const double* rb, const double* rc, long long* x, long long* c) {
+  qs::QL q[8];
+  int flags = 0;
+  qs::q60_triple_coef(ra, rb, rc, q, &flags);
+  for (int k = 0; k < 8; ++k) c[k] = (long long)q[k].h * (1ll << 30) + q[k].l;
+  qs::Q3 P[4][3];
+  qs::q60_triple_q3(q, P);
+  int64_t v[8];
+  for (int k = 0; k < 8; ++k) v[k] = (__builtin_popcount(k & flags) & 1) ? -x[k] : x[k];
+  qs::q60_triple_comp(v, P);
+  for (int k = 0; k < 8; ++k) x[k] = v[k];
+  return flags;
+}
 // two real orthogonal 2x2 ops (ra on quad bit a, rb on bit b; row-major) on one
 // component of a quad x[4] (Q60 integers, index bit(a) + 2 bit(b)), through the
 // two-complex-product form of the pair kernels

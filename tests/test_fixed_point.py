@@ -33,6 +33,8 @@ def fc():
     lib.fc_to_double_nb.argtypes = [ctypes.c_longlong]
     lib.fc_pair_coef.restype = ctypes.c_int
     lib.fc_pair_coef.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.fc_triple_comp.restype = ctypes.c_int
+    lib.fc_triple_comp.argtypes = [ctypes.c_void_p] * 5
     lib.fc_pair_comp.restype = None
     lib.fc_pair_comp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc_dot2.restype = ctypes.c_longlong
@@ -254,3 +256,55 @@ def test_pair_as_two_complex_products(fc, fa, fb):
         exact = [Ur + Vr, Ui + Vi, Ui - Vi, Vr - Ur]
         for qo in range(4):
             assert abs(Fraction(int(out[qo])) - exact[qo]) <= 12, (qo, float(Fraction(int(out[qo])) - exact[qo]))
+
+
+@pytest.mark.parametrize("flags", range(8))
+def test_triple_as_four_complex_products(fc, flags):
+    """R_c (x) R_b (x) R_a on an octet component through the four-complex-product
+    form (every combination of rotations and reflections): (1) the coefficients
+    reproduce the 8x8 Kronecker product of the double matrices within double
+    rounding; (2) the limb arithmetic equals the formula evaluated exactly on the
+    same Q60 integers within 20 units of 2^-60."""
+    g = np.random.Generator(np.random.PCG64(40 + flags))
+    sg = [(-1 if (flags >> i) & 1 else 1) for i in range(3)]
+    for _ in range(200):
+        rs = [_orth(g, (flags >> i) & 1) for i in range(3)]
+        v = g.normal(size=8)
+        v *= g.uniform(0, 1.25) / np.linalg.norm(v)
+        x = np.array([exact_q60(float(t)) for t in v], dtype=np.int64)
+        out = x.copy()
+        c = np.zeros(8, dtype=np.int64)
+        got_flags = fc.fc_triple_comp(rs[0].ctypes.data, rs[1].ctypes.data, rs[2].ctypes.data, out.ctypes.data,
+                                      c.ctypes.data)
+        assert got_flags == flags
+
+        def form(y, P, mul, add):
+            ur = [y[4 * k] - y[4 * k + 3] for k in (0, 1)]
+            ui = [y[4 * k + 1] + y[4 * k + 2] for k in (0, 1)]
+            vr = [y[4 * k] + y[4 * k + 3] for k in (0, 1)]
+            vi = [y[4 * k + 1] - y[4 * k + 2] for k in (0, 1)]
+            Y = [(ur[0] - ui[1], ui[0] + ur[1]), (ur[0] + ui[1], ui[0] - ur[1]),
+                 (vr[0] - vi[1], vi[0] + vr[1]), (vr[0] + vi[1], vi[0] - vr[1])]
+            R = [(mul(P[k][0], Y[k][0]) - mul(P[k][1], Y[k][1]), mul(P[k][1], Y[k][0]) + mul(P[k][0], Y[k][1]))
+                 for k in range(4)]
+            u0 = (R[0][0] + R[1][0], R[0][1] + R[1][1]); u1 = (R[0][1] - R[1][1], R[1][0] - R[0][0])
+            v0 = (R[2][0] + R[3][0], R[2][1] + R[3][1]); v1 = (R[2][1] - R[3][1], R[3][0] - R[2][0])
+            res = []
+            for u, w in ((u0, v0), (u1, v1)):
+                res += [u[0] + w[0], u[1] + w[1], u[1] - w[1], w[0] - u[0]]
+            return res
+
+        # (1) columns of the form against kron(rc, kron(rb, ra))
+        K = np.kron(rs[2].reshape(2, 2), np.kron(rs[1].reshape(2, 2), rs[0].reshape(2, 2)))
+        P = [(c[2 * k] / 2.0 ** 60, c[2 * k + 1] / 2.0 ** 60) for k in range(4)]
+        for qi in range(8):
+            y = [0.0] * 8
+            y[qi] = float(sg[0] ** (qi & 1) * sg[1] ** ((qi >> 1) & 1) * sg[2] ** ((qi >> 2) & 1))
+            col = form(y, P, lambda a, b: a * b, None)
+            assert np.max(np.abs(np.array(col) - K[:, qi])) < 6e-16, qi
+        # (2) limb arithmetic against the exact evaluation on the same integers
+        y = [Fraction(int(x[k])) * (sg[0] ** (k & 1) * sg[1] ** ((k >> 1) & 1) * sg[2] ** ((k >> 2) & 1)) for k in range(8)]
+        Pq = [(Fraction(int(c[2 * k]), 1 << 60), Fraction(int(c[2 * k + 1]), 1 << 60)) for k in range(4)]
+        exact = form(y, Pq, lambda a, b: a * b, None)
+        for k in range(8):
+            assert abs(Fraction(int(out[k])) - exact[k]) <= 20, (k, float(Fraction(int(out[k])) - exact[k]))

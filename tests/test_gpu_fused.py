@@ -183,8 +183,8 @@ def test_config1_full_state_against_oracle_n30(q, orc):
 
 @pytest.mark.parametrize("bits", [0, 4])
 def test_both_q60_tile_engines(q, orc, bits):
-    """The Q60 tile engines: per-op shared-memory sweeps (0) and register phases
-    (4, the default) against the oracle on random circuits with controls inside
+    """The Q60 tile engines: per-op shared-memory sweeps (0, the default) and
+    register phases (4) against the oracle on random circuits with controls inside
     and outside the tiles, the brickwork, the ansatz and tile widths 4..12."""
     q.qs_set_register_phases(bits)
     try:
@@ -216,7 +216,7 @@ def test_both_q60_tile_engines(q, orc, bits):
                 q.qs_plan_free(p)
             assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL, m
     finally:
-        q.qs_set_register_phases(4)
+        q.qs_set_register_phases(0)
 
 
 def run_chain_circuit(n, seed):
@@ -336,16 +336,18 @@ def test_phase_tables_survive_host_buffer_growth(q, orc):
 
 @pytest.mark.parametrize("n,kind", [(9, "brick"), (14, "brick"), (12, "rand"), (13, "hea")])
 def test_rotation_pairs_match_oracle(q, orc, n, kind):
-    """Q60 tile passes with pairs of real rotations run as 4x4 ops on quads (with
-    and without the preceding phase table fused into the pair), against the oracle
-    (1e-12) and with the switch off; the limb products per step are the same."""
+    """Q60 tile passes with groups of real rotations: triples on octets as four
+    complex products and pairs on quads as two (with and without the preceding
+    phase table fused into the group), against the oracle (1e-12) and with the
+    switch off; triples take no more limb products than pairs, and pairs fewer
+    than the rotations one at a time."""
     g = {"brick": lambda: w.layered_u3_cz(n, 12, 4), "rand": lambda: w.random_circuit(n, 400, 12),
          "hea": lambda: w.hea_ansatz(n, 4)[0]}[kind]()
     params = w.uniform_angles(400, 5)
     ref = orc.as_complex(orc.run(n, g, params))
     work = {}
     try:
-        for on in (1, 2, 0):
+        for on in (1, 3, 2, 0):
             q.qs_set_rotation_pairs(on)
             p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
             h = q.qs_alloc(n)
@@ -362,4 +364,4 @@ def test_rotation_pairs_match_oracle(q, orc, n, kind):
             work[on] = sum(r["int_ops"] for r in recs if r["kind"] == q._lib.K_TILE)
     finally:
         q.qs_set_rotation_pairs(True)
-    assert work[1] == work[2] == work[0]
+    assert work[1] <= work[3] == work[2] < work[0]
