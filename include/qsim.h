@@ -248,14 +248,6 @@ int qs_set_phase_tables(int on);
  * 0 neither.  Always QS_OK. */
 int qs_set_rotation_pairs(int on);
 
-/* Process-wide choice of the Q60 tile-pass kernel: 0 (default) runs one
- * shared-memory sweep per op; bits = 4 runs the register-phase engine (the ops
- * of a pass grouped into phases of four tile qubits; each thread applies a
- * phase's ops to the 16 amplitudes of its group, streaming them through
- * registers a quad at a time; tiles of 4..12 qubits).  Both give the amplitudes
- * within the Q60 rounding; the switch is for measurement.  Errors: INVALID_ARG
- * for other values. */
-int qs_set_register_phases(int bits);
 
 /* Greedy plan with an explicit tile width: tiles of tile_qubits (4..13) qubits,
  * the "block size" of the fusion (13: 128 KiB tiles, one 512-thread CTA per SM).
@@ -277,41 +269,26 @@ int qs_plan_pass_info(const qs_plan* p, size_t pass, int* kind, uint64_t* qmask,
  * gates in order (up to rounding).  Kind 0: the 2x2 matrix m (row-major,
  * interleaved complex) on `target` with controls ctrl_mask.  Kind 1: phase table
  * `table`, a diagonal over the pass's `bits` qubits: amplitude x gets T[j], j =
- * the bits of x at the pass's qubits in ascending order; the tables are written
- * one after another, 2^bits complex (interleaved) entries each (every table of a
- * pass has the pass's tile width).  *count / *ntables receive the totals (only
- * the first cap ops and table_cap tables are written). */
+ * the bits of x at the pass's qubits in ascending order, times
+ * (-1)^(x_{sign_q[i]} x_{sign_t[i]}) for i < nsigns (CZs between a qubit outside
+ * the pass's qubits and one of them, absorbed by the table; sign_q and sign_t
+ * are qubit numbers); the tables are written one after another, 2^bits complex
+ * (interleaved) entries each (every table of a pass has the pass's tile width).
+ * *count / *ntables receive the totals (only the first cap ops and table_cap
+ * tables are written). */
 typedef struct qs_pass_op {
   int32_t kind;
   int32_t target;
   uint64_t ctrl_mask;
   double m[8];
   int32_t table, bits;
+  int32_t nsigns;
+  uint8_t sign_q[16], sign_t[16];
 } qs_pass_op;
 int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
                      int q60, qs_pass_op* ops, size_t cap, size_t* count, double* tables, size_t table_cap,
                      size_t* ntables);
 
-/* Register program of a tile pass on the Q60 register-phase engine (the
- * kernel behind Q60 tile passes of 4..12 qubits; Section "Quantum circuit
- * fusion" with the gate work in on-chip memory, Section "GPU optimization"),
- * host only: the pass's op list (qs_plan_pass_ops, q60 = 1) regrouped into
- * register phases.  A phase holds four tile qubits in registers (reg_bits, a
- * mask over tile bits); its ops run there in order, after reordering only ops
- * that commute.  Each step names the op(s) of the list it runs: src0 (and
- * src1, the second rotation of a pair: kind 0), and table_src, a phase-table op
- * that runs just before the pair inside it (-1 if none).  kind: 0 pair of real
- * rotations, 1 real 2x2, 2 general 2x2, 3 antidiagonal, 4 diagonal, 5 |1>
- * phase, 6 diagonal on a qubit outside the phase's registers, 7 phase table.
- * Up to cap steps are written; *count receives the total.  Errors: INVALID_ARG
- * (NULL pointers, pass out of range or a per-gate pass, plan/program mismatch),
- * UNSUPPORTED (tile width outside 4..12). */
-typedef struct qs_reg_step {
-  int32_t phase, kind, src0, src1, table_src;
-  uint32_t reg_bits;
-} qs_reg_step;
-int qs_plan_pass_program(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
-                         qs_reg_step* steps, size_t cap, size_t* count);
 
 /* ---- learned fusion cost model (not in the paper, whose fusion has no cost
  * model): a 3-layer tanh perceptron h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),

@@ -45,14 +45,10 @@ class PlanStats(ctypes.Structure):
                 ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double), ("tile_qubits", ctypes.c_int64)]
 
 
-class RegStep(ctypes.Structure):
-    _fields_ = [("phase", ctypes.c_int32), ("kind", ctypes.c_int32), ("src0", ctypes.c_int32),
-                ("src1", ctypes.c_int32), ("table_src", ctypes.c_int32), ("reg_bits", ctypes.c_uint32)]
-
-
 class PassOp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("target", ctypes.c_int32), ("ctrl_mask", ctypes.c_uint64),
-                ("m", ctypes.c_double * 8), ("table", ctypes.c_int32), ("bits", ctypes.c_int32)]
+                ("m", ctypes.c_double * 8), ("table", ctypes.c_int32), ("bits", ctypes.c_int32),
+                ("nsigns", ctypes.c_int32), ("sign_q", ctypes.c_uint8 * 16), ("sign_t", ctypes.c_uint8 * 16)]
 
 
 class TimingRecord(ctypes.Structure):
@@ -91,7 +87,6 @@ SIGNATURES = {
     "qs_plan_create": (I32, [I32, P, SZ, I32, I32, PP]),
     "qs_plan_free": (I32, [P]),
     "qs_plan_create_tiled": (I32, [I32, P, SZ, I32, PP]),
-    "qs_set_register_phases": (I32, [I32]),
     "qs_plan_get_stats": (I32, [P, ctypes.POINTER(PlanStats)]),
     "qs_plan_pass_info": (I32, [P, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64), P, SZ,
                                 ctypes.POINTER(SZ)]),
@@ -106,7 +101,6 @@ SIGNATURES = {
     "qs_set_aggregate": (I32, [I32]),
     "qs_set_phase_tables": (I32, [I32]),
     "qs_set_rotation_pairs": (I32, [I32]),
-    "qs_plan_pass_program": (I32, [P, SZ, P, SZ, P, ctypes.POINTER(RegStep), SZ, ctypes.POINTER(SZ)]),
     "qs_plan_pass_ops": (I32, [P, SZ, P, SZ, P, I32, ctypes.POINTER(PassOp), SZ, ctypes.POINTER(SZ), P, SZ,
                                ctypes.POINTER(SZ)]),
     "qs_mlp_create": (I32, [I32, I32, P, U64, PP]),
@@ -402,10 +396,6 @@ def qs_set_rotation_pairs(on):
     _chk(lib().qs_set_rotation_pairs(int(on)))
 
 
-def qs_set_register_phases(bits: int):
-    _chk(lib().qs_set_register_phases(int(bits)))
-
-
 def qs_plan_create_tiled(n: int, gates, tile_qubits: int) -> int:
     g = as_gates(gates)
     h = ctypes.c_void_p()
@@ -450,27 +440,13 @@ def qs_plan_pass_ops(p: int, i: int, gates, params=None, q60: bool = True):
     out = []
     for o in ops[:cnt.value]:
         if o.kind == 1:
-            out.append({"kind": 1, "table": o.table, "bits": o.bits})
+            out.append({"kind": 1, "table": o.table, "bits": o.bits,
+                        "signs": [(o.sign_q[i], o.sign_t[i]) for i in range(o.nsigns)]})
         else:
             m = np.array(o.m[:]).view(np.complex128).reshape(2, 2)
             out.append({"kind": 0, "target": o.target, "ctrl_mask": o.ctrl_mask, "m": m})
     tables = tab.view(np.complex128).reshape(-1, 1 << bits)[:nt.value].copy()
     return out, tables
-
-
-def qs_plan_pass_program(p: int, i: int, gates, params=None) -> list[dict]:
-    """The register program of a tile pass (host only): one dict per step with
-    phase, kind, src0, src1, table_src (indices into qs_plan_pass_ops' list) and
-    reg_bits (the phase's register tile bits)."""
-    g = as_gates(gates)
-    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
-    cnt = ctypes.c_size_t()
-    args = (p, i, g.ctypes.data if len(g) else None, len(g), None if pr is None else pr.ctypes.data)
-    _chk(lib().qs_plan_pass_program(*args, None, 0, ctypes.byref(cnt)))
-    st = (RegStep * max(1, cnt.value))()
-    _chk(lib().qs_plan_pass_program(*args, st, cnt.value, ctypes.byref(cnt)))
-    return [{"phase": x.phase, "kind": x.kind, "src0": x.src0, "src1": x.src1, "table_src": x.table_src,
-             "reg_bits": x.reg_bits} for x in st[:cnt.value]]
 
 
 def qs_plan_passes(p: int) -> list:

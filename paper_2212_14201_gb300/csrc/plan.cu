@@ -22,7 +22,6 @@
 #include <vector>
 
 #include "q60pair.cuh"
-#include "regtile.h"
 #include "tile.h"
 
 using namespace qs;
@@ -304,11 +303,35 @@ static Zyz zyz(const Mat2& U) {
   return z;
 }
 
-// A diagonal over the tile: entry j for tile index j (bit b of j = tile bit b).
+// A diagonal over the tile: entry j for tile index j (bit b of j = tile bit b),
+// times a sign per tile: (-1)^(x_q j_t) for each (q, t) in signs (a CZ between
+// the qubit q outside the tile and the tile bit t; x_q is the tile's own bit q).
 struct PhaseTable {
   int m = 0;
   std::vector<C2> t;
+  std::vector<std::pair<int, int>> signs;  // (global qubit outside the tile, tile bit)
 };
+
+// A diagonal op that is a CZ between a tile bit and a qubit outside the tile:
+// diag(1, -1) on its target with exactly one control, one of the two qubits
+// inside the tile.  Returns the tile bit and the outside qubit.
+static bool cz_across(const Op1& o, const int* local, int* tile_bit, int* outside) {
+  if (__builtin_popcountll(o.cmask) != 1 || o.code1 != U_MINUS_ONE) return false;
+  if (!(o.cls == OP_PHASE1 || (o.cls == OP_DIAG && o.code0 == U_ONE))) return false;
+  const int c = __builtin_ctzll(o.cmask);
+  const int lt = local[o.target], lc = local[c];
+  if (lt >= 0 && lc < 0) {
+    *tile_bit = lt;
+    *outside = c;
+    return true;
+  }
+  if (lt < 0 && lc >= 0) {
+    *tile_bit = lc;
+    *outside = o.target;
+    return true;
+  }
+  return false;
+}
 
 // Rewrites ops (one pass, pass order) into real rotations, phase-table markers
 // (cls = kTableMark, target = table index) and the other ops unchanged.
@@ -341,6 +364,13 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
     Op1 op;
   };
   std::vector<Term> terms;
+  // pending CZs between a tile bit and a qubit outside the tile (sign terms of
+  // the next table; ops of their own if no table is built)
+  struct XTerm {
+    int tb, q;
+    Op1 op;
+  };
+  std::vector<XTerm> xterms;
   auto reset = [&](int b) {
     d0[b] = {1.0, 0.0};
     d1[b] = {1.0, 0.0};
@@ -375,21 +405,38 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       else terms[k++] = terms[i];
     }
     terms.resize(k);
+    k = 0;
+    for (size_t i = 0; i < xterms.size(); ++i) {
+      if (xterms[i].tb == b) out->push_back(xterms[i].op);
+      else xterms[k++] = xterms[i];
+    }
+    xterms.resize(k);
   };
   // candidate pulls for a flush before op i: per tile bit, the diagonal gates
   // before its next general op, and that op
   struct Pull {
     std::vector<size_t> diags;
+    std::vector<size_t> xs;  // CZs across the tile boundary on this tile bit before its next general op
     long gen = -1;
+    size_t stop = 0;         // the first op that acts non-diagonally on this tile bit (N if none)
   };
+  // in-tile controlled diagonal gates ahead of every non-diagonal op on their
+  // qubits: they commute back to the table and join it
+  std::vector<size_t> tpull;
   auto plan_pulls = [&](size_t i, Pull* P) {
     int count = 0;
     for (int b = 0; b < m; ++b) {
       P[b] = Pull();
+      P[b].stop = N;
       const int q = gq[b];
       for (size_t j = i; j < N; ++j) {
         if (consumed[j] || ops[j].cls == OP_IDENTITY) continue;
         const Op1& o = ops[j];
+        int xtb, xq;
+        if (cz_across(o, local, &xtb, &xq)) {  // diagonal: commutes up to here; a sign term if on b
+          if (xtb == b) P[b].xs.push_back(j);
+          continue;
+        }
         if (o.target != q) continue;  // untouched, or q only a control: commutes
         if (diag_cls(o.cls)) {
           if (o.cmask == 0) P[b].diags.push_back(j);
@@ -399,14 +446,51 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
           P[b].gen = (long)j;
           ++count;
         }
+        P[b].stop = j;
         break;
       }
+    }
+    tpull.clear();
+    for (size_t j = i; j < N; ++j) {
+      if (consumed[j] || ops[j].cls == OP_IDENTITY || !diag_cls(ops[j].cls) || ops[j].cmask == 0) continue;
+      const Op1& o = ops[j];
+      const uint64_t qs = o.cmask | (1ull << o.target);
+      bool ok = true;
+      for (uint64_t c = qs; c && ok; c &= c - 1) {
+        const int bq = local[__builtin_ctzll(c)];
+        ok = bq >= 0 && j < P[bq].stop;
+      }
+      if (ok) tpull.push_back(j);
     }
     return count;
   };
   // applies every pending diagonal (and the pulls): one table if two or more
   // things are pending, else each as its own op
   auto commit = [&](Pull* P) {
+    // CZs across the boundary ahead of each tile bit's next general op join the
+    // table's sign terms (as far as the table has room for them)
+    size_t room = tables->size() < (size_t)TILE_MAX_SIGNED_TABLES ? (size_t)TILE_MAX_SIGNS : 0;
+    room = room > xterms.size() ? room - xterms.size() : 0;
+    for (int b = 0; b < m && room; ++b)
+      for (size_t j : P[b].xs) {
+        if (!room) break;
+        int xtb, xq;
+        cz_across(ops[j], local, &xtb, &xq);
+        xterms.push_back(XTerm{xtb, xq, ops[j]});
+        consumed[j] = 1;
+        --room;
+      }
+    for (size_t j : tpull) {
+      const Op1& o = ops[j];
+      C2 e0, e1;
+      diag_of(o, &e0, &e1);
+      uint32_t lm = 0;
+      for (uint64_t c = o.cmask; c; c &= c - 1) lm |= 1u << local[__builtin_ctzll(c)];
+      const int tb = local[o.target];
+      terms.push_back(Term{lm | (1u << tb), lm, tb, e0, e1, o});
+      consumed[j] = 1;
+    }
+    tpull.clear();
     for (int b = 0; b < m; ++b) {
       for (size_t j : P[b].diags) {
         C2 e0, e1;
@@ -419,7 +503,7 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
         pulled[P[b].gen] = 1;
       }
     }
-    int cnt = (int)terms.size();
+    int cnt = (int)terms.size() + (int)xterms.size();
     for (int b = 0; b < m; ++b) cnt += has[b];
     if (cnt < 2) {
       for (int b = 0; b < m; ++b) {
@@ -443,6 +527,15 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       for (size_t j = 0; j < t.t.size(); ++j)
         if ((j & tm.lmask) == tm.lmask) t.t[j] = cmul2(t.t[j], ((j >> tm.tb) & 1) ? tm.e1 : tm.e0);
     terms.clear();
+    // sign terms: a table of a pass may carry TILE_MAX_SIGNS of them, and only the
+    // first TILE_MAX_SIGNED_TABLES tables of a pass carry any; the rest stay ops
+    for (const XTerm& x : xterms) {
+      if (tables->size() < (size_t)TILE_MAX_SIGNED_TABLES && t.signs.size() < (size_t)TILE_MAX_SIGNS)
+        t.signs.push_back({x.q, x.tb});
+      else
+        out->push_back(x.op);
+    }
+    xterms.clear();
     Op1 mark{};
     mark.cls = kTableMark;
     mark.target = (int)tables->size();
@@ -455,6 +548,11 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
     if (consumed[i] || ops[i].cls == OP_IDENTITY) continue;
     const Op1& o = ops[i];
     const int b = local[o.target];
+    int xtb = -1, xq = -1;
+    if (cz_across(o, local, &xtb, &xq)) {  // a CZ across the tile boundary: pending sign term
+      xterms.push_back(XTerm{xtb, xq, o});
+      continue;
+    }
     if (b < 0) {  // diagonal on a qubit outside the tile: commutes with every table
       out->push_back(o);
       continue;
@@ -492,6 +590,11 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
       if (has[bb] && P[bb].gen < 0) ++lone;
     double term_gain = 0.0;
     for (const Term& tm : terms) term_gain += est_op(tm.op);
+    for (const XTerm& x : xterms) term_gain += est_op(x.op);
+    for (int bb = 0; bb < m; ++bb)
+      for (size_t j : P[bb].xs) term_gain += est_op(ops[j]);
+    for (size_t j : tpull) term_gain += est_op(ops[j]);
+    if (kPullGain * pulls + kPhaseGain * lone + term_gain < kTableCost) tpull.clear();  // no table now
     if (kPullGain * pulls + kPhaseGain * lone + term_gain >= kTableCost) {
       commit(P.data());
       if (elig[i]) {  // pulled by the commit
@@ -518,6 +621,7 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
   }
   // what is left at the end of the pass
   std::vector<Pull> none(m);
+  tpull.clear();
   commit(none.data());
 }
 
@@ -807,7 +911,17 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
     if (rops[i].cls == kTableMark) {
       o.kind = 1;
       o.table = rops[i].target;
-      o.bits = pt[rops[i].target].m;
+      const PhaseTable& tb = pt[rops[i].target];
+      o.bits = tb.m;
+      o.nsigns = (int32_t)tb.signs.size();
+      for (size_t k = 0; k < tb.signs.size() && k < 16; ++k) {
+        o.sign_q[k] = (uint8_t)tb.signs[k].first;
+        // the tile bit back to its qubit
+        int q = 0;
+        for (int b = 0; b < p->n; ++b)
+          if (local[b] == tb.signs[k].second) q = b;
+        o.sign_t[k] = (uint8_t)q;
+      }
       continue;
     }
     o.kind = 0;
@@ -828,9 +942,6 @@ extern "C" int qs_plan_pass_ops(const qs_plan* p, size_t pass, const qs_gate* ga
   return QS_OK;
 }
 
-// Q60 tile engine: 0 = one shared-memory sweep per op (k_tile<EngQ60>, the
-// default), 4 = register phases (tile_q60.cu), kept for measurement.
-static int g_register_bits = 0;
 static bool g_aggregate = true;
 static bool g_rotation_pairs = true;
 static bool g_fuse_tables = true;
@@ -849,11 +960,6 @@ extern "C" int qs_set_aggregate(int on) {
   return QS_OK;
 }
 
-extern "C" int qs_set_register_phases(int bits) {
-  if (bits != 0 && bits != 4) return fail(QS_ERR_INVALID_ARG, "register bits %d: use 0 or 4", bits);
-  g_register_bits = bits;
-  return QS_OK;
-}
 
 // Copies a pass's phase tables to the device in the layout the tile kernel reads:
 // per table three arrays of 2^m limb pairs (the Gauss-form parts re, im, nim of
@@ -950,389 +1056,6 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
   return QS_OK;
 }
 
-// ---- register programs (Q60 register-phase engine, tile_q60.cu) --------------------
-// The pass's op list becomes register phases (regprog.h); inside a phase,
-// consecutive uncontrolled real rotations on two register bits become one PAIR
-// (a real 4x4), and a phase table directly before such a pair runs inside it.
-// Each table use gets a copy of the table in the order its phase's threads read
-// it.  steps[] records, per emitted op, which ops of the list it runs (for the
-// host tests of qs_plan_pass_program).
-struct RtProgram {
-  std::vector<RtPhase> phases;
-  std::vector<RtRun> runs;
-  std::vector<RtOp> ops;
-  std::vector<int> ncoef;                 // coefficient limb pairs of each op
-  std::vector<QL> coef;
-  std::vector<qs_reg_step> steps;         // parallel to ops
-  std::vector<std::pair<int, int>> uses;  // (table index, phase index) of RtOp.table
-  double int_ops = 0.0;                   // limb products per amplitude of the state
-};
-
-static int build_rt_program(int n, const std::vector<Op1>& rops, const int* local, int m, RtProgram* pr) {
-  std::vector<RpIn> in;
-  std::vector<int> src;
-  for (size_t i = 0; i < rops.size(); ++i) {
-    const Op1& o = rops[i];
-    if (o.cls == OP_IDENTITY) continue;
-    RpIn x{IK_DIAG, -1, 0, false};
-    if (o.cls == kTableMark) {
-      x.kind = IK_TABLE;
-    } else {
-      for (int b = 0; b < n; ++b)
-        if (((o.cmask >> b) & 1) && local[b] >= 0) x.lcm |= 1u << local[b];
-      x.tb = local[o.target];
-      if (o.cls == OP_ANTI || o.cls == OP_REAL || o.cls == OP_GENERAL) {
-        if (x.tb < 0)
-          return fail(QS_ERR_INVALID_ARG, "plan does not match the program (non-diagonal op on qubit %d outside its tile)",
-                      o.target);
-        x.kind = IK_MIX;
-        x.pairable = o.cls == OP_REAL && o.cmask == 0;
-      }
-    }
-    in.push_back(x);
-    src.push_back((int)i);
-  }
-  // one emitted op before its coefficients are known: a table, a pair (a, b) or a single a
-  struct Item {
-    int kind;       // RtKind
-    int a, b;       // indices into rops (b: the pair's second rotation, -1)
-    int table;      // table index (TABLE, or a table that runs first in a PAIR), -1
-    int tsrc;       // rops index of that table op, -1
-    int ra, rb;     // register bits: the single's target (ra), the pair's two rotations (ra, rb)
-  };
-  const std::vector<RpPhase> phases = rp_build_phases(in, m);
-  for (size_t p = 0; p < phases.size(); ++p) {
-    const RpPhase& rp = phases[p];
-    RtPhase ph;
-    memset(&ph, 0, sizeof ph);
-    int reg[32];
-    for (int b = 0; b < 32; ++b) reg[b] = -1;
-    int r = 0;
-    for (int b = 0; b < m; ++b)
-      if ((rp.P >> b) & 1) {
-        ph.rb[r] = (uint8_t)b;
-        reg[b] = r++;
-      }
-    if (r != RP_BITS) return fail(QS_ERR_INVALID_ARG, "internal: register phase with %d bits", r);
-    rp_group_bits(rp.P, m, ph.gl);
-    // the phase's items in order: pairs of consecutive rotations, tables fused into the pair after them
-    std::vector<Item> items;
-    auto src_op = [&](size_t k) -> const Op1& { return rops[src[rp.ops[k]]]; };
-    auto pairable = [&](size_t k) {
-      if (!g_rotation_pairs || k + 1 >= rp.ops.size()) return false;
-      const Op1& x = src_op(k);
-      const Op1& y = src_op(k + 1);
-      return x.cls == OP_REAL && y.cls == OP_REAL && x.cmask == 0 && y.cmask == 0 && x.target != y.target;
-    };
-    for (size_t k = 0; k < rp.ops.size(); ++k) {
-      const Op1& o = src_op(k);
-      const int sk = src[rp.ops[k]];
-      if (o.cls == kTableMark) {
-        if (g_fuse_tables && pairable(k + 1)) {
-          const Op1& x = src_op(k + 1);
-          const Op1& y = src_op(k + 2);
-          items.push_back({RK_PAIR, src[rp.ops[k + 1]], src[rp.ops[k + 2]], o.target, sk, reg[local[x.target]],
-                           reg[local[y.target]]});
-          k += 2;
-        } else {
-          items.push_back({RK_TABLE, sk, -1, o.target, -1, -1, -1});
-        }
-        continue;
-      }
-      if (pairable(k)) {
-        const Op1& y = src_op(k + 1);
-        items.push_back({RK_PAIR, sk, src[rp.ops[k + 1]], -1, -1, reg[local[o.target]], reg[local[y.target]]});
-        ++k;
-        continue;
-      }
-      const int tb = local[o.target];
-      const bool in_reg = tb >= 0 && reg[tb] >= 0;
-      int kind;
-      switch (o.cls) {
-        case OP_REAL: kind = RK_REAL; break;
-        case OP_GENERAL: kind = RK_GEN; break;
-        case OP_ANTI: kind = RK_ANTI; break;
-        case OP_DIAG: kind = in_reg ? RK_DIAG : RK_SCAL; break;
-        default: kind = in_reg ? RK_PH1 : RK_SCAL; break;
-      }
-      items.push_back({kind, sk, -1, -1, -1, in_reg ? reg[tb] : -1, -1});
-    }
-    // runs: consecutive items on one quad structure (two register bits)
-    ph.run_begin = (uint16_t)pr->runs.size();
-    size_t it = 0;
-    while (it < items.size()) {
-      int b0 = -1, b1 = -1;
-      size_t end = it;
-      for (; end < items.size(); ++end) {
-        const Item& x = items[end];
-        bool ok = true;
-        int n0 = b0, n1 = b1;
-        auto want = [&](int bit) {  // bit must be one of the run's two
-          if (bit == n0 || bit == n1) return;
-          if (n0 < 0) n0 = bit;
-          else if (n1 < 0) n1 = bit;
-          else ok = false;
-        };
-        if (x.kind == RK_PAIR) {
-          want(x.ra);
-          want(x.rb);
-        } else if (x.kind != RK_SCAL && x.kind != RK_TABLE) {
-          want(x.ra);
-        }
-        if (!ok) break;
-        b0 = n0;
-        b1 = n1;
-      }
-      for (int f = 0; f < RP_BITS && (b0 < 0 || b1 < 0); ++f) {
-        if (f == b0 || f == b1) continue;
-        if (b0 < 0) b0 = f;
-        else b1 = f;
-      }
-      RtRun run;
-      memset(&run, 0, sizeof run);
-      run.r0 = (uint8_t)b0;
-      run.r1 = (uint8_t)b1;
-      run.op_begin = (uint16_t)pr->ops.size();
-      for (size_t j = it; j < end; ++j) {
-        const Item& x = items[j];
-        RtOp t;
-        memset(&t, 0, sizeof t);
-        t.kind = (uint8_t)x.kind;
-        t.table = -1;
-        t.coef = (uint16_t)pr->coef.size();
-        int nc = 0;
-        if (x.table >= 0) {
-          pr->uses.push_back({x.table, (int)p});
-          t.table = (int16_t)(pr->uses.size() - 1);
-          pr->int_ops += 9.0;
-        }
-        if (x.kind == RK_PAIR) {
-          // quad index bit(run.r0) + 2 bit(run.r1)
-          const Op1& oa = rops[x.a];
-          const Op1& ob = rops[x.b];
-          const Op1& on0 = x.ra == b0 ? oa : ob;  // the rotation on run bit r0
-          const Op1& on1 = x.ra == b0 ? ob : oa;
-          double m0[4], m1[4];
-          for (int e = 0; e < 4; ++e) {
-            m0[e] = on0.m.m[e].re;
-            m1[e] = on1.m.m[e].re;
-          }
-          QL cf[6];
-          int flags = 0;
-          q60_pair_coef(m0, m1, cf, &flags);
-          for (int e = 0; e < 6; ++e) pr->coef.push_back(cf[e]);
-          t.role = (uint8_t)flags;
-          nc = 6;
-          pr->int_ops += 12.0;  // 8 real products per quad and component: 2 x 3 x 8 / 4 per amplitude
-        } else if (x.kind != RK_TABLE) {
-          const Op1& o = rops[x.a];
-          uint32_t lcm = 0;
-          uint64_t ext = 0;
-          for (int b = 0; b < n; ++b)
-            if ((o.cmask >> b) & 1) {
-              if (local[b] >= 0) lcm |= 1u << local[b];
-              else ext |= 1ull << b;
-            }
-          uint32_t cr = 0, gm = 0;
-          for (int b = 0; b < m; ++b)
-            if ((lcm >> b) & 1) {
-              if (reg[b] >= 0) cr |= 1u << reg[b];
-              else gm |= 1u << b;
-            }
-          t.ext = ext;
-          t.gmask = (uint16_t)gm;
-          t.cr = (uint8_t)cr;
-          t.code0 = (uint8_t)(o.cls == OP_PHASE1 ? U_ONE : o.code0);
-          t.code1 = (uint8_t)o.code1;
-          if (x.kind == RK_SCAL) {
-            const int tb = local[o.target];
-            t.sout = tb < 0 ? 1 : 0;
-            t.sbit = (uint8_t)(tb < 0 ? o.target : tb);
-          } else {
-            t.role = (uint8_t)(x.ra == b0 ? 0 : 1);
-          }
-          if (x.kind == RK_REAL) {
-            for (int e = 0; e < 4; ++e) pr->coef.push_back(q60_split(q60_from_double(o.m.m[e].re)));
-            nc = 4;
-          } else {
-            for (int e = 0; e < 4; ++e) {
-              const QC c = x.kind == RK_GEN ? qc_make_gauss(o.m.m[e].re, o.m.m[e].im) : qc_make(o.m.m[e].re, o.m.m[e].im);
-              pr->coef.push_back(c.re);
-              pr->coef.push_back(c.im);
-              pr->coef.push_back(c.nim);
-            }
-            nc = 12;
-          }
-          pr->int_ops += class_touch_fraction(o) * op_int_ops_per_amp(o);
-        }
-        pr->ops.push_back(t);
-        pr->ncoef.push_back(nc);
-        qs_reg_step st;
-        st.phase = (int32_t)p;
-        st.kind = x.kind;
-        st.src0 = x.a;
-        st.src1 = x.b;
-        st.table_src = x.tsrc;
-        st.reg_bits = rp.P;
-        pr->steps.push_back(st);
-      }
-      run.op_end = (uint16_t)pr->ops.size();
-      pr->runs.push_back(run);
-      it = end;
-    }
-    ph.run_end = (uint16_t)pr->runs.size();
-    pr->phases.push_back(ph);
-  }
-  return QS_OK;
-}
-
-// Tile index of register index k of group g in a phase.
-static uint32_t rt_index(const RtPhase& ph, int m, uint32_t g, uint32_t k) {
-  uint32_t j = 0;
-  for (int i = 0; i + RP_BITS < m; ++i) j |= ((g >> i) & 1u) << ph.gl[i];
-  for (int r = 0; r < RP_BITS; ++r) j |= ((k >> r) & 1u) << ph.rb[r];
-  return j;
-}
-
-// Device copy of the program's table uses (int4 entries, thread-major), through
-// the state's pinned staging buffer (see upload_tables for the ordering rules).
-static int upload_rt_tables(qs_state* s, const RtProgram& pr, const std::vector<PhaseTable>& pt, int m,
-                            const int4** dev) {
-  const size_t per = (size_t)1 << m;
-  const size_t bytes = pr.uses.size() * per * sizeof(int4);
-  if (!s->tables_ev) QS_CUDA(cudaEventCreateWithFlags(&s->tables_ev, cudaEventDisableTiming));
-  QS_CUDA(cudaEventSynchronize(s->tables_ev));
-  if (s->tables_pinned_bytes < bytes) {
-    if (s->tables_pinned) cudaFreeHost(s->tables_pinned);
-    s->tables_pinned = nullptr;
-    s->tables_pinned_bytes = 0;
-    QS_CUDA(cudaMallocHost(&s->tables_pinned, bytes));
-    s->tables_pinned_bytes = bytes;
-  }
-  if (s->tables_bytes < bytes) {
-    if (s->tables) {
-      QS_CUDA(cudaStreamSynchronize(s->stream));
-      cudaFree(s->tables);
-    }
-    s->tables = nullptr;
-    s->tables_bytes = 0;
-    QS_CUDA(cudaMalloc(&s->tables, bytes));
-    s->tables_bytes = bytes;
-  }
-  int4* host = (int4*)s->tables_pinned;
-  const uint32_t G = (uint32_t)(per >> RP_BITS);
-  for (size_t u = 0; u < pr.uses.size(); ++u) {
-    const PhaseTable& t = pt[pr.uses[u].first];
-    const RtPhase& ph = pr.phases[pr.uses[u].second];
-    int4* out = host + u * per;
-    for (uint32_t g = 0; g < G; ++g)
-      for (uint32_t k = 0; k < 16; ++k) {
-        const C2 z = t.t[rt_index(ph, m, g, k)];
-        const QL c = q60_split(q60_from_double(z.re)), d = q60_split(q60_from_double(z.im));
-        out[g * 16 + k] = make_int4(c.h, c.l, d.h, d.l);
-      }
-  }
-  QS_CUDA(cudaMemcpyAsync(s->tables, host, bytes, cudaMemcpyHostToDevice, s->stream));
-  QS_CUDA(cudaEventRecord(s->tables_ev, s->stream));
-  *dev = (const int4*)s->tables;
-  return QS_OK;
-}
-
-static int run_tile_pass_rt(qs_state* s, const PlanPass& ps, const std::vector<Op1>& rops,
-                            const std::vector<PhaseTable>& ptables, const int* local, int m) {
-  const int n = s->n;
-  RtProgram pr;
-  QS_TRY(build_rt_program(n, rops, local, m, &pr));
-  if (pr.ops.empty()) return QS_OK;
-  for (const auto& u : pr.uses)
-    if (u.first < 0 || (size_t)u.first >= ptables.size() || ptables[u.first].t.size() != ((size_t)1 << m))
-      return fail(QS_ERR_INVALID_ARG, "internal: malformed phase-table use");
-  RtArgs* g = new (std::nothrow) RtArgs;
-  if (!g) return fail(QS_ERR_OOM, "host allocation failed");
-  memset(g, 0, offsetof(RtArgs, phases));
-  const uint64_t Q = ps.qmask;
-  int L = 0;
-  while (L < n && ((Q >> L) & 1)) ++L;
-  g->n = n;
-  g->m = m;
-  g->ntiles = 1ull << (n - m);
-  for (int b = L; b < n; ++b)
-    if ((Q >> b) & 1) g->qhigh[g->nhigh++] = b;
-  for (int b = 0; b < n; ++b)
-    if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
-  int rc = QS_OK;
-  if (!pr.uses.empty()) rc = upload_rt_tables(s, pr, ptables, m, &g->tables);
-  const double N = (double)(1ull << n);
-  size_t p = 0;
-  while (rc == QS_OK && p < pr.phases.size()) {
-    g->nphases = g->nruns = g->nops = g->ncoef = 0;
-    double io = 0.0;
-    while (p < pr.phases.size()) {
-      const RtPhase& ph = pr.phases[p];
-      int nc = 0, no = 0;
-      for (int u = ph.run_begin; u < ph.run_end; ++u)
-        for (int o = pr.runs[u].op_begin; o < pr.runs[u].op_end; ++o) {
-          nc += pr.ncoef[o];
-          ++no;
-        }
-      const int nr = ph.run_end - ph.run_begin;
-      if (g->nphases + 1 > RT_MAX_PHASES || g->nruns + nr > RT_MAX_RUNS || g->nops + no > RT_MAX_OPS ||
-          g->ncoef + nc > RT_MAX_COEF)
-        break;
-      RtPhase& q = g->phases[g->nphases++];
-      q = ph;
-      q.run_begin = (uint16_t)g->nruns;
-      for (int u = ph.run_begin; u < ph.run_end; ++u) {
-        RtRun ru = pr.runs[u];
-        ru.op_begin = (uint16_t)g->nops;
-        for (int o = pr.runs[u].op_begin; o < pr.runs[u].op_end; ++o) {
-          RtOp t = pr.ops[o];
-          for (int c = 0; c < pr.ncoef[o]; ++c) g->coef[g->ncoef + c] = pr.coef[t.coef + c];
-          t.coef = (uint16_t)g->ncoef;
-          g->ncoef += pr.ncoef[o];
-          g->ops[g->nops++] = t;
-        }
-        ru.op_end = (uint16_t)g->nops;
-        g->runs[g->nruns++] = ru;
-      }
-      q.run_end = (uint16_t)g->nruns;
-      ++p;
-    }
-    if (g->nphases == 0) {
-      rc = fail(QS_ERR_UNSUPPORTED, "a register phase exceeds the launch limits (%d ops, %d coefficients)",
-                RT_MAX_OPS, RT_MAX_COEF);
-      break;
-    }
-    // the roofline counts of this launch: its share of the program's limb products
-    io = pr.int_ops * N * (double)g->nops / (double)pr.ops.size();
-    rc = launch_tile_q60(s, *g, io, (int)ps.gates.size(), Q);
-  }
-  delete g;
-  return rc;
-}
-
-extern "C" int qs_plan_pass_program(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng,
-                                    const double* params, qs_reg_step* steps, size_t cap, size_t* count) {
-  clear_error();
-  if (!p || !count || (cap && !steps)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
-  if (pass >= p->passes.size()) return fail(QS_ERR_INVALID_ARG, "pass %zu of %zu", pass, p->passes.size());
-  if (p->ng != ng || p->fingerprint != fingerprint(gates, ng)) return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
-  QS_TRY(validate_gates(gates, ng, p->n, params));
-  const PlanPass& ps = p->passes[pass];
-  if (ps.kind != PASS_TILE) return fail(QS_ERR_INVALID_ARG, "pass %zu is a per-gate pass", pass);
-  std::vector<Op1> rops;
-  std::vector<PhaseTable> pt;
-  int local[64];
-  int m = 0;
-  QS_TRY(build_pass_ops(p->n, ps, gates, params, true, &rops, &pt, local, &m));
-  if (m < RT_MIN_M || m > RT_MAX_M) return fail(QS_ERR_UNSUPPORTED, "tile width %d has no register program", m);
-  RtProgram pr;
-  QS_TRY(build_rt_program(p->n, rops, local, m, &pr));
-  *count = pr.steps.size();
-  for (size_t i = 0; i < pr.steps.size() && i < cap; ++i) steps[i] = pr.steps[i];
-  return QS_OK;
-}
-
 static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed) {
   const int n = s->n;
   TileArgs* g = new (std::nothrow) TileArgs;
@@ -1344,10 +1067,6 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   std::vector<PhaseTable> ptables;
   const bool f32 = s->prec == 64;  // complex64 state: FP32 engine
   int rc = build_pass_ops(n, ps, gates, params, (fixed && s->prec == 128) || f32, &rops, &ptables, local, &m);
-  if (rc == QS_OK && fixed && s->prec == 128 && g_register_bits == RP_BITS && m >= RT_MIN_M && m <= RT_MAX_M) {
-    delete g;
-    return run_tile_pass_rt(s, ps, rops, ptables, local, m);
-  }
   int L = 0;
   while (L < n && ((Q >> L) & 1)) ++L;
   g->n = n;
@@ -1515,6 +1234,20 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     if ((o.kind == TOP_REAL2 || o.kind == TOP_REAL3) && (k + 1 >= g->nops || g->ops[k + 1].kind != TOP_CONT ||
                                 (o.code1 >= 0 && (size_t)o.code1 >= ptables.size())))
       rc = fail(QS_ERR_INVALID_ARG, "internal: malformed rotation-pair op");
+  }
+  for (int t = 0; t < TILE_MAX_SIGNED_TABLES; ++t) g->signs[t].n = 0;
+  for (size_t t = 0; rc == QS_OK && t < ptables.size(); ++t) {
+    const auto& sg = ptables[t].signs;
+    if (sg.empty()) continue;
+    if (t >= (size_t)TILE_MAX_SIGNED_TABLES || sg.size() > (size_t)TILE_MAX_SIGNS) {
+      rc = fail(QS_ERR_INVALID_ARG, "internal: phase table %zu with %zu sign terms", t, sg.size());
+      break;
+    }
+    g->signs[t].n = (uint8_t)sg.size();
+    for (size_t k = 0; k < sg.size(); ++k) {
+      g->signs[t].q[k] = (uint8_t)sg[k].first;
+      g->signs[t].t[k] = (uint8_t)sg[k].second;
+    }
   }
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, f32);
   if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,

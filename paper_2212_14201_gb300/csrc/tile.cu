@@ -28,6 +28,17 @@ __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint
   return i | set;
 }
 
+// The sign mask of table t in the tile at `base`: amplitude j takes the sign
+// (-1)^popc(j & S).
+__device__ __forceinline__ uint32_t table_sign_mask(const TileArgs& g, int t, uint64_t base) {
+  if (t >= TILE_MAX_SIGNED_TABLES) return 0;
+  const TileSigns& sg = g.signs[t];
+  uint32_t S = 0;
+  for (int i = 0; i < sg.n; ++i)
+    if ((base >> sg.q[i]) & 1ull) S |= 1u << sg.t[i];
+  return S;
+}
+
 // ---- FP64 engine -------------------------------------------------------------------
 struct EngF64 {
   using T = double2;  // shared-memory element
@@ -193,7 +204,7 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
 // shared-memory round trip, index arithmetic and barrier.
 template <int THREADS>
 __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* m0,
-                                          int flags, const int2* tab) {
+                                          int flags, const int2* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
@@ -210,7 +221,7 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
         const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
         int64_t vr, vi;
         q60_gauss_mul(u, q60_split(v[c].x), q60_split(v[c].y), q60_split(v[c].x + v[c].y), &vr, &vi);
-        v[c] = make_longlong2(vr, vi);
+        v[c] = (__popc(jj[c] & S) & 1) ? make_longlong2(-vr, -vi) : make_longlong2(vr, vi);
       }
     }
     q60_pair_quad(v[0], v[1], v[2], v[3], m0, flags);
@@ -225,7 +236,7 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
 // single rotation take 24.  With a phase table, as in quad_real.
 template <int THREADS>
 __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tb, uint32_t tc,
-                                           const Q3 (&P)[4][3], int flags, const int2* tab) {
+                                           const Q3 (&P)[4][3], int flags, const int2* tab, uint32_t S) {
   const uint32_t p0 = min(ta, min(tb, tc)), p2 = max(ta, max(tb, tc));
   const uint32_t p1 = (ta | tb | tc) & ~(p0 | p2);
   const uint32_t cnt = TS >> 3;
@@ -244,7 +255,7 @@ __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_
         const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
         int64_t vr, vi;
         q60_gauss_mul(u, q60_split(v[k].x), q60_split(v[k].y), q60_split(v[k].x + v[k].y), &vr, &vi);
-        v[k] = make_longlong2(vr, vi);
+        v[k] = (__popc(jj[k] & S) & 1) ? make_longlong2(-vr, -vi) : make_longlong2(vr, vi);
       }
     }
     q60_triple_octet(v, P, flags);
@@ -258,7 +269,7 @@ __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_
 // table of float2 entries (one per amplitude of the tile).
 template <int THREADS>
 __device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const float* m0,
-                                              const float* m1, const float2* tab) {
+                                              const float* m1, const float2* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
@@ -271,7 +282,8 @@ __device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_
     for (int c = 0; c < 4; ++c) {
       v[c] = tile[jj[c]];
       if (tab) {
-        const float2 u = __ldg(tab + jj[c]);
+        float2 u = __ldg(tab + jj[c]);
+        if (__popc(jj[c] & S) & 1) u = make_float2(-u.x, -u.y);
         v[c] = make_float2(fmaf(u.x, v[c].x, -u.y * v[c].y), fmaf(u.x, v[c].y, u.y * v[c].x));
       }
     }
@@ -319,8 +331,11 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
       if constexpr (std::is_same<E, EngF32>::value) {
         if (op.kind == TOP_DTABLE) {
           const float2* tf = reinterpret_cast<const float2*>(g.tables) + (size_t)lcm * TS;
+          const uint32_t S = table_sign_mask(g, (int)lcm, base);
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
-            const float2 u = __ldg(tf + j), v = tile[j];
+            float2 u = __ldg(tf + j);
+            const float2 v = tile[j];
+            if (__popc(j & S) & 1) u = make_float2(-u.x, -u.y);
             tile[j] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
           }
           __syncthreads();
@@ -330,7 +345,8 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           const float2* tab =
               op.code1 >= 0 ? reinterpret_cast<const float2*>(g.tables) + (size_t)op.code1 * TS : nullptr;
           quad_real_f32<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const float*>(op.f),
-                                 reinterpret_cast<const float*>(g.ops[k + 1].f), tab);
+                                 reinterpret_cast<const float*>(g.ops[k + 1].f), tab,
+                                 op.code1 >= 0 ? table_sign_mask(g, op.code1, base) : 0u);
           ++k;  // the continuation slot
           __syncthreads();
           continue;
@@ -343,6 +359,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           const int2* tre = reinterpret_cast<const int2*>(g.tables) + (size_t)lcm * 3 * TS;
           const int2* tim = tre + TS;
           const int2* tnim = tim + TS;
+          const uint32_t S = table_sign_mask(g, (int)lcm, base);
 #pragma unroll 4
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             const int2 ur = __ldg(tre + j), ui = __ldg(tim + j), un = __ldg(tnim + j);
@@ -350,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
             const longlong2 a = tile[j];
             int64_t re, im;
             q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
-            tile[j] = make_longlong2(re, im);
+            tile[j] = (__popc(j & S) & 1) ? make_longlong2(-re, -im) : make_longlong2(re, im);
           }
           __syncthreads();
           continue;
@@ -366,10 +383,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           for (int e = 0; e < 12; ++e) P[e / 3][e % 3] = e < 8 ? pq0[e] : pq1[e - 8];
           if (tab)
             octet_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, 1u << (op.lcmask >> 8), P,
-                                (int)(op.lcmask & 7), tab);
+                                (int)(op.lcmask & 7), tab, table_sign_mask(g, op.code1, base));
           else
             octet_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, 1u << (op.lcmask >> 8), P,
-                                (int)(op.lcmask & 7), nullptr);
+                                (int)(op.lcmask & 7), nullptr, 0u);
           ++k;  // the continuation slot
           __syncthreads();
           continue;
@@ -379,10 +396,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
                                           : nullptr;
           if (tab)
             quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
-                               (int)op.lcmask, tab);
+                               (int)op.lcmask, tab, table_sign_mask(g, op.code1, base));
           else
             quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
-                               (int)op.lcmask, nullptr);
+                               (int)op.lcmask, nullptr, 0u);
           ++k;  // the continuation slot
           __syncthreads();
           continue;

@@ -12,6 +12,15 @@ constexpr int TILE_MAX_M = 13;      // widest tile: 2^13 x 16 B = 128 KiB of sha
 constexpr int TILE_DEFAULT_M = 12;  // greedy plans: 2^12 x 16 B = 64 KiB, 3 CTAs per SM
 constexpr int TILE_LOW = 3;     // qubits 0..2 are always in a tile: 128-byte contiguous runs
 constexpr int TILE_MAX_OPS = 256;
+constexpr int TILE_MAX_SIGNED_TABLES = 32;  // tables of a pass that may carry sign terms
+constexpr int TILE_MAX_SIGNS = 16;          // sign terms per table
+
+// Sign terms of a phase table: (-1)^(x_q j_t) for each (q, t), with x_q the tile's
+// bit q (a qubit outside the tile) and j_t tile bit t of the amplitude.
+struct TileSigns {
+  uint8_t n;
+  uint8_t q[TILE_MAX_SIGNS], t[TILE_MAX_SIGNS];
+};
 
 enum TileOpKind : int8_t {
   TOP_PHASE1 = OP_PHASE1,
@@ -57,6 +66,7 @@ struct TileArgs {
   int outpos[QS_MAX_QUBITS];  // their global positions (ascending)
   int nops;
   const QL* tables;  // DTABLE ops: per table the Gauss-form parts re, im, nim, 2^m limb pairs each
+  TileSigns signs[TILE_MAX_SIGNED_TABLES];  // sign terms of tables 0..31
   TileOp ops[TILE_MAX_OPS];
 };
 static_assert(sizeof(TileArgs) < 32000, "tile arguments must fit the kernel parameter space");

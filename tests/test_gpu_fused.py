@@ -181,42 +181,37 @@ def test_config1_full_state_against_oracle_n30(q, orc):
         assert mabs < TOL, name
 
 
-@pytest.mark.parametrize("bits", [0, 4])
-def test_both_q60_tile_engines(q, orc, bits):
-    """The Q60 tile engines: per-op shared-memory sweeps (0, the default) and
-    register phases (4) against the oracle on random circuits with controls inside
-    and outside the tiles, the brickwork, the ansatz and tile widths 4..12."""
-    q.qs_set_register_phases(bits)
-    try:
-        cases = [(13, w.random_circuit(13, 400, 3, two_qubit_prob=0.4), None),
-                 (17, w.layered_u3_cz(17, 12, 1), None), (16, w.random_circuit(16, 300, 8), None),
-                 (15, w.hea_ansatz(15, 4)[0], w.uniform_angles(120, 3)), (9, run_chain_circuit(9, 4), None)]
-        for n, g, th in cases:
-            p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
-            h = q.qs_alloc(n)
-            try:
-                q.qs_set_arith(h, q.ARITH_FIXED)
-                q.qs_apply(h, g, th, p)
-                psi = q.qs_get_state(h)
-            finally:
-                q.qs_free(h)
-                q.qs_plan_free(p)
-            assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g, th)))) < TOL, n
-        for m in range(4, 13):
-            n = 14
-            g = w.random_circuit(n, 300, 30 + m, two_qubit_prob=0.4)
-            p = q.qs_plan_create_tiled(n, g, m)
-            h = q.qs_alloc(n)
-            try:
-                q.qs_set_arith(h, q.ARITH_FIXED)
-                q.qs_apply(h, g, None, p)
-                psi = q.qs_get_state(h)
-            finally:
-                q.qs_free(h)
-                q.qs_plan_free(p)
-            assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL, m
-    finally:
-        q.qs_set_register_phases(0)
+def test_q60_tile_engine_all_widths(q, orc):
+    """The Q60 tile engine against the oracle on random circuits with controls
+    inside and outside the tiles, the brickwork, the ansatz, and every tile width
+    4..13."""
+    cases = [(13, w.random_circuit(13, 400, 3, two_qubit_prob=0.4), None),
+             (17, w.layered_u3_cz(17, 12, 1), None), (16, w.random_circuit(16, 300, 8), None),
+             (15, w.hea_ansatz(15, 4)[0], w.uniform_angles(120, 3)), (9, run_chain_circuit(9, 4), None)]
+    for n, g, th in cases:
+        p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+        h = q.qs_alloc(n)
+        try:
+            q.qs_set_arith(h, q.ARITH_FIXED)
+            q.qs_apply(h, g, th, p)
+            psi = q.qs_get_state(h)
+        finally:
+            q.qs_free(h)
+            q.qs_plan_free(p)
+        assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g, th)))) < TOL, n
+    for m in range(4, 14):
+        n = 15
+        g = w.random_circuit(n, 300, 30 + m, two_qubit_prob=0.4)
+        p = q.qs_plan_create_tiled(n, g, m)
+        h = q.qs_alloc(n)
+        try:
+            q.qs_set_arith(h, q.ARITH_FIXED)
+            q.qs_apply(h, g, None, p)
+            psi = q.qs_get_state(h)
+        finally:
+            q.qs_free(h)
+            q.qs_plan_free(p)
+        assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL, m
 
 
 def run_chain_circuit(n, seed):
