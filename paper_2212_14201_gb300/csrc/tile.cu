@@ -29,13 +29,14 @@ __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint
 }
 
 // The sign mask of table t in the tile at `base`: amplitude j takes the sign
-// (-1)^popc(j & S).
+// (-1)^popc(j & S), S = XOR over the terms (q, t) with x_q = 1 of bit t (two terms
+// on the same tile bit cancel when both of their outside qubits are set).
 __device__ __forceinline__ uint32_t table_sign_mask(const TileArgs& g, int t, uint64_t base) {
   if (t >= TILE_MAX_SIGNED_TABLES) return 0;
   const TileSigns& sg = g.signs[t];
   uint32_t S = 0;
   for (int i = 0; i < sg.n; ++i)
-    if ((base >> sg.q[i]) & 1ull) S |= 1u << sg.t[i];
+    if ((base >> sg.q[i]) & 1ull) S ^= 1u << sg.t[i];
   return S;
 }
 
