@@ -18,6 +18,17 @@
 
 namespace qs {
 
+// Shared-memory swizzle of the tile: element j (16 or 8 bytes) lives at
+// j ^ sw(j), where sw folds tile bits 3, 4, 5 into bits 0..2 with the vectors 7,
+// 3, 5 (a linear map, so the physical index of a sum of disjoint bit sets is the
+// XOR of theirs).  An op on tile bits B enumerates its pairs, quads or octets with
+// consecutive threads on the lowest tile bits outside B; without the swizzle a
+// quarter-warp hits one bank group as soon as B contains bits 0..2 (up to 8-way
+// conflicts).  With these vectors every op on at most three tile bits has its
+// lanes on at least four distinct bank groups (the best a 3-bit swizzle of bits
+// 3..5 allows; 18 of the 299 such bit sets keep a 2-way conflict).
+__device__ __forceinline__ uint32_t tsw(uint32_t j) { return j ^ ((0x3958f8u >> (3u * ((j >> 3) & 7u))) & 7u); }
+
 // Insert zero bits at the set positions of `fixed` (ascending), then OR `set`.
 __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint32_t set) {
   while (fixed) {
@@ -175,10 +186,11 @@ template <class E, int KIND, int THREADS>
 __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uint32_t fixed, uint32_t lcm, uint32_t tb,
                                           const TileOp& op) {
   using T = typename E::T;
+  const uint32_t tbp = tsw(tb);
 #pragma unroll 4
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     // without in-tile controls the insertion of one zero bit is a mask and an add
-    const uint32_t j0 = lcm ? tile_expand(i, fixed, lcm) : i + (i & ~(tb - 1)), j1 = j0 | tb;
+    const uint32_t j0 = tsw(lcm ? tile_expand(i, fixed, lcm) : i + (i & ~(tb - 1))), j1 = j0 ^ tbp;
     const T a0 = tile[j0], a1 = tile[j1];
     T b0, b1;
     if (KIND == TOP_DIAG) {
@@ -207,16 +219,19 @@ template <int THREADS>
 __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* m0,
                                           int flags, const int2* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
+  const uint32_t pa = tsw(ta), pb = tsw(tbb);
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     uint32_t j = i + (i & ~(lo - 1));  // insert a zero bit at lo, then at hi
     j = j + (j & ~(hi - 1));
     const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
+    const uint32_t pj = tsw(j);
+    const uint32_t pp[4] = {pj, pj ^ pa, pj ^ pb, pj ^ pa ^ pb};
     longlong2 v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      v[c] = tile[jj[c]];
+      v[c] = tile[pp[c]];
       if (tab) {
         const int2 ur = __ldg(tab + jj[c]), ui = __ldg(tab + TS + jj[c]), un = __ldg(tab + 2 * TS + jj[c]);
         const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
@@ -227,7 +242,7 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
     }
     q60_pair_quad(v[0], v[1], v[2], v[3], m0, flags);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) tile[jj[c]] = v[c];
+    for (int c = 0; c < 4; ++c) tile[pp[c]] = v[c];
   }
 }
 
@@ -240,17 +255,20 @@ __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_
                                            const Q3 (&P)[4][3], int flags, const int2* tab, uint32_t S) {
   const uint32_t p0 = min(ta, min(tb, tc)), p2 = max(ta, max(tb, tc));
   const uint32_t p1 = (ta | tb | tc) & ~(p0 | p2);
+  const uint32_t pa = tsw(ta), pb = tsw(tb), pc = tsw(tc);
   const uint32_t cnt = TS >> 3;
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     uint32_t j = i + (i & ~(p0 - 1));  // insert zero bits at p0 < p1 < p2
     j = j + (j & ~(p1 - 1));
     j = j + (j & ~(p2 - 1));
-    uint32_t jj[8];
+    uint32_t jj[8], pp[8];
+    const uint32_t pj = tsw(j);
     longlong2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       jj[k] = j | ((k & 1) ? ta : 0u) | ((k & 2) ? tb : 0u) | ((k & 4) ? tc : 0u);
-      v[k] = tile[jj[k]];
+      pp[k] = pj ^ ((k & 1) ? pa : 0u) ^ ((k & 2) ? pb : 0u) ^ ((k & 4) ? pc : 0u);
+      v[k] = tile[pp[k]];
       if (tab) {
         const int2 ur = __ldg(tab + jj[k]), ui = __ldg(tab + TS + jj[k]), un = __ldg(tab + 2 * TS + jj[k]);
         const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
@@ -261,7 +279,7 @@ __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_
     }
     q60_triple_octet(v, P, flags);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) tile[jj[k]] = v[k];
+    for (int k = 0; k < 8; ++k) tile[pp[k]] = v[k];
   }
 }
 
@@ -272,16 +290,19 @@ template <int THREADS>
 __device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const float* m0,
                                               const float* m1, const float2* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
+  const uint32_t pa = tsw(ta), pb = tsw(tbb);
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     uint32_t j = i + (i & ~(lo - 1));
     j = j + (j & ~(hi - 1));
     const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
+    const uint32_t pj = tsw(j);
+    const uint32_t pp[4] = {pj, pj ^ pa, pj ^ pb, pj ^ pa ^ pb};
     float2 v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      v[c] = tile[jj[c]];
+      v[c] = tile[pp[c]];
       if (tab) {
         float2 u = __ldg(tab + jj[c]);
         if (__popc(jj[c] & S) & 1) u = make_float2(-u.x, -u.y);
@@ -298,7 +319,7 @@ __device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_
         xr = fmaf(u, v[c].x, xr);
         xi = fmaf(u, v[c].y, xi);
       }
-      tile[jj[k]] = make_float2(xr, xi);
+      tile[pp[k]] = make_float2(xr, xi);
     }
   }
 }
@@ -323,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
     __syncthreads();  // offs ready / previous tile stored
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[tsw(j)] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
     __syncthreads();
     for (int k = 0; k < g.nops; ++k) {
       const TileOp& op = g.ops[k];
@@ -335,9 +356,9 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           const uint32_t S = table_sign_mask(g, (int)lcm, base);
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             float2 u = __ldg(tf + j);
-            const float2 v = tile[j];
+            const float2 v = tile[tsw(j)];
             if (__popc(j & S) & 1) u = make_float2(-u.x, -u.y);
-            tile[j] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
+            tile[tsw(j)] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
           }
           __syncthreads();
           continue;
@@ -365,10 +386,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             const int2 ur = __ldg(tre + j), ui = __ldg(tim + j), un = __ldg(tnim + j);
             const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
-            const longlong2 a = tile[j];
+            const longlong2 a = tile[tsw(j)];
             int64_t re, im;
             q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
-            tile[j] = (__popc(j & S) & 1) ? make_longlong2(-re, -im) : make_longlong2(re, im);
+            tile[tsw(j)] = (__popc(j & S) & 1) ? make_longlong2(-re, -im) : make_longlong2(re, im);
           }
           __syncthreads();
           continue;
@@ -413,7 +434,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
         const int e = one ? 3 : 0;
         const uint32_t cnt = TS >> __popc(lcm);
         for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
-          uint32_t j = tile_expand(i, lcm, lcm);
+          const uint32_t j = tsw(tile_expand(i, lcm, lcm));
           tile[j] = E::mul(tile[j], code, op, e);
         }
       } else {
@@ -422,7 +443,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
         const uint32_t cnt = TS >> __popc(fixed);
         if (op.kind == TOP_PHASE1) {
           for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
-            uint32_t j = tile_expand(i, fixed, lcm) | tb;
+            const uint32_t j = tsw(tile_expand(i, fixed, lcm) | tb);
             tile[j] = E::mul(tile[j], op.code1, op, 3);
           }
         } else if (op.kind == TOP_GENERAL) {
@@ -437,7 +458,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
       }
       __syncthreads();
     }
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[j]);
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[tsw(j)]);
   }
 }
 
