@@ -27,7 +27,11 @@ namespace qs {
 // conflicts).  With these vectors every op on at most three tile bits has its
 // lanes on at least four distinct bank groups (the best a 3-bit swizzle of bits
 // 3..5 allows; 18 of the 299 such bit sets keep a 2-way conflict).
-__device__ __forceinline__ uint32_t tsw(uint32_t j) { return j ^ ((0x3958f8u >> (3u * ((j >> 3) & 7u))) & 7u); }
+__device__ __forceinline__ uint32_t tsw_bits(uint32_t j) { return (0x3958f8u >> (3u * ((j >> 3) & 7u))) & 7u; }
+__device__ __forceinline__ uint32_t tsw(uint32_t j) { return j ^ tsw_bits(j); }
+// In a loop over i = threadIdx.x + k * THREADS (THREADS >= 64) whose element index
+// j inserts zero bits into i, bits 3..5 of j come from the low bits of i, i.e. from
+// threadIdx.x alone: the swizzle is one XOR with a per-thread constant.
 
 // Insert zero bits at the set positions of `fixed` (ascending), then OR `set`.
 __device__ __forceinline__ uint32_t tile_expand(uint32_t i, uint32_t fixed, uint32_t set) {
@@ -187,10 +191,11 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
                                           const TileOp& op) {
   using T = typename E::T;
   const uint32_t tbp = tsw(tb);
+  const uint32_t csw = tsw_bits(lcm ? tile_expand(threadIdx.x, fixed, lcm) : threadIdx.x + (threadIdx.x & ~(tb - 1)));
 #pragma unroll 4
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     // without in-tile controls the insertion of one zero bit is a mask and an add
-    const uint32_t j0 = tsw(lcm ? tile_expand(i, fixed, lcm) : i + (i & ~(tb - 1))), j1 = j0 ^ tbp;
+    const uint32_t j0 = (lcm ? tile_expand(i, fixed, lcm) : i + (i & ~(tb - 1))) ^ csw, j1 = j0 ^ tbp;
     const T a0 = tile[j0], a1 = tile[j1];
     T b0, b1;
     if (KIND == TOP_DIAG) {
@@ -220,13 +225,18 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
                                           int flags, const int2* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t pa = tsw(ta), pb = tsw(tbb);
+  uint32_t csw;
+  {
+    uint32_t j = threadIdx.x + (threadIdx.x & ~(lo - 1));
+    csw = tsw_bits(j + (j & ~(hi - 1)));
+  }
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     uint32_t j = i + (i & ~(lo - 1));  // insert a zero bit at lo, then at hi
     j = j + (j & ~(hi - 1));
     const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
-    const uint32_t pj = tsw(j);
+    const uint32_t pj = j ^ csw;
     const uint32_t pp[4] = {pj, pj ^ pa, pj ^ pb, pj ^ pa ^ pb};
     longlong2 v[4];
 #pragma unroll
@@ -256,13 +266,19 @@ __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_
   const uint32_t p0 = min(ta, min(tb, tc)), p2 = max(ta, max(tb, tc));
   const uint32_t p1 = (ta | tb | tc) & ~(p0 | p2);
   const uint32_t pa = tsw(ta), pb = tsw(tb), pc = tsw(tc);
+  uint32_t csw;
+  {
+    uint32_t j = threadIdx.x + (threadIdx.x & ~(p0 - 1));
+    j = j + (j & ~(p1 - 1));
+    csw = tsw_bits(j + (j & ~(p2 - 1)));
+  }
   const uint32_t cnt = TS >> 3;
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     uint32_t j = i + (i & ~(p0 - 1));  // insert zero bits at p0 < p1 < p2
     j = j + (j & ~(p1 - 1));
     j = j + (j & ~(p2 - 1));
     uint32_t jj[8], pp[8];
-    const uint32_t pj = tsw(j);
+    const uint32_t pj = j ^ csw;
     longlong2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -291,13 +307,18 @@ __device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_
                                               const float* m1, const float2* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t pa = tsw(ta), pb = tsw(tbb);
+  uint32_t csw;
+  {
+    uint32_t j = threadIdx.x + (threadIdx.x & ~(lo - 1));
+    csw = tsw_bits(j + (j & ~(hi - 1)));
+  }
   const uint32_t cnt = TS >> 2;
 #pragma unroll 2
   for (uint32_t i = threadIdx.x; i < cnt; i += THREADS) {
     uint32_t j = i + (i & ~(lo - 1));
     j = j + (j & ~(hi - 1));
     const uint32_t jj[4] = {j, j | ta, j | tbb, j | ta | tbb};
-    const uint32_t pj = tsw(j);
+    const uint32_t pj = j ^ csw;
     const uint32_t pp[4] = {pj, pj ^ pa, pj ^ pb, pj ^ pa ^ pb};
     float2 v[4];
 #pragma unroll
@@ -340,11 +361,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
     offs[h] = o;
   }
   const uint32_t lowmask = (1u << L) - 1;
+  const uint32_t tsq = tsw_bits(threadIdx.x);  // swizzle of the sequential loops over j
   for (uint64_t r = blockIdx.x; r < g.ntiles; r += gridDim.x) {
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
     __syncthreads();  // offs ready / previous tile stored
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[tsw(j)] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j ^ tsq] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
     __syncthreads();
     for (int k = 0; k < g.nops; ++k) {
       const TileOp& op = g.ops[k];
@@ -356,9 +378,9 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           const uint32_t S = table_sign_mask(g, (int)lcm, base);
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             float2 u = __ldg(tf + j);
-            const float2 v = tile[tsw(j)];
+            const float2 v = tile[j ^ tsq];
             if (__popc(j & S) & 1) u = make_float2(-u.x, -u.y);
-            tile[tsw(j)] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
+            tile[j ^ tsq] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
           }
           __syncthreads();
           continue;
@@ -386,10 +408,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             const int2 ur = __ldg(tre + j), ui = __ldg(tim + j), un = __ldg(tnim + j);
             const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
-            const longlong2 a = tile[tsw(j)];
+            const longlong2 a = tile[j ^ tsq];
             int64_t re, im;
             q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
-            tile[tsw(j)] = (__popc(j & S) & 1) ? make_longlong2(-re, -im) : make_longlong2(re, im);
+            tile[j ^ tsq] = (__popc(j & S) & 1) ? make_longlong2(-re, -im) : make_longlong2(re, im);
           }
           __syncthreads();
           continue;
@@ -458,7 +480,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
       }
       __syncthreads();
     }
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[tsw(j)]);
+    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[j ^ tsq]);
   }
 }
 
