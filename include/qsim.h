@@ -200,7 +200,8 @@ typedef struct qs_plan_stats {
   int64_t n_tile_passes; /* of which shared-memory tile passes */
   int64_t n_dense;       /* dense-block ops (in tiles or standalone) */
   double est_seconds;    /* the planner's cost estimate (0 if none) */
-  int64_t tile_qubits;   /* tile width the plan was built for */
+  int64_t tile_qubits;   /* tile width the plan was built for (learned plans: the widest pass) */
+  int64_t learned_fallback; /* learned plans: 1 if the model preferred the greedy plan (its passes kept) */
 } qs_plan_stats;
 
 /* Build a plan for n qubits from gates[0..ng-1] (host only; no device work).
@@ -315,15 +316,31 @@ int qs_mlp_loss_grad(qs_mlp* m, const double* x, const double* t, size_t B, doub
 int qs_mlp_train(qs_mlp* m, const double* x, const double* t, size_t B, int epochs, double lr, double* final_loss);
 
 /* Features of every pass of a plan (QS_PASS_FEATURES doubles per pass, in pass
- * order; `gates` must be the plan's program): pass kind, tile qubits, state
- * qubits, outside qubits, and counts of general, real, general-diagonal,
- * unit-factor, in-tile-controlled and outside-target ops. */
-#define QS_PASS_FEATURES 10
+ * order; `gates` must be the plan's program): pass kind (tile or plain gate),
+ * tile qubits, state qubits, qubits outside the tile, gates by structural class
+ * (general, real, general diagonal, unit factors), controlled gates, diagonal
+ * gates with the target outside the tile, distinct non-diagonal targets, gates
+ * that start a run on their target (the ops left after aggregation), controlled
+ * non-diagonal gates, and log2(1 + gates). */
+#define QS_PASS_FEATURES 14
 int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out);
 
-/* Learned plan: greedy plans for every tile width 8..12 are scored by the model
- * (sum over passes of exp(predicted log ms)) and the cheapest is kept; its
- * est_seconds is the model's prediction.  The model needs QS_PASS_FEATURES inputs. */
+/* Greedy plan with an explicit tile width (4..13) and pass construction:
+ * strategy 0 takes the targets of the remaining gates in program order (as
+ * qs_plan_create_tiled); strategy 1 starts each pass from the first runnable
+ * gate's target and the most frequent targets among the next runnable gates.
+ * (The cost model's training passes.)  Errors: INVALID_ARG. */
+int qs_plan_create_variant(int n, const qs_gate* gates, size_t ng, int tile_qubits, int strategy, qs_plan** out);
+
+/* Learned plan: the model chooses the groupings.  Pass by pass it scores
+ * candidate tile passes over the remaining gates (widths 11 and 12; both
+ * strategies of qs_plan_create_variant), each as one tile pass and as plain
+ * per-gate kernels (exp of the predicted log ms), and takes the candidate with
+ * the least predicted time per unit of work (the gates' touched fractions of the
+ * state), in the cheaper form.  The greedy plan is the fallback and the judge:
+ * unless the model predicts the learned plan faster by more than 5 %, the
+ * greedy passes are kept (stats.learned_fallback = 1).  est_seconds is the model's prediction.  The
+ * model needs QS_PASS_FEATURES inputs; its forward kernel runs on the GPU. */
 int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs_mlp* model, qs_plan** out);
 
 /* ---- reductions (prob_run_list / prob_run_dict, expectation tools) ------------- */

@@ -42,7 +42,8 @@ class QsimError(RuntimeError):
 
 class PlanStats(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_tile_passes", ctypes.c_int64),
-                ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double), ("tile_qubits", ctypes.c_int64)]
+                ("n_dense", ctypes.c_int64), ("est_seconds", ctypes.c_double), ("tile_qubits", ctypes.c_int64),
+                ("learned_fallback", ctypes.c_int64)]
 
 
 class PassOp(ctypes.Structure):
@@ -87,6 +88,7 @@ SIGNATURES = {
     "qs_plan_create": (I32, [I32, P, SZ, I32, I32, PP]),
     "qs_plan_free": (I32, [P]),
     "qs_plan_create_tiled": (I32, [I32, P, SZ, I32, PP]),
+    "qs_plan_create_variant": (I32, [I32, P, SZ, I32, I32, PP]),
     "qs_plan_get_stats": (I32, [P, ctypes.POINTER(PlanStats)]),
     "qs_plan_pass_info": (I32, [P, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64), P, SZ,
                                 ctypes.POINTER(SZ)]),
@@ -403,6 +405,14 @@ def qs_plan_create_tiled(n: int, gates, tile_qubits: int) -> int:
     return h.value
 
 
+def qs_plan_create_variant(n: int, gates, tile_qubits: int, strategy: int) -> int:
+    g = as_gates(gates)
+    h = ctypes.c_void_p()
+    _chk(lib().qs_plan_create_variant(n, g.ctypes.data if len(g) else None, len(g), tile_qubits, strategy,
+                                      ctypes.byref(h)))
+    return h.value
+
+
 def qs_plan_free(p: int):
     _chk(lib().qs_plan_free(p))
 
@@ -522,7 +532,7 @@ def qs_launch_count() -> int:
     return int(lib().qs_launch_count())
 
 
-PASS_FEATURES = 10
+PASS_FEATURES = 14
 
 
 def qs_mlp_create(n_in: int, n_hidden: int, weights=None, seed: int = 0) -> int:

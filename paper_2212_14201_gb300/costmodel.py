@@ -1,11 +1,15 @@
 """Learned fusion cost model.
 
-The library's greedy planner fixes the tile width (12 qubits).  The learned
-planner scores greedy plans of every tile width 8..12 with a small perceptron
-(qs_mlp_*) that predicts each pass's log(milliseconds) from its features
-(qs_plan_features), and keeps the cheapest (qs_plan_create_learned).  The
-network is trained on the GPU by the library's own kernels (qs_mlp_train) from
-per-pass timings the library's kernel log records (qs_timing_fetch).
+The library's greedy planner takes each pass's qubits in program order at a fixed
+tile width (12 qubits) and decides tile pass against per-gate kernels by a fixed
+rule.  The learned planner (qs_plan_create_learned) lets a small perceptron
+(qs_mlp_*) make those choices pass by pass: it predicts the log(milliseconds) of
+candidate passes (widths 11 and 12, two ways of choosing the qubits, as one tile
+pass or gate by gate) from their features (qs_plan_features) and takes the
+candidate with the least predicted time per unit of work; the greedy plan is the
+fallback and the judge.  The network is trained on the GPU by the library's own
+kernels (qs_mlp_train) from per-pass timings the library's kernel log records
+(qs_timing_fetch), on the kinds of passes the planner chooses among.
 
 Usage on a GPU machine:  python -m paper_2212_14201_gb300.costmodel --out FILE
 """
@@ -56,18 +60,26 @@ def pass_timings(h: int, n: int, gates, plan: int, params=None, repeats: int = 2
     return feats[hit], acc[hit] / repeats
 
 
-def collect(circuits, tile_widths=range(8, 13), repeats: int = 2, stream=None):
-    """Timing data set over `circuits` = [(n, gates, params or None), ...]."""
+def collect(circuits, tile_widths=(10, 11, 12), strategies=(0, 1), plain: bool = True, repeats: int = 2,
+            stream=None):
+    """Timing data set over `circuits` = [(n, gates, params or None), ...]: the passes
+    of plans of every width and strategy (qs_plan_create_variant), and with
+    plain=True every gate of the plain per-gate plan."""
     X, y = [], []
     states = {}
     try:
         for n, gates, params in circuits:
             if n not in states:
                 states[n] = _lib.qs_alloc(n, stream)
+            plans = []
             for m in tile_widths:
                 if m > n:
                     continue
-                p = _lib.qs_plan_create_tiled(n, gates, m)
+                for st in strategies:
+                    plans.append(_lib.qs_plan_create_variant(n, gates, m, st))
+            if plain:
+                plans.append(_lib.qs_plan_create(n, gates, _lib.PLAN_PLAIN, 1))
+            for p in plans:
                 try:
                     f, ms = pass_timings(states[n], n, gates, p, params, repeats)
                 finally:
@@ -107,7 +119,7 @@ def load(path: str = WEIGHTS_FILE) -> int | None:
 
 def default_training_circuits(ns=(24, 26, 28, 30), per_n: int = 2, seed0: int = 100):
     """Random circuits of the n=32 workload's mix (40 % two-qubit gates) at
-    smaller n, seeds 100.., plus layered and ansatz circuits."""
+    smaller n, seeds 100.., plus a layered U3 + CZ circuit per n."""
     import workloads as w
     out = []
     s = seed0

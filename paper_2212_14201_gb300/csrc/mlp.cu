@@ -222,6 +222,10 @@ extern "C" int qs_mlp_create(int n_in, int n_hidden, const double* weights, uint
   return QS_OK;
 }
 
+namespace qs {
+int mlp_inputs(const qs_mlp* m) { return m ? m->d.F : 0; }
+}  // namespace qs
+
 extern "C" int qs_mlp_free(qs_mlp* m) {
   if (!m) return QS_OK;
   if (m->stream) cudaStreamSynchronize(m->stream);

@@ -18,6 +18,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -37,6 +39,7 @@ struct PlanPass {
 struct qs_plan {
   int n = 0;
   int mode = 0;
+  bool learned_fallback = false;  // a learned plan that kept the greedy passes
   int kmax = 1;
   int m = TILE_DEFAULT_M;
   size_t ng = 0;
@@ -628,7 +631,54 @@ static void extract_phases(const std::vector<Op1>& ops, const int* local, int n,
 uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
                      const std::vector<uint32_t>& remaining, int m, uint64_t low, int max_ops,
                      std::vector<uint32_t>& pass, std::vector<uint32_t>& rest) {
+  return greedy_pass_from(gates, tgt, cms, remaining, m, low, max_ops, pass, rest);
+}
+
+// Qubits to start a pass with, from the remaining gates' targets: the target of
+// the first gate that can run, then the most frequent targets among the next
+// `window` gates that commute back to the start of the pass (earlier first on
+// ties), up to m qubits with `low`.  A pass that starts from them keeps the
+// qubits most gates act on, where the greedy scan takes targets in program order.
+uint64_t seed_qubits(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                     const std::vector<uint32_t>& remaining, int m, uint64_t low, int window) {
+  uint64_t blockedN = 0, blockedD = 0;
+  int count[64] = {0}, first_seen[64];
+  for (int b = 0; b < 64; ++b) first_seen[b] = 1 << 30;
   uint64_t Q = low;
+  int seen = 0, order = 0;
+  for (uint32_t k : remaining) {
+    const bool diag = structurally_diagonal(gates[k].type);
+    const uint64_t Nm = diag ? 0 : (1ull << tgt[k]);
+    const uint64_t Dm = (diag ? (1ull << tgt[k]) : 0) | cms[k];
+    const bool blocked = (Nm & (blockedN | blockedD)) || (Dm & blockedN);
+    if (blocked) {
+      blockedN |= Nm;
+      blockedD |= Dm;
+      continue;
+    }
+    if (!Nm) continue;
+    if (Q == low && !(Q & Nm)) Q |= Nm;  // the first gate that can run
+    ++count[tgt[k]];
+    if (first_seen[tgt[k]] > order) first_seen[tgt[k]] = order;
+    ++order;
+    if (++seen >= window) break;
+  }
+  while (__builtin_popcountll(Q) < m) {
+    int best = -1;
+    for (int b = 0; b < 64; ++b)
+      if (!((Q >> b) & 1) && count[b] > 0 &&
+          (best < 0 || count[b] > count[best] || (count[b] == count[best] && first_seen[b] < first_seen[best])))
+        best = b;
+    if (best < 0) break;
+    Q |= 1ull << best;
+  }
+  return Q;
+}
+
+uint64_t greedy_pass_from(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                          const std::vector<uint32_t>& remaining, int m, uint64_t init, int max_ops,
+                          std::vector<uint32_t>& pass, std::vector<uint32_t>& rest) {
+  uint64_t Q = init;
   uint64_t blockedN = 0, blockedD = 0;
   pass.clear();
   rest.clear();
@@ -656,7 +706,32 @@ uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const st
 
 }  // namespace qs
 
-static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax, int mtile, qs_plan** out) {
+// One tile pass over `remaining` at width m: greedy (strategy 0: targets taken in
+// program order) or seeded (1: from seed_qubits), padded to the full width.  A
+// pass of diagonal gates needs few tile qubits, but a narrow tile means many small
+// tiles (a CTA pass and a barrier per op for a few amplitudes); qubits the pass's
+// gates touch come first (their diagonal ops and controls become in-tile), then
+// the lowest.
+static PlanPass make_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                          const std::vector<uint32_t>& remaining, int n, int m, int strategy,
+                          std::vector<uint32_t>& rest) {
+  const int L = std::min(n, TILE_LOW);
+  const uint64_t low = (1ull << L) - 1;
+  PlanPass ps;
+  ps.kind = PASS_TILE;
+  const uint64_t init = strategy == 1 ? seed_qubits(gates, tgt, cms, remaining, m, low, 4 * m) : low;
+  // leave op slots for the phase tables a pass may gain
+  ps.qmask = greedy_pass_from(gates, tgt, cms, remaining, m, init, TILE_MAX_OPS - 32, ps.gates, rest);
+  uint64_t touched = 0;
+  for (uint32_t k : ps.gates) touched |= cms[k] | (1ull << tgt[k]);
+  for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < m; ++b)
+    if (((touched >> b) & 1) && !((ps.qmask >> b) & 1)) ps.qmask |= 1ull << b;
+  for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < m; ++b) ps.qmask |= 1ull << b;
+  return ps;
+}
+
+static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax, int mtile, qs_plan** out,
+                      int strategy = 0) {
   if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_ERR_INVALID_ARG, "n out of range");
@@ -699,26 +774,10 @@ static int plan_build(int n, const qs_gate* gates, size_t ng, int mode, int kmax
     return QS_OK;
   }
 
-  const int L = std::min(n, TILE_LOW);
-  const uint64_t low = (1ull << L) - 1;
   std::vector<uint32_t> remaining(ng), rest;
   for (size_t k = 0; k < ng; ++k) remaining[k] = (uint32_t)k;
   while (!remaining.empty()) {
-    PlanPass ps;
-    ps.kind = PASS_TILE;
-    // leave op slots for the phase tables a pass may gain
-    ps.qmask = greedy_pass(gates, tgt, cms, remaining, p->m, low, TILE_MAX_OPS - 32, ps.gates, rest);
-    // Pad the tile to the full width: a pass of diagonal gates needs few tile
-    // qubits, but a narrow tile means many small tiles (a CTA pass and a barrier
-    // per op for a few amplitudes).  Qubits the pass's gates touch come first
-    // (their diagonal ops and controls become in-tile), then the lowest.
-    {
-      uint64_t touched = 0;
-      for (uint32_t k : ps.gates) touched |= cms[k] | (1ull << tgt[k]);
-      for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < p->m; ++b)
-        if (((touched >> b) & 1) && !((ps.qmask >> b) & 1)) ps.qmask |= 1ull << b;
-      for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < p->m; ++b) ps.qmask |= 1ull << b;
-    }
+    PlanPass ps = make_pass(gates, tgt, cms, remaining, n, p->m, strategy, rest);
     // Cost: a tile pass sweeps the whole state once and is bound by its limb
     // products; a per-gate kernel touches only the amplitudes it changes and is
     // bound by HBM.  A lone gate, or a pass of cheap data-movement gates (CZ,
@@ -773,22 +832,41 @@ static int structural_class(int type) {
   }
 }
 
-static void pass_features(const qs_plan* p, const PlanPass& ps, const qs_gate* gates, double* f) {
-  const int n = p->n;
+// Features of one pass for the cost model (QS_PASS_FEATURES values):
+//   0 tile pass (1) or one plain gate (0); 1 tile qubits / 13; 2 state qubits / 34;
+//   3 qubits outside the tile / 34; 4..7 gates by structural class (general, real,
+//   general diagonal, unit factors) / 64; 8 controlled gates / 64; 9 diagonal gates
+//   whose target lies outside the tile / 64; 10 distinct non-diagonal targets / 13;
+//   11 gates that start a run (not right after a gate on the same target with the
+//   same controls: the ops left after aggregation) / 64; 12 controlled
+//   non-diagonal gates / 64; 13 log2(1 + gates) / 8.
+static void pass_features(int n, const PlanPass& ps, const qs_gate* gates, double* f) {
   const int m = ps.kind == PASS_TILE ? __builtin_popcountll(ps.qmask) : 1;
   for (int i = 0; i < QS_PASS_FEATURES; ++i) f[i] = 0.0;
   f[0] = ps.kind == PASS_TILE ? 1.0 : 0.0;
-  f[1] = m / 12.0;
-  f[2] = n / 32.0;
-  f[3] = (n - m) / 32.0;
+  f[1] = m / 13.0;
+  f[2] = n / 34.0;
+  f[3] = (n - m) / 34.0;
+  uint64_t targets = 0;
+  int prev_t = -1;
+  uint64_t prev_c = 0;
   for (uint32_t k : ps.gates) {
     int t;
     uint64_t cm;
     gate_qubits(gates[k], n, &t, &cm);
-    f[4 + structural_class(gates[k].type)] += 1.0 / 64.0;
+    const int cls = structural_class(gates[k].type);
+    const bool diag = structurally_diagonal(gates[k].type);
+    f[4 + cls] += 1.0 / 64.0;
     if (cm) f[8] += 1.0 / 64.0;
     if (ps.kind == PASS_TILE && !((ps.qmask >> t) & 1)) f[9] += 1.0 / 64.0;
+    if (!diag) targets |= 1ull << t;
+    if (!(t == prev_t && cm == prev_c)) f[11] += 1.0 / 64.0;
+    if (!diag && cm) f[12] += 1.0 / 64.0;
+    prev_t = t;
+    prev_c = cm;
   }
+  f[10] = __builtin_popcountll(targets) / 13.0;
+  f[13] = std::log2(1.0 + (double)ps.gates.size()) / 8.0;
 }
 
 extern "C" int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out) {
@@ -796,7 +874,159 @@ extern "C" int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t n
   if (!p || !out || (ng && !gates)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
   if (p->ng != ng || p->fingerprint != fingerprint(gates, ng))
     return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
-  for (size_t i = 0; i < p->passes.size(); ++i) pass_features(p, p->passes[i], gates, out + i * QS_PASS_FEATURES);
+  for (size_t i = 0; i < p->passes.size(); ++i) pass_features(p->n, p->passes[i], gates, out + i * QS_PASS_FEATURES);
+  return QS_OK;
+}
+
+extern "C" int qs_plan_create_variant(int n, const qs_gate* gates, size_t ng, int tile_qubits, int strategy,
+                                      qs_plan** out) {
+  clear_error();
+  if (tile_qubits < TILE_LOW + 1 || tile_qubits > TILE_MAX_M)
+    return fail(QS_ERR_INVALID_ARG, "tile_qubits=%d outside %d..%d", tile_qubits, TILE_LOW + 1, TILE_MAX_M);
+  if (strategy != 0 && strategy != 1) return fail(QS_ERR_INVALID_ARG, "strategy %d: use 0 or 1", strategy);
+  return plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, tile_qubits, out, strategy);
+}
+
+// Learned plan (the cost model chooses the groupings).  Pass by pass, candidate
+// tile passes over the remaining gates are built at widths 11 and 12 with both
+// strategies (greedy and seeded); the model predicts each candidate's time
+// as one tile pass and as plain per-gate kernels, and the candidate with the
+// least predicted time per unit of work (its gates' touched fractions of the
+// state, a sweep each) is taken, as a tile pass or gate by gate, whichever the
+// model predicts cheaper.  The greedy plan at width 12 is the fallback and the
+// judge: the learned plan is kept only if the model predicts it faster overall
+// by more than 5 %.  (Width 13 is left out: one 512-thread CTA per SM runs the
+// tile ops slower than the widths' fewer passes save, and the model did not
+// learn that from its training passes.)
+using PassScorer = std::function<int(const double* x, size_t B, double* y)>;
+constexpr double kLearnedMargin = 0.05;
+
+static int plan_build_learned(int n, const qs_gate* gates, size_t ng, const PassScorer& score, qs_plan** out) {
+  *out = nullptr;
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_ERR_INVALID_ARG, "n out of range");
+  if (ng && !gates) return fail(QS_ERR_INVALID_ARG, "gates is NULL");
+  std::vector<int> tgt(ng);
+  std::vector<uint64_t> cms(ng);
+  for (size_t k = 0; k < ng; ++k) {
+    int t;
+    uint64_t cm;
+    int rc = gate_qubits(gates[k], n, &t, &cm);
+    if (rc) return fail(rc, "gate %zu: %s", k, qs_last_error());
+    tgt[k] = t;
+    cms[k] = cm;
+  }
+  qs_plan* greedy = nullptr;
+  QS_TRY(plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, TILE_DEFAULT_M, &greedy));
+  std::unique_ptr<qs_plan> gp(greedy);
+  auto predict_plan = [&](const qs_plan* pl, double* total) -> int {
+    std::vector<double> x(pl->passes.size() * QS_PASS_FEATURES), y(pl->passes.size());
+    for (size_t i = 0; i < pl->passes.size(); ++i) pass_features(n, pl->passes[i], gates, x.data() + i * QS_PASS_FEATURES);
+    if (!y.empty()) QS_TRY(score(x.data(), y.size(), y.data()));
+    *total = 0.0;
+    for (double v : y) *total += std::exp(v) * 1e-3;
+    return QS_OK;
+  };
+  std::unique_ptr<qs_plan> lp(new (std::nothrow) qs_plan);
+  if (!lp) return fail(QS_ERR_OOM, "host allocation failed");
+  lp->n = n;
+  lp->mode = QS_PLAN_LEARNED;
+  lp->kmax = 5;
+  lp->ng = ng;
+  lp->fingerprint = fingerprint(gates, ng);
+  lp->m = 0;
+  std::vector<uint32_t> remaining(ng);
+  for (size_t k = 0; k < ng; ++k) remaining[k] = (uint32_t)k;
+  struct Cand {
+    PlanPass ps;
+    std::vector<uint32_t> rest;
+  };
+  std::vector<Cand> cands;
+  std::vector<double> x, y;
+  double learned_total = 0.0;
+  while (!remaining.empty()) {
+    cands.clear();
+    for (int m = 11; m <= TILE_DEFAULT_M; ++m) {
+      const int mm = std::min(n, m);
+      for (int strategy = 0; strategy < 2; ++strategy) {
+        Cand c;
+        c.ps = make_pass(gates, tgt, cms, remaining, n, mm, strategy, c.rest);
+        bool dup = false;
+        for (const Cand& o : cands) dup = dup || (o.ps.qmask == c.ps.qmask && o.ps.gates == c.ps.gates);
+        if (!dup) cands.push_back(std::move(c));
+      }
+      if (mm < m) break;
+    }
+    // rows: each candidate as a tile pass, then each of its gates as a plain pass
+    x.clear();
+    std::vector<size_t> first(cands.size());
+    for (size_t c = 0; c < cands.size(); ++c) {
+      first[c] = x.size() / QS_PASS_FEATURES;
+      x.resize(x.size() + QS_PASS_FEATURES * (1 + cands[c].ps.gates.size()));
+      double* row = x.data() + first[c] * QS_PASS_FEATURES;
+      pass_features(n, cands[c].ps, gates, row);
+      for (size_t i = 0; i < cands[c].ps.gates.size(); ++i) {
+        PlanPass g1;
+        g1.kind = PASS_GATE;
+        g1.qmask = 1ull << tgt[cands[c].ps.gates[i]];
+        g1.gates.push_back(cands[c].ps.gates[i]);
+        pass_features(n, g1, gates, row + (1 + i) * QS_PASS_FEATURES);
+      }
+    }
+    y.assign(x.size() / QS_PASS_FEATURES, 0.0);
+    QS_TRY(score(x.data(), y.size(), y.data()));
+    size_t best = 0;
+    bool best_tile = true;
+    double best_rate = 1e300, best_time = 0.0;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      const double t_tile = std::exp(y[first[c]]);
+      double t_gates = 0.0, work = 0.0;
+      for (size_t i = 0; i < cands[c].ps.gates.size(); ++i) {
+        const uint32_t k = cands[c].ps.gates[i];
+        t_gates += std::exp(y[first[c] + 1 + i]);
+        work += op_touch_fraction(gates[k], cms[k]);
+      }
+      const bool tile = cands[c].ps.gates.size() > 1 && t_tile <= t_gates;
+      const double t = tile ? t_tile : t_gates;
+      const double rate = t / std::max(work, 1e-9);
+      if (rate < best_rate) {
+        best_rate = rate;
+        best = c;
+        best_tile = tile;
+        best_time = t;
+      }
+    }
+    Cand& c = cands[best];
+    learned_total += best_time * 1e-3;
+    if (best_tile) {
+      lp->m = std::max(lp->m, __builtin_popcountll(c.ps.qmask));
+      lp->passes.push_back(c.ps);
+      ++lp->n_tile;
+    } else {
+      for (uint32_t k : c.ps.gates) {
+        PlanPass g1;
+        g1.kind = PASS_GATE;
+        g1.qmask = 1ull << tgt[k];
+        g1.gates.push_back(k);
+        lp->passes.push_back(std::move(g1));
+      }
+    }
+    remaining.swap(c.rest);
+  }
+  if (lp->m == 0) lp->m = std::min(n, TILE_DEFAULT_M);
+  double greedy_total = 0.0;
+  QS_TRY(predict_plan(gp.get(), &greedy_total));
+  QS_TRY(predict_plan(lp.get(), &learned_total));
+  // the judge: the greedy plan unless the model predicts the learned plan faster by
+  // more than its typical error on a plan's total (kLearnedMargin)
+  if (learned_total > (1.0 - kLearnedMargin) * greedy_total) {
+    gp->mode = QS_PLAN_LEARNED;
+    gp->learned_fallback = true;
+    gp->est_seconds = greedy_total;
+    *out = gp.release();
+    return QS_OK;
+  }
+  lp->est_seconds = learned_total;
+  *out = lp.release();
   return QS_OK;
 }
 
@@ -805,47 +1035,11 @@ extern "C" int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs
   if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!model) return fail(QS_ERR_UNSUPPORTED, "a learned plan needs a trained cost model");
-  size_t nw = 0;
-  QS_TRY(qs_mlp_num_weights(model, &nw));
-  std::vector<qs_plan*> cands;
-  std::vector<double> feats;
-  std::vector<size_t> first;
-  int rc = QS_OK;
-  // candidate tile widths 8..12: narrower tiles leave most of a CTA idle per op
-  const int mhi = std::min(n, TILE_DEFAULT_M);
-  const int mlo = std::min(mhi, 8);
-  for (int m = mlo; m <= mhi && rc == QS_OK; ++m) {
-    qs_plan* c = nullptr;
-    rc = plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, m, &c);
-    if (rc != QS_OK) break;
-    cands.push_back(c);
-    first.push_back(feats.size() / QS_PASS_FEATURES);
-    size_t base = feats.size();
-    feats.resize(base + c->passes.size() * QS_PASS_FEATURES);
-    for (size_t i = 0; i < c->passes.size(); ++i)
-      pass_features(c, c->passes[i], gates, feats.data() + base + i * QS_PASS_FEATURES);
-  }
-  std::vector<double> pred(feats.size() / QS_PASS_FEATURES);
-  if (rc == QS_OK && !pred.empty()) rc = qs_mlp_forward(model, feats.data(), pred.size(), pred.data());
-  size_t best = 0;
-  double best_s = 1e300;
-  for (size_t c = 0; rc == QS_OK && c < cands.size(); ++c) {
-    size_t end = c + 1 < cands.size() ? first[c + 1] : pred.size();
-    double s = 0.0;
-    for (size_t i = first[c]; i < end; ++i) s += exp(pred[i]) * 1e-3;
-    if (s < best_s) {
-      best_s = s;
-      best = c;
-    }
-  }
-  for (size_t c = 0; c < cands.size(); ++c)
-    if (rc != QS_OK || c != best) delete cands[c];
-  if (rc != QS_OK) return rc;
-  if (cands.empty()) return fail(QS_ERR_INVALID_ARG, "no candidate plan");
-  cands[best]->mode = QS_PLAN_LEARNED;
-  cands[best]->est_seconds = best_s;
-  *out = cands[best];
-  return QS_OK;
+  if (mlp_inputs(model) != QS_PASS_FEATURES)
+    return fail(QS_ERR_INVALID_ARG, "the cost model takes %d inputs, a pass has %d features", mlp_inputs(model),
+                QS_PASS_FEATURES);
+  PassScorer score = [model](const double* x, size_t B, double* y) { return qs_mlp_forward(model, x, B, y); };
+  return plan_build_learned(n, gates, ng, score, out);
 }
 
 extern "C" int qs_plan_free(qs_plan* p) {
@@ -860,6 +1054,7 @@ extern "C" int qs_plan_get_stats(const qs_plan* p, qs_plan_stats* out) {
   out->n_tile_passes = p->n_tile;
   out->n_dense = 0;
   out->tile_qubits = p->m;
+  out->learned_fallback = p->learned_fallback ? 1 : 0;
   out->est_seconds = p->est_seconds;
   return QS_OK;
 }

@@ -54,9 +54,13 @@ def test_mlp_training_fits_a_smooth_function(q):
 
 
 def test_learned_plan_versus_greedy(q, orc):
-    """Train on per-pass timings of n=20..22 random circuits (seeds 100..), then
-    on held-out circuits the learned plan must give the oracle's amplitudes and
-    must not be slower than the greedy plan (it may pick the same tile width)."""
+    """Train on per-pass timings of n=20..22 random circuits (seeds 100..; passes of
+    every candidate kind: widths 10..12, both ways of choosing a pass's qubits, and
+    plain per-gate kernels), then on held-out circuits: the learned plan gives the
+    oracle's amplitudes, every pass is a valid reordering, and the judge holds: the
+    learned plan is never measurably slower than the greedy plan.  The measured
+    ratio is printed (on these families the greedy choices are already the best
+    ones the planner can make, and the learned plan keeps them)."""
     import torch
     from paper_2212_14201_gb300 import costmodel
     train_c = [(n, w.random_circuit(n, 300, 100 + i, two_qubit_prob=0.4), None) for i, n in enumerate((20, 21, 22, 22))]
@@ -69,6 +73,8 @@ def test_learned_plan_versus_greedy(q, orc):
             g = w.random_circuit(n, 400, seed, two_qubit_prob=0.4)
             pl = q.qs_plan_create_learned(n, g, m)
             pg = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+            order = np.concatenate([idx for _, _, idx in q.qs_plan_passes(pl)])
+            assert sorted(order.tolist()) == list(range(len(g)))
             h = q.qs_alloc(n, torch.cuda.current_stream())
             try:
                 if n <= 18:
@@ -88,9 +94,10 @@ def test_learned_plan_versus_greedy(q, orc):
                         best = min(best, e0.elapsed_time(e1))
                     times[name] = best
                 st = q.qs_plan_get_stats(pl)
-                print(f"n={n}: learned tile width {st['tile_qubits']} {times['learned']:.3f} ms, "
-                      f"greedy {times['greedy']:.3f} ms")
-                assert times["learned"] <= 1.10 * times["greedy"] + 0.05
+                print(f"n={n}: learned {times['learned']:.3f} ms ({st['n_passes']} passes, greedy kept: "
+                      f"{bool(st['learned_fallback'])}), greedy {times['greedy']:.3f} ms, "
+                      f"gain {times['greedy'] / times['learned']:.4f}")
+                assert times["learned"] <= 1.02 * times["greedy"] + 0.02
             finally:
                 q.qs_free(h)
                 q.qs_plan_free(pl)
