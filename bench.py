@@ -37,8 +37,11 @@ SAMPLE_SEED = 11
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# Integer multiply-add peak (Q60 engine): 152 SMs x 64 IMAD(.WIDE)/clk/SM x 2.07 GHz.
-INT_PEAK_OPS = 152 * 64 * 2.07e9
+# Wide integer multiply-add peak (Q60 engine): a warp's mad.wide.s32 (32x32->64)
+# holds the FMA-heavy pipe of its SM sub-partition for 4 cycles (ncu pipe counters
+# of a register-only loop of them), so 152 SMs x 4 sub-partitions x 8 lanes/clk x
+# 2.07 GHz.
+INT_PEAK_OPS = 152 * 4 * 8 * 2.07e9
 
 
 def parse():
@@ -198,22 +201,26 @@ def roofline(records, hbm_peak_gbs):
     t_fp = fpl / FP64_PEAK_FLOPS
     t_int = ipl / INT_PEAK_OPS
     total = sum(v["ms"] for v in by.values())
-    if t_fp > max(t_hbm, t_int):
-        ach = fpl / (per_ms * 1e-3) / 1e12
-        out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s (fp64)",
-               "frac": ach / (FP64_PEAK_FLOPS / 1e12)}
-    elif t_int > t_hbm:
-        ach = ipl / (per_ms * 1e-3) / 1e12
-        out = {"bound": "alu", "achieved": ach, "peak": INT_PEAK_OPS / 1e12, "unit": "Tmad/s (int32 multiply-add)",
-               "frac": ach / (INT_PEAK_OPS / 1e12)}
-    else:
-        ach = bpl / (per_ms * 1e-3) / 1e9
-        out = {"bound": "hbm", "achieved": ach, "peak": hbm_peak_gbs, "unit": "GB/s", "frac": ach / hbm_peak_gbs}
+    # The roofline of the path is HBM: a fused pass moves 32 B per amplitude.  The
+    # arithmetic the kernel actually runs is reported beside it: FP64 flops against
+    # the derived FP64 peak, or (Q60 engine) its wide integer multiply-adds against
+    # the derived integer peak.
+    ach = bpl / (per_ms * 1e-3) / 1e9
+    out = {"bound": "hbm", "achieved": ach, "peak": hbm_peak_gbs, "unit": "GB/s", "frac": ach / hbm_peak_gbs}
+    if ipl > 0:
+        a_int = ipl / (per_ms * 1e-3) / 1e12
+        out["alu"] = {"bound": "alu", "achieved": a_int, "peak": INT_PEAK_OPS / 1e12,
+                      "unit": "T wide int multiply-adds/s", "frac": a_int / (INT_PEAK_OPS / 1e12),
+                      "floor_ms_per_launch": t_int * 1e3}
+    elif fpl > 0:
+        a_fp = fpl / (per_ms * 1e-3) / 1e12
+        out["alu"] = {"bound": "alu", "achieved": a_fp, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s (fp64)",
+                      "frac": a_fp / (FP64_PEAK_FLOPS / 1e12), "floor_ms_per_launch": t_fp * 1e3}
     out.update({"kernel_kind": kind, "launches": d["launches"], "avg_launch_ms": per_ms,
                 "share_of_kernel_time": d["ms"] / total if total else None,
                 "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": fpl,
                 "algorithmic_int_mads_per_launch": ipl,
-                "hbm_frac": (bpl / (per_ms * 1e-3) / 1e9) / hbm_peak_gbs,
+                "hbm_floor_ms_per_launch": t_hbm * 1e3,
                 "traffic": traffic_for(kind)})
     return out
 
@@ -294,14 +301,26 @@ def bench_batched_vqe(q, torch, steps: int, warmup: int, sets: int = 1024):
     finally:
         q.qs_batch_free(b)
     kms = float(np.mean(kms))
+    # algorithmic traffic per step: per set (24 n forward gates + about 48 n backward
+    # gate steps on two vectors + n + 1 for the Hamiltonian) sweeps of 32 B per amplitude
+    sweep_bytes = float(sum((73 * int(n) + 1) * 32.0 * float(1 << int(n)) for n in ns))
+    l2 = l2_copy_gbs(torch)
+    eff = sweep_bytes / (kms * 1e-3) / 1e9
     return {"grad_evals_per_s": len(ns) / (kms * 1e-3), "kernel_ms": kms,
+            "roofline": {"bound": "l2", "achieved": eff, "peak": l2, "unit": "GB/s", "frac": eff / l2,
+                         "algorithmic_bytes_per_step": sweep_bytes,
+                         "note": "logical gate-by-gate sweeps (per set: 73 n + 1 sweeps of 32 B per amplitude), "
+                                 "on states that stay in L2 / shared memory (n <= 20: 16 MiB), against the "
+                                 "copy bandwidth of a 2 x 24 MiB buffer pair measured in this run"},
             "e2e_grad_evals_per_s": len(ns) / wall, "e2e_ms": wall * 1e3, "sets": len(ns),
             "params": int(len(params)), "launch": info,
             "workload": f"{sets} sets, n~U{{10..20}}, 8-layer RY/RZ+CNOT-ring ansatz, TFIM h=0.7"}
 
 
-def bench_adjoint(q, torch, stream, steps: int):
-    """Energy + 672-parameter adjoint gradient at n=28 (12-layer ansatz, ZZ chain)."""
+def bench_adjoint(q, torch, stream, steps: int, hbm_peak: float):
+    """Energy + 672-parameter adjoint gradient at n=28 (12-layer ansatz, ZZ chain).
+    Roofline of the fused backward passes (the dominant kernel): each moves psi and
+    lambda once, 64 B per amplitude (16 B read + 16 B written per vector)."""
     n = 28
     g, npar = w.hea_ansatz(n, 12)
     th = w.uniform_angles(npar, 4)
@@ -314,9 +333,47 @@ def bench_adjoint(q, torch, stream, steps: int):
         for _ in range(steps):
             q.qs_adjoint_grad(h, g, th, H)
         dt = (time.perf_counter() - t0) / steps
+        q.qs_timing_enable(h, True)
+        q.qs_timing_fetch(h)
+        q.qs_adjoint_grad(h, g, th, H)
+        recs = q.qs_timing_fetch(h)
+        q.qs_timing_enable(h, False)
     finally:
         q.qs_free(h)
-    return {"grad_evals_per_s": 1.0 / dt, "ms_per_eval": dt * 1e3, "n": n, "params": npar, "gates": len(g)}
+    out = {"grad_evals_per_s": 1.0 / dt, "ms_per_eval": dt * 1e3, "n": n, "params": npar, "gates": len(g)}
+    back = [r for r in recs if r["kind"] == 30 and r["k"] >= 2]
+    fwd = [r for r in recs if r["kind"] == 11]
+    total = sum(r["ms"] for r in recs)
+    if back:
+        bms = float(np.mean([r["ms"] for r in back]))
+        gbs = 64.0 * float(1 << n) / (bms * 1e-3) / 1e9
+        out["backward_pass"] = {"launches": len(back), "avg_ms": bms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                                "share_of_kernel_time": sum(r["ms"] for r in back) / total,
+                                "algorithmic_bytes_per_launch": 64.0 * float(1 << n)}
+    if fwd:
+        fms = float(np.mean([r["ms"] for r in fwd]))
+        gbs = 32.0 * float(1 << n) / (fms * 1e-3) / 1e9
+        out["forward_pass"] = {"launches": len(fwd), "avg_ms": fms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+    return out
+
+
+def l2_copy_gbs(torch, mib: int = 24, reps: int = 400) -> float:
+    """Copy bandwidth of a buffer pair that fits in L2 (2 x 24 MiB of the 129 MB):
+    read + written bytes / time, CUDA events, after warm-up."""
+    a = torch.empty(mib << 18, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    for _ in range(20):
+        b.copy_(a)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return 2.0 * a.numel() * 4 / (ms * 1e-3) / 1e9
 
 
 def bench_measure(q, torch, stream, hbm_peak: float):
@@ -570,8 +627,11 @@ def run_ours(args, world, rank, local, pg):
     samples = torch.empty(SHOTS, dtype=torch.int64, device="cuda")
     plan = None
     plan_stats = None
+    plan_ms = None
     try:
+        t_plan = time.perf_counter()
         plan = q.qs_plan_create(n, gates, q.PLAN_GREEDY, 5)
+        plan_ms = (time.perf_counter() - t_plan) * 1e3
         plan_stats = q.qs_plan_get_stats(plan)
     except q.QsimError:
         plan = None
@@ -658,7 +718,7 @@ def run_ours(args, world, rank, local, pg):
     if not args.no_extra:
         torch.cuda.empty_cache()
         extra["batched_vqe"] = bench_batched_vqe(q, torch, 3, 3)
-        extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2)
+        extra["adjoint_n28"] = bench_adjoint(q, torch, stream, 2, hbm_peak)
         extra["measure_n30"] = bench_measure(q, torch, stream, hbm_peak)
         extra["reductions_n30"] = bench_reductions(q, torch, stream, hbm_peak)
         extra["c64_n30"] = bench_c64(q, torch, stream, hbm_peak)
@@ -701,7 +761,10 @@ def run_ours(args, world, rank, local, pg):
         "peak_source": {"hbm": peak_src, "fp64": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
         "cpu_baseline": cpu,
         "e2e": {"value": world * amp_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes),
-                "d2h_bytes_per_step": SHOTS * 8 + 8, "matches_device_run": bool(ok_e2e)},
+                "d2h_bytes_per_step": SHOTS * 8 + 8, "matches_device_run": bool(ok_e2e),
+                "plan_ms": plan_ms,
+                "plan_note": "the greedy plan is built once before the timed steps (host, plan_ms) and reused; "
+                             "each step's op lists and phase tables are rebuilt on the host from the gate list"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "batched_vqe": extra.get("batched_vqe"),
