@@ -92,6 +92,39 @@ const char* qs_last_error(void);
 /* Largest qubit count a state may have in this build (34). */
 int qs_max_qubits(void);
 
+/* ---- host-side fault injection ---------------------------------------------------
+ * Drives the library's error paths without a GPU fault.  One fault is armed per
+ * process.  QS_FAULT_ALLOC fails device and pinned-host allocations (every
+ * cudaMalloc / cudaMallocAsync / cudaMallocHost the library makes) before they
+ * reach CUDA, as an out-of-memory would: the call returns QS_ERR_OOM.
+ * QS_FAULT_LAUNCH fails the check that follows a kernel launch as a launch
+ * failure would: the call returns QS_ERR_CUDA (that kernel has already been
+ * queued; its stream and the context stay usable, as they do after a real
+ * non-sticky launch error).  qs_last_error() then ends in "(injected by the
+ * armed fault)".
+ *
+ * On error, every entry point frees what it allocated during the call.  A call
+ * that only reads a state (reductions, sampling, copies out) leaves it unchanged.
+ * A call that writes the state (qs_apply, qs_run_*, qs_measure, ...) may have run
+ * some of its kernels before the failing allocation or launch, so the amplitudes
+ * are then unspecified; the handle stays valid, and qs_set_zero / qs_set_state
+ * make it usable again.
+ *
+ * qs_fault_set(kind, after, count): the first `after` events of `kind` pass, the
+ * next `count` fail (count -1: all that follow); kind QS_FAULT_NONE disarms.
+ * INVALID_ARG for an unknown kind, after < 0, count 0 or count < -1.
+ * The environment variable QS_FAULT = "alloc" | "launch", optionally followed by
+ * ":after" and ":count" (default 0 and 1), arms the same fault when the library
+ * loads; an unparsable value arms nothing, and qs_fault_get's env_status holds
+ * the parse result (QS_OK or INVALID_ARG).
+ * qs_fault_get: the armed kind, events still to pass, failures still to inject
+ * (-1: unlimited), failures injected so far; any pointer may be NULL. */
+#define QS_FAULT_NONE 0
+#define QS_FAULT_ALLOC 1
+#define QS_FAULT_LAUNCH 2
+int qs_fault_set(int kind, long long after, long long count);
+int qs_fault_get(int* kind, long long* after, long long* left, long long* fired, int* env_status);
+
 /* ---- states (qAlloc_many / init_qvm in the paper's listings) --------------------- */
 
 /* Allocate an n-qubit state (1 <= n <= qs_max_qubits()) on the current CUDA
@@ -384,9 +417,11 @@ int qs_expect_z_all(const qs_state* s, double* out);
  * Asynchronous: results are in device_out once `stream` reaches this point.
  * The partial sums live in one file-scope device array (25,600 doubles,
  * 200 KiB), which every GPU that loads the library holds until the process
- * exits.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
+ * exits.  Each call outside stream capture looks up that array's device address
+ * (cudaGetSymbolAddress, which allocates nothing) with the device current;
+ * during capture the address of the last call on that device is used, so make
+ * a first call on each device before any stream capture (a call captured first
+ * fails with UNSUPPORTED).  All calls share the array and it keeps the last call's
  * contents, which no call reads before rewriting; calls whose kernels overlap on
  * the GPU (other streams, other host threads) race on it and must be ordered by
  * the caller. */

@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import (ARITH_AUTO, ARITH_FIXED, ARITH_FP64, GATE_DTYPE, NOISE_DTYPE, PAULI_DTYPE, PINSTR_DTYPE, PLAN_GREEDY,  # noqa: F401
+from ._lib import (ARITH_AUTO, ARITH_FIXED, ARITH_FP64, FAULT_ALLOC, FAULT_LAUNCH, FAULT_NONE, GATE_DTYPE, NOISE_DTYPE, PAULI_DTYPE, PINSTR_DTYPE, PLAN_GREEDY,  # noqa: F401
                    PLAN_LEARNED, PLAN_PLAIN, QsimError)
 
 # every C entry point's wrapper, under its C name

@@ -69,6 +69,10 @@ PP = ctypes.POINTER(ctypes.c_void_p)
 SIGNATURES = {
     "qs_last_error": (ctypes.c_char_p, []),
     "qs_max_qubits": (I32, []),
+    "qs_fault_set": (I32, [I32, ctypes.c_longlong, ctypes.c_longlong]),
+    "qs_fault_get": (I32, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                           ctypes.POINTER(ctypes.c_int)]),
     "qs_alloc": (I32, [I32, P, PP]),
     "qs_alloc_external": (I32, [I32, P, P, PP]),
     "qs_alloc_c64": (I32, [I32, P, PP]),
@@ -197,6 +201,22 @@ def qs_last_error() -> str:
 
 def qs_max_qubits() -> int:
     return lib().qs_max_qubits()
+
+
+FAULT_NONE, FAULT_ALLOC, FAULT_LAUNCH = 0, 1, 2
+
+
+def qs_fault_set(kind: int, after: int = 0, count: int = 1) -> None:
+    """Arm the host-side fault: the first `after` events of `kind` pass, the next
+    `count` fail (-1: all); FAULT_NONE disarms."""
+    _chk(lib().qs_fault_set(kind, after, count))
+
+
+def qs_fault_get() -> dict:
+    k, env = ctypes.c_int(), ctypes.c_int()
+    a, l, f = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _chk(lib().qs_fault_get(ctypes.byref(k), ctypes.byref(a), ctypes.byref(l), ctypes.byref(f), ctypes.byref(env)))
+    return {"kind": k.value, "after": a.value, "left": l.value, "fired": f.value, "env_status": env.value}
 
 
 def qs_alloc(n: int, stream=None) -> int:

@@ -486,10 +486,10 @@ static int backward_fused(qs_state* s, double2* lam, const qs_gate* gates, size_
   QC* d_mats = nullptr;
   QC* d_dgm = nullptr;
   QL* d_rpm = nullptr;
-  QS_CUDA(cudaMallocAsync((void**)&d_ops, sizeof(BOp) * std::max<size_t>(1, ops.size()), s->stream));
-  cudaError_t e = cudaMallocAsync((void**)&d_mats, sizeof(QC) * std::max<size_t>(4, mats.size()), s->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_dgm, sizeof(QC) * std::max<size_t>(16, dgm.size()), s->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_rpm, sizeof(QL) * std::max<size_t>(16, rpm.size()), s->stream);
+  QS_CUDA(dmalloc_async((void**)&d_ops, sizeof(BOp) * std::max<size_t>(1, ops.size()), s->stream));
+  cudaError_t e = dmalloc_async((void**)&d_mats, sizeof(QC) * std::max<size_t>(4, mats.size()), s->stream);
+  if (e == cudaSuccess) e = dmalloc_async((void**)&d_dgm, sizeof(QC) * std::max<size_t>(16, dgm.size()), s->stream);
+  if (e == cudaSuccess) e = dmalloc_async((void**)&d_rpm, sizeof(QL) * std::max<size_t>(16, rpm.size()), s->stream);
   if (e == cudaSuccess && !rpm.empty())
     e = cudaMemcpyAsync(d_rpm, rpm.data(), sizeof(QL) * rpm.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && !ops.empty())
@@ -638,7 +638,7 @@ extern "C" int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, con
   const size_t bytes = N * sizeof(double2);
   // lambda lives next to the state for the duration of the call
   double2* lam = nullptr;
-  QS_CUDA(cudaMallocAsync((void**)&lam, bytes, s->stream));
+  QS_CUDA(dmalloc_async((void**)&lam, bytes, s->stream));
   const int nblocks = 608;
   double* part = nullptr;
   double* sums = nullptr;
@@ -648,8 +648,8 @@ extern "C" int qs_adjoint_grad(qs_state* s, const qs_gate* gates, size_t ng, con
     if (part) cudaFreeAsync(part, s->stream);
     if (sums) cudaFreeAsync(sums, s->stream);
   };
-  cudaError_t e = cudaMallocAsync((void**)&part, sizeof(double) * nblocks * (nslots + 1), s->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&sums, sizeof(double) * (nslots + 1), s->stream);
+  cudaError_t e = dmalloc_async((void**)&part, sizeof(double) * nblocks * (nslots + 1), s->stream);
+  if (e == cudaSuccess) e = dmalloc_async((void**)&sums, sizeof(double) * (nslots + 1), s->stream);
   if (e != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "adjoint workspace");

@@ -474,7 +474,7 @@ template <class T>
 static int upload(qs_batch* b, const std::vector<T>& v, const T** out) {
   void* p = nullptr;
   size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
-  QS_CUDA(cudaMalloc(&p, bytes));
+  QS_CUDA(dmalloc(&p, bytes));
   b->dev.push_back(p);
   if (!v.empty()) QS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   *out = (const T*)p;
@@ -482,7 +482,7 @@ static int upload(qs_batch* b, const std::vector<T>& v, const T** out) {
 }
 
 static int dev_alloc(qs_batch* b, size_t bytes, void** out) {
-  QS_CUDA(cudaMalloc(out, std::max<size_t>(bytes, 16)));
+  QS_CUDA(dmalloc(out, std::max<size_t>(bytes, 16)));
   b->dev.push_back(*out);
   return QS_OK;
 }
@@ -735,9 +735,9 @@ extern "C" int qs_batch_create(size_t nsets, const int* n_per_set, const qs_gate
   if (rc == QS_OK && chk(dev_alloc(b, std::max<size_t>(1, bgates.size()) * 4 * sizeof(QC), &p))) a.matb = (QC*)p;
   if (rc == QS_OK && chk(dev_alloc(b, sizeof(int), &p))) a.counter = (int*)p;
   if (rc == QS_OK) {
-    e = cudaMallocHost(&b->h_params, np * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_grads, np * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_energies, nsets * sizeof(double));
+    e = hmalloc_pinned(&b->h_params, np * sizeof(double));
+    if (e == cudaSuccess) e = hmalloc_pinned(&b->h_grads, np * sizeof(double));
+    if (e == cudaSuccess) e = hmalloc_pinned(&b->h_energies, nsets * sizeof(double));
     if (e != cudaSuccess) chk(cuda_fail(e, "cudaMallocHost"));
   }
   if (rc == QS_OK) {

@@ -2,9 +2,11 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "fixed.h"
 #include "internal.h"
@@ -23,9 +25,64 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// ---- host-side fault injection ----------------------------------------------------
+// One armed fault for the process: events of kind g_fault_kind (allocations through
+// dmalloc / dmalloc_async / hmalloc_pinned, or launch checks) pass g_fault_after
+// times, then the next g_fault_count fail (-1: all of them).  QS_FAULT in the
+// environment arms it when the library loads.
+static std::atomic<int> g_fault_kind{QS_FAULT_NONE};
+static std::atomic<long long> g_fault_after{0};
+static std::atomic<long long> g_fault_left{0};
+static std::atomic<long long> g_fault_fired{0};
+static thread_local bool t_injected = false;
+
+static int fault_arm(int kind, long long after, long long count) {
+  if (kind != QS_FAULT_NONE && kind != QS_FAULT_ALLOC && kind != QS_FAULT_LAUNCH)
+    return fail(QS_ERR_INVALID_ARG, "fault kind %d", kind);
+  if (after < 0 || count < -1 || count == 0) return fail(QS_ERR_INVALID_ARG, "fault after=%lld count=%lld", after, count);
+  g_fault_kind.store(QS_FAULT_NONE);
+  g_fault_after.store(after);
+  g_fault_left.store(count);
+  g_fault_fired.store(0);
+  g_fault_kind.store(kind);
+  return QS_OK;
+}
+
+bool fault_fire(int kind) {
+  if (g_fault_kind.load(std::memory_order_relaxed) != kind) return false;
+  if (g_fault_after.fetch_sub(1) > 0) return false;
+  g_fault_after.store(0);
+  long long left = g_fault_left.load();
+  while (true) {
+    if (left == 0) return false;
+    if (left < 0) break;  // every event fails
+    if (g_fault_left.compare_exchange_weak(left, left - 1)) break;
+  }
+  g_fault_fired.fetch_add(1);
+  t_injected = true;
+  return true;
+}
+
+// QS_FAULT = "alloc" | "launch", optionally ":after" and ":count" (count -1: every
+// event after the first `after`); anything else leaves the library unarmed.
+static int parse_fault_spec(const char* spec) {
+  if (!spec || !*spec) return QS_OK;
+  char kind[16] = {0};
+  long long after = 0, count = 1;
+  int got = sscanf(spec, "%15[a-z]:%lld:%lld", kind, &after, &count);
+  if (got < 1) return fail(QS_ERR_INVALID_ARG, "QS_FAULT=%s", spec);
+  int k = strcmp(kind, "alloc") == 0 ? QS_FAULT_ALLOC : strcmp(kind, "launch") == 0 ? QS_FAULT_LAUNCH : -1;
+  if (k < 0) return fail(QS_ERR_INVALID_ARG, "QS_FAULT=%s: kind is alloc or launch", spec);
+  return fault_arm(k, after, count);
+}
+
+static const int g_fault_from_env = parse_fault_spec(getenv("QS_FAULT"));
+
 int cuda_fail(cudaError_t e, const char* what) {
-  return fail(e == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA, "%s: %s", what,
-              cudaGetErrorString(e));
+  const bool inj = t_injected;
+  t_injected = false;
+  return fail(e == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA, "%s: %s%s", what,
+              cudaGetErrorString(e), inj ? " (injected by the armed fault)" : "");
 }
 
 void clear_error() { g_err.clear(); }
@@ -33,6 +90,7 @@ void clear_error() { g_err.clear(); }
 int launch_check(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, what);
+  if (fault_fire(QS_FAULT_LAUNCH)) return cuda_fail(cudaErrorLaunchFailure, what);
   return QS_OK;
 }
 
@@ -59,7 +117,7 @@ int ensure_pinned(qs_state* s, size_t bytes) {
   if (s->pinned) cudaFreeHost(s->pinned);
   s->pinned = nullptr;
   s->pinned_bytes = 0;
-  QS_CUDA(cudaMallocHost(&s->pinned, bytes));
+  QS_CUDA(hmalloc_pinned(&s->pinned, bytes));
   s->pinned_bytes = bytes;
   return QS_OK;
 }
@@ -240,6 +298,20 @@ extern "C" const char* qs_last_error(void) { return g_err.c_str(); }
 
 extern "C" int qs_max_qubits(void) { return QS_MAX_QUBITS; }
 
+extern "C" int qs_fault_set(int kind, long long after, long long count) {
+  clear_error();
+  return fault_arm(kind, after, count);
+}
+
+extern "C" int qs_fault_get(int* kind, long long* after, long long* left, long long* fired, int* env_status) {
+  if (kind) *kind = g_fault_kind.load();
+  if (after) *after = std::max(0ll, g_fault_after.load());
+  if (left) *left = g_fault_left.load();
+  if (fired) *fired = g_fault_fired.load();
+  if (env_status) *env_status = g_fault_from_env;
+  return QS_OK;
+}
+
 __global__ void k_set_zero(double2* __restrict__ a, size_t N) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -270,7 +342,7 @@ static int create(int n, void* dev, void* stream, qs_state** out, int prec = 128
     s->owns = false;
     s->bound = 0;
   } else {
-    cudaError_t e = cudaMalloc(&s->amps, bytes);
+    cudaError_t e = dmalloc(&s->amps, bytes);
     if (e != cudaSuccess) {
       delete s;
       return cuda_fail(e, "cudaMalloc(state)");
@@ -278,7 +350,7 @@ static int create(int n, void* dev, void* stream, qs_state** out, int prec = 128
     s->owns = true;
   }
   s->ws_bytes = workspace_bytes(n);
-  cudaError_t e = cudaMalloc(&s->ws, s->ws_bytes);
+  cudaError_t e = dmalloc(&s->ws, s->ws_bytes);
   if (e != cudaSuccess) {
     if (s->owns) cudaFree(s->amps);
     delete s;

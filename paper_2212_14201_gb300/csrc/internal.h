@@ -99,6 +99,28 @@ void clear_error();
 int check_state(const qs_state* s);
 int launch_check(const char* what);  // cudaGetLastError after a launch
 
+// ---- host-side fault injection (qs_fault_set, QS_FAULT) --------------------------
+// True when the armed fault of `kind` (QS_FAULT_ALLOC or QS_FAULT_LAUNCH) fires at
+// this event; the next cuda_fail on this thread then marks its message as injected.
+bool fault_fire(int kind);
+// Every device and pinned-host allocation of the library goes through these, so
+// that an armed allocation fault fails it as cudaErrorMemoryAllocation would.
+template <class T>
+inline cudaError_t dmalloc(T** p, size_t bytes) {
+  if (fault_fire(QS_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
+  return cudaMalloc((void**)p, bytes);
+}
+template <class T>
+inline cudaError_t dmalloc_async(T** p, size_t bytes, cudaStream_t st) {
+  if (fault_fire(QS_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync((void**)p, bytes, st);
+}
+template <class T>
+inline cudaError_t hmalloc_pinned(T** p, size_t bytes) {
+  if (fault_fire(QS_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
+  return cudaMallocHost((void**)p, bytes);
+}
+
 // ---- complex helpers (host) ---------------------------------------------------
 struct C2 {
   double re, im;

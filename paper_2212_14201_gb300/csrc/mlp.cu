@@ -159,14 +159,14 @@ static int mlp_reserve(qs_mlp* m, long long B) {
   if (B <= m->cap) return QS_OK;
   mlp_free_batch(m);
   const long long F = m->d.F, H = m->d.H;
-  QS_CUDA(cudaMalloc(&m->x, sizeof(double) * B * F));
-  QS_CUDA(cudaMalloc(&m->t, sizeof(double) * B));
-  QS_CUDA(cudaMalloc(&m->y, sizeof(double) * B));
-  QS_CUDA(cudaMalloc(&m->h1, sizeof(double) * B * H));
-  QS_CUDA(cudaMalloc(&m->h2, sizeof(double) * B * H));
-  QS_CUDA(cudaMalloc(&m->dy, sizeof(double) * B));
-  QS_CUDA(cudaMalloc(&m->d1, sizeof(double) * B * H));
-  QS_CUDA(cudaMalloc(&m->d2, sizeof(double) * B * H));
+  QS_CUDA(dmalloc(&m->x, sizeof(double) * B * F));
+  QS_CUDA(dmalloc(&m->t, sizeof(double) * B));
+  QS_CUDA(dmalloc(&m->y, sizeof(double) * B));
+  QS_CUDA(dmalloc(&m->h1, sizeof(double) * B * H));
+  QS_CUDA(dmalloc(&m->h2, sizeof(double) * B * H));
+  QS_CUDA(dmalloc(&m->dy, sizeof(double) * B));
+  QS_CUDA(dmalloc(&m->d1, sizeof(double) * B * H));
+  QS_CUDA(dmalloc(&m->d2, sizeof(double) * B * H));
   m->cap = B;
   return QS_OK;
 }
@@ -206,11 +206,11 @@ extern "C" int qs_mlp_create(int n_in, int n_hidden, const double* weights, uint
     w0[m->d.ob3] = 0.0;
   }
   cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&m->w, sizeof(double) * NW);
-  if (e == cudaSuccess) e = cudaMalloc(&m->m1, sizeof(double) * NW);
-  if (e == cudaSuccess) e = cudaMalloc(&m->m2, sizeof(double) * NW);
-  if (e == cudaSuccess) e = cudaMalloc(&m->g, sizeof(double) * NW);
-  if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
+  if (e == cudaSuccess) e = dmalloc(&m->w, sizeof(double) * NW);
+  if (e == cudaSuccess) e = dmalloc(&m->m1, sizeof(double) * NW);
+  if (e == cudaSuccess) e = dmalloc(&m->m2, sizeof(double) * NW);
+  if (e == cudaSuccess) e = dmalloc(&m->g, sizeof(double) * NW);
+  if (e == cudaSuccess) e = dmalloc(&m->loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpy(m->w, w0.data(), sizeof(double) * NW, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->m1, 0, sizeof(double) * NW);
   if (e == cudaSuccess) e = cudaMemset(m->m2, 0, sizeof(double) * NW);

@@ -416,7 +416,7 @@ extern "C" int qs_readout_error(uint64_t* samples, size_t shots, int n, double f
   if (!shots) return QS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   uint64_t* d = samples;
-  if (!on_device) QS_CUDA(cudaMallocAsync(&d, shots * sizeof(uint64_t), st));
+  if (!on_device) QS_CUDA(dmalloc_async(&d, shots * sizeof(uint64_t), st));
   int rc = QS_OK;
   cudaError_t e = cudaSuccess;
   if (!on_device) e = cudaMemcpyAsync(d, samples, shots * sizeof(uint64_t), cudaMemcpyHostToDevice, st);

@@ -108,7 +108,7 @@ struct PaBlock {
     for (size_t j = start; j < items.size(); ++j) {
       PaItem& it = items[j];
       if (it.kind != 0) {
-        if (!snap[j]) QS_CUDA(cudaMallocAsync(&snap[j], bytes, s->stream));
+        if (!snap[j]) QS_CUDA(dmalloc_async(&snap[j], bytes, s->stream));
         QS_CUDA(cudaMemcpyAsync(snap[j], s->amps, bytes, cudaMemcpyDeviceToDevice, s->stream));
       }
       if (it.kind == 0) {
@@ -202,8 +202,8 @@ extern "C" int qs_partial_amplitudes(int n, const qs_gate* gates, size_t ng, con
   uint64_t* didx = nullptr;
   double2* dout = nullptr;
   const size_t cnt = std::max<size_t>(count, 1);
-  QS_CUDA(cudaMallocAsync(&didx, cnt * sizeof(uint64_t), st));
-  cudaError_t e = cudaMallocAsync(&dout, cnt * sizeof(double2), st);
+  QS_CUDA(dmalloc_async(&didx, cnt * sizeof(uint64_t), st));
+  cudaError_t e = dmalloc_async(&dout, cnt * sizeof(double2), st);
   int rc = e == cudaSuccess ? QS_OK : cuda_fail(e, "cudaMallocAsync(out)");
   if (rc == QS_OK && count) {
     e = cudaMemcpyAsync(didx, indices, count * sizeof(uint64_t), cudaMemcpyHostToDevice, st);

@@ -1174,7 +1174,7 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
     if (s->tables_pinned) cudaFreeHost(s->tables_pinned);
     s->tables_pinned = nullptr;
     s->tables_pinned_bytes = 0;
-    QS_CUDA(cudaMallocHost(&s->tables_pinned, bytes));
+    QS_CUDA(hmalloc_pinned(&s->tables_pinned, bytes));
     s->tables_pinned_bytes = bytes;
   }
   if (s->tables_bytes < bytes) {
@@ -1184,7 +1184,7 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
     }
     s->tables = nullptr;
     s->tables_bytes = 0;
-    QS_CUDA(cudaMalloc(&s->tables, bytes));
+    QS_CUDA(dmalloc(&s->tables, bytes));
     s->tables_bytes = bytes;
   }
   if (f32) {

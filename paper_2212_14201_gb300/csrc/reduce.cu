@@ -791,7 +791,7 @@ namespace qs {
 int marginal_host(qs_state* s, const int* qubits, int nq, double* out, bool allow_exact) {
   size_t H = (size_t)1 << nq;
   double* tmp = nullptr;
-  QS_CUDA(cudaMallocAsync(&tmp, H * sizeof(double), s->stream));
+  QS_CUDA(dmalloc_async(&tmp, H * sizeof(double), s->stream));
   int rc = marginal_device(s, qubits, nq, tmp, allow_exact);
   if (rc == QS_OK) {
     cudaError_t e = cudaMemcpyAsync(out, tmp, H * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -812,7 +812,7 @@ extern "C" int qs_probs(const qs_state* cs, const int* qubits, int nq, double* o
   size_t H = (size_t)1 << nq;
   if (on_device) return marginal_device(s, qubits, nq, out);
   double* tmp = nullptr;
-  QS_CUDA(cudaMallocAsync(&tmp, H * sizeof(double), s->stream));
+  QS_CUDA(dmalloc_async(&tmp, H * sizeof(double), s->stream));
   int rc = marginal_device(s, qubits, nq, tmp);
   if (rc == QS_OK) {
     cudaError_t e = cudaMemcpyAsync(out, tmp, H * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -1051,21 +1051,41 @@ extern "C" int qs_expect_pauli(const qs_state* cs, const qs_pauli* terms, size_t
 #define QS_NOALLOC_EZ_SLOTS (1024 * 25)
 static __device__ __align__(256) double g_noalloc_ez_partials[QS_NOALLOC_EZ_SLOTS];
 
-// Device address of g_noalloc_ez_partials, looked up once per device (the name
-// itself is only a host-side stand-in and must not be passed to a kernel).
+// Register bits r of k_expect_z for n qubits (as the entry point chooses them) and
+// the partials a launch writes: 2^(n - r) CTAs, r + 1 values each.
+constexpr int noalloc_ez_r(int n) {
+  return std::min(std::max(8, n - 10), std::min(n, 8 + ZMAXJ));
+}
+constexpr bool noalloc_ez_fits() {
+  for (int n = QS_NOALLOC_EZ_MIN_QUBITS; n <= QS_NOALLOC_EZ_MAX_QUBITS; ++n)
+    if ((1ll << (n - noalloc_ez_r(n))) * (noalloc_ez_r(n) + 1) > QS_NOALLOC_EZ_SLOTS) return false;
+  return true;
+}
+static_assert(noalloc_ez_fits(), "the static partials array must hold the largest launch of its qubit range");
+
+// Device address of g_noalloc_ez_partials (the name itself is only a host-side
+// stand-in and must not be passed to a kernel).  Outside stream capture it is
+// looked up on every call (cudaGetSymbolAddress allocates nothing), so a context
+// that was torn down and created again cannot leave a stale address; during
+// capture, when runtime calls may not be allowed, the address of the last call
+// on the device is used.
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[64] = {nullptr};
 
-static int noalloc_scratch(double** out) {
+static int noalloc_scratch(cudaStream_t st, double** out) {
   int dev = 0;
   QS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(QS_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  QS_CUDA(cudaStreamIsCapturing(st, &cs));
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ez_partials);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_ez_partials)");
     g_noalloc_ptr[dev] = (double*)p;
+  } else if (!g_noalloc_ptr[dev]) {
+    return fail(QS_ERR_UNSUPPORTED, "make the first qs_expect_z_all_noalloc call on a device before stream capture");
   }
   *out = g_noalloc_ptr[dev];
   return QS_OK;
@@ -1078,14 +1098,11 @@ extern "C" int qs_expect_z_all_noalloc(const double* device_amps, int n, double*
     return fail(QS_ERR_INVALID_ARG, "qs_expect_z_all_noalloc supports %d <= n <= %d qubits (got n=%d)",
                 QS_NOALLOC_EZ_MIN_QUBITS, QS_NOALLOC_EZ_MAX_QUBITS, n);
   if ((uintptr_t)device_amps & 15) return fail(QS_ERR_INVALID_ARG, "amplitudes not 16-byte aligned");
-  double* part = nullptr;
-  QS_TRY(noalloc_scratch(&part));
-  int r = std::max(8, n - 10);
-  r = std::min(r, std::min(n, 8 + ZMAXJ));
-  const int nblocks = 1 << (n - r);
-  if ((size_t)nblocks * (size_t)(r + 1) > QS_NOALLOC_EZ_SLOTS)
-    return fail(QS_ERR_INVALID_ARG, "n=%d needs more scratch than the static array holds", n);
   cudaStream_t st = (cudaStream_t)stream;
+  double* part = nullptr;
+  QS_TRY(noalloc_scratch(st, &part));
+  const int r = noalloc_ez_r(n);
+  const int nblocks = 1 << (n - r);
   note_launch(2);
   // every partial that k_expect_z_finish reads is written first by k_expect_z, so
   // nothing left over from an earlier call is read

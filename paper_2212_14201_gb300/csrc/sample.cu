@@ -196,7 +196,7 @@ extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint
       if (p) cudaFreeAsync(p, st);
     }
   } cpb{nullptr, s->stream};
-  QS_CUDA(cudaMallocAsync(&cpb.p, (size_t)(N / K) * sizeof(double), s->stream));  // 1/64 of the state's bytes
+  QS_CUDA(dmalloc_async(&cpb.p, (size_t)(N / K) * sizeof(double), s->stream));  // 1/64 of the state's bytes
   double* cp = (double*)cpb.p;
   int g1 = (int)std::min<int64_t>((nb + 127) / 128, 152 * 16);
   KTimer kt(s, QS_K_REDUCE, s->n, 3, 0, 0, (double)N, 4.0 * (double)N);
@@ -215,7 +215,7 @@ extern "C" int qs_sample(const qs_state* cs, uint64_t seed, uint64_t shots, uint
   QS_TRY(launch_check("superblock offset"));
   uint64_t* dout = out;
   if (!on_device) {
-    const cudaError_t e = cudaMallocAsync((void**)&dout, shots * sizeof(uint64_t), s->stream);
+    const cudaError_t e = dmalloc_async((void**)&dout, shots * sizeof(uint64_t), s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(samples)");
   }
   int g3 = (int)std::min<uint64_t>((shots + 127) / 128, 152 * 16);

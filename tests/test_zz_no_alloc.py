@@ -18,14 +18,18 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
 
-def test_noalloc_expect_z_matches_allocating_entry_point():
+def test_noalloc_expect_z_matches_allocating_entry_point_and_oracle():
     import torch
     assert torch.cuda.is_available()
     import paper_2212_14201_gb300 as q
     q.build()
     lib = q._lib.lib()
     stream = torch.cuda.current_stream()
-    for n, seed in ((14, 1), (20, 2)):
+    import oracle as orc
+    orc.build()
+    # a small n right after a larger one: fewer CTAs run over partials that the
+    # larger call left in the shared array
+    for n, seed in ((14, 1), (20, 2), (9, 3)):
         g = w.random_circuit(n, 150, seed, two_qubit_prob=0.4)
         h = q.qs_alloc(n, stream)
         try:
@@ -40,7 +44,11 @@ def test_noalloc_expect_z_matches_allocating_entry_point():
                                          ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, q.qs_last_error()
         torch.cuda.synchronize()
-        assert float(np.max(np.abs(out.cpu().numpy() - want))) < TOL
+        got = out.cpu().numpy()
+        assert float(np.max(np.abs(got - want))) < TOL
+        # the floating-point reduction it runs, against the CPU oracle on the same state
+        st = amps.cpu().numpy()
+        assert float(np.max(np.abs(got - orc.expect_z(st, n)))) < TOL
 
 
 def test_noalloc_rejects_sizes_outside_its_range():
