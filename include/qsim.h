@@ -274,12 +274,13 @@ int qs_set_phase_tables(int on);
  * complex products per quad and component (u = z0 + i z1 and v = z0 - i z1,
  * z_b the complex number formed along the first qubit: both rotations act on u
  * and v as multiplications), three on amplitude octets as four complex products
- * (the same basis change along each further qubit): 8 and 16 real products
- * where the rotations apart take 16 and 24.  A phase table op just before the
- * group runs inside its loop.  Results agree with the switch off within the
- * Q60 rounding.  For measurement: on = 1 (default) triples and pairs with
- * tables fused, 3 pairs only with tables fused, 2 pairs without table fusion,
- * 0 neither.  Always QS_OK. */
+ * (the same basis change along each further qubit), four on one component of 16
+ * amplitudes as eight: 8, 16 and 32 real products where the rotations apart take
+ * 16, 24 and 64.  A phase table op just before a pair or triple runs inside its
+ * loop.  Results agree with the switch off within the Q60 rounding.  For
+ * measurement: on = 1 (default) groups of four, three and two, 4 groups of three
+ * and two, 3 pairs only with tables fused, 2 pairs without table fusion, 0
+ * none.  Always QS_OK. */
 int qs_set_rotation_pairs(int on);
 
 

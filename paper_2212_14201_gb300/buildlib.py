@@ -42,7 +42,7 @@ def _stale(out: str, deps: list[str]) -> bool:
 def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
         os.path.join(HERE, os.pardir, "include", "qsim.h")]
     flags = NVCC_FLAGS + (extra or [])
     objs = []

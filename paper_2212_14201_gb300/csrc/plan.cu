@@ -1142,11 +1142,13 @@ static bool g_rotation_pairs = true;
 static bool g_fuse_tables = true;
 
 static bool g_rotation_triples = true;
+static bool g_rotation_quads = true;
 
 extern "C" int qs_set_rotation_pairs(int on) {
   g_rotation_pairs = on != 0;
   g_fuse_tables = on > 0 && on != 2;
-  g_rotation_triples = on == 1;
+  g_rotation_triples = on == 1 || on == 4;
+  g_rotation_quads = on == 1;
   return QS_OK;
 }
 
@@ -1167,7 +1169,8 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
   size_t per = 0;
   for (const PhaseTable& t : pt) per = std::max(per, t.t.size());
   // FP32 engine: one float2 per entry (table t at t * 2^m)
-  const size_t bytes = f32 ? pt.size() * per * sizeof(float2) : pt.size() * 3 * per * sizeof(QL);
+  // Q60 engine: per entry the limbs of c = Re T and d = Im T (16 bytes)
+  const size_t bytes = f32 ? pt.size() * per * sizeof(float2) : pt.size() * 2 * per * sizeof(QL);
   if (!s->tables_ev) QS_CUDA(cudaEventCreateWithFlags(&s->tables_ev, cudaEventDisableTiming));
   QS_CUDA(cudaEventSynchronize(s->tables_ev));
   if (s->tables_pinned_bytes < bytes) {
@@ -1195,14 +1198,10 @@ static int upload_tables(qs_state* s, const std::vector<PhaseTable>& pt, const Q
   }
   QL* host = (QL*)s->tables_pinned;
   for (size_t t = 0; !f32 && t < pt.size(); ++t) {
-    QL* re = host + t * 3 * per;
-    QL* im = re + per;
-    QL* nim = im + per;
+    QL* e = host + t * 2 * per;
     for (size_t j = 0; j < pt[t].t.size(); ++j) {
-      const QC c = qc_make_gauss(pt[t].t[j].re, pt[t].t[j].im);
-      re[j] = c.re;
-      im[j] = c.im;
-      nim[j] = c.nim;
+      e[2 * j] = q60_split(q60_from_double(pt[t].t[j].re));
+      e[2 * j + 1] = q60_split(q60_from_double(pt[t].t[j].im));
     }
   }
   QS_CUDA(cudaMemcpyAsync(s->tables, host, bytes, cudaMemcpyHostToDevice, s->stream));
@@ -1251,7 +1250,11 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
   return QS_OK;
 }
 
-static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed) {
+// io: TileArgs::io (Q60 engine only); *launched: whether a kernel ran (a pass
+// whose ops all cancel launches nothing).
+static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed,
+                         int io, bool* launched) {
+  *launched = false;
   const int n = s->n;
   TileArgs* g = new (std::nothrow) TileArgs;
   if (!g) return fail(QS_ERR_OOM, "host allocation failed");
@@ -1274,14 +1277,69 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   for (int b = 0; b < n; ++b)
     if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
   g->nops = 0;
+  g->io = (fixed && s->prec == 128) ? io : 0;
   g->tables = nullptr;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
   const bool pairs = ((fixed && s->prec == 128) || f32) && g_rotation_pairs;
   const bool triples = g_rotation_triples;
+  const bool quads = g_rotation_quads;
   auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
+  if (rc == QS_OK && pairs && quads && !f32) {
+    // Within each run of consecutive real rotations on distinct tile qubits (they
+    // commute), order them by (tile bit mod 3, tile bit): the groups of four then
+    // mix low and high bits, so a group's 16 amplitudes per lane pair never span
+    // only tile bits 4 and up of the lanes' addresses (shared-memory bank spread).
+    for (size_t i = 0; i < rops.size();) {
+      if (!in_tile_real(rops[i])) {
+        ++i;
+        continue;
+      }
+      size_t e = i;
+      uint32_t seen = 0;
+      while (e < rops.size() && in_tile_real(rops[e]) && !((seen >> local[rops[e].target]) & 1)) {
+        seen |= 1u << local[rops[e].target];
+        ++e;
+      }
+      if (e - i >= 5)
+        std::stable_sort(rops.begin() + i, rops.begin() + e, [&](const Op1& x, const Op1& y) {
+          const int bx = local[x.target], by = local[y.target];
+          return bx % 3 != by % 3 ? bx % 3 < by % 3 : bx < by;
+        });
+      i = e;
+    }
+  }
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
+    if (pairs && quads && !f32 && i + 3 < rops.size() && g->nops + 3 <= TILE_MAX_OPS && in_tile_real(op) &&
+        in_tile_real(rops[i + 1]) && in_tile_real(rops[i + 2]) && in_tile_real(rops[i + 3])) {
+      const uint32_t tm = (1u << local[op.target]) | (1u << local[rops[i + 1].target]) |
+                          (1u << local[rops[i + 2].target]) | (1u << local[rops[i + 3].target]);
+      if (__builtin_popcount(tm) == 4) {
+        // four real rotations on different tile qubits: one op on one component of
+        // 16 amplitudes at a time (three slots); a table before it stays its own op
+        TileOp* t = &g->ops[g->nops];
+        memset(t, 0, 3 * sizeof(TileOp));
+        t[0].kind = TOP_REAL4;
+        t[0].tb = (int8_t)local[op.target];
+        t[0].code0 = (int8_t)local[rops[i + 1].target];
+        t[0].code1 = -1;
+        t[1].kind = t[2].kind = TOP_CONT;
+        double mr[4][4];
+        for (int q = 0; q < 4; ++q)
+          for (int e = 0; e < 4; ++e) mr[q][e] = rops[i + q].m.m[e].re;
+        Q3 P[24];
+        int flags = 0;
+        q60_quad4_coef(mr[0], mr[1], mr[2], mr[3], P, &flags);
+        for (int e = 0; e < 24; ++e) reinterpret_cast<Q3*>(t[e / 8].q)[e % 8] = P[e];
+        t[0].lcmask = (uint32_t)flags | ((uint32_t)local[rops[i + 2].target] << 8) |
+                      ((uint32_t)local[rops[i + 3].target] << 16);
+        int_ops += N * 12.0;  // 32 real products per 16 values of a component: 12 limb products per amplitude
+        g->nops += 3;
+        i += 3;
+        continue;
+      }
+    }
     if (pairs && triples && !f32 && i + 2 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
         in_tile_real(rops[i + 2]) && rops[i + 1].target != op.target && rops[i + 2].target != op.target &&
         rops[i + 2].target != rops[i + 1].target) {
@@ -1379,7 +1437,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       to.ext_cmask = 0;
       to.code0 = to.code1 = U_GENERAL;
       if (f32) flops += N * 6.0;  // one complex product per amplitude
-      else int_ops += N * 9.0;    // one complex product (Gauss: 9 limb products) per amplitude
+      else int_ops += N * 12.0;   // one complex product (four real ones, 12 limb products) per amplitude
       ++g->nops;
       continue;
     }
@@ -1445,8 +1503,10 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     }
   }
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, f32);
-  if (rc == QS_OK && g->nops > 0) rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0,
-                                                   (int)ps.gates.size(), fixed);
+  if (rc == QS_OK && g->nops > 0) {
+    rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0, (int)ps.gates.size(), fixed);
+    *launched = rc == QS_OK;
+  }
   delete g;
   return rc;
 }
@@ -1455,8 +1515,18 @@ int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* pa
                   bool fixed) {
   if (plan->n != s->n || plan->ng != ng || plan->fingerprint != fingerprint(gates, ng))
     return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
-  for (const PlanPass& ps : plan->passes) {
+  // Between consecutive Q60 tile passes the buffer keeps the Q60 integers (the
+  // same 16 bytes per amplitude): no conversion to complex128 and back, and no
+  // rounding to double in between.  It is complex128 again when the call returns.
+  const bool q60 = fixed && s->prec == 128;
+  bool held = false;
+  for (size_t i = 0; i < plan->passes.size(); ++i) {
+    const PlanPass& ps = plan->passes[i];
     if (ps.kind == PASS_GATE) {
+      if (held) {
+        QS_TRY(launch_q60_release(s));
+        held = false;
+      }
       const qs_gate& g = gates[ps.gates[0]];
       int t;
       uint64_t cm;
@@ -1465,8 +1535,12 @@ int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* pa
       QS_TRY(gate_matrix(g, params, &m));
       QS_TRY(launch_op1(s, classify(t, cm, m), fixed));
     } else {
-      QS_TRY(run_tile_pass(s, ps, gates, params, fixed));
+      const bool next_tile = q60 && i + 1 < plan->passes.size() && plan->passes[i + 1].kind == PASS_TILE;
+      bool launched = false;
+      QS_TRY(run_tile_pass(s, ps, gates, params, fixed, (held ? 1 : 0) | (next_tile ? 2 : 0), &launched));
+      if (launched) held = next_tile;
     }
   }
+  if (held) QS_TRY(launch_q60_release(s));
   return QS_OK;
 }

@@ -200,6 +200,77 @@ __device__ __forceinline__ void q60_triple_octet(longlong2 (&v)[8], const Q3 (&P
 }
 #endif
 
+// Four real rotations on tile bits a, b, c, d, applied to ONE component of 16
+// amplitudes x[k] (k = bit(a) + 2 bit(b) + 4 bit(c) + 8 bit(d)) as eight complex
+// products.  The pairs along a are complex numbers z_j = x[2j] + i x[2j+1]
+// (j = bit(b) + 2 bit(c) + 4 bit(d)); the basis change along each of b, c, d maps
+// a pair (lo, hi) of complex values to (lo + i hi, lo - i hi), after which
+// R_d (x) R_c (x) R_b (x) R_a multiplies channel j by w_a times, for each of b, c,
+// d, its w or (when the channel's bit for it is set) conj(w) (C^(x)4 splits into
+// eight copies of C).  The inverse maps (A, B) back to (A + B, -i (A - B)); its
+// 1/8 is in the coefficients.  32 real products per 16 values of a component:
+// two per value for four rotations, where triples spend two per value on three.
+// Real and imaginary parts are independent under real rotations, so a thread
+// can take one component of 16 amplitudes.
+// Bounds: each channel is a signed sum of 8 of the 16 values, so by Cauchy-
+// Schwarz |Y| <= sqrt(8) * 1.25 < 3.54 (< 2^61.83 in Q60 units) for a state of
+// norm <= 1.25: the 31-bit split leaves |h| < 2^31; |P| <= 1/8 keeps the mid
+// accumulator of two products of two limb pairs below 2^63.  Each output sums 8
+// rounded products: at most 36 units of 2^-60 of error.
+// The 24 coefficients come in three runs of 8 (P0, P1, P2: they sit in three
+// consecutive op slots).
+QS_HD Q3 q3_at(int i, const Q3* P0, const Q3* P1, const Q3* P2) {
+  return i < 8 ? P0[i] : (i < 16 ? P1[i - 8] : P2[i - 16]);
+}
+QS_HD void q60_quad4_comp(int64_t (&x)[16], const Q3* P0, const Q3* P1, const Q3* P2) {
+  int64_t zr[8], zi[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    zr[j] = x[2 * j];
+    zi[j] = x[2 * j + 1];
+  }
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (!(j & bit)) {
+        const int64_t lr = zr[j], li = zi[j], hr = zr[j | bit], hi = zi[j | bit];
+        zr[j] = lr - hi;  // lo + i hi
+        zi[j] = li + hr;
+        zr[j | bit] = lr + hi;  // lo - i hi
+        zi[j | bit] = li - hr;
+      }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int32_t rh = (int32_t)(zr[k] >> 31), rl = (int32_t)(zr[k] & 0x7FFFFFFF);
+    const int32_t ih = (int32_t)(zi[k] >> 31), il = (int32_t)(zi[k] & 0x7FFFFFFF);
+    QAcc A = qacc_new(), B = qacc_new();
+    const Q3 pr = q3_at(3 * k, P0, P1, P2), pi = q3_at(3 * k + 1, P0, P1, P2), pn = q3_at(3 * k + 2, P0, P1, P2);
+    q3_add(A, pr, rh, rl);  // re = P.re Y.re - P.im Y.im
+    q3_add(A, pn, ih, il);
+    q3_add(B, pi, rh, rl);  // im = P.im Y.re + P.re Y.im
+    q3_add(B, pr, ih, il);
+    zr[k] = qacc_round(A);
+    zi[k] = qacc_round(B);
+  }
+#pragma unroll
+  for (int bit = 4; bit >= 1; bit >>= 1)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (!(j & bit)) {
+        const int64_t ar = zr[j], ai = zi[j], br = zr[j | bit], bi = zi[j | bit];
+        zr[j] = ar + br;  // lo = A + B
+        zi[j] = ai + bi;
+        zr[j | bit] = ai - bi;  // hi = -i (A - B)
+        zi[j | bit] = br - ar;
+      }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    x[2 * j] = zr[j];
+    x[2 * j + 1] = zi[j];
+  }
+}
+
 // Host: rotation angle (c, s) of a real orthogonal 2x2 (row-major) and whether it
 // is a reflection R Z.
 inline int q60_orth_angle(const double* m, double* c, double* s) {
@@ -232,6 +303,30 @@ inline void q60_triple_coef(const double* ra, const double* rb, const double* rc
     const double re = 0.25 * (abr * cc - abi * sck), im = 0.25 * (abi * cc + abr * sck);
     out[2 * k] = q60_split(q60_from_double(re));
     out[2 * k + 1] = q60_split(q60_from_double(im));
+  }
+}
+
+// Host: the eight coefficients of R_d (x) R_c (x) R_b (x) R_a for q60_quad4_comp
+// as Q3 limbs (channel k: re, im, -im at P[3k..3k+2]) and the reflection flags
+// (bit 0: a ... bit 3: d; a reflection's sign flip of its bit-1 half comes first).
+inline void q60_quad4_coef(const double* ra, const double* rb, const double* rc, const double* rd, Q3 P[24],
+                           int* flags) {
+  double c[4], s[4];
+  const double* r[4] = {ra, rb, rc, rd};
+  *flags = 0;
+  for (int q = 0; q < 4; ++q) *flags |= q60_orth_angle(r[q], &c[q], &s[q]) << q;
+  for (int k = 0; k < 8; ++k) {
+    double wr = c[0], wi = s[0];
+    for (int q = 1; q < 4; ++q) {
+      const double sq = ((k >> (q - 1)) & 1) ? -s[q] : s[q];
+      const double tr = wr * c[q] - wi * sq, ti = wi * c[q] + wr * sq;
+      wr = tr;
+      wi = ti;
+    }
+    const QL re = q60_split(q60_from_double(0.125 * wr)), im = q60_split(q60_from_double(0.125 * wi));
+    P[3 * k] = q3_of(re);
+    P[3 * k + 1] = q3_of(im);
+    P[3 * k + 2] = q3_neg(P[3 * k + 1]);
   }
 }
 

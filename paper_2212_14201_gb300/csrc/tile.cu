@@ -56,6 +56,22 @@ __device__ __forceinline__ uint32_t table_sign_mask(const TileArgs& g, int t, ui
 }
 
 // ---- FP64 engine -------------------------------------------------------------------
+// a * T (Q60), T = c + i d from a phase table entry {c.h, c.l, d.h, d.l} (16 bytes),
+// negated when neg: four limb products (direct form: fewer integer-pipe
+// instructions than the three-product Gauss form, and 16 instead of 24 bytes a
+// table entry from L2).
+__device__ __forceinline__ longlong2 table_mul(const int4 e, longlong2 a, bool neg) {
+  const int32_t m = neg ? -1 : 0;
+  const QL c{(e.x ^ m) - m, (e.y ^ m) - m}, d{(e.z ^ m) - m, (e.w ^ m) - m}, nd{-d.h, -d.l};
+  const QL ar = q60_split(a.x), ai = q60_split(a.y);
+  QAcc re = qacc_new(), im = qacc_new();
+  qacc_add(re, c, ar);
+  qacc_add(re, nd, ai);
+  qacc_add(im, d, ar);
+  qacc_add(im, c, ai);
+  return make_longlong2(qacc_round(re), qacc_round(im));
+}
+
 struct EngF64 {
   using T = double2;  // shared-memory element
   using G = double2;  // global element
@@ -97,10 +113,10 @@ struct EngQ60 {
   using G = double2;
   static constexpr int kMinBlocks = 3;  // 64 KiB tiles: three per SM; registers must not cut that
   static __device__ __forceinline__ T load(const double2& a) {
-    return make_longlong2(q60_from_double(a.x), q60_from_double(a.y));
+    return make_longlong2(q60_from_double_nb(a.x), q60_from_double_nb(a.y));
   }
   static __device__ __forceinline__ double2 store(const T& a) {
-    return make_double2(q60_to_double(a.x), q60_to_double(a.y));
+    return make_double2(q60_to_double_nb(a.x), q60_to_double_nb(a.y));
   }
   static __device__ __forceinline__ T unit(T a, int code) {
     switch (code) {
@@ -222,7 +238,7 @@ __device__ __forceinline__ void pair_loop(typename E::T* tile, uint32_t cnt, uin
 // shared-memory round trip, index arithmetic and barrier.
 template <int THREADS>
 __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tbb, const QL* m0,
-                                          int flags, const int2* tab, uint32_t S) {
+                                          int flags, const int4* tab, uint32_t S) {
   const uint32_t lo = min(ta, tbb), hi = max(ta, tbb);
   const uint32_t pa = tsw(ta), pb = tsw(tbb);
   uint32_t csw;
@@ -242,13 +258,7 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       v[c] = tile[pp[c]];
-      if (tab) {
-        const int2 ur = __ldg(tab + jj[c]), ui = __ldg(tab + TS + jj[c]), un = __ldg(tab + 2 * TS + jj[c]);
-        const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
-        int64_t vr, vi;
-        q60_gauss_mul(u, q60_split(v[c].x), q60_split(v[c].y), q60_split(v[c].x + v[c].y), &vr, &vi);
-        v[c] = (__popc(jj[c] & S) & 1) ? make_longlong2(-vr, -vi) : make_longlong2(vr, vi);
-      }
+      if (tab) v[c] = table_mul(__ldg(tab + jj[c]), v[c], __popc(jj[c] & S) & 1);
     }
     q60_pair_quad(v[0], v[1], v[2], v[3], m0, flags);
 #pragma unroll
@@ -262,7 +272,7 @@ __device__ __forceinline__ void quad_real(longlong2* tile, uint32_t TS, uint32_t
 // single rotation take 24.  With a phase table, as in quad_real.
 template <int THREADS>
 __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tb, uint32_t tc,
-                                           const Q3 (&P)[4][3], int flags, const int2* tab, uint32_t S) {
+                                           const Q3 (&P)[4][3], int flags, const int4* tab, uint32_t S) {
   const uint32_t p0 = min(ta, min(tb, tc)), p2 = max(ta, max(tb, tc));
   const uint32_t p1 = (ta | tb | tc) & ~(p0 | p2);
   const uint32_t pa = tsw(ta), pb = tsw(tb), pc = tsw(tc);
@@ -285,17 +295,58 @@ __device__ __forceinline__ void octet_real(longlong2* tile, uint32_t TS, uint32_
       jj[k] = j | ((k & 1) ? ta : 0u) | ((k & 2) ? tb : 0u) | ((k & 4) ? tc : 0u);
       pp[k] = pj ^ ((k & 1) ? pa : 0u) ^ ((k & 2) ? pb : 0u) ^ ((k & 4) ? pc : 0u);
       v[k] = tile[pp[k]];
-      if (tab) {
-        const int2 ur = __ldg(tab + jj[k]), ui = __ldg(tab + TS + jj[k]), un = __ldg(tab + 2 * TS + jj[k]);
-        const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
-        int64_t vr, vi;
-        q60_gauss_mul(u, q60_split(v[k].x), q60_split(v[k].y), q60_split(v[k].x + v[k].y), &vr, &vi);
-        v[k] = (__popc(jj[k] & S) & 1) ? make_longlong2(-vr, -vi) : make_longlong2(vr, vi);
-      }
+      if (tab) v[k] = table_mul(__ldg(tab + jj[k]), v[k], __popc(jj[k] & S) & 1);
     }
     q60_triple_octet(v, P, flags);
 #pragma unroll
     for (int k = 0; k < 8; ++k) tile[pp[k]] = v[k];
+  }
+}
+
+// Four real rotations on tile bits ta < ... (any order) on one component of 16
+// amplitudes per work item: item t takes group t >> 1 and component t & 1, so the
+// two lanes of a pair read the two halves of the same 16-byte amplitudes.
+template <int THREADS>
+__device__ __forceinline__ void quad4_real(longlong2* tile, uint32_t TS, uint32_t ta, uint32_t tb, uint32_t tc,
+                                           uint32_t td, const Q3* P0, const Q3* P1, const Q3* P2, int flags) {
+  const uint32_t all = ta | tb | tc | td;
+  uint32_t p[4], rest = all;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {  // the four bits in ascending order
+    p[e] = rest & (0u - rest);
+    rest ^= p[e];
+  }
+  const uint32_t pa = tsw(ta), pb = tsw(tb), pc = tsw(tc), pd = tsw(td);
+  const uint32_t grp0 = threadIdx.x >> 1;
+  uint32_t csw;
+  {
+    uint32_t j = grp0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) j = j + (j & ~(p[e] - 1));
+    csw = tsw_bits(j);
+  }
+  int64_t* comp = reinterpret_cast<int64_t*>(tile) + (threadIdx.x & 1);
+  const uint32_t cnt = TS >> 4;
+  for (uint32_t g = grp0; g < cnt; g += THREADS / 2) {
+    uint32_t j = g;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) j = j + (j & ~(p[e] - 1));  // insert zero bits at p[0] < ... < p[3]
+    const uint32_t pj = j ^ csw;
+    uint32_t pp[16];
+    int64_t x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      pp[k] = pj ^ ((k & 1) ? pa : 0u) ^ ((k & 2) ? pb : 0u) ^ ((k & 4) ? pc : 0u) ^ ((k & 8) ? pd : 0u);
+      x[k] = comp[2 * pp[k]];
+    }
+    if (flags) {
+#pragma unroll
+      for (int k = 1; k < 16; ++k)
+        if (__popc(k & flags) & 1) x[k] = -x[k];
+    }
+    q60_quad4_comp(x, P0, P1, P2);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) comp[2 * pp[k]] = x[k];
   }
 }
 
@@ -366,7 +417,17 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
     __syncthreads();  // offs ready / previous tile stored
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j ^ tsq] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
+    if constexpr (std::is_same<E, EngQ60>::value) {
+      if (g.io & 1) {
+        const longlong2* ai = reinterpret_cast<const longlong2*>(a);
+        for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j ^ tsq] = ai[base + offs[j >> L] + (j & lowmask)];
+      } else {
+        for (uint32_t j = threadIdx.x; j < TS; j += THREADS)
+          tile[j ^ tsq] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
+      }
+    } else {
+      for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j ^ tsq] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
+    }
     __syncthreads();
     for (int k = 0; k < g.nops; ++k) {
       const TileOp& op = g.ops[k];
@@ -400,25 +461,26 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
         if (op.kind == TOP_DTABLE) {
           // one table entry per amplitude, read through the read-only path (every
           // tile reads the same table: it stays in L2)
-          const int2* tre = reinterpret_cast<const int2*>(g.tables) + (size_t)lcm * 3 * TS;
-          const int2* tim = tre + TS;
-          const int2* tnim = tim + TS;
+          const int4* tab = reinterpret_cast<const int4*>(g.tables) + (size_t)lcm * TS;
           const uint32_t S = table_sign_mask(g, (int)lcm, base);
-#pragma unroll 4
-          for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
-            const int2 ur = __ldg(tre + j), ui = __ldg(tim + j), un = __ldg(tnim + j);
-            const QC u{{ur.x, ur.y}, {ui.x, ui.y}, {un.x, un.y}};
-            const longlong2 a = tile[j ^ tsq];
-            int64_t re, im;
-            q60_gauss_mul(u, q60_split(a.x), q60_split(a.y), q60_split(a.x + a.y), &re, &im);
-            tile[j ^ tsq] = (__popc(j & S) & 1) ? make_longlong2(-re, -im) : make_longlong2(re, im);
-          }
+#pragma unroll 8
+          for (uint32_t j = threadIdx.x; j < TS; j += THREADS)
+            tile[j ^ tsq] = table_mul(__ldg(tab + j), tile[j ^ tsq], __popc(j & S) & 1);
+          __syncthreads();
+          continue;
+        }
+        if (op.kind == TOP_REAL4) {
+          // 24 Q3 coefficients: 8 in q[] of this slot and of each of the next two
+          quad4_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, 1u << ((op.lcmask >> 8) & 31),
+                              1u << ((op.lcmask >> 16) & 31), reinterpret_cast<const Q3*>(op.q),
+                              reinterpret_cast<const Q3*>(g.ops[k + 1].q), reinterpret_cast<const Q3*>(g.ops[k + 2].q),
+                              (int)(op.lcmask & 15));
+          k += 2;  // the continuation slots
           __syncthreads();
           continue;
         }
         if (op.kind == TOP_REAL3) {
-          const int2* tab = op.code1 >= 0 ? reinterpret_cast<const int2*>(g.tables) + (size_t)op.code1 * 3 * TS
-                                          : nullptr;
+          const int4* tab = op.code1 >= 0 ? reinterpret_cast<const int4*>(g.tables) + (size_t)op.code1 * TS : nullptr;
           // 12 Q3 coefficients: 8 in this slot's q[] (96 bytes), 4 in the next slot's
           const Q3* pq0 = reinterpret_cast<const Q3*>(op.q);
           const Q3* pq1 = reinterpret_cast<const Q3*>(g.ops[k + 1].q);
@@ -436,8 +498,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
           continue;
         }
         if (op.kind == TOP_REAL2) {
-          const int2* tab = op.code1 >= 0 ? reinterpret_cast<const int2*>(g.tables) + (size_t)op.code1 * 3 * TS
-                                          : nullptr;
+          const int4* tab = op.code1 >= 0 ? reinterpret_cast<const int4*>(g.tables) + (size_t)op.code1 * TS : nullptr;
           if (tab)
             quad_real<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, reinterpret_cast<const QL*>(op.q),
                                (int)op.lcmask, tab, table_sign_mask(g, op.code1, base));
@@ -480,7 +541,23 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
       }
       __syncthreads();
     }
+    if constexpr (std::is_same<E, EngQ60>::value) {
+      if (g.io & 2) {
+        longlong2* ao = reinterpret_cast<longlong2*>(a);
+        for (uint32_t j = threadIdx.x; j < TS; j += THREADS) ao[base + offs[j >> L] + (j & lowmask)] = tile[j ^ tsq];
+        continue;
+      }
+    }
     for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[j ^ tsq]);
+  }
+}
+
+// In-place Q60 integer pairs -> complex128 (the same rounding as a tile pass's store).
+__global__ void k_q60_release(double2* __restrict__ a, size_t N) {
+  longlong2* v = reinterpret_cast<longlong2*>(a);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const longlong2 x = v[i];
+    a[i] = make_double2(q60_to_double_nb(x.x), q60_to_double_nb(x.y));
   }
 }
 
@@ -509,6 +586,14 @@ static int launch_engine(qs_state* s, const TileArgs& g) {
   const size_t smem = ((H * sizeof(uint64_t) + 15) & ~(size_t)15) + (sizeof(typename E::T) << g.m);
   if (g.m >= 13) return launch_engine_t<E, 512>(s, g, smem);
   return launch_engine_t<E, 256>(s, g, smem);
+}
+
+int launch_q60_release(qs_state* s) {
+  const size_t N = (size_t)1 << s->n;
+  const int blocks = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
+  KTimer kt(s, QS_K_OTHER, 0, 0, 0, 0, (double)N, 0.0);
+  k_q60_release<<<blocks, 256, 0, s->stream>>>(s->amps, N);
+  return launch_check("q60 release");
 }
 
 int launch_tile(qs_state* s, const TileArgs& g, double flops, double int_ops, int ngates, bool fixed) {

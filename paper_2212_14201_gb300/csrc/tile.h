@@ -42,6 +42,10 @@ enum TileOpKind : int8_t {
                    // four complex products (q60pair.cuh); the 12 Q3 coefficients (4 x re, im,
                    // -im): 8 in q[] of this slot, 4 in the next; reflection flags in
                    // lcmask & 7; code1 >= 0: phase table code1 applied first
+  TOP_REAL4 = 14,  // Q60 only: four real rotations on tile bits tb, code0, (lcmask >> 8) & 31 and
+                   // (lcmask >> 16) & 31, one amplitude component of 16 at a time, as eight
+                   // complex products (q60_quad4_comp); the 24 Q3 coefficients fill q[] of
+                   // this slot and the next two; reflection flags in lcmask & 15
 };
 
 struct TileOp {
@@ -65,12 +69,19 @@ struct TileArgs {
   int nout;          // qubits outside the tile
   int outpos[QS_MAX_QUBITS];  // their global positions (ascending)
   int nops;
-  const QL* tables;  // DTABLE ops: per table the Gauss-form parts re, im, nim, 2^m limb pairs each
+  // Q60 engine: bit 0, the buffer holds Q60 integers (int64 pairs) left by the
+  // previous tile pass instead of complex128; bit 1, store Q60 integers for the
+  // next tile pass.  0 for the other engines.
+  int io;
+  const QL* tables;  // DTABLE ops: per table 2^m entries, each the limb pairs of Re and Im (Q60)
   TileSigns signs[TILE_MAX_SIGNED_TABLES];  // sign terms of tables 0..31
   TileOp ops[TILE_MAX_OPS];
 };
 static_assert(sizeof(TileArgs) < 32000, "tile arguments must fit the kernel parameter space");
 
 int launch_tile(qs_state* s, const TileArgs& args, double flops, double int_ops, int ngates, bool fixed);
+// Converts a buffer of Q60 integer pairs (left by a tile pass with io bit 1) back
+// to complex128 in place.
+int launch_q60_release(qs_state* s);
 
 }  // namespace qs

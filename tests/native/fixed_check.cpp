@@ -39,6 +39,24 @@ int fc_triple_comp(const double* ra, const double* rb, const double* rc, long lo
   for (int k = 0; k < 8; ++k) x[k] = v[k];
   return flags;
 }
+// four real orthogonal 2x2 ops on one component of 16 amplitudes x[16] (Q60
+// integers, index bit(a) + 2 bit(b) + 4 bit(c) + 8 bit(d)) through the
+// eight-complex-product form; coefficients (re, im of channel k) into c[16]
+int fc_quad4_comp(const double* ra, const double* rb, const double* rc, const double* rd, long long* x,
+                  long long* c) {
+  qs::Q3 P[24];
+  int flags = 0;
+  qs::q60_quad4_coef(ra, rb, rc, rd, P, &flags);
+  for (int k = 0; k < 8; ++k) {
+    c[2 * k] = (long long)P[3 * k].h * (1ll << 30) + P[3 * k].l2 / 2;
+    c[2 * k + 1] = (long long)P[3 * k + 1].h * (1ll << 30) + P[3 * k + 1].l2 / 2;
+  }
+  int64_t v[16];
+  for (int k = 0; k < 16; ++k) v[k] = (__builtin_popcount(k & flags) & 1) ? -x[k] : x[k];
+  qs::q60_quad4_comp(v, P, P + 8, P + 16);
+  for (int k = 0; k < 16; ++k) x[k] = v[k];
+  return flags;
+}
 // two real orthogonal 2x2 ops (ra on quad bit a, rb on bit b; row-major) on one
 // component of a quad x[4] (Q60 integers, index bit(a) + 2 bit(b)), through the
 // two-complex-product form of the pair kernels

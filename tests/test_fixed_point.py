@@ -35,6 +35,8 @@ def fc():
     lib.fc_pair_coef.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc_triple_comp.restype = ctypes.c_int
     lib.fc_triple_comp.argtypes = [ctypes.c_void_p] * 5
+    lib.fc_quad4_comp.restype = ctypes.c_int
+    lib.fc_quad4_comp.argtypes = [ctypes.c_void_p] * 6
     lib.fc_pair_comp.restype = None
     lib.fc_pair_comp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc_dot2.restype = ctypes.c_longlong
@@ -308,3 +310,66 @@ def test_triple_as_four_complex_products(fc, flags):
         exact = form(y, Pq, lambda a, b: a * b, None)
         for k in range(8):
             assert abs(Fraction(int(out[k])) - exact[k]) <= 20, (k, float(Fraction(int(out[k])) - exact[k]))
+
+
+def _form4(y, P, mul):
+    """R_d (x) R_c (x) R_b (x) R_a on one component of 16 values through eight
+    complex products: pairs along a as complex numbers, the basis change
+    (lo, hi) -> (lo + i hi, lo - i hi) along b, c, d, channel k times P[k], and
+    the inverse (A, B) -> (A + B, -i (A - B)); values as (re, im) pairs."""
+    z = [(y[2 * j], y[2 * j + 1]) for j in range(8)]
+    for bit in (1, 2, 4):
+        for j in range(8):
+            if not j & bit:
+                (lr, li), (hr, hi) = z[j], z[j | bit]
+                z[j], z[j | bit] = (lr - hi, li + hr), (lr + hi, li - hr)
+    z = [(mul(P[k][0], z[k][0]) - mul(P[k][1], z[k][1]), mul(P[k][1], z[k][0]) + mul(P[k][0], z[k][1]))
+         for k in range(8)]
+    for bit in (4, 2, 1):
+        for j in range(8):
+            if not j & bit:
+                (ar, ai), (br, bi) = z[j], z[j | bit]
+                z[j], z[j | bit] = (ar + br, ai + bi), (ai - bi, br - ar)
+    out = []
+    for re, im in z:
+        out += [re, im]
+    return out
+
+
+@pytest.mark.parametrize("flags", [0, 1, 6, 9, 15])
+def test_quad4_as_eight_complex_products(fc, flags):
+    """Four rotations or reflections on one component of 16 amplitudes through the
+    eight-complex-product form: (1) the coefficients reproduce the 16x16 Kronecker
+    product of the double matrices within double rounding; (2) the limb arithmetic
+    equals the form evaluated exactly on the same Q60 integers within 36 units of
+    2^-60 (eight rounded products per output)."""
+    g = np.random.Generator(np.random.PCG64(70 + flags))
+    sg = [(-1 if (flags >> i) & 1 else 1) for i in range(4)]
+
+    def sgn(k):
+        return sg[0] ** (k & 1) * sg[1] ** ((k >> 1) & 1) * sg[2] ** ((k >> 2) & 1) * sg[3] ** ((k >> 3) & 1)
+    for _ in range(100):
+        rs = [_orth(g, (flags >> i) & 1) for i in range(4)]
+        v = g.normal(size=16)
+        v *= g.uniform(0, 1.25) / np.linalg.norm(v)
+        x = np.array([exact_q60(float(t)) for t in v], dtype=np.int64)
+        out = x.copy()
+        c = np.zeros(16, dtype=np.int64)
+        got_flags = fc.fc_quad4_comp(rs[0].ctypes.data, rs[1].ctypes.data, rs[2].ctypes.data, rs[3].ctypes.data,
+                                     out.ctypes.data, c.ctypes.data)
+        assert got_flags == flags
+        # (1) columns of the form against kron(rd, kron(rc, kron(rb, ra)))
+        K = np.kron(rs[3].reshape(2, 2), np.kron(rs[2].reshape(2, 2), np.kron(rs[1].reshape(2, 2),
+                                                                               rs[0].reshape(2, 2))))
+        P = [(c[2 * k] / 2.0 ** 60, c[2 * k + 1] / 2.0 ** 60) for k in range(8)]
+        for qi in range(16):
+            y = [0.0] * 16
+            y[qi] = float(sgn(qi))
+            col = _form4(y, P, lambda a, b: a * b)
+            assert np.max(np.abs(np.array(col) - K[:, qi])) < 1e-15, qi
+        # (2) limb arithmetic against the exact evaluation on the same integers
+        y = [Fraction(int(x[k])) * sgn(k) for k in range(16)]
+        Pq = [(Fraction(int(c[2 * k]), 1 << 60), Fraction(int(c[2 * k + 1]), 1 << 60)) for k in range(8)]
+        exact = _form4(y, Pq, lambda a, b: a * b)
+        for k in range(16):
+            assert abs(Fraction(int(out[k])) - exact[k]) <= 36, (k, float(Fraction(int(out[k])) - exact[k]))

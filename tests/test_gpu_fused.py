@@ -331,18 +331,19 @@ def test_phase_tables_survive_host_buffer_growth(q, orc):
 
 @pytest.mark.parametrize("n,kind", [(9, "brick"), (14, "brick"), (12, "rand"), (13, "hea")])
 def test_rotation_pairs_match_oracle(q, orc, n, kind):
-    """Q60 tile passes with groups of real rotations: triples on octets as four
-    complex products and pairs on quads as two (with and without the preceding
-    phase table fused into the group), against the oracle (1e-12) and with the
-    switch off; triples take no more limb products than pairs, and pairs fewer
-    than the rotations one at a time."""
+    """Q60 tile passes with groups of real rotations: four on one component of 16
+    amplitudes as eight complex products, triples on octets as four and pairs on
+    quads as two (with and without the preceding phase table fused into the
+    group), against the oracle (1e-12) and with the switch off; groups of four
+    take no more limb products than triples, triples no more than pairs, and
+    pairs fewer than the rotations one at a time."""
     g = {"brick": lambda: w.layered_u3_cz(n, 12, 4), "rand": lambda: w.random_circuit(n, 400, 12),
          "hea": lambda: w.hea_ansatz(n, 4)[0]}[kind]()
     params = w.uniform_angles(400, 5)
     ref = orc.as_complex(orc.run(n, g, params))
     work = {}
     try:
-        for on in (1, 3, 2, 0):
+        for on in (1, 4, 3, 2, 0):
             q.qs_set_rotation_pairs(on)
             p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
             h = q.qs_alloc(n)
@@ -359,4 +360,4 @@ def test_rotation_pairs_match_oracle(q, orc, n, kind):
             work[on] = sum(r["int_ops"] for r in recs if r["kind"] == q._lib.K_TILE)
     finally:
         q.qs_set_rotation_pairs(True)
-    assert work[1] <= work[3] == work[2] < work[0]
+    assert work[1] <= work[4] <= work[3] == work[2] < work[0]
