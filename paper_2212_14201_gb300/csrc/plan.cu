@@ -1285,7 +1285,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   const bool triples = g_rotation_triples;
   const bool quads = g_rotation_quads;
   auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
-  if (rc == QS_OK && pairs && quads && !f32) {
+  if (rc == QS_OK && pairs && quads) {
     // Within each run of consecutive real rotations on distinct tile qubits (they
     // commute), order them by (tile bit mod 3, tile bit): the groups of four then
     // mix low and high bits, so a group's 16 amplitudes per lane pair never span
@@ -1311,6 +1311,35 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   }
   for (size_t i = 0; rc == QS_OK && i < rops.size(); ++i) {
     const Op1& op = rops[i];
+    if (pairs && quads && f32 && i + 3 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
+        in_tile_real(rops[i + 2]) && in_tile_real(rops[i + 3])) {
+      const uint32_t tm = (1u << local[op.target]) | (1u << local[rops[i + 1].target]) |
+                          (1u << local[rops[i + 2].target]) | (1u << local[rops[i + 3].target]);
+      if (__builtin_popcount(tm) == 4) {
+        // FP32: four real rotations on 16 amplitudes in registers (one slot), a
+        // phase table just before them applied in the same loop
+        int tab = -1;
+        if (g_fuse_tables && i > 0 && rops[i - 1].cls == kTableMark && g->nops > 0 &&
+            g->ops[g->nops - 1].kind == TOP_DTABLE && g->ops[g->nops - 1].lcmask < 128) {
+          --g->nops;
+          tab = (int)g->ops[g->nops].lcmask;
+        }
+        TileOp& t0 = g->ops[g->nops];
+        memset(&t0, 0, sizeof t0);
+        t0.kind = TOP_REAL4;
+        t0.tb = (int8_t)local[op.target];
+        t0.code0 = (int8_t)local[rops[i + 1].target];
+        t0.code1 = (int8_t)tab;
+        t0.lcmask = ((uint32_t)local[rops[i + 2].target] << 8) | ((uint32_t)local[rops[i + 3].target] << 16);
+        float* f = reinterpret_cast<float*>(t0.q);
+        for (int q = 0; q < 4; ++q)
+          for (int e = 0; e < 4; ++e) f[4 * q + e] = (float)rops[i + q].m.m[e].re;
+        flops += N * 24.0;  // per rotation and amplitude: two components x (1 mul + 1 fma)
+        g->nops += 1;
+        i += 3;
+        continue;
+      }
+    }
     if (pairs && quads && !f32 && i + 3 < rops.size() && g->nops + 3 <= TILE_MAX_OPS && in_tile_real(op) &&
         in_tile_real(rops[i + 1]) && in_tile_real(rops[i + 2]) && in_tile_real(rops[i + 3])) {
       const uint32_t tm = (1u << local[op.target]) | (1u << local[rops[i + 1].target]) |

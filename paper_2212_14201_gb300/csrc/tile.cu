@@ -169,7 +169,7 @@ struct EngQ60 {
 struct EngF32 {
   using T = float2;
   using G = float2;
-  static constexpr int kMinBlocks = 5;  // 32 KiB tiles; five per SM leave the quad ops unspilled (5/6/7: 460/517/626 ms)
+  static constexpr int kMinBlocks = 4;  // 32 KiB tiles; four per SM leave the 16-amplitude register groups unspilled
   static __device__ __forceinline__ T load(const float2& a) { return a; }
   static __device__ __forceinline__ float2 store(const T& a) { return a; }
   static __device__ __forceinline__ float2 u(const TileOp& op, int e) { return op.f[e]; }
@@ -396,6 +396,84 @@ __device__ __forceinline__ void quad_real_f32(float2* tile, uint32_t TS, uint32_
   }
 }
 
+// FP32 engine: four real rotations (row-major 2x2 each, r[4q..4q+3] for bits a, b,
+// c, d) on groups of 16 amplitudes held in registers, one after another, after an
+// optional phase table: one shared-memory round trip for up to five ops.
+template <int THREADS>
+__device__ __forceinline__ void quad4_f32(float2* tile, uint32_t TS, uint32_t ta, uint32_t tb, uint32_t tc,
+                                          uint32_t td, const float* r, const float2* tab, uint32_t S) {
+  const uint32_t all = ta | tb | tc | td;
+  uint32_t p[4], rest = all;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {  // the four bits in ascending order
+    p[e] = rest & (0u - rest);
+    rest ^= p[e];
+  }
+  const uint32_t pa = tsw(ta), pb = tsw(tb), pc = tsw(tc), pd = tsw(td);
+  uint32_t csw;
+  {
+    uint32_t j = threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) j = j + (j & ~(p[e] - 1));
+    csw = tsw_bits(j);
+  }
+  const uint32_t cnt = TS >> 4;
+  for (uint32_t g = threadIdx.x; g < cnt; g += THREADS) {
+    uint32_t j = g;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) j = j + (j & ~(p[e] - 1));  // insert zero bits at p[0] < ... < p[3]
+    const uint32_t pj = j ^ csw;
+    auto slot = [&](int k) {
+      return pj ^ ((k & 1) ? pa : 0u) ^ ((k & 2) ? pb : 0u) ^ ((k & 4) ? pc : 0u) ^ ((k & 8) ? pd : 0u);
+    };
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      v[k] = tile[slot(k)];
+      if (tab) {
+        const uint32_t jk = j | ((k & 1) ? ta : 0u) | ((k & 2) ? tb : 0u) | ((k & 4) ? tc : 0u) | ((k & 8) ? td : 0u);
+        float2 u = __ldg(tab + jk);
+        if (__popc(jk & S) & 1) u = make_float2(-u.x, -u.y);
+        v[k] = make_float2(fmaf(u.x, v[k].x, -u.y * v[k].y), fmaf(u.x, v[k].y, u.y * v[k].x));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float m00 = r[4 * q], m01 = r[4 * q + 1], m10 = r[4 * q + 2], m11 = r[4 * q + 3];
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (!(k & (1 << q))) {
+          const float2 x0 = v[k], x1 = v[k | (1 << q)];
+          v[k] = make_float2(fmaf(m01, x1.x, m00 * x0.x), fmaf(m01, x1.y, m00 * x0.y));
+          v[k | (1 << q)] = make_float2(fmaf(m11, x1.x, m10 * x0.x), fmaf(m11, x1.y, m10 * x0.y));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) tile[slot(k)] = v[k];
+  }
+}
+
+// Loads a tile into shared memory with eight global loads in flight per thread
+// before their shared-memory stores (thread t takes j = t, t + THREADS, ...; the
+// swizzle tsq depends only on bits the stride keeps).
+template <int THREADS, class T, class S, class F>
+__device__ __forceinline__ void load_tile(T* tile, const S* src, uint64_t base, const uint64_t* offs, int L,
+                                          uint32_t lowmask, uint32_t TS, uint32_t tsq, F conv) {
+  constexpr uint32_t U = 8;
+  uint32_t j = threadIdx.x;
+  for (; j + (U - 1) * THREADS < TS; j += U * THREADS) {
+    S v[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t jj = j + u * THREADS;
+      v[u] = src[base + offs[jj >> L] + (jj & lowmask)];
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) tile[(j + u * THREADS) ^ tsq] = conv(v[u]);
+  }
+  for (; j < TS; j += THREADS) tile[j ^ tsq] = conv(src[base + offs[j >> L] + (j & lowmask)]);
+}
+
 template <class E, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
@@ -417,16 +495,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
     uint64_t base = 0;
     for (int b = 0; b < g.nout; ++b) base |= ((r >> b) & 1ull) << g.outpos[b];
     __syncthreads();  // offs ready / previous tile stored
+    auto conv = [](const typename E::G& v) { return E::load(v); };
     if constexpr (std::is_same<E, EngQ60>::value) {
-      if (g.io & 1) {
-        const longlong2* ai = reinterpret_cast<const longlong2*>(a);
-        for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j ^ tsq] = ai[base + offs[j >> L] + (j & lowmask)];
-      } else {
-        for (uint32_t j = threadIdx.x; j < TS; j += THREADS)
-          tile[j ^ tsq] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
-      }
+      if (g.io & 1)
+        load_tile<THREADS>(tile, reinterpret_cast<const longlong2*>(a), base, offs, L, lowmask, TS, tsq,
+                           [](const longlong2& v) { return v; });
+      else
+        load_tile<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq, conv);
     } else {
-      for (uint32_t j = threadIdx.x; j < TS; j += THREADS) tile[j ^ tsq] = E::load(a[base + offs[j >> L] + (j & lowmask)]);
+      load_tile<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq, conv);
     }
     __syncthreads();
     for (int k = 0; k < g.nops; ++k) {
@@ -437,12 +514,22 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
         if (op.kind == TOP_DTABLE) {
           const float2* tf = reinterpret_cast<const float2*>(g.tables) + (size_t)lcm * TS;
           const uint32_t S = table_sign_mask(g, (int)lcm, base);
+#pragma unroll 8
           for (uint32_t j = threadIdx.x; j < TS; j += THREADS) {
             float2 u = __ldg(tf + j);
             const float2 v = tile[j ^ tsq];
             if (__popc(j & S) & 1) u = make_float2(-u.x, -u.y);
             tile[j ^ tsq] = make_float2(fmaf(u.x, v.x, -u.y * v.y), fmaf(u.x, v.y, u.y * v.x));
           }
+          __syncthreads();
+          continue;
+        }
+        if (op.kind == TOP_REAL4) {
+          const float2* tab =
+              op.code1 >= 0 ? reinterpret_cast<const float2*>(g.tables) + (size_t)op.code1 * TS : nullptr;
+          quad4_f32<THREADS>(tile, TS, 1u << op.tb, 1u << op.code0, 1u << ((op.lcmask >> 8) & 31),
+                             1u << ((op.lcmask >> 16) & 31), reinterpret_cast<const float*>(op.q), tab,
+                             op.code1 >= 0 ? table_sign_mask(g, op.code1, base) : 0u);
           __syncthreads();
           continue;
         }

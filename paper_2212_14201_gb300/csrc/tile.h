@@ -42,10 +42,12 @@ enum TileOpKind : int8_t {
                    // four complex products (q60pair.cuh); the 12 Q3 coefficients (4 x re, im,
                    // -im): 8 in q[] of this slot, 4 in the next; reflection flags in
                    // lcmask & 7; code1 >= 0: phase table code1 applied first
-  TOP_REAL4 = 14,  // Q60 only: four real rotations on tile bits tb, code0, (lcmask >> 8) & 31 and
-                   // (lcmask >> 16) & 31, one amplitude component of 16 at a time, as eight
-                   // complex products (q60_quad4_comp); the 24 Q3 coefficients fill q[] of
-                   // this slot and the next two; reflection flags in lcmask & 15
+  TOP_REAL4 = 14,  // four real rotations on tile bits tb, code0, (lcmask >> 8) & 31 and
+                   // (lcmask >> 16) & 31.  Q60: one amplitude component of 16 at a time, as
+                   // eight complex products (q60_quad4_comp); the 24 Q3 coefficients fill q[]
+                   // of this slot and the next two; reflection flags in lcmask & 15.  FP32:
+                   // 16 amplitudes in registers, the four row-major matrices as 16 floats in
+                   // q[] of this one slot; code1 >= 0: phase table code1 applied first
 };
 
 struct TileOp {
