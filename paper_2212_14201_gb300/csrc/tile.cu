@@ -474,6 +474,25 @@ __device__ __forceinline__ void load_tile(T* tile, const S* src, uint64_t base, 
   for (; j < TS; j += THREADS) tile[j ^ tsq] = conv(src[base + offs[j >> L] + (j & lowmask)]);
 }
 
+// Stores a tile the same way, eight shared-memory reads before their global stores.
+template <int THREADS, class T, class D, class F>
+__device__ __forceinline__ void store_tile(const T* tile, D* dst, uint64_t base, const uint64_t* offs, int L,
+                                           uint32_t lowmask, uint32_t TS, uint32_t tsq, F conv) {
+  constexpr uint32_t U = 8;
+  uint32_t j = threadIdx.x;
+  for (; j + (U - 1) * THREADS < TS; j += U * THREADS) {
+    T v[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) v[u] = tile[(j + u * THREADS) ^ tsq];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t jj = j + u * THREADS;
+      dst[base + offs[jj >> L] + (jj & lowmask)] = conv(v[u]);
+    }
+  }
+  for (; j < TS; j += THREADS) dst[base + offs[j >> L] + (j & lowmask)] = conv(tile[j ^ tsq]);
+}
+
 template <class E, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k_tile(typename E::G* __restrict__ a, const __grid_constant__ TileArgs g) {
   using T = typename E::T;
@@ -630,12 +649,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
     }
     if constexpr (std::is_same<E, EngQ60>::value) {
       if (g.io & 2) {
-        longlong2* ao = reinterpret_cast<longlong2*>(a);
-        for (uint32_t j = threadIdx.x; j < TS; j += THREADS) ao[base + offs[j >> L] + (j & lowmask)] = tile[j ^ tsq];
+        store_tile<THREADS>(tile, reinterpret_cast<longlong2*>(a), base, offs, L, lowmask, TS, tsq,
+                            [](const longlong2& v) { return v; });
         continue;
       }
     }
-    for (uint32_t j = threadIdx.x; j < TS; j += THREADS) a[base + offs[j >> L] + (j & lowmask)] = E::store(tile[j ^ tsq]);
+    store_tile<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq, [](const T& v) { return E::store(v); });
   }
 }
 
