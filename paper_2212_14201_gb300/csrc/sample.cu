@@ -20,6 +20,7 @@
 // same additions in the same order as a scan from the block's start).
 #include <algorithm>
 
+#include "ieee_sq.h"
 #include "internal.h"
 
 namespace qs {
@@ -38,14 +39,35 @@ __global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, i
     double S = 0.0;
     long long last = -1;
     for (int64_t j = 0; j < L; j += 4) {
-      double2 v0 = ld_amp(p, j), v1 = ld_amp(p, j + 1 < L ? j + 1 : j), v2 = ld_amp(p, j + 2 < L ? j + 2 : j),
-              v3 = ld_amp(p, j + 3 < L ? j + 3 : j);
-      double q0 = p_exact(v0);
-      S = __dadd_rn(S, q0);
-      if (q0 > 0.0) last = b * L + j;
-      if (j + 1 < L) { double q = p_exact(v1); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 1; }
-      if (j + 2 < L) { double q = p_exact(v2); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 2; }
-      if (j + 3 < L) { double q = p_exact(v3); S = __dadd_rn(S, q); if (q > 0.0) last = b * L + j + 3; }
+      const double2 v[4] = {ld_amp(p, j), ld_amp(p, j + 1 < L ? j + 1 : j), ld_amp(p, j + 2 < L ? j + 2 : j),
+                            ld_amp(p, j + 3 < L ? j + 3 : j)};
+      // the squares on the integer pipes (bit-identical to the FP64 products) when
+      // every component of the four is in range; else, for the whole warp, on the
+      // FP64 pipe (one vote, so the fallback is a real branch)
+      double sr[4], si[4];
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        bool o1, o2;
+        sr[k] = sq_rn_int(v[k].x, &o1);
+        si[k] = sq_rn_int(v[k].y, &o2);
+        ok = ok && o1 && o2;
+      }
+      if (!__all_sync(__activemask(), ok)) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          sr[k] = __dmul_rn(v[k].x, v[k].x);
+          si[k] = __dmul_rn(v[k].y, v[k].y);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k == 0 || j + k < L) {
+          const double q = __dadd_rn(sr[k], si[k]);
+          S = __dadd_rn(S, q);
+          if (q_bits(q) != 0) last = b * L + j + k;  // q >= +0: a nonzero bit pattern is q > 0
+        }
+      }
       if (K >= 4 && ((j + 4) & (K - 1)) == 0 && j + 4 < L) cp[b * M + (j + 4) / K - 1] = S;
     }
     T[b] = S;

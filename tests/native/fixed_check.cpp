@@ -1,6 +1,7 @@
 // Host-side harness for the Q60 helpers of the CUDA library (compiled by the
 // test suite with g++; exercises the same inline functions the kernels use).
 #include "fixed.h"
+#include "ieee_sq.h"
 #include "q60pair.cuh"
 
 extern "C" {
@@ -109,4 +110,12 @@ long long fc_dot4(const long long* u, const long long* a) {
   for (int i = 0; i < 4; ++i) qs::qacc_add(acc, qs::q60_split(u[i]), qs::q60_split(a[i]));
   return (long long)qs::qacc_result(acc);
 }
+}
+
+// fl(x * x) from integer operations (the sampler's squares); *ok as the helper sets it
+extern "C" double fc_sq_rn(double x, int* ok) {
+  bool o = false;
+  const double r = qs::sq_rn_int(x, &o);
+  *ok = o ? 1 : 0;
+  return r;
 }

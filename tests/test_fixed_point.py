@@ -37,6 +37,8 @@ def fc():
     lib.fc_triple_comp.argtypes = [ctypes.c_void_p] * 5
     lib.fc_quad4_comp.restype = ctypes.c_int
     lib.fc_quad4_comp.argtypes = [ctypes.c_void_p] * 6
+    lib.fc_sq_rn.restype = ctypes.c_double
+    lib.fc_sq_rn.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
     lib.fc_pair_comp.restype = None
     lib.fc_pair_comp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc_dot2.restype = ctypes.c_longlong
@@ -373,3 +375,38 @@ def test_quad4_as_eight_complex_products(fc, flags):
         exact = _form4(y, Pq, lambda a, b: a * b)
         for k in range(16):
             assert abs(Fraction(int(out[k])) - exact[k]) <= 36, (k, float(Fraction(int(out[k])) - exact[k]))
+
+
+def test_integer_square_is_ieee_multiplication(fc):
+    """The sampler's squares from integer operations equal IEEE 754 binary64
+    multiplication x * x (round to nearest, ties to even) bit for bit: random
+    significands over the whole valid exponent range, both signs, zero, the range
+    ends, products just below and at a power of two, and exact ties (a significand
+    of 27 significant bits whose square has a set round bit and no sticky bits)."""
+    g = np.random.Generator(np.random.PCG64(91))
+    xs = [0.0, -0.0, 1.0, -1.0, 2.0 ** -511, 2.0 ** 511 * (1 - 2.0 ** -53), 1.25, 0.7071067811865476,
+          np.nextafter(np.sqrt(2.0), 0.0), np.sqrt(2.0), np.nextafter(1.0, 2.0), np.nextafter(2.0, 0.0)]
+    xs += list(g.uniform(-1.5, 1.5, size=20000))
+    xs += list(g.uniform(1.0, 2.0, size=20000) * 2.0 ** g.integers(-511, 511, size=20000).astype(np.float64))
+    xs += list(2.0 ** -15 * g.normal(size=20000))
+    ties = 0
+    for k in range(1, 4000, 2):                       # odd 27-bit significands above 2^26.5
+        m = (1 << 27) - k
+        x = float(m) * 2.0 ** -26 * (1.0 if k % 3 else 2.0 ** -200)
+        xs.append(x)
+        p = m * m                                     # exact square
+        top = p.bit_length() - 1
+        sh = top - 52
+        if sh > 0 and (p >> (sh - 1)) & 1 and p & ((1 << (sh - 1)) - 1) == 0:
+            ties += 1
+    assert ties > 100
+    ok = ctypes.c_int()
+    for x in xs:
+        x = float(x)
+        got = fc.fc_sq_rn(x, ctypes.byref(ok))
+        assert ok.value == 1, x
+        want = np.float64(x) * np.float64(x)
+        assert np.float64(got).view(np.uint64) == want.view(np.uint64), (x, got, want)
+    for x in (2.0 ** -512, 2.0 ** -600, 5e-324, 2.0 ** 512, float("inf")):
+        fc.fc_sq_rn(x, ctypes.byref(ok))
+        assert ok.value == 0, x

@@ -361,3 +361,35 @@ def test_rotation_pairs_match_oracle(q, orc, n, kind):
     finally:
         q.qs_set_rotation_pairs(True)
     assert work[1] <= work[4] <= work[3] == work[2] < work[0]
+
+
+def test_q60_buffer_between_tile_and_gate_passes(q, orc):
+    """Consecutive Q60 tile passes keep Q60 integers in the state buffer; a
+    per-gate pass after a tile pass, and the end of the call, find complex128
+    again.  Plans of 4-qubit tiles on random circuits mix the two pass kinds
+    (tile, gate, tile, ... and a trailing run of gate passes); each is checked
+    to contain such a pattern and then against the oracle."""
+    n = 14
+    seen = set()
+    for seed in range(5):
+        g = w.random_circuit(n, 120, seed, two_qubit_prob=0.4)
+        p = q.qs_plan_create_variant(n, g, 4, 0)
+        kinds = "".join(str(k) for k, _, _ in q.qs_plan_passes(p))
+        if "101" in kinds:
+            seen.add("tile-gate-tile")
+        if "110" in kinds:
+            seen.add("tiles then gate")
+        if kinds.endswith("1"):
+            seen.add("ends on a tile pass")
+        h = q.qs_alloc(n)
+        try:
+            q.qs_set_arith(h, q.ARITH_FIXED)
+            q.qs_apply(h, g, None, p)
+            psi = q.qs_get_state(h)
+            # the buffer itself (not a converted copy) holds complex128 after the call
+            assert abs(float(np.sum(np.abs(psi) ** 2)) - 1.0) < 1e-12
+        finally:
+            q.qs_free(h)
+            q.qs_plan_free(p)
+        assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL, (seed, kinds)
+    assert {"tile-gate-tile", "tiles then gate", "ends on a tile pass"} <= seen, seen
