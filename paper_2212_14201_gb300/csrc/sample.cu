@@ -41,29 +41,28 @@ __global__ void k_block_totals(const A* __restrict__ a, int64_t nb, int64_t L, i
     for (int64_t j = 0; j < L; j += 4) {
       const double2 v[4] = {ld_amp(p, j), ld_amp(p, j + 1 < L ? j + 1 : j), ld_amp(p, j + 2 < L ? j + 2 : j),
                             ld_amp(p, j + 3 < L ? j + 3 : j)};
-      // the squares on the integer pipes (bit-identical to the FP64 products) when
-      // every component of the four is in range; else, for the whole warp, on the
-      // FP64 pipe (one vote, so the fallback is a real branch)
-      double sr[4], si[4];
+      // p = fl(fl(re^2) + fl(im^2)) on the integer pipes (bit-identical to the FP64
+      // operations) when every component of the four is in range; else, for the
+      // whole warp, on the FP64 pipe (one vote, so the fallback is a real branch)
+      double pq[4];
       bool ok = true;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        bool o1, o2;
-        sr[k] = sq_rn_int(v[k].x, &o1);
-        si[k] = sq_rn_int(v[k].y, &o2);
-        ok = ok && o1 && o2;
+        bool o1, o2, o3 = true;
+        const double sr = sq_rn_int(v[k].x, &o1), si = sq_rn_int(v[k].y, &o2);
+        // the sum on the integer pipes for half of the amplitudes, on the FP64 pipe
+        // for the other half: the two pipes then finish together
+        pq[k] = (k & 1) ? __dadd_rn(sr, si) : add_rn_pos_int(sr, si, &o3);
+        ok = ok && o1 && o2 && o3;
       }
       if (!__all_sync(__activemask(), ok)) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          sr[k] = __dmul_rn(v[k].x, v[k].x);
-          si[k] = __dmul_rn(v[k].y, v[k].y);
-        }
+        for (int k = 0; k < 4; ++k) pq[k] = p_exact(v[k]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (k == 0 || j + k < L) {
-          const double q = __dadd_rn(sr[k], si[k]);
+          const double q = pq[k];
           S = __dadd_rn(S, q);
           if (q_bits(q) != 0) last = b * L + j + k;  // q >= +0: a nonzero bit pattern is q > 0
         }

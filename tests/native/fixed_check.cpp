@@ -119,3 +119,10 @@ extern "C" double fc_sq_rn(double x, int* ok) {
   *ok = o ? 1 : 0;
   return r;
 }
+// fl(a + b) for a, b >= 0 from integer operations (the sampler's p = re^2 + im^2)
+extern "C" double fc_add_rn_pos(double a, double b, int* ok) {
+  bool o = false;
+  const double r = qs::add_rn_pos_int(a, b, &o);
+  *ok = o ? 1 : 0;
+  return r;
+}

@@ -37,6 +37,8 @@ def fc():
     lib.fc_triple_comp.argtypes = [ctypes.c_void_p] * 5
     lib.fc_quad4_comp.restype = ctypes.c_int
     lib.fc_quad4_comp.argtypes = [ctypes.c_void_p] * 6
+    lib.fc_add_rn_pos.restype = ctypes.c_double
+    lib.fc_add_rn_pos.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
     lib.fc_sq_rn.restype = ctypes.c_double
     lib.fc_sq_rn.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
     lib.fc_pair_comp.restype = None
@@ -410,3 +412,35 @@ def test_integer_square_is_ieee_multiplication(fc):
     for x in (2.0 ** -512, 2.0 ** -600, 5e-324, 2.0 ** 512, float("inf")):
         fc.fc_sq_rn(x, ctypes.byref(ok))
         assert ok.value == 0, x
+
+
+def test_integer_sum_is_ieee_addition(fc):
+    """fl(a + b) of non-negative doubles from integer operations equals IEEE 754
+    binary64 addition bit for bit: exponent differences 0..70 in both orders,
+    zeros, exact ties below an even and an odd significand, carries into the next
+    binade, and squares of amplitudes as the sampler forms them."""
+    g = np.random.Generator(np.random.PCG64(92))
+    pairs = [(0.0, 0.0), (0.0, 1.5), (2.0 ** -52, 0.0), (1.0, 2.0 ** -53), (1.0 + 2.0 ** -52, 2.0 ** -53),
+             (1.0, 3 * 2.0 ** -53), (np.nextafter(2.0, 0.0), 2.0 ** -53), (np.nextafter(2.0, 0.0), 2.0 ** -52),
+             (1.0, 1.0), (1.5, 1.5), (2.0 ** 1000, 2.0 ** 1000), (1.0, 2.0 ** -1000),
+             (1.0, 2.0 ** -53 * (1 + 2.0 ** -52)), (1.0 + 2.0 ** -52, 2.0 ** -53 * (1 + 2.0 ** -52)),
+             (1.0, 2.0 ** -53 * (1 - 2.0 ** -53))]  # half an ulp plus / minus a sticky bit
+    for d in range(0, 71):
+        a = g.uniform(1.0, 2.0, size=300) * 2.0 ** g.integers(-300, 300, size=300)
+        b = g.uniform(1.0, 2.0, size=300) * a * 2.0 ** -d
+        pairs += list(zip(a, b)) + list(zip(b, a))
+        # ties: b exactly half an ulp of a (times an odd integer below 2^10)
+        for k in (1, 3, 5, 1023):
+            pairs.append((a[0], k * np.spacing(a[0]) / 2.0 ** min(d, 10)))
+    v = 2.0 ** -15 * g.normal(size=(20000, 2))
+    pairs += [(x * x, y * y) for x, y in v]
+    ok = ctypes.c_int()
+    for a, b in pairs:
+        a, b = float(a), float(b)
+        got = fc.fc_add_rn_pos(a, b, ctypes.byref(ok))
+        assert ok.value == 1, (a, b)
+        want = np.float64(a) + np.float64(b)
+        assert np.float64(got).view(np.uint64) == want.view(np.uint64), (a, b, got, want)
+    for a, b in ((-1.0, 1.0), (5e-324, 1.0), (float("inf"), 1.0), (2.0 ** 1023, 1.0)):
+        fc.fc_add_rn_pos(a, b, ctypes.byref(ok))
+        assert ok.value == 0, (a, b)
