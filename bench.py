@@ -598,6 +598,31 @@ def bench_learned_plan(q, torch, stream):
                 q.qs_plan_free(p)
     finally:
         q.qs_free(h)
+    # a held-out n=30 random circuit (600 gates, 40 % two-qubit, seed 302): best of two applies per plan
+    try:
+        n2 = 30
+        g2 = w.random_circuit(n2, 600, 302, two_qubit_prob=0.4)
+        h2 = q.qs_alloc(n2, stream)
+        held = {"n": n2, "gates": len(g2), "seed": 302}
+        try:
+            for name, p in (("greedy", q.qs_plan_create(n2, g2, q.PLAN_GREEDY, 5)),
+                            ("learned", q.qs_plan_create_learned(n2, g2, model))):
+                best = 1e30
+                for _ in range(3):
+                    q.qs_set_zero(h2)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    q.qs_apply(h2, g2, None, p)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                held[name] = {"ms": best, "passes": q.qs_plan_get_stats(p)["n_passes"]}
+                q.qs_plan_free(p)
+            held["learned_gain_vs_greedy"] = held["greedy"]["ms"] / held["learned"]["ms"]
+        finally:
+            q.qs_free(h2)
+        out["held_out_n30"] = held
+    finally:
         q.qs_mlp_free(model)
     return out
 

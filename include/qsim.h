@@ -355,27 +355,56 @@ int qs_mlp_train(qs_mlp* m, const double* x, const double* t, size_t B, int epoc
  * (general, real, general diagonal, unit factors), controlled gates, diagonal
  * gates with the target outside the tile, distinct non-diagonal targets, gates
  * that start a run on their target (the ops left after aggregation), controlled
- * non-diagonal gates, and log2(1 + gates). */
-#define QS_PASS_FEATURES 14
+ * non-diagonal gates, log2(1 + gates), and for a tile pass the kernel ops of
+ * qs_plan_pass_kernel_ops (limb products per amplitude, phase tables, groups of
+ * four, three and two real rotations, single rotations, general ops, phase and
+ * diagonal ops, anti-diagonal ops, per-tile scalars, shared-memory sweeps).
+ * Parametrised records are featurised with generic angles. */
+#define QS_PASS_FEATURES 25
 int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out);
+
+/* Kernel ops of one pass of a plan as the Q60 tile engine would run it on a
+ * complex128 state (host only, nothing launched; `params` as for qs_apply):
+ * counts[k] (QS_KOP_KINDS entries) = ops of kind k: 1 one-qubit phase, 2
+ * diagonal, 3 anti-diagonal, 4 real, 5 general 2x2, 9 diagonal on a qubit outside
+ * the tile (a per-tile scalar), 10 phase tables (those fused into a rotation
+ * group included), 11/13/14 groups of two/three/four real rotations; counts[0]
+ * = the phase tables fused into a rotation group (no sweep of their own);
+ * *int_ops_per_amp = the pass's limb products per amplitude of the state.  A
+ * pass of plain per-gate kernels reports zeros.  Errors: INVALID_ARG. */
+#define QS_KOP_KINDS 15
+int qs_plan_pass_kernel_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng, const double* params,
+                            int64_t* counts, double* int_ops_per_amp);
 
 /* Greedy plan with an explicit tile width (4..13) and pass construction:
  * strategy 0 takes the targets of the remaining gates in program order (as
  * qs_plan_create_tiled); strategy 1 starts each pass from the first runnable
- * gate's target and the most frequent targets among the next runnable gates.
- * (The cost model's training passes.)  Errors: INVALID_ARG. */
+ * gate's target and the most frequent targets among the next runnable gates;
+ * strategy 2 (lookahead) takes the strategy-0 pass or a variant of it kept off
+ * one of the qubits the strategy-0 scan added, whichever absorbs the most gates
+ * together with the strategy-0 pass after it.  (The cost model's training
+ * passes.)  Errors: INVALID_ARG. */
 int qs_plan_create_variant(int n, const qs_gate* gates, size_t ng, int tile_qubits, int strategy, qs_plan** out);
 
 /* Learned plan: the model chooses the groupings.  Pass by pass it scores
- * candidate tile passes over the remaining gates (widths 11 and 12; both
- * strategies of qs_plan_create_variant), each as one tile pass and as plain
- * per-gate kernels (exp of the predicted log ms), and takes the candidate with
- * the least predicted time per unit of work (the gates' touched fractions of the
- * state), in the cheaper form.  The greedy plan is the fallback and the judge:
- * unless the model predicts the learned plan faster by more than 5 %, the
- * greedy passes are kept (stats.learned_fallback = 1).  est_seconds is the model's prediction.  The
+ * candidate tile passes over the remaining gates (widths 11 and 12; strategies
+ * 0 and 1 of qs_plan_create_variant and every variant of strategy 2), each as
+ * one tile pass and as plain per-gate kernels (exp of the predicted log ms),
+ * together with the strategy-0 pass that would follow it, and takes the
+ * candidate with the least predicted time per unit of work over the two passes
+ * (the gates' touched fractions of the state), in the cheaper form.  The greedy
+ * plan is the fallback and the judge: unless the model predicts the learned
+ * plan faster by more than 5 %, the greedy passes are kept
+ * (stats.learned_fallback = 1).  est_seconds is the model's prediction.  The
  * model needs QS_PASS_FEATURES inputs; its forward kernel runs on the GPU. */
 int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs_mlp* model, qs_plan** out);
+
+/* The same planner with a caller's cost model: score(ctx, x, B, y) writes the
+ * predicted log(milliseconds) y[s] of the B passes whose features are the rows
+ * x[s*QS_PASS_FEATURES ..] (host arrays, valid during the callback) and returns
+ * 0, or non-zero to abandon the plan (INVALID_ARG).  Runs on the host only. */
+typedef int (*qs_pass_scorer)(void* ctx, const double* x, size_t B, double* y);
+int qs_plan_create_scored(int n, const qs_gate* gates, size_t ng, qs_pass_scorer score, void* ctx, qs_plan** out);
 
 /* ---- reductions (prob_run_list / prob_run_dict, expectation tools) ------------- */
 

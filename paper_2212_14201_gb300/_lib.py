@@ -119,6 +119,8 @@ SIGNATURES = {
     "qs_mlp_train": (I32, [P, P, P, SZ, I32, DBL, ctypes.POINTER(DBL)]),
     "qs_plan_features": (I32, [P, P, SZ, P]),
     "qs_plan_create_learned": (I32, [I32, P, SZ, P, PP]),
+    "qs_plan_create_scored": (I32, [I32, P, SZ, P, P, PP]),
+    "qs_plan_pass_kernel_ops": (I32, [P, SZ, P, SZ, P, P, ctypes.POINTER(DBL)]),
     "qs_batch_create": (I32, [SZ, P, P, P, P, P, P, PP]),
     "qs_batch_run": (I32, [P, P, P, P, I32]),
     "qs_batch_last_ms": (I32, [P, ctypes.POINTER(DBL)]),
@@ -552,7 +554,7 @@ def qs_launch_count() -> int:
     return int(lib().qs_launch_count())
 
 
-PASS_FEATURES = 14
+PASS_FEATURES = 25
 
 
 def qs_mlp_create(n_in: int, n_hidden: int, weights=None, seed: int = 0) -> int:
@@ -620,6 +622,44 @@ def qs_plan_create_learned(n: int, gates, model: int) -> int:
     g = as_gates(gates)
     h = ctypes.c_void_p()
     _chk(lib().qs_plan_create_learned(n, g.ctypes.data if len(g) else None, len(g), model, ctypes.byref(h)))
+    return h.value
+
+
+KOP_KINDS = 15
+
+
+def qs_plan_pass_kernel_ops(p: int, i: int, gates, params=None):
+    """(counts by kernel op kind, limb products per amplitude) of pass i."""
+    g = as_gates(gates)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    counts = np.zeros(KOP_KINDS, dtype=np.int64)
+    ipa = ctypes.c_double()
+    _chk(lib().qs_plan_pass_kernel_ops(p, i, g.ctypes.data if len(g) else None, len(g),
+                                       None if pr is None else pr.ctypes.data, counts.ctypes.data, ctypes.byref(ipa)))
+    return counts, ipa.value
+
+
+PASS_SCORER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                               ctypes.POINTER(ctypes.c_double))
+
+
+def qs_plan_create_scored(n: int, gates, score) -> int:
+    """Learned-planner groupings with a host cost model: score(x) maps a
+    (B, PASS_FEATURES) array of pass features to B predicted log(ms)."""
+    g = as_gates(gates)
+
+    def cb(_ctx, x, B, y):
+        try:
+            xs = np.ctypeslib.as_array(x, shape=(B * PASS_FEATURES,)).reshape(B, PASS_FEATURES).copy()
+            np.ctypeslib.as_array(y, shape=(B,))[:] = np.asarray(score(xs), dtype=np.float64).reshape(B)
+            return 0
+        except Exception:
+            return 1
+
+    fn = PASS_SCORER(cb)
+    h = ctypes.c_void_p()
+    _chk(lib().qs_plan_create_scored(n, g.ctypes.data if len(g) else None, len(g),
+                                     ctypes.cast(fn, ctypes.c_void_p), None, ctypes.byref(h)))
     return h.value
 
 

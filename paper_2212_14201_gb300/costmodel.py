@@ -4,10 +4,12 @@ The library's greedy planner takes each pass's qubits in program order at a fixe
 tile width (12 qubits) and decides tile pass against per-gate kernels by a fixed
 rule.  The learned planner (qs_plan_create_learned) lets a small perceptron
 (qs_mlp_*) make those choices pass by pass: it predicts the log(milliseconds) of
-candidate passes (widths 11 and 12, two ways of choosing the qubits, as one tile
-pass or gate by gate) from their features (qs_plan_features) and takes the
-candidate with the least predicted time per unit of work; the greedy plan is the
-fallback and the judge.  The network is trained on the GPU by the library's own
+candidate passes (widths 11 and 12; the greedy qubit set, a seeded one, and the
+greedy set kept off one of its qubits; as one tile pass or gate by gate) and of
+the greedy pass that would follow each, from their features
+(qs_plan_features: the gates, and the kernel ops the tile engine would run for
+the pass), and takes the candidate with the least predicted time per unit of
+work over the two; the greedy plan is the fallback and the judge.  The network is trained on the GPU by the library's own
 kernels (qs_mlp_train) from per-pass timings the library's kernel log records
 (qs_timing_fetch), on the kinds of passes the planner chooses among.
 
@@ -60,7 +62,7 @@ def pass_timings(h: int, n: int, gates, plan: int, params=None, repeats: int = 2
     return feats[hit], acc[hit] / repeats
 
 
-def collect(circuits, tile_widths=(10, 11, 12), strategies=(0, 1), plain: bool = True, repeats: int = 2,
+def collect(circuits, tile_widths=(10, 11, 12), strategies=(0, 1, 2), plain: bool = True, repeats: int = 2,
             stream=None):
     """Timing data set over `circuits` = [(n, gates, params or None), ...]: the passes
     of plans of every width and strategy (qs_plan_create_variant), and with
@@ -119,7 +121,8 @@ def load(path: str = WEIGHTS_FILE) -> int | None:
 
 def default_training_circuits(ns=(24, 26, 28, 30), per_n: int = 2, seed0: int = 100):
     """Random circuits of the n=32 workload's mix (40 % two-qubit gates) at
-    smaller n, seeds 100.., plus a layered U3 + CZ circuit per n."""
+    smaller n, seeds 100.., plus a layered U3 + CZ circuit per n (12 layers: deep
+    enough for lookahead passes that span several layers)."""
     import workloads as w
     out = []
     s = seed0
@@ -127,7 +130,7 @@ def default_training_circuits(ns=(24, 26, 28, 30), per_n: int = 2, seed0: int = 
         for _ in range(per_n):
             out.append((n, w.random_circuit(n, 400, s, two_qubit_prob=0.4), None))
             s += 1
-        out.append((n, w.layered_u3_cz(n, 6, s), None))
+        out.append((n, w.layered_u3_cz(n, 12, s), None))
         s += 1
     return out
 

@@ -173,10 +173,10 @@ uint64_t greedy_pass(const qs_gate* gates, const std::vector<int>& tgt, const st
                      const std::vector<uint32_t>& remaining, int m, uint64_t low, int max_ops,
                      std::vector<uint32_t>& pass, std::vector<uint32_t>& rest);
 // The same scan starting from the qubit set `init` (it grows while it has fewer
-// than m qubits).
+// than m qubits, never by a qubit of `forbid`).
 uint64_t greedy_pass_from(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
                           const std::vector<uint32_t>& remaining, int m, uint64_t init, int max_ops,
-                          std::vector<uint32_t>& pass, std::vector<uint32_t>& rest);
+                          std::vector<uint32_t>& pass, std::vector<uint32_t>& rest, uint64_t forbid = 0);
 // A starting qubit set for a pass: `low`, the first runnable gate's target and
 // the most frequent targets among the next `window` runnable gates (m qubits).
 uint64_t seed_qubits(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,

@@ -677,7 +677,7 @@ uint64_t seed_qubits(const qs_gate* gates, const std::vector<int>& tgt, const st
 
 uint64_t greedy_pass_from(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
                           const std::vector<uint32_t>& remaining, int m, uint64_t init, int max_ops,
-                          std::vector<uint32_t>& pass, std::vector<uint32_t>& rest) {
+                          std::vector<uint32_t>& pass, std::vector<uint32_t>& rest, uint64_t forbid) {
   uint64_t Q = init;
   uint64_t blockedN = 0, blockedD = 0;
   pass.clear();
@@ -689,7 +689,7 @@ uint64_t greedy_pass_from(const qs_gate* gates, const std::vector<int>& tgt, con
     const uint64_t Dm = (diag ? (1ull << tgt[k]) : 0) | cms[k];
     bool conflict = (Nm & (blockedN | blockedD)) || (Dm & blockedN) || nops >= max_ops;
     if (!conflict && Nm && !(Q & Nm)) {
-      if (__builtin_popcountll(Q) < m) Q |= Nm;
+      if (__builtin_popcountll(Q) < m && !(Nm & forbid)) Q |= Nm;
       else conflict = true;
     }
     if (conflict) {
@@ -706,27 +706,66 @@ uint64_t greedy_pass_from(const qs_gate* gates, const std::vector<int>& tgt, con
 
 }  // namespace qs
 
-// One tile pass over `remaining` at width m: greedy (strategy 0: targets taken in
-// program order) or seeded (1: from seed_qubits), padded to the full width.  A
-// pass of diagonal gates needs few tile qubits, but a narrow tile means many small
-// tiles (a CTA pass and a barrier per op for a few amplitudes); qubits the pass's
-// gates touch come first (their diagonal ops and controls become in-tile), then
-// the lowest.
-static PlanPass make_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
-                          const std::vector<uint32_t>& remaining, int n, int m, int strategy,
-                          std::vector<uint32_t>& rest) {
-  const int L = std::min(n, TILE_LOW);
-  const uint64_t low = (1ull << L) - 1;
-  PlanPass ps;
-  ps.kind = PASS_TILE;
-  const uint64_t init = strategy == 1 ? seed_qubits(gates, tgt, cms, remaining, m, low, 4 * m) : low;
-  // leave op slots for the phase tables a pass may gain
-  ps.qmask = greedy_pass_from(gates, tgt, cms, remaining, m, init, TILE_MAX_OPS - 32, ps.gates, rest);
+// One tile pass over `remaining` at width m, padded to the full width:
+//   strategy 0  greedy: targets taken in program order;
+//   strategy 1  seeded: the scan starts from seed_qubits;
+//   strategy 2  lookahead: the greedy pass, or a variant of it that never takes
+//               one of the qubits the greedy scan added, whichever absorbs the
+//               most gates together with the greedy pass that follows it.
+// A greedy tile closes over the first m targets in program order; a target whose
+// gates soon wait on qubits outside the tile (the edge of a brickwork wavefront)
+// can hold a slot that another qubit would fill with more gates, and the pass
+// after it can start further along.  `forbid` (strategy 0) keeps the scan off
+// those qubits.  A pass of diagonal gates needs few tile qubits, but a narrow
+// tile means many small tiles (a CTA pass and a barrier per op for a few
+// amplitudes); qubits the pass's gates touch come first in the padding (their
+// diagonal ops and controls become in-tile), then the lowest.
+static uint64_t low_qubits(int n) { return (1ull << std::min(n, TILE_LOW)) - 1; }
+constexpr int kPassMaxGates = TILE_MAX_OPS - 32;  // op slots left for the phase tables a pass may gain
+
+static void pad_pass(PlanPass& ps, const std::vector<int>& tgt, const std::vector<uint64_t>& cms, int n, int m) {
   uint64_t touched = 0;
   for (uint32_t k : ps.gates) touched |= cms[k] | (1ull << tgt[k]);
   for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < m; ++b)
     if (((touched >> b) & 1) && !((ps.qmask >> b) & 1)) ps.qmask |= 1ull << b;
   for (int b = 0; b < n && __builtin_popcountll(ps.qmask) < m; ++b) ps.qmask |= 1ull << b;
+}
+
+// Gates the greedy pass at width m would absorb from `rest`.
+static size_t greedy_absorbed(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                              const std::vector<uint32_t>& rest, int n, int m) {
+  if (rest.empty()) return 0;
+  std::vector<uint32_t> p2, r2;
+  greedy_pass_from(gates, tgt, cms, rest, m, low_qubits(n), kPassMaxGates, p2, r2);
+  return p2.size();
+}
+
+static PlanPass make_pass(const qs_gate* gates, const std::vector<int>& tgt, const std::vector<uint64_t>& cms,
+                          const std::vector<uint32_t>& remaining, int n, int m, int strategy,
+                          std::vector<uint32_t>& rest, uint64_t forbid = 0, uint64_t* grown = nullptr) {
+  const uint64_t low = low_qubits(n);
+  PlanPass ps;
+  ps.kind = PASS_TILE;
+  if (strategy == 2) {
+    uint64_t g0 = 0;
+    ps = make_pass(gates, tgt, cms, remaining, n, m, 0, rest, 0, &g0);
+    size_t best = ps.gates.size() + greedy_absorbed(gates, tgt, cms, rest, n, m);
+    std::vector<uint32_t> r;
+    for (uint64_t c = g0; c; c &= c - 1) {
+      PlanPass v = make_pass(gates, tgt, cms, remaining, n, m, 0, r, c & (~c + 1));
+      const size_t a = v.gates.size() + greedy_absorbed(gates, tgt, cms, r, n, m);
+      if (a > best) {
+        best = a;
+        ps = std::move(v);
+        rest.swap(r);
+      }
+    }
+    return ps;
+  }
+  const uint64_t init = strategy == 1 ? seed_qubits(gates, tgt, cms, remaining, m, low, 4 * m) : low;
+  ps.qmask = greedy_pass_from(gates, tgt, cms, remaining, m, init, kPassMaxGates, ps.gates, rest, forbid);
+  if (grown) *grown = ps.qmask & ~low;
+  pad_pass(ps, tgt, cms, n, m);
   return ps;
 }
 
@@ -832,6 +871,25 @@ static int structural_class(int type) {
   }
 }
 
+static int tile_pass_profile(int n, const PlanPass& ps, const qs_gate* gates, const double* params,
+                             int64_t* counts, double* int_ops_per_amp);
+
+// The program as the planner sees it: a parametrised record (param_idx >= 0) takes
+// fixed generic angles, so that the rewrite of a pass into kernel ops (which
+// depends on the matrices only through their structure for generic angles) can
+// run before the parameters are known.
+static std::vector<qs_gate> structural_program(const qs_gate* gates, size_t ng) {
+  std::vector<qs_gate> g(gates, gates + ng);
+  for (qs_gate& r : g)
+    if (r.param_idx >= 0) {
+      r.param_idx = -1;
+      r.p[0] = 0.7;
+      r.p[1] = 0.3;
+      r.p[2] = 0.5;
+    }
+  return g;
+}
+
 // Features of one pass for the cost model (QS_PASS_FEATURES values):
 //   0 tile pass (1) or one plain gate (0); 1 tile qubits / 13; 2 state qubits / 34;
 //   3 qubits outside the tile / 34; 4..7 gates by structural class (general, real,
@@ -839,8 +897,14 @@ static int structural_class(int type) {
 //   whose target lies outside the tile / 64; 10 distinct non-diagonal targets / 13;
 //   11 gates that start a run (not right after a gate on the same target with the
 //   same controls: the ops left after aggregation) / 64; 12 controlled
-//   non-diagonal gates / 64; 13 log2(1 + gates) / 8.
-static void pass_features(int n, const PlanPass& ps, const qs_gate* gates, double* f) {
+//   non-diagonal gates / 64; 13 log2(1 + gates) / 8;
+// and for a tile pass the kernel ops the Q60 engine runs (tile_pass_profile):
+//   14 limb products per amplitude / 256; 15 phase tables / 16; 16, 17, 18 groups
+//   of four, three, two real rotations / 16; 19 single real rotations / 16;
+//   20 general 2x2 ops / 16; 21 phase and diagonal ops / 16; 22 anti-diagonal ops
+//   / 16; 23 per-tile scalars / 16; 24 kernel ops (shared-memory sweeps) / 64.
+// `gates` is the structural program (structural_program).
+static int pass_features(int n, const PlanPass& ps, const qs_gate* gates, double* f) {
   const int m = ps.kind == PASS_TILE ? __builtin_popcountll(ps.qmask) : 1;
   for (int i = 0; i < QS_PASS_FEATURES; ++i) f[i] = 0.0;
   f[0] = ps.kind == PASS_TILE ? 1.0 : 0.0;
@@ -867,6 +931,25 @@ static void pass_features(int n, const PlanPass& ps, const qs_gate* gates, doubl
   }
   f[10] = __builtin_popcountll(targets) / 13.0;
   f[13] = std::log2(1.0 + (double)ps.gates.size()) / 8.0;
+  if (ps.kind == PASS_TILE && !ps.gates.empty()) {
+    int64_t c[QS_KOP_KINDS];
+    double ipa = 0.0;
+    QS_TRY(tile_pass_profile(n, ps, gates, nullptr, c, &ipa));
+    f[14] = ipa / 256.0;
+    f[15] = c[TOP_DTABLE] / 16.0;
+    f[16] = c[TOP_REAL4] / 16.0;
+    f[17] = c[TOP_REAL3] / 16.0;
+    f[18] = c[TOP_REAL2] / 16.0;
+    f[19] = c[TOP_REAL] / 16.0;
+    f[20] = c[TOP_GENERAL] / 16.0;
+    f[21] = (c[TOP_PHASE1] + c[TOP_DIAG]) / 16.0;
+    f[22] = c[TOP_ANTI] / 16.0;
+    f[23] = c[TOP_SCALAR] / 16.0;
+    int64_t sweeps = -c[0];  // tables run inside a rotation group's loop take no sweep of their own
+    for (int k = 1; k < QS_KOP_KINDS; ++k) sweeps += c[k];
+    f[24] = sweeps / 64.0;
+  }
+  return QS_OK;
 }
 
 extern "C" int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* out) {
@@ -874,7 +957,9 @@ extern "C" int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t n
   if (!p || !out || (ng && !gates)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
   if (p->ng != ng || p->fingerprint != fingerprint(gates, ng))
     return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
-  for (size_t i = 0; i < p->passes.size(); ++i) pass_features(p->n, p->passes[i], gates, out + i * QS_PASS_FEATURES);
+  const std::vector<qs_gate> sg = structural_program(gates, ng);
+  for (size_t i = 0; i < p->passes.size(); ++i)
+    QS_TRY(pass_features(p->n, p->passes[i], sg.data(), out + i * QS_PASS_FEATURES));
   return QS_OK;
 }
 
@@ -883,21 +968,23 @@ extern "C" int qs_plan_create_variant(int n, const qs_gate* gates, size_t ng, in
   clear_error();
   if (tile_qubits < TILE_LOW + 1 || tile_qubits > TILE_MAX_M)
     return fail(QS_ERR_INVALID_ARG, "tile_qubits=%d outside %d..%d", tile_qubits, TILE_LOW + 1, TILE_MAX_M);
-  if (strategy != 0 && strategy != 1) return fail(QS_ERR_INVALID_ARG, "strategy %d: use 0 or 1", strategy);
+  if (strategy < 0 || strategy > 2) return fail(QS_ERR_INVALID_ARG, "strategy %d: use 0, 1 or 2", strategy);
   return plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, tile_qubits, out, strategy);
 }
 
 // Learned plan (the cost model chooses the groupings).  Pass by pass, candidate
-// tile passes over the remaining gates are built at widths 11 and 12 with both
-// strategies (greedy and seeded); the model predicts each candidate's time
-// as one tile pass and as plain per-gate kernels, and the candidate with the
-// least predicted time per unit of work (its gates' touched fractions of the
-// state, a sweep each) is taken, as a tile pass or gate by gate, whichever the
-// model predicts cheaper.  The greedy plan at width 12 is the fallback and the
-// judge: the learned plan is kept only if the model predicts it faster overall
-// by more than 5 %.  (Width 13 is left out: one 512-thread CTA per SM runs the
-// tile ops slower than the widths' fewer passes save, and the model did not
-// learn that from its training passes.)
+// tile passes over the remaining gates are built at widths 11 and 12: the greedy
+// pass, the seeded pass, and the greedy pass kept off each one of the qubits the
+// greedy scan added (strategy 2's variants).  The model predicts each
+// candidate's time as one tile pass and as plain per-gate kernels, and the time
+// of the greedy pass that would follow it; the candidate with the least
+// predicted time per unit of work over the two passes (their gates' touched
+// fractions of the state, a sweep each) is taken, as a tile pass or gate by gate,
+// whichever the model predicts cheaper.  The greedy plan at width 12 is the
+// fallback and the judge: the learned plan is kept only if the model predicts it
+// faster overall by more than 5 %.  (Width 13 is left out: one 512-thread CTA per
+// SM runs the tile ops slower than the widths' fewer passes save, and the model
+// did not learn that from its training passes.)
 using PassScorer = std::function<int(const double* x, size_t B, double* y)>;
 constexpr double kLearnedMargin = 0.05;
 
@@ -918,9 +1005,11 @@ static int plan_build_learned(int n, const qs_gate* gates, size_t ng, const Pass
   qs_plan* greedy = nullptr;
   QS_TRY(plan_build(n, gates, ng, QS_PLAN_GREEDY, 5, TILE_DEFAULT_M, &greedy));
   std::unique_ptr<qs_plan> gp(greedy);
+  const std::vector<qs_gate> sg = structural_program(gates, ng);
   auto predict_plan = [&](const qs_plan* pl, double* total) -> int {
     std::vector<double> x(pl->passes.size() * QS_PASS_FEATURES), y(pl->passes.size());
-    for (size_t i = 0; i < pl->passes.size(); ++i) pass_features(n, pl->passes[i], gates, x.data() + i * QS_PASS_FEATURES);
+    for (size_t i = 0; i < pl->passes.size(); ++i)
+      QS_TRY(pass_features(n, pl->passes[i], sg.data(), x.data() + i * QS_PASS_FEATURES));
     if (!y.empty()) QS_TRY(score(x.data(), y.size(), y.data()));
     *total = 0.0;
     for (double v : y) *total += std::exp(v) * 1e-3;
@@ -939,38 +1028,55 @@ static int plan_build_learned(int n, const qs_gate* gates, size_t ng, const Pass
   struct Cand {
     PlanPass ps;
     std::vector<uint32_t> rest;
+    PlanPass next;  // the greedy pass that would follow (no gates at the end)
   };
   std::vector<Cand> cands;
   std::vector<double> x, y;
   double learned_total = 0.0;
+  auto add_cand = [&](Cand&& c) {
+    if (c.ps.gates.empty()) return;
+    for (const Cand& o : cands)
+      if (o.ps.qmask == c.ps.qmask && o.ps.gates == c.ps.gates) return;
+    if (!c.rest.empty()) {
+      std::vector<uint32_t> r2;
+      c.next = make_pass(gates, tgt, cms, c.rest, n, std::min(n, TILE_DEFAULT_M), 0, r2);
+    }
+    cands.push_back(std::move(c));
+  };
   while (!remaining.empty()) {
     cands.clear();
     for (int m = 11; m <= TILE_DEFAULT_M; ++m) {
       const int mm = std::min(n, m);
+      uint64_t grown = 0;
       for (int strategy = 0; strategy < 2; ++strategy) {
         Cand c;
-        c.ps = make_pass(gates, tgt, cms, remaining, n, mm, strategy, c.rest);
-        bool dup = false;
-        for (const Cand& o : cands) dup = dup || (o.ps.qmask == c.ps.qmask && o.ps.gates == c.ps.gates);
-        if (!dup) cands.push_back(std::move(c));
+        c.ps = make_pass(gates, tgt, cms, remaining, n, mm, strategy, c.rest, 0, strategy == 0 ? &grown : nullptr);
+        add_cand(std::move(c));
+      }
+      for (uint64_t b = grown; b; b &= b - 1) {
+        Cand c;
+        c.ps = make_pass(gates, tgt, cms, remaining, n, mm, 0, c.rest, b & (~b + 1));
+        add_cand(std::move(c));
       }
       if (mm < m) break;
     }
-    // rows: each candidate as a tile pass, then each of its gates as a plain pass
+    // rows: each candidate as a tile pass, then each of its gates as a plain pass,
+    // then the pass after it
     x.clear();
     std::vector<size_t> first(cands.size());
     for (size_t c = 0; c < cands.size(); ++c) {
       first[c] = x.size() / QS_PASS_FEATURES;
-      x.resize(x.size() + QS_PASS_FEATURES * (1 + cands[c].ps.gates.size()));
+      x.resize(x.size() + QS_PASS_FEATURES * (2 + cands[c].ps.gates.size()));
       double* row = x.data() + first[c] * QS_PASS_FEATURES;
-      pass_features(n, cands[c].ps, gates, row);
+      QS_TRY(pass_features(n, cands[c].ps, sg.data(), row));
       for (size_t i = 0; i < cands[c].ps.gates.size(); ++i) {
         PlanPass g1;
         g1.kind = PASS_GATE;
         g1.qmask = 1ull << tgt[cands[c].ps.gates[i]];
         g1.gates.push_back(cands[c].ps.gates[i]);
-        pass_features(n, g1, gates, row + (1 + i) * QS_PASS_FEATURES);
+        QS_TRY(pass_features(n, g1, sg.data(), row + (1 + i) * QS_PASS_FEATURES));
       }
+      QS_TRY(pass_features(n, cands[c].next, sg.data(), row + (1 + cands[c].ps.gates.size()) * QS_PASS_FEATURES));
     }
     y.assign(x.size() / QS_PASS_FEATURES, 0.0);
     QS_TRY(score(x.data(), y.size(), y.data()));
@@ -978,16 +1084,19 @@ static int plan_build_learned(int n, const qs_gate* gates, size_t ng, const Pass
     bool best_tile = true;
     double best_rate = 1e300, best_time = 0.0;
     for (size_t c = 0; c < cands.size(); ++c) {
+      const size_t ngc = cands[c].ps.gates.size();
       const double t_tile = std::exp(y[first[c]]);
-      double t_gates = 0.0, work = 0.0;
-      for (size_t i = 0; i < cands[c].ps.gates.size(); ++i) {
+      double t_gates = 0.0, work = 0.0, work_next = 0.0;
+      for (size_t i = 0; i < ngc; ++i) {
         const uint32_t k = cands[c].ps.gates[i];
         t_gates += std::exp(y[first[c] + 1 + i]);
         work += op_touch_fraction(gates[k], cms[k]);
       }
-      const bool tile = cands[c].ps.gates.size() > 1 && t_tile <= t_gates;
+      for (uint32_t k : cands[c].next.gates) work_next += op_touch_fraction(gates[k], cms[k]);
+      const double t_next = cands[c].next.gates.empty() ? 0.0 : std::exp(y[first[c] + 1 + ngc]);
+      const bool tile = ngc > 1 && t_tile <= t_gates;
       const double t = tile ? t_tile : t_gates;
-      const double rate = t / std::max(work, 1e-9);
+      const double rate = (t + t_next) / std::max(work + work_next, 1e-9);
       if (rate < best_rate) {
         best_rate = rate;
         best = c;
@@ -1040,6 +1149,19 @@ extern "C" int qs_plan_create_learned(int n, const qs_gate* gates, size_t ng, qs
                 QS_PASS_FEATURES);
   PassScorer score = [model](const double* x, size_t B, double* y) { return qs_mlp_forward(model, x, B, y); };
   return plan_build_learned(n, gates, ng, score, out);
+}
+
+extern "C" int qs_plan_create_scored(int n, const qs_gate* gates, size_t ng, qs_pass_scorer score, void* ctx,
+                                     qs_plan** out) {
+  clear_error();
+  if (!out) return fail(QS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!score) return fail(QS_ERR_INVALID_ARG, "score is NULL");
+  PassScorer sc = [score, ctx](const double* x, size_t B, double* y) {
+    const int rc = score(ctx, x, B, y);
+    return rc ? fail(QS_ERR_INVALID_ARG, "the pass scorer returned %d", rc) : QS_OK;
+  };
+  return plan_build_learned(n, gates, ng, sc, out);
 }
 
 extern "C" int qs_plan_free(qs_plan* p) {
@@ -1250,21 +1372,19 @@ static int build_pass_ops(int n, const PlanPass& ps, const qs_gate* gates, const
   return QS_OK;
 }
 
-// io: TileArgs::io (Q60 engine only); *launched: whether a kernel ran (a pass
-// whose ops all cancel launches nothing).
-static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed,
-                         int io, bool* launched) {
-  *launched = false;
-  const int n = s->n;
-  TileArgs* g = new (std::nothrow) TileArgs;
-  if (!g) return fail(QS_ERR_OOM, "host allocation failed");
+// The kernel arguments of one tile pass on an n-qubit state of precision `prec`
+// (128 complex128, 64 complex64), host only: the op slots in `g`, the phase
+// tables in `ptables` (not yet on the device), and the pass's FP64 flops and Q60
+// limb products.
+static int build_tile_args(int n, int prec, const PlanPass& ps, const qs_gate* gates, const double* params,
+                           bool fixed, int io, TileArgs* g, std::vector<PhaseTable>& ptables, double* flops_out,
+                           double* int_ops_out) {
   const uint64_t Q = ps.qmask;
   int local[64];
   int m = 0;
   std::vector<Op1> rops;
-  std::vector<PhaseTable> ptables;
-  const bool f32 = s->prec == 64;  // complex64 state: FP32 engine
-  int rc = build_pass_ops(n, ps, gates, params, (fixed && s->prec == 128) || f32, &rops, &ptables, local, &m);
+  const bool f32 = prec == 64;  // complex64 state: FP32 engine
+  int rc = build_pass_ops(n, ps, gates, params, (fixed && prec == 128) || f32, &rops, &ptables, local, &m);
   int L = 0;
   while (L < n && ((Q >> L) & 1)) ++L;
   g->n = n;
@@ -1277,11 +1397,11 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   for (int b = 0; b < n; ++b)
     if (!((Q >> b) & 1)) g->outpos[g->nout++] = b;
   g->nops = 0;
-  g->io = (fixed && s->prec == 128) ? io : 0;
+  g->io = (fixed && prec == 128) ? io : 0;
   g->tables = nullptr;
   double flops = 0.0, int_ops = 0.0;
   const double N = (double)(1ull << n);
-  const bool pairs = ((fixed && s->prec == 128) || f32) && g_rotation_pairs;
+  const bool pairs = ((fixed && prec == 128) || f32) && g_rotation_pairs;
   const bool triples = g_rotation_triples;
   const bool quads = g_rotation_quads;
   auto in_tile_real = [&](const Op1& o) { return o.cls == OP_REAL && o.cmask == 0 && local[o.target] >= 0; };
@@ -1475,7 +1595,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
     const int t = op.target;
     const uint64_t cm = op.cmask;
     TileOp& to = g->ops[g->nops];
-    if (s->prec == 64)
+    if (prec == 64)
       for (int e = 0; e < 4; ++e) to.f[e] = make_float2((float)mat.m[e].re, (float)mat.m[e].im);
     else if (fixed && op.cls == OP_GENERAL)  // three limb products per complex product
       for (int e = 0; e < 4; ++e) to.q[e] = qc_make_gauss(mat.m[e].re, mat.m[e].im);
@@ -1531,13 +1651,65 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
       g->signs[t].t[k] = (uint8_t)sg[k].second;
     }
   }
-  if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, f32);
+  *flops_out = flops;
+  *int_ops_out = int_ops;
+  return rc;
+}
+
+// io: TileArgs::io (Q60 engine only); *launched: whether a kernel ran (a pass
+// whose ops all cancel launches nothing).
+static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, const double* params, bool fixed,
+                         int io, bool* launched) {
+  *launched = false;
+  TileArgs* g = new (std::nothrow) TileArgs;
+  if (!g) return fail(QS_ERR_OOM, "host allocation failed");
+  std::vector<PhaseTable> ptables;
+  double flops = 0.0, int_ops = 0.0;
+  int rc = build_tile_args(s->n, s->prec, ps, gates, params, fixed, io, g, ptables, &flops, &int_ops);
+  if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, s->prec == 64);
   if (rc == QS_OK && g->nops > 0) {
     rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0, (int)ps.gates.size(), fixed);
     *launched = rc == QS_OK;
   }
   delete g;
   return rc;
+}
+
+// Kernel ops of one tile pass by kind (host only; the Q60 engine on a complex128
+// state): counts[k] for TileOpKind k (continuation slots not counted; phase tables
+// that run inside a rotation group's loop counted in counts[TOP_DTABLE] and again
+// in counts[0]), and the pass's limb products per amplitude.
+static int tile_pass_profile(int n, const PlanPass& ps, const qs_gate* gates, const double* params,
+                             int64_t* counts, double* int_ops_per_amp) {
+  for (int k = 0; k < QS_KOP_KINDS; ++k) counts[k] = 0;
+  *int_ops_per_amp = 0.0;
+  if (ps.kind != PASS_TILE) return QS_OK;
+  std::unique_ptr<TileArgs> g(new (std::nothrow) TileArgs);
+  if (!g) return fail(QS_ERR_OOM, "host allocation failed");
+  std::vector<PhaseTable> ptables;
+  double flops = 0.0, int_ops = 0.0;
+  QS_TRY(build_tile_args(n, 128, ps, gates, params, true, 0, g.get(), ptables, &flops, &int_ops));
+  for (int k = 0; k < g->nops; ++k) {
+    const int kind = g->ops[k].kind;
+    if (kind == TOP_CONT) continue;
+    if (kind >= 0 && kind < QS_KOP_KINDS) ++counts[kind];
+    if ((kind == TOP_REAL2 || kind == TOP_REAL3 || kind == TOP_REAL4) && g->ops[k].code1 >= 0) {
+      ++counts[TOP_DTABLE];  // a table fused into the group's loop
+      ++counts[0];
+    }
+  }
+  *int_ops_per_amp = int_ops / (double)(1ull << n);
+  return QS_OK;
+}
+
+extern "C" int qs_plan_pass_kernel_ops(const qs_plan* p, size_t pass, const qs_gate* gates, size_t ng,
+                                       const double* params, int64_t* counts, double* int_ops_per_amp) {
+  clear_error();
+  if (!p || !counts || !int_ops_per_amp || (ng && !gates)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+  if (p->ng != ng || p->fingerprint != fingerprint(gates, ng))
+    return fail(QS_ERR_INVALID_ARG, "plan does not match the program");
+  if (pass >= p->passes.size()) return fail(QS_ERR_INVALID_ARG, "pass %zu of %zu", pass, p->passes.size());
+  return tile_pass_profile(p->n, p->passes[pass], gates, params, counts, int_ops_per_amp);
 }
 
 int qs_apply_plan(qs_state* s, const qs_gate* gates, size_t ng, const double* params, const qs_plan* plan,

@@ -22,8 +22,8 @@ def target_of(rec):
     return int(rec["q1"]) if int(rec["type"]) in TWO else int(rec["q0"])
 
 
-def check_plan(q, orc, n, gates, params=None):
-    p = q.qs_plan_create(n, gates, q.PLAN_GREEDY, 5)
+def check_plan(q, orc, n, gates, params=None, make=None):
+    p = q.qs_plan_create(n, gates, q.PLAN_GREEDY, 5) if make is None else make(n, gates)
     try:
         passes = q.qs_plan_passes(p)
         stats = q.qs_plan_get_stats(p)
@@ -148,8 +148,9 @@ def test_pass_op_lists_compose_to_their_passes(q, orc, tables, aggregate):
     q.qs_set_phase_tables(tables)
     q.qs_set_aggregate(aggregate)
     try:
-        for n, g, params in cases:
-            p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+        for (n, g, params), lookahead in [(c, la) for c in cases for la in (False, True)]:
+            p = q.qs_plan_create_variant(n, g, max(4, min(n, 12)), 2) if lookahead else \
+                q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
             try:
                 st = w.random_state(n, 17 + n)
                 st = st / np.sqrt(np.sum(st * st))
@@ -249,3 +250,89 @@ def test_tables_absorb_cz_across_tile_boundaries(q):
         assert signs >= 140 and left <= 30, (signs, left)
     finally:
         q.qs_plan_free(p)
+
+
+def shipped_scorer(orc):
+    """The shipped cost model's forward pass on the host (the oracle's perceptron)."""
+    import json
+    import os
+    import paper_2212_14201_gb300 as pkg
+    path = os.path.join(os.path.dirname(pkg.__file__), "costmodel_weights.json")
+    with open(path) as f:
+        d = json.load(f)
+    wts = np.asarray(d["weights"], dtype=np.float64)
+    return lambda x: orc.mlp_forward(d["features"], d["hidden"], wts, x)
+
+
+@pytest.mark.parametrize("n,maker,seed", [(13, "random", 2), (16, "random", 3), (14, "layered", 4), (16, "layered", 5)])
+def test_lookahead_plans_are_valid_reorderings(q, orc, n, maker, seed):
+    """Strategy 2 (the greedy pass or a variant kept off one of its qubits) keeps
+    every gate exactly once in a commuting order: the replay equals the program."""
+    g = w.random_circuit(n, 500, seed, two_qubit_prob=0.4) if maker == "random" else w.layered_u3_cz(n, 16, seed)
+    for m in (8, 11):
+        check_plan(q, orc, n, g, make=lambda nn, gg: q.qs_plan_create_variant(nn, gg, m, 2))
+
+
+def test_lookahead_absorbs_more_per_pass(q):
+    """On brickwork (config 1's structure: n=30, 20 layers of U3 + CZ) and on the
+    n=32 random workload, the lookahead passes cover the program in fewer passes
+    than the program-order greedy passes (20 -> 13 and 36 -> 32 at width 12)."""
+    for n, g in ((30, w.layered_u3_cz(30, 20, 1)), (32, w.random_circuit(32, 2000, 2, two_qubit_prob=0.4))):
+        counts = []
+        for strategy in (0, 2):
+            p = q.qs_plan_create_variant(n, g, 12, strategy)
+            try:
+                counts.append(q.qs_plan_get_stats(p)["n_passes"])
+            finally:
+                q.qs_plan_free(p)
+        assert counts[1] < counts[0], (n, counts)
+
+
+@pytest.mark.parametrize("n,maker,seed", [(14, "random", 6), (16, "layered", 7)])
+def test_scored_plans_are_valid_reorderings(q, orc, n, maker, seed):
+    """The learned planner driven by a host cost model (qs_plan_create_scored):
+    whatever it chooses is a valid reordering, with tile passes of at most 12
+    qubits holding the low qubits."""
+    g = w.random_circuit(n, 500, seed, two_qubit_prob=0.4) if maker == "random" else w.layered_u3_cz(n, 16, seed)
+    sc = shipped_scorer(orc)
+    check_plan(q, orc, n, g, make=lambda nn, gg: q.qs_plan_create_scored(nn, gg, sc))
+    # a cost model that charges every pass alike prefers the candidates that absorb the most
+    flat = lambda x: np.zeros(len(x))
+    check_plan(q, orc, n, g, make=lambda nn, gg: q.qs_plan_create_scored(nn, gg, flat))
+
+
+def test_shipped_model_prefers_its_plans_where_it_chooses_them(q, orc):
+    """The shipped cost model through the planner (host forward pass, planning
+    only): on the n=32 random workload (2000 gates, seed 2) and an n=28 brickwork
+    it keeps its own groupings (no fallback) and predicts them more than the
+    judge's 5 % faster than the greedy plan; on config 1's brickwork (n=30, 20
+    layers) its pass-by-pass choices are the greedy passes.  Every learned plan
+    holds every gate exactly once."""
+    sc = shipped_scorer(orc)
+
+    def predicted(p, g):
+        return float(np.sum(np.exp(sc(q.qs_plan_features(p, g)))))
+
+    for n, g, chooses in ((32, w.random_circuit(32, 2000, 2, two_qubit_prob=0.4), True),
+                          (28, w.layered_u3_cz(28, 12, 301), True), (30, w.layered_u3_cz(30, 20, 1), False)):
+        pl = q.qs_plan_create_scored(n, g, sc)
+        pg = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+        try:
+            st = q.qs_plan_get_stats(pl)
+            order = np.concatenate([idx for _, _, idx in q.qs_plan_passes(pl)])
+            assert sorted(order.tolist()) == list(range(len(g)))
+            tl, tg = predicted(pl, g), predicted(pg, g)
+            if chooses:
+                assert st["learned_fallback"] == 0 and tl < 0.95 * tg, (n, tl, tg)
+            else:
+                assert tl <= tg * (1 + 1e-12)
+        finally:
+            q.qs_plan_free(pl)
+            q.qs_plan_free(pg)
+
+
+def test_scorer_failure_is_reported(q):
+    def bad(x):
+        raise RuntimeError("no model")
+    with pytest.raises(q.QsimError):
+        q.qs_plan_create_scored(8, w.random_circuit(8, 50, 1), bad)
