@@ -369,7 +369,8 @@ int qs_plan_features(const qs_plan* p, const qs_gate* gates, size_t ng, double* 
  * diagonal, 3 anti-diagonal, 4 real, 5 general 2x2, 9 diagonal on a qubit outside
  * the tile (a per-tile scalar), 10 phase tables (those fused into a rotation
  * group included), 11/13/14 groups of two/three/four real rotations; counts[0]
- * = the phase tables fused into a rotation group (no sweep of their own);
+ * = the phase tables fused into a rotation group or into the tile's load or
+ * store (no sweep of their own);
  * *int_ops_per_amp = the pass's limb products per amplitude of the state.  A
  * pass of plain per-gate kernels reports zeros.  Errors: INVALID_ARG. */
 #define QS_KOP_KINDS 15

@@ -1629,6 +1629,22 @@ static int build_tile_args(int n, int prec, const PlanPass& ps, const qs_gate* g
     int_ops += N * class_touch_fraction(op) * op_int_ops_per_amp(op);
     ++g->nops;
   }
+  // Q60 engine: a phase table that opens or closes the pass runs inside the tile's
+  // load or store loop (no shared-memory sweep and barrier of its own).
+  if (rc == QS_OK && fixed && prec == 128 && g_fuse_tables) {
+    auto table_op = [&](const TileOp& o) {
+      return o.kind == TOP_DTABLE && o.lcmask < ptables.size() && o.lcmask < 255 && o.tb == m;
+    };
+    if (g->nops > 0 && table_op(g->ops[0])) {
+      g->io |= (int)(g->ops[0].lcmask + 1) << 8;
+      memmove(&g->ops[0], &g->ops[1], sizeof(TileOp) * (size_t)(g->nops - 1));
+      --g->nops;
+    }
+    if (g->nops > 0 && table_op(g->ops[g->nops - 1])) {
+      g->io |= (int)(g->ops[g->nops - 1].lcmask + 1) << 16;
+      --g->nops;
+    }
+  }
   for (int k = 0; rc == QS_OK && k < g->nops; ++k) {
     const TileOp& o = g->ops[k];
     if (o.kind == TOP_DTABLE && (o.lcmask >= ptables.size() || o.tb != m || ptables[o.lcmask].t.size() != ((size_t)1 << m)))
@@ -1667,7 +1683,7 @@ static int run_tile_pass(qs_state* s, const PlanPass& ps, const qs_gate* gates, 
   double flops = 0.0, int_ops = 0.0;
   int rc = build_tile_args(s->n, s->prec, ps, gates, params, fixed, io, g, ptables, &flops, &int_ops);
   if (rc == QS_OK && !ptables.empty()) rc = upload_tables(s, ptables, &g->tables, s->prec == 64);
-  if (rc == QS_OK && g->nops > 0) {
+  if (rc == QS_OK && (g->nops > 0 || (g->io >> 8) != 0)) {
     rc = launch_tile(s, *g, fixed ? 0.0 : flops, fixed ? int_ops : 0.0, (int)ps.gates.size(), fixed);
     *launched = rc == QS_OK;
   }
@@ -1689,6 +1705,8 @@ static int tile_pass_profile(int n, const PlanPass& ps, const qs_gate* gates, co
   std::vector<PhaseTable> ptables;
   double flops = 0.0, int_ops = 0.0;
   QS_TRY(build_tile_args(n, 128, ps, gates, params, true, 0, g.get(), ptables, &flops, &int_ops));
+  if ((g->io >> 8) & 255) ++counts[TOP_DTABLE], ++counts[0];   // tables run in the load or store loop
+  if ((g->io >> 16) & 255) ++counts[TOP_DTABLE], ++counts[0];
   for (int k = 0; k < g->nops; ++k) {
     const int kind = g->ops[k].kind;
     if (kind == TOP_CONT) continue;

@@ -474,6 +474,34 @@ __device__ __forceinline__ void load_tile(T* tile, const S* src, uint64_t base, 
   for (; j < TS; j += THREADS) tile[j ^ tsq] = conv(src[base + offs[j >> L] + (j & lowmask)]);
 }
 
+// The same load with a phase table applied on the way in (the pass's first op):
+// element j is multiplied by tab[j], negated where popc(j & S) is odd; four loads
+// in flight (the table entries take the other registers).
+template <int THREADS, class S, class F>
+__device__ __forceinline__ void load_tile_table(longlong2* tile, const S* src, uint64_t base, const uint64_t* offs,
+                                                int L, uint32_t lowmask, uint32_t TS, uint32_t tsq, F conv,
+                                                const int4* tab, uint32_t Sg) {
+  constexpr uint32_t U = 4;
+  uint32_t j = threadIdx.x;
+  for (; j + (U - 1) * THREADS < TS; j += U * THREADS) {
+    S v[U];
+    int4 e[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t jj = j + u * THREADS;
+      v[u] = src[base + offs[jj >> L] + (jj & lowmask)];
+      e[u] = __ldg(tab + jj);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t jj = j + u * THREADS;
+      tile[jj ^ tsq] = table_mul(e[u], conv(v[u]), __popc(jj & Sg) & 1);
+    }
+  }
+  for (; j < TS; j += THREADS)
+    tile[j ^ tsq] = table_mul(__ldg(tab + j), conv(src[base + offs[j >> L] + (j & lowmask)]), __popc(j & Sg) & 1);
+}
+
 // Stores a tile the same way, eight shared-memory reads before their global stores.
 template <int THREADS, class T, class D, class F>
 __device__ __forceinline__ void store_tile(const T* tile, D* dst, uint64_t base, const uint64_t* offs, int L,
@@ -491,6 +519,31 @@ __device__ __forceinline__ void store_tile(const T* tile, D* dst, uint64_t base,
     }
   }
   for (; j < TS; j += THREADS) dst[base + offs[j >> L] + (j & lowmask)] = conv(tile[j ^ tsq]);
+}
+
+// The same store with a phase table applied on the way out (the pass's last op).
+template <int THREADS, class D, class F>
+__device__ __forceinline__ void store_tile_table(const longlong2* tile, D* dst, uint64_t base, const uint64_t* offs,
+                                                 int L, uint32_t lowmask, uint32_t TS, uint32_t tsq, F conv,
+                                                 const int4* tab, uint32_t Sg) {
+  constexpr uint32_t U = 4;
+  uint32_t j = threadIdx.x;
+  for (; j + (U - 1) * THREADS < TS; j += U * THREADS) {
+    longlong2 v[U];
+    int4 e[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      v[u] = tile[(j + u * THREADS) ^ tsq];
+      e[u] = __ldg(tab + j + u * THREADS);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t jj = j + u * THREADS;
+      dst[base + offs[jj >> L] + (jj & lowmask)] = conv(table_mul(e[u], v[u], __popc(jj & Sg) & 1));
+    }
+  }
+  for (; j < TS; j += THREADS)
+    dst[base + offs[j >> L] + (j & lowmask)] = conv(table_mul(__ldg(tab + j), tile[j ^ tsq], __popc(j & Sg) & 1));
 }
 
 template <class E, int THREADS>
@@ -516,11 +569,21 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
     __syncthreads();  // offs ready / previous tile stored
     auto conv = [](const typename E::G& v) { return E::load(v); };
     if constexpr (std::is_same<E, EngQ60>::value) {
-      if (g.io & 1)
+      const int lt = ((g.io >> 8) & 255) - 1;  // a phase table applied on load
+      if (lt >= 0) {
+        const int4* tab = reinterpret_cast<const int4*>(g.tables) + (size_t)lt * TS;
+        const uint32_t Sg = table_sign_mask(g, lt, base);
+        if (g.io & 1)
+          load_tile_table<THREADS>(tile, reinterpret_cast<const longlong2*>(a), base, offs, L, lowmask, TS, tsq,
+                                   [](const longlong2& v) { return v; }, tab, Sg);
+        else
+          load_tile_table<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq, conv, tab, Sg);
+      } else if (g.io & 1) {
         load_tile<THREADS>(tile, reinterpret_cast<const longlong2*>(a), base, offs, L, lowmask, TS, tsq,
                            [](const longlong2& v) { return v; });
-      else
+      } else {
         load_tile<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq, conv);
+      }
     } else {
       load_tile<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq, conv);
     }
@@ -648,6 +711,18 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? E::kMinBlocks : 1) k
       __syncthreads();
     }
     if constexpr (std::is_same<E, EngQ60>::value) {
+      const int st = ((g.io >> 16) & 255) - 1;  // a phase table applied on store
+      if (st >= 0) {
+        const int4* tab = reinterpret_cast<const int4*>(g.tables) + (size_t)st * TS;
+        const uint32_t Sg = table_sign_mask(g, st, base);
+        if (g.io & 2)
+          store_tile_table<THREADS>(tile, reinterpret_cast<longlong2*>(a), base, offs, L, lowmask, TS, tsq,
+                                    [](const longlong2& v) { return v; }, tab, Sg);
+        else
+          store_tile_table<THREADS>(tile, a, base, offs, L, lowmask, TS, tsq,
+                                    [](const longlong2& v) { return E::store(v); }, tab, Sg);
+        continue;
+      }
       if (g.io & 2) {
         store_tile<THREADS>(tile, reinterpret_cast<longlong2*>(a), base, offs, L, lowmask, TS, tsq,
                             [](const longlong2& v) { return v; });

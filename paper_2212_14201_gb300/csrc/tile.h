@@ -73,7 +73,9 @@ struct TileArgs {
   int nops;
   // Q60 engine: bit 0, the buffer holds Q60 integers (int64 pairs) left by the
   // previous tile pass instead of complex128; bit 1, store Q60 integers for the
-  // next tile pass.  0 for the other engines.
+  // next tile pass; bits 8..15, 1 + the phase table applied as each element is
+  // loaded (0: none); bits 16..23, 1 + the phase table applied as each element is
+  // stored (0: none).  0 for the other engines.
   int io;
   const QL* tables;  // DTABLE ops: per table 2^m entries, each the limb pairs of Re and Im (Q60)
   TileSigns signs[TILE_MAX_SIGNED_TABLES];  // sign terms of tables 0..31
