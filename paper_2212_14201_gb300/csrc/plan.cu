@@ -1460,7 +1460,25 @@ static int build_tile_args(int n, int prec, const PlanPass& ps, const qs_gate* g
         continue;
       }
     }
-    if (pairs && quads && !f32 && i + 3 < rops.size() && g->nops + 3 <= TILE_MAX_OPS && in_tile_real(op) &&
+    // A run of r >= 5 rotations on distinct tile qubits right after a phase table
+    // (not the pass's first op, which runs in the tile's load loop) starts with a
+    // triple (r = 4k + 1 or 4k + 3) or a pair (r = 4k + 2): the group takes the
+    // table into its loop, and the run still takes as many sweeps as groups of
+    // four first would (r = 9: triple, four, pair against four, four, single).
+    int lead = 0;
+    if (pairs && quads && triples && g_fuse_tables && !f32 && in_tile_real(op) && i > 0 &&
+        rops[i - 1].cls == kTableMark && g->nops >= 2 && g->ops[g->nops - 1].kind == TOP_DTABLE &&
+        g->ops[g->nops - 1].lcmask < 128) {
+      size_t e = i;
+      uint32_t seen = 0;
+      while (e < rops.size() && in_tile_real(rops[e]) && !((seen >> local[rops[e].target]) & 1)) {
+        seen |= 1u << local[rops[e].target];
+        ++e;
+      }
+      const size_t r = e - i;
+      if (r >= 5 && r % 4 != 0) lead = r % 4 == 2 ? 2 : 3;
+    }
+    if (lead == 0 && pairs && quads && !f32 && i + 3 < rops.size() && g->nops + 3 <= TILE_MAX_OPS && in_tile_real(op) &&
         in_tile_real(rops[i + 1]) && in_tile_real(rops[i + 2]) && in_tile_real(rops[i + 3])) {
       const uint32_t tm = (1u << local[op.target]) | (1u << local[rops[i + 1].target]) |
                           (1u << local[rops[i + 2].target]) | (1u << local[rops[i + 3].target]);
@@ -1489,7 +1507,7 @@ static int build_tile_args(int n, int prec, const PlanPass& ps, const qs_gate* g
         continue;
       }
     }
-    if (pairs && triples && !f32 && i + 2 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
+    if (lead != 2 && pairs && triples && !f32 && i + 2 < rops.size() && in_tile_real(op) && in_tile_real(rops[i + 1]) &&
         in_tile_real(rops[i + 2]) && rops[i + 1].target != op.target && rops[i + 2].target != op.target &&
         rops[i + 2].target != rops[i + 1].target) {
       // three real rotations on different tile qubits: one op on octets (two slots)

