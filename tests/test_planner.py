@@ -345,3 +345,36 @@ def test_scorer_failure_is_reported(q):
         raise RuntimeError("no model")
     with pytest.raises(q.QsimError):
         q.qs_plan_create_scored(8, w.random_circuit(8, 50, 1), bad)
+
+
+@pytest.mark.parametrize("n,maker,seed", [(30, "layered", 1), (16, "layered", 2), (20, "random", 3), (12, "chain", 4)])
+def test_kernel_ops_cover_the_pass_ops(q, n, maker, seed):
+    """The tile engine's op slots for each pass (qs_plan_pass_kernel_ops) account for
+    the pass's op list (qs_plan_pass_ops) exactly: every phase table once (as its
+    own sweep, inside a rotation group's loop, or in the tile's load or store loop),
+    every in-tile uncontrolled real rotation in exactly one group of four, three or
+    two or as a single rotation, and 12 limb products per amplitude for each group,
+    single rotation and table."""
+    g = {"layered": lambda: w.layered_u3_cz(n, 20, seed),
+         "random": lambda: w.random_circuit(n, 400, seed, two_qubit_prob=0.4),
+         "chain": lambda: chain_circuit(n, seed)}[maker]()
+    p = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    try:
+        for i, (kind, qm, idx) in enumerate(q.qs_plan_passes(p)):
+            c, ipa = q.qs_plan_pass_kernel_ops(p, i, g)
+            if kind != 1:
+                assert not c.any() and ipa == 0.0
+                continue
+            ops, _ = q.qs_plan_pass_ops(p, i, g)
+            tables = sum(1 for o in ops if o["kind"] == 1)
+            reals = sum(1 for o in ops if o["kind"] == 0 and o["ctrl_mask"] == 0 and (qm >> o["target"]) & 1
+                        and np.all(np.imag(o["m"]) == 0) and o["m"][0, 0] != 0 and o["m"][0, 1] != 0)
+            assert c[10] == tables, (i, c, tables)
+            assert 4 * c[14] + 3 * c[13] + 2 * c[11] + c[4] == reals, (i, c, reals)
+            assert 0 <= c[0] <= c[10]
+            # tables in rotation-group loops: at most one per group; in load/store: at most two
+            assert c[0] <= c[11] + c[13] + c[14] + 2
+            grouped = c[14] + c[13] + c[11] + c[4] + c[10]
+            assert ipa >= 12.0 * grouped - 1e-9
+    finally:
+        q.qs_plan_free(p)
