@@ -46,6 +46,53 @@ def test_fused_random_circuits(q, orc, arith, n, ng, seed, p2):
     assert np.max(np.abs(psi - orc.as_complex(orc.run(n, g)))) < TOL
 
 
+def _table_edge_programs(n, seed):
+    """(a) diagonal gates only: one tile pass whose only kernel op is a phase table;
+    (b) RZ, RY and RZ layers (and CZs): a pass opened and closed by a table."""
+    rng = w.SplitMix64(seed)
+    a = [w.gate("RZ", k, theta=rng.angle()) for k in range(n)] + [w.gate("CZ", k, k + 1) for k in range(0, n - 1, 2)] + \
+        [w.gate("T", k) for k in range(0, n, 3)]
+    b = [w.gate("RZ", k, theta=rng.angle()) for k in range(n)] + [w.gate("RY", k, theta=rng.angle()) for k in range(n)] + \
+        [w.gate("RZ", k, theta=rng.angle()) for k in range(n)] + [w.gate("CZ", k, k + 1) for k in range(1, n - 1, 2)]
+    return w.pack(a), w.pack(b)
+
+
+@pytest.mark.parametrize("n", [6, 14, 20])
+def test_phase_tables_in_load_and_store_loops(q, orc, n):
+    """Q60 passes whose phase tables run in the tile's load and store loops: a pass
+    whose only op is such a table (no shared-memory op at all), a pass opened and
+    closed by one, and the two programs applied one after the other to the same
+    state, against the oracle within 1e-12."""
+    ga, gb = _table_edge_programs(n, n)
+    pa = q.qs_plan_create(n, ga, q.PLAN_GREEDY, 5)
+    pb = q.qs_plan_create(n, gb, q.PLAN_GREEDY, 5)
+    h = q.qs_alloc(n)
+    try:
+        c, _ = q.qs_plan_pass_kernel_ops(pa, 0, ga)
+        assert c[0] >= 1                      # the table rides in a load or store loop
+        if n == 6:
+            assert c[1:].sum() - c[0] == 0    # and the pass has no other op
+        c, _ = q.qs_plan_pass_kernel_ops(pb, 0, gb)
+        assert c[0] >= 2
+        q.qs_set_arith(h, q.ARITH_FIXED)
+        q.qs_apply(h, ga, None, pa)
+        assert np.max(np.abs(q.qs_get_state(h) - orc.as_complex(orc.run(n, ga)))) < TOL
+        q.qs_set_zero(h)
+        q.qs_apply(h, gb, None, pb)
+        assert np.max(np.abs(q.qs_get_state(h) - orc.as_complex(orc.run(n, gb)))) < TOL
+        init = w.random_state_fast(n, 5)
+        init = init / np.sqrt(np.sum(init * init))
+        q.qs_set_state(h, orc.as_complex(init))
+        q.qs_apply(h, ga, None, pa)
+        q.qs_apply(h, gb, None, pb)
+        want = orc.as_complex(orc.apply_circuit(orc.apply_circuit(init.copy(), n, ga), n, gb))
+        assert np.max(np.abs(q.qs_get_state(h) - want)) < TOL
+    finally:
+        q.qs_free(h)
+        q.qs_plan_free(pa)
+        q.qs_plan_free(pb)
+
+
 @pytest.mark.parametrize("n", [12, 14, 17, 21])
 def test_fused_brickwork(q, orc, arith, n):
     g = w.layered_u3_cz(n, 20, 1)
