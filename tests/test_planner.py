@@ -378,3 +378,31 @@ def test_kernel_ops_cover_the_pass_ops(q, n, maker, seed):
             assert ipa >= 12.0 * grouped - 1e-9
     finally:
         q.qs_plan_free(p)
+
+
+def test_features_of_parametrised_programs(q):
+    """Pass features need no parameters: a parametrised program (every rotation
+    reads a parameter) is featurised with generic angles, and gives the features of
+    the same program with generic explicit angles in its records; the kernel-op
+    part of every tile pass is filled in (at least one shared-memory sweep; limb
+    products where it has rotations)."""
+    n = 14
+    g, npar = w.hea_ansatz(n, 3)
+    explicit = g.copy()
+    for r in explicit:
+        if r["param_idx"] >= 0:
+            r["p"][0], r["p"][1], r["p"][2] = 1.1, 0.4, 2.3
+            r["param_idx"] = -1
+    p1 = q.qs_plan_create(n, g, q.PLAN_GREEDY, 5)
+    p2 = q.qs_plan_create(n, explicit, q.PLAN_GREEDY, 5)
+    try:
+        f1, f2 = q.qs_plan_features(p1, g), q.qs_plan_features(p2, explicit)
+        assert f1.shape == (q.qs_plan_get_stats(p1)["n_passes"], q._lib.PASS_FEATURES) and f1.shape == f2.shape
+        assert np.array_equal(f1, f2)
+        tile = f1[f1[:, 0] == 1.0]
+        assert len(tile) >= 1 and np.any(tile[:, 14] > 0) and np.all(tile[:, 24] > 0)
+        gate = f1[f1[:, 0] == 0.0]
+        assert np.all(gate[:, 14:] == 0.0)
+    finally:
+        q.qs_plan_free(p1)
+        q.qs_plan_free(p2)
